@@ -1,0 +1,143 @@
+/*
+ * spingp.h -- C ABI of the GB300 library for exact inference in state-space
+ * temporal Gaussian processes through their block-tridiagonal precision
+ * (SpInGP, Grigorievskiy, Lawrence & Sarkka, arXiv 1610.08035).
+ *
+ * Model (Sec. 2.1, Eq. ss1): z_{i+1} = A_i z_i + q_i, q_i ~ N(0, Q_i);
+ * y_i = H z_i + e_i, e_i ~ N(0, sigma_n^2), for sorted times t_0 <= ... <= t_{n-1},
+ * with A_i = expm(F (t_{i+1} - t_i)), Q_i = Pinf - A_i Pinf A_i^T and the first
+ * state z_0 ~ N(0, Pinf).  The stacked state covariance has a block-
+ * tridiagonal inverse (Theorem 1); the posterior precision is
+ * K~ = Kinv + G^T Sigma^-1 G with G = I_n (x) H and Sigma = sigma_n^2 I (Sec. 2.2).
+ *
+ * Conventions for every entry point below:
+ *   - All array arguments are DEVICE pointers to FP64 data owned by the
+ *     caller, on the current CUDA device; nothing is copied to the host.
+ *   - theta is a device array of spingp_num_params(model) entries: for each
+ *     component its parameters in the order listed at spingp_kind, then the
+ *     noise variance sigma_n^2 last.  Every entry must be finite and > 0.
+ *   - ws is caller-owned device scratch of at least
+ *     spingp_workspace_bytes(model, n, what) bytes, 256-byte aligned; the
+ *     library allocates no device memory on these paths.  One workspace must
+ *     not be used by two calls that can overlap on the GPU.
+ *   - stream is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued asynchronously.  Argument errors that the host can see are
+ *     returned at once and nothing is launched.  Errors that only the device
+ *     can see (unsorted or non-finite inputs, a non-positive theta entry, a
+ *     non-positive innovation variance) are recorded in a status word inside
+ *     ws: pass SPINGP_SYNC in flags to have the call synchronise the stream
+ *     and return that status, or call spingp_ws_status() later.  Without
+ *     SPINGP_SYNC the call launches kernels only (no host synchronisation,
+ *     no allocation) and may be captured into a CUDA graph.
+ *   - Outputs are written on the stream; their contents are unspecified when
+ *     the call reports an error.
+ */
+#ifndef SPINGP_H
+#define SPINGP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPINGP_OK = 0,
+    SPINGP_EINVAL = 1,       /* bad argument: NULL pointer, n < 1, bad theta, workspace too small */
+    SPINGP_ENOTSORTED = 2,   /* some t[i+1] < t[i] */
+    SPINGP_ENONFINITE = 3,   /* a time or an observation is NaN or infinite */
+    SPINGP_ENUMERIC = 4,     /* an innovation variance or a pivot was not positive and finite */
+    SPINGP_ECUDA = 5,        /* a CUDA runtime call failed */
+    SPINGP_ETIMEOUT = 6,     /* reserved for bounded device-side waits */
+    SPINGP_ENOMEM = 7,       /* host memory allocation failed */
+    SPINGP_EUNSUPPORTED = 8  /* model structure not implemented by this build */
+} spingp_status;
+
+/* Covariance families (Sec. 2.1).  Parameters per component, in theta order:
+ *   MATERN12/32/52: (lengthscale l, variance s); state dim 1/2/3; the
+ *       companion-form SDE of (d/dt + lam)^b with lam = sqrt(2b-1)/l
+ *       (Eq. ss_matern gives the 3/2 case).
+ *   PERIODIC (order J): (variance, lengthscale, period); state dim 2(J+1).
+ *   QUASIPERIODIC (order J, Matern envelope): (variance, lengthscale, period,
+ *       envelope lengthscale); state dim 2(J+1) x envelope dim (Eq. co2_1). */
+typedef enum {
+    SPINGP_MATERN12 = 1,
+    SPINGP_MATERN32 = 2,
+    SPINGP_MATERN52 = 3,
+    SPINGP_PERIODIC = 4,
+    SPINGP_QUASIPERIODIC = 5
+} spingp_kind;
+
+typedef struct {
+    int n_comp;          /* number of summed components (>= 1) */
+    const int* kinds;    /* n_comp spingp_kind values (host memory) */
+    const int* orders;   /* harmonic order J per component, or NULL */
+    const int* envs;     /* envelope kind per quasi-periodic component, or NULL */
+} spingp_model_desc;
+
+typedef struct spingp_model spingp_model;
+
+/* What a workspace is sized for. */
+typedef enum { SPINGP_WS_LOGLIK = 0, SPINGP_WS_GRAD = 1, SPINGP_WS_POSTERIOR = 2 } spingp_ws_kind;
+
+#define SPINGP_SYNC 1u
+
+/* Create a model handle from a host-side description (Sec. 2.1).  The handle
+ * holds host constants only; it owns no device memory.  Returns EINVAL for a
+ * malformed description and EUNSUPPORTED for a structure this build does not
+ * run on the GPU.  *out is set to NULL on error. */
+spingp_status spingp_model_create(const spingp_model_desc* desc, spingp_model** out);
+void spingp_model_destroy(spingp_model* model);
+
+/* Number of theta entries (noise variance included) and state dimension b. */
+int spingp_num_params(const spingp_model* model);
+int spingp_state_dim(const spingp_model* model);
+
+/* Chunk length L: the number of consecutive steps one GPU thread eliminates
+ * sequentially before the odd-even reduction across chunks.  0 selects the
+ * built-in default.  Returns EINVAL outside [8, 65536]. */
+spingp_status spingp_set_chunk_len(spingp_model* model, int chunk_len);
+int spingp_get_chunk_len(const spingp_model* model, int64_t n);
+
+/* Workspace bytes needed for one series of n steps. */
+size_t spingp_workspace_bytes(const spingp_model* model, int64_t n, spingp_ws_kind what);
+
+/* Log marginal likelihood (Eq. ml2), written to ll_out[0].  Computed through
+ * the determinant lemma (Eq. det_1) and subproblems 1 and 3: a sequential
+ * elimination inside chunks of L steps, an odd-even cyclic reduction of the
+ * chunk Schur complements, and the prediction-error decomposition within each
+ * chunk.  t: n sorted times; y: n observations. */
+spingp_status spingp_loglik(const spingp_model* model, const double* t, const double* y, int64_t n,
+                            const double* theta, double* ll_out,
+                            void* ws, size_t ws_bytes, unsigned flags, void* stream);
+
+/* Log-likelihood and its gradient with respect to every theta entry (Sec. 2.4,
+ * the data-fit derivative and the trace term of Eq. dd1), written to ll_out[0]
+ * and grad_out[0 .. num_params-1].  The trace of subproblem 4 is evaluated
+ * through the selected inverse of K~ in adjoint form: a reverse sweep per
+ * chunk, seeded by the reduced suffix information, chained through
+ * d expm(F dt)/dtheta and dQ/dtheta. */
+spingp_status spingp_grad(const spingp_model* model, const double* t, const double* y, int64_t n,
+                          const double* theta, double* ll_out, double* grad_out,
+                          void* ws, size_t ws_bytes, unsigned flags, void* stream);
+
+/* Posterior of the latent function at the training times (Eq. mean6,
+ * subproblem 1, and the diagonal of Eq. k3, subproblem 2): mean_out[i] = H m^s_i
+ * and var_out[i] = H P^s_i H^T (latent variance, no noise added), where P^s_i
+ * are the diagonal blocks of inv(K~).  ll_out may be NULL. */
+spingp_status spingp_posterior(const spingp_model* model, const double* t, const double* y, int64_t n,
+                               const double* theta, double* ll_out, double* mean_out, double* var_out,
+                               void* ws, size_t ws_bytes, unsigned flags, void* stream);
+
+/* Synchronise the stream and return the device status recorded in ws by the
+ * last call that used it (SPINGP_OK if none). */
+spingp_status spingp_ws_status(void* ws, void* stream);
+
+const char* spingp_status_str(spingp_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPINGP_H */

@@ -659,7 +659,8 @@ static int two_filter_adjoint(int b, const double* mb, const double* Pb, const d
 /* Log-likelihood and its gradient with respect to all P parameters.
    Optionally also the posterior mean / latent variance from the same pass. */
 int oseq_grad(int ncomp, const int* kind, const int* order, const int* env, const double* th,
-              const double* t, const double* y, long n, double* ll, double* grad, double* mean, double* var) {
+              const double* t, const double* y, long n, double* ll, double* grad, double* mean, double* var,
+              double* gabs) {
     om_t om; int st = om_init(&om, ncomp, kind, order, env);
     if (st) return st;
     st = check_inputs(th, om.P, t, y, n);
@@ -677,7 +678,7 @@ int oseq_grad(int ncomp, const int* kind, const int* order, const int* env, cons
     double Pinf[OB2], H[OMAXB], A[OB2], Q[OB2];
     om_pinf(&om, th, Pinf, dPinf);
     om_H(&om, H);
-    for (int p = 0; p < P; ++p) grad[p] = 0.0;
+    for (int p = 0; p < P; ++p) { grad[p] = 0.0; if (gabs) gabs[p] = 0.0; }
     /* backward information of y_{n-1}: J = H^T H / s2, eta = H^T y / s2 */
     double J[OB2], eta[OMAXB];
     for (int r = 0; r < b; ++r) { eta[r] = H[r] * y[n - 1] / s2; for (int c = 0; c < b; ++c) J[r * b + c] = H[r] * H[c] / s2; }
@@ -698,19 +699,28 @@ int oseq_grad(int ncomp, const int* kind, const int* order, const int* env, cons
             double Abar[OB2], X[OB2];
             mm(b, Qbar, A, X); mm(b, X, Pp, T);
             for (int r = 0; r < b; ++r) for (int c = 0; c < b; ++c) Abar[r * b + c] = v[r] * m[c] + 2.0 * T[r * b + c];
-            for (int p = 0; p < P; ++p)
-                grad[p] += mdot(b, Abar, dA + (size_t)p * b * b) + mdot(b, Qbar, dQ + (size_t)p * b * b);
+            for (int p = 0; p < P; ++p) {
+                double term = mdot(b, Abar, dA + (size_t)p * b * b) + mdot(b, Qbar, dQ + (size_t)p * b * b);
+                grad[p] += term;
+                if (gabs) gabs[p] += fabs(term);
+            }
         } else {
             memset(mb, 0, sizeof(double) * b);
             mcopy(b, Pinf, Pb);
             if ((st = two_filter_adjoint(b, mb, Pb, J, eta, v, Qbar, msm, Psm))) goto out;
-            for (int p = 0; p < P; ++p) grad[p] += mdot(b, Qbar, dPinf + (size_t)p * b * b);
+            for (int p = 0; p < P; ++p) {
+                double term = mdot(b, Qbar, dPinf + (size_t)p * b * b);
+                grad[p] += term;
+                if (gabs) gabs[p] += fabs(term);
+            }
         }
         /* observation noise: d/ds2 sum_i log N(y_i; H z_i, s2) averaged over the posterior */
         double hm = 0.0, hph = 0.0;
         for (int r = 0; r < b; ++r) { hm += H[r] * msm[r]; for (int c = 0; c < b; ++c) hph += H[r] * Psm[r * b + c] * H[c]; }
         double e = y[i] - hm;
-        gs2 += (e * e + hph) / (2.0 * s2 * s2) - 0.5 / s2;
+        double gterm = (e * e + hph) / (2.0 * s2 * s2) - 0.5 / s2;
+        gs2 += gterm;
+        if (gabs) gabs[P - 1] += fabs(gterm);
         if (mean) mean[i] = hm;
         if (var) var[i] = hph;
         if (i > 0) {

@@ -51,7 +51,7 @@ def bind(path):
     lib.oseq_discretize.argtypes = [ctypes.c_int, I, I, I, D, ctypes.c_double, D, D, D, D, D, D]
     lib.oseq_loglik.argtypes = [ctypes.c_int, I, I, I, D, D, D, L, D]
     lib.oseq_smoother.argtypes = [ctypes.c_int, I, I, I, D, D, D, L, D, D, D, D, D, D]
-    lib.oseq_grad.argtypes = [ctypes.c_int, I, I, I, D, D, D, L, D, D, D, D]
+    lib.oseq_grad.argtypes = [ctypes.c_int, I, I, I, D, D, D, L, D, D, D, D, D]
     lib.oseq_sample.argtypes = [ctypes.c_int, I, I, I, D, D, L, D, D]
     for f in ("oseq_dims", "oseq_continuous", "oseq_discretize", "oseq_loglik",
               "oseq_smoother", "oseq_grad", "oseq_sample"):
@@ -146,21 +146,27 @@ def smoother(spec, theta, t, y, blocks=False):
     return out
 
 
-def grad(spec, theta, t, y, posterior=False):
+def grad(spec, theta, t, y, posterior=False, l1=False):
     """Log-likelihood and gradient with respect to every entry of theta
     (two-filter adjoint).  With posterior=True also the mean / latent variance
-    obtained from the same two filters."""
+    obtained from the same two filters.  With l1=True also the sum over steps
+    of the absolute per-step contributions to each gradient entry (the scale
+    against which cancellation in the sum is judged); it is appended last."""
     lib = _load()
     t = _f64(t); y = _f64(y)
     n = len(t)
     ll = np.zeros(1); g = np.zeros(n_params(spec))
     mean = np.zeros(n) if posterior else None
     var = np.zeros(n) if posterior else None
+    gabs = np.zeros(n_params(spec)) if l1 else None
     _check(lib.oseq_grad(*_spec_args(spec), _dp(_theta(spec, theta)), _dp(t), _dp(y), n, _dp(ll), _dp(g),
-                         _dp(mean), _dp(var)))
+                         _dp(mean), _dp(var), _dp(gabs)))
+    out = (float(ll[0]), g)
     if posterior:
-        return float(ll[0]), g, mean, var
-    return float(ll[0]), g
+        out = out + (mean, var)
+    if l1:
+        out = out + (gabs,)
+    return out
 
 
 def sample(spec, theta, t, eps):

@@ -1,0 +1,172 @@
+// capi.cu -- the extern "C" boundary declared in include/spingp.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <mutex>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "spingp.h"
+#include "internal.h"
+
+#define SPG_MAXC 8
+#define SPG_MAXDEV 64
+
+struct spingp_model {
+    int ncomp;
+    int kinds[SPG_MAXC], orders[SPG_MAXC], envs[SPG_MAXC];
+    int b, P;
+    int chunk_len;   // 0 = default
+};
+
+namespace {
+
+std::mutex g_prep_mu;
+bool g_prepared[SPG_MAXDEV];
+
+// one-time per-device set-up (shared-memory opt-in of the scan kernels)
+spingp_status prepare_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= SPG_MAXDEV) return SPINGP_ECUDA;
+    std::lock_guard<std::mutex> lock(g_prep_mu);
+    if (!g_prepared[dev]) {
+        if (spg::matern_prepare()) return SPINGP_ECUDA;
+        g_prepared[dev] = true;
+    }
+    return SPINGP_OK;
+}
+
+int matern_dim(int kind) { return kind; }
+
+int64_t default_chunk(int64_t n) {
+    // about 2e4 chunks (enough threads to cover the GPU), L a power of two in [16, 512]
+    int64_t L = 16;
+    while (L < 512 && L * 20000 < n) L *= 2;
+    return L;
+}
+
+int64_t chunk_len(const spingp_model* m, int64_t n) {
+    return m->chunk_len > 0 ? (int64_t)m->chunk_len : default_chunk(n);
+}
+
+bool single_matern(const spingp_model* m) { return m->ncomp == 1 && m->kinds[0] >= 1 && m->kinds[0] <= 3; }
+
+spingp_status run(const spingp_model* m, int mode, const double* t, const double* y, int64_t n,
+                  const double* theta, double* ll, double* grad, double* mean, double* var, void* ws,
+                  size_t ws_bytes, unsigned flags, void* stream) {
+    if (!m || !t || !y || !theta || !ws || n < 1) return SPINGP_EINVAL;
+    if (((uintptr_t)ws & 255u) != 0) return SPINGP_EINVAL;
+    if (!single_matern(m)) return SPINGP_EUNSUPPORTED;
+    const int64_t L = chunk_len(m, n);
+    if (ws_bytes < spg::matern_ws_bytes(m->b, n, L, mode)) return SPINGP_EINVAL;
+    spingp_status st = prepare_device();
+    if (st != SPINGP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (spg::matern_run(m->b, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s)) return SPINGP_ECUDA;
+    if (flags & SPINGP_SYNC) return spingp_ws_status(ws, stream);
+    return SPINGP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+spingp_status spingp_model_create(const spingp_model_desc* d, spingp_model** out) {
+    if (!out) return SPINGP_EINVAL;
+    *out = NULL;
+    if (!d || d->n_comp < 1 || d->n_comp > SPG_MAXC || !d->kinds) return SPINGP_EINVAL;
+    spingp_model m;
+    memset(&m, 0, sizeof(m));
+    m.ncomp = d->n_comp;
+    for (int c = 0; c < d->n_comp; ++c) {
+        const int k = d->kinds[c];
+        const int J = d->orders ? d->orders[c] : 0;
+        const int env = d->envs ? d->envs[c] : 0;
+        m.kinds[c] = k; m.orders[c] = J; m.envs[c] = env;
+        if (k >= SPINGP_MATERN12 && k <= SPINGP_MATERN52) { m.b += matern_dim(k); m.P += 2; }
+        else if (k == SPINGP_PERIODIC) { if (J < 0 || J > 64) return SPINGP_EINVAL; m.b += 2 * (J + 1); m.P += 3; }
+        else if (k == SPINGP_QUASIPERIODIC) {
+            if (J < 0 || J > 64 || env < SPINGP_MATERN12 || env > SPINGP_MATERN52) return SPINGP_EINVAL;
+            m.b += 2 * (J + 1) * matern_dim(env); m.P += 4;
+        } else return SPINGP_EINVAL;
+    }
+    m.P += 1;
+    if (!single_matern(&m)) return SPINGP_EUNSUPPORTED;
+    spingp_model* h = (spingp_model*)malloc(sizeof(spingp_model));
+    if (!h) return SPINGP_ENOMEM;
+    *h = m;
+    *out = h;
+    return SPINGP_OK;
+}
+
+void spingp_model_destroy(spingp_model* m) { free(m); }
+
+int spingp_num_params(const spingp_model* m) { return m ? m->P : -1; }
+int spingp_state_dim(const spingp_model* m) { return m ? m->b : -1; }
+
+spingp_status spingp_set_chunk_len(spingp_model* m, int L) {
+    if (!m || (L != 0 && (L < 8 || L > 65536))) return SPINGP_EINVAL;
+    m->chunk_len = L;
+    return SPINGP_OK;
+}
+
+int spingp_get_chunk_len(const spingp_model* m, int64_t n) { return m ? (int)chunk_len(m, n) : -1; }
+
+size_t spingp_workspace_bytes(const spingp_model* m, int64_t n, spingp_ws_kind what) {
+    if (!m || n < 1 || !single_matern(m)) return 0;
+    const int mode = what == SPINGP_WS_GRAD ? spg::MODE_GRAD
+                   : what == SPINGP_WS_POSTERIOR ? spg::MODE_POSTERIOR : spg::MODE_LOGLIK;
+    return spg::matern_ws_bytes(m->b, n, chunk_len(m, n), mode);
+}
+
+spingp_status spingp_loglik(const spingp_model* m, const double* t, const double* y, int64_t n,
+                            const double* theta, double* ll_out, void* ws, size_t ws_bytes, unsigned flags,
+                            void* stream) {
+    if (!ll_out) return SPINGP_EINVAL;
+    return run(m, spg::MODE_LOGLIK, t, y, n, theta, ll_out, NULL, NULL, NULL, ws, ws_bytes, flags, stream);
+}
+
+spingp_status spingp_grad(const spingp_model* m, const double* t, const double* y, int64_t n, const double* theta,
+                          double* ll_out, double* grad_out, void* ws, size_t ws_bytes, unsigned flags,
+                          void* stream) {
+    if (!ll_out || !grad_out) return SPINGP_EINVAL;
+    return run(m, spg::MODE_GRAD, t, y, n, theta, ll_out, grad_out, NULL, NULL, ws, ws_bytes, flags, stream);
+}
+
+spingp_status spingp_posterior(const spingp_model* m, const double* t, const double* y, int64_t n,
+                               const double* theta, double* ll_out, double* mean_out, double* var_out, void* ws,
+                               size_t ws_bytes, unsigned flags, void* stream) {
+    if (!mean_out || !var_out) return SPINGP_EINVAL;
+    return run(m, spg::MODE_POSTERIOR, t, y, n, theta, ll_out, NULL, mean_out, var_out, ws, ws_bytes, flags,
+               stream);
+}
+
+spingp_status spingp_ws_status(void* ws, void* stream) {
+    if (!ws) return SPINGP_EINVAL;
+    int bits = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&bits, ws, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SPINGP_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SPINGP_ECUDA;
+    if (bits & spg::ST_EINVAL) return SPINGP_EINVAL;
+    if (bits & spg::ST_ENONFINITE) return SPINGP_ENONFINITE;
+    if (bits & spg::ST_ENOTSORTED) return SPINGP_ENOTSORTED;
+    if (bits & spg::ST_ENUMERIC) return SPINGP_ENUMERIC;
+    return SPINGP_OK;
+}
+
+const char* spingp_status_str(spingp_status s) {
+    switch (s) {
+    case SPINGP_OK: return "ok";
+    case SPINGP_EINVAL: return "invalid argument";
+    case SPINGP_ENOTSORTED: return "times are not sorted";
+    case SPINGP_ENONFINITE: return "non-finite time or observation";
+    case SPINGP_ENUMERIC: return "non-positive innovation variance or pivot";
+    case SPINGP_ECUDA: return "CUDA runtime error";
+    case SPINGP_ETIMEOUT: return "device wait timed out";
+    case SPINGP_ENOMEM: return "out of host memory";
+    case SPINGP_EUNSUPPORTED: return "model not supported by this build";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

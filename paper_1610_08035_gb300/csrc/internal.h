@@ -1,0 +1,21 @@
+// internal.h -- declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+namespace spg {
+
+// device status bits (the status word at the start of every workspace)
+enum { ST_EINVAL = 1 << 1, ST_ENOTSORTED = 1 << 2, ST_ENONFINITE = 1 << 3, ST_ENUMERIC = 1 << 4 };
+
+// what a chain run computes
+enum { MODE_LOGLIK = 0, MODE_GRAD = 1, MODE_POSTERIOR = 2 };
+
+size_t matern_ws_bytes(int b, int64_t n, int64_t L, int mode);
+int matern_prepare();
+int matern_run(int b, int mode, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
+               double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws, cudaStream_t st);
+
+}  // namespace spg

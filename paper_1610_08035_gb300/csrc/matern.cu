@@ -1,0 +1,690 @@
+// matern.cu -- the hot path for Matern chains (state dimension b = 1, 2, 3).
+//
+// One series of n steps is cut into chunks of L consecutive steps.
+//   k_fold      one thread per chunk: discretisation (Sec. 2.1) and sequential
+//               elimination of the chunk's interior nodes of K~ (Sec. 3.1,
+//               subproblems 1 and 3) into one boundary element (chain.cuh).
+//   k_scan_tile odd-even block cyclic reduction of the chunk elements: each
+//               CTA pairs neighbouring elements level by level (eliminating
+//               every other boundary node), recursing over CTA totals across
+//               the grid; the back-substitution sweep returns, for every
+//               chunk, the filtered state before it (prefix) and the
+//               information of all observations after it (suffix).
+//   k_chunk     one thread per chunk: the prediction-error decomposition of
+//               the log-likelihood (Eq. ml2 via Eq. det_1) from the chunk's
+//               prefix state; for the gradient and the posterior, a reverse
+//               sweep seeded by the suffix information that yields the
+//               selected inverse of K~ in adjoint form and the per-step
+//               hyperparameter adjoints (Sec. 2.4, Eq. dd1).
+//   k_finalize  fixed-order reduction of the per-chunk partial sums.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "chain.cuh"
+#include "internal.h"
+
+namespace spg {
+
+static constexpr double LOG_2PI = 1.8378770664093454836;
+
+struct ChainArgs {
+    const double* t;
+    const double* y;
+    int64_t n;
+    int64_t L;
+    int64_t nchunks;
+    const double* theta;
+    int* status;
+};
+
+template <int B>
+__device__ __forceinline__ bool theta_ok(double ell, double sf, double s2) {
+    return ell > 0.0 && sf > 0.0 && s2 > 0.0 && isfinite(ell) && isfinite(sf) && isfinite(s2);
+}
+
+// ------------------------------------------------------------------ k_fold
+
+template <int B>
+__global__ void __launch_bounds__(128) k_fold(ChainArgs a, double* __restrict__ E) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= a.nchunks) return;
+    const double ell = a.theta[0], sf = a.theta[1], s2 = a.theta[2];
+    int bad = theta_ok<B>(ell, sf, s2) ? 0 : ST_EINVAL;
+    const double lam = sqrt(2.0 * B - 1.0) / ell;
+    const int64_t s = c * a.L;
+    const int64_t e = min(a.n, s + a.L);
+    Elem<B> el;
+    elem_identity<B>(el);
+    if (s == 0) {
+        // the first state has the stationary prior: no dependence on an earlier node
+#pragma unroll
+        for (int i = 0; i < B; ++i)
+#pragma unroll
+            for (int j = 0; j < B; ++j) { el.A[i][j] = 0.0; el.C[i][j] = sf * p1<B>(i, j); }
+    }
+    double tp = (s > 0) ? a.t[s - 1] : 0.0;
+    for (int64_t i = s; i < e; ++i) {
+        const double ti = a.t[i], yi = a.y[i];
+        if (!isfinite(ti) || !isfinite(yi)) bad |= ST_ENONFINITE;
+        if (i > 0) {
+            const double dt = ti - tp;
+            if (dt < 0.0) bad |= ST_ENOTSORTED;
+            const double x = lam * dt;
+            double Ph[B][B], T[B][B], D[B][B];
+            phi<B>(x, exp(-x), Ph);
+            // A <- Phi A,  bv <- Phi bv,  C <- Phi (C - Pinf) Phi^T + Pinf
+            mat_mul<B>(Ph, el.A, T);
+#pragma unroll
+            for (int r = 0; r < B; ++r)
+#pragma unroll
+                for (int q = 0; q < B; ++q) el.A[r][q] = T[r][q];
+            double w[B];
+            mat_vec<B>(Ph, el.bv, w);
+#pragma unroll
+            for (int r = 0; r < B; ++r) el.bv[r] = w[r];
+#pragma unroll
+            for (int r = 0; r < B; ++r)
+#pragma unroll
+                for (int q = 0; q < B; ++q) D[r][q] = el.C[r][q] - sf * p1<B>(r, q);
+            mat_mul<B>(Ph, D, T);
+            mat_mul_t_sym<B>(T, Ph, el.C);
+#pragma unroll
+            for (int r = 0; r < B; ++r)
+#pragma unroll
+                for (int q = 0; q < B; ++q) el.C[r][q] += sf * p1<B>(r, q);
+        }
+        // condition on y_i: innovation of y_i given the node before the chunk
+        const double S = el.C[0][0] + s2;
+        const double rS = 1.0 / S;
+        const double res = yi - el.bv[0];
+        double a0[B], c0[B];
+#pragma unroll
+        for (int r = 0; r < B; ++r) { a0[r] = el.A[0][r]; c0[r] = el.C[r][0]; }
+        const double rr = res * rS;
+#pragma unroll
+        for (int r = 0; r < B; ++r) {
+            el.eta[r] = fma(a0[r], rr, el.eta[r]);
+            const double ar = a0[r] * rS;
+#pragma unroll
+            for (int q = r; q < B; ++q) { el.J[r][q] = fma(ar, a0[q], el.J[r][q]); el.J[q][r] = el.J[r][q]; }
+        }
+#pragma unroll
+        for (int r = 0; r < B; ++r) {
+            el.bv[r] = fma(c0[r], rr, el.bv[r]);
+            const double g = c0[r] * rS;
+#pragma unroll
+            for (int q = 0; q < B; ++q) el.A[r][q] = fma(-g, a0[q], el.A[r][q]);
+#pragma unroll
+            for (int q = r; q < B; ++q) { el.C[r][q] = fma(-g, c0[q], el.C[r][q]); el.C[q][r] = el.C[r][q]; }
+        }
+        tp = ti;
+    }
+    if (bad) atomicOr(a.status, bad);
+    elem_store<B>(E, a.nchunks, c, el);
+}
+
+// ------------------------------------------------------------------ k_scan_tile (odd-even reduction)
+
+template <int B, int TS>
+struct ScanSmem {
+    static constexpr int NE = Dims<B>::NE, NM = Dims<B>::NM;
+    static constexpr size_t bytes = sizeof(double) * (size_t)(2 * TS) * (NE + 2 * NM);
+};
+
+template <int TS>
+__device__ __forceinline__ int node_off(int level) { return 2 * TS - ((2 * TS) >> level); }
+
+template <int B>
+__device__ __forceinline__ void elem_to_smem(double* p, const Elem<B>& e) { elem_store<B>(p, 1, 0, e); }
+template <int B>
+__device__ __forceinline__ void elem_from_smem(const double* p, Elem<B>& e) { elem_load<B>(p, 1, 0, e); }
+
+// One tile = TS threads x G consecutive elements.  Up-sweep: each thread
+// eliminates its G elements sequentially, then neighbouring thread totals are
+// paired level by level (odd-even).  With DOWN, the back-substitution sweep
+// writes, for every element k, the state before it (pre_out, NM fields) and the
+// information after it (suf_out, NM fields), given the tile's own prefix and
+// suffix (pre_in / suf_in, NULL at the top level).
+template <int B, int TS, bool DOWN>
+__global__ void __launch_bounds__(TS) k_scan_tile(const double* __restrict__ E, int64_t ne, int G,
+                                                   double* __restrict__ totals, int64_t ntiles,
+                                                   const double* __restrict__ pre_in, const double* __restrict__ suf_in,
+                                                   double* __restrict__ pre_out, double* __restrict__ suf_out) {
+    constexpr int NE = Dims<B>::NE, NM = Dims<B>::NM;
+    constexpr int LV = (TS == 32) ? 5 : (TS == 64) ? 6 : (TS == 128) ? 7 : 8;
+    static_assert((1 << LV) == TS, "TS must be 32, 64, 128 or 256");
+    extern __shared__ double sm[];
+    double* nodes = sm;
+    double* preN = nodes + 2 * TS * NE;
+    double* sufN = preN + 2 * TS * NM;
+
+    const int tid = threadIdx.x;
+    const int64_t tile = blockIdx.x;
+    const int64_t lo = tile * (int64_t)TS * G + (int64_t)tid * G;
+    const int64_t hi = min(ne, lo + G);
+
+    Elem<B> agg;
+    if (lo < hi) {
+        elem_load<B>(E, ne, lo, agg);
+        for (int64_t k = lo + 1; k < hi; ++k) {
+            Elem<B> e, r;
+            elem_load<B>(E, ne, k, e);
+            combine<B>(agg, e, r);
+            agg = r;
+        }
+    } else {
+        elem_identity<B>(agg);
+    }
+    elem_to_smem<B>(nodes + (size_t)tid * NE, agg);
+    __syncthreads();
+#pragma unroll 1
+    for (int l = 1; l <= LV; ++l) {
+        const int cnt = TS >> l;
+        if (tid < cnt) {
+            Elem<B> x, y, r;
+            elem_from_smem<B>(nodes + (size_t)(node_off<TS>(l - 1) + 2 * tid) * NE, x);
+            elem_from_smem<B>(nodes + (size_t)(node_off<TS>(l - 1) + 2 * tid + 1) * NE, y);
+            combine<B>(x, y, r);
+            elem_to_smem<B>(nodes + (size_t)(node_off<TS>(l) + tid) * NE, r);
+        }
+        __syncthreads();
+    }
+    if constexpr (!DOWN) {
+        if (tid == 0) {
+            Elem<B> r;
+            elem_from_smem<B>(nodes + (size_t)node_off<TS>(LV) * NE, r);
+            elem_store<B>(totals, ntiles, tile, r);
+        }
+        return;
+    } else {
+        if (tid == 0) {
+            double v[B], S[B][B];
+#pragma unroll
+            for (int i = 0; i < B; ++i) { v[i] = 0.0;
+#pragma unroll
+                for (int j = 0; j < B; ++j) S[i][j] = 0.0; }
+            if (pre_in) vs_load<B>(pre_in, ntiles, tile, v, S);
+            vs_store<B>(preN + (size_t)node_off<TS>(LV) * NM, 1, 0, v, S);
+#pragma unroll
+            for (int i = 0; i < B; ++i) { v[i] = 0.0;
+#pragma unroll
+                for (int j = 0; j < B; ++j) S[i][j] = 0.0; }
+            if (suf_in) vs_load<B>(suf_in, ntiles, tile, v, S);
+            vs_store<B>(sufN + (size_t)node_off<TS>(LV) * NM, 1, 0, v, S);
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int l = LV; l >= 1; --l) {
+            const int cnt = TS >> (l - 1);
+            if (tid < cnt) {
+                const int parent = tid >> 1;
+                double pm[B], pP[B][B], sv[B], sJ[B][B], om[B], oP[B][B];
+                vs_load<B>(preN + (size_t)(node_off<TS>(l) + parent) * NM, 1, 0, pm, pP);
+                vs_load<B>(sufN + (size_t)(node_off<TS>(l) + parent) * NM, 1, 0, sv, sJ);
+                Elem<B> sib;
+                if (tid & 1) {
+                    elem_from_smem<B>(nodes + (size_t)(node_off<TS>(l - 1) + tid - 1) * NE, sib);
+                    state_through<B>(pm, pP, sib, om, oP);
+                    vs_store<B>(preN + (size_t)(node_off<TS>(l - 1) + tid) * NM, 1, 0, om, oP);
+                    vs_store<B>(sufN + (size_t)(node_off<TS>(l - 1) + tid) * NM, 1, 0, sv, sJ);
+                } else {
+                    elem_from_smem<B>(nodes + (size_t)(node_off<TS>(l - 1) + tid + 1) * NE, sib);
+                    info_through<B>(sib, sv, sJ, om, oP);
+                    vs_store<B>(preN + (size_t)(node_off<TS>(l - 1) + tid) * NM, 1, 0, pm, pP);
+                    vs_store<B>(sufN + (size_t)(node_off<TS>(l - 1) + tid) * NM, 1, 0, om, oP);
+                }
+            }
+            __syncthreads();
+        }
+        // walk this thread's own elements
+        double m[B], P[B][B];
+        vs_load<B>(preN + (size_t)tid * NM, 1, 0, m, P);
+        for (int64_t k = lo; k < hi; ++k) {
+            vs_store<B>(pre_out, ne, k, m, P);
+            if (k + 1 < hi) {
+                Elem<B> e;
+                double mo[B], Po[B][B];
+                elem_load<B>(E, ne, k, e);
+                state_through<B>(m, P, e, mo, Po);
+#pragma unroll
+                for (int i = 0; i < B; ++i) { m[i] = mo[i];
+#pragma unroll
+                    for (int j = 0; j < B; ++j) P[i][j] = Po[i][j]; }
+            }
+        }
+        vs_load<B>(sufN + (size_t)tid * NM, 1, 0, m, P);
+        for (int64_t k = hi - 1; k >= lo; --k) {
+            vs_store<B>(suf_out, ne, k, m, P);
+            if (k > lo) {
+                Elem<B> e;
+                double mo[B], Po[B][B];
+                elem_load<B>(E, ne, k, e);
+                info_through<B>(e, m, P, mo, Po);
+#pragma unroll
+                for (int i = 0; i < B; ++i) { m[i] = mo[i];
+#pragma unroll
+                    for (int j = 0; j < B; ++j) P[i][j] = Po[i][j]; }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ k_chunk (forward, then reverse sweep)
+
+// per-chunk partial sums: ll, d/dlam, d/d(s_n), the P1-adjoint (packed)
+template <int B> struct Acc { static constexpr int N = 3 + Dims<B>::NS; };
+// per-step stored values: predicted mean (B), predicted covariance (packed), innovation, exp(-x)
+template <int B> struct Stored { static constexpr int N = B + Dims<B>::NS + 2; };
+
+template <int B, int MODE>
+__global__ void __launch_bounds__(128) k_chunk(ChainArgs a, const double* __restrict__ pre,
+                                               const double* __restrict__ suf, double* __restrict__ store,
+                                               double* __restrict__ part, double* __restrict__ mean_out,
+                                               double* __restrict__ var_out) {
+    constexpr int NS = Dims<B>::NS;
+    constexpr int NF = Stored<B>::N;
+    constexpr bool BWD = (MODE != MODE_LOGLIK);
+    constexpr bool GRAD = (MODE == MODE_GRAD);
+    constexpr bool POST = (MODE == MODE_POSTERIOR);
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= a.nchunks) return;
+    const int64_t nc = a.nchunks;
+    const double ell = a.theta[0], sf = a.theta[1], s2 = a.theta[2];
+    const double lam = sqrt(2.0 * B - 1.0) / ell;
+    const int64_t s = c * a.L;
+    const int64_t e = min(a.n, s + a.L);
+    int bad = 0;
+
+    double m[B], P[B][B];
+    if (c > 0) {
+        vs_load<B>(pre, nc, c, m, P);
+    } else {
+#pragma unroll
+        for (int i = 0; i < B; ++i) { m[i] = 0.0;
+#pragma unroll
+            for (int j = 0; j < B; ++j) P[i][j] = 0.0; }
+    }
+    double acc = 0.0;   // sum of v^2/S + log S
+    double tp = (s > 0) ? a.t[s - 1] : 0.0;
+    for (int64_t i = s; i < e; ++i) {
+        const double ti = a.t[i], yi = a.y[i];
+        double mb[B], Pb[B][B], ex = 1.0;
+        if (i == 0) {
+#pragma unroll
+            for (int r = 0; r < B; ++r) { mb[r] = 0.0;
+#pragma unroll
+                for (int q = 0; q < B; ++q) Pb[r][q] = sf * p1<B>(r, q); }
+        } else {
+            const double x = lam * (ti - tp);
+            ex = exp(-x);
+            double Ph[B][B], D[B][B], T[B][B];
+            phi<B>(x, ex, Ph);
+            mat_vec<B>(Ph, m, mb);
+#pragma unroll
+            for (int r = 0; r < B; ++r)
+#pragma unroll
+                for (int q = 0; q < B; ++q) D[r][q] = P[r][q] - sf * p1<B>(r, q);
+            mat_mul<B>(Ph, D, T);
+            mat_mul_t_sym<B>(T, Ph, Pb);
+#pragma unroll
+            for (int r = 0; r < B; ++r)
+#pragma unroll
+                for (int q = 0; q < B; ++q) Pb[r][q] += sf * p1<B>(r, q);
+        }
+        const double S = Pb[0][0] + s2;
+        if (!(S > 0.0) || !isfinite(S)) bad |= ST_ENUMERIC;
+        const double rS = 1.0 / S;
+        const double v = yi - mb[0];
+        acc += fma(v * v, rS, log(S));
+        if constexpr (BWD) {
+            const int64_t j = i - s;
+            double* st = store + (j * NF) * nc + c;
+            int f = 0;
+#pragma unroll
+            for (int r = 0; r < B; ++r) st[(f++) * nc] = mb[r];
+#pragma unroll
+            for (int r = 0; r < B; ++r)
+#pragma unroll
+                for (int q = r; q < B; ++q) st[(f++) * nc] = Pb[r][q];
+            st[(f++) * nc] = v;
+            st[(f++) * nc] = ex;
+        }
+        const double vr = v * rS;
+#pragma unroll
+        for (int r = 0; r < B; ++r) {
+            m[r] = fma(Pb[r][0], vr, mb[r]);
+            const double g = Pb[r][0] * rS;
+#pragma unroll
+            for (int q = r; q < B; ++q) { P[r][q] = fma(-g, Pb[q][0], Pb[r][q]); P[q][r] = P[r][q]; }
+        }
+        tp = ti;
+    }
+    const double llp = -0.5 * (acc + (double)(e - s) * LOG_2PI);
+    if (bad) atomicOr(a.status, bad);
+    if constexpr (!BWD) {
+        part[c] = llp;
+        return;
+    } else {
+        // adjoint of the filtered state at the chunk's last step from the
+        // information of all later observations: W = (I + J P)^-1,
+        // lh = -W (eta - J m), Lh = W J
+        double eta[B], J[B][B];
+        if (c + 1 < nc) {
+            vs_load<B>(suf, nc, c, eta, J);
+        } else {
+#pragma unroll
+            for (int i = 0; i < B; ++i) { eta[i] = 0.0;
+#pragma unroll
+                for (int j = 0; j < B; ++j) J[i][j] = 0.0; }
+        }
+        double lh[B], Lh[B][B];
+        {
+            double N[B][B], W[B][B], w[B];
+            mat_mul<B>(J, P, N);
+#pragma unroll
+            for (int i = 0; i < B; ++i) N[i][i] += 1.0;
+            inv_pp<B>(N, W);
+            mat_vec<B>(J, m, w);
+#pragma unroll
+            for (int i = 0; i < B; ++i) w[i] = eta[i] - w[i];
+            mat_vec<B>(W, w, lh);
+#pragma unroll
+            for (int i = 0; i < B; ++i) lh[i] = -lh[i];
+            mat_mul<B>(W, J, Lh);
+            symmetrize<B>(Lh);
+        }
+        double gl = 0.0, gs = 0.0, GP[B][B];
+#pragma unroll
+        for (int i = 0; i < B; ++i)
+#pragma unroll
+            for (int j = 0; j < B; ++j) GP[i][j] = 0.0;
+        for (int64_t i = e - 1; i >= s; --i) {
+            const int64_t j = i - s;
+            const double* st = store + (j * NF) * nc + c;
+            double mb[B], Pb[B][B];
+            int f = 0;
+#pragma unroll
+            for (int r = 0; r < B; ++r) mb[r] = st[(f++) * nc];
+#pragma unroll
+            for (int r = 0; r < B; ++r)
+#pragma unroll
+                for (int q = r; q < B; ++q) { Pb[r][q] = st[(f++) * nc]; Pb[q][r] = Pb[r][q]; }
+            const double v = st[(f++) * nc];
+            const double ex = st[(f++) * nc];
+            const double S = Pb[0][0] + s2;
+            const double rS = 1.0 / S;
+            double k[B];
+#pragma unroll
+            for (int r = 0; r < B; ++r) k[r] = Pb[r][0] * rS;
+            double kl = 0.0, u[B], kuk = 0.0;
+#pragma unroll
+            for (int r = 0; r < B; ++r) kl = fma(k[r], lh[r], kl);
+            mat_vec<B>(Lh, k, u);
+#pragma unroll
+            for (int r = 0; r < B; ++r) kuk = fma(k[r], u[r], kuk);
+            // data-space adjoint: al = (C^-1 y)_i, cc = (C^-1)_ii
+            const double al = fma(v, rS, kl);
+            const double cc = rS + kuk;
+            gs = fma(al, al, gs) - cc;
+            if constexpr (POST) {
+                mean_out[i] = fma(-s2, al, a.y[i]);
+                var_out[i] = s2 * k[0] - s2 * s2 * kuk;
+            }
+            // adjoint at the predicted level: lt, Lt; d l / d(predicted cov) = G
+            double lt[B], Lt[B][B], G[B][B];
+#pragma unroll
+            for (int r = 0; r < B; ++r) {
+                lt[r] = lh[r];
+#pragma unroll
+                for (int q = 0; q < B; ++q) Lt[r][q] = Lh[r][q];
+            }
+            lt[0] -= al;
+#pragma unroll
+            for (int q = 1; q < B; ++q) { Lt[0][q] -= u[q]; Lt[q][0] = Lt[0][q]; }
+            Lt[0][0] = Lt[0][0] - 2.0 * u[0] + cc;
+            if constexpr (GRAD) {
+#pragma unroll
+                for (int r = 0; r < B; ++r)
+#pragma unroll
+                    for (int q = r; q < B; ++q) {
+                        G[r][q] = 0.5 * fma(lt[r], lt[q], -Lt[r][q]);
+                        G[q][r] = G[r][q];
+                        GP[r][q] += G[r][q];
+                    }
+            }
+            if (i > 0) {
+                const double dt = a.t[i] - a.t[i - 1];
+                const double x = lam * dt;
+                if constexpr (GRAD) {
+                    // d l / dx = -lt^T F1 mb + 2 <G, F1 (Pb - Pinf)>
+                    double fm = 0.0, fg = 0.0;
+#pragma unroll
+                    for (int r = 0; r + 1 < B; ++r) fm = fma(lt[r], mb[r + 1], fm);
+                    double cm = 0.0;
+#pragma unroll
+                    for (int q = 0; q < B; ++q) cm = fma(fcoef<B>(q), mb[q], cm);
+                    fm = fma(-lt[B - 1], cm, fm);
+                    double D[B][B];
+#pragma unroll
+                    for (int r = 0; r < B; ++r)
+#pragma unroll
+                        for (int q = 0; q < B; ++q) D[r][q] = Pb[r][q] - sf * p1<B>(r, q);
+#pragma unroll
+                    for (int r = 0; r + 1 < B; ++r)
+#pragma unroll
+                        for (int q = 0; q < B; ++q) fg = fma(G[r][q], D[r + 1][q], fg);
+#pragma unroll
+                    for (int q = 0; q < B; ++q) {
+                        double cd = 0.0;
+#pragma unroll
+                        for (int jj = 0; jj < B; ++jj) cd = fma(fcoef<B>(jj), D[jj][q], cd);
+                        fg = fma(-G[B - 1][q], cd, fg);
+                    }
+                    gl = fma(2.0 * fg - fm, dt, gl);
+                }
+                double Ph[B][B], T[B][B];
+                phi<B>(x, ex, Ph);
+                mat_tvec<B>(Ph, lt, lh);
+                mat_mul<B>(Lt, Ph, T);
+                mat_tmul_sym<B>(Ph, T, Lh);
+                if constexpr (GRAD) {
+#pragma unroll
+                    for (int r = 0; r < B; ++r)
+#pragma unroll
+                        for (int q = r; q < B; ++q) {
+                            GP[r][q] -= 0.5 * fma(lh[r], lh[q], -Lh[r][q]);
+                            GP[q][r] = GP[r][q];
+                        }
+                }
+            }
+        }
+        constexpr int NA = Acc<B>::N;
+        part[0 * nc + c] = llp;
+        if constexpr (GRAD) {
+            part[1 * nc + c] = gl;
+            part[2 * nc + c] = gs;
+            int f = 3;
+#pragma unroll
+            for (int r = 0; r < B; ++r)
+#pragma unroll
+                for (int q = r; q < B; ++q) part[(f++) * nc + c] = GP[r][q];
+            static_assert(3 + NS == NA, "accumulator layout");
+        }
+    }
+}
+
+// ------------------------------------------------------------------ k_finalize (fixed-order reduction)
+
+template <int B>
+__global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ part, int64_t nc, int na,
+                                                  const double* __restrict__ theta, double* __restrict__ ll_out,
+                                                  double* __restrict__ grad_out) {
+    __shared__ double red[256 * Acc<B>::N];
+    const int tid = threadIdx.x;
+    for (int f = 0; f < na; ++f) {
+        double s = 0.0;
+        for (int64_t c = tid; c < nc; c += 256) s += part[f * nc + c];
+        red[f * 256 + tid] = s;
+    }
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w)
+            for (int f = 0; f < na; ++f) red[f * 256 + tid] += red[f * 256 + tid + w];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (ll_out) ll_out[0] = red[0];
+        if (grad_out && na == Acc<B>::N) {
+            const double ell = theta[0];
+            const double lam = sqrt(2.0 * B - 1.0) / ell;
+            grad_out[0] = red[1 * 256] * (-lam / ell);   // dl/dl = dl/dlam * dlam/dl
+            double gsf = 0.0;
+            int f = 3;
+#pragma unroll
+            for (int r = 0; r < B; ++r)
+#pragma unroll
+                for (int q = r; q < B; ++q) {
+                    const double w = (r == q) ? 1.0 : 2.0;
+                    gsf += w * p1<B>(r, q) * red[(f++) * 256];
+                }
+            grad_out[1] = gsf;
+            grad_out[2] = 0.5 * red[2 * 256];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+static constexpr int SCAN_TS = 64;
+static constexpr int SCAN_G = 8;
+static constexpr int CHUNK_TPB = 128;
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Workspace layout: [status | elements | prefix | suffix | scan levels | partials | stored steps]
+template <int B>
+struct Layout {
+    int64_t nc;
+    size_t off_E, off_pre, off_suf, off_part, off_store, total;
+    int nlev;
+    int64_t lev_n[8];
+    size_t lev_tot[8], lev_pre[8], lev_suf[8];
+
+    Layout(int64_t n, int64_t L, int mode) {
+        constexpr int NE = Dims<B>::NE, NM = Dims<B>::NM;
+        nc = (n + L - 1) / L;
+        size_t o = 256;  // status word region
+        off_E = o; o = align256(o + sizeof(double) * NE * nc);
+        off_pre = o; o = align256(o + sizeof(double) * NM * nc);
+        off_suf = o; o = align256(o + sizeof(double) * NM * nc);
+        nlev = 0;
+        int64_t ne = nc;
+        const int64_t per_tile = (int64_t)SCAN_TS * SCAN_G;
+        while (ne > per_tile) {
+            const int64_t nt = (ne + per_tile - 1) / per_tile;
+            lev_n[nlev] = nt;
+            lev_tot[nlev] = o; o = align256(o + sizeof(double) * NE * nt);
+            lev_pre[nlev] = o; o = align256(o + sizeof(double) * NM * nt);
+            lev_suf[nlev] = o; o = align256(o + sizeof(double) * NM * nt);
+            ++nlev;
+            ne = nt;
+        }
+        off_part = o; o = align256(o + sizeof(double) * Acc<B>::N * nc);
+        off_store = o;
+        if (mode != MODE_LOGLIK) o = align256(o + sizeof(double) * Stored<B>::N * (size_t)L * nc);
+        total = o;
+    }
+};
+
+template <int B>
+static void scan_level(const double* E, int64_t ne, double* pre_out, double* suf_out, const Layout<B>& lay,
+                       char* ws, int lev, cudaStream_t st) {
+    const int64_t per_tile = (int64_t)SCAN_TS * SCAN_G;
+    const size_t smem = ScanSmem<B, SCAN_TS>::bytes;
+    if (ne <= per_tile) {
+        k_scan_tile<B, SCAN_TS, true><<<1, SCAN_TS, smem, st>>>(E, ne, SCAN_G, nullptr, 1, nullptr, nullptr,
+                                                                pre_out, suf_out);
+        return;
+    }
+    const int64_t nt = lay.lev_n[lev];
+    double* tot = (double*)(ws + lay.lev_tot[lev]);
+    double* tpre = (double*)(ws + lay.lev_pre[lev]);
+    double* tsuf = (double*)(ws + lay.lev_suf[lev]);
+    k_scan_tile<B, SCAN_TS, false><<<(unsigned)nt, SCAN_TS, smem, st>>>(E, ne, SCAN_G, tot, nt, nullptr, nullptr,
+                                                                       nullptr, nullptr);
+    scan_level<B>(tot, nt, tpre, tsuf, lay, ws, lev + 1, st);
+    k_scan_tile<B, SCAN_TS, true><<<(unsigned)nt, SCAN_TS, smem, st>>>(E, ne, SCAN_G, nullptr, nt, tpre, tsuf,
+                                                                      pre_out, suf_out);
+}
+
+template <int B>
+size_t matern_ws_bytes_t(int64_t n, int64_t L, int mode) { return Layout<B>(n, L, mode).total; }
+
+template <int B>
+int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
+                 double* ll_out, double* grad_out, double* mean_out, double* var_out, void* wsv, cudaStream_t st) {
+    Layout<B> lay(n, L, mode);
+    char* ws = (char*)wsv;
+    int* status = (int*)ws;
+    double* E = (double*)(ws + lay.off_E);
+    double* pre = (double*)(ws + lay.off_pre);
+    double* suf = (double*)(ws + lay.off_suf);
+    double* part = (double*)(ws + lay.off_part);
+    double* store = (double*)(ws + lay.off_store);
+    ChainArgs a{t, y, n, L, lay.nc, theta, status};
+    const unsigned grid = (unsigned)((lay.nc + CHUNK_TPB - 1) / CHUNK_TPB);
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
+    k_fold<B><<<grid, CHUNK_TPB, 0, st>>>(a, E);
+    scan_level<B>(E, lay.nc, pre, suf, lay, ws, 0, st);
+    int na = 1;
+    switch (mode) {
+    case MODE_LOGLIK:
+        k_chunk<B, MODE_LOGLIK><<<grid, CHUNK_TPB, 0, st>>>(a, pre, suf, store, part, nullptr, nullptr);
+        break;
+    case MODE_GRAD:
+        k_chunk<B, MODE_GRAD><<<grid, CHUNK_TPB, 0, st>>>(a, pre, suf, store, part, nullptr, nullptr);
+        na = Acc<B>::N;
+        break;
+    default:
+        k_chunk<B, MODE_POSTERIOR><<<grid, CHUNK_TPB, 0, st>>>(a, pre, suf, store, part, mean_out, var_out);
+        break;
+    }
+    if (mode != MODE_POSTERIOR || ll_out)
+        k_finalize<B><<<1, 256, 0, st>>>(part, lay.nc, na, theta, ll_out, grad_out);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+template <int B>
+static void set_smem_attr() {
+    cudaFuncSetAttribute(k_scan_tile<B, SCAN_TS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)ScanSmem<B, SCAN_TS>::bytes);
+    cudaFuncSetAttribute(k_scan_tile<B, SCAN_TS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)ScanSmem<B, SCAN_TS>::bytes);
+}
+
+size_t matern_ws_bytes(int b, int64_t n, int64_t L, int mode) {
+    switch (b) {
+    case 1: return matern_ws_bytes_t<1>(n, L, mode);
+    case 2: return matern_ws_bytes_t<2>(n, L, mode);
+    default: return matern_ws_bytes_t<3>(n, L, mode);
+    }
+}
+
+int matern_prepare() {
+    set_smem_attr<1>();
+    set_smem_attr<2>();
+    set_smem_attr<3>();
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+int matern_run(int b, int mode, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
+               double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws, cudaStream_t st) {
+    switch (b) {
+    case 1: return matern_run_t<1>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st);
+    case 2: return matern_run_t<2>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st);
+    default: return matern_run_t<3>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st);
+    }
+}
+
+}  // namespace spg

@@ -1,0 +1,265 @@
+"""Thin Python binding of the C ABI in include/spingp.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``_lib/libspingp.so``; there is no
+CPU fallback.  Torch provides device memory and the current stream.  The
+functions named ``spingp_*`` mirror the C entry points one to one; ``Model``
+and ``LogLik`` are conveniences on top of them.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libspingp.so")
+
+OK, EINVAL, ENOTSORTED, ENONFINITE, ENUMERIC, ECUDA, ETIMEOUT, ENOMEM, EUNSUPPORTED = range(9)
+WS_LOGLIK, WS_GRAD, WS_POSTERIOR = 0, 1, 2
+SYNC = 1
+
+KINDS = {"matern12": 1, "matern32": 2, "matern52": 3, "periodic": 4, "quasiperiodic": 5}
+
+# names exported by the library, in the order of include/spingp.h
+EXPORTS = ("spingp_model_create", "spingp_model_destroy", "spingp_num_params", "spingp_state_dim",
+           "spingp_set_chunk_len", "spingp_get_chunk_len", "spingp_workspace_bytes", "spingp_loglik",
+           "spingp_grad", "spingp_posterior", "spingp_ws_status", "spingp_status_str")
+
+_lib = None
+
+
+class SpinGPError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = _status_str(status)
+        super().__init__("%s%s (status %d)" % (what + ": " if what else "", msg, status))
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("n_comp", ctypes.c_int), ("kinds", ctypes.POINTER(ctypes.c_int)),
+                ("orders", ctypes.POINTER(ctypes.c_int)), ("envs", ctypes.POINTER(ctypes.c_int))]
+
+
+def load():
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("CUDA library missing: %s (build it with __graft_entry__.build())" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, dp, i64, sz, u32 = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t, ctypes.c_uint
+    lib.spingp_model_create.argtypes = [ctypes.POINTER(_Desc), ctypes.POINTER(vp)]
+    lib.spingp_model_destroy.argtypes = [vp]
+    lib.spingp_model_destroy.restype = None
+    lib.spingp_num_params.argtypes = [vp]
+    lib.spingp_state_dim.argtypes = [vp]
+    lib.spingp_set_chunk_len.argtypes = [vp, ctypes.c_int]
+    lib.spingp_get_chunk_len.argtypes = [vp, i64]
+    lib.spingp_workspace_bytes.argtypes = [vp, i64, ctypes.c_int]
+    lib.spingp_workspace_bytes.restype = sz
+    lib.spingp_loglik.argtypes = [vp, dp, dp, i64, dp, dp, vp, sz, u32, vp]
+    lib.spingp_grad.argtypes = [vp, dp, dp, i64, dp, dp, dp, vp, sz, u32, vp]
+    lib.spingp_posterior.argtypes = [vp, dp, dp, i64, dp, dp, dp, dp, vp, sz, u32, vp]
+    lib.spingp_ws_status.argtypes = [vp, vp]
+    lib.spingp_status_str.argtypes = [ctypes.c_int]
+    lib.spingp_status_str.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _status_str(st):
+    try:
+        return load().spingp_status_str(st).decode()
+    except Exception:
+        return "status"
+
+
+def _check(st, what):
+    if st != OK:
+        raise SpinGPError(st, what)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev_f64(x, name):
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+        raise TypeError("%s must be a contiguous float64 CUDA tensor" % name)
+    return x
+
+
+# ---------------------------------------------------------------- the C entry points, one to one
+
+def spingp_model_create(spec):
+    """spec: a list of components, each "matern12" | "matern32" | "matern52" |
+    ("periodic", J) | ("quasiperiodic", J, envelope)."""
+    lib = load()
+    if isinstance(spec, (str, tuple)):
+        spec = [spec]
+    kinds, orders, envs = [], [], []
+    for comp in spec:
+        comp = (comp,) if isinstance(comp, str) else tuple(comp)
+        kinds.append(KINDS[comp[0]])
+        orders.append(int(comp[1]) if len(comp) > 1 else 0)
+        envs.append(KINDS[comp[2]] if len(comp) > 2 else 0)
+    n = len(kinds)
+    arr = ctypes.c_int * n
+    desc = _Desc(n, arr(*kinds), arr(*orders), arr(*envs))
+    h = ctypes.c_void_p()
+    _check(lib.spingp_model_create(ctypes.byref(desc), ctypes.byref(h)), "spingp_model_create")
+    return h
+
+
+def spingp_model_destroy(h):
+    load().spingp_model_destroy(h)
+
+
+def spingp_num_params(h):
+    return load().spingp_num_params(h)
+
+
+def spingp_state_dim(h):
+    return load().spingp_state_dim(h)
+
+
+def spingp_set_chunk_len(h, L):
+    _check(load().spingp_set_chunk_len(h, int(L)), "spingp_set_chunk_len")
+
+
+def spingp_get_chunk_len(h, n):
+    return load().spingp_get_chunk_len(h, int(n))
+
+
+def spingp_workspace_bytes(h, n, what):
+    return load().spingp_workspace_bytes(h, int(n), int(what))
+
+
+def spingp_loglik(h, t, y, n, theta, ll_out, ws, ws_bytes, flags, stream=None):
+    return load().spingp_loglik(h, _ptr(t), _ptr(y), int(n), _ptr(theta), _ptr(ll_out), _ptr(ws), ws_bytes,
+                                flags, stream if stream is not None else _stream())
+
+
+def spingp_grad(h, t, y, n, theta, ll_out, grad_out, ws, ws_bytes, flags, stream=None):
+    return load().spingp_grad(h, _ptr(t), _ptr(y), int(n), _ptr(theta), _ptr(ll_out), _ptr(grad_out), _ptr(ws),
+                              ws_bytes, flags, stream if stream is not None else _stream())
+
+
+def spingp_posterior(h, t, y, n, theta, ll_out, mean_out, var_out, ws, ws_bytes, flags, stream=None):
+    return load().spingp_posterior(h, _ptr(t), _ptr(y), int(n), _ptr(theta), _ptr(ll_out), _ptr(mean_out),
+                                   _ptr(var_out), _ptr(ws), ws_bytes, flags,
+                                   stream if stream is not None else _stream())
+
+
+def spingp_ws_status(ws, stream=None):
+    return load().spingp_ws_status(_ptr(ws), stream if stream is not None else _stream())
+
+
+def spingp_status_str(st):
+    return _status_str(st)
+
+
+# ---------------------------------------------------------------- conveniences
+
+class Model:
+    """A model handle with workspace management on the current device."""
+
+    def __init__(self, spec, chunk_len=0):
+        self.spec = spec
+        self.h = spingp_model_create(spec)
+        if chunk_len:
+            spingp_set_chunk_len(self.h, chunk_len)
+        self._ws = {}
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and _lib is not None:
+            _lib.spingp_model_destroy(h)
+            self.h = None
+
+    @property
+    def num_params(self):
+        return spingp_num_params(self.h)
+
+    @property
+    def state_dim(self):
+        return spingp_state_dim(self.h)
+
+    def set_chunk_len(self, L):
+        spingp_set_chunk_len(self.h, L)
+        self._ws.clear()
+
+    def chunk_len(self, n):
+        return spingp_get_chunk_len(self.h, n)
+
+    def workspace(self, n, what, device=None):
+        nbytes = spingp_workspace_bytes(self.h, n, what)
+        if nbytes == 0:
+            raise SpinGPError(EUNSUPPORTED, "spingp_workspace_bytes")
+        device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        key = (what, device)
+        ws = self._ws.get(key)
+        if ws is None or ws.numel() < nbytes:
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+            self._ws[key] = ws
+        return ws
+
+    def _args(self, t, y, theta):
+        _dev_f64(t, "t"); _dev_f64(y, "y"); _dev_f64(theta, "theta")
+        if t.dim() != 1 or y.shape != t.shape:
+            raise ValueError("t and y must be 1-D of the same length")
+        if theta.numel() != self.num_params:
+            raise ValueError("theta must have %d entries" % self.num_params)
+        return t.numel()
+
+    def loglik(self, t, y, theta, sync=True, out=None):
+        n = self._args(t, y, theta)
+        ws = self.workspace(n, WS_LOGLIK, t.device)
+        ll = out if out is not None else torch.empty(1, dtype=torch.float64, device=t.device)
+        _check(spingp_loglik(self.h, t, y, n, theta, ll, ws, ws.numel(), SYNC if sync else 0), "spingp_loglik")
+        return ll
+
+    def grad(self, t, y, theta, sync=True, out=None):
+        n = self._args(t, y, theta)
+        ws = self.workspace(n, WS_GRAD, t.device)
+        if out is None:
+            ll = torch.empty(1, dtype=torch.float64, device=t.device)
+            g = torch.empty(self.num_params, dtype=torch.float64, device=t.device)
+        else:
+            ll, g = out
+        _check(spingp_grad(self.h, t, y, n, theta, ll, g, ws, ws.numel(), SYNC if sync else 0), "spingp_grad")
+        return ll, g
+
+    def posterior(self, t, y, theta, sync=True, with_loglik=True):
+        n = self._args(t, y, theta)
+        ws = self.workspace(n, WS_POSTERIOR, t.device)
+        mean = torch.empty(n, dtype=torch.float64, device=t.device)
+        var = torch.empty(n, dtype=torch.float64, device=t.device)
+        ll = torch.empty(1, dtype=torch.float64, device=t.device) if with_loglik else None
+        _check(spingp_posterior(self.h, t, y, n, theta, ll, mean, var, ws, ws.numel(), SYNC if sync else 0),
+               "spingp_posterior")
+        return mean, var, ll
+
+
+class LogLik(torch.autograd.Function):
+    """log p(y | t, theta) with the hand-written adjoint as its backward.
+
+    forward runs spingp_grad once and keeps the gradient; backward returns
+    grad_output * gradient for theta (t and y get no gradient)."""
+
+    @staticmethod
+    def forward(ctx, theta, t, y, model):
+        ll, g = model.grad(t, y, theta.detach().contiguous())
+        ctx.save_for_backward(g)
+        return ll[0]
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (g,) = ctx.saved_tensors
+        return grad_out * g, None, None, None

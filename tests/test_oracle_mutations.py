@@ -28,8 +28,8 @@ C_MUTANTS = [
      "mm(b, Gt, Psn, Pc + (size_t)i * b * b);"),
     ("rotation transposed", "double R[4] = {cs, -sn, sn, cs};", "double R[4] = {cs, sn, -sn, cs};"),
     ("gradient drops dQ term",
-     "grad[p] += mdot(b, Abar, dA + (size_t)p * b * b) + mdot(b, Qbar, dQ + (size_t)p * b * b);",
-     "grad[p] += mdot(b, Abar, dA + (size_t)p * b * b);"),
+     "double term = mdot(b, Abar, dA + (size_t)p * b * b) + mdot(b, Qbar, dQ + (size_t)p * b * b);",
+     "double term = mdot(b, Abar, dA + (size_t)p * b * b);"),
     ("Bessel series index", "term *= h * h / ((double)k * (double)(k + j));",
      "term *= h * h / ((double)k * (double)(k + j + 1));"),
     ("RTS gain transposed", "for (int r = 0; r < b; ++r) for (int c = 0; c < b; ++c) G[r * b + c] = Gt[c * b + r];",
