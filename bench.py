@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Benchmark: log-likelihood + gradient throughput of exact state-space GP
+inference (time steps per second), FP64, one Matern-5/2 series (b = 3) of
+N = 2^22 steps with dt ~ Exp(0.01), l = 0.5, s_f = 2, s_n = 0.05.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl spingp|reference]
+
+Prints one JSON line (rank 0).  The device-timed value brackets each step's
+spingp_grad call with CUDA events on its stream, after an untimed 256 MiB
+write that flushes L2; with N GPUs (torchrun) every rank runs its own
+independent series (replicas, weak scaling), the time is the max over ranks
+and the value counts the steps of all ranks.  Extra keys: the roofline of the
+dominant kernel (live stage timing), the HBM roofline of the whole step, the
+end-to-end figure through the public API with host buffers, the "plain GPU
+form" comparator (the forward kernel run 2P+1 times for central differences),
+the oracle timed on host cores, and SM clocks sampled during the timed region.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "loglik+grad time steps/s (FP64, N=2^22,b=3) vs plain GPU form; % HBM roofline"
+WORKLOAD = "matern52_n4m"
+
+# FP64 flops executed per time step by each stage of the gradient call for
+# b = 3 (2 x DFMA + DADD + DMUL thread instructions, counted with ncu at
+# N = 2^21, L = 32; profiles/k_chunk_grad_matern52_n2m.md).
+FLOPS_PER_STEP = {"elimination": 275.5, "chunk_pass": 515.7}
+# DRAM bytes per step moved by the chunk pass (ncu dram__bytes_read + write,
+# same capture); None once the kernel has changed since the counters were taken
+DRAM_BYTES_PER_STEP = {"chunk_pass": 166.8}
+# algorithmic HBM bytes per step of the whole call: t and y in (16 B); the
+# gradient and log-likelihood outputs are O(1) per series
+ALGO_BYTES_PER_STEP = 16.0
+FP64_NOMINAL_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # SMs x max SM clock x FP64 flop/clk/SM
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="spingp", choices=["spingp", "reference"])
+    ap.add_argument("--n", type=int, default=0, help="override the series length (profiling runs only)")
+    ap.add_argument("--chunk", type=int, default=-1, help="chunk length; -1 = autotune, 0 = library default")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index, enabled=True):
+        self.p = None
+        if not enabled:
+            return
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(gpu_index)],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, smax, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- the oracle (CPU baseline / reference arm)
+
+def oracle_rate(s, sample_n, reps=1):
+    """Steps/s of the sequential FP64 oracle (Kalman filter + two-filter
+    adjoint, one host thread) on the first sample_n steps of the workload."""
+    from oracle import seq
+    t, y = s.t[:sample_n], s.y[:sample_n]
+    seq.grad(s.spec, s.theta, t[:1000], y[:1000])        # builds/loads the oracle library
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        seq.grad(s.spec, s.theta, t, y)
+        times.append(time.perf_counter() - t0)
+    return sample_n / float(np.median(times)), times
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1610_08035_gb300 import synth
+    s = synth.single(WORKLOAD, n=args.n or None)
+    sample = min(len(s.t), 1 << 18)
+    for _ in range(args.warmup):
+        oracle_rate(s, min(sample, 1 << 14))
+    rates = []
+    for _ in range(args.steps):
+        r, _ = oracle_rate(s, sample)
+        rates.append(r)
+    value = float(np.median(rates))
+    desc = "first %d steps of the %d-step workload per step, sequential C oracle (Kalman filter + two-filter adjoint)" % (
+        sample, len(s.t))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sample / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": len(s.t), "b": 3, "sample_steps": sample},
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------- the CUDA path
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_1610_08035_gb300 import autotune, spingp, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # each rank: its own independent series of the same shape (replicas)
+    s = synth.single(WORKLOAD, n=args.n or None, seed=1 + 1000 * rank)
+    n = len(s.t)
+    T = torch.tensor(s.t, device=dev)
+    Y = torch.tensor(s.y, device=dev)
+    TH = torch.tensor(s.theta, device=dev)
+    model = spingp.Model(s.spec)
+    if args.chunk >= 0:
+        model.set_chunk_len(args.chunk)
+    else:
+        autotune.tune(model, T, Y, TH, spingp.WS_GRAD)
+    L = model.chunk_len(n)
+    ll = torch.empty(1, dtype=torch.float64, device=dev)
+    g = torch.empty(3, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    for _ in range(max(args.warmup, 0)):
+        model.grad(T, Y, TH, sync=True, out=(ll, g))
+    fp64_tflops = spingp.spingp_probe_fp64(dev)
+
+    # ---- device-timed region
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    spingp.spingp_profile_enable(model.h, True)
+    spingp.spingp_profile_read(model.h)
+    barrier()
+    clocks = ClockSampler(local, enabled=not args.no_clocks)
+    time.sleep(0.3 if not args.no_clocks else 0.0)
+    for k in range(K):
+        flush.fill_(k & 0xFF)                        # 256 MiB write: L2 (~126 MiB) flushed, untimed
+        evs[k][0].record()
+        model.grad(T, Y, TH, sync=False, out=(ll, g))
+        evs[k][1].record()
+    barrier()
+    clk = clocks.stop()
+    stages, calls = spingp.spingp_profile_read(model.h)
+    spingp.spingp_profile_enable(model.h, False)
+    st = spingp.spingp_ws_status(model.workspace(n, spingp.WS_GRAD, dev))
+    if st != spingp.OK:
+        raise spingp.SpinGPError(st, "benchmark step")
+    ms_steps = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(np.sum(ms_steps))
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / K
+    value = world * n / (ms_per_step * 1e-3)
+
+    # ---- roofline of the dominant stage (live stage times over the timed region)
+    stage_ms = {k: v / max(calls, 1) for k, v in stages.items()}
+    dom = max(stage_ms, key=stage_ms.get)
+    flops = FLOPS_PER_STEP.get(dom)
+    achieved = flops * n / (stage_ms[dom] * 1e-3) / 1e12 if flops else None
+    traffic = DRAM_BYTES_PER_STEP.get(dom)
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
+            "frac": achieved / fp64_tflops if achieved else None,
+            "traffic": traffic * n if traffic else None,
+            "peak_kind": "measured FP64 FMA probe (spingp_probe_fp64); nominal %.3f" % FP64_NOMINAL_TFLOPS,
+            "ms_per_launch": stage_ms[dom]}
+    hbm = {"algorithmic_bytes_per_step": ALGO_BYTES_PER_STEP,
+           "achieved_gbs": ALGO_BYTES_PER_STEP * n / (ms_per_step * 1e-3) / 1e9}
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        with open(peaks_path) as f:
+            hbm_peak = json.load(f).get("hbm_gbs")
+        hbm["peak_gbs"] = hbm_peak
+        hbm["frac"] = hbm["achieved_gbs"] / hbm_peak if hbm_peak else None
+        hbm["peak_kind"] = "measured (MEASURED_PEAKS.json)"
+    else:
+        hbm["peak_gbs"] = 6800.0
+        hbm["frac"] = hbm["achieved_gbs"] / 6800.0
+        hbm["peak_kind"] = "fallback"
+
+    out = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+           "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": n, "b": 3, "model": "matern52", "chunk_len": L,
+                      "theta": [float(v) for v in s.theta], "parallelism": "replicas" if world > 1 else "single",
+                      "l2": "flushed between timed iterations (256 MiB write, untimed)"},
+           "roofline": roof, "hbm_roofline": hbm, "stages_ms_per_call": stage_ms,
+           "gpu_launches": spingp.spingp_launch_count(model.h, n, spingp.WS_GRAD) * K,
+           "clocks": clk}
+
+    # ---- end to end through the public API: pinned host buffers in, results out, every step
+    if not args.no_e2e:
+        th = torch.from_numpy(s.t).pin_memory()
+        yh = torch.from_numpy(s.y).pin_memory()
+        res_h = torch.empty(4, dtype=torch.float64).pin_memory()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record()
+        for _ in range(K):
+            T.copy_(th, non_blocking=True)
+            Y.copy_(yh, non_blocking=True)
+            model.grad(T, Y, TH, sync=False, out=(ll, g))
+            res_h[0:1].copy_(ll, non_blocking=True)
+            res_h[1:4].copy_(g, non_blocking=True)
+        e1.record()
+        barrier()
+        e2e_ms = e0.elapsed_time(e1) / K
+        if world > 1:
+            tt = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_ms = float(tt.item())
+        out["e2e"] = {"value": world * n / (e2e_ms * 1e-3), "unit": "steps/s", "h2d_bytes_per_step": 16 * n,
+                      "d2h_bytes_per_step": 32, "ms_per_step": e2e_ms}
+
+    # ---- the plain GPU form: forward kernel (2P+1) times, central differences
+    if not args.no_comparator:
+        P = 3
+        h = 1e-5
+        thetas = [TH.clone()]
+        for p in range(P):
+            for sgn in (1.0, -1.0):
+                v = TH.clone()
+                v[p] = v[p] * (1.0 + sgn * h)
+                thetas.append(v)
+        lls = torch.empty(len(thetas), dtype=torch.float64, device=dev)
+        fwd = spingp.Model(s.spec, chunk_len=L)
+        for v in thetas:
+            fwd.loglik(T, Y, v, sync=True)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        comp_ms = 0.0
+        for k in range(K):
+            flush.fill_(k & 0xFF)
+            c0.record()
+            for i, v in enumerate(thetas):
+                fwd.loglik(T, Y, v, sync=False, out=lls[i:i + 1])
+            c1.record()
+            torch.cuda.synchronize()
+            comp_ms += c0.elapsed_time(c1)
+        comp_ms /= K
+        lv = lls.cpu().numpy()
+        fd = np.array([(lv[1 + 2 * p] - lv[2 + 2 * p]) / (2 * h * s.theta[p]) for p in range(P)])
+        gad = g.cpu().numpy()
+        out["comparator"] = {"kind": "forward kernel x %d (central differences, one launch sequence each)" % len(thetas),
+                             "value": world * n / (comp_ms * 1e-3), "unit": "steps/s", "ms_per_step": comp_ms,
+                             "speedup_of_adjoint": comp_ms / ms_per_step,
+                             "fd_grad_rel_err": float(np.max(np.abs(fd - gad) / np.abs(gad)))}
+
+    # ---- the oracle on the host cores (rank 0, single GPU only)
+    if not args.no_cpu_baseline and world == 1:
+        sample = min(n, 1 << 20)
+        rate, _ = oracle_rate(s, sample)
+        out["cpu_baseline"] = {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                               "sample": "first %d of %d steps, sequential C oracle (Kalman filter + two-filter "
+                                         "adjoint), 1 host thread" % (sample, n)}
+
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -130,6 +130,28 @@ spingp_status spingp_posterior(const spingp_model* model, const double* t, const
                                const double* theta, double* ll_out, double* mean_out, double* var_out,
                                void* ws, size_t ws_bytes, unsigned flags, void* stream);
 
+/* Number of kernels one call of the given kind launches for n steps (the
+ * discretisation/elimination pass, the reduction tiles, the per-chunk pass
+ * and the final reduction). */
+int spingp_launch_count(const spingp_model* model, int64_t n, spingp_ws_kind what);
+
+/* Stage timing.  While enabled, every call on this model records CUDA events
+ * on its stream around its four stages: 0 discretisation + in-chunk
+ * elimination, 1 odd-even reduction, 2 per-chunk forward/reverse pass,
+ * 3 final reduction.  spingp_profile_read synchronises on the recorded events,
+ * writes the summed milliseconds per stage to ms_out[0..3] and the number of
+ * calls to *calls, and clears the record.  Not for use during stream capture;
+ * a model with profiling enabled must not be shared between host threads. */
+spingp_status spingp_profile_enable(spingp_model* model, int on);
+spingp_status spingp_profile_read(spingp_model* model, double* ms_out, int* calls);
+
+/* Measured FP64 throughput of the current device: a kernel of independent
+ * fused multiply-adds (no memory traffic) on every SM, timed with CUDA events.
+ * scratch: device memory of at least spingp_probe_fp64_bytes() bytes for the
+ * kernel's results.  Synchronises the stream; writes TFLOP/s to *tflops_out. */
+size_t spingp_probe_fp64_bytes(void);
+spingp_status spingp_probe_fp64(void* scratch, size_t scratch_bytes, double* tflops_out, void* stream);
+
 /* Synchronise the stream and return the device status recorded in ws by the
  * last call that used it (SPINGP_OK if none). */
 spingp_status spingp_ws_status(void* ws, void* stream);

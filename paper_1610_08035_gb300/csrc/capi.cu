@@ -12,11 +12,20 @@
 #define SPG_MAXC 8
 #define SPG_MAXDEV 64
 
+// Stage-timing record: five events per call, reused across calls.
+struct spg_prof {
+    int on;
+    int used;                      // calls recorded since the last read
+    int cap;
+    cudaEvent_t (*ev)[5];
+};
+
 struct spingp_model {
     int ncomp;
     int kinds[SPG_MAXC], orders[SPG_MAXC], envs[SPG_MAXC];
     int b, P;
     int chunk_len;   // 0 = default
+    spg_prof* prof;  // NULL unless profiling was enabled
 };
 
 namespace {
@@ -62,7 +71,22 @@ spingp_status run(const spingp_model* m, int mode, const double* t, const double
     spingp_status st = prepare_device();
     if (st != SPINGP_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    if (spg::matern_run(m->b, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s)) return SPINGP_ECUDA;
+    cudaEvent_t* ev = NULL;
+    spg_prof* pr = m->prof;
+    if (pr && pr->on) {
+        if (pr->used == pr->cap) {
+            const int cap = pr->cap ? 2 * pr->cap : 16;
+            cudaEvent_t(*nev)[5] = (cudaEvent_t(*)[5])realloc(pr->ev, sizeof(cudaEvent_t[5]) * cap);
+            if (!nev) return SPINGP_ENOMEM;
+            for (int i = pr->cap; i < cap; ++i)
+                for (int k = 0; k < 5; ++k)
+                    if (cudaEventCreate(&nev[i][k]) != cudaSuccess) return SPINGP_ECUDA;
+            pr->ev = nev;
+            pr->cap = cap;
+        }
+        ev = pr->ev[pr->used++];
+    }
+    if (spg::matern_run(m->b, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s, ev)) return SPINGP_ECUDA;
     if (flags & SPINGP_SYNC) return spingp_ws_status(ws, stream);
     return SPINGP_OK;
 }
@@ -99,7 +123,16 @@ spingp_status spingp_model_create(const spingp_model_desc* d, spingp_model** out
     return SPINGP_OK;
 }
 
-void spingp_model_destroy(spingp_model* m) { free(m); }
+void spingp_model_destroy(spingp_model* m) {
+    if (!m) return;
+    if (m->prof) {
+        for (int i = 0; i < m->prof->cap; ++i)
+            for (int k = 0; k < 5; ++k) cudaEventDestroy(m->prof->ev[i][k]);
+        free(m->prof->ev);
+        free(m->prof);
+    }
+    free(m);
+}
 
 int spingp_num_params(const spingp_model* m) { return m ? m->P : -1; }
 int spingp_state_dim(const spingp_model* m) { return m ? m->b : -1; }
@@ -139,6 +172,49 @@ spingp_status spingp_posterior(const spingp_model* m, const double* t, const dou
     if (!mean_out || !var_out) return SPINGP_EINVAL;
     return run(m, spg::MODE_POSTERIOR, t, y, n, theta, ll_out, NULL, mean_out, var_out, ws, ws_bytes, flags,
                stream);
+}
+
+int spingp_launch_count(const spingp_model* m, int64_t n, spingp_ws_kind what) {
+    if (!m || n < 1 || !single_matern(m)) return -1;
+    const int mode = what == SPINGP_WS_GRAD ? spg::MODE_GRAD
+                   : what == SPINGP_WS_POSTERIOR ? spg::MODE_POSTERIOR : spg::MODE_LOGLIK;
+    return spg::matern_launch_count(m->b, n, chunk_len(m, n), mode);
+}
+
+spingp_status spingp_profile_enable(spingp_model* m, int on) {
+    if (!m) return SPINGP_EINVAL;
+    if (!m->prof) {
+        m->prof = (spg_prof*)calloc(1, sizeof(spg_prof));
+        if (!m->prof) return SPINGP_ENOMEM;
+    }
+    m->prof->on = on ? 1 : 0;
+    return SPINGP_OK;
+}
+
+spingp_status spingp_profile_read(spingp_model* m, double* ms_out, int* calls) {
+    if (!m || !ms_out) return SPINGP_EINVAL;
+    for (int k = 0; k < 4; ++k) ms_out[k] = 0.0;
+    if (calls) *calls = 0;
+    spg_prof* pr = m->prof;
+    if (!pr) return SPINGP_OK;
+    for (int i = 0; i < pr->used; ++i) {
+        if (cudaEventSynchronize(pr->ev[i][4]) != cudaSuccess) return SPINGP_ECUDA;
+        for (int k = 0; k < 4; ++k) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, pr->ev[i][k], pr->ev[i][k + 1]) != cudaSuccess) return SPINGP_ECUDA;
+            ms_out[k] += ms;
+        }
+    }
+    if (calls) *calls = pr->used;
+    pr->used = 0;
+    return SPINGP_OK;
+}
+
+size_t spingp_probe_fp64_bytes(void) { return spg::probe_fp64_bytes(); }
+
+spingp_status spingp_probe_fp64(void* scratch, size_t bytes, double* tflops_out, void* stream) {
+    if (!scratch || !tflops_out) return SPINGP_EINVAL;
+    return spg::probe_fp64(scratch, bytes, tflops_out, (cudaStream_t)stream) ? SPINGP_ECUDA : SPINGP_OK;
 }
 
 spingp_status spingp_ws_status(void* ws, void* stream) {

@@ -15,7 +15,13 @@ enum { MODE_LOGLIK = 0, MODE_GRAD = 1, MODE_POSTERIOR = 2 };
 
 size_t matern_ws_bytes(int b, int64_t n, int64_t L, int mode);
 int matern_prepare();
+// ev: NULL, or 5 events recorded around the four stages
 int matern_run(int b, int mode, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
-               double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws, cudaStream_t st);
+               double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws, cudaStream_t st,
+               cudaEvent_t* ev);
+int matern_launch_count(int b, int64_t n, int64_t L, int mode);
+
+size_t probe_fp64_bytes();
+int probe_fp64(void* scratch, size_t bytes, double* tflops, cudaStream_t st);
 
 }  // namespace spg

@@ -622,8 +622,22 @@ template <int B>
 size_t matern_ws_bytes_t(int64_t n, int64_t L, int mode) { return Layout<B>(n, L, mode).total; }
 
 template <int B>
+static int scan_launches(int64_t ne, const Layout<B>& lay, int lev) {
+    const int64_t per_tile = (int64_t)SCAN_TS * SCAN_G;
+    if (ne <= per_tile) return 1;
+    return 2 + scan_launches<B>(lay.lev_n[lev], lay, lev + 1);
+}
+
+template <int B>
+int matern_launch_count_t(int64_t n, int64_t L, int mode) {
+    Layout<B> lay(n, L, mode);
+    return 1 + scan_launches<B>(lay.nc, lay, 0) + 1 + 1;
+}
+
+template <int B>
 int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
-                 double* ll_out, double* grad_out, double* mean_out, double* var_out, void* wsv, cudaStream_t st) {
+                 double* ll_out, double* grad_out, double* mean_out, double* var_out, void* wsv, cudaStream_t st,
+                 cudaEvent_t* ev) {
     Layout<B> lay(n, L, mode);
     char* ws = (char*)wsv;
     int* status = (int*)ws;
@@ -635,8 +649,11 @@ int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t 
     ChainArgs a{t, y, n, L, lay.nc, theta, status};
     const unsigned grid = (unsigned)((lay.nc + CHUNK_TPB - 1) / CHUNK_TPB);
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
+    if (ev) cudaEventRecord(ev[0], st);
     k_fold<B><<<grid, CHUNK_TPB, 0, st>>>(a, E);
+    if (ev) cudaEventRecord(ev[1], st);
     scan_level<B>(E, lay.nc, pre, suf, lay, ws, 0, st);
+    if (ev) cudaEventRecord(ev[2], st);
     int na = 1;
     switch (mode) {
     case MODE_LOGLIK:
@@ -650,8 +667,10 @@ int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t 
         k_chunk<B, MODE_POSTERIOR><<<grid, CHUNK_TPB, 0, st>>>(a, pre, suf, store, part, mean_out, var_out);
         break;
     }
-    if (mode != MODE_POSTERIOR || ll_out)
-        k_finalize<B><<<1, 256, 0, st>>>(part, lay.nc, na, theta, ll_out, grad_out);
+    if (ev) cudaEventRecord(ev[3], st);
+    // the final reduction always runs (it is cheap), so the launch count is fixed per kind
+    k_finalize<B><<<1, 256, 0, st>>>(part, lay.nc, na, theta, ll_out, grad_out);
+    if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
@@ -679,11 +698,20 @@ int matern_prepare() {
 }
 
 int matern_run(int b, int mode, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
-               double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws, cudaStream_t st) {
+               double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws, cudaStream_t st,
+               cudaEvent_t* ev) {
     switch (b) {
-    case 1: return matern_run_t<1>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st);
-    case 2: return matern_run_t<2>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st);
-    default: return matern_run_t<3>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st);
+    case 1: return matern_run_t<1>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev);
+    case 2: return matern_run_t<2>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev);
+    default: return matern_run_t<3>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev);
+    }
+}
+
+int matern_launch_count(int b, int64_t n, int64_t L, int mode) {
+    switch (b) {
+    case 1: return matern_launch_count_t<1>(n, L, mode);
+    case 2: return matern_launch_count_t<2>(n, L, mode);
+    default: return matern_launch_count_t<3>(n, L, mode);
     }
 }
 

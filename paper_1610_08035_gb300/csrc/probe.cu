@@ -1,0 +1,57 @@
+// probe.cu -- measured FP64 throughput of the current device (the ALU roofline
+// denominator for the FP64-bound chain kernels).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace spg {
+
+static constexpr int PROBE_THREADS = 256;
+static constexpr int PROBE_BLOCKS_PER_SM = 4;
+static constexpr int PROBE_ITERS = 8192;
+
+// eight independent FMA chains per thread: issue-bound on the FP64 pipe
+__global__ void __launch_bounds__(PROBE_THREADS) k_probe_fp64(double* out, int iters, double a, double b) {
+    double x0 = threadIdx.x * 1e-3, x1 = x0 + 1.0, x2 = x0 + 2.0, x3 = x0 + 3.0;
+    double x4 = x0 + 4.0, x5 = x0 + 5.0, x6 = x0 + 6.0, x7 = x0 + 7.0;
+    for (int i = 0; i < iters; ++i) {
+        x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+        x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+    }
+    out[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+static int sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return sms;
+}
+
+size_t probe_fp64_bytes() { return sizeof(double) * (size_t)sm_count() * PROBE_BLOCKS_PER_SM * PROBE_THREADS; }
+
+int probe_fp64(void* scratch, size_t bytes, double* tflops, cudaStream_t st) {
+    const int sms = sm_count();
+    if (sms <= 0 || !scratch || bytes < probe_fp64_bytes()) return 1;
+    const unsigned blocks = (unsigned)(sms * PROBE_BLOCKS_PER_SM);
+    double* out = (double*)scratch;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return 1;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return 1; }
+    k_probe_fp64<<<blocks, PROBE_THREADS, 0, st>>>(out, 64, 1.0000001, 1e-9);
+    cudaEventRecord(e0, st);
+    k_probe_fp64<<<blocks, PROBE_THREADS, 0, st>>>(out, PROBE_ITERS, 1.0000001, 1e-9);
+    cudaEventRecord(e1, st);
+    int rc = cudaEventSynchronize(e1) == cudaSuccess ? 0 : 1;
+    float ms = 0.0f;
+    if (!rc) rc = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess ? 0 : 1;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc || ms <= 0.0f) return 1;
+    const double flops = 2.0 * 8.0 * PROBE_ITERS * (double)blocks * PROBE_THREADS;
+    *tflops = flops / (ms * 1e-3) / 1e12;
+    return 0;
+}
+
+}  // namespace spg

@@ -22,7 +22,10 @@ KINDS = {"matern12": 1, "matern32": 2, "matern52": 3, "periodic": 4, "quasiperio
 # names exported by the library, in the order of include/spingp.h
 EXPORTS = ("spingp_model_create", "spingp_model_destroy", "spingp_num_params", "spingp_state_dim",
            "spingp_set_chunk_len", "spingp_get_chunk_len", "spingp_workspace_bytes", "spingp_loglik",
-           "spingp_grad", "spingp_posterior", "spingp_ws_status", "spingp_status_str")
+           "spingp_grad", "spingp_posterior", "spingp_launch_count", "spingp_profile_enable",
+           "spingp_profile_read", "spingp_probe_fp64_bytes", "spingp_probe_fp64", "spingp_ws_status",
+           "spingp_status_str")
+STAGES = ("elimination", "reduction", "chunk_pass", "final_reduction")
 
 _lib = None
 
@@ -60,6 +63,12 @@ def load():
     lib.spingp_loglik.argtypes = [vp, dp, dp, i64, dp, dp, vp, sz, u32, vp]
     lib.spingp_grad.argtypes = [vp, dp, dp, i64, dp, dp, dp, vp, sz, u32, vp]
     lib.spingp_posterior.argtypes = [vp, dp, dp, i64, dp, dp, dp, dp, vp, sz, u32, vp]
+    lib.spingp_launch_count.argtypes = [vp, i64, ctypes.c_int]
+    lib.spingp_profile_enable.argtypes = [vp, ctypes.c_int]
+    lib.spingp_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+    lib.spingp_probe_fp64_bytes.argtypes = []
+    lib.spingp_probe_fp64_bytes.restype = sz
+    lib.spingp_probe_fp64.argtypes = [vp, sz, ctypes.POINTER(ctypes.c_double), vp]
     lib.spingp_ws_status.argtypes = [vp, vp]
     lib.spingp_status_str.argtypes = [ctypes.c_int]
     lib.spingp_status_str.restype = ctypes.c_char_p
@@ -155,6 +164,33 @@ def spingp_posterior(h, t, y, n, theta, ll_out, mean_out, var_out, ws, ws_bytes,
     return load().spingp_posterior(h, _ptr(t), _ptr(y), int(n), _ptr(theta), _ptr(ll_out), _ptr(mean_out),
                                    _ptr(var_out), _ptr(ws), ws_bytes, flags,
                                    stream if stream is not None else _stream())
+
+
+def spingp_launch_count(h, n, what):
+    return load().spingp_launch_count(h, int(n), int(what))
+
+
+def spingp_profile_enable(h, on):
+    _check(load().spingp_profile_enable(h, 1 if on else 0), "spingp_profile_enable")
+
+
+def spingp_profile_read(h):
+    """Summed milliseconds per stage since the last read, and the call count."""
+    ms = (ctypes.c_double * 4)()
+    calls = ctypes.c_int()
+    _check(load().spingp_profile_read(h, ms, ctypes.byref(calls)), "spingp_profile_read")
+    return dict(zip(STAGES, list(ms))), calls.value
+
+
+def spingp_probe_fp64(device=None):
+    """Measured FP64 TFLOP/s of the current device (independent FMA chains)."""
+    lib = load()
+    scratch = torch.empty(lib.spingp_probe_fp64_bytes(), dtype=torch.uint8,
+                          device=device if device is not None else "cuda")
+    out = ctypes.c_double()
+    _check(lib.spingp_probe_fp64(_ptr(scratch), scratch.numel(), ctypes.byref(out), _stream()),
+           "spingp_probe_fp64")
+    return out.value
 
 
 def spingp_ws_status(ws, stream=None):
