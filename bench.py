@@ -32,11 +32,11 @@ WORKLOAD = "matern52_n4m"
 
 # FP64 flops executed per time step by each stage of the gradient call for
 # b = 3 (2 x DFMA + DADD + DMUL thread instructions, counted with ncu at
-# N = 2^21, L = 32; profiles/k_chunk_grad_matern52_n2m.md).
-FLOPS_PER_STEP = {"elimination": 275.5, "chunk_pass": 515.7}
+# N = 2^21, L = 36; profiles/k_chunk_grad_matern52_n2m.md).
+FLOPS_PER_STEP = {"elimination": 275.9, "chunk_pass": 379.0}
 # DRAM bytes per step moved by the chunk pass (ncu dram__bytes_read + write,
 # same capture); None once the kernel has changed since the counters were taken
-DRAM_BYTES_PER_STEP = {"chunk_pass": 166.8}
+DRAM_BYTES_PER_STEP = {"chunk_pass": 333.9}
 # algorithmic HBM bytes per step of the whole call: t and y in (16 B); the
 # gradient and log-likelihood outputs are O(1) per series
 ALGO_BYTES_PER_STEP = 16.0

@@ -17,6 +17,20 @@ from . import spingp
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 CANDIDATES = (16, 32, 64, 128, 256)
+CHUNKS_PER_BLOCK = 128          # threads (chunks) per block of the chain kernels
+
+
+def wave_candidates(n, sms):
+    """Chunk lengths for which the chain kernels' block count is a whole
+    multiple of the SM count (1..16 blocks per SM), so that no SM runs a
+    partial last wave, plus the powers of two."""
+    out = set(CANDIDATES)
+    for per_sm in (1, 2, 3, 4, 5, 6, 8, 10, 12, 16):
+        blocks = per_sm * sms
+        L = -(-n // (blocks * CHUNKS_PER_BLOCK))
+        if 8 <= L <= 4096:
+            out.add(int(L))
+    return sorted(out)
 
 
 def _cache_path():
@@ -46,7 +60,7 @@ def _store(cache):
     os.replace(tmp, path)
 
 
-def tune(model, t, y, theta, what=spingp.WS_GRAD, candidates=CANDIDATES, reps=3):
+def tune(model, t, y, theta, what=spingp.WS_GRAD, candidates=None, reps=3):
     """Pick and set the fastest chunk length for this call kind and size.
     Returns the chosen length (0 = library default)."""
     if os.environ.get("SPINGP_TUNE", "1") == "0":
@@ -60,6 +74,9 @@ def tune(model, t, y, theta, what=spingp.WS_GRAD, candidates=CANDIDATES, reps=3)
         return cache[key]
     call = {spingp.WS_GRAD: model.grad, spingp.WS_LOGLIK: model.loglik,
             spingp.WS_POSTERIOR: model.posterior}[what]
+    if candidates is None:
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        candidates = wave_candidates(n, sms)
     best, best_ms = 0, float("inf")
     for L in candidates:
         if L * 4 > n and L != candidates[0]:

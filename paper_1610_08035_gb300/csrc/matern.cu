@@ -27,6 +27,7 @@
 namespace spg {
 
 static constexpr double LOG_2PI = 1.8378770664093454836;
+static constexpr double LN2 = 0.69314718055994530942;
 
 struct ChainArgs {
     const double* t;
@@ -34,6 +35,7 @@ struct ChainArgs {
     int64_t n;
     int64_t L;
     int64_t nchunks;
+    int64_t nblocks;   // ceil(nchunks / CTA)
     const double* theta;
     int* status;
 };
@@ -43,85 +45,152 @@ __device__ __forceinline__ bool theta_ok(double ell, double sf, double s2) {
     return ell > 0.0 && sf > 0.0 && s2 > 0.0 && isfinite(ell) && isfinite(sf) && isfinite(s2);
 }
 
+// ------------------------------------------------------------------ chunk-tree constants
+
+// The chain kernels group CTA consecutive chunks per thread block.  Their
+// elements are the leaves of a binary tree of depth CTA_LV whose nodes
+// (255 per block) are the odd-even reduction levels inside the block: node
+// (l, j) eliminates the interior boundary nodes of chunks [j 2^l, (j+1) 2^l).
+static constexpr int CTA = 128;
+static constexpr int CTA_LV = 7;
+static constexpr int TREE = 2 * CTA;      // node slots per block (255 used)
+static_assert((1 << CTA_LV) == CTA, "CTA must be 2^CTA_LV");
+
+__device__ __forceinline__ int tree_off(int level) { return TREE - (TREE >> level); }
+
+// Renormalise a running product to [1, 2) and move its binary exponent into
+// an integer (bit operations only), so that log det needs one log per chunk.
+__device__ __forceinline__ void renorm(double& prod, int& expo) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(prod);
+    expo += (int)((bits >> 52) & 0x7ffULL) - 1023;
+    prod = __longlong_as_double((long long)((bits & 0x800FFFFFFFFFFFFFULL) | 0x3FF0000000000000ULL));
+}
+
 // ------------------------------------------------------------------ k_fold
 
+// One thread per chunk: discretise every step (storing Phi for the later
+// pass) and eliminate the chunk's interior nodes into its element; then the
+// block's odd-even up-sweep over its CTA elements, writing every tree node
+// and the block total.  The conditional covariance is carried as C - Pinf,
+// so the prediction is a single sandwich Phi (C - Pinf) Phi^T.
 template <int B>
-__global__ void __launch_bounds__(128) k_fold(ChainArgs a, double* __restrict__ E) {
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= a.nchunks) return;
+__global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict__ nodes, double* __restrict__ btot,
+                                              double* __restrict__ phis) {
+    constexpr int NE = Dims<B>::NE;
+    __shared__ double sm[CTA * NE];
+    const int tid = threadIdx.x;
+    const int64_t blk = blockIdx.x;
+    const int64_t c = blk * CTA + tid;
+    const int64_t nc = a.nchunks;
     const double ell = a.theta[0], sf = a.theta[1], s2 = a.theta[2];
     int bad = theta_ok<B>(ell, sf, s2) ? 0 : ST_EINVAL;
     const double lam = sqrt(2.0 * B - 1.0) / ell;
-    const int64_t s = c * a.L;
-    const int64_t e = min(a.n, s + a.L);
     Elem<B> el;
     elem_identity<B>(el);
-    if (s == 0) {
-        // the first state has the stationary prior: no dependence on an earlier node
+    if (c < nc) {
+        const int64_t s = c * a.L;
+        const int64_t e = min(a.n, s + a.L);
+        // el.C holds C - Pinf until the end of the chunk
+        if (s == 0) {
+            // the first state has the stationary prior: no dependence on an earlier node
 #pragma unroll
-        for (int i = 0; i < B; ++i)
+            for (int i = 0; i < B; ++i)
 #pragma unroll
-            for (int j = 0; j < B; ++j) { el.A[i][j] = 0.0; el.C[i][j] = sf * p1<B>(i, j); }
-    }
-    double tp = (s > 0) ? a.t[s - 1] : 0.0;
-    for (int64_t i = s; i < e; ++i) {
-        const double ti = a.t[i], yi = a.y[i];
-        if (!isfinite(ti) || !isfinite(yi)) bad |= ST_ENONFINITE;
-        if (i > 0) {
-            const double dt = ti - tp;
-            if (dt < 0.0) bad |= ST_ENOTSORTED;
-            const double x = lam * dt;
-            double Ph[B][B], T[B][B], D[B][B];
-            phi<B>(x, exp(-x), Ph);
-            // A <- Phi A,  bv <- Phi bv,  C <- Phi (C - Pinf) Phi^T + Pinf
-            mat_mul<B>(Ph, el.A, T);
+                for (int j = 0; j < B; ++j) { el.A[i][j] = 0.0; el.C[i][j] = 0.0; }
+        } else {
 #pragma unroll
-            for (int r = 0; r < B; ++r)
+            for (int i = 0; i < B; ++i)
 #pragma unroll
-                for (int q = 0; q < B; ++q) el.A[r][q] = T[r][q];
-            double w[B];
-            mat_vec<B>(Ph, el.bv, w);
-#pragma unroll
-            for (int r = 0; r < B; ++r) el.bv[r] = w[r];
-#pragma unroll
-            for (int r = 0; r < B; ++r)
-#pragma unroll
-                for (int q = 0; q < B; ++q) D[r][q] = el.C[r][q] - sf * p1<B>(r, q);
-            mat_mul<B>(Ph, D, T);
-            mat_mul_t_sym<B>(T, Ph, el.C);
-#pragma unroll
-            for (int r = 0; r < B; ++r)
-#pragma unroll
-                for (int q = 0; q < B; ++q) el.C[r][q] += sf * p1<B>(r, q);
+                for (int j = 0; j < B; ++j) el.C[i][j] = -sf * p1<B>(i, j);
         }
-        // condition on y_i: innovation of y_i given the node before the chunk
-        const double S = el.C[0][0] + s2;
-        const double rS = 1.0 / S;
-        const double res = yi - el.bv[0];
-        double a0[B], c0[B];
+        double tp = (s > 0) ? a.t[s - 1] : 0.0;
+        for (int64_t i = s; i < e; ++i) {
+            const double ti = a.t[i], yi = a.y[i];
+            if (!isfinite(ti) || !isfinite(yi)) bad |= ST_ENONFINITE;
+            if (i > 0) {
+                const double dt = ti - tp;
+                if (dt < 0.0) bad |= ST_ENOTSORTED;
+                const double x = lam * dt;
+                double Ph[B][B], T[B][B];
+                phi<B>(x, exp(-x), Ph);
+                {
+                    double* ph = phis + ((i - s) * (B * B)) * nc + c;
 #pragma unroll
-        for (int r = 0; r < B; ++r) { a0[r] = el.A[0][r]; c0[r] = el.C[r][0]; }
-        const double rr = res * rS;
+                    for (int r = 0; r < B; ++r)
 #pragma unroll
-        for (int r = 0; r < B; ++r) {
-            el.eta[r] = fma(a0[r], rr, el.eta[r]);
-            const double ar = a0[r] * rS;
+                        for (int q = 0; q < B; ++q) ph[(r * B + q) * nc] = Ph[r][q];
+                }
+                // A <- Phi A,  bv <- Phi bv,  C <- Phi (C - Pinf) Phi^T + Pinf
+                mat_mul<B>(Ph, el.A, T);
 #pragma unroll
-            for (int q = r; q < B; ++q) { el.J[r][q] = fma(ar, a0[q], el.J[r][q]); el.J[q][r] = el.J[r][q]; }
+                for (int r = 0; r < B; ++r)
+#pragma unroll
+                    for (int q = 0; q < B; ++q) el.A[r][q] = T[r][q];
+                double w[B];
+                mat_vec<B>(Ph, el.bv, w);
+#pragma unroll
+                for (int r = 0; r < B; ++r) el.bv[r] = w[r];
+                mat_mul<B>(Ph, el.C, T);
+                mat_mul_t_sym<B>(T, Ph, el.C);
+            }
+            // condition on y_i: innovation of y_i given the node before the chunk
+            double a0[B], c0[B];
+#pragma unroll
+            for (int r = 0; r < B; ++r) {
+                a0[r] = el.A[0][r];
+                c0[r] = (p1<B>(r, 0) != 0.0) ? el.C[r][0] + sf * p1<B>(r, 0) : el.C[r][0];
+            }
+            const double S = c0[0] + s2;
+            const double rS = 1.0 / S;
+            const double res = yi - el.bv[0];
+            const double rr = res * rS;
+#pragma unroll
+            for (int r = 0; r < B; ++r) {
+                el.eta[r] = fma(a0[r], rr, el.eta[r]);
+                const double ar = a0[r] * rS;
+#pragma unroll
+                for (int q = r; q < B; ++q) { el.J[r][q] = fma(ar, a0[q], el.J[r][q]); el.J[q][r] = el.J[r][q]; }
+            }
+#pragma unroll
+            for (int r = 0; r < B; ++r) {
+                el.bv[r] = fma(c0[r], rr, el.bv[r]);
+                const double g = c0[r] * rS;
+#pragma unroll
+                for (int q = 0; q < B; ++q) el.A[r][q] = fma(-g, a0[q], el.A[r][q]);
+#pragma unroll
+                for (int q = r; q < B; ++q) { el.C[r][q] = fma(-g, c0[q], el.C[r][q]); el.C[q][r] = el.C[r][q]; }
+            }
+            tp = ti;
         }
 #pragma unroll
-        for (int r = 0; r < B; ++r) {
-            el.bv[r] = fma(c0[r], rr, el.bv[r]);
-            const double g = c0[r] * rS;
+        for (int r = 0; r < B; ++r)
 #pragma unroll
-            for (int q = 0; q < B; ++q) el.A[r][q] = fma(-g, a0[q], el.A[r][q]);
-#pragma unroll
-            for (int q = r; q < B; ++q) { el.C[r][q] = fma(-g, c0[q], el.C[r][q]); el.C[q][r] = el.C[r][q]; }
-        }
-        tp = ti;
+            for (int q = 0; q < B; ++q) el.C[r][q] += sf * p1<B>(r, q);
     }
     if (bad) atomicOr(a.status, bad);
-    elem_store<B>(E, a.nchunks, c, el);
+    // odd-even up-sweep inside the block (chunks past the end are identities)
+    const int64_t nld = a.nblocks * TREE;
+    elem_store<B>(nodes, nld, blk * TREE + tid, el);
+    elem_store<B>(sm, 1, (int64_t)tid * NE, el);
+    __syncthreads();
+#pragma unroll 1
+    for (int l = 1; l <= CTA_LV; ++l) {
+        const int cnt = CTA >> l;
+        Elem<B> r;
+        if (tid < cnt) {
+            Elem<B> x, y;
+            elem_load<B>(sm, 1, (int64_t)(2 * tid) * NE, x);
+            elem_load<B>(sm, 1, (int64_t)(2 * tid + 1) * NE, y);
+            combine<B>(x, y, r);
+        }
+        __syncthreads();
+        if (tid < cnt) {
+            elem_store<B>(sm, 1, (int64_t)tid * NE, r);
+            elem_store<B>(nodes, nld, blk * TREE + tree_off(l) + tid, r);
+            if (l == CTA_LV) elem_store<B>(btot, a.nblocks, blk, r);
+        }
+        __syncthreads();
+    }
 }
 
 // ------------------------------------------------------------------ k_scan_tile (odd-even reduction)
@@ -272,259 +341,336 @@ __global__ void __launch_bounds__(TS) k_scan_tile(const double* __restrict__ E, 
 
 // ------------------------------------------------------------------ k_chunk (forward, then reverse sweep)
 
-// per-chunk partial sums: ll, d/dlam, d/d(s_n), the P1-adjoint (packed)
+// per-block partial sums: ll, d/dlam, d/d(s_n), the adjoint of Pinf on the
+// entries where P1 is non-zero (packed; the others stay zero)
 template <int B> struct Acc { static constexpr int N = 3 + Dims<B>::NS; };
-// per-step stored values: predicted mean (B), predicted covariance (packed), innovation, exp(-x)
+// per-step stored values: predicted mean (B), predicted covariance minus Pinf
+// (packed), innovation, 1/S
 template <int B> struct Stored { static constexpr int N = B + Dims<B>::NS + 2; };
 
+// One thread per chunk, CTA chunks per block.
+//  1. Back-substitution of the block's odd-even tree: from the block's own
+//     prefix state and suffix information (grid level) down to every chunk.
+//  2. Forward: the Kalman recursion over the chunk from its prefix state,
+//     prediction-error log-likelihood; for BWD modes the predicted moments
+//     are stored per step.
+//  3. BWD: the reverse sweep.  At the chunk's last step the suffix
+//     information (eta, J) becomes the adjoint of the filtered state,
+//     lh = -(I + J P)^-1 (eta - J m), Lh = (I + J P)^-1 J; then per step
+//     (inversion-free; the modified Bryson-Frazier form of the smoother):
+//       al = v/S + k^T lh          (C^-1 y)_i
+//       cc = 1/S + k^T Lh k        (C^-1)_ii
+//       lt = lh - al e1,  Lt = (I - k e1^T)^T Lh (I - k e1^T) + e1 e1^T / S
+//       G  = (lt lt^T - Lt)/2      d ll / d(predicted covariance)
+//       lh <- Phi^T lt, Lh <- Phi^T Lt Phi   (to the previous step)
+//     posterior mean_i = y_i - s_n al, latent variance = s_n k_0 - s_n^2 k^T Lh k
+//     (the diagonal of the selected inverse); gradient terms
+//       d ll/dx_i = -lt^T F1 mb + 2 <G, F1 (Pb - Pinf)>,  x_i = lam dt_i
+//       d ll/ds_n = sum (al^2 - cc)/2,  d ll/dPinf = sum G - sum Phi^T G Phi.
+//  4. Fixed-order block reduction of the partial sums.
 template <int B, int MODE>
-__global__ void __launch_bounds__(128) k_chunk(ChainArgs a, const double* __restrict__ pre,
-                                               const double* __restrict__ suf, double* __restrict__ store,
+__global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __restrict__ nodes,
+                                               const double* __restrict__ bpre, const double* __restrict__ bsuf,
+                                               const double* __restrict__ phis, double* __restrict__ store,
                                                double* __restrict__ part, double* __restrict__ mean_out,
                                                double* __restrict__ var_out) {
-    constexpr int NS = Dims<B>::NS;
+    constexpr int NE = Dims<B>::NE;
+    constexpr int NM = Dims<B>::NM;
     constexpr int NF = Stored<B>::N;
+    constexpr int NA = Acc<B>::N;
     constexpr bool BWD = (MODE != MODE_LOGLIK);
     constexpr bool GRAD = (MODE == MODE_GRAD);
     constexpr bool POST = (MODE == MODE_POSTERIOR);
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= a.nchunks) return;
+    (void)NE;
+    __shared__ double spre[CTA * NM];
+    __shared__ double ssuf[BWD ? CTA * NM : 1];
+    __shared__ double red[CTA * NA];
+    const int tid = threadIdx.x;
+    const int64_t blk = blockIdx.x;
+    const int64_t c = blk * CTA + tid;
     const int64_t nc = a.nchunks;
+    const int64_t nld = a.nblocks * TREE;
     const double ell = a.theta[0], sf = a.theta[1], s2 = a.theta[2];
     const double lam = sqrt(2.0 * B - 1.0) / ell;
-    const int64_t s = c * a.L;
-    const int64_t e = min(a.n, s + a.L);
-    int bad = 0;
 
-    double m[B], P[B][B];
-    if (c > 0) {
-        vs_load<B>(pre, nc, c, m, P);
-    } else {
-#pragma unroll
-        for (int i = 0; i < B; ++i) { m[i] = 0.0;
-#pragma unroll
-            for (int j = 0; j < B; ++j) P[i][j] = 0.0; }
+    // ---- 1. back-substitution inside the block
+    if (tid == 0) {
+        double v[B], S[B][B];
+        vs_load<B>(bpre, a.nblocks, blk, v, S);
+        vs_store<B>(spre, 1, 0, v, S);
+        if constexpr (BWD) {
+            vs_load<B>(bsuf, a.nblocks, blk, v, S);
+            vs_store<B>(ssuf, 1, 0, v, S);
+        }
     }
-    double acc = 0.0;   // sum of v^2/S + log S
-    double tp = (s > 0) ? a.t[s - 1] : 0.0;
-    for (int64_t i = s; i < e; ++i) {
-        const double ti = a.t[i], yi = a.y[i];
-        double mb[B], Pb[B][B], ex = 1.0;
-        if (i == 0) {
+    __syncthreads();
+#pragma unroll 1
+    for (int l = CTA_LV; l >= 1; --l) {
+        const int cnt = CTA >> (l - 1);
+        double pm[B], pP[B][B], sv[B], sJ[B][B];
+        if (tid < cnt) {
+            const int parent = tid >> 1;
+            vs_load<B>(spre, 1, (int64_t)parent * NM, pm, pP);
+            if constexpr (BWD) vs_load<B>(ssuf, 1, (int64_t)parent * NM, sv, sJ);
+            Elem<B> sib;
+            if (tid & 1) {
+                elem_load<B>(nodes, nld, blk * TREE + tree_off(l - 1) + tid - 1, sib);
+                double om[B], oP[B][B];
+                state_through<B>(pm, pP, sib, om, oP);
 #pragma unroll
-            for (int r = 0; r < B; ++r) { mb[r] = 0.0;
+                for (int i = 0; i < B; ++i) { pm[i] = om[i];
 #pragma unroll
-                for (int q = 0; q < B; ++q) Pb[r][q] = sf * p1<B>(r, q); }
-        } else {
-            const double x = lam * (ti - tp);
-            ex = exp(-x);
-            double Ph[B][B], D[B][B], T[B][B];
-            phi<B>(x, ex, Ph);
-            mat_vec<B>(Ph, m, mb);
+                    for (int j = 0; j < B; ++j) pP[i][j] = oP[i][j]; }
+            } else if constexpr (BWD) {
+                elem_load<B>(nodes, nld, blk * TREE + tree_off(l - 1) + tid + 1, sib);
+                double ov[B], oJ[B][B];
+                info_through<B>(sib, sv, sJ, ov, oJ);
+#pragma unroll
+                for (int i = 0; i < B; ++i) { sv[i] = ov[i];
+#pragma unroll
+                    for (int j = 0; j < B; ++j) sJ[i][j] = oJ[i][j]; }
+            }
+        }
+        __syncthreads();
+        if (tid < cnt) {
+            vs_store<B>(spre, 1, (int64_t)tid * NM, pm, pP);
+            if constexpr (BWD) vs_store<B>(ssuf, 1, (int64_t)tid * NM, sv, sJ);
+        }
+        __syncthreads();
+    }
+
+    double acc[NA];
+#pragma unroll
+    for (int f = 0; f < NA; ++f) acc[f] = 0.0;
+    int bad = 0;
+    if (c < nc) {
+        const int64_t s = c * a.L;
+        const int64_t e = min(a.n, s + a.L);
+        // ---- 2. forward: filtered mean m and D = P - Pinf
+        double m[B], D[B][B];
+        {
+            double P[B][B];
+            vs_load<B>(spre, 1, (int64_t)tid * NM, m, P);
 #pragma unroll
             for (int r = 0; r < B; ++r)
 #pragma unroll
                 for (int q = 0; q < B; ++q) D[r][q] = P[r][q] - sf * p1<B>(r, q);
-            mat_mul<B>(Ph, D, T);
-            mat_mul_t_sym<B>(T, Ph, Pb);
-#pragma unroll
-            for (int r = 0; r < B; ++r)
-#pragma unroll
-                for (int q = 0; q < B; ++q) Pb[r][q] += sf * p1<B>(r, q);
         }
-        const double S = Pb[0][0] + s2;
-        if (!(S > 0.0) || !isfinite(S)) bad |= ST_ENUMERIC;
-        const double rS = 1.0 / S;
-        const double v = yi - mb[0];
-        acc += fma(v * v, rS, log(S));
-        if constexpr (BWD) {
+        double quad = 0.0, prod = 1.0;
+        int expo = 0;
+        for (int64_t i = s; i < e; ++i) {
             const int64_t j = i - s;
-            double* st = store + (j * NF) * nc + c;
-            int f = 0;
+            const double yi = a.y[i];
+            double mb[B], Db[B][B];
+            if (i == 0) {
 #pragma unroll
-            for (int r = 0; r < B; ++r) st[(f++) * nc] = mb[r];
+                for (int r = 0; r < B; ++r) { mb[r] = 0.0;
 #pragma unroll
-            for (int r = 0; r < B; ++r)
-#pragma unroll
-                for (int q = r; q < B; ++q) st[(f++) * nc] = Pb[r][q];
-            st[(f++) * nc] = v;
-            st[(f++) * nc] = ex;
-        }
-        const double vr = v * rS;
-#pragma unroll
-        for (int r = 0; r < B; ++r) {
-            m[r] = fma(Pb[r][0], vr, mb[r]);
-            const double g = Pb[r][0] * rS;
-#pragma unroll
-            for (int q = r; q < B; ++q) { P[r][q] = fma(-g, Pb[q][0], Pb[r][q]); P[q][r] = P[r][q]; }
-        }
-        tp = ti;
-    }
-    const double llp = -0.5 * (acc + (double)(e - s) * LOG_2PI);
-    if (bad) atomicOr(a.status, bad);
-    if constexpr (!BWD) {
-        part[c] = llp;
-        return;
-    } else {
-        // adjoint of the filtered state at the chunk's last step from the
-        // information of all later observations: W = (I + J P)^-1,
-        // lh = -W (eta - J m), Lh = W J
-        double eta[B], J[B][B];
-        if (c + 1 < nc) {
-            vs_load<B>(suf, nc, c, eta, J);
-        } else {
-#pragma unroll
-            for (int i = 0; i < B; ++i) { eta[i] = 0.0;
-#pragma unroll
-                for (int j = 0; j < B; ++j) J[i][j] = 0.0; }
-        }
-        double lh[B], Lh[B][B];
-        {
-            double N[B][B], W[B][B], w[B];
-            mat_mul<B>(J, P, N);
-#pragma unroll
-            for (int i = 0; i < B; ++i) N[i][i] += 1.0;
-            inv_pp<B>(N, W);
-            mat_vec<B>(J, m, w);
-#pragma unroll
-            for (int i = 0; i < B; ++i) w[i] = eta[i] - w[i];
-            mat_vec<B>(W, w, lh);
-#pragma unroll
-            for (int i = 0; i < B; ++i) lh[i] = -lh[i];
-            mat_mul<B>(W, J, Lh);
-            symmetrize<B>(Lh);
-        }
-        double gl = 0.0, gs = 0.0, GP[B][B];
-#pragma unroll
-        for (int i = 0; i < B; ++i)
-#pragma unroll
-            for (int j = 0; j < B; ++j) GP[i][j] = 0.0;
-        for (int64_t i = e - 1; i >= s; --i) {
-            const int64_t j = i - s;
-            const double* st = store + (j * NF) * nc + c;
-            double mb[B], Pb[B][B];
-            int f = 0;
-#pragma unroll
-            for (int r = 0; r < B; ++r) mb[r] = st[(f++) * nc];
-#pragma unroll
-            for (int r = 0; r < B; ++r)
-#pragma unroll
-                for (int q = r; q < B; ++q) { Pb[r][q] = st[(f++) * nc]; Pb[q][r] = Pb[r][q]; }
-            const double v = st[(f++) * nc];
-            const double ex = st[(f++) * nc];
-            const double S = Pb[0][0] + s2;
-            const double rS = 1.0 / S;
-            double k[B];
-#pragma unroll
-            for (int r = 0; r < B; ++r) k[r] = Pb[r][0] * rS;
-            double kl = 0.0, u[B], kuk = 0.0;
-#pragma unroll
-            for (int r = 0; r < B; ++r) kl = fma(k[r], lh[r], kl);
-            mat_vec<B>(Lh, k, u);
-#pragma unroll
-            for (int r = 0; r < B; ++r) kuk = fma(k[r], u[r], kuk);
-            // data-space adjoint: al = (C^-1 y)_i, cc = (C^-1)_ii
-            const double al = fma(v, rS, kl);
-            const double cc = rS + kuk;
-            gs = fma(al, al, gs) - cc;
-            if constexpr (POST) {
-                mean_out[i] = fma(-s2, al, a.y[i]);
-                var_out[i] = s2 * k[0] - s2 * s2 * kuk;
-            }
-            // adjoint at the predicted level: lt, Lt; d l / d(predicted cov) = G
-            double lt[B], Lt[B][B], G[B][B];
-#pragma unroll
-            for (int r = 0; r < B; ++r) {
-                lt[r] = lh[r];
-#pragma unroll
-                for (int q = 0; q < B; ++q) Lt[r][q] = Lh[r][q];
-            }
-            lt[0] -= al;
-#pragma unroll
-            for (int q = 1; q < B; ++q) { Lt[0][q] -= u[q]; Lt[q][0] = Lt[0][q]; }
-            Lt[0][0] = Lt[0][0] - 2.0 * u[0] + cc;
-            if constexpr (GRAD) {
+                    for (int q = 0; q < B; ++q) Db[r][q] = 0.0; }
+            } else {
+                double Ph[B][B], T[B][B];
+                const double* ph = phis + (j * (B * B)) * nc + c;
 #pragma unroll
                 for (int r = 0; r < B; ++r)
 #pragma unroll
-                    for (int q = r; q < B; ++q) {
-                        G[r][q] = 0.5 * fma(lt[r], lt[q], -Lt[r][q]);
-                        G[q][r] = G[r][q];
-                        GP[r][q] += G[r][q];
-                    }
+                    for (int q = 0; q < B; ++q) Ph[r][q] = ph[(r * B + q) * nc];
+                mat_vec<B>(Ph, m, mb);
+                mat_mul<B>(Ph, D, T);
+                mat_mul_t_sym<B>(T, Ph, Db);
             }
-            if (i > 0) {
-                const double dt = a.t[i] - a.t[i - 1];
-                const double x = lam * dt;
-                if constexpr (GRAD) {
-                    // d l / dx = -lt^T F1 mb + 2 <G, F1 (Pb - Pinf)>
-                    double fm = 0.0, fg = 0.0;
+            double p0[B];   // first column of the predicted covariance
 #pragma unroll
-                    for (int r = 0; r + 1 < B; ++r) fm = fma(lt[r], mb[r + 1], fm);
-                    double cm = 0.0;
+            for (int r = 0; r < B; ++r) p0[r] = (r == 0 || p1<B>(r, 0) != 0.0) ? Db[r][0] + sf * p1<B>(r, 0) : Db[r][0];
+            const double S = p0[0] + s2;
+            if (!(S > 0.0) || !isfinite(S)) bad |= ST_ENUMERIC;
+            const double rS = 1.0 / S;
+            const double v = yi - mb[0];
+            quad = fma(v * v, rS, quad);
+            prod *= S;
+            renorm(prod, expo);
+            if constexpr (BWD) {
+                double* st = store + (j * NF) * nc + c;
+                int f = 0;
 #pragma unroll
-                    for (int q = 0; q < B; ++q) cm = fma(fcoef<B>(q), mb[q], cm);
-                    fm = fma(-lt[B - 1], cm, fm);
-                    double D[B][B];
+                for (int r = 0; r < B; ++r) st[(f++) * nc] = mb[r];
 #pragma unroll
-                    for (int r = 0; r < B; ++r)
+                for (int r = 0; r < B; ++r)
 #pragma unroll
-                        for (int q = 0; q < B; ++q) D[r][q] = Pb[r][q] - sf * p1<B>(r, q);
+                    for (int q = r; q < B; ++q) st[(f++) * nc] = Db[r][q];
+                st[(f++) * nc] = v;
+                st[(f++) * nc] = rS;
+            }
+            const double vr = v * rS;
 #pragma unroll
-                    for (int r = 0; r + 1 < B; ++r)
+            for (int r = 0; r < B; ++r) {
+                m[r] = fma(p0[r], vr, mb[r]);
+                const double g = p0[r] * rS;
 #pragma unroll
-                        for (int q = 0; q < B; ++q) fg = fma(G[r][q], D[r + 1][q], fg);
+                for (int q = r; q < B; ++q) { D[r][q] = fma(-g, p0[q], Db[r][q]); D[q][r] = D[r][q]; }
+            }
+        }
+        acc[0] = -0.5 * (quad + log(prod) + (double)expo * LN2 + (double)(e - s) * LOG_2PI);
+
+        if constexpr (BWD) {
+            // ---- 3. reverse sweep, seeded by the information after the chunk
+            double lh[B], Lh[B][B];
+            {
+                double eta[B], J[B][B], P[B][B], N[B][B], W[B][B], w[B];
+                vs_load<B>(ssuf, 1, (int64_t)tid * NM, eta, J);
 #pragma unroll
-                    for (int q = 0; q < B; ++q) {
-                        double cd = 0.0;
+                for (int r = 0; r < B; ++r)
 #pragma unroll
-                        for (int jj = 0; jj < B; ++jj) cd = fma(fcoef<B>(jj), D[jj][q], cd);
-                        fg = fma(-G[B - 1][q], cd, fg);
-                    }
-                    gl = fma(2.0 * fg - fm, dt, gl);
+                    for (int q = 0; q < B; ++q) P[r][q] = D[r][q] + sf * p1<B>(r, q);
+                mat_mul<B>(J, P, N);
+#pragma unroll
+                for (int i = 0; i < B; ++i) N[i][i] += 1.0;
+                inv_pp<B>(N, W);
+                mat_vec<B>(J, m, w);
+#pragma unroll
+                for (int i = 0; i < B; ++i) w[i] = eta[i] - w[i];
+                mat_vec<B>(W, w, lh);
+#pragma unroll
+                for (int i = 0; i < B; ++i) lh[i] = -lh[i];
+                mat_mul<B>(W, J, Lh);
+                symmetrize<B>(Lh);
+            }
+            double gl = 0.0, gs = 0.0, GP[B][B];
+#pragma unroll
+            for (int i = 0; i < B; ++i)
+#pragma unroll
+                for (int j = 0; j < B; ++j) GP[i][j] = 0.0;
+            for (int64_t i = e - 1; i >= s; --i) {
+                const int64_t j = i - s;
+                const double* st = store + (j * NF) * nc + c;
+                double mb[B], Db[B][B];
+                int f = 0;
+#pragma unroll
+                for (int r = 0; r < B; ++r) mb[r] = st[(f++) * nc];
+#pragma unroll
+                for (int r = 0; r < B; ++r)
+#pragma unroll
+                    for (int q = r; q < B; ++q) { Db[r][q] = st[(f++) * nc]; Db[q][r] = Db[r][q]; }
+                const double v = st[(f++) * nc];
+                const double rS = st[(f++) * nc];
+                double k[B];
+#pragma unroll
+                for (int r = 0; r < B; ++r)
+                    k[r] = ((r == 0 || p1<B>(r, 0) != 0.0) ? Db[r][0] + sf * p1<B>(r, 0) : Db[r][0]) * rS;
+                double kl = 0.0, u[B], kuk = 0.0;
+#pragma unroll
+                for (int r = 0; r < B; ++r) kl = fma(k[r], lh[r], kl);
+                mat_vec<B>(Lh, k, u);
+#pragma unroll
+                for (int r = 0; r < B; ++r) kuk = fma(k[r], u[r], kuk);
+                const double al = fma(v, rS, kl);     // (C^-1 y)_i
+                const double cc = rS + kuk;           // (C^-1)_ii
+                if constexpr (GRAD) gs = fma(al, al, gs) - cc;
+                if constexpr (POST) {
+                    mean_out[i] = fma(-s2, al, a.y[i]);
+                    var_out[i] = s2 * k[0] - s2 * s2 * kuk;
                 }
-                double Ph[B][B], T[B][B];
-                phi<B>(x, ex, Ph);
-                mat_tvec<B>(Ph, lt, lh);
-                mat_mul<B>(Lt, Ph, T);
-                mat_tmul_sym<B>(Ph, T, Lh);
+                double lt[B], Lt[B][B], G[B][B];
+#pragma unroll
+                for (int r = 0; r < B; ++r) {
+                    lt[r] = lh[r];
+#pragma unroll
+                    for (int q = 0; q < B; ++q) Lt[r][q] = Lh[r][q];
+                }
+                lt[0] -= al;
+#pragma unroll
+                for (int q = 1; q < B; ++q) { Lt[0][q] -= u[q]; Lt[q][0] = Lt[0][q]; }
+                Lt[0][0] = Lt[0][0] - 2.0 * u[0] + cc;
                 if constexpr (GRAD) {
 #pragma unroll
                     for (int r = 0; r < B; ++r)
 #pragma unroll
                         for (int q = r; q < B; ++q) {
-                            GP[r][q] -= 0.5 * fma(lh[r], lh[q], -Lh[r][q]);
-                            GP[q][r] = GP[r][q];
+                            G[r][q] = 0.5 * fma(lt[r], lt[q], -Lt[r][q]);
+                            G[q][r] = G[r][q];
+                            if (p1<B>(r, q) != 0.0) GP[r][q] += G[r][q];
                         }
                 }
+                if (i > 0) {
+                    const double dt = a.t[i] - a.t[i - 1];
+                    if constexpr (GRAD) {
+                        // d ll / dx = -lt^T F1 mb + 2 <G, F1 Db>
+                        double fm = 0.0, fg = 0.0, cm = 0.0;
+#pragma unroll
+                        for (int r = 0; r + 1 < B; ++r) fm = fma(lt[r], mb[r + 1], fm);
+#pragma unroll
+                        for (int q = 0; q < B; ++q) cm = fma(fcoef<B>(q), mb[q], cm);
+                        fm = fma(-lt[B - 1], cm, fm);
+#pragma unroll
+                        for (int r = 0; r + 1 < B; ++r)
+#pragma unroll
+                            for (int q = 0; q < B; ++q) fg = fma(G[r][q], Db[r + 1][q], fg);
+#pragma unroll
+                        for (int q = 0; q < B; ++q) {
+                            double cd = 0.0;
+#pragma unroll
+                            for (int jj = 0; jj < B; ++jj) cd = fma(fcoef<B>(jj), Db[jj][q], cd);
+                            fg = fma(-G[B - 1][q], cd, fg);
+                        }
+                        gl = fma(2.0 * fg - fm, dt, gl);
+                    }
+                    double Ph[B][B], T[B][B];
+                    const double* ph = phis + (j * (B * B)) * nc + c;
+#pragma unroll
+                    for (int r = 0; r < B; ++r)
+#pragma unroll
+                        for (int q = 0; q < B; ++q) Ph[r][q] = ph[(r * B + q) * nc];
+                    mat_tvec<B>(Ph, lt, lh);
+                    mat_mul<B>(Lt, Ph, T);
+                    mat_tmul_sym<B>(Ph, T, Lh);
+                    if constexpr (GRAD) {
+#pragma unroll
+                        for (int r = 0; r < B; ++r)
+#pragma unroll
+                            for (int q = r; q < B; ++q)
+                                if (p1<B>(r, q) != 0.0) GP[r][q] -= 0.5 * fma(lh[r], lh[q], -Lh[r][q]);
+                    }
+                }
+            }
+            if constexpr (GRAD) {
+                acc[1] = gl;
+                acc[2] = gs;
+                int f = 3;
+#pragma unroll
+                for (int r = 0; r < B; ++r)
+#pragma unroll
+                    for (int q = r; q < B; ++q) acc[f++] = GP[r][q];
             }
         }
-        constexpr int NA = Acc<B>::N;
-        part[0 * nc + c] = llp;
-        if constexpr (GRAD) {
-            part[1 * nc + c] = gl;
-            part[2 * nc + c] = gs;
-            int f = 3;
-#pragma unroll
-            for (int r = 0; r < B; ++r)
-#pragma unroll
-                for (int q = r; q < B; ++q) part[(f++) * nc + c] = GP[r][q];
-            static_assert(3 + NS == NA, "accumulator layout");
-        }
     }
+    if (bad) atomicOr(a.status, bad);
+    // ---- 4. fixed-order reduction of the block's partial sums
+    constexpr int NU = GRAD ? NA : 1;
+#pragma unroll
+    for (int f = 0; f < NU; ++f) red[f * CTA + tid] = acc[f];
+    __syncthreads();
+#pragma unroll 1
+    for (int w = CTA / 2; w > 0; w >>= 1) {
+        if (tid < w)
+#pragma unroll
+            for (int f = 0; f < NU; ++f) red[f * CTA + tid] += red[f * CTA + tid + w];
+        __syncthreads();
+    }
+    if (tid == 0)
+#pragma unroll
+        for (int f = 0; f < NU; ++f) part[f * a.nblocks + blk] = red[f * CTA];
 }
 
 // ------------------------------------------------------------------ k_finalize (fixed-order reduction)
 
 template <int B>
-__global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ part, int64_t nc, int na,
+__global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ part, int64_t nb, int na,
                                                   const double* __restrict__ theta, double* __restrict__ ll_out,
                                                   double* __restrict__ grad_out) {
     __shared__ double red[256 * Acc<B>::N];
     const int tid = threadIdx.x;
     for (int f = 0; f < na; ++f) {
         double s = 0.0;
-        for (int64_t c = tid; c < nc; c += 256) s += part[f * nc + c];
+        for (int64_t c = tid; c < nb; c += 256) s += part[f * nb + c];
         red[f * 256 + tid] = s;
     }
     __syncthreads();
@@ -556,17 +702,25 @@ __global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ par
 
 // ------------------------------------------------------------------ host side
 
-static constexpr int SCAN_TS = 64;
-static constexpr int SCAN_G = 8;
-static constexpr int CHUNK_TPB = 128;
+// grid-level reduction of the block totals: tiles of SCAN_TS threads x G
+// elements; small tiles keep each level spread over many SMs (the FP64 pipe
+// of a single SM would otherwise serialise the top of the tree)
+static constexpr int SCAN_TS = 32;
+static constexpr int SCAN_GTOP = 1;    // largest G of a single top tile
+static constexpr int SCAN_GMID = 1;    // G of the tiles of a multi-tile level
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Workspace layout: [status | elements | prefix | suffix | scan levels | partials | stored steps]
+static int64_t top_g(int64_t ne) { return (ne + SCAN_TS - 1) / SCAN_TS; }
+static bool single_tile(int64_t ne) { return ne <= (int64_t)SCAN_TS * SCAN_GTOP; }
+static int64_t mid_tiles(int64_t ne) { return (ne + (int64_t)SCAN_TS * SCAN_GMID - 1) / ((int64_t)SCAN_TS * SCAN_GMID); }
+
+// Workspace: [status | tree nodes | block totals | block prefix | block suffix |
+//             grid scan levels | Phi per step | block partials | stored steps]
 template <int B>
 struct Layout {
-    int64_t nc;
-    size_t off_E, off_pre, off_suf, off_part, off_store, total;
+    int64_t nc, nb;
+    size_t off_nodes, off_btot, off_bpre, off_bsuf, off_phis, off_part, off_store, total;
     int nlev;
     int64_t lev_n[8];
     size_t lev_tot[8], lev_pre[8], lev_suf[8];
@@ -574,15 +728,16 @@ struct Layout {
     Layout(int64_t n, int64_t L, int mode) {
         constexpr int NE = Dims<B>::NE, NM = Dims<B>::NM;
         nc = (n + L - 1) / L;
+        nb = (nc + CTA - 1) / CTA;
         size_t o = 256;  // status word region
-        off_E = o; o = align256(o + sizeof(double) * NE * nc);
-        off_pre = o; o = align256(o + sizeof(double) * NM * nc);
-        off_suf = o; o = align256(o + sizeof(double) * NM * nc);
+        off_nodes = o; o = align256(o + sizeof(double) * NE * (size_t)nb * TREE);
+        off_btot = o; o = align256(o + sizeof(double) * NE * nb);
+        off_bpre = o; o = align256(o + sizeof(double) * NM * nb);
+        off_bsuf = o; o = align256(o + sizeof(double) * NM * nb);
         nlev = 0;
-        int64_t ne = nc;
-        const int64_t per_tile = (int64_t)SCAN_TS * SCAN_G;
-        while (ne > per_tile) {
-            const int64_t nt = (ne + per_tile - 1) / per_tile;
+        int64_t ne = nb;
+        while (!single_tile(ne)) {
+            const int64_t nt = mid_tiles(ne);
             lev_n[nlev] = nt;
             lev_tot[nlev] = o; o = align256(o + sizeof(double) * NE * nt);
             lev_pre[nlev] = o; o = align256(o + sizeof(double) * NM * nt);
@@ -590,7 +745,8 @@ struct Layout {
             ++nlev;
             ne = nt;
         }
-        off_part = o; o = align256(o + sizeof(double) * Acc<B>::N * nc);
+        off_phis = o; o = align256(o + sizeof(double) * (size_t)(B * B) * L * nc);
+        off_part = o; o = align256(o + sizeof(double) * Acc<B>::N * nb);
         off_store = o;
         if (mode != MODE_LOGLIK) o = align256(o + sizeof(double) * Stored<B>::N * (size_t)L * nc);
         total = o;
@@ -600,38 +756,36 @@ struct Layout {
 template <int B>
 static void scan_level(const double* E, int64_t ne, double* pre_out, double* suf_out, const Layout<B>& lay,
                        char* ws, int lev, cudaStream_t st) {
-    const int64_t per_tile = (int64_t)SCAN_TS * SCAN_G;
     const size_t smem = ScanSmem<B, SCAN_TS>::bytes;
-    if (ne <= per_tile) {
-        k_scan_tile<B, SCAN_TS, true><<<1, SCAN_TS, smem, st>>>(E, ne, SCAN_G, nullptr, 1, nullptr, nullptr,
-                                                                pre_out, suf_out);
+    if (single_tile(ne)) {
+        k_scan_tile<B, SCAN_TS, true><<<1, SCAN_TS, smem, st>>>(E, ne, (int)top_g(ne), nullptr, 1, nullptr,
+                                                                nullptr, pre_out, suf_out);
         return;
     }
     const int64_t nt = lay.lev_n[lev];
     double* tot = (double*)(ws + lay.lev_tot[lev]);
     double* tpre = (double*)(ws + lay.lev_pre[lev]);
     double* tsuf = (double*)(ws + lay.lev_suf[lev]);
-    k_scan_tile<B, SCAN_TS, false><<<(unsigned)nt, SCAN_TS, smem, st>>>(E, ne, SCAN_G, tot, nt, nullptr, nullptr,
-                                                                       nullptr, nullptr);
+    k_scan_tile<B, SCAN_TS, false><<<(unsigned)nt, SCAN_TS, smem, st>>>(E, ne, SCAN_GMID, tot, nt, nullptr,
+                                                                       nullptr, nullptr, nullptr);
     scan_level<B>(tot, nt, tpre, tsuf, lay, ws, lev + 1, st);
-    k_scan_tile<B, SCAN_TS, true><<<(unsigned)nt, SCAN_TS, smem, st>>>(E, ne, SCAN_G, nullptr, nt, tpre, tsuf,
+    k_scan_tile<B, SCAN_TS, true><<<(unsigned)nt, SCAN_TS, smem, st>>>(E, ne, SCAN_GMID, nullptr, nt, tpre, tsuf,
                                                                       pre_out, suf_out);
+}
+
+template <int B>
+static int scan_launches(int64_t ne, const Layout<B>& lay, int lev) {
+    if (single_tile(ne)) return 1;
+    return 2 + scan_launches<B>(lay.lev_n[lev], lay, lev + 1);
 }
 
 template <int B>
 size_t matern_ws_bytes_t(int64_t n, int64_t L, int mode) { return Layout<B>(n, L, mode).total; }
 
 template <int B>
-static int scan_launches(int64_t ne, const Layout<B>& lay, int lev) {
-    const int64_t per_tile = (int64_t)SCAN_TS * SCAN_G;
-    if (ne <= per_tile) return 1;
-    return 2 + scan_launches<B>(lay.lev_n[lev], lay, lev + 1);
-}
-
-template <int B>
 int matern_launch_count_t(int64_t n, int64_t L, int mode) {
     Layout<B> lay(n, L, mode);
-    return 1 + scan_launches<B>(lay.nc, lay, 0) + 1 + 1;
+    return 1 + scan_launches<B>(lay.nb, lay, 0) + 1 + 1;
 }
 
 template <int B>
@@ -641,35 +795,38 @@ int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t 
     Layout<B> lay(n, L, mode);
     char* ws = (char*)wsv;
     int* status = (int*)ws;
-    double* E = (double*)(ws + lay.off_E);
-    double* pre = (double*)(ws + lay.off_pre);
-    double* suf = (double*)(ws + lay.off_suf);
+    double* nodes = (double*)(ws + lay.off_nodes);
+    double* btot = (double*)(ws + lay.off_btot);
+    double* bpre = (double*)(ws + lay.off_bpre);
+    double* bsuf = (double*)(ws + lay.off_bsuf);
+    double* phis = (double*)(ws + lay.off_phis);
     double* part = (double*)(ws + lay.off_part);
     double* store = (double*)(ws + lay.off_store);
-    ChainArgs a{t, y, n, L, lay.nc, theta, status};
-    const unsigned grid = (unsigned)((lay.nc + CHUNK_TPB - 1) / CHUNK_TPB);
+    ChainArgs a{t, y, n, L, lay.nc, lay.nb, theta, status};
+    const unsigned grid = (unsigned)lay.nb;
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
     if (ev) cudaEventRecord(ev[0], st);
-    k_fold<B><<<grid, CHUNK_TPB, 0, st>>>(a, E);
+    k_fold<B><<<grid, CTA, 0, st>>>(a, nodes, btot, phis);
     if (ev) cudaEventRecord(ev[1], st);
-    scan_level<B>(E, lay.nc, pre, suf, lay, ws, 0, st);
+    scan_level<B>(btot, lay.nb, bpre, bsuf, lay, ws, 0, st);
     if (ev) cudaEventRecord(ev[2], st);
     int na = 1;
     switch (mode) {
     case MODE_LOGLIK:
-        k_chunk<B, MODE_LOGLIK><<<grid, CHUNK_TPB, 0, st>>>(a, pre, suf, store, part, nullptr, nullptr);
+        k_chunk<B, MODE_LOGLIK><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part, nullptr, nullptr);
         break;
     case MODE_GRAD:
-        k_chunk<B, MODE_GRAD><<<grid, CHUNK_TPB, 0, st>>>(a, pre, suf, store, part, nullptr, nullptr);
+        k_chunk<B, MODE_GRAD><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part, nullptr, nullptr);
         na = Acc<B>::N;
         break;
     default:
-        k_chunk<B, MODE_POSTERIOR><<<grid, CHUNK_TPB, 0, st>>>(a, pre, suf, store, part, mean_out, var_out);
+        k_chunk<B, MODE_POSTERIOR><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part, mean_out,
+                                                        var_out);
         break;
     }
     if (ev) cudaEventRecord(ev[3], st);
     // the final reduction always runs (it is cheap), so the launch count is fixed per kind
-    k_finalize<B><<<1, 256, 0, st>>>(part, lay.nc, na, theta, ll_out, grad_out);
+    k_finalize<B><<<1, 256, 0, st>>>(part, lay.nb, na, theta, ll_out, grad_out);
     if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
