@@ -152,6 +152,35 @@ spingp_status spingp_profile_read(spingp_model* model, double* ms_out, int* call
 size_t spingp_probe_fp64_bytes(void);
 spingp_status spingp_probe_fp64(void* scratch, size_t scratch_bytes, double* tflops_out, void* stream);
 
+/* Size of the fixed device scratch used by spingp_loglik_noalloc (8 MiB). */
+#define SPINGP_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* Log-likelihood without any device allocation, for callers that cannot
+ * allocate device memory at the point of the call: code running while a
+ * stream is being captured into a CUDA graph without a memory pool, real-time
+ * or embedded callers whose memory is all reserved at start-up, plug-ins whose
+ * host framework owns the device allocator, or callers that must not risk the
+ * implicit device synchronisation an allocation or a free can cause.  (The
+ * paper has no counterpart: this is a deployment variant of spingp_loglik.)
+ *
+ * Same arguments and result as spingp_loglik, without the workspace: the
+ * scratch is a file-scope array of SPINGP_NOALLOC_SCRATCH_BYTES in the
+ * library's device image, which every GPU that loads the library keeps until
+ * the process exits.  A series whose spingp_workspace_bytes(model, n,
+ * SPINGP_WS_LOGLIK) exceeds that size is rejected with SPINGP_EINVAL before
+ * anything is launched (with the default chunk length this admits every
+ * n <= 65536 for state dimension b <= 3).  The call allocates nothing and
+ * frees nothing.  The first call on a device performs a one-time set-up for
+ * that device (looking up the array's device address); make that first call
+ * before capturing any stream.  All calls on a device share the one array
+ * and it keeps the last call's contents: the call clears what must start at
+ * zero itself, and two calls that can overlap on the GPU (different streams,
+ * or different host threads) race on the scratch and corrupt each other.
+ * With SPINGP_SYNC the call synchronises the stream and returns the device
+ * status, as spingp_loglik does. */
+spingp_status spingp_loglik_noalloc(const spingp_model* model, const double* t, const double* y, int64_t n,
+                                    const double* theta, double* ll_out, unsigned flags, void* stream);
+
 /* Synchronise the stream and return the device status recorded in ws by the
  * last call that used it (SPINGP_OK if none). */
 spingp_status spingp_ws_status(void* ws, void* stream);

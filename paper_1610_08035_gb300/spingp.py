@@ -23,8 +23,8 @@ KINDS = {"matern12": 1, "matern32": 2, "matern52": 3, "periodic": 4, "quasiperio
 EXPORTS = ("spingp_model_create", "spingp_model_destroy", "spingp_num_params", "spingp_state_dim",
            "spingp_set_chunk_len", "spingp_get_chunk_len", "spingp_workspace_bytes", "spingp_loglik",
            "spingp_grad", "spingp_posterior", "spingp_launch_count", "spingp_profile_enable",
-           "spingp_profile_read", "spingp_probe_fp64_bytes", "spingp_probe_fp64", "spingp_ws_status",
-           "spingp_status_str")
+           "spingp_profile_read", "spingp_probe_fp64_bytes", "spingp_probe_fp64", "spingp_loglik_noalloc",
+           "spingp_ws_status", "spingp_status_str")
 STAGES = ("elimination", "reduction", "chunk_pass", "final_reduction")
 
 _lib = None
@@ -69,6 +69,7 @@ def load():
     lib.spingp_probe_fp64_bytes.argtypes = []
     lib.spingp_probe_fp64_bytes.restype = sz
     lib.spingp_probe_fp64.argtypes = [vp, sz, ctypes.POINTER(ctypes.c_double), vp]
+    lib.spingp_loglik_noalloc.argtypes = [vp, dp, dp, i64, dp, dp, u32, vp]
     lib.spingp_ws_status.argtypes = [vp, vp]
     lib.spingp_status_str.argtypes = [ctypes.c_int]
     lib.spingp_status_str.restype = ctypes.c_char_p
@@ -191,6 +192,13 @@ def spingp_probe_fp64(device=None):
     _check(lib.spingp_probe_fp64(_ptr(scratch), scratch.numel(), ctypes.byref(out), _stream()),
            "spingp_probe_fp64")
     return out.value
+
+
+def spingp_loglik_noalloc(h, t, y, n, theta, ll_out, flags, stream=None):
+    """spingp_loglik without a workspace: the library's fixed device scratch
+    is used instead, so nothing is allocated (see include/spingp.h)."""
+    return load().spingp_loglik_noalloc(h, _ptr(t), _ptr(y), int(n), _ptr(theta), _ptr(ll_out), flags,
+                                        stream if stream is not None else _stream())
 
 
 def spingp_ws_status(ws, stream=None):
