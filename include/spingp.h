@@ -130,10 +130,47 @@ spingp_status spingp_posterior(const spingp_model* model, const double* t, const
                                const double* theta, double* ll_out, double* mean_out, double* var_out,
                                void* ws, size_t ws_bytes, unsigned flags, void* stream);
 
+/* ---- batches of independent series ----------------------------------------
+ * n_series series, each with its own hyperparameters, concatenated: series i
+ * owns steps [offsets[i], offsets[i+1]) of t and y, with offsets[0] = 0,
+ * offsets non-decreasing and offsets[n_series] = n_total (an empty series has
+ * log-likelihood 0 and a zero gradient).  offsets is a DEVICE array of
+ * n_series + 1 int64; n_series and n_total are host values (they size the
+ * launch, so a call can be captured into a CUDA graph).  theta is a device
+ * array of n_series x num_params entries (row i: series i).  Times must be
+ * non-decreasing within each series.  Malformed offsets are detected on the
+ * device (EINVAL through the status word) and then no series is processed.
+ * One odd-even reduction runs over the chunks of all series together: the
+ * first chunk of every series starts from the stationary prior, whose
+ * element passes no information between neighbouring series. */
+size_t spingp_workspace_bytes_batched(const spingp_model* model, int64_t n_series, int64_t n_total,
+                                      spingp_ws_kind what);
+
+/* Per-series log-likelihoods (Eq. ml2) into ll_out[0 .. n_series-1]. */
+spingp_status spingp_loglik_batched(const spingp_model* model, const int64_t* offsets, int64_t n_series,
+                                    int64_t n_total, const double* t, const double* y, const double* theta,
+                                    double* ll_out, void* ws, size_t ws_bytes, unsigned flags, void* stream);
+
+/* Per-series log-likelihoods and gradients (Sec. 2.4): ll_out[i] and
+ * grad_out[i * num_params + p]. */
+spingp_status spingp_grad_batched(const spingp_model* model, const int64_t* offsets, int64_t n_series,
+                                  int64_t n_total, const double* t, const double* y, const double* theta,
+                                  double* ll_out, double* grad_out, void* ws, size_t ws_bytes, unsigned flags,
+                                  void* stream);
+
+/* Per-step posterior mean and latent variance of every series (Eqs. mean6,
+ * k3), indexed like t and y; per-series log-likelihoods into ll_out (may be
+ * NULL). */
+spingp_status spingp_posterior_batched(const spingp_model* model, const int64_t* offsets, int64_t n_series,
+                                       int64_t n_total, const double* t, const double* y, const double* theta,
+                                       double* ll_out, double* mean_out, double* var_out, void* ws,
+                                       size_t ws_bytes, unsigned flags, void* stream);
+
 /* Number of kernels one call of the given kind launches for n steps (the
  * discretisation/elimination pass, the reduction tiles, the per-chunk pass
  * and the final reduction). */
 int spingp_launch_count(const spingp_model* model, int64_t n, spingp_ws_kind what);
+int spingp_launch_count_batched(const spingp_model* model, int64_t n_series, int64_t n_total, spingp_ws_kind what);
 
 /* Stage timing.  While enabled, every call on this model records CUDA events
  * on its stream around its four stages: 0 discretisation + in-chunk

@@ -60,6 +60,25 @@ int64_t chunk_len(const spingp_model* m, int64_t n) {
 
 bool single_matern(const spingp_model* m) { return m->ncomp == 1 && m->kinds[0] >= 1 && m->kinds[0] <= 3; }
 
+// the next five stage events of a profiled model (NULL when not profiling)
+spingp_status profile_slot(const spingp_model* m, cudaEvent_t** ev) {
+    *ev = NULL;
+    spg_prof* pr = m->prof;
+    if (!pr || !pr->on) return SPINGP_OK;
+    if (pr->used == pr->cap) {
+        const int cap = pr->cap ? 2 * pr->cap : 16;
+        cudaEvent_t(*nev)[5] = (cudaEvent_t(*)[5])realloc(pr->ev, sizeof(cudaEvent_t[5]) * cap);
+        if (!nev) return SPINGP_ENOMEM;
+        for (int i = pr->cap; i < cap; ++i)
+            for (int k = 0; k < 5; ++k)
+                if (cudaEventCreate(&nev[i][k]) != cudaSuccess) return SPINGP_ECUDA;
+        pr->ev = nev;
+        pr->cap = cap;
+    }
+    *ev = pr->ev[pr->used++];
+    return SPINGP_OK;
+}
+
 spingp_status run(const spingp_model* m, int mode, const double* t, const double* y, int64_t n,
                   const double* theta, double* ll, double* grad, double* mean, double* var, void* ws,
                   size_t ws_bytes, unsigned flags, void* stream) {
@@ -72,21 +91,46 @@ spingp_status run(const spingp_model* m, int mode, const double* t, const double
     if (st != SPINGP_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t* ev = NULL;
-    spg_prof* pr = m->prof;
-    if (pr && pr->on) {
-        if (pr->used == pr->cap) {
-            const int cap = pr->cap ? 2 * pr->cap : 16;
-            cudaEvent_t(*nev)[5] = (cudaEvent_t(*)[5])realloc(pr->ev, sizeof(cudaEvent_t[5]) * cap);
-            if (!nev) return SPINGP_ENOMEM;
-            for (int i = pr->cap; i < cap; ++i)
-                for (int k = 0; k < 5; ++k)
-                    if (cudaEventCreate(&nev[i][k]) != cudaSuccess) return SPINGP_ECUDA;
-            pr->ev = nev;
-            pr->cap = cap;
-        }
-        ev = pr->ev[pr->used++];
-    }
+    st = profile_slot(m, &ev);
+    if (st != SPINGP_OK) return st;
     if (spg::matern_run(m->b, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s, ev)) return SPINGP_ECUDA;
+    if (flags & SPINGP_SYNC) return spingp_ws_status(ws, stream);
+    return SPINGP_OK;
+}
+
+int64_t chunk_len_batched(const spingp_model* m, int64_t n_series, int64_t n_total) {
+    if (m->chunk_len > 0) return m->chunk_len;
+    // the single-series default for the whole batch, at most half the mean length
+    int64_t L = default_chunk(n_total);
+    const int64_t mean_len = n_series > 0 ? n_total / n_series : n_total;
+    while (L > 16 && 2 * L > mean_len) L /= 2;
+    return L;
+}
+
+int ws_mode(spingp_ws_kind what) {
+    return what == SPINGP_WS_GRAD ? spg::MODE_GRAD : what == SPINGP_WS_POSTERIOR ? spg::MODE_POSTERIOR
+                                                                                   : spg::MODE_LOGLIK;
+}
+
+spingp_status run_batched(const spingp_model* m, int mode, const int64_t* offsets, int64_t n_series,
+                          int64_t n_total, const double* t, const double* y, const double* theta, double* ll,
+                          double* grad, double* mean, double* var, void* ws, size_t ws_bytes, unsigned flags,
+                          void* stream) {
+    if (!m || !offsets || !theta || !ws || n_series < 1 || n_total < 0) return SPINGP_EINVAL;
+    if (n_total > 0 && (!t || !y)) return SPINGP_EINVAL;
+    if (((uintptr_t)ws & 255u) != 0) return SPINGP_EINVAL;
+    if (!single_matern(m)) return SPINGP_EUNSUPPORTED;
+    const int64_t L = chunk_len_batched(m, n_series, n_total);
+    if (ws_bytes < spg::matern_ws_bytes_batched(m->b, n_series, n_total, L, mode)) return SPINGP_EINVAL;
+    spingp_status st = prepare_device();
+    if (st != SPINGP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t* ev = NULL;
+    st = profile_slot(m, &ev);
+    if (st != SPINGP_OK) return st;
+    if (spg::matern_run_batched(m->b, mode, offsets, n_series, n_total, t, y, L, theta, ll, grad, mean, var, ws, s,
+                                ev))
+        return SPINGP_ECUDA;
     if (flags & SPINGP_SYNC) return spingp_ws_status(ws, stream);
     return SPINGP_OK;
 }
@@ -94,6 +138,40 @@ spingp_status run(const spingp_model* m, int mode, const double* t, const double
 }  // namespace
 
 extern "C" {
+
+size_t spingp_workspace_bytes_batched(const spingp_model* m, int64_t n_series, int64_t n_total,
+                                      spingp_ws_kind what) {
+    if (!m || n_series < 1 || n_total < 0 || !single_matern(m)) return 0;
+    return spg::matern_ws_bytes_batched(m->b, n_series, n_total, chunk_len_batched(m, n_series, n_total),
+                                        ws_mode(what));
+}
+
+spingp_status spingp_loglik_batched(const spingp_model* m, const int64_t* offsets, int64_t n_series,
+                                    int64_t n_total, const double* t, const double* y, const double* theta,
+                                    double* ll_out, void* ws, size_t ws_bytes, unsigned flags, void* stream) {
+    if (!ll_out) return SPINGP_EINVAL;
+    return run_batched(m, spg::MODE_LOGLIK, offsets, n_series, n_total, t, y, theta, ll_out, NULL, NULL, NULL, ws,
+                       ws_bytes, flags, stream);
+}
+
+spingp_status spingp_grad_batched(const spingp_model* m, const int64_t* offsets, int64_t n_series,
+                                  int64_t n_total, const double* t, const double* y, const double* theta,
+                                  double* ll_out, double* grad_out, void* ws, size_t ws_bytes, unsigned flags,
+                                  void* stream) {
+    if (!ll_out || !grad_out) return SPINGP_EINVAL;
+    return run_batched(m, spg::MODE_GRAD, offsets, n_series, n_total, t, y, theta, ll_out, grad_out, NULL, NULL,
+                       ws, ws_bytes, flags, stream);
+}
+
+spingp_status spingp_posterior_batched(const spingp_model* m, const int64_t* offsets, int64_t n_series,
+                                       int64_t n_total, const double* t, const double* y, const double* theta,
+                                       double* ll_out, double* mean_out, double* var_out, void* ws,
+                                       size_t ws_bytes, unsigned flags, void* stream) {
+    if (n_total > 0 && (!mean_out || !var_out)) return SPINGP_EINVAL;
+    return run_batched(m, spg::MODE_POSTERIOR, offsets, n_series, n_total, t, y, theta, ll_out, NULL, mean_out,
+                       var_out, ws, ws_bytes, flags, stream);
+}
+
 
 spingp_status spingp_model_create(const spingp_model_desc* d, spingp_model** out) {
     if (!out) return SPINGP_EINVAL;
@@ -179,6 +257,12 @@ int spingp_launch_count(const spingp_model* m, int64_t n, spingp_ws_kind what) {
     const int mode = what == SPINGP_WS_GRAD ? spg::MODE_GRAD
                    : what == SPINGP_WS_POSTERIOR ? spg::MODE_POSTERIOR : spg::MODE_LOGLIK;
     return spg::matern_launch_count(m->b, n, chunk_len(m, n), mode);
+}
+
+int spingp_launch_count_batched(const spingp_model* m, int64_t n_series, int64_t n_total, spingp_ws_kind what) {
+    if (!m || n_series < 1 || n_total < 0 || !single_matern(m)) return -1;
+    return spg::matern_launch_count_batched(m->b, n_series, n_total, chunk_len_batched(m, n_series, n_total),
+                                            ws_mode(what));
 }
 
 spingp_status spingp_profile_enable(spingp_model* m, int on) {

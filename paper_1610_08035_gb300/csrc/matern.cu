@@ -34,11 +34,56 @@ struct ChainArgs {
     const double* y;
     int64_t n;
     int64_t L;
-    int64_t nchunks;
-    int64_t nblocks;   // ceil(nchunks / CTA)
+    int64_t nchunks;          // chunk slots (for batches: an upper bound)
+    int64_t nblocks;          // ceil(nchunks / CTA)
     const double* theta;
     int* status;
+    // batches of independent series (NULL / 0 for one series)
+    const int64_t* offsets;   // [nseries + 1] first step of each series
+    const int64_t* cstart;    // [nseries + 1] first chunk of each series
+    int64_t nseries;
+    int P;                    // theta entries per series
 };
+
+// The steps of chunk c: [s, e), inside the series that starts at step s0 and
+// whose hyperparameters start at th.  In a batch the chunks of each series
+// are consecutive; a series' first chunk starts from the stationary prior, and
+// that element (A = 0, eta = J = 0) stops information crossing between
+// series in both directions, so one reduction over all chunks serves every
+// series at once.
+struct ChunkRange {
+    int64_t s, e, s0, series;
+    const double* th;
+    bool valid;
+};
+
+template <bool BATCH>
+__device__ __forceinline__ ChunkRange chunk_range(const ChainArgs& a, int64_t c) {
+    ChunkRange r;
+    if constexpr (!BATCH) {
+        r.valid = c < a.nchunks;
+        r.s = c * a.L;
+        r.e = min(a.n, r.s + a.L);
+        r.s0 = 0;
+        r.series = 0;
+        r.th = a.theta;
+    } else {
+        r.valid = c < a.cstart[a.nseries];
+        int64_t lo = 0, hi = a.nseries;   // largest series with cstart <= c
+        if (r.valid) {
+            while (hi - lo > 1) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (a.cstart[mid] <= c) lo = mid; else hi = mid;
+            }
+        }
+        r.series = lo;
+        r.s0 = a.offsets[lo];
+        r.s = r.s0 + (c - a.cstart[lo]) * a.L;
+        r.e = min(a.offsets[lo + 1], r.s + a.L);
+        r.th = a.theta + lo * (int64_t)a.P;
+    }
+    return r;
+}
 
 template <int B>
 __device__ __forceinline__ bool theta_ok(double ell, double sf, double s2) {
@@ -73,7 +118,7 @@ __device__ __forceinline__ void renorm(double& prod, int& expo) {
 // block's odd-even up-sweep over its CTA elements, writing every tree node
 // and the block total.  The conditional covariance is carried as C - Pinf,
 // so the prediction is a single sandwich Phi (C - Pinf) Phi^T.
-template <int B>
+template <int B, bool BATCH>
 __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict__ nodes, double* __restrict__ btot,
                                               double* __restrict__ phis) {
     constexpr int NE = Dims<B>::NE;
@@ -82,16 +127,17 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
     const int64_t blk = blockIdx.x;
     const int64_t c = blk * CTA + tid;
     const int64_t nc = a.nchunks;
-    const double ell = a.theta[0], sf = a.theta[1], s2 = a.theta[2];
-    int bad = theta_ok<B>(ell, sf, s2) ? 0 : ST_EINVAL;
-    const double lam = sqrt(2.0 * B - 1.0) / ell;
+    const ChunkRange cr = chunk_range<BATCH>(a, c);
     Elem<B> el;
     elem_identity<B>(el);
-    if (c < nc) {
-        const int64_t s = c * a.L;
-        const int64_t e = min(a.n, s + a.L);
+    int bad = 0;
+    if (cr.valid) {
+        const double ell = cr.th[0], sf = cr.th[1], s2 = cr.th[2];
+        if (!theta_ok<B>(ell, sf, s2)) bad |= ST_EINVAL;
+        const double lam = sqrt(2.0 * B - 1.0) / ell;
+        const int64_t s = cr.s, e = cr.e;
         // el.C holds C - Pinf until the end of the chunk
-        if (s == 0) {
+        if (s == cr.s0) {
             // the first state has the stationary prior: no dependence on an earlier node
 #pragma unroll
             for (int i = 0; i < B; ++i)
@@ -103,11 +149,11 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
 #pragma unroll
                 for (int j = 0; j < B; ++j) el.C[i][j] = -sf * p1<B>(i, j);
         }
-        double tp = (s > 0) ? a.t[s - 1] : 0.0;
+        double tp = (s > cr.s0) ? a.t[s - 1] : 0.0;
         for (int64_t i = s; i < e; ++i) {
             const double ti = a.t[i], yi = a.y[i];
             if (!isfinite(ti) || !isfinite(yi)) bad |= ST_ENONFINITE;
-            if (i > 0) {
+            if (i > cr.s0) {
                 const double dt = ti - tp;
                 if (dt < 0.0) bad |= ST_ENOTSORTED;
                 const double x = lam * dt;
@@ -368,7 +414,7 @@ template <int B> struct Stored { static constexpr int N = B + Dims<B>::NS + 2; }
 //       d ll/dx_i = -lt^T F1 mb + 2 <G, F1 (Pb - Pinf)>,  x_i = lam dt_i
 //       d ll/ds_n = sum (al^2 - cc)/2,  d ll/dPinf = sum G - sum Phi^T G Phi.
 //  4. Fixed-order block reduction of the partial sums.
-template <int B, int MODE>
+template <int B, int MODE, bool BATCH>
 __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __restrict__ nodes,
                                                const double* __restrict__ bpre, const double* __restrict__ bsuf,
                                                const double* __restrict__ phis, double* __restrict__ store,
@@ -390,8 +436,8 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
     const int64_t c = blk * CTA + tid;
     const int64_t nc = a.nchunks;
     const int64_t nld = a.nblocks * TREE;
-    const double ell = a.theta[0], sf = a.theta[1], s2 = a.theta[2];
-    const double lam = sqrt(2.0 * B - 1.0) / ell;
+    const ChunkRange cr = chunk_range<BATCH>(a, c);
+    const double sf = cr.th[1], s2 = cr.th[2];
 
     // ---- 1. back-substitution inside the block
     if (tid == 0) {
@@ -443,9 +489,8 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
 #pragma unroll
     for (int f = 0; f < NA; ++f) acc[f] = 0.0;
     int bad = 0;
-    if (c < nc) {
-        const int64_t s = c * a.L;
-        const int64_t e = min(a.n, s + a.L);
+    if (cr.valid) {
+        const int64_t s = cr.s, e = cr.e;
         // ---- 2. forward: filtered mean m and D = P - Pinf
         double m[B], D[B][B];
         {
@@ -462,7 +507,7 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
             const int64_t j = i - s;
             const double yi = a.y[i];
             double mb[B], Db[B][B];
-            if (i == 0) {
+            if (i == cr.s0) {
 #pragma unroll
                 for (int r = 0; r < B; ++r) { mb[r] = 0.0;
 #pragma unroll
@@ -590,7 +635,7 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
                             if (p1<B>(r, q) != 0.0) GP[r][q] += G[r][q];
                         }
                 }
-                if (i > 0) {
+                if (i > cr.s0) {
                     const double dt = a.t[i] - a.t[i - 1];
                     if constexpr (GRAD) {
                         // d ll / dx = -lt^T F1 mb + 2 <G, F1 Db>
@@ -643,21 +688,28 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
         }
     }
     if (bad) atomicOr(a.status, bad);
-    // ---- 4. fixed-order reduction of the block's partial sums
     constexpr int NU = GRAD ? NA : 1;
+    if constexpr (BATCH) {
+        // per-chunk partial sums; the per-series reduction follows
+        if (cr.valid)
 #pragma unroll
-    for (int f = 0; f < NU; ++f) red[f * CTA + tid] = acc[f];
-    __syncthreads();
-#pragma unroll 1
-    for (int w = CTA / 2; w > 0; w >>= 1) {
-        if (tid < w)
+            for (int f = 0; f < NU; ++f) part[f * nc + c] = acc[f];
+    } else {
+        // ---- 4. fixed-order reduction of the block's partial sums
 #pragma unroll
-            for (int f = 0; f < NU; ++f) red[f * CTA + tid] += red[f * CTA + tid + w];
+        for (int f = 0; f < NU; ++f) red[f * CTA + tid] = acc[f];
         __syncthreads();
-    }
-    if (tid == 0)
+#pragma unroll 1
+        for (int w = CTA / 2; w > 0; w >>= 1) {
+            if (tid < w)
 #pragma unroll
-        for (int f = 0; f < NU; ++f) part[f * a.nblocks + blk] = red[f * CTA];
+                for (int f = 0; f < NU; ++f) red[f * CTA + tid] += red[f * CTA + tid + w];
+            __syncthreads();
+        }
+        if (tid == 0)
+#pragma unroll
+            for (int f = 0; f < NU; ++f) part[f * a.nblocks + blk] = red[f * CTA];
+    }
 }
 
 // ------------------------------------------------------------------ k_finalize (fixed-order reduction)
@@ -700,6 +752,104 @@ __global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ par
     }
 }
 
+// ------------------------------------------------------------------ batches: chunk offsets and per-series sums
+
+// cstart[i] = sum_{k<i} ceil(len_k / L), one CTA.  Offsets must start at 0,
+// never decrease and end at n_total; otherwise EINVAL is recorded and every
+// series gets zero chunks, so the later kernels touch nothing.
+static constexpr int CS_THREADS = 1024;
+
+__global__ void __launch_bounds__(CS_THREADS) k_chunk_starts(const int64_t* __restrict__ offsets, int64_t nseries,
+                                                            int64_t n_total, int64_t L, int64_t* __restrict__ cstart,
+                                                            int* status) {
+    __shared__ int64_t wsum[CS_THREADS / 32];
+    __shared__ int bad_any;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) bad_any = (offsets[0] != 0 || offsets[nseries] != n_total) ? 1 : 0;
+    __syncthreads();
+    int bad = 0;
+    for (int64_t i = tid; i < nseries; i += CS_THREADS)
+        if (offsets[i + 1] < offsets[i]) bad = 1;
+    if (bad) atomicOr(&bad_any, 1);
+    __syncthreads();
+    const bool ok = bad_any == 0;
+    if (!ok && tid == 0) atomicOr(status, ST_EINVAL);
+    int64_t carry = 0;
+    for (int64_t base = 0; base < nseries; base += CS_THREADS) {
+        const int64_t i = base + tid;
+        int64_t cnt = 0;
+        if (ok && i < nseries) cnt = (offsets[i + 1] - offsets[i] + L - 1) / L;
+        // inclusive warp scan, then across warps
+        int64_t x = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t yv = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += yv;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t w = (lane < CS_THREADS / 32) ? wsum[lane] : 0;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int64_t yv = __shfl_up_sync(0xffffffffu, w, d);
+                if (lane >= d) w += yv;
+            }
+            if (lane < CS_THREADS / 32) wsum[lane] = w;
+        }
+        __syncthreads();
+        const int64_t before = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - cnt;
+        if (i < nseries) cstart[i] = before;
+        carry += wsum[CS_THREADS / 32 - 1];
+        __syncthreads();
+    }
+    if (tid == 0) cstart[nseries] = carry;
+}
+
+// One warp per series: fixed-order sum of its chunks' partials, chain rule.
+template <int B>
+__global__ void __launch_bounds__(256) k_finalize_batched(const double* __restrict__ part, int64_t nc, int na,
+                                                          const int64_t* __restrict__ cstart, int64_t nseries,
+                                                          const double* __restrict__ theta, int P,
+                                                          double* __restrict__ ll_out, double* __restrict__ grad_out) {
+    constexpr int NA = Acc<B>::N;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nseries) return;
+    const int64_t c0 = cstart[w], c1 = cstart[w + 1];
+    double acc[NA];
+#pragma unroll
+    for (int f = 0; f < NA; ++f) acc[f] = 0.0;
+    for (int64_t c = c0 + lane; c < c1; c += 32)
+#pragma unroll
+        for (int f = 0; f < NA; ++f)
+            if (f < na) acc[f] += part[f * nc + c];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1)
+#pragma unroll
+        for (int f = 0; f < NA; ++f) acc[f] += __shfl_xor_sync(0xffffffffu, acc[f], d);
+    if (lane == 0) {
+        if (ll_out) ll_out[w] = acc[0];
+        if (grad_out && na == NA) {
+            const double ell = theta[w * P];
+            const double lam = sqrt(2.0 * B - 1.0) / ell;
+            double* g = grad_out + w * P;
+            g[0] = acc[1] * (-lam / ell);
+            double gsf = 0.0;
+            int f = 3;
+#pragma unroll
+            for (int r = 0; r < B; ++r)
+#pragma unroll
+                for (int q = r; q < B; ++q) {
+                    const double wt = (r == q) ? 1.0 : 2.0;
+                    gsf += wt * p1<B>(r, q) * acc[f++];
+                }
+            g[1] = gsf;
+            g[2] = 0.5 * acc[2];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ host side
 
 // grid-level reduction of the block totals: tiles of SCAN_TS threads x G
@@ -725,11 +875,17 @@ struct Layout {
     int64_t lev_n[8];
     size_t lev_tot[8], lev_pre[8], lev_suf[8];
 
-    Layout(int64_t n, int64_t L, int mode) {
+    size_t off_cstart;
+
+    // one series of n steps (nseries = 0), or a batch of nseries series with
+    // n steps in total (chunk slots: an upper bound on the chunk count)
+    Layout(int64_t n, int64_t L, int mode, int64_t nseries = 0) {
         constexpr int NE = Dims<B>::NE, NM = Dims<B>::NM;
-        nc = (n + L - 1) / L;
+        nc = (n + L - 1) / L + nseries;
         nb = (nc + CTA - 1) / CTA;
         size_t o = 256;  // status word region
+        off_cstart = o;
+        if (nseries > 0) o = align256(o + sizeof(int64_t) * (size_t)(nseries + 1));
         off_nodes = o; o = align256(o + sizeof(double) * NE * (size_t)nb * TREE);
         off_btot = o; o = align256(o + sizeof(double) * NE * nb);
         off_bpre = o; o = align256(o + sizeof(double) * NM * nb);
@@ -746,7 +902,7 @@ struct Layout {
             ne = nt;
         }
         off_phis = o; o = align256(o + sizeof(double) * (size_t)(B * B) * L * nc);
-        off_part = o; o = align256(o + sizeof(double) * Acc<B>::N * nb);
+        off_part = o; o = align256(o + sizeof(double) * Acc<B>::N * (nseries > 0 ? nc : nb));
         off_store = o;
         if (mode != MODE_LOGLIK) o = align256(o + sizeof(double) * Stored<B>::N * (size_t)L * nc);
         total = o;
@@ -802,31 +958,91 @@ int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t 
     double* phis = (double*)(ws + lay.off_phis);
     double* part = (double*)(ws + lay.off_part);
     double* store = (double*)(ws + lay.off_store);
-    ChainArgs a{t, y, n, L, lay.nc, lay.nb, theta, status};
+    ChainArgs a{t, y, n, L, lay.nc, lay.nb, theta, status, nullptr, nullptr, 0, 3};
     const unsigned grid = (unsigned)lay.nb;
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
     if (ev) cudaEventRecord(ev[0], st);
-    k_fold<B><<<grid, CTA, 0, st>>>(a, nodes, btot, phis);
+    k_fold<B, false><<<grid, CTA, 0, st>>>(a, nodes, btot, phis);
     if (ev) cudaEventRecord(ev[1], st);
     scan_level<B>(btot, lay.nb, bpre, bsuf, lay, ws, 0, st);
     if (ev) cudaEventRecord(ev[2], st);
     int na = 1;
     switch (mode) {
     case MODE_LOGLIK:
-        k_chunk<B, MODE_LOGLIK><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part, nullptr, nullptr);
+        k_chunk<B, MODE_LOGLIK, false><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part, nullptr,
+                                                            nullptr);
         break;
     case MODE_GRAD:
-        k_chunk<B, MODE_GRAD><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part, nullptr, nullptr);
+        k_chunk<B, MODE_GRAD, false><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part, nullptr,
+                                                          nullptr);
         na = Acc<B>::N;
         break;
     default:
-        k_chunk<B, MODE_POSTERIOR><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part, mean_out,
+        k_chunk<B, MODE_POSTERIOR, false><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part, mean_out,
                                                         var_out);
         break;
     }
     if (ev) cudaEventRecord(ev[3], st);
     // the final reduction always runs (it is cheap), so the launch count is fixed per kind
     k_finalize<B><<<1, 256, 0, st>>>(part, lay.nb, na, theta, ll_out, grad_out);
+    if (ev) cudaEventRecord(ev[4], st);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+template <int B>
+size_t matern_ws_bytes_batched_t(int64_t nseries, int64_t n_total, int64_t L, int mode) {
+    return Layout<B>(n_total, L, mode, nseries).total;
+}
+
+template <int B>
+int matern_launch_count_batched_t(int64_t nseries, int64_t n_total, int64_t L, int mode) {
+    Layout<B> lay(n_total, L, mode, nseries);
+    return 1 + 1 + scan_launches<B>(lay.nb, lay, 0) + 1 + 1;
+}
+
+template <int B>
+int matern_run_batched_t(int mode, const int64_t* offsets, int64_t nseries, int64_t n_total, const double* t,
+                         const double* y, int64_t L, const double* theta, double* ll_out, double* grad_out,
+                         double* mean_out, double* var_out, void* wsv, cudaStream_t st, cudaEvent_t* ev) {
+    Layout<B> lay(n_total, L, mode, nseries);
+    char* ws = (char*)wsv;
+    int* status = (int*)ws;
+    int64_t* cstart = (int64_t*)(ws + lay.off_cstart);
+    double* nodes = (double*)(ws + lay.off_nodes);
+    double* btot = (double*)(ws + lay.off_btot);
+    double* bpre = (double*)(ws + lay.off_bpre);
+    double* bsuf = (double*)(ws + lay.off_bsuf);
+    double* phis = (double*)(ws + lay.off_phis);
+    double* part = (double*)(ws + lay.off_part);
+    double* store = (double*)(ws + lay.off_store);
+    ChainArgs a{t, y, n_total, L, lay.nc, lay.nb, theta, status, offsets, cstart, nseries, 3};
+    const unsigned grid = (unsigned)lay.nb;
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
+    if (ev) cudaEventRecord(ev[0], st);
+    k_chunk_starts<<<1, CS_THREADS, 0, st>>>(offsets, nseries, n_total, L, cstart, status);
+    k_fold<B, true><<<grid, CTA, 0, st>>>(a, nodes, btot, phis);
+    if (ev) cudaEventRecord(ev[1], st);
+    scan_level<B>(btot, lay.nb, bpre, bsuf, lay, ws, 0, st);
+    if (ev) cudaEventRecord(ev[2], st);
+    int na = 1;
+    switch (mode) {
+    case MODE_LOGLIK:
+        k_chunk<B, MODE_LOGLIK, true><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part, nullptr,
+                                                           nullptr);
+        break;
+    case MODE_GRAD:
+        k_chunk<B, MODE_GRAD, true><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part, nullptr,
+                                                         nullptr);
+        na = Acc<B>::N;
+        break;
+    default:
+        k_chunk<B, MODE_POSTERIOR, true><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part, mean_out,
+                                                              var_out);
+        break;
+    }
+    if (ev) cudaEventRecord(ev[3], st);
+    const unsigned fgrid = (unsigned)((nseries * 32 + 255) / 256);
+    k_finalize_batched<B><<<fgrid, 256, 0, st>>>(part, lay.nc, na, cstart, nseries, theta, 3, ll_out, grad_out);
     if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
@@ -861,6 +1077,35 @@ int matern_run(int b, int mode, const double* t, const double* y, int64_t n, int
     case 1: return matern_run_t<1>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev);
     case 2: return matern_run_t<2>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev);
     default: return matern_run_t<3>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev);
+    }
+}
+
+size_t matern_ws_bytes_batched(int b, int64_t nseries, int64_t n_total, int64_t L, int mode) {
+    switch (b) {
+    case 1: return matern_ws_bytes_batched_t<1>(nseries, n_total, L, mode);
+    case 2: return matern_ws_bytes_batched_t<2>(nseries, n_total, L, mode);
+    default: return matern_ws_bytes_batched_t<3>(nseries, n_total, L, mode);
+    }
+}
+
+int matern_launch_count_batched(int b, int64_t nseries, int64_t n_total, int64_t L, int mode) {
+    switch (b) {
+    case 1: return matern_launch_count_batched_t<1>(nseries, n_total, L, mode);
+    case 2: return matern_launch_count_batched_t<2>(nseries, n_total, L, mode);
+    default: return matern_launch_count_batched_t<3>(nseries, n_total, L, mode);
+    }
+}
+
+int matern_run_batched(int b, int mode, const int64_t* offsets, int64_t nseries, int64_t n_total, const double* t,
+                       const double* y, int64_t L, const double* theta, double* ll_out, double* grad_out,
+                       double* mean_out, double* var_out, void* ws, cudaStream_t st, cudaEvent_t* ev) {
+    switch (b) {
+    case 1: return matern_run_batched_t<1>(mode, offsets, nseries, n_total, t, y, L, theta, ll_out, grad_out,
+                                           mean_out, var_out, ws, st, ev);
+    case 2: return matern_run_batched_t<2>(mode, offsets, nseries, n_total, t, y, L, theta, ll_out, grad_out,
+                                           mean_out, var_out, ws, st, ev);
+    default: return matern_run_batched_t<3>(mode, offsets, nseries, n_total, t, y, L, theta, ll_out, grad_out,
+                                            mean_out, var_out, ws, st, ev);
     }
 }
 

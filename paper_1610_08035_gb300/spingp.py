@@ -22,7 +22,9 @@ KINDS = {"matern12": 1, "matern32": 2, "matern52": 3, "periodic": 4, "quasiperio
 # names exported by the library, in the order of include/spingp.h
 EXPORTS = ("spingp_model_create", "spingp_model_destroy", "spingp_num_params", "spingp_state_dim",
            "spingp_set_chunk_len", "spingp_get_chunk_len", "spingp_workspace_bytes", "spingp_loglik",
-           "spingp_grad", "spingp_posterior", "spingp_launch_count", "spingp_profile_enable",
+           "spingp_grad", "spingp_posterior", "spingp_workspace_bytes_batched", "spingp_loglik_batched",
+           "spingp_grad_batched", "spingp_posterior_batched", "spingp_launch_count",
+           "spingp_launch_count_batched", "spingp_profile_enable",
            "spingp_profile_read", "spingp_probe_fp64_bytes", "spingp_probe_fp64", "spingp_loglik_noalloc",
            "spingp_ws_status", "spingp_status_str")
 STAGES = ("elimination", "reduction", "chunk_pass", "final_reduction")
@@ -63,7 +65,13 @@ def load():
     lib.spingp_loglik.argtypes = [vp, dp, dp, i64, dp, dp, vp, sz, u32, vp]
     lib.spingp_grad.argtypes = [vp, dp, dp, i64, dp, dp, dp, vp, sz, u32, vp]
     lib.spingp_posterior.argtypes = [vp, dp, dp, i64, dp, dp, dp, dp, vp, sz, u32, vp]
+    lib.spingp_workspace_bytes_batched.argtypes = [vp, i64, i64, ctypes.c_int]
+    lib.spingp_workspace_bytes_batched.restype = sz
+    lib.spingp_loglik_batched.argtypes = [vp, dp, i64, i64, dp, dp, dp, dp, vp, sz, u32, vp]
+    lib.spingp_grad_batched.argtypes = [vp, dp, i64, i64, dp, dp, dp, dp, dp, vp, sz, u32, vp]
+    lib.spingp_posterior_batched.argtypes = [vp, dp, i64, i64, dp, dp, dp, dp, dp, dp, vp, sz, u32, vp]
     lib.spingp_launch_count.argtypes = [vp, i64, ctypes.c_int]
+    lib.spingp_launch_count_batched.argtypes = [vp, i64, i64, ctypes.c_int]
     lib.spingp_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.spingp_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
     lib.spingp_probe_fp64_bytes.argtypes = []
@@ -165,6 +173,34 @@ def spingp_posterior(h, t, y, n, theta, ll_out, mean_out, var_out, ws, ws_bytes,
     return load().spingp_posterior(h, _ptr(t), _ptr(y), int(n), _ptr(theta), _ptr(ll_out), _ptr(mean_out),
                                    _ptr(var_out), _ptr(ws), ws_bytes, flags,
                                    stream if stream is not None else _stream())
+
+
+def spingp_workspace_bytes_batched(h, n_series, n_total, what):
+    return load().spingp_workspace_bytes_batched(h, int(n_series), int(n_total), int(what))
+
+
+def spingp_loglik_batched(h, offsets, n_series, n_total, t, y, theta, ll_out, ws, ws_bytes, flags, stream=None):
+    return load().spingp_loglik_batched(h, _ptr(offsets), int(n_series), int(n_total), _ptr(t), _ptr(y),
+                                        _ptr(theta), _ptr(ll_out), _ptr(ws), ws_bytes, flags,
+                                        stream if stream is not None else _stream())
+
+
+def spingp_grad_batched(h, offsets, n_series, n_total, t, y, theta, ll_out, grad_out, ws, ws_bytes, flags,
+                        stream=None):
+    return load().spingp_grad_batched(h, _ptr(offsets), int(n_series), int(n_total), _ptr(t), _ptr(y), _ptr(theta),
+                                      _ptr(ll_out), _ptr(grad_out), _ptr(ws), ws_bytes, flags,
+                                      stream if stream is not None else _stream())
+
+
+def spingp_posterior_batched(h, offsets, n_series, n_total, t, y, theta, ll_out, mean_out, var_out, ws, ws_bytes,
+                             flags, stream=None):
+    return load().spingp_posterior_batched(h, _ptr(offsets), int(n_series), int(n_total), _ptr(t), _ptr(y),
+                                           _ptr(theta), _ptr(ll_out), _ptr(mean_out), _ptr(var_out), _ptr(ws),
+                                           ws_bytes, flags, stream if stream is not None else _stream())
+
+
+def spingp_launch_count_batched(h, n_series, n_total, what):
+    return load().spingp_launch_count_batched(h, int(n_series), int(n_total), int(what))
 
 
 def spingp_launch_count(h, n, what):
@@ -288,6 +324,70 @@ class Model:
         ll = torch.empty(1, dtype=torch.float64, device=t.device) if with_loglik else None
         _check(spingp_posterior(self.h, t, y, n, theta, ll, mean, var, ws, ws.numel(), SYNC if sync else 0),
                "spingp_posterior")
+        return mean, var, ll
+
+
+class Batch:
+    """A batch of independent series sharing one model structure: device
+    offsets (int64, n_series + 1), concatenated t and y, and one theta row per
+    series.  Methods mirror Model's and return per-series results."""
+
+    def __init__(self, model, offsets, t, y):
+        if not (isinstance(offsets, torch.Tensor) and offsets.is_cuda and offsets.dtype == torch.int64):
+            raise TypeError("offsets must be an int64 CUDA tensor")
+        _dev_f64(t, "t"); _dev_f64(y, "y")
+        self.model, self.offsets, self.t, self.y = model, offsets.contiguous(), t, y
+        self.n_series = offsets.numel() - 1
+        self.n_total = t.numel()
+        if self.n_series < 1 or y.numel() != self.n_total:
+            raise ValueError("need at least one series and len(y) == len(t)")
+        self._ws = {}
+
+    def workspace(self, what):
+        nbytes = spingp_workspace_bytes_batched(self.model.h, self.n_series, self.n_total, what)
+        if nbytes == 0:
+            raise SpinGPError(EUNSUPPORTED, "spingp_workspace_bytes_batched")
+        ws = self._ws.get(what)
+        if ws is None or ws.numel() < nbytes:
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=self.t.device)
+            self._ws[what] = ws
+        return ws
+
+    def _theta(self, theta):
+        _dev_f64(theta, "theta")
+        if theta.numel() != self.n_series * self.model.num_params:
+            raise ValueError("theta must have n_series x %d entries" % self.model.num_params)
+        return theta
+
+    def loglik(self, theta, sync=True, out=None):
+        ws = self.workspace(WS_LOGLIK)
+        ll = out if out is not None else torch.empty(self.n_series, dtype=torch.float64, device=self.t.device)
+        _check(spingp_loglik_batched(self.model.h, self.offsets, self.n_series, self.n_total, self.t, self.y,
+                                     self._theta(theta), ll, ws, ws.numel(), SYNC if sync else 0),
+               "spingp_loglik_batched")
+        return ll
+
+    def grad(self, theta, sync=True, out=None):
+        ws = self.workspace(WS_GRAD)
+        if out is None:
+            ll = torch.empty(self.n_series, dtype=torch.float64, device=self.t.device)
+            g = torch.empty(self.n_series * self.model.num_params, dtype=torch.float64, device=self.t.device)
+        else:
+            ll, g = out
+        _check(spingp_grad_batched(self.model.h, self.offsets, self.n_series, self.n_total, self.t, self.y,
+                                   self._theta(theta), ll, g, ws, ws.numel(), SYNC if sync else 0),
+               "spingp_grad_batched")
+        return ll, g.view(self.n_series, self.model.num_params)
+
+    def posterior(self, theta, sync=True):
+        ws = self.workspace(WS_POSTERIOR)
+        dev = self.t.device
+        mean = torch.empty(self.n_total, dtype=torch.float64, device=dev)
+        var = torch.empty(self.n_total, dtype=torch.float64, device=dev)
+        ll = torch.empty(self.n_series, dtype=torch.float64, device=dev)
+        _check(spingp_posterior_batched(self.model.h, self.offsets, self.n_series, self.n_total, self.t, self.y,
+                                        self._theta(theta), ll, mean, var, ws, ws.numel(), SYNC if sync else 0),
+               "spingp_posterior_batched")
         return mean, var, ll
 
 
