@@ -26,6 +26,8 @@ struct spingp_model {
     int b, P;
     int chunk_len;   // 0 = default
     spg_prof* prof;  // NULL unless profiling was enabled
+    int group;       // 1: structured model on the group path (spg::GModel below)
+    spg::GModel gm;
 };
 
 namespace {
@@ -54,11 +56,48 @@ int64_t default_chunk(int64_t n) {
     return L;
 }
 
+int64_t default_group_chunk(int64_t n);
+
 int64_t chunk_len(const spingp_model* m, int64_t n) {
-    return m->chunk_len > 0 ? (int64_t)m->chunk_len : default_chunk(n);
+    if (m->chunk_len > 0) return (int64_t)m->chunk_len;
+    return m->group ? default_group_chunk(n) : default_chunk(n);
 }
 
 bool single_matern(const spingp_model* m) { return m->ncomp == 1 && m->kinds[0] >= 1 && m->kinds[0] <= 3; }
+
+// Build the 2x2-block description for the group path; false if the model has
+// a component that is not made of 2x2 blocks or is too large.
+bool build_group(spingp_model* m) {
+    spg::GModel g;
+    memset(&g, 0, sizeof(g));
+    if (m->ncomp > spg::GMAXCOMP) return false;
+    int K = 0, P = 0;
+    for (int c = 0; c < m->ncomp; ++c) {
+        const int k = m->kinds[c];
+        g.ckind[c] = k;
+        g.cpoff[c] = P;
+        int nb, kind;
+        if (k == SPINGP_MATERN32) { nb = 1; kind = 0; P += 2; }
+        else if (k == SPINGP_PERIODIC) { nb = m->orders[c] + 1; kind = 1; P += 3; }
+        else if (k == SPINGP_QUASIPERIODIC && m->envs[c] == SPINGP_MATERN12) { nb = m->orders[c] + 1; kind = 2; P += 4; }
+        else return false;
+        for (int j = 0; j < nb; ++j) {
+            if (K >= spg::GMAXBLK) return false;
+            g.bkind[K] = kind; g.bcomp[K] = c; g.bj[K] = (kind == 0) ? 0 : j;
+            ++K;
+        }
+    }
+    g.K = K; g.b = 2 * K; g.P = P + 1; g.ncomp = m->ncomp;
+    if (g.b != m->b || g.P != m->P) return false;
+    m->gm = g;
+    return true;
+}
+
+int64_t default_group_chunk(int64_t n) {
+    // about 2400 chunk groups (16 lanes each) keep every SM busy
+    int64_t L = (n + 2431) / 2432;
+    return L < 4 ? 4 : (L > 4096 ? 4096 : L);
+}
 
 // the next five stage events of a profiled model (NULL when not profiling)
 spingp_status profile_slot(const spingp_model* m, cudaEvent_t** ev) {
@@ -84,16 +123,19 @@ spingp_status run(const spingp_model* m, int mode, const double* t, const double
                   size_t ws_bytes, unsigned flags, void* stream) {
     if (!m || !t || !y || !theta || !ws || n < 1) return SPINGP_EINVAL;
     if (((uintptr_t)ws & 255u) != 0) return SPINGP_EINVAL;
-    if (!single_matern(m)) return SPINGP_EUNSUPPORTED;
+    if (!single_matern(m) && !m->group) return SPINGP_EUNSUPPORTED;
     const int64_t L = chunk_len(m, n);
-    if (ws_bytes < spg::matern_ws_bytes(m->b, n, L, mode)) return SPINGP_EINVAL;
+    const size_t need = m->group ? spg::group_ws_bytes(n, L, mode) : spg::matern_ws_bytes(m->b, n, L, mode);
+    if (ws_bytes < need) return SPINGP_EINVAL;
     spingp_status st = prepare_device();
     if (st != SPINGP_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t* ev = NULL;
     st = profile_slot(m, &ev);
     if (st != SPINGP_OK) return st;
-    if (spg::matern_run(m->b, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s, ev)) return SPINGP_ECUDA;
+    const int rc = m->group ? spg::group_run(m->gm, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s, ev)
+                            : spg::matern_run(m->b, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s, ev);
+    if (rc) return SPINGP_ECUDA;
     if (flags & SPINGP_SYNC) return spingp_ws_status(ws, stream);
     return SPINGP_OK;
 }
@@ -136,6 +178,10 @@ spingp_status run_batched(const spingp_model* m, int mode, const int64_t* offset
 }
 
 }  // namespace
+
+namespace spg {
+bool model_on_chain_path(const spingp_model* m) { return m && !m->group && single_matern(m); }
+}  // namespace spg
 
 extern "C" {
 
@@ -193,7 +239,10 @@ spingp_status spingp_model_create(const spingp_model_desc* d, spingp_model** out
         } else return SPINGP_EINVAL;
     }
     m.P += 1;
-    if (!single_matern(&m)) return SPINGP_EUNSUPPORTED;
+    if (!single_matern(&m)) {
+        if (!build_group(&m)) return SPINGP_EUNSUPPORTED;
+        m.group = 1;
+    }
     spingp_model* h = (spingp_model*)malloc(sizeof(spingp_model));
     if (!h) return SPINGP_ENOMEM;
     *h = m;
@@ -224,9 +273,11 @@ spingp_status spingp_set_chunk_len(spingp_model* m, int L) {
 int spingp_get_chunk_len(const spingp_model* m, int64_t n) { return m ? (int)chunk_len(m, n) : -1; }
 
 size_t spingp_workspace_bytes(const spingp_model* m, int64_t n, spingp_ws_kind what) {
-    if (!m || n < 1 || !single_matern(m)) return 0;
+    if (!m || n < 1) return 0;
     const int mode = what == SPINGP_WS_GRAD ? spg::MODE_GRAD
                    : what == SPINGP_WS_POSTERIOR ? spg::MODE_POSTERIOR : spg::MODE_LOGLIK;
+    if (m->group) return spg::group_ws_bytes(n, chunk_len(m, n), mode);
+    if (!single_matern(m)) return 0;
     return spg::matern_ws_bytes(m->b, n, chunk_len(m, n), mode);
 }
 
@@ -253,9 +304,11 @@ spingp_status spingp_posterior(const spingp_model* m, const double* t, const dou
 }
 
 int spingp_launch_count(const spingp_model* m, int64_t n, spingp_ws_kind what) {
-    if (!m || n < 1 || !single_matern(m)) return -1;
+    if (!m || n < 1) return -1;
     const int mode = what == SPINGP_WS_GRAD ? spg::MODE_GRAD
                    : what == SPINGP_WS_POSTERIOR ? spg::MODE_POSTERIOR : spg::MODE_LOGLIK;
+    if (m->group) return spg::group_launch_count(n, chunk_len(m, n), mode);
+    if (!single_matern(m)) return -1;
     return spg::matern_launch_count(m->b, n, chunk_len(m, n), mode);
 }
 

@@ -1,0 +1,990 @@
+// group.cu -- the hot path for structured state spaces built from 2x2 blocks:
+// sums of Matern-3/2, periodic (order J) and quasi-periodic (order J with a
+// Matern-1/2 envelope) components, state dimension b = 2K <= 16 (Sec. 2.1;
+// the quasi-periodic family is Eq. co2_1's periodicity term).
+//
+// Structure exploited: the transition A_n = blockdiag(Phi_1 .. Phi_K) is block
+// diagonal with 2x2 blocks (a Matern-3/2 block in scaled coordinates, or a
+// rotation by j w dt, damped by the envelope), Pinf is diagonal, and H picks
+// the first coordinate of every block.  The posterior covariance is dense, so
+// the Kalman and adjoint recursions run on a group of 16 lanes per chunk: lane
+// c owns column c of every b x b matrix.  Left products with the block
+// diagonal Phi are then local to a lane, right products need the partner
+// column of the same block (one shuffle per entry), and H^T-column sums of a
+// symmetric matrix are local as well.
+//
+// Kernels, in order:
+//   k_gsetup     per-block constants from theta (Pinf weights, rates)
+//   k_gdisc      one thread per step: Phi_n for every block (stored)
+//   k_gfold      one group per chunk: sequential elimination into an element
+//   k_gscan_up / k_gscan_down   odd-even reduction of chunk elements, level by
+//                level, with group-cooperative combines (global memory)
+//   k_gchunk     one group per chunk: forward recursion, reverse sweep,
+//                posterior and gradient terms
+//   k_gfinal     fixed-order reduction and chain rule
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "chain.cuh"
+#include "internal.h"
+#include "spingp.h"
+
+namespace spg {
+
+static constexpr int GL = 16;               // lanes per group = largest state dimension
+static constexpr int GK = GL / 2;           // largest number of 2x2 blocks
+static constexpr int GCTA = 128;            // threads per block: 8 groups
+static constexpr int GGRP = GCTA / GL;
+static constexpr int GNE = 3 * GL + 2;      // per-lane values of an element: A, C, J columns, bv, eta
+static constexpr int GNM = GL + 1;          // per-lane values of a state / information: column + vector entry
+static constexpr int GNC = 3;               // per-block constants: Pinf weight, d weight/dvar, d weight/dlen
+static constexpr double G_LOG_2PI = 1.8378770664093454836;
+static constexpr double G_LN2 = 0.69314718055994530942;
+
+// block kinds
+enum { GB_MATERN32 = 0, GB_PERIODIC = 1, GB_QUASI = 2 };
+
+// per-chunk partial sums: ll, noise, per component (rate, envelope rate), then
+// the diagonal of the Pinf adjoint for every state (lane)
+static constexpr int GPART = 2 + 2 * GMAXCOMP + GL;
+
+__device__ __forceinline__ unsigned half_mask() { return (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu; }
+
+__device__ __forceinline__ double gshfl(double v, int src) { return __shfl_sync(half_mask(), v, src, GL); }
+__device__ __forceinline__ double gxor(double v, int m) { return __shfl_xor_sync(half_mask(), v, m, GL); }
+
+// fixed-order sum over the 16 lanes of a group (same result in every lane)
+__device__ __forceinline__ double gsum(double v) {
+#pragma unroll
+    for (int m = 8; m > 0; m >>= 1) v += gxor(v, m);
+    return v;
+}
+
+// all 16 entries of a lane-distributed vector
+__device__ __forceinline__ void ggather(double mine, double (&v)[GL]) {
+#pragma unroll
+    for (int r = 0; r < GL; ++r) v[r] = gshfl(mine, r);
+}
+
+// ------------------------------------------------------------------ setup: per-block constants
+
+// Pinf of block k is w_k I2 with w_k = variance (Matern) or variance * c_j e^-x I_j(x),
+// x = 1/lp^2 (periodic, quasi-periodic); also dw/dvariance and dw/dlp.
+__device__ double g_bessel_i(int j, double x) {
+    const double h = 0.5 * x;
+    double term = 1.0;
+    for (int i = 1; i <= j; ++i) term *= h / i;
+    double s = term;
+    for (int k = 1; k < 500; ++k) {
+        term *= h * h / ((double)k * (double)(k + j));
+        s += term;
+        if (term < 1e-18 * s) break;
+    }
+    return s;
+}
+
+__global__ void k_gsetup(GModel gm, const double* __restrict__ theta, double* __restrict__ gconst, int* status) {
+    const int k = threadIdx.x;
+    if (k == 0) {
+        for (int p = 0; p < gm.P; ++p)
+            if (!(theta[p] > 0.0) || !isfinite(theta[p])) atomicOr(status, ST_EINVAL);
+    }
+    if (k >= gm.K) return;
+    const int c = gm.bcomp[k];
+    const double* th = theta + gm.cpoff[c];
+    double w = 0.0, dwv = 0.0, dwl = 0.0;
+    if (gm.bkind[k] == GB_MATERN32) {
+        w = th[1]; dwv = 1.0; dwl = 0.0;
+    } else {
+        const int j = gm.bj[k];
+        const double var = th[0], lp = th[1];
+        const double x = 1.0 / (lp * lp), ex = exp(-x), cj = (j == 0) ? 1.0 : 2.0;
+        const double Ij = g_bessel_i(j, x);
+        const double dIj = 0.5 * (g_bessel_i(j == 0 ? 1 : j - 1, x) + g_bessel_i(j + 1, x));
+        const double u = cj * ex * Ij;
+        w = var * u;
+        dwv = u;
+        dwl = var * cj * ex * (dIj - Ij) * (-2.0 / (lp * lp * lp));
+    }
+    gconst[k * GNC + 0] = w;
+    gconst[k * GNC + 1] = dwv;
+    gconst[k * GNC + 2] = dwl;
+}
+
+// ------------------------------------------------------------------ discretisation: Phi_n per block
+
+// Phi for step i (transition from t_{i-1}): 4 entries per block, row-major.
+__global__ void __launch_bounds__(256) k_gdisc(GModel gm, const double* __restrict__ t, const double* __restrict__ y,
+                                                int64_t n, const double* __restrict__ theta,
+                                                double* __restrict__ phis, int* status) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int bad = 0;
+    if (!isfinite(t[i]) || !isfinite(y[i])) bad |= ST_ENONFINITE;
+    const double dt = (i > 0) ? t[i] - t[i - 1] : 0.0;
+    if (dt < 0.0) bad |= ST_ENOTSORTED;
+    double* ph = phis + i * (4 * GK);
+#pragma unroll 1
+    for (int k = 0; k < GK; ++k) {
+        double p00 = 0.0, p01 = 0.0, p10 = 0.0, p11 = 0.0;
+        if (k < gm.K) {
+            const double* th = theta + gm.cpoff[gm.bcomp[k]];
+            if (gm.bkind[k] == GB_MATERN32) {
+                const double lam = sqrt(3.0) / th[0];
+                double P[2][2];
+                phi<2>(lam * dt, exp(-lam * dt), P);
+                p00 = P[0][0]; p01 = P[0][1]; p10 = P[1][0]; p11 = P[1][1];
+            } else {
+                const double w = 2.0 * M_PI / th[2];
+                double sn, cs;
+                sincos(gm.bj[k] * w * dt, &sn, &cs);
+                const double env = (gm.bkind[k] == GB_QUASI) ? exp(-dt / th[3]) : 1.0;
+                p00 = env * cs; p01 = -env * sn; p10 = env * sn; p11 = env * cs;
+            }
+        }
+        ph[4 * k + 0] = p00; ph[4 * k + 1] = p01; ph[4 * k + 2] = p10; ph[4 * k + 3] = p11;
+    }
+    if (bad) atomicOr(status, bad);
+}
+
+// ------------------------------------------------------------------ group linear algebra on columns
+
+// X <- blockdiag(Phi) X  (column-local: rows 2k, 2k+1 mix)
+__device__ __forceinline__ void g_left(const double* __restrict__ ph, double (&X)[GL]) {
+#pragma unroll
+    for (int k = 0; k < GK; ++k) {
+        const double a = ph[4 * k], b = ph[4 * k + 1], c = ph[4 * k + 2], d = ph[4 * k + 3];
+        const double x0 = X[2 * k], x1 = X[2 * k + 1];
+        X[2 * k] = fma(a, x0, b * x1);
+        X[2 * k + 1] = fma(c, x0, d * x1);
+    }
+}
+// X <- blockdiag(Phi)^T X
+__device__ __forceinline__ void g_left_t(const double* __restrict__ ph, double (&X)[GL]) {
+#pragma unroll
+    for (int k = 0; k < GK; ++k) {
+        const double a = ph[4 * k], b = ph[4 * k + 1], c = ph[4 * k + 2], d = ph[4 * k + 3];
+        const double x0 = X[2 * k], x1 = X[2 * k + 1];
+        X[2 * k] = fma(a, x0, c * x1);
+        X[2 * k + 1] = fma(b, x0, d * x1);
+    }
+}
+// column c of X Phi^T (right product: the partner column of c's block)
+__device__ __forceinline__ void g_right_t(const double* __restrict__ ph, int lane, double (&X)[GL]) {
+    const int k = lane >> 1, odd = lane & 1;
+    // row 'odd' of Phi_k: (Phi X^T)... column c of X Phi^T = sum_q X[:, 2k+q] Phi_k[odd][q]
+    const double f0 = ph[4 * k + 2 * odd], f1 = ph[4 * k + 2 * odd + 1];
+#pragma unroll
+    for (int r = 0; r < GL; ++r) {
+        const double p = gxor(X[r], 1);
+        const double x0 = odd ? p : X[r], x1 = odd ? X[r] : p;
+        X[r] = fma(f0, x0, f1 * x1);
+    }
+}
+// column c of X Phi: sum_q X[:, 2k+q] Phi_k[q][odd]
+__device__ __forceinline__ void g_right(const double* __restrict__ ph, int lane, double (&X)[GL]) {
+    const int k = lane >> 1, odd = lane & 1;
+    const double f0 = ph[4 * k + odd], f1 = ph[4 * k + 2 + odd];
+#pragma unroll
+    for (int r = 0; r < GL; ++r) {
+        const double p = gxor(X[r], 1);
+        const double x0 = odd ? p : X[r], x1 = odd ? X[r] : p;
+        X[r] = fma(f0, x0, f1 * x1);
+    }
+}
+// entry c of blockdiag(Phi) v for a lane-distributed vector
+__device__ __forceinline__ double g_vleft(const double* __restrict__ ph, int lane, double v) {
+    const int k = lane >> 1, odd = lane & 1;
+    const double p = gxor(v, 1);
+    const double v0 = odd ? p : v, v1 = odd ? v : p;
+    return fma(ph[4 * k + 2 * odd], v0, ph[4 * k + 2 * odd + 1] * v1);
+}
+// entry c of blockdiag(Phi)^T v
+__device__ __forceinline__ double g_vleft_t(const double* __restrict__ ph, int lane, double v) {
+    const int k = lane >> 1, odd = lane & 1;
+    const double p = gxor(v, 1);
+    const double v0 = odd ? p : v, v1 = odd ? v : p;
+    return fma(ph[4 * k + odd], v0, ph[4 * k + 2 + odd] * v1);
+}
+// h^T x for a column: sum of the even entries
+__device__ __forceinline__ double g_hsum(const double (&X)[GL]) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < GK; ++k) s += X[2 * k];
+    return s;
+}
+
+// ------------------------------------------------------------------ elements in global memory
+
+struct GElem {
+    double A[GL], C[GL], J[GL];   // column 'lane'
+    double bv, eta;               // entry 'lane'
+};
+
+// element e's value f of lane l at base[(f * ne + e) * GL + l]
+__device__ __forceinline__ void gelem_store(double* __restrict__ base, int64_t ne, int64_t e, int lane,
+                                            const GElem& x) {
+    double* p = base + e * GL + lane;
+    const int64_t s = ne * GL;
+#pragma unroll
+    for (int r = 0; r < GL; ++r) { p[r * s] = x.A[r]; p[(GL + r) * s] = x.C[r]; p[(2 * GL + r) * s] = x.J[r]; }
+    p[3 * GL * s] = x.bv;
+    p[(3 * GL + 1) * s] = x.eta;
+}
+__device__ __forceinline__ void gelem_load(const double* __restrict__ base, int64_t ne, int64_t e, int lane,
+                                           GElem& x) {
+    const double* p = base + e * GL + lane;
+    const int64_t s = ne * GL;
+#pragma unroll
+    for (int r = 0; r < GL; ++r) { x.A[r] = p[r * s]; x.C[r] = p[(GL + r) * s]; x.J[r] = p[(2 * GL + r) * s]; }
+    x.bv = p[3 * GL * s];
+    x.eta = p[(3 * GL + 1) * s];
+}
+// a state (m, P) or information (eta, J): column + entry
+__device__ __forceinline__ void gvs_store(double* __restrict__ base, int64_t ne, int64_t e, int lane,
+                                          const double (&S)[GL], double v) {
+    double* p = base + e * GL + lane;
+    const int64_t s = ne * GL;
+#pragma unroll
+    for (int r = 0; r < GL; ++r) p[r * s] = S[r];
+    p[GL * s] = v;
+}
+__device__ __forceinline__ void gvs_load(const double* __restrict__ base, int64_t ne, int64_t e, int lane,
+                                         double (&S)[GL], double& v) {
+    const double* p = base + e * GL + lane;
+    const int64_t s = ne * GL;
+#pragma unroll
+    for (int r = 0; r < GL; ++r) S[r] = p[r * s];
+    v = p[GL * s];
+}
+
+// ------------------------------------------------------------------ group matrix products through shared memory
+
+// Per-group shared scratch: one b x b matrix stored by columns (col c at sm[c*GL])
+// and inverse workspace.
+struct GSmem {
+    double X[GL * GL];
+    double N[GL * GL];
+    double R[GL * GL];
+};
+
+__device__ __forceinline__ void g_put(double* __restrict__ sm, int lane, const double (&col)[GL]) {
+#pragma unroll
+    for (int r = 0; r < GL; ++r) sm[lane * GL + r] = col[r];
+}
+// out = M y where M's columns are in sm (column-major) and y is this lane's column
+__device__ __forceinline__ void g_mul(const double* __restrict__ sm, const double (&y)[GL], double (&out)[GL]) {
+#pragma unroll
+    for (int r = 0; r < GL; ++r) out[r] = 0.0;
+#pragma unroll
+    for (int k = 0; k < GL; ++k) {
+        const double yk = y[k];
+#pragma unroll
+        for (int r = 0; r < GL; ++r) out[r] = fma(sm[k * GL + r], yk, out[r]);
+    }
+}
+// out = M^T y
+__device__ __forceinline__ void g_tmul(const double* __restrict__ sm, const double (&y)[GL], double (&out)[GL]) {
+#pragma unroll
+    for (int r = 0; r < GL; ++r) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < GL; ++k) s = fma(sm[r * GL + k], y[k], s);
+        out[r] = s;
+    }
+}
+// row 'lane' of M (columns in sm) dotted with a full vector
+__device__ __forceinline__ double g_rowdot(const double* __restrict__ sm, int lane, const double (&v)[GL]) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < GL; ++k) s = fma(sm[k * GL + lane], v[k], s);
+    return s;
+}
+
+// M = (I + X Y)^-1 with X (symmetric) given by this lane's column Xc, Y by its
+// column Yc; result: this lane's column of M in Mc.  Gauss-Jordan with partial
+// pivoting on the group (columns in shared memory).  I + X Y has eigenvalues >= 1.
+__device__ void g_inv_ixy(GSmem& s, int lane, const double (&Xc)[GL], const double (&Yc)[GL], double (&Mc)[GL]) {
+    const unsigned mask = half_mask();
+    g_put(s.X, lane, Xc);
+    __syncwarp(mask);
+    double col[GL];
+    g_mul(s.X, Yc, col);            // column 'lane' of X Y
+#pragma unroll
+    for (int r = 0; r < GL; ++r)
+        if (r == lane) col[r] += 1.0;
+    __syncwarp(mask);
+    g_put(s.N, lane, col);
+#pragma unroll
+    for (int r = 0; r < GL; ++r) s.R[lane * GL + r] = (r == lane) ? 1.0 : 0.0;
+    __syncwarp(mask);
+#pragma unroll 1
+    for (int k = 0; k < GL; ++k) {
+        // pivot row: largest |N[r][k]| for r >= k (every lane computes the same)
+        int p = k;
+        double best = fabs(s.N[k * GL + k]);
+        for (int r = k + 1; r < GL; ++r) {
+            const double v = fabs(s.N[k * GL + r]);
+            if (v > best) { best = v; p = r; }
+        }
+        __syncwarp(mask);
+        if (p != k) {
+            double u = s.N[lane * GL + k]; s.N[lane * GL + k] = s.N[lane * GL + p]; s.N[lane * GL + p] = u;
+            u = s.R[lane * GL + k]; s.R[lane * GL + k] = s.R[lane * GL + p]; s.R[lane * GL + p] = u;
+        }
+        __syncwarp(mask);
+        const double piv = s.N[k * GL + k];
+        const double inv = 1.0 / piv;
+        double nk = s.N[lane * GL + k] * inv, rk = s.R[lane * GL + k] * inv;
+        double colk[GL];
+#pragma unroll
+        for (int r = 0; r < GL; ++r) colk[r] = s.N[k * GL + r];
+        __syncwarp(mask);
+#pragma unroll
+        for (int r = 0; r < GL; ++r) {
+            if (r == k) continue;
+            s.N[lane * GL + r] = fma(-colk[r], nk, s.N[lane * GL + r]);
+            s.R[lane * GL + r] = fma(-colk[r], rk, s.R[lane * GL + r]);
+        }
+        s.N[lane * GL + k] = nk;
+        s.R[lane * GL + k] = rk;
+        __syncwarp(mask);
+    }
+#pragma unroll
+    for (int r = 0; r < GL; ++r) Mc[r] = s.R[lane * GL + r];
+    __syncwarp(mask);
+}
+
+// column 'lane' of X Z^T where X's and Z's columns are put in s.X and s.N
+__device__ __forceinline__ void g_mul_bt(GSmem& s, int lane, const double (&Xc)[GL], const double (&Zc)[GL],
+                                         double (&out)[GL]) {
+    const unsigned mask = half_mask();
+    g_put(s.X, lane, Xc);
+    g_put(s.N, lane, Zc);
+    __syncwarp(mask);
+    double zrow[GL];
+#pragma unroll
+    for (int k = 0; k < GL; ++k) zrow[k] = s.N[k * GL + lane];   // Z[lane][k]
+    g_mul(s.X, zrow, out);                                       // sum_k X[:, k] Z[lane][k]
+    __syncwarp(mask);
+}
+// symmetrise a column-distributed matrix: X <- (X + X^T)/2
+__device__ __forceinline__ void g_sym(GSmem& s, int lane, double (&Xc)[GL]) {
+    const unsigned mask = half_mask();
+    g_put(s.X, lane, Xc);
+    __syncwarp(mask);
+#pragma unroll
+    for (int q = 0; q < GL; ++q) Xc[q] = 0.5 * (Xc[q] + s.X[q * GL + lane]);
+    __syncwarp(mask);
+}
+
+// (ei then ej): the same combine as the b <= 3 chain path, every product
+// through the group:  M = (I + C_i J_j)^-1,  A = A_j M A_i,
+// bv = A_j M (bv_i + C_i eta_j) + bv_j,  C = A_j M C_i A_j^T + C_j,
+// eta = A_i^T M^T (eta_j - J_j bv_i) + eta_i,  J = A_i^T M^T J_j A_i + J_i.
+__device__ void g_combine(GSmem& s, int lane, const GElem& ei, const GElem& ej, GElem& r) {
+    const unsigned mask = half_mask();
+    double M[GL], T[GL], U[GL], v[GL];
+    g_inv_ixy(s, lane, ei.C, ej.J, M);
+    // A
+    g_put(s.X, lane, M); __syncwarp(mask);
+    g_mul(s.X, ei.A, T); __syncwarp(mask);            // M A_i
+    g_put(s.X, lane, ej.A); __syncwarp(mask);
+    g_mul(s.X, T, r.A); __syncwarp(mask);             // A_j M A_i
+    // bv
+    ggather(ej.eta, v);
+    double wc = ei.bv;
+#pragma unroll
+    for (int k = 0; k < GL; ++k) wc = fma(ei.C[k], v[k], wc);
+    ggather(wc, v);
+    g_put(s.X, lane, M); __syncwarp(mask);
+    const double zc = g_rowdot(s.X, lane, v); __syncwarp(mask);
+    ggather(zc, v);
+    g_put(s.X, lane, ej.A); __syncwarp(mask);
+    r.bv = g_rowdot(s.X, lane, v) + ej.bv; __syncwarp(mask);
+    // C
+    g_put(s.X, lane, M); __syncwarp(mask);
+    g_mul(s.X, ei.C, T); __syncwarp(mask);            // M C_i
+    g_put(s.X, lane, ej.A); __syncwarp(mask);
+    g_mul(s.X, T, U); __syncwarp(mask);               // A_j M C_i
+    g_mul_bt(s, lane, U, ej.A, T);                    // (A_j M C_i) A_j^T
+#pragma unroll
+    for (int q = 0; q < GL; ++q) r.C[q] = T[q] + ej.C[q];
+    g_sym(s, lane, r.C);
+    // eta
+    ggather(ei.bv, v);
+    double w2 = ej.eta;
+#pragma unroll
+    for (int k = 0; k < GL; ++k) w2 = fma(-ej.J[k], v[k], w2);
+    ggather(w2, v);
+    double z2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < GL; ++k) z2 = fma(M[k], v[k], z2);
+    ggather(z2, v);
+    double e2 = ei.eta;
+#pragma unroll
+    for (int k = 0; k < GL; ++k) e2 = fma(ei.A[k], v[k], e2);
+    r.eta = e2;
+    // J
+    g_put(s.X, lane, M); __syncwarp(mask);
+    g_tmul(s.X, ej.J, T); __syncwarp(mask);           // M^T J_j
+    g_put(s.X, lane, T); __syncwarp(mask);
+    g_mul(s.X, ei.A, U); __syncwarp(mask);            // M^T J_j A_i
+    g_put(s.X, lane, ei.A); __syncwarp(mask);
+    g_tmul(s.X, U, T); __syncwarp(mask);              // A_i^T M^T J_j A_i
+#pragma unroll
+    for (int q = 0; q < GL; ++q) r.J[q] = T[q] + ei.J[q];
+    g_sym(s, lane, r.J);
+}
+
+// N(m, P) before element e, pushed through it:  M = (I + P J_e)^-1,
+// m' = A_e M (m + P eta_e) + bv_e,  P' = A_e M P A_e^T + C_e.
+__device__ void g_state_through(GSmem& s, int lane, const double (&P)[GL], double m, const GElem& e,
+                                double (&Po)[GL], double& mo) {
+    const unsigned mask = half_mask();
+    double M[GL], T[GL], U[GL], v[GL];
+    g_inv_ixy(s, lane, P, e.J, M);
+    ggather(e.eta, v);
+    double wc = m;
+#pragma unroll
+    for (int k = 0; k < GL; ++k) wc = fma(P[k], v[k], wc);
+    ggather(wc, v);
+    g_put(s.X, lane, M); __syncwarp(mask);
+    const double zc = g_rowdot(s.X, lane, v); __syncwarp(mask);
+    ggather(zc, v);
+    g_put(s.X, lane, e.A); __syncwarp(mask);
+    mo = g_rowdot(s.X, lane, v) + e.bv; __syncwarp(mask);
+    g_put(s.X, lane, M); __syncwarp(mask);
+    g_mul(s.X, P, T); __syncwarp(mask);               // M P
+    g_put(s.X, lane, e.A); __syncwarp(mask);
+    g_mul(s.X, T, U); __syncwarp(mask);               // A_e M P
+    g_mul_bt(s, lane, U, e.A, T);
+#pragma unroll
+    for (int q = 0; q < GL; ++q) Po[q] = T[q] + e.C[q];
+    g_sym(s, lane, Po);
+}
+
+// information (eta, J) after element e pulled back through it and joined
+// with e's own:  M = (I + C_e J)^-1,  eta' = A_e^T M^T (eta - J bv_e) + eta_e,
+// J' = A_e^T M^T J A_e + J_e.
+__device__ void g_info_through(GSmem& s, int lane, const GElem& e, const double (&J)[GL], double eta,
+                               double (&Jo)[GL], double& eo) {
+    const unsigned mask = half_mask();
+    double M[GL], T[GL], U[GL], v[GL];
+    g_inv_ixy(s, lane, e.C, J, M);
+    ggather(e.bv, v);
+    double w2 = eta;
+#pragma unroll
+    for (int k = 0; k < GL; ++k) w2 = fma(-J[k], v[k], w2);
+    ggather(w2, v);
+    double z2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < GL; ++k) z2 = fma(M[k], v[k], z2);
+    ggather(z2, v);
+    double e2 = e.eta;
+#pragma unroll
+    for (int k = 0; k < GL; ++k) e2 = fma(e.A[k], v[k], e2);
+    eo = e2;
+    g_put(s.X, lane, M); __syncwarp(mask);
+    g_tmul(s.X, J, T); __syncwarp(mask);              // M^T J
+    g_put(s.X, lane, T); __syncwarp(mask);
+    g_mul(s.X, e.A, U); __syncwarp(mask);             // M^T J A_e
+    g_put(s.X, lane, e.A); __syncwarp(mask);
+    g_tmul(s.X, U, T); __syncwarp(mask);              // A_e^T M^T J A_e
+#pragma unroll
+    for (int q = 0; q < GL; ++q) Jo[q] = T[q] + e.J[q];
+    g_sym(s, lane, Jo);
+}
+
+// ------------------------------------------------------------------ k_gfold: in-chunk elimination
+
+struct GArgs {
+    GModel gm;
+    const double* t;
+    const double* y;
+    int64_t n, L, nc;
+    const double* theta;
+    const double* gconst;
+    const double* phis;
+    int* status;
+};
+
+__global__ void __launch_bounds__(GCTA) k_gfold(GArgs a, double* __restrict__ nodes) {
+    const int lane = threadIdx.x & (GL - 1);
+    const int64_t c = blockIdx.x * (int64_t)GGRP + (threadIdx.x >> 4);
+    if (c >= a.nc) return;   // the whole group leaves together
+    const bool on = lane < a.gm.b;
+    const bool even = (lane & 1) == 0;
+    const double s2 = a.theta[a.gm.P - 1];
+    const double pw = on ? a.gconst[(lane >> 1) * GNC] : 0.0;   // Pinf[lane][lane]
+    const int64_t s = c * a.L, e = min(a.n, s + a.L);
+    GElem el;
+    double Cm[GL];   // C - Pinf, column lane
+#pragma unroll
+    for (int r = 0; r < GL; ++r) {
+        el.A[r] = (s > 0 && r == lane && on) ? 1.0 : 0.0;
+        el.J[r] = 0.0;
+        Cm[r] = (s > 0 && r == lane) ? -pw : 0.0;
+    }
+    el.bv = 0.0;
+    el.eta = 0.0;
+    for (int64_t i = s; i < e; ++i) {
+        const double yi = a.y[i];
+        if (i > 0) {
+            const double* ph = a.phis + i * (4 * GK);
+            g_left(ph, el.A);
+            el.bv = g_vleft(ph, lane, el.bv);
+            g_left(ph, Cm);
+            g_right_t(ph, lane, Cm);
+        }
+        const double c0 = g_hsum(Cm) + (even ? pw : 0.0);   // (C h)[lane]
+        const double a0 = g_hsum(el.A);                      // (h^T A)[lane]
+        const double S = s2 + gsum(even ? c0 : 0.0);
+        const double rS = 1.0 / S;
+        const double res = yi - gsum(even ? el.bv : 0.0);
+        const double rr = res * rS;
+        el.eta = fma(a0, rr, el.eta);
+        double v[GL];
+        ggather(a0, v);
+        const double ar = a0 * rS;
+#pragma unroll
+        for (int r = 0; r < GL; ++r) el.J[r] = fma(v[r], ar, el.J[r]);
+        el.bv = fma(c0, rr, el.bv);
+        ggather(c0, v);
+        const double cr = c0 * rS;
+#pragma unroll
+        for (int r = 0; r < GL; ++r) {
+            el.A[r] = fma(-v[r], ar, el.A[r]);
+            Cm[r] = fma(-v[r], cr, Cm[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < GL; ++r) el.C[r] = Cm[r] + ((r == lane) ? pw : 0.0);
+    gelem_store(nodes, a.nc, c, lane, el);
+}
+
+// ------------------------------------------------------------------ odd-even reduction, level by level
+
+// level l from level l-1: node j = (2j) then (2j+1), or a copy of 2j at the end
+__global__ void __launch_bounds__(GCTA) k_gscan_up(const double* __restrict__ lo, int64_t nlo,
+                                                   double* __restrict__ hi, int64_t nhi) {
+    __shared__ GSmem sm[GGRP];
+    const int lane = threadIdx.x & (GL - 1);
+    const int g = threadIdx.x >> 4;
+    const int64_t j = blockIdx.x * (int64_t)GGRP + g;
+    if (j >= nhi) return;
+    GElem x, y, r;
+    gelem_load(lo, nlo, 2 * j, lane, x);
+    if (2 * j + 1 < nlo) {
+        gelem_load(lo, nlo, 2 * j + 1, lane, y);
+        g_combine(sm[g], lane, x, y, r);
+        gelem_store(hi, nhi, j, lane, r);
+    } else {
+        gelem_store(hi, nhi, j, lane, x);
+    }
+}
+
+// back-substitution from level l (parents) to level l-1 (children): prefix
+// state before each child and the information after it
+__global__ void __launch_bounds__(GCTA) k_gscan_down(const double* __restrict__ lo, int64_t nlo,
+                                                     const double* __restrict__ ppre, const double* __restrict__ psuf,
+                                                     int64_t nhi, double* __restrict__ cpre,
+                                                     double* __restrict__ csuf) {
+    __shared__ GSmem sm[GGRP];
+    const int lane = threadIdx.x & (GL - 1);
+    const int g = threadIdx.x >> 4;
+    const int64_t j = blockIdx.x * (int64_t)GGRP + g;
+    if (j >= nlo) return;
+    double P[GL], m, J[GL], eta;
+    const int64_t parent = j >> 1;
+    if (ppre) {
+        gvs_load(ppre, nhi, parent, lane, P, m);
+        gvs_load(psuf, nhi, parent, lane, J, eta);
+    } else {
+#pragma unroll
+        for (int r = 0; r < GL; ++r) { P[r] = 0.0; J[r] = 0.0; }
+        m = 0.0; eta = 0.0;
+    }
+    GElem sib;
+    if (j & 1) {
+        gelem_load(lo, nlo, j - 1, lane, sib);
+        double Po[GL], mo;
+        g_state_through(sm[g], lane, P, m, sib, Po, mo);
+        gvs_store(cpre, nlo, j, lane, Po, mo);
+        gvs_store(csuf, nlo, j, lane, J, eta);
+    } else {
+        gvs_store(cpre, nlo, j, lane, P, m);
+        if (j + 1 < nlo) {
+            gelem_load(lo, nlo, j + 1, lane, sib);
+            double Jo[GL], eo;
+            g_info_through(sm[g], lane, sib, J, eta, Jo, eo);
+            gvs_store(csuf, nlo, j, lane, Jo, eo);
+        } else {
+            gvs_store(csuf, nlo, j, lane, J, eta);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ k_gchunk: forward, reverse sweep
+
+static constexpr int GNF = GL + 3;   // stored per lane per step: predicted covariance column, mean entry, v, 1/S
+
+template <int MODE>
+__global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restrict__ pre,
+                                                 const double* __restrict__ suf, double* __restrict__ store,
+                                                 double* __restrict__ part, double* __restrict__ mean_out,
+                                                 double* __restrict__ var_out) {
+    constexpr bool BWD = (MODE != MODE_LOGLIK);
+    constexpr bool GRAD = (MODE == MODE_GRAD);
+    constexpr bool POST = (MODE == MODE_POSTERIOR);
+    __shared__ GSmem sm[GGRP];
+    const int lane = threadIdx.x & (GL - 1);
+    const int g = threadIdx.x >> 4;
+    const int64_t c = blockIdx.x * (int64_t)GGRP + g;
+    if (c >= a.nc) return;
+    const int64_t nc = a.nc;
+    const bool on = lane < a.gm.b;
+    const bool even = (lane & 1) == 0;
+    const double s2 = a.theta[a.gm.P - 1];
+    const double pw = on ? a.gconst[(lane >> 1) * GNC] : 0.0;
+    const int64_t s = c * a.L, e = min(a.n, s + a.L);
+    int bad = 0;
+
+    // ---- forward from the prefix state (m, D = P - Pinf)
+    double m, D[GL];
+    {
+        double P[GL];
+        gvs_load(pre, nc, c, lane, P, m);
+#pragma unroll
+        for (int r = 0; r < GL; ++r) D[r] = P[r] - ((r == lane) ? pw : 0.0);
+    }
+    double quad = 0.0, prod = 1.0;
+    int expo = 0;
+    for (int64_t i = s; i < e; ++i) {
+        const int64_t j = i - s;
+        const double yi = a.y[i];
+        double mb, Db[GL];
+        if (i == 0) {
+            mb = 0.0;
+#pragma unroll
+            for (int r = 0; r < GL; ++r) Db[r] = 0.0;
+        } else {
+            const double* ph = a.phis + i * (4 * GK);
+            mb = g_vleft(ph, lane, m);
+#pragma unroll
+            for (int r = 0; r < GL; ++r) Db[r] = D[r];
+            g_left(ph, Db);
+            g_right_t(ph, lane, Db);
+        }
+        const double p0 = g_hsum(Db) + (even ? pw : 0.0);
+        const double S = s2 + gsum(even ? p0 : 0.0);
+        if (!(S > 0.0) || !isfinite(S)) bad |= ST_ENUMERIC;
+        const double rS = 1.0 / S;
+        const double v = yi - gsum(even ? mb : 0.0);
+        quad = fma(v * v, rS, quad);
+        prod *= S;
+        {
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(prod);
+            expo += (int)((bits >> 52) & 0x7ffULL) - 1023;
+            prod = __longlong_as_double((long long)((bits & 0x800FFFFFFFFFFFFFULL) | 0x3FF0000000000000ULL));
+        }
+        if constexpr (BWD) {
+            double* st = store + ((j * nc + c) * GNF) * GL + lane;
+#pragma unroll
+            for (int r = 0; r < GL; ++r) st[r * GL] = Db[r];
+            st[GL * GL] = mb;
+            st[(GL + 1) * GL] = v;
+            st[(GL + 2) * GL] = rS;
+        }
+        double pv[GL];
+        ggather(p0, pv);
+        m = fma(p0, v * rS, mb);
+        const double pr = p0 * rS;
+#pragma unroll
+        for (int r = 0; r < GL; ++r) D[r] = fma(-pv[r], pr, Db[r]);
+    }
+    double acc[2 + 2 * GMAXCOMP];
+#pragma unroll
+    for (int f = 0; f < 2 + 2 * GMAXCOMP; ++f) acc[f] = 0.0;
+    if (lane == 0) acc[0] = -0.5 * (quad + log(prod) + (double)expo * G_LN2 + (double)(e - s) * G_LOG_2PI);
+
+    if constexpr (BWD) {
+        // ---- adjoint of the last filtered state from the information after the chunk
+        double lh, Lh[GL];
+        {
+            double J[GL], eta, P[GL], W[GL], v[GL];
+            gvs_load(suf, nc, c, lane, J, eta);
+#pragma unroll
+            for (int r = 0; r < GL; ++r) P[r] = D[r] + ((r == lane) ? pw : 0.0);
+            g_inv_ixy(sm[g], lane, J, P, W);            // (I + J P)^-1
+            ggather(m, v);
+            double w = eta;
+#pragma unroll
+            for (int k = 0; k < GL; ++k) w = fma(-J[k], v[k], w);   // (eta - J m)[lane]
+            ggather(w, v);
+            const unsigned mask = half_mask();
+            g_put(sm[g].X, lane, W); __syncwarp(mask);
+            lh = -g_rowdot(sm[g].X, lane, v); __syncwarp(mask);
+            g_mul(sm[g].X, J, Lh); __syncwarp(mask);     // W J
+            g_sym(sm[g], lane, Lh);
+        }
+        double gp = 0.0;   // diagonal entry 'lane' of the Pinf adjoint
+        for (int64_t i = e - 1; i >= s; --i) {
+            const int64_t j = i - s;
+            const double* st = store + ((j * nc + c) * GNF) * GL + lane;
+            double Db[GL];
+#pragma unroll
+            for (int r = 0; r < GL; ++r) Db[r] = st[r * GL];
+            const double mb = st[GL * GL];
+            const double v = st[(GL + 1) * GL];
+            const double rS = st[(GL + 2) * GL];
+            const double k = (g_hsum(Db) + (even ? pw : 0.0)) * rS;
+            const double kl = gsum(k * lh);
+            double kv[GL];
+            ggather(k, kv);
+            double u = 0.0;
+#pragma unroll
+            for (int r = 0; r < GL; ++r) u = fma(Lh[r], kv[r], u);
+            const double kuk = gsum(k * u);
+            const double al = fma(v, rS, kl);
+            const double cc = rS + kuk;
+            if constexpr (GRAD) {
+                if (lane == 0) acc[1] = fma(al, al, acc[1]) - cc;
+            }
+            if constexpr (POST) {
+                const double hk = gsum(even ? k : 0.0);
+                if (lane == 0) {
+                    mean_out[i] = fma(-s2, al, a.y[i]);
+                    var_out[i] = s2 * hk - s2 * s2 * kuk;
+                }
+            }
+            const double lt = lh - (even ? al : 0.0);
+            double uv[GL], Lt[GL];
+            ggather(u, uv);
+#pragma unroll
+            for (int r = 0; r < GL; ++r) {
+                double x = Lh[r];
+                if ((r & 1) == 0) x -= u;
+                if (even) x -= uv[r];
+                if ((r & 1) == 0 && even) x += cc;
+                Lt[r] = x;
+            }
+            double lv[GL], G[GL];
+            ggather(lt, lv);
+#pragma unroll
+            for (int r = 0; r < GL; ++r) G[r] = 0.5 * fma(lv[r], lt, -Lt[r]);
+            if constexpr (GRAD) {
+#pragma unroll
+                for (int r = 0; r < GL; ++r)
+                    if (r == lane) gp += G[r];
+            }
+            if (i > 0) {
+                const double* ph = a.phis + i * (4 * GK);
+                if constexpr (GRAD) {
+                    const double dt = a.t[i] - a.t[i - 1];
+                    // per block: 2 <G_k,:, X_k Db_k,:> (column 'lane' part) - lt_k^T X_k mb_k (row 'lane' part)
+                    const double mp = gxor(mb, 1);
+                    const double mb0 = even ? mb : mp, mb1 = even ? mp : mb;
+#pragma unroll
+                    for (int kb = 0; kb < GK; ++kb) {
+                        if (kb >= a.gm.K) break;
+                        const int kind = a.gm.bkind[kb];
+                        const int cp = a.gm.bcomp[kb];
+                        const double d0 = Db[2 * kb], d1 = Db[2 * kb + 1];
+                        const double g0 = G[2 * kb], g1 = G[2 * kb + 1];
+                        const bool mine = (lane >> 1) == kb;
+                        double rate = 0.0, envr = 0.0;
+                        if (kind == GB_MATERN32) {
+                            // X = [[0, 1], [-1, -2]]
+                            rate = 2.0 * (g0 * d1 + g1 * (-d0 - 2.0 * d1));
+                            if (mine) rate -= lt * (even ? mb1 : (-mb0 - 2.0 * mb1));
+                        } else {
+                            // X = j [[0, -1], [1, 0]] (rotation rate w); envelope X = -I
+                            const double jj = (double)a.gm.bj[kb];
+                            rate = jj * 2.0 * (g0 * (-d1) + g1 * d0);
+                            if (mine) rate -= jj * lt * (even ? -mb1 : mb0);
+                            if (kind == GB_QUASI) {
+                                envr = -2.0 * (g0 * d0 + g1 * d1);
+                                if (mine) envr += lt * (even ? mb0 : mb1);
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < GMAXCOMP; ++q)
+                            if (q == cp) {
+                                acc[2 + 2 * q] = fma(rate, dt, acc[2 + 2 * q]);
+                                acc[3 + 2 * q] = fma(envr, dt, acc[3 + 2 * q]);
+                            }
+                    }
+                }
+                // propagate to the previous step: lh = Phi^T lt, Lh = Phi^T Lt Phi
+                lh = g_vleft_t(ph, lane, lt);
+#pragma unroll
+                for (int r = 0; r < GL; ++r) Lh[r] = Lt[r];
+                g_right(ph, lane, Lh);
+                g_left_t(ph, Lh);
+                if constexpr (GRAD) {
+                    double ld = 0.0;
+#pragma unroll
+                    for (int r = 0; r < GL; ++r)
+                        if (r == lane) ld = Lh[r];
+                    gp -= 0.5 * fma(lh, lh, -ld);
+                }
+            }
+        }
+        if constexpr (GRAD) part[(2 + 2 * GMAXCOMP + lane) * nc + c] = gp;
+    }
+    if (bad) atomicOr(a.status, bad);
+    // per-chunk partials: group sums for the scalar slots, per-lane for the Pinf diagonal
+#pragma unroll
+    for (int f = 0; f < 2 + 2 * GMAXCOMP; ++f) acc[f] = gsum(acc[f]);
+    const int nu = GRAD ? 2 + 2 * GMAXCOMP : 1;
+    if (lane == 0)
+        for (int f = 0; f < nu; ++f) part[f * nc + c] = acc[f];
+}
+
+// ------------------------------------------------------------------ k_gfinal: fixed-order sums, chain rule
+
+static constexpr int GFIN = 128;
+
+__global__ void __launch_bounds__(GFIN) k_gfinal(GModel gm, const double* __restrict__ part, int64_t nc, int na,
+                                                 const double* __restrict__ theta, const double* __restrict__ gconst,
+                                                 double* __restrict__ ll_out, double* __restrict__ grad_out) {
+    __shared__ double red[GFIN * GPART];
+    __shared__ double tot[GPART];
+    const int tid = threadIdx.x;
+    for (int f = 0; f < na; ++f) {
+        double s = 0.0;
+        for (int64_t c = tid; c < nc; c += GFIN) s += part[f * nc + c];
+        red[f * GFIN + tid] = s;
+    }
+    __syncthreads();
+    for (int w = GFIN / 2; w > 0; w >>= 1) {
+        if (tid < w)
+            for (int f = 0; f < na; ++f) red[f * GFIN + tid] += red[f * GFIN + tid + w];
+        __syncthreads();
+    }
+    if (tid < na) tot[tid] = red[tid * GFIN];
+    __syncthreads();
+    if (tid != 0) return;
+    if (ll_out) ll_out[0] = tot[0];
+    if (!grad_out || na != GPART) return;
+    for (int p = 0; p < gm.P; ++p) grad_out[p] = 0.0;
+    grad_out[gm.P - 1] = 0.5 * tot[1];
+    for (int q = 0; q < gm.ncomp; ++q) {
+        const double* th = theta + gm.cpoff[q];
+        double* g = grad_out + gm.cpoff[q];
+        const double rate = tot[2 + 2 * q], envr = tot[3 + 2 * q];
+        if (gm.ckind[q] == SPINGP_MATERN32) {
+            const double lam = sqrt(3.0) / th[0];
+            g[0] = rate * (-lam / th[0]);
+        } else {
+            const double per = th[2];
+            g[2] = rate * (-2.0 * M_PI / (per * per));            // d w / d period
+            if (gm.ckind[q] == SPINGP_QUASIPERIODIC) g[3] = envr * (-1.0 / (th[3] * th[3]));   // lam_e = 1/l_e
+        }
+    }
+    // Pinf entries: block k is w_k I2
+    for (int k = 0; k < gm.K; ++k) {
+        const int q = gm.bcomp[k];
+        const double gk = tot[2 + 2 * GMAXCOMP + 2 * k] + tot[2 + 2 * GMAXCOMP + 2 * k + 1];
+        double* g = grad_out + gm.cpoff[q];
+        if (gm.ckind[q] == SPINGP_MATERN32) {
+            g[1] += gk * gconst[k * GNC + 1];
+        } else {
+            g[0] += gk * gconst[k * GNC + 1];
+            g[1] += gk * gconst[k * GNC + 2];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+static size_t galign(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct GLayout {
+    int64_t nc;
+    int nlev;               // levels above the chunk elements
+    int64_t lev_n[40];      // node counts, level 0 = chunks
+    size_t off_gconst, off_phis, off_nodes[40], off_pre[40], off_suf[40], off_part, off_store, total;
+
+    GLayout(int64_t n, int64_t L, int mode) {
+        nc = (n + L - 1) / L;
+        size_t o = 256;
+        off_gconst = o; o = galign(o + sizeof(double) * GK * GNC);
+        off_phis = o; o = galign(o + sizeof(double) * 4 * GK * (size_t)n);
+        nlev = 0;
+        lev_n[0] = nc;
+        while (lev_n[nlev] > 1) { lev_n[nlev + 1] = (lev_n[nlev] + 1) / 2; ++nlev; }
+        for (int l = 0; l <= nlev; ++l) {
+            off_nodes[l] = o; o = galign(o + sizeof(double) * GNE * GL * (size_t)lev_n[l]);
+            off_pre[l] = o; o = galign(o + sizeof(double) * GNM * GL * (size_t)lev_n[l]);
+            off_suf[l] = o; o = galign(o + sizeof(double) * GNM * GL * (size_t)lev_n[l]);
+        }
+        off_part = o; o = galign(o + sizeof(double) * GPART * (size_t)nc);
+        off_store = o;
+        if (mode != MODE_LOGLIK) o = galign(o + sizeof(double) * GNF * GL * (size_t)L * nc);
+        total = o;
+    }
+};
+
+size_t group_ws_bytes(int64_t n, int64_t L, int mode) { return GLayout(n, L, mode).total; }
+
+int group_launch_count(int64_t n, int64_t L, int mode) {
+    GLayout lay(n, L, mode);
+    return 2 + 1 + 2 * lay.nlev + 1 + 1;
+}
+
+int group_run(const GModel& gm, int mode, const double* t, const double* y, int64_t n, int64_t L,
+              const double* theta, double* ll_out, double* grad_out, double* mean_out, double* var_out, void* wsv,
+              cudaStream_t st, cudaEvent_t* ev) {
+    GLayout lay(n, L, mode);
+    char* ws = (char*)wsv;
+    int* status = (int*)ws;
+    double* gconst = (double*)(ws + lay.off_gconst);
+    double* phis = (double*)(ws + lay.off_phis);
+    double* part = (double*)(ws + lay.off_part);
+    double* store = (double*)(ws + lay.off_store);
+    GArgs a{gm, t, y, n, L, lay.nc, theta, gconst, phis, status};
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
+    if (ev) cudaEventRecord(ev[0], st);
+    k_gsetup<<<1, 32, 0, st>>>(gm, theta, gconst, status);
+    k_gdisc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gm, t, y, n, theta, phis, status);
+    const unsigned cgrid = (unsigned)((lay.nc + GGRP - 1) / GGRP);
+    k_gfold<<<cgrid, GCTA, 0, st>>>(a, (double*)(ws + lay.off_nodes[0]));
+    if (ev) cudaEventRecord(ev[1], st);
+    for (int l = 1; l <= lay.nlev; ++l)
+        k_gscan_up<<<(unsigned)((lay.lev_n[l] + GGRP - 1) / GGRP), GCTA, 0, st>>>(
+            (const double*)(ws + lay.off_nodes[l - 1]), lay.lev_n[l - 1], (double*)(ws + lay.off_nodes[l]),
+            lay.lev_n[l]);
+    for (int l = lay.nlev; l >= 1; --l) {
+        const bool top = (l == lay.nlev);
+        k_gscan_down<<<(unsigned)((lay.lev_n[l - 1] + GGRP - 1) / GGRP), GCTA, 0, st>>>(
+            (const double*)(ws + lay.off_nodes[l - 1]), lay.lev_n[l - 1],
+            top ? nullptr : (const double*)(ws + lay.off_pre[l]), top ? nullptr : (const double*)(ws + lay.off_suf[l]),
+            lay.lev_n[l], (double*)(ws + lay.off_pre[l - 1]), (double*)(ws + lay.off_suf[l - 1]));
+    }
+    if (lay.nlev == 0) {
+        // one chunk: zero prefix and suffix
+        if (cudaMemsetAsync(ws + lay.off_pre[0], 0, sizeof(double) * GNM * GL, st) != cudaSuccess) return 1;
+        if (cudaMemsetAsync(ws + lay.off_suf[0], 0, sizeof(double) * GNM * GL, st) != cudaSuccess) return 1;
+    }
+    if (ev) cudaEventRecord(ev[2], st);
+    const double* pre = (const double*)(ws + lay.off_pre[0]);
+    const double* suf = (const double*)(ws + lay.off_suf[0]);
+    int na = 1;
+    if (mode == MODE_LOGLIK) {
+        k_gchunk<MODE_LOGLIK><<<cgrid, GCTA, 0, st>>>(a, pre, suf, store, part, nullptr, nullptr);
+    } else if (mode == MODE_GRAD) {
+        k_gchunk<MODE_GRAD><<<cgrid, GCTA, 0, st>>>(a, pre, suf, store, part, nullptr, nullptr);
+        na = GPART;
+    } else {
+        k_gchunk<MODE_POSTERIOR><<<cgrid, GCTA, 0, st>>>(a, pre, suf, store, part, mean_out, var_out);
+    }
+    if (ev) cudaEventRecord(ev[3], st);
+    k_gfinal<<<1, GFIN, 0, st>>>(gm, part, lay.nc, na, theta, gconst, ll_out, grad_out);
+    if (ev) cudaEventRecord(ev[4], st);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+}  // namespace spg

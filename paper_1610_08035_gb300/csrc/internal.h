@@ -7,6 +7,17 @@
 
 namespace spg {
 
+// structured models on the group path: sums of components whose transitions
+// are 2x2 blocks (Matern-3/2, periodic, quasi-periodic with a Matern-1/2
+// envelope); state dimension b = 2K <= 16
+static constexpr int GMAXCOMP = 4;
+static constexpr int GMAXBLK = 8;
+struct GModel {
+    int b, K, P, ncomp;
+    int bkind[GMAXBLK], bcomp[GMAXBLK], bj[GMAXBLK];   // per block: kind, component, harmonic
+    int ckind[GMAXCOMP], cpoff[GMAXCOMP];              // per component: spingp_kind, theta offset
+};
+
 // device status bits (the status word at the start of every workspace)
 enum { ST_EINVAL = 1 << 1, ST_ENOTSORTED = 1 << 2, ST_ENONFINITE = 1 << 3, ST_ENUMERIC = 1 << 4 };
 
@@ -32,4 +43,18 @@ int matern_run_batched(int b, int mode, const int64_t* offsets, int64_t nseries,
 size_t probe_fp64_bytes();
 int probe_fp64(void* scratch, size_t bytes, double* tflops, cudaStream_t st);
 
+}  // namespace spg
+
+namespace spg {
+size_t group_ws_bytes(int64_t n, int64_t L, int mode);
+int group_launch_count(int64_t n, int64_t L, int mode);
+int group_run(const GModel& gm, int mode, const double* t, const double* y, int64_t n, int64_t L,
+              const double* theta, double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws,
+              cudaStream_t st, cudaEvent_t* ev);
+}  // namespace spg
+
+struct spingp_model;
+namespace spg {
+// true when the model runs on the b <= 3 chain kernels (matern.cu)
+bool model_on_chain_path(const spingp_model* m);
 }  // namespace spg

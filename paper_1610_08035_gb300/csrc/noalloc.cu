@@ -43,6 +43,7 @@ extern "C" spingp_status spingp_loglik_noalloc(const spingp_model* model, const 
                                                int64_t n, const double* theta, double* ll_out, unsigned flags,
                                                void* stream) {
     if (!model || !t || !y || !theta || !ll_out || n < 1) return SPINGP_EINVAL;
+    if (!spg::model_on_chain_path(model)) return SPINGP_EUNSUPPORTED;
     const size_t need = spingp_workspace_bytes(model, n, SPINGP_WS_LOGLIK);
     if (need == 0) return SPINGP_EUNSUPPORTED;
     if (need > (size_t)SPINGP_NOALLOC_SCRATCH_BYTES) return SPINGP_EINVAL;   // series too long for the fixed scratch

@@ -1,0 +1,101 @@
+"""GPU parity for structured models on the group path (sums of Matern-3/2,
+periodic and quasi-periodic components, b = 2K <= 16) against the oracle.
+Tolerances as in test_gpu_parity."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import seq  # noqa: E402
+from paper_1610_08035_gb300 import spingp, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+CONFIG3 = (["matern32", ("quasiperiodic", 6, "matern12")], [1.0, 1.0, 1.0, 1.0, 1.0, 10.0, 0.01])
+MODELS = [
+    CONFIG3,
+    (["matern32", "matern32"], [0.7, 1.2, 3.0, 0.5, 0.05]),
+    ([("periodic", 3)], [1.2, 1.0, 0.8, 0.1]),
+    (["matern32", ("periodic", 2)], [0.5, 0.8, 1.1, 0.9, 1.7, 0.05]),
+    ([("quasiperiodic", 3, "matern12")], [0.9, 1.3, 0.6, 3.0, 0.02]),
+]
+
+
+def _t(a):
+    return torch.tensor(np.asarray(a, dtype=np.float64), device=DEV)
+
+
+def series(n, mean_dt, seed, ties=0, gaps=0):
+    rng = np.random.default_rng(seed)
+    d = rng.exponential(mean_dt, n)
+    d[0] = 0.0
+    if ties:
+        d[::ties] = 0.0
+    if gaps:
+        d[gaps::gaps * 3 + 1] = 200 * mean_dt
+    t = np.cumsum(d)
+    y = synth.two_sinusoids(t, 1.0, 1.0, 0.05, rng)
+    return t, y
+
+
+def check(spec, theta, t, y, L=0, posterior=True):
+    m = spingp.Model(spec, chunk_len=L)
+    T, Y, TH = _t(t), _t(y), _t(theta)
+    ll, g = m.grad(T, Y, TH)
+    ll, g = float(ll.cpu()[0]), g.cpu().numpy()
+    ll1 = float(m.loglik(T, Y, TH).cpu()[0])
+    if posterior:
+        mean, var, ll2 = m.posterior(T, Y, TH)
+        llo, go, mo, vo, g1 = seq.grad(spec, theta, t, y, posterior=True, l1=True)
+        dm = np.abs(mean.cpu().numpy() - mo)
+        assert np.all(dm <= 1e-8 * np.maximum(np.abs(mo), np.sqrt(vo))), dm.max()
+        assert np.all(np.abs(var.cpu().numpy() - vo) <= 1e-8 * vo), np.max(np.abs(var.cpu().numpy() - vo) / vo)
+        assert abs(float(ll2.cpu()[0]) - llo) <= 1e-9 * abs(llo)
+    else:
+        llo, go, g1 = seq.grad(spec, theta, t, y, l1=True)
+    assert abs(ll - llo) <= 1e-9 * abs(llo), (ll, llo)
+    assert abs(ll1 - llo) <= 1e-9 * abs(llo), (ll1, llo)
+    assert np.all(np.abs(g - go) <= 1e-8 * np.maximum(np.abs(go), g1)), (g, go, g1)
+
+
+@pytest.mark.parametrize("spec,theta", MODELS)
+@pytest.mark.parametrize("n,L", [(1, 0), (5, 0), (1000, 8), (3000, 0), (4099, 64)])
+def test_group_parity(spec, theta, n, L):
+    t, y = series(n, 0.01, n + L)
+    check(spec, theta, t, y, L)
+
+
+@pytest.mark.parametrize("spec,theta", MODELS[:3])
+def test_group_ties_and_gaps(spec, theta):
+    t, y = series(6000, 0.01, 4, ties=7, gaps=53)
+    check(spec, theta, t, y, 16)
+
+
+def test_config3_against_oracle():
+    """Matern-3/2 + quasi-periodic (order 6, Matern-1/2 envelope), b = 16, the
+    benchmark's chunk length, 2^16 steps against the oracle."""
+    s = synth.single("sum_qp_n1m", n=1 << 16)
+    check(s.spec, s.theta, s.t, s.y, 0, posterior=True)
+
+
+def test_config3_full_size_identity():
+    """b = 16 at N = 2^20: scaling every variance (s_m32, s_per, s_n) by c scales
+    C by c, so sum_v s_v dl/ds_v = (y^T C^-1 y - N)/2 with y^T C^-1 y read off
+    l(2 s) - l(s)."""
+    s = synth.single("sum_qp_n1m")
+    m = spingp.Model(s.spec)
+    T, Y = _t(s.t), _t(s.y)
+    th = s.theta.copy()
+    ll, g = m.grad(T, Y, _t(th))
+    ll, g = float(ll.cpu()[0]), g.cpu().numpy()
+    var_idx = [1, 2, 6]
+    th2 = th.copy(); th2[var_idx] *= 2.0
+    ll2 = float(m.loglik(T, Y, _t(th2)).cpu()[0])
+    n = len(s.t)
+    q = 4.0 * (ll2 - ll + 0.5 * n * np.log(2.0))
+    lhs = sum(th[i] * g[i] for i in var_idx)
+    assert abs(lhs - (0.5 * q - 0.5 * n)) <= 1e-8 * (sum(abs(th[i] * g[i]) for i in var_idx) + n)
+    # deterministic
+    ll_b, g_b = m.grad(T, Y, _t(th))
+    assert float(ll_b.cpu()[0]) == ll and np.array_equal(g_b.cpu().numpy(), g)
