@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the secondary workloads (b = 16 sum, 4096-series batch, N = 2^26)")
     return ap.parse_args()
 
 
@@ -144,6 +146,109 @@ def run_reference(args):
         "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+# ---------------------------------------------------------------- secondary workloads
+
+def _time_calls(fn, K, flush, torch):
+    """Mean device time of fn over K calls, L2 flushed (untimed) before each."""
+    ms = 0.0
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    return ms / K
+
+
+def extra_workloads(args, dev, flush, world):
+    """loglik + gradient throughput of the other configurations: the b = 16
+    sum (Matern-3/2 + quasi-periodic), the batch of 4096 independent series of
+    uneven length, and the N = 2^26 Matern-3/2 series; each with its own
+    launch count and, for the batch, the plain GPU form (forward kernel run
+    2P+1 times per series, one launch sequence per series)."""
+    import torch
+
+    from paper_1610_08035_gb300 import autotune, spingp, synth
+
+    K = max(3, min(args.steps, 5))
+    res = {}
+    for name in ("sum_qp_n1m", "matern32_n64m"):
+        s = synth.single(name)
+        T, Y, TH = (torch.tensor(a, device=dev) for a in (s.t, s.y, s.theta))
+        m = spingp.Model(s.spec)
+        if name == "matern32_n64m":
+            autotune.tune(m, T, Y, TH, spingp.WS_GRAD)
+        P = m.num_params
+        ll = torch.empty(1, dtype=torch.float64, device=dev)
+        g = torch.empty(P, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            m.grad(T, Y, TH, out=(ll, g))
+        ms = _time_calls(lambda: m.grad(T, Y, TH, sync=False, out=(ll, g)), K, flush, torch)
+        st = spingp.spingp_ws_status(m.workspace(len(s.t), spingp.WS_GRAD, dev))
+        res[name] = {"value": world * len(s.t) / (ms * 1e-3), "unit": "steps/s", "ms_per_step": ms, "n": len(s.t),
+                     "b": m.state_dim, "params": P, "chunk_len": m.chunk_len(len(s.t)), "status": st,
+                     "gpu_launches_per_step": spingp.spingp_launch_count(m.h, len(s.t), spingp.WS_GRAD)}
+        del T, Y, TH, m
+        torch.cuda.empty_cache()
+    # the batch
+    s = synth.batched()
+    off = torch.tensor(s.extra["offsets"], dtype=torch.int64, device=dev)
+    T, Y = torch.tensor(s.t, device=dev), torch.tensor(s.y, device=dev)
+    TH = torch.tensor(s.theta, device=dev)
+    m = spingp.Model("matern52")
+    bt = spingp.Batch(m, off, T, Y)
+    B = bt.n_series
+    ll = torch.empty(B, dtype=torch.float64, device=dev)
+    g = torch.empty(3 * B, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        bt.grad(TH, out=(ll, g))
+    # captured once into a CUDA graph and replayed (no host work per call)
+    stream = torch.cuda.Stream(device=dev)
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            bt.grad(TH, sync=False, out=(ll, g))
+    torch.cuda.current_stream().wait_stream(stream)
+    ms = _time_calls(graph.replay, K, flush, torch)
+    n_total = len(s.t)
+    entry = {"value": world * n_total / (ms * 1e-3), "unit": "steps/s", "ms_per_step": ms, "n_series": B,
+             "n_total": n_total, "b": 3, "captured_graph": True,
+             "gpu_launches_per_step": spingp.spingp_launch_count_batched(m.h, B, n_total, spingp.WS_GRAD)}
+    if not args.no_comparator:
+        # plain GPU form: per series, the forward kernel at theta and theta +- h e_p
+        h = 1e-5
+        offs = s.extra["offsets"]
+        fwd = spingp.Model("matern52")
+        thetas = torch.tensor(s.extra["thetas"], device=dev)
+        pert = [thetas.clone()]
+        for p in range(3):
+            for sgn in (1.0, -1.0):
+                v = thetas.clone()
+                v[:, p] *= 1.0 + sgn * h
+                pert.append(v)
+        outs = torch.empty(len(pert), B, dtype=torch.float64, device=dev)
+        views = [(T[offs[i]:offs[i + 1]], Y[offs[i]:offs[i + 1]]) for i in range(B)]
+        pth = [[v[i].contiguous() for i in range(B)] for v in pert]
+
+        def fd_step():
+            for q in range(len(pert)):
+                for i in range(B):
+                    fwd.loglik(views[i][0], views[i][1], pth[q][i], sync=False, out=outs[q, i:i + 1])
+
+        # workspaces sized once per length before timing
+        for i in sorted(range(B), key=lambda i: -(offs[i + 1] - offs[i]))[:1]:
+            fwd.loglik(views[i][0], views[i][1], pth[0][i])
+        cms = _time_calls(fd_step, 1, flush, torch)
+        entry["comparator"] = {"kind": "forward kernel x 7 per series, one launch sequence per series",
+                               "value": world * n_total / (cms * 1e-3), "unit": "steps/s", "ms_per_step": cms,
+                               "speedup_of_batched_adjoint": cms / ms}
+    res["batched_4096"] = entry
+    return res
 
 
 # ---------------------------------------------------------------- the CUDA path
@@ -311,6 +416,10 @@ def main():
                              "value": world * n / (comp_ms * 1e-3), "unit": "steps/s", "ms_per_step": comp_ms,
                              "speedup_of_adjoint": comp_ms / ms_per_step,
                              "fd_grad_rel_err": float(np.max(np.abs(fd - gad) / np.abs(gad)))}
+
+    # ---- secondary workloads: the other configurations of the same path
+    if not args.no_extra and not args.n:
+        out["workloads"] = extra_workloads(args, dev, flush, world)
 
     # ---- the oracle on the host cores (rank 0, single GPU only)
     if not args.no_cpu_baseline and world == 1:

@@ -202,3 +202,35 @@ def test_workspace_too_small_is_rejected():
     g = torch.empty(3, dtype=torch.float64, device=DEV)
     st = spingp.spingp_grad(m.h, T, Y, 1000, TH, ll, g, ws, ws.numel(), spingp.SYNC)
     assert st == spingp.EINVAL
+
+
+def test_large_series_full_size():
+    """Matern-3/2, N = 2^26, dt ~ Exp(0.001), l = 0.05 (the long-series
+    workload) in the default launch configuration.  Checks: the log-likelihood
+    against the oracle over the whole series; the posterior mean and variance
+    at 16 sampled steps against the oracle on a window of +-20000 steps around
+    each (400 lengthscales: the data outside the window changes the posterior
+    at its centre by far less than FP64 resolution); and the variance-scaling
+    identity for the gradient."""
+    s = synth.single("matern32_n64m")
+    m = spingp.Model(s.spec)
+    T, Y, TH = _t(s.t), _t(s.y), _t(s.theta)
+    ll, g = m.grad(T, Y, TH)
+    ll, g = float(ll.cpu()[0]), g.cpu().numpy()
+    llo = seq.loglik(s.spec, s.theta, s.t, s.y)
+    assert abs(ll - llo) <= 1e-9 * abs(llo), (ll, llo)
+    mean, var, _ = m.posterior(T, Y, TH, with_loglik=False)
+    mean, var = mean.cpu().numpy(), var.cpu().numpy()
+    idx = np.random.default_rng(1).integers(20000, len(s.t) - 20000, 16)
+    for i in idx:
+        a, b = i - 20000, i + 20001
+        sm = seq.smoother(s.spec, s.theta, s.t[a:b], s.y[a:b])
+        mo, vo = sm["mean"][20000], sm["var"][20000]
+        assert abs(mean[i] - mo) <= 1e-8 * max(abs(mo), np.sqrt(vo)), (i, mean[i], mo)
+        assert abs(var[i] - vo) <= 1e-8 * vo, (i, var[i], vo)
+    th2 = s.theta.copy(); th2[1] *= 2; th2[2] *= 2
+    ll2 = float(m.loglik(T, Y, _t(th2)).cpu()[0])
+    n = len(s.t)
+    q = 4.0 * (ll2 - ll + 0.5 * n * np.log(2.0))
+    lhs = s.theta[1] * g[1] + s.theta[2] * g[2]
+    assert abs(lhs - (0.5 * q - 0.5 * n)) <= 1e-8 * (abs(s.theta[1] * g[1]) + abs(s.theta[2] * g[2]) + n)
