@@ -30,13 +30,16 @@ sys.path.insert(0, ROOT)
 METRIC = "loglik+grad time steps/s (FP64, N=2^22,b=3) vs plain GPU form; % HBM roofline"
 WORKLOAD = "matern52_n4m"
 
-# FP64 flops executed per time step by each stage of the gradient call for
-# b = 3 (2 x DFMA + DADD + DMUL thread instructions, counted with ncu at
-# N = 2^21, L = 36; profiles/k_chunk_grad_matern52_n2m.md).
-FLOPS_PER_STEP = {"elimination": 275.9, "chunk_pass": 379.0}
+# FP64 work per time step of each stage of the gradient call for b = 3, counted
+# with ncu at the benchmark's chunk length 108 (N = 2^21;
+# profiles/chain_kernels_grad_matern52_n2m.md): flops = 2 x DFMA + DADD + DMUL
+# thread instructions; FP64 instructions = everything the FP64 pipe executed
+# (the pipe issues one warp instruction per 16 cycles per SM whatever its kind).
+FLOPS_PER_STEP = {"elimination": 264.6, "chunk_pass": 361.7}
+FP64_INST_PER_STEP = {"elimination": 167.0, "chunk_pass": 227.1}
 # DRAM bytes per step moved by the chunk pass (ncu dram__bytes_read + write,
 # same capture); None once the kernel has changed since the counters were taken
-DRAM_BYTES_PER_STEP = {"chunk_pass": 333.9}
+DRAM_BYTES_PER_STEP = {"chunk_pass": 305.7}
 # algorithmic HBM bytes per step of the whole call: t and y in (16 B); the
 # gradient and log-likelihood outputs are O(1) per series
 ALGO_BYTES_PER_STEP = 16.0
@@ -331,11 +334,16 @@ def main():
     flops = FLOPS_PER_STEP.get(dom)
     achieved = flops * n / (stage_ms[dom] * 1e-3) / 1e12 if flops else None
     traffic = DRAM_BYTES_PER_STEP.get(dom)
+    inst = FP64_INST_PER_STEP.get(dom)
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
             "frac": achieved / fp64_tflops if achieved else None,
             "traffic": traffic * n if traffic else None,
             "peak_kind": "measured FP64 FMA probe (spingp_probe_fp64); nominal %.3f" % FP64_NOMINAL_TFLOPS,
-            "ms_per_launch": stage_ms[dom]}
+            "ms_per_launch": stage_ms[dom],
+            # the FP64 pipe's instruction rate: every FP64 instruction (not only
+            # FMAs) takes a pipe slot; peak = probe FMA rate = TFLOP/s / 2
+            "fp64_inst_per_s": inst * n / (stage_ms[dom] * 1e-3) if inst else None,
+            "pipe_frac": inst * n / (stage_ms[dom] * 1e-3) / (fp64_tflops * 1e12 / 2.0) if inst else None}
     hbm = {"algorithmic_bytes_per_step": ALGO_BYTES_PER_STEP,
            "achieved_gbs": ALGO_BYTES_PER_STEP * n / (ms_per_step * 1e-3) / 1e9}
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
