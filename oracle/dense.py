@@ -154,3 +154,17 @@ def grad(spec, theta, t, y):
     for D in dK + [np.eye(n)]:
         g.append(0.5 * (a @ D @ a) - 0.5 * np.sum(Cinv * D))
     return ll, np.array(g)
+
+
+def predict(spec, theta, t, y, t_star):
+    """Latent posterior mean and variance at new times (Eq. mean2 and the
+    variance formula of Sec. 2.2): K(t*, t) C^-1 y and k(0) - K(t*, t) C^-1 K(t, t*)."""
+    t = np.asarray(t, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    t_star = np.asarray(t_star, dtype=np.float64)
+    _, _, _, cf = _factor(spec, theta, t)
+    Ks, _ = kernel(spec, theta, t_star[:, None] - t[None, :])
+    k0, _ = kernel(spec, theta, np.zeros(1))
+    a = cho_solve(cf, y)
+    V = solve_triangular(cf[0], Ks.T, lower=True)
+    return Ks @ a, k0[0] - np.sum(V * V, axis=0)

@@ -29,7 +29,10 @@
  *   - A_n maps the state at t_n to the state at t_{n+1};
  *   - the noise parameter is the variance sigma_n^2; gradients are taken with
  *     respect to the raw parameters (lengthscales, variances, period);
- *   - the latent variance H P^s H^T is reported (no noise added).
+ *   - the latent variance H P^s H^T is reported (no noise added);
+ *   - a NaN observation is missing: infinite noise there, so the state is
+ *     predicted but not updated (the augmented formulation of Eqs. mean4-mean6:
+ *     test points carry Sigma' = infinity and y' = 0).
  *
  * Covariance families (parameter order in theta, noise variance last):
  *   1 Matern-1/2 (b=1), 2 Matern-3/2 (b=2), 3 Matern-5/2 (b=3):
@@ -429,7 +432,8 @@ static int check_inputs(const double* th, int P, const double* t, const double* 
     if (n < 1) return E_INVAL;
     for (int p = 0; p < P; ++p) if (!(th[p] > 0.0) || !isfinite(th[p])) return E_INVAL;
     for (long i = 0; i < n; ++i) {
-        if (!isfinite(t[i]) || (y && !isfinite(y[i]))) return E_NONFINITE;
+        /* a NaN observation is a missing one (a test point); infinities are errors */
+        if (!isfinite(t[i]) || (y && isinf(y[i]))) return E_NONFINITE;
         if (i > 0 && t[i] < t[i - 1]) return E_NOTSORTED;
     }
     return OK;
@@ -535,17 +539,23 @@ static int kf_forward(const om_t* om, const double* th, const double* t, const d
             for (int k = 0; k < b * b; ++k) Pb[k] += Q[k];
             msym(b, Pb);
         }
-        double PH[OMAXB];
-        mv(b, Pb, H, PH);
-        double S = s2, hm = 0.0;
-        for (int k = 0; k < b; ++k) { S += H[k] * PH[k]; hm += H[k] * mb[k]; }
-        if (!(S > 0.0)) return E_NUMERIC;
-        double v = y[i] - hm;
-        for (int k = 0; k < b; ++k) K[k] = PH[k] / S;
-        for (int k = 0; k < b; ++k) m[k] = mb[k] + K[k] * v;
-        for (int r = 0; r < b; ++r) for (int c = 0; c < b; ++c) P[r * b + c] = Pb[r * b + c] - K[r] * S * K[c];
-        msym(b, P);
-        acc += -0.5 * (log(2.0 * M_PI * S) + v * v / S);
+        if (isnan(y[i])) {
+            /* missing observation: infinite noise, no update (Eqs. mean4-mean6) */
+            memcpy(m, mb, sizeof(double) * b);
+            mcopy(b, Pb, P);
+        } else {
+            double PH[OMAXB];
+            mv(b, Pb, H, PH);
+            double S = s2, hm = 0.0;
+            for (int k = 0; k < b; ++k) { S += H[k] * PH[k]; hm += H[k] * mb[k]; }
+            if (!(S > 0.0)) return E_NUMERIC;
+            double v = y[i] - hm;
+            for (int k = 0; k < b; ++k) K[k] = PH[k] / S;
+            for (int k = 0; k < b; ++k) m[k] = mb[k] + K[k] * v;
+            for (int r = 0; r < b; ++r) for (int c = 0; c < b; ++c) P[r * b + c] = Pb[r * b + c] - K[r] * S * K[c];
+            msym(b, P);
+            acc += -0.5 * (log(2.0 * M_PI * S) + v * v / S);
+        }
         if (mf) memcpy(mf + (size_t)i * b, m, sizeof(double) * b);
         if (Pf) memcpy(Pf + (size_t)i * b * b, P, sizeof(double) * b * b);
     }
@@ -681,7 +691,11 @@ int oseq_grad(int ncomp, const int* kind, const int* order, const int* env, cons
     for (int p = 0; p < P; ++p) { grad[p] = 0.0; if (gabs) gabs[p] = 0.0; }
     /* backward information of y_{n-1}: J = H^T H / s2, eta = H^T y / s2 */
     double J[OB2], eta[OMAXB];
-    for (int r = 0; r < b; ++r) { eta[r] = H[r] * y[n - 1] / s2; for (int c = 0; c < b; ++c) J[r * b + c] = H[r] * H[c] / s2; }
+    const double w_last = isnan(y[n - 1]) ? 0.0 : 1.0 / s2;   /* a missing observation carries no information */
+    for (int r = 0; r < b; ++r) {
+        eta[r] = (w_last != 0.0) ? H[r] * y[n - 1] * w_last : 0.0;
+        for (int c = 0; c < b; ++c) J[r * b + c] = H[r] * H[c] * w_last;
+    }
     double gs2 = 0.0;
     for (long i = n - 1; i >= 0; --i) {
         double mb[OMAXB], Pb[OB2], T[OB2], v[OMAXB], Qbar[OB2], msm[OMAXB], Psm[OB2];
@@ -717,10 +731,12 @@ int oseq_grad(int ncomp, const int* kind, const int* order, const int* env, cons
         /* observation noise: d/ds2 sum_i log N(y_i; H z_i, s2) averaged over the posterior */
         double hm = 0.0, hph = 0.0;
         for (int r = 0; r < b; ++r) { hm += H[r] * msm[r]; for (int c = 0; c < b; ++c) hph += H[r] * Psm[r * b + c] * H[c]; }
-        double e = y[i] - hm;
-        double gterm = (e * e + hph) / (2.0 * s2 * s2) - 0.5 / s2;
-        gs2 += gterm;
-        if (gabs) gabs[P - 1] += fabs(gterm);
+        if (!isnan(y[i])) {
+            double e = y[i] - hm;
+            double gterm = (e * e + hph) / (2.0 * s2 * s2) - 0.5 / s2;
+            gs2 += gterm;
+            if (gabs) gabs[P - 1] += fabs(gterm);
+        }
         if (mean) mean[i] = hm;
         if (var) var[i] = hph;
         if (i > 0) {
@@ -735,7 +751,8 @@ int oseq_grad(int ncomp, const int* kind, const int* order, const int* env, cons
             mm(b, MJ, A, T); mtm(b, A, T, J);
             msym(b, J);
             mtv(b, A, Me, eta);
-            for (int r = 0; r < b; ++r) { eta[r] += H[r] * y[i - 1] / s2; for (int c = 0; c < b; ++c) J[r * b + c] += H[r] * H[c] / s2; }
+            if (!isnan(y[i - 1]))
+                for (int r = 0; r < b; ++r) { eta[r] += H[r] * y[i - 1] / s2; for (int c = 0; c < b; ++c) J[r * b + c] += H[r] * H[c] / s2; }
         }
     }
     grad[P - 1] = gs2;

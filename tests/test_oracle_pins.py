@@ -365,3 +365,30 @@ def test_sample_has_model_covariance():
     C = K + theta[-1] * np.eye(5)
     emp = draws.T @ draws / len(draws)
     assert np.max(np.abs(emp - C)) <= 0.05 * np.max(C)
+
+
+@pytest.mark.parametrize("spec,theta", ALL)
+def test_missing_observations_are_test_points(spec, theta):
+    """Eqs. mean4-mean6: a test point enters the chain with infinite noise (a
+    NaN observation).  The smoother's mean and latent variance there equal the
+    textbook predictive equations of the dense GP on the observed points, and
+    the log-likelihood and gradient equal those of the observed points alone."""
+    rng = np.random.default_rng(12)
+    t_obs, y_obs = _series(300, 0.05, 13)
+    t_new = np.sort(rng.uniform(t_obs[0] - 0.5, t_obs[-1] + 0.5, 60))
+    t_all = np.concatenate([t_obs, t_new])
+    order = np.argsort(t_all, kind="stable")
+    t_all = t_all[order]
+    y_all = np.concatenate([y_obs, np.full(len(t_new), np.nan)])[order]
+    is_new = order >= len(t_obs)
+    sm = seq.smoother(spec, theta, t_all, y_all)
+    md, vd = dense.predict(spec, theta, t_obs, y_obs, t_all[is_new])
+    tol = 1e-10 if spec in [s for s, _ in MATERN] else 1e-8
+    assert np.max(np.abs(sm["mean"][is_new] - md)) <= tol * max(1.0, np.max(np.abs(md)))
+    assert np.max(np.abs(sm["var"][is_new] - vd) / vd) <= tol * 10
+    ll_obs, g_obs = seq.grad(spec, theta, t_obs, y_obs)
+    ll_all, g_all = seq.grad(spec, theta, t_all, y_all)
+    assert abs(ll_all - ll_obs) <= 1e-12 * abs(ll_obs)
+    assert np.all(np.abs(g_all - g_obs) <= 1e-9 * np.maximum(1.0, np.abs(g_obs)))
+    _, g_dense = dense.grad(spec, theta, t_obs, y_obs)
+    assert np.all(np.abs(g_all - g_dense) <= 1e-8 * np.maximum(1.0, np.abs(g_dense)))
