@@ -82,6 +82,13 @@ typedef struct spingp_model spingp_model;
 typedef enum { SPINGP_WS_LOGLIK = 0, SPINGP_WS_GRAD = 1, SPINGP_WS_POSTERIOR = 2 } spingp_ws_kind;
 
 #define SPINGP_SYNC 1u
+/* Treat NaN observations as missing: the state at that time is predicted but
+ * not conditioned on (infinite noise there).  This is the augmented
+ * formulation of Eqs. mean4-mean6: put the test times into t with y = NaN and
+ * spingp_posterior returns the predictive mean and latent variance at them;
+ * log-likelihoods and gradients then cover the observed points only.  Without
+ * this flag a NaN observation is an error (SPINGP_ENONFINITE). */
+#define SPINGP_MISSING_NAN 2u
 
 /* Create a model handle from a host-side description (Sec. 2.1).  The handle
  * holds host constants only; it owns no device memory.  Returns EINVAL for a

@@ -133,8 +133,9 @@ spingp_status run(const spingp_model* m, int mode, const double* t, const double
     cudaEvent_t* ev = NULL;
     st = profile_slot(m, &ev);
     if (st != SPINGP_OK) return st;
-    const int rc = m->group ? spg::group_run(m->gm, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s, ev)
-                            : spg::matern_run(m->b, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s, ev);
+    const int miss = (flags & SPINGP_MISSING_NAN) ? 1 : 0;
+    const int rc = m->group ? spg::group_run(m->gm, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s, ev, miss)
+                            : spg::matern_run(m->b, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s, ev, miss);
     if (rc) return SPINGP_ECUDA;
     if (flags & SPINGP_SYNC) return spingp_ws_status(ws, stream);
     return SPINGP_OK;
@@ -171,7 +172,7 @@ spingp_status run_batched(const spingp_model* m, int mode, const int64_t* offset
     st = profile_slot(m, &ev);
     if (st != SPINGP_OK) return st;
     if (spg::matern_run_batched(m->b, mode, offsets, n_series, n_total, t, y, L, theta, ll, grad, mean, var, ws, s,
-                                ev))
+                                ev, (flags & SPINGP_MISSING_NAN) ? 1 : 0))
         return SPINGP_ECUDA;
     if (flags & SPINGP_SYNC) return spingp_ws_status(ws, stream);
     return SPINGP_OK;

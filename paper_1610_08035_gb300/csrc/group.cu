@@ -117,11 +117,11 @@ __global__ void k_gsetup(GModel gm, const double* __restrict__ theta, double* __
 // Phi for step i (transition from t_{i-1}): 4 entries per block, row-major.
 __global__ void __launch_bounds__(256) k_gdisc(GModel gm, const double* __restrict__ t, const double* __restrict__ y,
                                                 int64_t n, const double* __restrict__ theta,
-                                                double* __restrict__ phis, int* status) {
+                                                double* __restrict__ phis, int* status, int missing) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     int bad = 0;
-    if (!isfinite(t[i]) || !isfinite(y[i])) bad |= ST_ENONFINITE;
+    if (!isfinite(t[i]) || (!isfinite(y[i]) && !(missing && isnan(y[i])))) bad |= ST_ENONFINITE;
     const double dt = (i > 0) ? t[i] - t[i - 1] : 0.0;
     if (dt < 0.0) bad |= ST_ENOTSORTED;
     double* ph = phis + i * (4 * GK);
@@ -508,6 +508,7 @@ struct GArgs {
     const double* gconst;
     const double* phis;
     int* status;
+    int missing;          // 1: a NaN observation is missing (a test point)
 };
 
 __global__ void __launch_bounds__(GCTA) k_gfold(GArgs a, double* __restrict__ nodes) {
@@ -538,6 +539,7 @@ __global__ void __launch_bounds__(GCTA) k_gfold(GArgs a, double* __restrict__ no
             g_left(ph, Cm);
             g_right_t(ph, lane, Cm);
         }
+        if (a.missing && isnan(yi)) continue;               // missing: no update (Eqs. mean4-mean6)
         const double c0 = g_hsum(Cm) + (even ? pw : 0.0);   // (C h)[lane]
         const double a0 = g_hsum(el.A);                      // (h^T A)[lane]
         const double S = s2 + gsum(even ? c0 : 0.0);
@@ -661,9 +663,11 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
     }
     double quad = 0.0, prod = 1.0;
     int expo = 0;
+    int64_t nobs = 0;
     for (int64_t i = s; i < e; ++i) {
         const int64_t j = i - s;
         const double yi = a.y[i];
+        const bool obs = !(a.missing && isnan(yi));   // the same in every lane of the group
         double mb, Db[GL];
         if (i == 0) {
             mb = 0.0;
@@ -678,16 +682,19 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
             g_right_t(ph, lane, Db);
         }
         const double p0 = g_hsum(Db) + (even ? pw : 0.0);
-        const double S = s2 + gsum(even ? p0 : 0.0);
-        if (!(S > 0.0) || !isfinite(S)) bad |= ST_ENUMERIC;
-        const double rS = 1.0 / S;
-        const double v = yi - gsum(even ? mb : 0.0);
-        quad = fma(v * v, rS, quad);
-        prod *= S;
-        {
+        // a missing observation stores v = 1/S = 0, so the reverse sweep passes through it
+        double rS = 0.0, v = 0.0;
+        if (obs) {
+            const double S = s2 + gsum(even ? p0 : 0.0);
+            if (!(S > 0.0) || !isfinite(S)) bad |= ST_ENUMERIC;
+            rS = 1.0 / S;
+            v = yi - gsum(even ? mb : 0.0);
+            quad = fma(v * v, rS, quad);
+            prod *= S;
             const unsigned long long bits = (unsigned long long)__double_as_longlong(prod);
             expo += (int)((bits >> 52) & 0x7ffULL) - 1023;
             prod = __longlong_as_double((long long)((bits & 0x800FFFFFFFFFFFFFULL) | 0x3FF0000000000000ULL));
+            ++nobs;
         }
         if constexpr (BWD) {
             double* st = store + ((j * nc + c) * GNF) * GL + lane;
@@ -707,7 +714,7 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
     double acc[2 + 2 * GMAXCOMP];
 #pragma unroll
     for (int f = 0; f < 2 + 2 * GMAXCOMP; ++f) acc[f] = 0.0;
-    if (lane == 0) acc[0] = -0.5 * (quad + log(prod) + (double)expo * G_LN2 + (double)(e - s) * G_LOG_2PI);
+    if (lane == 0) acc[0] = -0.5 * (quad + log(prod) + (double)expo * G_LN2 + (double)nobs * G_LOG_2PI);
 
     if constexpr (BWD) {
         // ---- adjoint of the last filtered state from the information after the chunk
@@ -753,10 +760,27 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                 if (lane == 0) acc[1] = fma(al, al, acc[1]) - cc;
             }
             if constexpr (POST) {
-                const double hk = gsum(even ? k : 0.0);
-                if (lane == 0) {
-                    mean_out[i] = fma(-s2, al, a.y[i]);
-                    var_out[i] = s2 * hk - s2 * s2 * kuk;
+                const double yi = a.y[i];
+                if (a.missing && isnan(yi)) {
+                    // predicted only: mean = h^T (mb - Pb lh), variance = h^T Pb h - (Pb h)^T Lh (Pb h)
+                    const double p0 = g_hsum(Db) + (even ? pw : 0.0);
+                    double pv[GL];
+                    ggather(p0, pv);
+                    double lp = 0.0;
+#pragma unroll
+                    for (int r = 0; r < GL; ++r) lp = fma(Lh[r], pv[r], lp);
+                    const double hm = gsum(even ? mb : 0.0), pl = gsum(p0 * lh);
+                    const double hph = gsum(even ? p0 : 0.0), plp = gsum(p0 * lp);
+                    if (lane == 0) {
+                        mean_out[i] = hm - pl;
+                        var_out[i] = hph - plp;
+                    }
+                } else {
+                    const double hk = gsum(even ? k : 0.0);
+                    if (lane == 0) {
+                        mean_out[i] = fma(-s2, al, yi);
+                        var_out[i] = s2 * hk - s2 * s2 * kuk;
+                    }
                 }
             }
             const double lt = lh - (even ? al : 0.0);
@@ -937,7 +961,7 @@ int group_launch_count(int64_t n, int64_t L, int mode) {
 
 int group_run(const GModel& gm, int mode, const double* t, const double* y, int64_t n, int64_t L,
               const double* theta, double* ll_out, double* grad_out, double* mean_out, double* var_out, void* wsv,
-              cudaStream_t st, cudaEvent_t* ev) {
+              cudaStream_t st, cudaEvent_t* ev, int missing) {
     GLayout lay(n, L, mode);
     char* ws = (char*)wsv;
     int* status = (int*)ws;
@@ -945,11 +969,11 @@ int group_run(const GModel& gm, int mode, const double* t, const double* y, int6
     double* phis = (double*)(ws + lay.off_phis);
     double* part = (double*)(ws + lay.off_part);
     double* store = (double*)(ws + lay.off_store);
-    GArgs a{gm, t, y, n, L, lay.nc, theta, gconst, phis, status};
+    GArgs a{gm, t, y, n, L, lay.nc, theta, gconst, phis, status, missing};
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
     if (ev) cudaEventRecord(ev[0], st);
     k_gsetup<<<1, 32, 0, st>>>(gm, theta, gconst, status);
-    k_gdisc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gm, t, y, n, theta, phis, status);
+    k_gdisc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gm, t, y, n, theta, phis, status, missing);
     const unsigned cgrid = (unsigned)((lay.nc + GGRP - 1) / GGRP);
     k_gfold<<<cgrid, GCTA, 0, st>>>(a, (double*)(ws + lay.off_nodes[0]));
     if (ev) cudaEventRecord(ev[1], st);

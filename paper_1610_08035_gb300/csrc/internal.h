@@ -27,9 +27,10 @@ enum { MODE_LOGLIK = 0, MODE_GRAD = 1, MODE_POSTERIOR = 2 };
 size_t matern_ws_bytes(int b, int64_t n, int64_t L, int mode);
 int matern_prepare();
 // ev: NULL, or 5 events recorded around the four stages
+// missing: 1 = a NaN observation is a missing one (predicted, not conditioned on)
 int matern_run(int b, int mode, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
                double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws, cudaStream_t st,
-               cudaEvent_t* ev);
+               cudaEvent_t* ev, int missing);
 int matern_launch_count(int b, int64_t n, int64_t L, int mode);
 
 // batches of independent series: offsets (device, nseries + 1 entries), theta
@@ -38,7 +39,7 @@ size_t matern_ws_bytes_batched(int b, int64_t nseries, int64_t n_total, int64_t 
 int matern_launch_count_batched(int b, int64_t nseries, int64_t n_total, int64_t L, int mode);
 int matern_run_batched(int b, int mode, const int64_t* offsets, int64_t nseries, int64_t n_total, const double* t,
                        const double* y, int64_t L, const double* theta, double* ll_out, double* grad_out,
-                       double* mean_out, double* var_out, void* ws, cudaStream_t st, cudaEvent_t* ev);
+                       double* mean_out, double* var_out, void* ws, cudaStream_t st, cudaEvent_t* ev, int missing);
 
 size_t probe_fp64_bytes();
 int probe_fp64(void* scratch, size_t bytes, double* tflops, cudaStream_t st);
@@ -50,7 +51,7 @@ size_t group_ws_bytes(int64_t n, int64_t L, int mode);
 int group_launch_count(int64_t n, int64_t L, int mode);
 int group_run(const GModel& gm, int mode, const double* t, const double* y, int64_t n, int64_t L,
               const double* theta, double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws,
-              cudaStream_t st, cudaEvent_t* ev);
+              cudaStream_t st, cudaEvent_t* ev, int missing);
 }  // namespace spg
 
 struct spingp_model;

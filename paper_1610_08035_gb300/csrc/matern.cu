@@ -43,6 +43,7 @@ struct ChainArgs {
     const int64_t* cstart;    // [nseries + 1] first chunk of each series
     int64_t nseries;
     int P;                    // theta entries per series
+    int missing;              // 1: a NaN observation is missing (a test point)
 };
 
 // The steps of chunk c: [s, e), inside the series that starts at step s0 and
@@ -152,7 +153,8 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
         double tp = (s > cr.s0) ? a.t[s - 1] : 0.0;
         for (int64_t i = s; i < e; ++i) {
             const double ti = a.t[i], yi = a.y[i];
-            if (!isfinite(ti) || !isfinite(yi)) bad |= ST_ENONFINITE;
+            const bool obs = !(a.missing && isnan(yi));
+            if (!isfinite(ti) || (obs && !isfinite(yi))) bad |= ST_ENONFINITE;
             if (i > cr.s0) {
                 const double dt = ti - tp;
                 if (dt < 0.0) bad |= ST_ENOTSORTED;
@@ -180,6 +182,8 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
                 mat_mul_t_sym<B>(T, Ph, el.C);
             }
             // condition on y_i: innovation of y_i given the node before the chunk
+            // (a missing observation has infinite noise: no update, Eqs. mean4-mean6)
+            if (obs) {
             double a0[B], c0[B];
 #pragma unroll
             for (int r = 0; r < B; ++r) {
@@ -205,6 +209,7 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
                 for (int q = 0; q < B; ++q) el.A[r][q] = fma(-g, a0[q], el.A[r][q]);
 #pragma unroll
                 for (int q = r; q < B; ++q) { el.C[r][q] = fma(-g, c0[q], el.C[r][q]); el.C[q][r] = el.C[r][q]; }
+            }
             }
             tp = ti;
         }
@@ -503,9 +508,11 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
         }
         double quad = 0.0, prod = 1.0;
         int expo = 0;
+        int64_t nobs = 0;
         for (int64_t i = s; i < e; ++i) {
             const int64_t j = i - s;
             const double yi = a.y[i];
+            const bool obs = !(a.missing && isnan(yi));
             double mb[B], Db[B][B];
             if (i == cr.s0) {
 #pragma unroll
@@ -526,13 +533,19 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
             double p0[B];   // first column of the predicted covariance
 #pragma unroll
             for (int r = 0; r < B; ++r) p0[r] = (r == 0 || p1<B>(r, 0) != 0.0) ? Db[r][0] + sf * p1<B>(r, 0) : Db[r][0];
-            const double S = p0[0] + s2;
-            if (!(S > 0.0) || !isfinite(S)) bad |= ST_ENUMERIC;
-            const double rS = 1.0 / S;
-            const double v = yi - mb[0];
-            quad = fma(v * v, rS, quad);
-            prod *= S;
-            renorm(prod, expo);
+            // a missing observation stores v = 1/S = 0: the reverse sweep then
+            // passes its adjoints through unchanged
+            double rS = 0.0, v = 0.0;
+            if (obs) {
+                const double S = p0[0] + s2;
+                if (!(S > 0.0) || !isfinite(S)) bad |= ST_ENUMERIC;
+                rS = 1.0 / S;
+                v = yi - mb[0];
+                quad = fma(v * v, rS, quad);
+                prod *= S;
+                renorm(prod, expo);
+                ++nobs;
+            }
             if constexpr (BWD) {
                 double* st = store + (j * NF) * nc + c;
                 int f = 0;
@@ -545,7 +558,7 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
                 st[(f++) * nc] = v;
                 st[(f++) * nc] = rS;
             }
-            const double vr = v * rS;
+            const double vr = v * rS;   // both zero for a missing observation: m = mb, D = Db
 #pragma unroll
             for (int r = 0; r < B; ++r) {
                 m[r] = fma(p0[r], vr, mb[r]);
@@ -554,7 +567,7 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
                 for (int q = r; q < B; ++q) { D[r][q] = fma(-g, p0[q], Db[r][q]); D[q][r] = D[r][q]; }
             }
         }
-        acc[0] = -0.5 * (quad + log(prod) + (double)expo * LN2 + (double)(e - s) * LOG_2PI);
+        acc[0] = -0.5 * (quad + log(prod) + (double)expo * LN2 + (double)nobs * LOG_2PI);
 
         if constexpr (BWD) {
             // ---- 3. reverse sweep, seeded by the information after the chunk
@@ -611,8 +624,22 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
                 const double cc = rS + kuk;           // (C^-1)_ii
                 if constexpr (GRAD) gs = fma(al, al, gs) - cc;
                 if constexpr (POST) {
-                    mean_out[i] = fma(-s2, al, a.y[i]);
-                    var_out[i] = s2 * k[0] - s2 * s2 * kuk;
+                    const double yi = a.y[i];
+                    if (a.missing && isnan(yi)) {
+                        // predicted only: mean = (mb - Pb lh)_0, variance = Pb_00 - Pb_0^T Lh Pb_0
+                        double p0[B], w[B], pl = 0.0, q = 0.0;
+#pragma unroll
+                        for (int r = 0; r < B; ++r)
+                            p0[r] = (r == 0 || p1<B>(r, 0) != 0.0) ? Db[r][0] + sf * p1<B>(r, 0) : Db[r][0];
+                        mat_vec<B>(Lh, p0, w);
+#pragma unroll
+                        for (int r = 0; r < B; ++r) { pl = fma(p0[r], lh[r], pl); q = fma(p0[r], w[r], q); }
+                        mean_out[i] = mb[0] - pl;
+                        var_out[i] = p0[0] - q;
+                    } else {
+                        mean_out[i] = fma(-s2, al, yi);
+                        var_out[i] = s2 * k[0] - s2 * s2 * kuk;
+                    }
                 }
                 double lt[B], Lt[B][B], G[B][B];
 #pragma unroll
@@ -947,7 +974,7 @@ int matern_launch_count_t(int64_t n, int64_t L, int mode) {
 template <int B>
 int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
                  double* ll_out, double* grad_out, double* mean_out, double* var_out, void* wsv, cudaStream_t st,
-                 cudaEvent_t* ev) {
+                 cudaEvent_t* ev, int missing) {
     Layout<B> lay(n, L, mode);
     char* ws = (char*)wsv;
     int* status = (int*)ws;
@@ -958,7 +985,7 @@ int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t 
     double* phis = (double*)(ws + lay.off_phis);
     double* part = (double*)(ws + lay.off_part);
     double* store = (double*)(ws + lay.off_store);
-    ChainArgs a{t, y, n, L, lay.nc, lay.nb, theta, status, nullptr, nullptr, 0, 3};
+    ChainArgs a{t, y, n, L, lay.nc, lay.nb, theta, status, nullptr, nullptr, 0, 3, missing};
     const unsigned grid = (unsigned)lay.nb;
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
     if (ev) cudaEventRecord(ev[0], st);
@@ -1003,7 +1030,8 @@ int matern_launch_count_batched_t(int64_t nseries, int64_t n_total, int64_t L, i
 template <int B>
 int matern_run_batched_t(int mode, const int64_t* offsets, int64_t nseries, int64_t n_total, const double* t,
                          const double* y, int64_t L, const double* theta, double* ll_out, double* grad_out,
-                         double* mean_out, double* var_out, void* wsv, cudaStream_t st, cudaEvent_t* ev) {
+                         double* mean_out, double* var_out, void* wsv, cudaStream_t st, cudaEvent_t* ev,
+                         int missing) {
     Layout<B> lay(n_total, L, mode, nseries);
     char* ws = (char*)wsv;
     int* status = (int*)ws;
@@ -1015,7 +1043,7 @@ int matern_run_batched_t(int mode, const int64_t* offsets, int64_t nseries, int6
     double* phis = (double*)(ws + lay.off_phis);
     double* part = (double*)(ws + lay.off_part);
     double* store = (double*)(ws + lay.off_store);
-    ChainArgs a{t, y, n_total, L, lay.nc, lay.nb, theta, status, offsets, cstart, nseries, 3};
+    ChainArgs a{t, y, n_total, L, lay.nc, lay.nb, theta, status, offsets, cstart, nseries, 3, missing};
     const unsigned grid = (unsigned)lay.nb;
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
     if (ev) cudaEventRecord(ev[0], st);
@@ -1072,11 +1100,12 @@ int matern_prepare() {
 
 int matern_run(int b, int mode, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
                double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws, cudaStream_t st,
-               cudaEvent_t* ev) {
+               cudaEvent_t* ev, int missing) {
     switch (b) {
-    case 1: return matern_run_t<1>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev);
-    case 2: return matern_run_t<2>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev);
-    default: return matern_run_t<3>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev);
+    case 1: return matern_run_t<1>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev, missing);
+    case 2: return matern_run_t<2>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev, missing);
+    default:
+        return matern_run_t<3>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev, missing);
     }
 }
 
@@ -1098,14 +1127,14 @@ int matern_launch_count_batched(int b, int64_t nseries, int64_t n_total, int64_t
 
 int matern_run_batched(int b, int mode, const int64_t* offsets, int64_t nseries, int64_t n_total, const double* t,
                        const double* y, int64_t L, const double* theta, double* ll_out, double* grad_out,
-                       double* mean_out, double* var_out, void* ws, cudaStream_t st, cudaEvent_t* ev) {
+                       double* mean_out, double* var_out, void* ws, cudaStream_t st, cudaEvent_t* ev, int missing) {
     switch (b) {
     case 1: return matern_run_batched_t<1>(mode, offsets, nseries, n_total, t, y, L, theta, ll_out, grad_out,
-                                           mean_out, var_out, ws, st, ev);
+                                           mean_out, var_out, ws, st, ev, missing);
     case 2: return matern_run_batched_t<2>(mode, offsets, nseries, n_total, t, y, L, theta, ll_out, grad_out,
-                                           mean_out, var_out, ws, st, ev);
+                                           mean_out, var_out, ws, st, ev, missing);
     default: return matern_run_batched_t<3>(mode, offsets, nseries, n_total, t, y, L, theta, ll_out, grad_out,
-                                            mean_out, var_out, ws, st, ev);
+                                            mean_out, var_out, ws, st, ev, missing);
     }
 }
 

@@ -52,7 +52,7 @@ extern "C" spingp_status spingp_loglik_noalloc(const spingp_model* model, const 
     if (st != SPINGP_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if (spg::matern_run(spingp_state_dim(model), spg::MODE_LOGLIK, t, y, n, spingp_get_chunk_len(model, n), theta,
-                        ll_out, nullptr, nullptr, nullptr, ws, s, nullptr))
+                        ll_out, nullptr, nullptr, nullptr, ws, s, nullptr, (flags & SPINGP_MISSING_NAN) ? 1 : 0))
         return SPINGP_ECUDA;
     if (flags & SPINGP_SYNC) return spingp_ws_status(ws, stream);
     return SPINGP_OK;

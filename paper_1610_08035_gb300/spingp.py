@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libspingp.so")
 OK, EINVAL, ENOTSORTED, ENONFINITE, ENUMERIC, ECUDA, ETIMEOUT, ENOMEM, EUNSUPPORTED = range(9)
 WS_LOGLIK, WS_GRAD, WS_POSTERIOR = 0, 1, 2
 SYNC = 1
+MISSING_NAN = 2
 
 KINDS = {"matern12": 1, "matern32": 2, "matern52": 3, "periodic": 4, "quasiperiodic": 5}
 
@@ -298,14 +299,19 @@ class Model:
             raise ValueError("theta must have %d entries" % self.num_params)
         return t.numel()
 
-    def loglik(self, t, y, theta, sync=True, out=None):
+    @staticmethod
+    def _flags(sync, missing):
+        return (SYNC if sync else 0) | (MISSING_NAN if missing else 0)
+
+    def loglik(self, t, y, theta, sync=True, out=None, missing=False):
         n = self._args(t, y, theta)
         ws = self.workspace(n, WS_LOGLIK, t.device)
         ll = out if out is not None else torch.empty(1, dtype=torch.float64, device=t.device)
-        _check(spingp_loglik(self.h, t, y, n, theta, ll, ws, ws.numel(), SYNC if sync else 0), "spingp_loglik")
+        _check(spingp_loglik(self.h, t, y, n, theta, ll, ws, ws.numel(), self._flags(sync, missing)),
+               "spingp_loglik")
         return ll
 
-    def grad(self, t, y, theta, sync=True, out=None):
+    def grad(self, t, y, theta, sync=True, out=None, missing=False):
         n = self._args(t, y, theta)
         ws = self.workspace(n, WS_GRAD, t.device)
         if out is None:
@@ -313,18 +319,34 @@ class Model:
             g = torch.empty(self.num_params, dtype=torch.float64, device=t.device)
         else:
             ll, g = out
-        _check(spingp_grad(self.h, t, y, n, theta, ll, g, ws, ws.numel(), SYNC if sync else 0), "spingp_grad")
+        _check(spingp_grad(self.h, t, y, n, theta, ll, g, ws, ws.numel(), self._flags(sync, missing)),
+               "spingp_grad")
         return ll, g
 
-    def posterior(self, t, y, theta, sync=True, with_loglik=True):
+    def posterior(self, t, y, theta, sync=True, with_loglik=True, missing=False):
         n = self._args(t, y, theta)
         ws = self.workspace(n, WS_POSTERIOR, t.device)
         mean = torch.empty(n, dtype=torch.float64, device=t.device)
         var = torch.empty(n, dtype=torch.float64, device=t.device)
         ll = torch.empty(1, dtype=torch.float64, device=t.device) if with_loglik else None
-        _check(spingp_posterior(self.h, t, y, n, theta, ll, mean, var, ws, ws.numel(), SYNC if sync else 0),
-               "spingp_posterior")
+        _check(spingp_posterior(self.h, t, y, n, theta, ll, mean, var, ws, ws.numel(),
+                                self._flags(sync, missing)), "spingp_posterior")
         return mean, var, ll
+
+    def predict(self, t, y, theta, t_star):
+        """Latent predictive mean and variance at new times t_star (Eqs.
+        mean4-mean6): the test times join the chain with missing (NaN)
+        observations, one posterior pass covers both.  t must be sorted;
+        t_star may be in any order.  Returns (mean, var) at t_star."""
+        _dev_f64(t_star, "t_star")
+        t_all = torch.cat([t, t_star])
+        y_all = torch.cat([y, torch.full_like(t_star, float("nan"))])
+        t_sorted, order = torch.sort(t_all, stable=True)
+        mean, var, _ = self.posterior(t_sorted, y_all[order].contiguous(), theta, with_loglik=False, missing=True)
+        where = torch.empty_like(order)
+        where[order] = torch.arange(order.numel(), device=order.device)
+        idx = where[t.numel():]
+        return mean[idx], var[idx]
 
 
 class Batch:
