@@ -167,15 +167,26 @@ def _time_calls(fn, K, flush, torch):
     return ms / K
 
 
-def extra_workloads(args, dev, flush, world):
+def extra_workloads(args, dev, flush, world, rank=0):
     """loglik + gradient throughput of the other configurations: the b = 16
     sum (Matern-3/2 + quasi-periodic), the batch of 4096 independent series of
     uneven length, and the N = 2^26 Matern-3/2 series; each with its own
     launch count and, for the batch, the plain GPU form (forward kernel run
-    2P+1 times per series, one launch sequence per series)."""
+    2P+1 times per series, one launch sequence per series).  With several
+    ranks the single series run as replicas (weak scaling) and the batch is
+    sharded across ranks by series (strong scaling: the same 4096 series in
+    total, no exchange on the data path)."""
     import torch
+    import torch.distributed as dist
 
-    from paper_1610_08035_gb300 import autotune, spingp, synth
+    from paper_1610_08035_gb300 import autotune, shard, spingp, synth
+
+    def max_ms(v):
+        if world == 1:
+            return v
+        x = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        return float(x.item())
 
     K = max(3, min(args.steps, 5))
     res = {}
@@ -190,15 +201,21 @@ def extra_workloads(args, dev, flush, world):
         g = torch.empty(P, dtype=torch.float64, device=dev)
         for _ in range(3):
             m.grad(T, Y, TH, out=(ll, g))
-        ms = _time_calls(lambda: m.grad(T, Y, TH, sync=False, out=(ll, g)), K, flush, torch)
+        ms = max_ms(_time_calls(lambda: m.grad(T, Y, TH, sync=False, out=(ll, g)), K, flush, torch))
         st = spingp.spingp_ws_status(m.workspace(len(s.t), spingp.WS_GRAD, dev))
         res[name] = {"value": world * len(s.t) / (ms * 1e-3), "unit": "steps/s", "ms_per_step": ms, "n": len(s.t),
                      "b": m.state_dim, "params": P, "chunk_len": m.chunk_len(len(s.t)), "status": st,
                      "gpu_launches_per_step": spingp.spingp_launch_count(m.h, len(s.t), spingp.WS_GRAD)}
         del T, Y, TH, m
         torch.cuda.empty_cache()
-    # the batch
+    # the batch (this rank's shard of whole series)
     s = synth.batched()
+    n_all = len(s.t)
+    if world > 1:
+        mine = shard.lpt_shard(np.diff(s.extra["offsets"]), world)[rank]
+        loc, tt, yy, thl = shard.local_batch(s.extra["offsets"], s.t, s.y, s.extra["thetas"], mine)
+        s.t, s.y, s.theta = tt, yy, thl.reshape(-1).copy()
+        s.extra = dict(offsets=loc, thetas=thl)
     off = torch.tensor(s.extra["offsets"], dtype=torch.int64, device=dev)
     T, Y = torch.tensor(s.t, device=dev), torch.tensor(s.y, device=dev)
     TH = torch.tensor(s.theta, device=dev)
@@ -217,10 +234,10 @@ def extra_workloads(args, dev, flush, world):
         with torch.cuda.graph(graph, stream=stream):
             bt.grad(TH, sync=False, out=(ll, g))
     torch.cuda.current_stream().wait_stream(stream)
-    ms = _time_calls(graph.replay, K, flush, torch)
+    ms = max_ms(_time_calls(graph.replay, K, flush, torch))
     n_total = len(s.t)
-    entry = {"value": world * n_total / (ms * 1e-3), "unit": "steps/s", "ms_per_step": ms, "n_series": B,
-             "n_total": n_total, "b": 3, "captured_graph": True,
+    entry = {"value": n_all / (ms * 1e-3), "unit": "steps/s", "ms_per_step": ms, "n_series": 4096,
+             "n_total": n_all, "b": 3, "captured_graph": True, "scaling": "strong",
              "gpu_launches_per_step": spingp.spingp_launch_count_batched(m.h, B, n_total, spingp.WS_GRAD)}
     if not args.no_comparator:
         # plain GPU form: per series, the forward kernel at theta and theta +- h e_p
@@ -246,9 +263,9 @@ def extra_workloads(args, dev, flush, world):
         # workspaces sized once per length before timing
         for i in sorted(range(B), key=lambda i: -(offs[i + 1] - offs[i]))[:1]:
             fwd.loglik(views[i][0], views[i][1], pth[0][i])
-        cms = _time_calls(fd_step, 1, flush, torch)
+        cms = max_ms(_time_calls(fd_step, 1, flush, torch))
         entry["comparator"] = {"kind": "forward kernel x 7 per series, one launch sequence per series",
-                               "value": world * n_total / (cms * 1e-3), "unit": "steps/s", "ms_per_step": cms,
+                               "value": n_all / (cms * 1e-3), "unit": "steps/s", "ms_per_step": cms,
                                "speedup_of_batched_adjoint": cms / ms}
     res["batched_4096"] = entry
     return res
@@ -427,7 +444,7 @@ def main():
 
     # ---- secondary workloads: the other configurations of the same path
     if not args.no_extra and not args.n:
-        out["workloads"] = extra_workloads(args, dev, flush, world)
+        out["workloads"] = extra_workloads(args, dev, flush, world, rank)
 
     # ---- the oracle on the host cores (rank 0, single GPU only)
     if not args.no_cpu_baseline and world == 1:

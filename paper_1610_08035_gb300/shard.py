@@ -1,0 +1,66 @@
+"""Sharding batches of independent series across ranks (one process per GPU).
+
+A batch of series has no exchange step: each rank takes a subset of whole
+series, runs the batched entry points on its own GPU, and only the per-series
+results are gathered at the end.  Series are assigned by the longest-
+processing-time rule (longest first, to the rank with the least work so far),
+which keeps every rank within one longest series of the mean load.
+
+Host-side logic only (no GPU work): the tests run it on CPU ranks with the
+gloo backend.
+"""
+import heapq
+
+import numpy as np
+import torch
+import torch.distributed as dist
+
+
+def lpt_shard(lengths, world):
+    """Assign series (given their lengths) to `world` ranks.  Returns one
+    sorted int64 array of series indices per rank."""
+    lengths = np.asarray(lengths, dtype=np.int64)
+    heap = [(0, r) for r in range(world)]
+    owner = np.empty(len(lengths), dtype=np.int64)
+    for i in np.argsort(-lengths, kind="stable"):
+        load, r = heapq.heappop(heap)
+        owner[i] = r
+        heapq.heappush(heap, (load + int(lengths[i]), r))
+    return [np.flatnonzero(owner == r) for r in range(world)]
+
+
+def local_batch(offsets, t, y, theta, series):
+    """The concatenated inputs of the given series: (offsets, t, y, theta)
+    with offsets starting at 0; theta has one row per series."""
+    offsets = np.asarray(offsets, dtype=np.int64)
+    lengths = offsets[series + 1] - offsets[series]
+    loc = np.zeros(len(series) + 1, dtype=np.int64)
+    loc[1:] = np.cumsum(lengths)
+    idx = np.concatenate([np.arange(offsets[i], offsets[i + 1]) for i in series]) if len(series) else \
+        np.empty(0, dtype=np.int64)
+    return loc, np.asarray(t)[idx], np.asarray(y)[idx], np.asarray(theta)[series]
+
+
+def gather_per_series(values, series, n_series, group=None):
+    """Gather per-series rows (a 2-D float64 tensor, one row per local series)
+    from every rank into the full (n_series, k) table, in series order, on
+    every rank.  The only collective of the batched path."""
+    world = dist.get_world_size(group)
+    k = values.shape[1]
+    counts = torch.tensor([len(series)], dtype=torch.int64)
+    all_counts = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
+    dist.all_gather(all_counts, counts, group=group)
+    m = int(max(c.item() for c in all_counts))
+    pad_v = torch.zeros(m, k, dtype=torch.float64, device=values.device)
+    pad_v[:len(series)] = values
+    pad_i = torch.full((m,), -1, dtype=torch.int64, device=values.device)
+    pad_i[:len(series)] = torch.as_tensor(series, dtype=torch.int64, device=values.device)
+    all_v = [torch.empty_like(pad_v) for _ in range(world)]
+    all_i = [torch.empty_like(pad_i) for _ in range(world)]
+    dist.all_gather(all_v, pad_v, group=group)
+    dist.all_gather(all_i, pad_i, group=group)
+    out = torch.zeros(n_series, k, dtype=torch.float64, device=values.device)
+    for v, i in zip(all_v, all_i):
+        keep = i >= 0
+        out[i[keep]] = v[keep]
+    return out
