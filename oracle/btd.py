@@ -78,3 +78,56 @@ def stacked(spec, theta, t):
 
 def block(M, b, i, j):
     return M[i * b:(i + 1) * b, j * b:(j + 1) * b]
+
+
+def blocks_of(M, b):
+    """Diagonal blocks D[i] = M[i,i] and sub-diagonal blocks O[i] = M[i+1,i]
+    of a dense block-tridiagonal matrix."""
+    n = M.shape[0] // b
+    D = np.array([block(M, b, i, i) for i in range(n)])
+    O = np.array([block(M, b, i + 1, i) for i in range(n - 1)]).reshape(max(n - 1, 0), b, b)
+    return D, O
+
+
+def thomas(D, O, r):
+    """The sequential block algorithm for a symmetric positive-definite BTD
+    matrix T (diagonal blocks D[i], sub-diagonal blocks O[i] = T[i+1, i]):
+    block LDL^T (Sec. 3.1's Thomas algorithm, subproblems 1 and 3) and the
+    selected inverse (subproblems 2 and 4) by the backward recursion of the
+    same factors.
+
+    Returns (logdet, x = T^-1 r, S_diag[i] = (T^-1)[i,i], S_off[i] = (T^-1)[i+1,i]).
+    """
+    D = np.asarray(D, dtype=np.float64)
+    O = np.asarray(O, dtype=np.float64)
+    r = np.asarray(r, dtype=np.float64)
+    n, b, _ = D.shape
+    S = np.empty_like(D)          # Schur complements (the pivots)
+    L = np.empty_like(O)          # L[i] = O[i] S[i]^-1
+    z = np.empty_like(r)
+    logdet = 0.0
+    for i in range(n):
+        Si = D[i].copy()
+        zi = r[i].copy()
+        if i > 0:
+            Si -= L[i - 1] @ O[i - 1].T
+            zi -= L[i - 1] @ z[i - 1]
+        S[i] = Si
+        z[i] = zi
+        logdet += np.linalg.slogdet(Si)[1]
+        if i + 1 < n:
+            L[i] = np.linalg.solve(Si.T, O[i].T).T
+    x = np.empty_like(r)
+    Sd = np.empty_like(D)
+    So = np.empty_like(O)
+    for i in range(n - 1, -1, -1):
+        Sinv = np.linalg.inv(S[i])
+        if i == n - 1:
+            x[i] = Sinv @ z[i]
+            Sd[i] = Sinv
+        else:
+            x[i] = Sinv @ z[i] - L[i].T @ x[i + 1]
+            So[i] = -Sd[i + 1] @ L[i]                      # (T^-1)[i+1, i]
+            Sd[i] = Sinv + L[i].T @ Sd[i + 1] @ L[i]
+        Sd[i] = 0.5 * (Sd[i] + Sd[i].T)
+    return logdet, x, Sd, So
