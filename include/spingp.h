@@ -225,6 +225,84 @@ spingp_status spingp_probe_fp64(void* scratch, size_t scratch_bytes, double* tfl
 spingp_status spingp_loglik_noalloc(const spingp_model* model, const double* t, const double* y, int64_t n,
                                     const double* theta, double* ll_out, unsigned flags, void* stream);
 
+/* ------------------------------------------------------------------------
+ * The method as the paper writes it (Sec. 2.2-3.1): the explicit block-
+ * tridiagonal posterior precision and a general symmetric BTD solver.
+ *
+ * These form Q_i^-1, whose condition number grows like (lam dt)^-(2b-2); they
+ * are exact algebra but lose about 2(b-1) log10(1 / (lam dt_min)) digits, so
+ * they are meant for well-separated times and for callers that bring their
+ * own BTD matrices.  The entry points above never form Q^-1 and stay exact
+ * for any gap, ties included.
+ *
+ * Block layout (b x b blocks, row-major, stored one after another):
+ *   D[i] = T[i][i]      for i = 0 .. n-1   (n b^2 doubles, symmetric blocks)
+ *   O[i] = T[i+1][i]    for i = 0 .. n-2   ((n-1) b^2 doubles; T[i][i+1] = O[i]^T)
+ *   vectors r, x: n b doubles, entry i*b + k.
+ * Same pointer, workspace, stream and status conventions as above; b <= 3.
+ * ------------------------------------------------------------------------ */
+
+/* Subproblems 1-3 of Sec. 3.1 for a symmetric positive-definite block-
+ * tridiagonal T (the posterior precision K~ of Eq. mean3 is one): x = T^-1 r,
+ * log det T, and, when Sdiag_out is not NULL, the block-tridiagonal part of
+ * T^-1 (its diagonal blocks Sdiag_out[i] = (T^-1)[i][i], n b^2 doubles, and
+ * sub-diagonal blocks Soff_out[i] = (T^-1)[i+1][i], (n-1) b^2 doubles;
+ * Soff_out may be NULL only when n = 1) -- the selected inverse that
+ * subproblems 2 and 4 need.  Odd-even block cyclic reduction: level l
+ * eliminates the odd-numbered nodes of level l-1 by Schur complement, the
+ * single node left is solved, and back-substitution recovers x and the
+ * selected inverse level by level (2 ceil(log2 n) + 2 kernels).  A pivot
+ * block that is not positive definite gives SPINGP_ENUMERIC.  logdet_out is
+ * one device double. */
+size_t spingp_btd_workspace_bytes(int b, int64_t n);
+spingp_status spingp_btd_solve(int b, int64_t n, const double* D, const double* O, const double* r,
+                               double* logdet_out, double* x_out, double* Sdiag_out, double* Soff_out, void* ws,
+                               size_t ws_bytes, unsigned flags, void* stream);
+int spingp_btd_launch_count(int64_t n);
+
+/* Subproblem 4 of Sec. 3.1 (Eq. comp_2; Eq. dd1 is its trace): the diagonal
+ * of S X, where S is the selected inverse from spingp_btd_solve (Sdiag, Soff)
+ * and X a symmetric block-tridiagonal matrix in the layout above (Xdiag,
+ * Xoff), together with its trace.  Only the block-tridiagonal part of S
+ * enters.  diag_out (n b doubles) may be NULL; trace_out is one device
+ * double, summed in a fixed order. */
+size_t spingp_btd_diag_product_workspace_bytes(int64_t n);
+spingp_status spingp_btd_diag_product(int b, int64_t n, const double* Sdiag, const double* Soff,
+                                      const double* Xdiag, const double* Xoff, double* diag_out,
+                                      double* trace_out, void* ws, size_t ws_bytes, unsigned flags, void* stream);
+
+/* Assembly of the posterior precision K~ = Kinv + G^T Sigma^-1 G for a single
+ * Matern component (Theorem 1 with Sec. 2.2), in the state coordinates of
+ * Eq. ss1 (z = (f, f', f'', ...)):
+ *   D_i = Q_{i-1}^-1 + A_i^T Q_i^-1 A_i + H^T H / sigma_n^2   (Q_{-1} = Pinf; no
+ *         A-term for the last step),
+ *   O_i = -Q_i^-1 A_i,   r_i = H^T y_i / sigma_n^2,
+ * and logdet_kinv_out = log det Kinv = -log det Pinf - sum_i log det Q_i, the
+ * term the determinant lemma (Eq. det_1) needs.  Times must be strictly
+ * increasing (a tie makes Q_i = 0 and gives SPINGP_ENUMERIC); NaN inputs give
+ * SPINGP_ENONFINITE. */
+size_t spingp_assemble_workspace_bytes(int64_t n);
+spingp_status spingp_assemble(const spingp_model* model, const double* t, const double* y, int64_t n,
+                              const double* theta, double* D_out, double* O_out, double* r_out,
+                              double* logdet_kinv_out, void* ws, size_t ws_bytes, unsigned flags, void* stream);
+
+/* The whole computation the paper's way, for a single Matern component:
+ * assembly, block cyclic reduction, then
+ *   ll = -1/2 (y^T y / sigma_n^2 - r^T x) - 1/2 (log det K~ - log det Kinv
+ *        + n log sigma_n^2) - n/2 log 2 pi                 (Eqs. ml2, det_1, mean3)
+ * with x = K~^-1 r.  what = SPINGP_WS_GRAD adds the gradient (grad_out[3],
+ * theta order) from Eq. dd1: for a covariance parameter,
+ *   d ll = -1/2 x^T dK~ x - 1/2 tr(K~^-1 dK~) + 1/2 d log det Kinv,
+ * where dK~ is block-tridiagonal, so the trace needs only the selected
+ * inverse (subproblem 4).  what = SPINGP_WS_POSTERIOR writes the latent
+ * posterior mean H x_i and variance H (K~^-1)_ii H^T (Eqs. mean3, k3).  Same
+ * input rules as spingp_assemble. */
+size_t spingp_literal_workspace_bytes(const spingp_model* model, int64_t n, spingp_ws_kind what);
+spingp_status spingp_literal(const spingp_model* model, spingp_ws_kind what, const double* t, const double* y,
+                             int64_t n, const double* theta, double* ll_out, double* grad_out, double* mean_out,
+                             double* var_out, void* ws, size_t ws_bytes, unsigned flags, void* stream);
+int spingp_literal_launch_count(int64_t n);
+
 /* Synchronise the stream and return the device status recorded in ws by the
  * last call that used it (SPINGP_OK if none). */
 spingp_status spingp_ws_status(void* ws, void* stream);

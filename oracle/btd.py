@@ -131,3 +131,30 @@ def thomas(D, O, r):
             Sd[i] = Sinv + L[i].T @ Sd[i + 1] @ L[i]
         Sd[i] = 0.5 * (Sd[i] + Sd[i].T)
     return logdet, x, Sd, So
+
+
+def dense_of(D, O):
+    """The dense symmetric matrix with diagonal blocks D[i] and sub-diagonal
+    blocks O[i] = T[i+1, i] (T[i, i+1] = O[i]^T)."""
+    D = np.asarray(D, dtype=np.float64)
+    O = np.asarray(O, dtype=np.float64)
+    n, b, _ = D.shape
+    T = np.zeros((n * b, n * b))
+    for i in range(n):
+        T[i * b:(i + 1) * b, i * b:(i + 1) * b] = D[i]
+        if i + 1 < n:
+            T[(i + 1) * b:(i + 2) * b, i * b:(i + 1) * b] = O[i]
+            T[i * b:(i + 1) * b, (i + 1) * b:(i + 2) * b] = O[i].T
+    return T
+
+
+def diag_product(D, O, Xd, Xo):
+    """Subproblem 4 (Sec. 3.1, Eq. comp_2) by its definition: the diagonal of
+    T^-1 X for a symmetric BTD matrix T (D, O) and a symmetric BTD right-hand
+    side X (Xd, Xo), with the dense inverse (small n only).  Returns
+    (diag as (n, b), trace)."""
+    T = dense_of(D, O)
+    X = dense_of(Xd, Xo)
+    d = np.diag(np.linalg.solve(T, X)).copy()
+    n, b = np.asarray(D).shape[:2]
+    return d.reshape(n, b), float(np.sum(d))

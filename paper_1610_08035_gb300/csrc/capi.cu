@@ -355,6 +355,92 @@ spingp_status spingp_probe_fp64(void* scratch, size_t bytes, double* tflops_out,
     return spg::probe_fp64(scratch, bytes, tflops_out, (cudaStream_t)stream) ? SPINGP_ECUDA : SPINGP_OK;
 }
 
+// ---------------------------------------------------------------- the method as written (Sec. 2.2, 3.1)
+
+static bool ws_ok(const void* ws, size_t have, size_t need) {
+    return ws && ((uintptr_t)ws & 255u) == 0 && have >= need;
+}
+static spingp_status finish(int rc, void* ws, unsigned flags, void* stream) {
+    if (rc) return SPINGP_ECUDA;
+    if (flags & SPINGP_SYNC) return spingp_ws_status(ws, stream);
+    return SPINGP_OK;
+}
+
+size_t spingp_btd_workspace_bytes(int b, int64_t n) {
+    if (b < 1 || b > 3 || n < 1) return 0;
+    return spg::btd_ws_bytes(b, n);
+}
+
+spingp_status spingp_btd_solve(int b, int64_t n, const double* D, const double* O, const double* r,
+                               double* logdet_out, double* x_out, double* Sdiag_out, double* Soff_out, void* ws,
+                               size_t ws_bytes, unsigned flags, void* stream) {
+    if (b < 1 || b > 3 || n < 1 || !D || !r || !logdet_out || !x_out) return SPINGP_EINVAL;
+    if (n > 1 && !O) return SPINGP_EINVAL;
+    if (!Sdiag_out && Soff_out) return SPINGP_EINVAL;          // the selected inverse is wanted whole or not at all
+    if (Sdiag_out && n > 1 && !Soff_out) return SPINGP_EINVAL;
+    if (!ws_ok(ws, ws_bytes, spg::btd_ws_bytes(b, n))) return SPINGP_EINVAL;
+    spingp_status st = prepare_device();
+    if (st != SPINGP_OK) return st;
+    // at n = 1 there is no off-diagonal block: a dummy pointer keeps the
+    // selected inverse switched on without being written
+    double* so = (n == 1 && Sdiag_out) ? Sdiag_out : Soff_out;
+    return finish(spg::btd_solve(b, n, D, O, r, logdet_out, x_out, Sdiag_out, so, ws, (cudaStream_t)stream), ws,
+                  flags, stream);
+}
+
+size_t spingp_btd_diag_product_workspace_bytes(int64_t n) { return n < 1 ? 0 : spg::diagprod_ws_bytes(n); }
+
+spingp_status spingp_btd_diag_product(int b, int64_t n, const double* Sdiag, const double* Soff,
+                                      const double* Xdiag, const double* Xoff, double* diag_out,
+                                      double* trace_out, void* ws, size_t ws_bytes, unsigned flags, void* stream) {
+    if (b < 1 || b > 3 || n < 1 || !Sdiag || !Xdiag || !trace_out) return SPINGP_EINVAL;
+    if (n > 1 && (!Soff || !Xoff)) return SPINGP_EINVAL;
+    if (!ws_ok(ws, ws_bytes, spg::diagprod_ws_bytes(n))) return SPINGP_EINVAL;
+    spingp_status st = prepare_device();
+    if (st != SPINGP_OK) return st;
+    return finish(spg::btd_diagprod(b, n, Sdiag, Soff, Xdiag, Xoff, diag_out, trace_out, ws, (cudaStream_t)stream),
+                  ws, flags, stream);
+}
+
+size_t spingp_assemble_workspace_bytes(int64_t n) { return n < 1 ? 0 : spg::assemble_ws_bytes(n); }
+
+spingp_status spingp_assemble(const spingp_model* m, const double* t, const double* y, int64_t n,
+                              const double* theta, double* D_out, double* O_out, double* r_out,
+                              double* logdet_kinv_out, void* ws, size_t ws_bytes, unsigned flags, void* stream) {
+    if (!m || !t || !y || !theta || n < 1 || !D_out || !r_out || !logdet_kinv_out) return SPINGP_EINVAL;
+    if (n > 1 && !O_out) return SPINGP_EINVAL;
+    if (!single_matern(m)) return SPINGP_EUNSUPPORTED;
+    if (!ws_ok(ws, ws_bytes, spg::assemble_ws_bytes(n))) return SPINGP_EINVAL;
+    spingp_status st = prepare_device();
+    if (st != SPINGP_OK) return st;
+    return finish(spg::assemble(m->b, t, y, n, theta, D_out, O_out, r_out, logdet_kinv_out, ws, (cudaStream_t)stream),
+                  ws, flags, stream);
+}
+
+size_t spingp_literal_workspace_bytes(const spingp_model* m, int64_t n, spingp_ws_kind what) {
+    if (!m || n < 1 || !single_matern(m)) return 0;
+    return spg::literal_ws_bytes(m->b, n, ws_mode(what));
+}
+
+spingp_status spingp_literal(const spingp_model* m, spingp_ws_kind what, const double* t, const double* y,
+                             int64_t n, const double* theta, double* ll_out, double* grad_out, double* mean_out,
+                             double* var_out, void* ws, size_t ws_bytes, unsigned flags, void* stream) {
+    if (!m || !t || !y || !theta || n < 1 || !ll_out) return SPINGP_EINVAL;
+    const int mode = ws_mode(what);
+    if (mode == spg::MODE_GRAD && !grad_out) return SPINGP_EINVAL;
+    if (mode == spg::MODE_POSTERIOR && (!mean_out || !var_out)) return SPINGP_EINVAL;
+    if (!single_matern(m)) return SPINGP_EUNSUPPORTED;
+    if (!ws_ok(ws, ws_bytes, spg::literal_ws_bytes(m->b, n, mode))) return SPINGP_EINVAL;
+    spingp_status st = prepare_device();
+    if (st != SPINGP_OK) return st;
+    return finish(spg::literal_run(m->b, mode, t, y, n, theta, ll_out, grad_out, mean_out, var_out, ws,
+                                   (cudaStream_t)stream),
+                  ws, flags, stream);
+}
+
+int spingp_literal_launch_count(int64_t n) { return n < 1 ? -1 : (int)spg::literal_launch_count(n); }
+int spingp_btd_launch_count(int64_t n) { return n < 1 ? -1 : (int)spg::btd_launch_count(n); }
+
 spingp_status spingp_ws_status(void* ws, void* stream) {
     if (!ws) return SPINGP_EINVAL;
     int bits = 0;

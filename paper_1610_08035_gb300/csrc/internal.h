@@ -41,6 +41,23 @@ int matern_run_batched(int b, int mode, const int64_t* offsets, int64_t nseries,
                        const double* y, int64_t L, const double* theta, double* ll_out, double* grad_out,
                        double* mean_out, double* var_out, void* ws, cudaStream_t st, cudaEvent_t* ev, int missing);
 
+// the paper's method as written (btd.cu): explicit K~ blocks, block cyclic
+// reduction with selected inverse, subproblem 4, and the composed literal path
+size_t btd_ws_bytes(int b, int64_t n);
+int btd_solve(int b, int64_t n, const double* D, const double* O, const double* r, double* logdet, double* x,
+              double* Sd, double* So, void* ws, cudaStream_t st);
+int64_t btd_launch_count(int64_t n);
+size_t diagprod_ws_bytes(int64_t n);
+int btd_diagprod(int b, int64_t n, const double* Sd, const double* So, const double* Xd, const double* Xo,
+                 double* diag, double* trace, void* ws, cudaStream_t st);
+size_t assemble_ws_bytes(int64_t n);
+int assemble(int b, const double* t, const double* y, int64_t n, const double* theta, double* D, double* O,
+             double* r, double* logdet_kinv, void* ws, cudaStream_t st);
+size_t literal_ws_bytes(int b, int64_t n, int mode);
+int literal_run(int b, int mode, const double* t, const double* y, int64_t n, const double* theta, double* ll,
+                double* grad, double* mean, double* var, void* ws, cudaStream_t st);
+int64_t literal_launch_count(int64_t n);
+
 size_t probe_fp64_bytes();
 int probe_fp64(void* scratch, size_t bytes, double* tflops, cudaStream_t st);
 

@@ -27,7 +27,10 @@ EXPORTS = ("spingp_model_create", "spingp_model_destroy", "spingp_num_params", "
            "spingp_grad_batched", "spingp_posterior_batched", "spingp_launch_count",
            "spingp_launch_count_batched", "spingp_profile_enable",
            "spingp_profile_read", "spingp_probe_fp64_bytes", "spingp_probe_fp64", "spingp_loglik_noalloc",
-           "spingp_ws_status", "spingp_status_str")
+           "spingp_btd_workspace_bytes", "spingp_btd_solve", "spingp_btd_launch_count",
+           "spingp_btd_diag_product_workspace_bytes", "spingp_btd_diag_product",
+           "spingp_assemble_workspace_bytes", "spingp_assemble", "spingp_literal_workspace_bytes",
+           "spingp_literal", "spingp_literal_launch_count", "spingp_ws_status", "spingp_status_str")
 STAGES = ("elimination", "reduction", "chunk_pass", "final_reduction")
 
 _lib = None
@@ -79,6 +82,20 @@ def load():
     lib.spingp_probe_fp64_bytes.restype = sz
     lib.spingp_probe_fp64.argtypes = [vp, sz, ctypes.POINTER(ctypes.c_double), vp]
     lib.spingp_loglik_noalloc.argtypes = [vp, dp, dp, i64, dp, dp, u32, vp]
+    lib.spingp_btd_workspace_bytes.argtypes = [ctypes.c_int, i64]
+    lib.spingp_btd_workspace_bytes.restype = sz
+    lib.spingp_btd_solve.argtypes = [ctypes.c_int, i64, dp, dp, dp, dp, dp, dp, dp, vp, sz, u32, vp]
+    lib.spingp_btd_launch_count.argtypes = [i64]
+    lib.spingp_btd_diag_product_workspace_bytes.argtypes = [i64]
+    lib.spingp_btd_diag_product_workspace_bytes.restype = sz
+    lib.spingp_btd_diag_product.argtypes = [ctypes.c_int, i64, dp, dp, dp, dp, dp, dp, vp, sz, u32, vp]
+    lib.spingp_assemble_workspace_bytes.argtypes = [i64]
+    lib.spingp_assemble_workspace_bytes.restype = sz
+    lib.spingp_assemble.argtypes = [vp, dp, dp, i64, dp, dp, dp, dp, dp, vp, sz, u32, vp]
+    lib.spingp_literal_workspace_bytes.argtypes = [vp, i64, ctypes.c_int]
+    lib.spingp_literal_workspace_bytes.restype = sz
+    lib.spingp_literal.argtypes = [vp, ctypes.c_int, dp, dp, i64, dp, dp, dp, dp, dp, vp, sz, u32, vp]
+    lib.spingp_literal_launch_count.argtypes = [i64]
     lib.spingp_ws_status.argtypes = [vp, vp]
     lib.spingp_status_str.argtypes = [ctypes.c_int]
     lib.spingp_status_str.restype = ctypes.c_char_p
@@ -238,6 +255,54 @@ def spingp_loglik_noalloc(h, t, y, n, theta, ll_out, flags, stream=None):
                                         stream if stream is not None else _stream())
 
 
+def spingp_btd_workspace_bytes(b, n):
+    return load().spingp_btd_workspace_bytes(int(b), int(n))
+
+
+def spingp_btd_solve(b, n, D, O, r, logdet_out, x_out, Sdiag_out, Soff_out, ws, ws_bytes, flags, stream=None):
+    return load().spingp_btd_solve(int(b), int(n), _ptr(D), _ptr(O), _ptr(r), _ptr(logdet_out), _ptr(x_out),
+                                   _ptr(Sdiag_out), _ptr(Soff_out), _ptr(ws), ws_bytes, flags,
+                                   stream if stream is not None else _stream())
+
+
+def spingp_btd_launch_count(n):
+    return load().spingp_btd_launch_count(int(n))
+
+
+def spingp_btd_diag_product_workspace_bytes(n):
+    return load().spingp_btd_diag_product_workspace_bytes(int(n))
+
+
+def spingp_btd_diag_product(b, n, Sdiag, Soff, Xdiag, Xoff, diag_out, trace_out, ws, ws_bytes, flags, stream=None):
+    return load().spingp_btd_diag_product(int(b), int(n), _ptr(Sdiag), _ptr(Soff), _ptr(Xdiag), _ptr(Xoff),
+                                          _ptr(diag_out), _ptr(trace_out), _ptr(ws), ws_bytes, flags,
+                                          stream if stream is not None else _stream())
+
+
+def spingp_assemble_workspace_bytes(n):
+    return load().spingp_assemble_workspace_bytes(int(n))
+
+
+def spingp_assemble(h, t, y, n, theta, D_out, O_out, r_out, logdet_kinv_out, ws, ws_bytes, flags, stream=None):
+    return load().spingp_assemble(h, _ptr(t), _ptr(y), int(n), _ptr(theta), _ptr(D_out), _ptr(O_out), _ptr(r_out),
+                                  _ptr(logdet_kinv_out), _ptr(ws), ws_bytes, flags,
+                                  stream if stream is not None else _stream())
+
+
+def spingp_literal_workspace_bytes(h, n, what):
+    return load().spingp_literal_workspace_bytes(h, int(n), int(what))
+
+
+def spingp_literal(h, what, t, y, n, theta, ll_out, grad_out, mean_out, var_out, ws, ws_bytes, flags, stream=None):
+    return load().spingp_literal(h, int(what), _ptr(t), _ptr(y), int(n), _ptr(theta), _ptr(ll_out),
+                                 _ptr(grad_out), _ptr(mean_out), _ptr(var_out), _ptr(ws), ws_bytes, flags,
+                                 stream if stream is not None else _stream())
+
+
+def spingp_literal_launch_count(n):
+    return load().spingp_literal_launch_count(int(n))
+
+
 def spingp_ws_status(ws, stream=None):
     return load().spingp_ws_status(_ptr(ws), stream if stream is not None else _stream())
 
@@ -347,6 +412,94 @@ class Model:
         where[order] = torch.arange(order.numel(), device=order.device)
         idx = where[t.numel():]
         return mean[idx], var[idx]
+
+
+    # ------------------------------------------------------------ the method as written (Sec. 2.2-3.1)
+
+    def _scratch(self, nbytes, device, name):
+        if nbytes == 0:
+            raise SpinGPError(EUNSUPPORTED, name)
+        return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+    def assemble(self, t, y, theta, sync=True):
+        """The explicit blocks of the posterior precision K~ (Theorem 1, Sec.
+        2.2): D (n, b, b), O (n-1, b, b) with O[i] = K~[i+1, i], r (n, b), and
+        log det Kinv.  Single Matern components only."""
+        n = self._args(t, y, theta)
+        b = self.state_dim
+        dev = t.device
+        D = torch.empty(n, b, b, dtype=torch.float64, device=dev)
+        O = torch.empty(max(n - 1, 0), b, b, dtype=torch.float64, device=dev)
+        r = torch.empty(n, b, dtype=torch.float64, device=dev)
+        ldk = torch.empty(1, dtype=torch.float64, device=dev)
+        ws = self._scratch(spingp_assemble_workspace_bytes(n), dev, "spingp_assemble")
+        _check(spingp_assemble(self.h, t, y, n, theta, D, O if n > 1 else None, r, ldk, ws, ws.numel(),
+                               SYNC if sync else 0), "spingp_assemble")
+        return D, O, r, ldk
+
+    def literal(self, t, y, theta, what=WS_LOGLIK, sync=True):
+        """Log-likelihood (and gradient, or posterior mean and variance) by
+        assembling K~ and running block cyclic reduction on it.  Returns ll,
+        (ll, grad) or (mean, var, ll) as what is WS_LOGLIK, WS_GRAD or
+        WS_POSTERIOR."""
+        n = self._args(t, y, theta)
+        dev = t.device
+        ll = torch.empty(1, dtype=torch.float64, device=dev)
+        g = torch.empty(self.num_params, dtype=torch.float64, device=dev) if what == WS_GRAD else None
+        mean = torch.empty(n, dtype=torch.float64, device=dev) if what == WS_POSTERIOR else None
+        var = torch.empty(n, dtype=torch.float64, device=dev) if what == WS_POSTERIOR else None
+        ws = self._scratch(spingp_literal_workspace_bytes(self.h, n, what), dev, "spingp_literal")
+        _check(spingp_literal(self.h, what, t, y, n, theta, ll, g, mean, var, ws, ws.numel(), SYNC if sync else 0),
+               "spingp_literal")
+        if what == WS_GRAD:
+            return ll, g
+        if what == WS_POSTERIOR:
+            return mean, var, ll
+        return ll
+
+
+def btd_solve(D, O, r, selected=True, sync=True):
+    """Subproblems 1-3 (Sec. 3.1) for a symmetric positive-definite block-
+    tridiagonal matrix with diagonal blocks D (n, b, b) and sub-diagonal blocks
+    O (n-1, b, b), O[i] = T[i+1, i]: returns (logdet, x, Sdiag, Soff) with
+    x = T^-1 r and, if selected, the block-tridiagonal part of T^-1."""
+    _dev_f64(D, "D"); _dev_f64(r, "r")
+    n, b = D.shape[0], D.shape[1]
+    if D.shape != (n, b, b) or r.shape != (n, b) or not 1 <= b <= 3:
+        raise ValueError("D must be (n, b, b) and r (n, b) with b <= 3")
+    if n > 1:
+        _dev_f64(O, "O")
+        if O.shape != (n - 1, b, b):
+            raise ValueError("O must be (n-1, b, b)")
+    dev = D.device
+    ld = torch.empty(1, dtype=torch.float64, device=dev)
+    x = torch.empty(n, b, dtype=torch.float64, device=dev)
+    Sd = torch.empty(n, b, b, dtype=torch.float64, device=dev) if selected else None
+    So = torch.empty(max(n - 1, 0), b, b, dtype=torch.float64, device=dev) if selected else None
+    nbytes = spingp_btd_workspace_bytes(b, n)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    _check(spingp_btd_solve(b, n, D, O if n > 1 else None, r, ld, x, Sd, So if (selected and n > 1) else None, ws,
+                            nbytes, SYNC if sync else 0), "spingp_btd_solve")
+    return ld, x, Sd, So
+
+
+def btd_diag_product(Sd, So, Xd, Xo, sync=True):
+    """Subproblem 4 (Sec. 3.1): the diagonal of S X and its trace, for the
+    selected inverse S (Sd, So) and a symmetric block-tridiagonal X (Xd, Xo)."""
+    _dev_f64(Sd, "Sdiag"); _dev_f64(Xd, "Xdiag")
+    n, b = Sd.shape[0], Sd.shape[1]
+    if Xd.shape != Sd.shape:
+        raise ValueError("Xdiag must match Sdiag")
+    if n > 1:
+        _dev_f64(So, "Soff"); _dev_f64(Xo, "Xoff")
+    dev = Sd.device
+    diag = torch.empty(n, b, dtype=torch.float64, device=dev)
+    tr = torch.empty(1, dtype=torch.float64, device=dev)
+    nbytes = spingp_btd_diag_product_workspace_bytes(n)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    _check(spingp_btd_diag_product(b, n, Sd, So if n > 1 else None, Xd, Xo if n > 1 else None, diag, tr, ws, nbytes,
+                                   SYNC if sync else 0), "spingp_btd_diag_product")
+    return diag, tr
 
 
 class Batch:

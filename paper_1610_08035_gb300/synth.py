@@ -14,7 +14,12 @@ Sec. 4.2, "two sinusoids immersed into Gaussian noise"):
   periods p_1 = 7.3 l and p_2 = 2.9 l tied to the lengthscale l of the
   workload and random phases, so the signal varies on the kernel's scale;
 * batches: lengths round(exp(U(log lo, log hi))), per-series lengthscale,
-  signal and noise variance log-uniform on the stated ranges.
+  signal and noise variance log-uniform on the stated ranges;
+* well-separated times (for the method as written, which forms Q^-1):
+  dt_i ~ Uniform(lo, hi) times the lengthscale;
+* general block-tridiagonal inputs: T = B B^T + ridge I for a random lower
+  block-bidiagonal B (diagonal blocks N(0, 1) + 2 I, sub-diagonal blocks
+  N(0, 1)), returned as its blocks without forming T.
 """
 from dataclasses import dataclass, field
 
@@ -95,3 +100,23 @@ def batched(n_series=4096, lo=256, hi=65536, mean_dt=0.01, seed=3, spec="matern5
     thetas = np.stack([ell, sf2, sn2], axis=1)
     return Series("batched_%d" % n_series, [spec], thetas.reshape(-1).copy(), t, y,
                   extra=dict(offsets=offsets, thetas=thetas))
+
+
+def separated_times(n, ell, rng, lo=0.3, hi=0.6):
+    d = rng.uniform(lo * ell, hi * ell, n)
+    d[0] = 0.0
+    return np.cumsum(d)
+
+
+def random_spd_btd(n, b, seed, ridge=0.1):
+    """Blocks of a random symmetric positive-definite block-tridiagonal
+    matrix T = B B^T + ridge I: D (n, b, b) with D[i] = T[i, i], O (n-1, b, b)
+    with O[i] = T[i+1, i], and a right-hand side r (n, b)."""
+    rng = np.random.default_rng(seed)
+    Bd = rng.standard_normal((n, b, b)) + 2.0 * np.eye(b)
+    Bs = rng.standard_normal((max(n - 1, 0), b, b))     # B[i+1, i]
+    D = Bd @ np.transpose(Bd, (0, 2, 1)) + ridge * np.eye(b)
+    D[1:] += Bs @ np.transpose(Bs, (0, 2, 1))
+    O = Bs @ np.transpose(Bd[:-1], (0, 2, 1))            # B[i+1,i] B[i,i]^T
+    r = rng.standard_normal((n, b))
+    return D, O, r

@@ -447,3 +447,29 @@ def test_literal_method_on_the_assembled_precision(spec, theta):
     assert np.max(np.abs(x - sm["ms"])) <= 1e-9 * max(1.0, np.max(np.abs(x)))
     assert np.max(np.abs(Sd - sm["Ps"])) <= 1e-9 * np.max(np.abs(sm["Ps"]))
     assert np.max(np.abs(So - sm["Pc"])) <= 1e-9 * np.max(np.abs(sm["Ps"]))
+
+
+def test_diag_product_is_the_log_det_derivative():
+    """Subproblem 4's trace is Jacobi's formula d/de log det(T + e X) =
+    tr(T^-1 X) (Eq. dd1): checked by a central difference of log det on a
+    random SPD BTD T and a random symmetric BTD X; X = T gives the identity."""
+    rng = np.random.default_rng(5)
+    for b, n in ((1, 9), (2, 7), (3, 6)):
+        D, O = btd.blocks_of(_random_spd_btd(n, b, 100 + b), b)
+        Xd = rng.standard_normal((n, b, b))
+        Xd = Xd + np.transpose(Xd, (0, 2, 1))
+        Xo = rng.standard_normal((n - 1, b, b))
+        d, tr = btd.diag_product(D, O, Xd, Xo)
+        h = 1e-5
+        lp = np.linalg.slogdet(btd.dense_of(D + h * Xd, O + h * Xo))[1]
+        lm = np.linalg.slogdet(btd.dense_of(D - h * Xd, O - h * Xo))[1]
+        assert abs(tr - (lp - lm) / (2 * h)) <= 1e-7 * max(1.0, abs(tr))
+        d1, tr1 = btd.diag_product(D, O, D, O)
+        assert np.allclose(d1, 1.0, atol=1e-12) and abs(tr1 - n * b) <= 1e-11
+        # only the block-tridiagonal part of T^-1 enters (Sec. 3.1): the same
+        # diagonal from the selected inverse of the sequential algorithm
+        _, _, Sd, So = btd.thomas(D, O, np.zeros((n, b)))
+        d2 = np.einsum("ipq,iqp->ip", Sd, Xd)
+        d2[1:] += np.einsum("ipq,ipq->ip", So, Xo)
+        d2[:-1] += np.einsum("iqp,iqp->ip", So, Xo)
+        assert np.allclose(d2, d, rtol=1e-11, atol=1e-12)
