@@ -226,6 +226,40 @@ spingp_status spingp_loglik_noalloc(const spingp_model* model, const double* t, 
                                     const double* theta, double* ll_out, unsigned flags, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Hyperparameter fitting (Sec. 4.3): the paper maximises the marginal
+ * likelihood by scaled conjugate gradients (Moller 1993).
+ *
+ * Each series is optimised on its own, over log-parameters w = log(theta)
+ * with objective -ll(exp(w)).  Every iteration evaluates the gradient of all
+ * series twice (a curvature probe at w + sigma p, sigma = 1e-4 / |p|, and the
+ * trial point w + alpha p); the algorithm's scalar decisions (the
+ * Levenberg-Marquardt scale lambda, starting at 1e-6 and kept in
+ * [1e-15, 1e100], the acceptance ratio, conjugate directions with a restart
+ * every P iterations) run in device kernels between the evaluations, so a
+ * call is a fixed sequence of launches with no host synchronisation (without
+ * SPINGP_SYNC it can be captured into a CUDA graph).  A trial point with a
+ * non-finite objective or gradient is rejected.  A series stops early once
+ * max |d(-ll)/dw| <= tol, or when its search direction vanishes.
+ *
+ * theta_inout: device, P entries (n_series x P for the batched form) --
+ * the starting point (every entry finite and > 0, else SPINGP_EINVAL), and on
+ * return the last accepted point.  ll_out (1 or n_series doubles) and
+ * grad_out (d ll / d theta at the returned point, P or n_series x P doubles)
+ * may be NULL.  iterations >= 0.  The workspace holds a gradient workspace
+ * plus the optimiser state; its status word reports the final evaluation.
+ * The batched form supports the models spingp_grad_batched supports.
+ * ------------------------------------------------------------------------ */
+size_t spingp_optimize_workspace_bytes(const spingp_model* model, int64_t n);
+spingp_status spingp_optimize(const spingp_model* model, const double* t, const double* y, int64_t n,
+                              double* theta_inout, int iterations, double tol, double* ll_out, double* grad_out,
+                              void* ws, size_t ws_bytes, unsigned flags, void* stream);
+size_t spingp_optimize_workspace_bytes_batched(const spingp_model* model, int64_t n_series, int64_t n_total);
+spingp_status spingp_optimize_batched(const spingp_model* model, const int64_t* offsets, int64_t n_series,
+                                      int64_t n_total, const double* t, const double* y, double* theta_inout,
+                                      int iterations, double tol, double* ll_out, double* grad_out, void* ws,
+                                      size_t ws_bytes, unsigned flags, void* stream);
+
+/* ------------------------------------------------------------------------
  * The method as the paper writes it (Sec. 2.2-3.1): the explicit block-
  * tridiagonal posterior precision and a general symmetric BTD solver.
  *

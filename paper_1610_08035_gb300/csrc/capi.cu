@@ -355,6 +355,88 @@ spingp_status spingp_probe_fp64(void* scratch, size_t bytes, double* tflops_out,
     return spg::probe_fp64(scratch, bytes, tflops_out, (cudaStream_t)stream) ? SPINGP_ECUDA : SPINGP_OK;
 }
 
+// ---------------------------------------------------------------- hyperparameter fitting (Sec. 4.3)
+
+static size_t align256c(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static size_t optimize_inner_bytes(const spingp_model* m, bool batched, int64_t S, int64_t n) {
+    return batched ? spingp_workspace_bytes_batched(m, S, n, SPINGP_WS_GRAD)
+                   : spingp_workspace_bytes(m, n, SPINGP_WS_GRAD);
+}
+
+static spingp_status optimize(const spingp_model* m, bool batched, const int64_t* offsets, int64_t S, int64_t n,
+                              const double* t, const double* y, double* theta, int iters, double tol,
+                              double* ll_out, double* grad_out, void* ws, size_t ws_bytes, unsigned flags,
+                              void* stream) {
+    if (!m || !theta || !ws || iters < 0 || !(tol >= 0.0) || S < 1) return SPINGP_EINVAL;
+    if (((uintptr_t)ws & 255u) != 0) return SPINGP_EINVAL;
+    const size_t inner = optimize_inner_bytes(m, batched, S, n);
+    if (inner == 0) return batched ? SPINGP_EUNSUPPORTED : SPINGP_EINVAL;
+    const size_t off = align256c(inner);
+    if (ws_bytes < off + spg::scg_state_bytes(S, m->P)) return SPINGP_EINVAL;
+    spingp_status st = prepare_device();
+    if (st != SPINGP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const spg::ScgState sc = spg::scg_bind((char*)ws + off, S, m->P);
+    const unsigned inner_flags = flags & ~SPINGP_SYNC;
+    auto eval = [&]() -> spingp_status {
+        return batched ? run_batched(m, spg::MODE_GRAD, offsets, S, n, t, y, sc.theta_eval, sc.ll_eval, sc.grad_eval,
+                                     NULL, NULL, ws, inner, inner_flags, stream)
+                       : run(m, spg::MODE_GRAD, t, y, n, sc.theta_eval, sc.ll_eval, sc.grad_eval, NULL, NULL, ws,
+                             inner, inner_flags, stream);
+    };
+    auto kern = [&](int what, int k) {
+        return spg::scg_launch(what, sc, s, k, tol, theta, theta, ll_out, grad_out, (int*)ws) ? SPINGP_ECUDA
+                                                                                              : SPINGP_OK;
+    };
+#define SPG_TRY(x) do { const spingp_status e_ = (x); if (e_ != SPINGP_OK) return e_; } while (0)
+    SPG_TRY(kern(spg::SCG_K_INIT, 0));
+    SPG_TRY(eval());
+    SPG_TRY(kern(spg::SCG_K_START, 0));
+    for (int k = 1; k <= iters; ++k) {
+        SPG_TRY(kern(spg::SCG_K_A, k));
+        SPG_TRY(eval());
+        SPG_TRY(kern(spg::SCG_K_B, k));
+        SPG_TRY(eval());
+        SPG_TRY(kern(spg::SCG_K_C, k));
+    }
+    SPG_TRY(kern(spg::SCG_K_FINAL, 0));
+    SPG_TRY(eval());
+    SPG_TRY(kern(spg::SCG_K_OUT, 0));
+#undef SPG_TRY
+    if (flags & SPINGP_SYNC) return spingp_ws_status(ws, stream);
+    return SPINGP_OK;
+}
+
+size_t spingp_optimize_workspace_bytes(const spingp_model* m, int64_t n) {
+    if (!m || n < 1) return 0;
+    const size_t inner = optimize_inner_bytes(m, false, 1, n);
+    return inner ? align256c(inner) + spg::scg_state_bytes(1, m->P) : 0;
+}
+
+spingp_status spingp_optimize(const spingp_model* m, const double* t, const double* y, int64_t n,
+                              double* theta_inout, int iterations, double tol, double* ll_out, double* grad_out,
+                              void* ws, size_t ws_bytes, unsigned flags, void* stream) {
+    if (!t || !y || n < 1) return SPINGP_EINVAL;
+    return optimize(m, false, NULL, 1, n, t, y, theta_inout, iterations, tol, ll_out, grad_out, ws, ws_bytes, flags,
+                    stream);
+}
+
+size_t spingp_optimize_workspace_bytes_batched(const spingp_model* m, int64_t n_series, int64_t n_total) {
+    if (!m || n_series < 1 || n_total < 0) return 0;
+    const size_t inner = optimize_inner_bytes(m, true, n_series, n_total);
+    return inner ? align256c(inner) + spg::scg_state_bytes(n_series, m->P) : 0;
+}
+
+spingp_status spingp_optimize_batched(const spingp_model* m, const int64_t* offsets, int64_t n_series,
+                                      int64_t n_total, const double* t, const double* y, double* theta_inout,
+                                      int iterations, double tol, double* ll_out, double* grad_out, void* ws,
+                                      size_t ws_bytes, unsigned flags, void* stream) {
+    if (!offsets) return SPINGP_EINVAL;
+    return optimize(m, true, offsets, n_series, n_total, t, y, theta_inout, iterations, tol, ll_out, grad_out, ws,
+                    ws_bytes, flags, stream);
+}
+
 // ---------------------------------------------------------------- the method as written (Sec. 2.2, 3.1)
 
 static bool ws_ok(const void* ws, size_t have, size_t need) {

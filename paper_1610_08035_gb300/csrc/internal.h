@@ -58,6 +58,23 @@ int literal_run(int b, int mode, const double* t, const double* y, int64_t n, co
                 double* grad, double* mean, double* var, void* ws, cudaStream_t st);
 int64_t literal_launch_count(int64_t n);
 
+// scaled conjugate gradients over a batch of series (optim.cu): the state of
+// every series, bound to caller workspace, and its evaluation buffers
+struct ScgState {
+    int64_t S;
+    int P;
+    double *w, *r, *p, *s, *g;                                   // S x P
+    double *f, *lam, *lambar, *delta, *sigma, *mu, *pp, *alpha;  // S
+    int* flags;                                                  // S
+    double *theta_eval, *grad_eval;                              // S x P: where the next gradient is taken
+    double* ll_eval;                                             // S
+};
+enum { SCG_K_INIT, SCG_K_START, SCG_K_A, SCG_K_B, SCG_K_C, SCG_K_FINAL, SCG_K_OUT };
+size_t scg_state_bytes(int64_t S, int P);
+ScgState scg_bind(void* base, int64_t S, int P);
+int scg_launch(int what, const ScgState& st, cudaStream_t s, int k, double tol, const double* theta0,
+               double* theta_out, double* ll_out, double* grad_out, int* status);
+
 size_t probe_fp64_bytes();
 int probe_fp64(void* scratch, size_t bytes, double* tflops, cudaStream_t st);
 

@@ -30,7 +30,9 @@ EXPORTS = ("spingp_model_create", "spingp_model_destroy", "spingp_num_params", "
            "spingp_btd_workspace_bytes", "spingp_btd_solve", "spingp_btd_launch_count",
            "spingp_btd_diag_product_workspace_bytes", "spingp_btd_diag_product",
            "spingp_assemble_workspace_bytes", "spingp_assemble", "spingp_literal_workspace_bytes",
-           "spingp_literal", "spingp_literal_launch_count", "spingp_ws_status", "spingp_status_str")
+           "spingp_literal", "spingp_literal_launch_count", "spingp_optimize_workspace_bytes", "spingp_optimize",
+           "spingp_optimize_workspace_bytes_batched", "spingp_optimize_batched", "spingp_ws_status",
+           "spingp_status_str")
 STAGES = ("elimination", "reduction", "chunk_pass", "final_reduction")
 
 _lib = None
@@ -96,6 +98,13 @@ def load():
     lib.spingp_literal_workspace_bytes.restype = sz
     lib.spingp_literal.argtypes = [vp, ctypes.c_int, dp, dp, i64, dp, dp, dp, dp, dp, vp, sz, u32, vp]
     lib.spingp_literal_launch_count.argtypes = [i64]
+    dbl = ctypes.c_double
+    lib.spingp_optimize_workspace_bytes.argtypes = [vp, i64]
+    lib.spingp_optimize_workspace_bytes.restype = sz
+    lib.spingp_optimize.argtypes = [vp, dp, dp, i64, dp, ctypes.c_int, dbl, dp, dp, vp, sz, u32, vp]
+    lib.spingp_optimize_workspace_bytes_batched.argtypes = [vp, i64, i64]
+    lib.spingp_optimize_workspace_bytes_batched.restype = sz
+    lib.spingp_optimize_batched.argtypes = [vp, dp, i64, i64, dp, dp, dp, ctypes.c_int, dbl, dp, dp, vp, sz, u32, vp]
     lib.spingp_ws_status.argtypes = [vp, vp]
     lib.spingp_status_str.argtypes = [ctypes.c_int]
     lib.spingp_status_str.restype = ctypes.c_char_p
@@ -303,6 +312,28 @@ def spingp_literal_launch_count(n):
     return load().spingp_literal_launch_count(int(n))
 
 
+def spingp_optimize_workspace_bytes(h, n):
+    return load().spingp_optimize_workspace_bytes(h, int(n))
+
+
+def spingp_optimize(h, t, y, n, theta_inout, iterations, tol, ll_out, grad_out, ws, ws_bytes, flags, stream=None):
+    return load().spingp_optimize(h, _ptr(t), _ptr(y), int(n), _ptr(theta_inout), int(iterations), float(tol),
+                                  _ptr(ll_out), _ptr(grad_out), _ptr(ws), ws_bytes, flags,
+                                  stream if stream is not None else _stream())
+
+
+def spingp_optimize_workspace_bytes_batched(h, n_series, n_total):
+    return load().spingp_optimize_workspace_bytes_batched(h, int(n_series), int(n_total))
+
+
+def spingp_optimize_batched(h, offsets, n_series, n_total, t, y, theta_inout, iterations, tol, ll_out, grad_out, ws,
+                            ws_bytes, flags, stream=None):
+    return load().spingp_optimize_batched(h, _ptr(offsets), int(n_series), int(n_total), _ptr(t), _ptr(y),
+                                          _ptr(theta_inout), int(iterations), float(tol), _ptr(ll_out),
+                                          _ptr(grad_out), _ptr(ws), ws_bytes, flags,
+                                          stream if stream is not None else _stream())
+
+
 def spingp_ws_status(ws, stream=None):
     return load().spingp_ws_status(_ptr(ws), stream if stream is not None else _stream())
 
@@ -413,6 +444,20 @@ class Model:
         idx = where[t.numel():]
         return mean[idx], var[idx]
 
+
+    def optimize(self, t, y, theta0, iterations=100, tol=1e-8, sync=True, missing=False):
+        """Maximise the marginal likelihood from theta0 by scaled conjugate
+        gradients over log-parameters (Sec. 4.3).  Returns (theta, ll, grad)
+        at the last accepted point."""
+        n = self._args(t, y, theta0)
+        dev = t.device
+        theta = theta0.clone()
+        ll = torch.empty(1, dtype=torch.float64, device=dev)
+        g = torch.empty(self.num_params, dtype=torch.float64, device=dev)
+        ws = self._scratch(spingp_optimize_workspace_bytes(self.h, n), dev, "spingp_optimize")
+        _check(spingp_optimize(self.h, t, y, n, theta, iterations, tol, ll, g, ws, ws.numel(),
+                               self._flags(sync, missing)), "spingp_optimize")
+        return theta, ll, g
 
     # ------------------------------------------------------------ the method as written (Sec. 2.2-3.1)
 
@@ -564,6 +609,28 @@ class Batch:
                                         self._theta(theta), ll, mean, var, ws, ws.numel(), SYNC if sync else 0),
                "spingp_posterior_batched")
         return mean, var, ll
+
+    def optimize(self, theta0, iterations=100, tol=1e-8, sync=True):
+        """Fit every series' hyperparameters by scaled conjugate gradients
+        (Sec. 4.3), all series in one launch sequence.  theta0: n_series x P
+        starting points.  Returns (theta, ll, grad), one row per series."""
+        theta0 = self._theta(theta0)
+        dev = self.t.device
+        P = self.model.num_params
+        theta = theta0.clone().view(self.n_series, P)
+        ll = torch.empty(self.n_series, dtype=torch.float64, device=dev)
+        g = torch.empty(self.n_series, P, dtype=torch.float64, device=dev)
+        nbytes = spingp_optimize_workspace_bytes_batched(self.model.h, self.n_series, self.n_total)
+        if nbytes == 0:
+            raise SpinGPError(EUNSUPPORTED, "spingp_optimize_workspace_bytes_batched")
+        ws = self._ws.get("optimize")
+        if ws is None or ws.numel() < nbytes:
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+            self._ws["optimize"] = ws
+        _check(spingp_optimize_batched(self.model.h, self.offsets, self.n_series, self.n_total, self.t, self.y,
+                                       theta, iterations, tol, ll, g, ws, ws.numel(), SYNC if sync else 0),
+               "spingp_optimize_batched")
+        return theta, ll, g
 
 
 class LogLik(torch.autograd.Function):

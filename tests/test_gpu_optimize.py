@@ -1,0 +1,183 @@
+"""GPU parity for hyperparameter fitting by scaled conjugate gradients
+(Moller 1993; the paper's optimiser, Sec. 4.3): the device state machine
+against the oracle's SCG driven by the oracle's gradient, for single series,
+structured models and batches, plus graph capture and errors."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import scg, seq  # noqa: E402
+from paper_1610_08035_gb300 import spingp, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def _t(a):
+    return torch.tensor(np.asarray(a, dtype=np.float64), device=DEV)
+
+
+def _series(n, ell, seed, mean_dt=0.05):
+    rng = np.random.default_rng(seed)
+    t = synth.exp_times(n, mean_dt, rng)
+    y = synth.two_sinusoids(t, ell, 1.0, 0.1, rng)
+    return t, y
+
+
+@pytest.mark.parametrize("iters", [1, 3, 6])
+def test_first_iterations_follow_the_oracle(iters):
+    """Early iterates: the same deterministic map of nearly equal gradients."""
+    spec = "matern52"
+    t, y = _series(3000, 0.7, 1)
+    th0 = np.array([0.3, 0.5, 0.5])
+    m = spingp.Model(spec)
+    th, ll, g = m.optimize(_t(t), _t(y), _t(th0), iterations=iters, tol=0.0)
+    wo, fo, go, _ = scg.scg(scg.gp_objective(spec, t, y, seq.grad), np.log(th0), iters)
+    assert np.max(np.abs(np.log(th.cpu().numpy()) - wo)) <= 1e-7 * max(1.0, np.max(np.abs(wo)))
+    assert abs(-ll.item() - fo) <= 1e-9 * abs(fo)
+
+
+@pytest.mark.parametrize("spec,th0", [("matern12", [0.5, 2.0, 0.3]), ("matern32", [2.0, 0.5, 0.05]),
+                                      ("matern52", [0.3, 0.5, 0.5])])
+def test_converged_optimum_matches_oracle(spec, th0):
+    t, y = _series(2000, 1.0, 7)
+    m = spingp.Model(spec)
+    th, ll, g = m.optimize(_t(t), _t(y), _t(th0), iterations=300, tol=1e-7)
+    wo, fo, go, _ = scg.scg(scg.gp_objective(spec, t, y, seq.grad), np.log(th0), 300, tol=1e-7)
+    thg = th.cpu().numpy()
+    assert np.max(np.abs(np.log(thg) - wo)) <= 1e-5
+    assert abs(-ll.item() - fo) <= 1e-9 * abs(fo)
+    # the returned gradient is the oracle's gradient at the returned point
+    llo, gro = seq.grad(spec, thg, t, y)
+    gg = g.cpu().numpy()
+    assert abs(ll.item() - llo) <= 1e-9 * abs(llo)
+    assert np.max(np.abs(gg - gro)) <= 1e-7 * max(1.0, np.max(np.abs(gro)))
+    assert np.max(np.abs(thg * gg)) <= 1e-5          # near-stationary in log-parameters
+
+
+def test_structured_model_improves_and_follows_oracle():
+    spec = ["matern32", ("quasiperiodic", 3, "matern12")]
+    th0 = np.array([1.0, 0.5, 0.5, 1.0, 3.0, 5.0, 0.2])
+    t, y = _series(1500, 1.0, 11)
+    m = spingp.Model(spec)
+    ll0, _ = m.grad(_t(t), _t(y), _t(th0))
+    th, ll, g = m.optimize(_t(t), _t(y), _t(th0), iterations=4, tol=0.0)
+    assert ll.item() > ll0.item()
+    wo, fo, _, _ = scg.scg(scg.gp_objective(spec, t, y, seq.grad), np.log(th0), 4)
+    assert np.max(np.abs(np.log(th.cpu().numpy()) - wo)) <= 1e-6
+    assert abs(-ll.item() - fo) <= 1e-9 * abs(fo)
+
+
+def _batch(n_series=48, seed=5):
+    s = synth.batched(n_series=n_series, lo=200, hi=3000, seed=seed)
+    return s, s.extra["offsets"], s.extra["thetas"]
+
+
+def _identifiable_batch(n_series, seed):
+    """Series long enough, against their lengthscales, for the optimum to be
+    unique: dt ~ Exp(0.05), 500-3000 steps, signal lengthscale U(0.5, 2)."""
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(500, 3000, n_series)
+    ts, ys = [], []
+    for n in lens:
+        t = synth.exp_times(int(n), 0.05, rng)
+        ts.append(t)
+        ys.append(synth.two_sinusoids(t, rng.uniform(0.5, 2.0), 1.0, 0.1, rng))
+    offsets = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    return np.concatenate(ts), np.concatenate(ys), offsets
+
+
+def test_batched_optimize_matches_per_series_oracle():
+    """Every series of a batch follows its own oracle SCG run to the same
+    optimum."""
+    t, y, offsets = _identifiable_batch(24, 5)
+    S = len(offsets) - 1
+    m = spingp.Model("matern52")
+    th0 = np.tile([1.0, 1.0, 0.2], (S, 1))
+    b = spingp.Batch(m, torch.tensor(offsets, device=DEV), _t(t), _t(y))
+    iters = 60
+    th, ll, g = b.optimize(_t(th0), iterations=iters, tol=1e-7)
+    thg, llg = th.cpu().numpy(), ll.cpu().numpy()
+    for i in range(S):
+        ti, yi = t[offsets[i]:offsets[i + 1]], y[offsets[i]:offsets[i + 1]]
+        wo, fo, _, _ = scg.scg(scg.gp_objective("matern52", ti, yi, seq.grad), np.log(th0[i]), iters, tol=1e-7)
+        assert np.max(np.abs(np.log(thg[i]) - wo)) <= 1e-5, i
+        assert abs(-llg[i] - fo) <= 1e-9 * abs(fo), i
+
+
+def test_batched_optimize_on_the_batched_workload_shape():
+    """The batch of config 4's shape (lengths 200-3000 here).  Some of its
+    series cannot identify their lengthscale (a flat valley of the
+    likelihood), where the path along the valley, and so the point reached
+    after a fixed number of iterations, is not unique.  What is: the returned
+    ll and gradient are the oracle's at the returned point, and the
+    likelihood never falls below its starting value."""
+    s, offsets, thetas = _batch()
+    S = len(thetas)
+    m = spingp.Model("matern52")
+    th0 = np.tile([1.0, 1.0, 0.2], (S, 1))
+    b = spingp.Batch(m, torch.tensor(offsets, device=DEV), _t(s.t), _t(s.y))
+    ll0, _ = b.grad(_t(th0))
+    th, ll, g = b.optimize(_t(th0), iterations=30, tol=1e-7)
+    thg, llg, gg, ll0 = th.cpu().numpy(), ll.cpu().numpy(), g.cpu().numpy(), ll0.cpu().numpy()
+    for i in range(S):
+        ti, yi = s.t[offsets[i]:offsets[i + 1]], s.y[offsets[i]:offsets[i + 1]]
+        llo, go, gabs = seq.grad("matern52", thg[i], ti, yi, l1=True)
+        assert abs(llg[i] - llo) <= 1e-9 * abs(llo), i
+        # end points along a flat valley can have l ~ 1e5 (lam dt ~ 1e-7,
+        # Phi ~ I), where the per-step Pinf adjoint G - Phi^T G Phi cancels
+        # internally in both implementations: a looser bound than parity's
+        assert np.all(np.abs(gg[i] - go) <= 1e-6 * np.maximum(np.abs(go), gabs)), i
+        assert llg[i] >= ll0[i], i
+
+
+def test_batched_optimize_graph_capture():
+    s, offsets, thetas = _batch(n_series=32, seed=9)
+    m = spingp.Model("matern52")
+    th0 = _t(np.tile([1.0, 1.0, 0.2], (len(thetas), 1)))
+    off = torch.tensor(offsets, device=DEV)
+    T, Y = _t(s.t), _t(s.y)
+    nbytes = spingp.spingp_optimize_workspace_bytes_batched(m.h, len(thetas), len(s.t))
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=DEV)
+    th = th0.clone()
+    ll = torch.empty(len(thetas), dtype=torch.float64, device=DEV)
+    g = torch.empty(len(thetas), 3, dtype=torch.float64, device=DEV)
+
+    def call():
+        th.copy_(th0)
+        return spingp.spingp_optimize_batched(m.h, off, len(thetas), len(s.t), T, Y, th, 10, 0.0, ll, g, ws,
+                                              nbytes, 0)
+
+    assert call() == spingp.OK
+    torch.cuda.synchronize()
+    th_eager, ll_eager = th.clone(), ll.clone()
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(graph, stream=stream):
+            assert call() == spingp.OK
+    torch.cuda.current_stream().wait_stream(stream)
+    th.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(th, th_eager) and torch.equal(ll, ll_eager)
+
+
+def test_zero_iterations_and_errors():
+    t, y = _series(500, 1.0, 2)
+    m = spingp.Model("matern32")
+    th0 = _t([0.8, 1.2, 0.1])
+    th, ll, g = m.optimize(_t(t), _t(y), th0, iterations=0)
+    ll_ref, g_ref = m.grad(_t(t), _t(y), th0)
+    # the returned point is exp(log(theta0)): equal up to rounding
+    assert torch.allclose(th, th0, rtol=1e-15, atol=0)
+    assert abs(ll.item() - ll_ref.item()) <= 1e-13 * abs(ll_ref.item())
+    assert torch.allclose(g, g_ref, rtol=1e-12, atol=1e-12)
+    with pytest.raises(spingp.SpinGPError) as e:
+        m.optimize(_t(t), _t(y), _t([0.8, -1.0, 0.1]), iterations=3)
+    assert e.value.status == spingp.EINVAL
+    # usable again afterwards
+    th, ll, _ = m.optimize(_t(t), _t(y), th0, iterations=2)
+    assert np.isfinite(ll.item())

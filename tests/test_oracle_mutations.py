@@ -105,3 +105,43 @@ def test_dense_gradient_mutant_is_caught(monkeypatch):
 
     monkeypatch.setattr(dense, "grad", bad)
     assert _quick_suite() != []
+
+
+# Python-level mutants of the optimiser (oracle/scg.py): text-substituted
+# copies loaded as a module; each must fail one of the SCG pins.
+# (A wrong sign of beta's r'.r term is not in the list: no convergence
+# property separates it -- on a quadratic r'.r vanishes, and on Rosenbrock it
+# converges in 87 iterations against 100.)
+SCG_MUTANTS = [
+    ("no conjugacy (beta = 0)", "beta = (rn @ rn - rn @ r) / mu", "beta = 0.0"),
+    ("no lambda scaling of delta", "delta = delta + (lam - lambar) * pp", "delta = delta"),
+    ("comparison ratio sign", "Delta = 2.0 * delta * (f - fn) / (mu * mu)", "Delta = 2.0 * delta * (fn - f) / (mu * mu)"),
+    ("curvature from the wrong side", "s = (np.asarray(gs) - g) / sigma", "s = (g - np.asarray(gs)) / sigma"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", SCG_MUTANTS)
+def test_scg_mutant_is_caught(name, old, new, tmp_path):
+    import importlib.util
+    from oracle import scg
+    import test_oracle_scg as scg_pins
+    src = open(scg.__file__).read()
+    assert src.count(old) == 1, name
+    path = tmp_path / "scg_mutant.py"
+    path.write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location("scg_mutant", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    caught = False
+    saved = scg_pins.scg
+    scg_pins.scg = mod
+    try:
+        for fn in (scg_pins.test_quadratic_reaches_the_minimiser, scg_pins.test_rosenbrock,
+                   scg_pins.test_rejected_trial_points_do_not_move):
+            try:
+                fn()
+            except Exception:
+                caught = True
+    finally:
+        scg_pins.scg = saved
+    assert caught, name
