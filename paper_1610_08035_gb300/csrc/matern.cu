@@ -22,6 +22,7 @@
 #include <stdint.h>
 
 #include "chain.cuh"
+#include "coop.cuh"
 #include "internal.h"
 
 namespace spg {
@@ -110,6 +111,120 @@ __device__ __forceinline__ void renorm(double& prod, int& expo) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(prod);
     expo += (int)((bits >> 52) & 0x7ffULL) - 1023;
     prod = __longlong_as_double((long long)((bits & 0x800FFFFFFFFFFFFFULL) | 0x3FF0000000000000ULL));
+}
+
+// ------------------------------------------------------------------ cooperative tree levels
+
+// Levels of the in-block tree with at most TREE_COOP_CNT nodes run on lane
+// groups (coop.cuh); wider levels keep one node per thread.
+static constexpr int TREE_COOP_CNT = 16;
+
+__device__ __forceinline__ int lv_of_cnt(int cnt) { return CTA_LV - 31 + __clz(cnt); }   // cnt = CTA >> l
+
+// Up-sweep levels with cnt <= TREE_COOP_CNT: node j of level l combines
+// nodes 2j, 2j+1 of level l-1 (in sm, compacted to the front); at most two
+// rounds of NG groups, results held until every group has read its inputs.
+template <int B>
+__device__ __forceinline__ void tree_up_coop(double* sm, double* __restrict__ nodes, int64_t nld, int64_t blk,
+                                             double* __restrict__ btot, int64_t nblocks) {
+    constexpr int NE = Dims<B>::NE, W = Coop<B>::W, NG = CTA / W, NGW = Coop<B>::NG_WARP;
+    static_assert(2 * NG >= TREE_COOP_CNT, "at most two rounds per level");
+    const int tid = threadIdx.x, g = tid / W, wg0 = (tid >> 5) * NGW;
+    const CPos<B> p;
+#pragma unroll 1
+    for (int cnt = TREE_COOP_CNT; cnt >= 1; cnt >>= 1) {
+        const int l = lv_of_cnt(cnt);
+        const bool act0 = wg0 < cnt, act1 = wg0 + NG < cnt;   // warp-uniform
+        CElem r0, r1;
+        if (act0) {
+            const int j = min(g, cnt - 1);
+            CElem x, y;
+            celem_load<B>(sm + (2 * j) * NE, 1, 0, x, p);
+            celem_load<B>(sm + (2 * j + 1) * NE, 1, 0, y, p);
+            ccombine<B>(x, y, r0, p);
+        }
+        if (act1) {
+            const int j = min(g + NG, cnt - 1);
+            CElem x, y;
+            celem_load<B>(sm + (2 * j) * NE, 1, 0, x, p);
+            celem_load<B>(sm + (2 * j + 1) * NE, 1, 0, y, p);
+            ccombine<B>(x, y, r1, p);
+        }
+        __syncthreads();
+        if (act0 && g < cnt) {
+            celem_store<B>(sm + g * NE, 1, 0, r0, p);
+            celem_store<B>(nodes, nld, blk * TREE + tree_off(l) + g, r0, p);
+            if (cnt == 1) celem_store<B>(btot, nblocks, blk, r0, p);
+        }
+        if (act1 && g + NG < cnt) {
+            celem_store<B>(sm + (g + NG) * NE, 1, 0, r1, p);
+            celem_store<B>(nodes, nld, blk * TREE + tree_off(l) + g + NG, r1, p);
+        }
+        __syncthreads();
+    }
+}
+
+// Down-sweep levels with at most TREE_COOP_CNT children: from the parents'
+// states / information (spre, ssuf at [0, cnt/2)) to the children's
+// ([0, cnt)).  Odd child 2j+1: the parent's state pushed through node 2j;
+// even child 2j: the parent's information pulled back through node 2j+1
+// (BWD only; otherwise the parent's information is not needed).  Groups
+// [0, NG/2) take the odd children and [NG/2, NG) the even ones, so the two
+// kinds never share a warp.
+template <int B, bool BWD>
+__device__ __forceinline__ void tree_down_coop(double* spre, double* ssuf, const double* __restrict__ nodes,
+                                               int64_t nld, int64_t blk) {
+    constexpr int NM = Dims<B>::NM, W = Coop<B>::W, NG = CTA / W, NGW = Coop<B>::NG_WARP, H = NG / 2;
+    static_assert(H % NGW == 0, "a warp's groups lie in one half");
+    static_assert(2 * H >= TREE_COOP_CNT / 2, "at most two rounds per level");
+    const int tid = threadIdx.x, g = tid / W, wg0 = (tid >> 5) * NGW;
+    const bool odd = g < H;
+    const int gi = odd ? g : g - H, wgi0 = odd ? wg0 : wg0 - H;
+    const CPos<B> p;
+#pragma unroll 1
+    for (int cnt = 2; cnt <= TREE_COOP_CNT; cnt <<= 1) {
+        const int half = cnt / 2;
+        const int lc = lv_of_cnt(cnt);   // the children's level
+        CVS a0, b0, a1, b1;              // (pre, suf) of the child, rounds 0 and 1
+        const bool act0 = wgi0 < half, act1 = wgi0 + H < half;
+        const bool need = odd || BWD;
+#pragma unroll
+        for (int round = 0; round < 2; ++round) {
+            const bool act = round ? act1 : act0;
+            if (!act) continue;
+            const int j = min(gi + round * H, half - 1);
+            CVS pre, suf, o;
+            cvs_load<B>(spre + j * NM, 1, 0, pre, p);
+            if (BWD) cvs_load<B>(ssuf + j * NM, 1, 0, suf, p);
+            else { suf.v = 0.0; suf.S = 0.0; }
+            if (odd) {
+                CElem e;
+                celem_load<B>(nodes, nld, blk * TREE + tree_off(lc) + 2 * j, e, p);
+                cstate_through<B>(pre, e, o, p);
+                (round ? a1 : a0) = o;
+                (round ? b1 : b0) = suf;
+            } else if (need) {
+                CElem e;
+                celem_load<B>(nodes, nld, blk * TREE + tree_off(lc) + 2 * j + 1, e, p);
+                cinfo_through<B>(e, suf, o, p);
+                (round ? a1 : a0) = pre;
+                (round ? b1 : b0) = o;
+            } else {
+                (round ? a1 : a0) = pre;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int round = 0; round < 2; ++round) {
+            const bool act = round ? act1 : act0;
+            const int jj = gi + round * H;
+            if (!act || jj >= half) continue;
+            const int k = odd ? 2 * jj + 1 : 2 * jj;
+            cvs_store<B>(spre + k * NM, 1, 0, round ? a1 : a0, p);
+            if (BWD) cvs_store<B>(ssuf + k * NM, 1, 0, round ? b1 : b0, p);
+        }
+        __syncthreads();
+    }
 }
 
 // ------------------------------------------------------------------ k_fold
@@ -219,13 +334,15 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
             for (int q = 0; q < B; ++q) el.C[r][q] += sf * p1<B>(r, q);
     }
     if (bad) atomicOr(a.status, bad);
-    // odd-even up-sweep inside the block (chunks past the end are identities)
+    // odd-even up-sweep inside the block (chunks past the end are identities):
+    // the wide lower levels one combine per thread, the upper levels (at most
+    // TREE_COOP_CNT combines) one combine per lane group
     const int64_t nld = a.nblocks * TREE;
     elem_store<B>(nodes, nld, blk * TREE + tid, el);
     elem_store<B>(sm, 1, (int64_t)tid * NE, el);
     __syncthreads();
 #pragma unroll 1
-    for (int l = 1; l <= CTA_LV; ++l) {
+    for (int l = 1; (CTA >> l) > TREE_COOP_CNT; ++l) {
         const int cnt = CTA >> l;
         Elem<B> r;
         if (tid < cnt) {
@@ -238,153 +355,144 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
         if (tid < cnt) {
             elem_store<B>(sm, 1, (int64_t)tid * NE, r);
             elem_store<B>(nodes, nld, blk * TREE + tree_off(l) + tid, r);
-            if (l == CTA_LV) elem_store<B>(btot, a.nblocks, blk, r);
         }
         __syncthreads();
     }
+    tree_up_coop<B>(sm, nodes, nld, blk, btot, a.nblocks);
 }
 
 // ------------------------------------------------------------------ k_scan_tile (odd-even reduction)
 
-template <int B, int TS>
+// A tile is SCAN_TS consecutive elements, reduced by one CTA of SCAN_CTA
+// threads whose lanes form groups of Coop<B>::W (coop.cuh): every combine,
+// state_through and info_through of the tile's tree is done by one group,
+// so a level costs one cooperative combine (~80 FP64 instructions per lane)
+// instead of a thread's full combine.
+static constexpr int SCAN_TS = 32;
+static constexpr int SCAN_LV = 5;
+static constexpr int SCAN_CTA = 256;
+static_assert((1 << SCAN_LV) == SCAN_TS, "SCAN_TS must be 2^SCAN_LV");
+
+template <int B>
 struct ScanSmem {
     static constexpr int NE = Dims<B>::NE, NM = Dims<B>::NM;
-    static constexpr size_t bytes = sizeof(double) * (size_t)(2 * TS) * (NE + 2 * NM);
+    static constexpr size_t bytes = sizeof(double) * (size_t)(2 * SCAN_TS) * (NE + 2 * NM);
 };
 
-template <int TS>
-__device__ __forceinline__ int node_off(int level) { return 2 * TS - ((2 * TS) >> level); }
+__device__ __forceinline__ int node_off(int level) { return 2 * SCAN_TS - ((2 * SCAN_TS) >> level); }
 
 template <int B>
-__device__ __forceinline__ void elem_to_smem(double* p, const Elem<B>& e) { elem_store<B>(p, 1, 0, e); }
-template <int B>
-__device__ __forceinline__ void elem_from_smem(const double* p, Elem<B>& e) { elem_load<B>(p, 1, 0, e); }
+__device__ __forceinline__ double elem_identity_field(int f) {
+    return (f < B * B && (f % (B + 1)) == 0) ? 1.0 : 0.0;   // A = I, everything else 0
+}
 
-// One tile = TS threads x G consecutive elements.  Up-sweep: each thread
-// eliminates its G elements sequentially, then neighbouring thread totals are
-// paired level by level (odd-even).  With DOWN, the back-substitution sweep
-// writes, for every element k, the state before it (pre_out, NM fields) and the
-// information after it (suf_out, NM fields), given the tile's own prefix and
-// suffix (pre_in / suf_in, NULL at the top level).
-template <int B, int TS, bool DOWN>
-__global__ void __launch_bounds__(TS) k_scan_tile(const double* __restrict__ E, int64_t ne, int G,
-                                                   double* __restrict__ totals, int64_t ntiles,
-                                                   const double* __restrict__ pre_in, const double* __restrict__ suf_in,
-                                                   double* __restrict__ pre_out, double* __restrict__ suf_out) {
-    constexpr int NE = Dims<B>::NE, NM = Dims<B>::NM;
-    constexpr int LV = (TS == 32) ? 5 : (TS == 64) ? 6 : (TS == 128) ? 7 : 8;
-    static_assert((1 << LV) == TS, "TS must be 32, 64, 128 or 256");
+// Up-sweep: the tile's elements are paired level by level (odd-even), every
+// node kept in shared memory; without DOWN the tile total is written.  With
+// DOWN, the back-substitution sweep writes, for every element k, the state
+// before it (pre_out, NM fields) and the information after it (suf_out),
+// given the tile's own prefix and suffix (pre_in / suf_in; NULL at the top
+// level, where the state before the first element is irrelevant: the first
+// element of a series has A = 0).
+template <int B, bool DOWN>
+__global__ void __launch_bounds__(SCAN_CTA, 1) k_scan_tile(const double* __restrict__ E, int64_t ne,
+                                                        double* __restrict__ totals, int64_t ntiles,
+                                                        const double* __restrict__ pre_in,
+                                                        const double* __restrict__ suf_in,
+                                                        double* __restrict__ pre_out, double* __restrict__ suf_out) {
+    constexpr int NE = Dims<B>::NE, NM = Dims<B>::NM, TS = SCAN_TS;
+    constexpr int W = Coop<B>::W, NG = SCAN_CTA / W, NGW = Coop<B>::NG_WARP;
+    static_assert(NG >= TS / 2, "one round per up-sweep level");
+    static_assert((NG / 2) % NGW == 0, "a warp's groups lie in one half");
     extern __shared__ double sm[];
     double* nodes = sm;
     double* preN = nodes + 2 * TS * NE;
     double* sufN = preN + 2 * TS * NM;
-
     const int tid = threadIdx.x;
+    const int g = tid / W;
+    const int wg0 = (tid >> 5) * NGW;   // first group of this warp
+    const CPos<B> p;
     const int64_t tile = blockIdx.x;
-    const int64_t lo = tile * (int64_t)TS * G + (int64_t)tid * G;
-    const int64_t hi = min(ne, lo + G);
+    const int64_t k0 = tile * (int64_t)TS;
 
-    Elem<B> agg;
-    if (lo < hi) {
-        elem_load<B>(E, ne, lo, agg);
-        for (int64_t k = lo + 1; k < hi; ++k) {
-            Elem<B> e, r;
-            elem_load<B>(E, ne, k, e);
-            combine<B>(agg, e, r);
-            agg = r;
-        }
-    } else {
-        elem_identity<B>(agg);
+    for (int idx = tid; idx < TS * NE; idx += SCAN_CTA) {
+        const int f = idx / TS, j = idx % TS;
+        nodes[j * NE + f] = (k0 + j < ne) ? E[(int64_t)f * ne + k0 + j] : elem_identity_field<B>(f);
     }
-    elem_to_smem<B>(nodes + (size_t)tid * NE, agg);
     __syncthreads();
 #pragma unroll 1
-    for (int l = 1; l <= LV; ++l) {
+    for (int l = 1; l <= SCAN_LV; ++l) {
         const int cnt = TS >> l;
-        if (tid < cnt) {
-            Elem<B> x, y, r;
-            elem_from_smem<B>(nodes + (size_t)(node_off<TS>(l - 1) + 2 * tid) * NE, x);
-            elem_from_smem<B>(nodes + (size_t)(node_off<TS>(l - 1) + 2 * tid + 1) * NE, y);
-            combine<B>(x, y, r);
-            elem_to_smem<B>(nodes + (size_t)(node_off<TS>(l) + tid) * NE, r);
+        if (wg0 < cnt) {   // warp-uniform
+            const int j = min(g, cnt - 1);
+            CElem x, y, r;
+            celem_load<B>(nodes + (node_off(l - 1) + 2 * j) * NE, 1, 0, x, p);
+            celem_load<B>(nodes + (node_off(l - 1) + 2 * j + 1) * NE, 1, 0, y, p);
+            ccombine<B>(x, y, r, p);
+            if (g < cnt) celem_store<B>(nodes + (node_off(l) + g) * NE, 1, 0, r, p);
         }
         __syncthreads();
     }
     if constexpr (!DOWN) {
-        if (tid == 0) {
-            Elem<B> r;
-            elem_from_smem<B>(nodes + (size_t)node_off<TS>(LV) * NE, r);
-            elem_store<B>(totals, ntiles, tile, r);
+        if (g == 0) {
+            CElem r;
+            celem_load<B>(nodes + node_off(SCAN_LV) * NE, 1, 0, r, p);
+            celem_store<B>(totals, ntiles, tile, r, p);
         }
         return;
     } else {
-        if (tid == 0) {
-            double v[B], S[B][B];
-#pragma unroll
-            for (int i = 0; i < B; ++i) { v[i] = 0.0;
-#pragma unroll
-                for (int j = 0; j < B; ++j) S[i][j] = 0.0; }
-            if (pre_in) vs_load<B>(pre_in, ntiles, tile, v, S);
-            vs_store<B>(preN + (size_t)node_off<TS>(LV) * NM, 1, 0, v, S);
-#pragma unroll
-            for (int i = 0; i < B; ++i) { v[i] = 0.0;
-#pragma unroll
-                for (int j = 0; j < B; ++j) S[i][j] = 0.0; }
-            if (suf_in) vs_load<B>(suf_in, ntiles, tile, v, S);
-            vs_store<B>(sufN + (size_t)node_off<TS>(LV) * NM, 1, 0, v, S);
+        if (g == 0) {
+            CVS x;
+            x.v = 0.0; x.S = 0.0;
+            if (pre_in) cvs_load<B>(pre_in, ntiles, tile, x, p);
+            cvs_store<B>(preN + node_off(SCAN_LV) * NM, 1, 0, x, p);
+            x.v = 0.0; x.S = 0.0;
+            if (suf_in) cvs_load<B>(suf_in, ntiles, tile, x, p);
+            cvs_store<B>(sufN + node_off(SCAN_LV) * NM, 1, 0, x, p);
         }
         __syncthreads();
+        // level l -> its children at level l-1: odd child 2j+1 gets the
+        // parent's state pushed through child 2j; even child 2j gets the
+        // parent's information pulled back through child 2j+1.  Groups
+        // [0, NG/2) take the odd children, [NG/2, NG) the even ones.
+        const bool odd = g < NG / 2;
+        const int gi = odd ? g : g - NG / 2;
+        const int wgi0 = odd ? wg0 : wg0 - NG / 2;
 #pragma unroll 1
-        for (int l = LV; l >= 1; --l) {
-            const int cnt = TS >> (l - 1);
-            if (tid < cnt) {
-                const int parent = tid >> 1;
-                double pm[B], pP[B][B], sv[B], sJ[B][B], om[B], oP[B][B];
-                vs_load<B>(preN + (size_t)(node_off<TS>(l) + parent) * NM, 1, 0, pm, pP);
-                vs_load<B>(sufN + (size_t)(node_off<TS>(l) + parent) * NM, 1, 0, sv, sJ);
-                Elem<B> sib;
-                if (tid & 1) {
-                    elem_from_smem<B>(nodes + (size_t)(node_off<TS>(l - 1) + tid - 1) * NE, sib);
-                    state_through<B>(pm, pP, sib, om, oP);
-                    vs_store<B>(preN + (size_t)(node_off<TS>(l - 1) + tid) * NM, 1, 0, om, oP);
-                    vs_store<B>(sufN + (size_t)(node_off<TS>(l - 1) + tid) * NM, 1, 0, sv, sJ);
-                } else {
-                    elem_from_smem<B>(nodes + (size_t)(node_off<TS>(l - 1) + tid + 1) * NE, sib);
-                    info_through<B>(sib, sv, sJ, om, oP);
-                    vs_store<B>(preN + (size_t)(node_off<TS>(l - 1) + tid) * NM, 1, 0, pm, pP);
-                    vs_store<B>(sufN + (size_t)(node_off<TS>(l - 1) + tid) * NM, 1, 0, om, oP);
+        for (int l = SCAN_LV; l >= 1; --l) {
+            const int half = (TS >> (l - 1)) / 2;
+#pragma unroll 1
+            for (int base = 0; base < half; base += NG / 2) {
+                if (base + wgi0 < half) {   // warp-uniform
+                    const int j = min(base + gi, half - 1);
+                    const bool mine = base + gi < half;
+                    CVS pre, suf, o;
+                    CElem e;
+                    cvs_load<B>(preN + (node_off(l) + j) * NM, 1, 0, pre, p);
+                    cvs_load<B>(sufN + (node_off(l) + j) * NM, 1, 0, suf, p);
+                    if (odd) {
+                        celem_load<B>(nodes + (node_off(l - 1) + 2 * j) * NE, 1, 0, e, p);
+                        cstate_through<B>(pre, e, o, p);
+                        if (mine) {
+                            cvs_store<B>(preN + (node_off(l - 1) + 2 * j + 1) * NM, 1, 0, o, p);
+                            cvs_store<B>(sufN + (node_off(l - 1) + 2 * j + 1) * NM, 1, 0, suf, p);
+                        }
+                    } else {
+                        celem_load<B>(nodes + (node_off(l - 1) + 2 * j + 1) * NE, 1, 0, e, p);
+                        cinfo_through<B>(e, suf, o, p);
+                        if (mine) {
+                            cvs_store<B>(preN + (node_off(l - 1) + 2 * j) * NM, 1, 0, pre, p);
+                            cvs_store<B>(sufN + (node_off(l - 1) + 2 * j) * NM, 1, 0, o, p);
+                        }
+                    }
                 }
             }
             __syncthreads();
         }
-        // walk this thread's own elements
-        double m[B], P[B][B];
-        vs_load<B>(preN + (size_t)tid * NM, 1, 0, m, P);
-        for (int64_t k = lo; k < hi; ++k) {
-            vs_store<B>(pre_out, ne, k, m, P);
-            if (k + 1 < hi) {
-                Elem<B> e;
-                double mo[B], Po[B][B];
-                elem_load<B>(E, ne, k, e);
-                state_through<B>(m, P, e, mo, Po);
-#pragma unroll
-                for (int i = 0; i < B; ++i) { m[i] = mo[i];
-#pragma unroll
-                    for (int j = 0; j < B; ++j) P[i][j] = Po[i][j]; }
-            }
-        }
-        vs_load<B>(sufN + (size_t)tid * NM, 1, 0, m, P);
-        for (int64_t k = hi - 1; k >= lo; --k) {
-            vs_store<B>(suf_out, ne, k, m, P);
-            if (k > lo) {
-                Elem<B> e;
-                double mo[B], Po[B][B];
-                elem_load<B>(E, ne, k, e);
-                info_through<B>(e, m, P, mo, Po);
-#pragma unroll
-                for (int i = 0; i < B; ++i) { m[i] = mo[i];
-#pragma unroll
-                    for (int j = 0; j < B; ++j) P[i][j] = Po[i][j]; }
+        for (int idx = tid; idx < TS * NM; idx += SCAN_CTA) {
+            const int f = idx / TS, j = idx % TS;
+            if (k0 + j < ne) {
+                pre_out[(int64_t)f * ne + k0 + j] = preN[j * NM + f];
+                suf_out[(int64_t)f * ne + k0 + j] = sufN[j * NM + f];
             }
         }
     }
@@ -444,7 +552,10 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
     const ChunkRange cr = chunk_range<BATCH>(a, c);
     const double sf = cr.th[1], s2 = cr.th[2];
 
-    // ---- 1. back-substitution inside the block
+    // ---- 1. back-substitution inside the block: the upper levels on lane
+    // groups, then one child per thread with the odd children (state pushed
+    // through the left sibling) on threads [0, CTA/2) and the even children
+    // (information pulled back through the right sibling) on [CTA/2, CTA)
     if (tid == 0) {
         double v[B], S[B][B];
         vs_load<B>(bpre, a.nblocks, blk, v, S);
@@ -455,37 +566,42 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
         }
     }
     __syncthreads();
+    tree_down_coop<B, BWD>(spre, ssuf, nodes, nld, blk);
 #pragma unroll 1
-    for (int l = CTA_LV; l >= 1; --l) {
-        const int cnt = CTA >> (l - 1);
+    for (int cnt = 2 * TREE_COOP_CNT; cnt <= CTA; cnt <<= 1) {
+        const int half = cnt / 2;
+        const int lc = lv_of_cnt(cnt);
+        const bool odd = tid < CTA / 2;
+        const int j = odd ? tid : tid - CTA / 2;
+        const bool act = j < half;
         double pm[B], pP[B][B], sv[B], sJ[B][B];
-        if (tid < cnt) {
-            const int parent = tid >> 1;
-            vs_load<B>(spre, 1, (int64_t)parent * NM, pm, pP);
-            if constexpr (BWD) vs_load<B>(ssuf, 1, (int64_t)parent * NM, sv, sJ);
+        if (act) {
+            vs_load<B>(spre, 1, (int64_t)j * NM, pm, pP);
+            if constexpr (BWD) vs_load<B>(ssuf, 1, (int64_t)j * NM, sv, sJ);
             Elem<B> sib;
-            if (tid & 1) {
-                elem_load<B>(nodes, nld, blk * TREE + tree_off(l - 1) + tid - 1, sib);
+            if (odd) {
+                elem_load<B>(nodes, nld, blk * TREE + tree_off(lc) + 2 * j, sib);
                 double om[B], oP[B][B];
                 state_through<B>(pm, pP, sib, om, oP);
 #pragma unroll
                 for (int i = 0; i < B; ++i) { pm[i] = om[i];
 #pragma unroll
-                    for (int j = 0; j < B; ++j) pP[i][j] = oP[i][j]; }
+                    for (int q = 0; q < B; ++q) pP[i][q] = oP[i][q]; }
             } else if constexpr (BWD) {
-                elem_load<B>(nodes, nld, blk * TREE + tree_off(l - 1) + tid + 1, sib);
+                elem_load<B>(nodes, nld, blk * TREE + tree_off(lc) + 2 * j + 1, sib);
                 double ov[B], oJ[B][B];
                 info_through<B>(sib, sv, sJ, ov, oJ);
 #pragma unroll
                 for (int i = 0; i < B; ++i) { sv[i] = ov[i];
 #pragma unroll
-                    for (int j = 0; j < B; ++j) sJ[i][j] = oJ[i][j]; }
+                    for (int q = 0; q < B; ++q) sJ[i][q] = oJ[i][q]; }
             }
         }
         __syncthreads();
-        if (tid < cnt) {
-            vs_store<B>(spre, 1, (int64_t)tid * NM, pm, pP);
-            if constexpr (BWD) vs_store<B>(ssuf, 1, (int64_t)tid * NM, sv, sJ);
+        if (act) {
+            const int k = odd ? 2 * j + 1 : 2 * j;
+            vs_store<B>(spre, 1, (int64_t)k * NM, pm, pP);
+            if constexpr (BWD) vs_store<B>(ssuf, 1, (int64_t)k * NM, sv, sJ);
         }
         __syncthreads();
     }
@@ -879,18 +995,13 @@ __global__ void __launch_bounds__(256) k_finalize_batched(const double* __restri
 
 // ------------------------------------------------------------------ host side
 
-// grid-level reduction of the block totals: tiles of SCAN_TS threads x G
-// elements; small tiles keep each level spread over many SMs (the FP64 pipe
-// of a single SM would otherwise serialise the top of the tree)
-static constexpr int SCAN_TS = 32;
-static constexpr int SCAN_GTOP = 1;    // largest G of a single top tile
-static constexpr int SCAN_GMID = 1;    // G of the tiles of a multi-tile level
+// grid-level reduction of the block totals: tiles of SCAN_TS elements, one
+// CTA each; small tiles keep each level spread over many SMs
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static int64_t top_g(int64_t ne) { return (ne + SCAN_TS - 1) / SCAN_TS; }
-static bool single_tile(int64_t ne) { return ne <= (int64_t)SCAN_TS * SCAN_GTOP; }
-static int64_t mid_tiles(int64_t ne) { return (ne + (int64_t)SCAN_TS * SCAN_GMID - 1) / ((int64_t)SCAN_TS * SCAN_GMID); }
+static bool single_tile(int64_t ne) { return ne <= (int64_t)SCAN_TS; }
+static int64_t mid_tiles(int64_t ne) { return (ne + SCAN_TS - 1) / SCAN_TS; }
 
 // Workspace: [status | tree nodes | block totals | block prefix | block suffix |
 //             grid scan levels | Phi per step | block partials | stored steps]
@@ -939,21 +1050,18 @@ struct Layout {
 template <int B>
 static void scan_level(const double* E, int64_t ne, double* pre_out, double* suf_out, const Layout<B>& lay,
                        char* ws, int lev, cudaStream_t st) {
-    const size_t smem = ScanSmem<B, SCAN_TS>::bytes;
+    const size_t smem = ScanSmem<B>::bytes;
     if (single_tile(ne)) {
-        k_scan_tile<B, SCAN_TS, true><<<1, SCAN_TS, smem, st>>>(E, ne, (int)top_g(ne), nullptr, 1, nullptr,
-                                                                nullptr, pre_out, suf_out);
+        k_scan_tile<B, true><<<1, SCAN_CTA, smem, st>>>(E, ne, nullptr, 1, nullptr, nullptr, pre_out, suf_out);
         return;
     }
     const int64_t nt = lay.lev_n[lev];
     double* tot = (double*)(ws + lay.lev_tot[lev]);
     double* tpre = (double*)(ws + lay.lev_pre[lev]);
     double* tsuf = (double*)(ws + lay.lev_suf[lev]);
-    k_scan_tile<B, SCAN_TS, false><<<(unsigned)nt, SCAN_TS, smem, st>>>(E, ne, SCAN_GMID, tot, nt, nullptr,
-                                                                       nullptr, nullptr, nullptr);
+    k_scan_tile<B, false><<<(unsigned)nt, SCAN_CTA, smem, st>>>(E, ne, tot, nt, nullptr, nullptr, nullptr, nullptr);
     scan_level<B>(tot, nt, tpre, tsuf, lay, ws, lev + 1, st);
-    k_scan_tile<B, SCAN_TS, true><<<(unsigned)nt, SCAN_TS, smem, st>>>(E, ne, SCAN_GMID, nullptr, nt, tpre, tsuf,
-                                                                      pre_out, suf_out);
+    k_scan_tile<B, true><<<(unsigned)nt, SCAN_CTA, smem, st>>>(E, ne, nullptr, nt, tpre, tsuf, pre_out, suf_out);
 }
 
 template <int B>
@@ -1077,10 +1185,10 @@ int matern_run_batched_t(int mode, const int64_t* offsets, int64_t nseries, int6
 
 template <int B>
 static void set_smem_attr() {
-    cudaFuncSetAttribute(k_scan_tile<B, SCAN_TS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)ScanSmem<B, SCAN_TS>::bytes);
-    cudaFuncSetAttribute(k_scan_tile<B, SCAN_TS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)ScanSmem<B, SCAN_TS>::bytes);
+    cudaFuncSetAttribute(k_scan_tile<B, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)ScanSmem<B>::bytes);
+    cudaFuncSetAttribute(k_scan_tile<B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)ScanSmem<B>::bytes);
 }
 
 size_t matern_ws_bytes(int b, int64_t n, int64_t L, int mode) {
