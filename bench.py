@@ -35,11 +35,11 @@ WORKLOAD = "matern52_n4m"
 # profiles/chain_kernels_grad_matern52_n2m.md): flops = 2 x DFMA + DADD + DMUL
 # thread instructions; FP64 instructions = everything the FP64 pipe executed
 # (the pipe issues one warp instruction per 16 cycles per SM whatever its kind).
-FLOPS_PER_STEP = {"elimination": 264.6, "chunk_pass": 361.7}
-FP64_INST_PER_STEP = {"elimination": 167.0, "chunk_pass": 227.1}
+FLOPS_PER_STEP = {"elimination": 268.2, "chunk_pass": 364.2}
+FP64_INST_PER_STEP = {"elimination": 167.9, "chunk_pass": 223.7}
 # DRAM bytes per step moved by the chunk pass (ncu dram__bytes_read + write,
 # same capture); None once the kernel has changed since the counters were taken
-DRAM_BYTES_PER_STEP = {"chunk_pass": 305.7}
+DRAM_BYTES_PER_STEP = {"chunk_pass": 305.4}
 # algorithmic HBM bytes per step of the whole call: t and y in (16 B); the
 # gradient and log-likelihood outputs are O(1) per series
 ALGO_BYTES_PER_STEP = 16.0
