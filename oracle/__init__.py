@@ -19,13 +19,18 @@ Two independent FP64 implementations of the same plain definition:
 
 Model specification (shared by both): a list of components, each one of
 ``"matern12"``, ``"matern32"``, ``"matern52"``, ``("periodic", J)`` or
-``("quasiperiodic", J, envelope)`` with envelope one of the Matern names.
+``("quasiperiodic", J, envelope)`` with envelope one of the Matern names, or
+``("eq", N)``: the exponentiated-quadratic covariance through its state-space
+approximation of even order N (the Taylor series of the inverse spectral
+density truncated at N; Hartikainen & Sarkka 2010, the approximation the
+paper's experiments use with N = 10).
 Parameter vector theta: per component (lengthscale, variance) for Matern;
 (variance, lengthscale, period) for periodic; (variance, lengthscale, period,
-envelope lengthscale) for quasi-periodic; the noise variance sigma_n^2 last.
+envelope lengthscale) for quasi-periodic; (lengthscale, variance) for eq; the
+noise variance sigma_n^2 last.
 """
 
-KIND_CODES = {"matern12": 1, "matern32": 2, "matern52": 3, "periodic": 4, "quasiperiodic": 5}
+KIND_CODES = {"matern12": 1, "matern32": 2, "matern52": 3, "periodic": 4, "quasiperiodic": 5, "eq": 6}
 
 
 def normalize_spec(spec):
@@ -42,13 +47,15 @@ def normalize_spec(spec):
         env = KIND_CODES[comp[2]] if len(comp) > 2 else 0
         if code == 5 and env == 0:
             raise ValueError("quasiperiodic needs an envelope kind")
+        if code == 6 and (order < 2 or order % 2):
+            raise ValueError("eq needs an even approximation order >= 2")
         out.append((code, order, env))
     return out
 
 
 def n_params(spec):
     """Number of entries of theta (noise variance included)."""
-    per_kind = {1: 2, 2: 2, 3: 2, 4: 3, 5: 4}
+    per_kind = {1: 2, 2: 2, 3: 2, 4: 3, 5: 4, 6: 2}
     return sum(per_kind[c] for c, _, _ in normalize_spec(spec)) + 1
 
 
@@ -59,6 +66,8 @@ def state_dim(spec):
             b += code
         elif code == 4:
             b += 2 * (order + 1)
-        else:
+        elif code == 5:
             b += 2 * (order + 1) * env
+        else:
+            b += order
     return b

@@ -14,6 +14,14 @@ here independently of any state-space construction:
   represents exactly).
 * quasi-periodic: periodic times a unit-variance Matern envelope (Eq. co2_1's
   quasi-periodic term).
+* exponentiated quadratic, state-space approximation of even order N
+  (Hartikainen & Sarkka 2010): the spectral density of s exp(-tau^2/(2 l^2)),
+  s sqrt(2 pi) l exp(-l^2 w^2 / 2), with exp(l^2 w^2 / 2) replaced by its
+  Taylor polynomial p(l w), p(u) = sum_{n<=N} (u^2/2)^n / n!.  Its covariance
+  is the inverse Fourier transform of that rational density, here by residues:
+  with u_j the roots of p in the upper half plane,
+      k(tau) = s sqrt(2 pi) Re( i sum_j exp(i u_j |tau| / l) / p'(u_j) )
+  (the roots by a library polynomial solver).
 * sums of components add.
 
 With C = K + sigma_n^2 I (Eq. k2, Sigma = sigma_n^2 I):
@@ -72,6 +80,41 @@ def _periodic(J, var, lp, per, tau):
     return var * base, base, var * dbase_dl, var * dbase_dp
 
 
+def _eq_poly(N):
+    """p(u) = sum_{n<=N} (u^2/2)^n / n!, coefficients highest degree first."""
+    c = np.zeros(2 * N + 1)
+    f = 1.0
+    for n in range(N + 1):
+        if n > 0:
+            f *= n
+        c[2 * N - 2 * n] = 0.5 ** n / f
+    return c
+
+
+def _eq(N, ell, var, tau):
+    """The order-N approximate EQ covariance and its derivatives (d/dl, d/dvar)."""
+    c = _eq_poly(N)
+    u = np.roots(c)
+    u = u[u.imag > 0]
+    dp = np.polyder(c)
+    s = np.abs(tau) / ell
+    g = np.zeros_like(s)
+    dg = np.zeros_like(s)
+    for uj in u:
+        w = 1.0 / np.polyval(dp, uj)
+        e = np.exp(1j * uj * s)
+        g = g + np.real(1j * w * e)
+        dg = dg + np.real(-uj * w * e)          # d/ds of Re(i w e^{i u s})
+    g = g * np.sqrt(2.0 * np.pi)
+    dg = dg * np.sqrt(2.0 * np.pi)
+    return var * g, var * dg * (-s / ell), g
+
+
+def eq_exact(var, ell, tau):
+    """The exponentiated-quadratic covariance itself, s exp(-tau^2 / (2 l^2))."""
+    return var * np.exp(-0.5 * (np.asarray(tau) / ell) ** 2)
+
+
 def periodic_exact(var, lp, per, tau):
     """The untruncated periodic covariance s exp(-2 sin^2(pi tau / p) / l^2)."""
     return var * np.exp(-2.0 * np.sin(np.pi * tau / per) ** 2 / (lp * lp))
@@ -90,6 +133,12 @@ def kernel(spec, theta, tau):
         if code <= 3:
             ell, var = theta[p], theta[p + 1]
             kv, dkl, base = _matern(code, ell, var, tau)
+            k += kv
+            dk += [dkl, base]
+            p += 2
+        elif code == 6:
+            ell, var = theta[p], theta[p + 1]
+            kv, dkl, base = _eq(order, ell, var, tau)
             k += kv
             dk += [dkl, base]
             p += 2

@@ -45,11 +45,23 @@
  *   5 quasi-periodic: periodic(J) times a unit-variance Matern envelope of
  *       kind env (Kronecker product of the two state spaces):
  *       (variance, lengthscale, period, envelope lengthscale).
+ *   6 exponentiated quadratic, state-space approximation of even order N
+ *       (b = N): (lengthscale, variance).  The spectral density
+ *       s sqrt(2 pi) l exp(-l^2 w^2/2) with exp(l^2 w^2/2) replaced by its
+ *       Taylor polynomial of order N in l^2 w^2/2 is rational; its stable
+ *       spectral factor gives the SDE f^(N) + a_{N-1} f^(N-1) + ... + a_0 f =
+ *       white noise of spectral density q_c (Hartikainen & Sarkka 2010):
+ *       F the companion matrix of s^N + a_{N-1} s^{N-1} + ... + a_0, whose
+ *       roots are the left-half-plane roots of sum_n (-s^2 l^2/2)^n / n!,
+ *       q_c = s sqrt(2 pi) l 2^N N! / l^(2N), H = e_1^T, Pinf from the
+ *       Lyapunov equation F P + P F^T + q_c e_N e_N^T = 0.
  *   Sums of components stack block-diagonally and concatenate H.
  */
+#include <complex.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#undef I   /* complex.h's imaginary unit macro; _Complex_I is used instead */
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -177,6 +189,9 @@ static int om_init(om_t* om, int ncomp, const int* kind, const int* order, const
         case 5:
             if (om->order[c] < 0 || om->env[c] < 1 || om->env[c] > 3) return E_INVAL;
             bc = 2 * (om->order[c] + 1) * matern_b(om->env[c]); np = 4; break;
+        case 6:
+            if (om->order[c] < 2 || om->order[c] % 2 || om->order[c] > 16) return E_INVAL;
+            bc = om->order[c]; np = 2; break;
         default: return E_INVAL;
         }
         om->off[c] = b; om->bc[c] = bc; om->poff[c] = P; om->np[c] = np;
@@ -267,6 +282,160 @@ static void matern_expm(int b, double lam, double dt, double* A, double* dAl) {
        commutes with it, so the shift needs no separate derivative term. */
 }
 
+/* ---------------------------------------------------------------- general matrix exponential */
+
+static double mnorm1(int n, const double* A) {
+    double best = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += fabs(A[i * n + j]);
+        if (s > best) best = s;
+    }
+    return best;
+}
+
+/* expm(M) by scaling and squaring: M / 2^s has 1-norm <= 1/4, its Taylor
+   series is summed until the terms vanish against the sum, then squared s
+   times.  n <= 2 OMAXB. */
+static void expm_taylor(int n, const double* M, double* E) {
+    double nrm = mnorm1(n, M);
+    int sq = 0;
+    while (nrm > 0.25) { nrm *= 0.5; ++sq; }
+    double scale = ldexp(1.0, -sq);
+    static double T[4 * OB2], U[4 * OB2], Ms[4 * OB2];
+    for (int i = 0; i < n * n; ++i) Ms[i] = M[i] * scale;
+    meye(n, E);
+    meye(n, T);
+    for (int k = 1; k < 60; ++k) {
+        mm(n, T, Ms, U);
+        double tn = 0.0, en = 0.0;
+        for (int i = 0; i < n * n; ++i) { T[i] = U[i] / k; E[i] += T[i]; tn += fabs(T[i]); en += fabs(E[i]); }
+        if (tn <= 1e-20 * en) break;
+    }
+    for (int r = 0; r < sq; ++r) {
+        mm(n, E, E, U);
+        mcopy(n, U, E);
+    }
+}
+
+/* ---------------------------------------------------------------- exponentiated quadratic (order N) */
+
+/* Left-half-plane roots of sum_{n<=N} (-s^2/2)^n / n! (l = 1).  As a
+   polynomial in w = s^2 it has degree N; its roots w_j (Durand-Kerner
+   iteration, then Newton polishing) give the stable roots s_j = -sqrt(w_j). */
+static void eq_roots(int N, double complex* sr) {
+    double complex cf[17];                       /* monic coefficients in w, cf[N] = 1 */
+    double fact = 1.0;
+    for (int n = 1; n <= N; ++n) fact *= n;
+    /* sum (-1/2)^n w^n / n!  divided by its leading coefficient (-1/2)^N / N! */
+    double lead = pow(-0.5, N) / fact, f = 1.0;
+    for (int n = 0; n <= N; ++n) {
+        if (n > 0) f *= n;
+        cf[n] = (pow(-0.5, n) / f) / lead;
+    }
+    double complex w[16];
+    double rad = 1.0;
+    for (int n = 0; n < N; ++n) { double a = cabs(cf[n]); if (pow(a, 1.0 / (N - n)) > rad) rad = pow(a, 1.0 / (N - n)); }
+    for (int j = 0; j < N; ++j) w[j] = rad * cpow(0.4 + 0.9 * _Complex_I, j);
+    for (int it = 0; it < 5000; ++it) {
+        double moved = 0.0;
+        for (int j = 0; j < N; ++j) {
+            double complex pv = 1.0;   /* monic: evaluate by Horner */
+            pv = cf[N];
+            for (int n = N - 1; n >= 0; --n) pv = pv * w[j] + cf[n];
+            double complex den = 1.0;
+            for (int k = 0; k < N; ++k) if (k != j) den *= (w[j] - w[k]);
+            double complex d = pv / den;
+            w[j] -= d;
+            if (cabs(d) > moved * cabs(w[j]) / (cabs(w[j]) + 1e-300)) moved = cabs(d) / (cabs(w[j]) + 1e-300);
+        }
+        if (moved < 1e-15) break;
+    }
+    for (int j = 0; j < N; ++j) {
+        for (int it = 0; it < 4; ++it) {     /* Newton polishing on the monic polynomial */
+            double complex pv = cf[N], dv = 0.0;
+            for (int n = N - 1; n >= 0; --n) { dv = dv * w[j] + pv; pv = pv * w[j] + cf[n]; }
+            if (cabs(dv) == 0.0) break;
+            w[j] -= pv / dv;
+        }
+        sr[j] = -csqrt(w[j]);
+        if (creal(sr[j]) > 0.0) sr[j] = -sr[j];
+    }
+}
+
+/* Monic stable factor s^N + a_{N-1} s^{N-1} + ... + a_0 (l = 1): coefficients a[0..N-1]. */
+static void eq_factor(int N, double* a) {
+    double complex sr[16], c[17];
+    eq_roots(N, sr);
+    c[0] = 1.0;
+    for (int k = 1; k <= N; ++k) c[k] = 0.0;
+    for (int j = 0; j < N; ++j)            /* multiply by (s - s_j); c[k] = coefficient of s^k */
+        for (int k = j + 1; k >= 0; --k) c[k] = (k > 0 ? c[k - 1] : 0.0) - sr[j] * c[k];
+    for (int k = 0; k < N; ++k) a[k] = creal(c[k]);
+}
+
+/* F (companion) for lengthscale l and dF/dl: a_k(l) = a_k(1) l^(k-N). */
+static void eq_F(int N, const double* a1, double ell, double* F, double* Fl) {
+    mzero(N, F); if (Fl) mzero(N, Fl);
+    for (int i = 0; i + 1 < N; ++i) F[i * N + i + 1] = 1.0;
+    for (int k = 0; k < N; ++k) {
+        F[(N - 1) * N + k] = -a1[k] * pow(ell, k - N);
+        if (Fl) Fl[(N - 1) * N + k] = -a1[k] * (k - N) * pow(ell, k - N - 1);
+    }
+}
+
+/* Unit-variance stationary covariance at l = 1, from the Lyapunov equation
+   F1 P + P F1^T + q1 e_N e_N^T = 0, q1 = sqrt(2 pi) 2^N N!, solved as the
+   linear system (I (x) F1 + F1 (x) I) vec P = -q1 vec(e_N e_N^T). */
+static int eq_P1(int N, const double* a1, double* P1) {
+    double F1[OB2];
+    eq_F(N, a1, 1.0, F1, NULL);
+    int m = N * N;
+    double* K = (double*)calloc((size_t)m * m, sizeof(double));
+    double* rhs = (double*)calloc((size_t)m, sizeof(double));
+    double* x = (double*)calloc((size_t)m, sizeof(double));
+    if (!K || !rhs || !x) { free(K); free(rhs); free(x); return E_NOMEM; }
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+            int r = i * N + j;   /* equation for entry (i, j): sum_k F[i][k] P[k][j] + P[i][k] F[j][k] */
+            for (int k = 0; k < N; ++k) {
+                K[(size_t)r * m + k * N + j] += F1[i * N + k];
+                K[(size_t)r * m + i * N + k] += F1[j * N + k];
+            }
+        }
+    double fact = 1.0;
+    for (int n = 1; n <= N; ++n) fact *= n;
+    rhs[(N - 1) * N + (N - 1)] = -sqrt(2.0 * M_PI) * pow(2.0, N) * fact;
+    /* Gaussian elimination with partial pivoting on the m x m system (in place) */
+    int st = OK;
+    for (int k = 0; k < m && st == OK; ++k) {
+        int p = k;
+        double best = fabs(K[(size_t)k * m + k]);
+        for (int i = k + 1; i < m; ++i)
+            if (fabs(K[(size_t)i * m + k]) > best) { best = fabs(K[(size_t)i * m + k]); p = i; }
+        if (best == 0.0) { st = E_NUMERIC; break; }
+        if (p != k) {
+            for (int j = 0; j < m; ++j) { double u = K[(size_t)k * m + j]; K[(size_t)k * m + j] = K[(size_t)p * m + j]; K[(size_t)p * m + j] = u; }
+            double u = rhs[k]; rhs[k] = rhs[p]; rhs[p] = u;
+        }
+        for (int i = k + 1; i < m; ++i) {
+            double f = K[(size_t)i * m + k] / K[(size_t)k * m + k];
+            if (f == 0.0) continue;
+            for (int j = k; j < m; ++j) K[(size_t)i * m + j] -= f * K[(size_t)k * m + j];
+            rhs[i] -= f * rhs[k];
+        }
+    }
+    for (int k = m - 1; k >= 0 && st == OK; --k) {
+        double v = rhs[k];
+        for (int j = k + 1; j < m; ++j) v -= K[(size_t)k * m + j] * x[j];
+        x[k] = v / K[(size_t)k * m + k];
+    }
+    for (int i = 0; i < m; ++i) P1[i] = x[i];
+    msym(N, P1);
+    free(K); free(rhs); free(x);
+    return st;
+}
+
 /* Modified Bessel function of the first kind I_j(x), by its power series
    sum_k (x/2)^(2k+j) / (k! (k+j)!). */
 static double bessel_i(int j, double x) {
@@ -315,6 +484,22 @@ static void om_pinf(const om_t* om, const double* th, double* Pinf, double* dPin
                         dPinf[(size_t)(po + 1) * b * b + (o + i) * b + o + j] = Pu[i * bc + j];
                     }
                 }
+        } else if (k == 6) {
+            int N = om->order[c];
+            double a1[16], P1[OB2];
+            eq_factor(N, a1);
+            eq_P1(N, a1, P1);
+            double ell = th[po], var = th[po + 1];
+            /* Pinf = var D P1 D with D = diag(l^-i): the scaling z = D z~ of time by l */
+            for (int i = 0; i < N; ++i)
+                for (int j = 0; j < N; ++j) {
+                    double dij = pow(ell, -(i + j));
+                    Pinf[(o + i) * b + o + j] = var * dij * P1[i * N + j];
+                    if (dPinf) {
+                        dPinf[(size_t)(po + 0) * b * b + (o + i) * b + o + j] = var * P1[i * N + j] * (-(i + j)) * dij / ell;
+                        dPinf[(size_t)(po + 1) * b * b + (o + i) * b + o + j] = dij * P1[i * N + j];
+                    }
+                }
         } else {
             int J = om->order[c];
             double q2[64], dq2[64], q2u[64];
@@ -360,6 +545,27 @@ static void om_transition(const om_t* om, const double* th, double dt, double* A
                     A[(o + i) * b + o + j] = Ac[i * bc + j];
                     if (dA) dA[(size_t)po * b * b + (o + i) * b + o + j] = dAc[i * bc + j] * dlam;
                 }
+        } else if (k == 6) {
+            /* expm(F dt) and its l-derivative: the upper-right block of
+               expm([[F, Fl], [0, F]] dt) (Van Loan 1978) */
+            int N = om->order[c], m = 2 * N;
+            double a1[16], F[OB2], Fl[OB2];
+            static double M[4 * OB2], E[4 * OB2];
+            eq_factor(N, a1);
+            eq_F(N, a1, th[po], F, Fl);
+            memset(M, 0, sizeof(double) * m * m);
+            for (int i = 0; i < N; ++i)
+                for (int j = 0; j < N; ++j) {
+                    M[i * m + j] = F[i * N + j] * dt;
+                    M[(i + N) * m + (j + N)] = F[i * N + j] * dt;
+                    M[i * m + (j + N)] = Fl[i * N + j] * dt;
+                }
+            expm_taylor(m, M, E);
+            for (int i = 0; i < N; ++i)
+                for (int j = 0; j < N; ++j) {
+                    A[(o + i) * b + o + j] = E[i * m + j];
+                    if (dA) dA[(size_t)po * b * b + (o + i) * b + o + j] = E[i * m + (j + N)];
+                }
         } else {
             int J = om->order[c];
             double per = th[po + 2], w = 2.0 * M_PI / per, dw = -2.0 * M_PI / (per * per);
@@ -395,7 +601,7 @@ static void om_H(const om_t* om, double* H) {
     memset(H, 0, sizeof(double) * om->b);
     for (int c = 0; c < om->ncomp; ++c) {
         int o = om->off[c], k = om->kind[c];
-        if (k <= 3) H[o] = 1.0;
+        if (k <= 3 || k == 6) H[o] = 1.0;
         else {
             int be = (k == 5) ? matern_b(om->env[c]) : 1;
             for (int j = 0; j <= om->order[c]; ++j) H[o + 2 * j * be] = 1.0;
@@ -441,6 +647,13 @@ static int check_inputs(const double* th, int P, const double* t, const double* 
 
 /* ---------------------------------------------------------------- exported: model pieces (for the pins) */
 
+/* The monic stable factor of the order-N approximation at l = 1 (pins). */
+int oseq_eq_factor(int N, double* a) {
+    if (N < 2 || N % 2 || N > 16 || !a) return E_INVAL;
+    eq_factor(N, a);
+    return OK;
+}
+
 int oseq_dims(int ncomp, const int* kind, const int* order, const int* env, int* b, int* P) {
     om_t om; int st = om_init(&om, ncomp, kind, order, env);
     if (st) return st;
@@ -466,6 +679,14 @@ int oseq_continuous(int ncomp, const int* kind, const int* order, const int* env
             matern_F(bc, lam, Fc, Fl);
             for (int i = 0; i < bc; ++i) for (int j = 0; j < bc; ++j) F[(o + i) * b + o + j] = Fc[i * bc + j];
             Lq[(o + bc - 1) * b + o + bc - 1] = th[po + 1] * matern_qc(bc, lam);
+        } else if (k == 6) {
+            int N = om.order[c];
+            double a1[16], Fc[OB2], fact = 1.0, ell = th[po];
+            eq_factor(N, a1);
+            eq_F(N, a1, ell, Fc, NULL);
+            for (int i = 0; i < N; ++i) for (int j = 0; j < N; ++j) F[(o + i) * b + o + j] = Fc[i * N + j];
+            for (int n = 1; n <= N; ++n) fact *= n;
+            Lq[(o + N - 1) * b + o + N - 1] = th[po + 1] * sqrt(2.0 * M_PI) * ell * pow(2.0, N) * fact / pow(ell, 2 * N);
         } else {
             int J = om.order[c];
             double w = 2.0 * M_PI / th[po + 2];

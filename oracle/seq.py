@@ -53,8 +53,9 @@ def bind(path):
     lib.oseq_smoother.argtypes = [ctypes.c_int, I, I, I, D, D, D, L, D, D, D, D, D, D]
     lib.oseq_grad.argtypes = [ctypes.c_int, I, I, I, D, D, D, L, D, D, D, D, D]
     lib.oseq_sample.argtypes = [ctypes.c_int, I, I, I, D, D, L, D, D]
+    lib.oseq_eq_factor.argtypes = [ctypes.c_int, D]
     for f in ("oseq_dims", "oseq_continuous", "oseq_discretize", "oseq_loglik",
-              "oseq_smoother", "oseq_grad", "oseq_sample"):
+              "oseq_smoother", "oseq_grad", "oseq_sample", "oseq_eq_factor"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -167,6 +168,15 @@ def grad(spec, theta, t, y, posterior=False, l1=False):
     if l1:
         out = out + (gabs,)
     return out
+
+
+def eq_factor(N):
+    """Coefficients a_0 .. a_{N-1} of the monic stable spectral factor of the
+    order-N exponentiated-quadratic approximation at unit lengthscale."""
+    lib = _load()
+    a = np.zeros(N)
+    _check(lib.oseq_eq_factor(int(N), _dp(a)))
+    return a
 
 
 def sample(spec, theta, t, eps):

@@ -34,6 +34,10 @@ C_MUTANTS = [
      "term *= h * h / ((double)k * (double)(k + j + 1));"),
     ("RTS gain transposed", "for (int r = 0; r < b; ++r) for (int c = 0; c < b; ++c) G[r * b + c] = Gt[c * b + r];",
      "for (int r = 0; r < b; ++r) for (int c = 0; c < b; ++c) G[r * b + c] = Gt[r * b + c];"),
+    ("EQ noise intensity drops sqrt(2 pi)", "rhs[(N - 1) * N + (N - 1)] = -sqrt(2.0 * M_PI) * pow(2.0, N) * fact;",
+     "rhs[(N - 1) * N + (N - 1)] = -pow(2.0, N) * fact;"),
+    ("EQ time-scaling exponent", "F[(N - 1) * N + k] = -a1[k] * pow(ell, k - N);",
+     "F[(N - 1) * N + k] = -a1[k] * pow(ell, k - N + 1);"),
     ("first-step prior dropped", "memset(mb, 0, sizeof(double) * b); mcopy(b, Pinf, Pb); }",
      "memset(mb, 0, sizeof(double) * b); meye(b, Pb); }"),
 ]
