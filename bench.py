@@ -169,7 +169,8 @@ def _time_calls(fn, K, flush, torch):
 
 def extra_workloads(args, dev, flush, world, rank=0):
     """loglik + gradient throughput of the other configurations: the b = 16
-    sum (Matern-3/2 + quasi-periodic), the batch of 4096 independent series of
+    sum (Matern-3/2 + quasi-periodic), the paper's own b = 12 timing model
+    (Matern-3/2 + the order-10 EQ approximation), the batch of 4096 independent series of
     uneven length, and the N = 2^26 Matern-3/2 series; each with its own
     launch count and, for the batch, the plain GPU form (forward kernel run
     2P+1 times per series, one launch sequence per series).  With several
@@ -190,7 +191,7 @@ def extra_workloads(args, dev, flush, world, rank=0):
 
     K = max(3, min(args.steps, 5))
     res = {}
-    for name in ("sum_qp_n1m", "matern32_n64m"):
+    for name in ("sum_qp_n1m", "m32_eq10_n1m", "matern32_n64m"):
         s = synth.single(name)
         T, Y, TH = (torch.tensor(a, device=dev) for a in (s.t, s.y, s.theta))
         m = spingp.Model(s.spec)

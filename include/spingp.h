@@ -60,13 +60,25 @@ typedef enum {
  *       (Eq. ss_matern gives the 3/2 case).
  *   PERIODIC (order J): (variance, lengthscale, period); state dim 2(J+1).
  *   QUASIPERIODIC (order J, Matern envelope): (variance, lengthscale, period,
- *       envelope lengthscale); state dim 2(J+1) x envelope dim (Eq. co2_1). */
+ *       envelope lengthscale); state dim 2(J+1) x envelope dim (Eq. co2_1).
+ *   EQ (order N, even, 2..16): (lengthscale, variance); state dim N.  The
+ *       exponentiated quadratic s exp(-t^2/(2 l^2)) through its state-space
+ *       approximation (Sec. 2.1; the paper's experiments use N = 10): the
+ *       spectral density with exp(l^2 w^2/2) replaced by its Taylor
+ *       polynomial of order N, whose stable spectral factor is an SDE of
+ *       order N (Hartikainen & Sarkka 2010).  The library works in real modal
+ *       coordinates (N/2 damped rotations).  The approximation error against
+ *       the exact covariance falls with N (below 2e-4 s at N = 10); the
+ *       state space is ill-conditioned at higher orders (at N = 10 its modal
+ *       variances reach ~1e6 s against f's s), which limits every result
+ *       to about 1e-10 relative.  At most one EQ component per model. */
 typedef enum {
     SPINGP_MATERN12 = 1,
     SPINGP_MATERN32 = 2,
     SPINGP_MATERN52 = 3,
     SPINGP_PERIODIC = 4,
-    SPINGP_QUASIPERIODIC = 5
+    SPINGP_QUASIPERIODIC = 5,
+    SPINGP_EQ = 6
 } spingp_kind;
 
 typedef struct {

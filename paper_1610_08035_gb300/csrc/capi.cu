@@ -58,9 +58,18 @@ int64_t default_chunk(int64_t n) {
 
 int64_t default_group_chunk(int64_t n);
 
+// An EQ component of order >= 8 is ill-conditioned in the modal coordinates
+// of the group path (its modal variances cancel to f's by ~7 digits), and
+// short chunks carry rank-deficient information about their entry state:
+// the default keeps its chunks at least this long.
+static constexpr int64_t EQ_MIN_CHUNK = 64;
+
 int64_t chunk_len(const spingp_model* m, int64_t n) {
     if (m->chunk_len > 0) return (int64_t)m->chunk_len;
-    return m->group ? default_group_chunk(n) : default_chunk(n);
+    if (!m->group) return default_chunk(n);
+    int64_t L = default_group_chunk(n);
+    if (m->gm.eq_nk >= 4 && L < EQ_MIN_CHUNK) L = EQ_MIN_CHUNK;
+    return L;
 }
 
 bool single_matern(const spingp_model* m) { return m->ncomp == 1 && m->kinds[0] >= 1 && m->kinds[0] <= 3; }
@@ -70,6 +79,7 @@ bool single_matern(const spingp_model* m) { return m->ncomp == 1 && m->kinds[0] 
 bool build_group(spingp_model* m) {
     spg::GModel g;
     memset(&g, 0, sizeof(g));
+    g.eq_comp = -1;
     if (m->ncomp > spg::GMAXCOMP) return false;
     int K = 0, P = 0;
     for (int c = 0; c < m->ncomp; ++c) {
@@ -80,6 +90,16 @@ bool build_group(spingp_model* m) {
         if (k == SPINGP_MATERN32) { nb = 1; kind = 0; P += 2; }
         else if (k == SPINGP_PERIODIC) { nb = m->orders[c] + 1; kind = 1; P += 3; }
         else if (k == SPINGP_QUASIPERIODIC && m->envs[c] == SPINGP_MATERN12) { nb = m->orders[c] + 1; kind = 2; P += 4; }
+        else if (k == SPINGP_EQ) {
+            if (g.eq_nk > 0) return false;                     // one EQ component
+            const int N = m->orders[c];
+            nb = N / 2; kind = 3; P += 2;
+            if (K + nb > spg::GMAXBLK) return false;
+            double a[8], b[8];
+            if (!spg::eq_modal(N, a, b, g.eqP, 16)) return false;
+            g.eq_comp = c; g.eq_k0 = K; g.eq_nk = nb;
+            for (int j = 0; j < nb; ++j) { g.eqa[K + j] = a[j]; g.eqb[K + j] = b[j]; }
+        }
         else return false;
         for (int j = 0; j < nb; ++j) {
             if (K >= spg::GMAXBLK) return false;
@@ -237,6 +257,9 @@ spingp_status spingp_model_create(const spingp_model_desc* d, spingp_model** out
         else if (k == SPINGP_QUASIPERIODIC) {
             if (J < 0 || J > 64 || env < SPINGP_MATERN12 || env > SPINGP_MATERN52) return SPINGP_EINVAL;
             m.b += 2 * (J + 1) * matern_dim(env); m.P += 4;
+        } else if (k == SPINGP_EQ) {
+            if (J < 2 || J > 16 || (J & 1)) return SPINGP_EINVAL;
+            m.b += J; m.P += 2;
         } else return SPINGP_EINVAL;
     }
     m.P += 1;

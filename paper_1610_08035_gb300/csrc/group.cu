@@ -1,12 +1,17 @@
 // group.cu -- the hot path for structured state spaces built from 2x2 blocks:
-// sums of Matern-3/2, periodic (order J) and quasi-periodic (order J with a
-// Matern-1/2 envelope) components, state dimension b = 2K <= 16 (Sec. 2.1;
-// the quasi-periodic family is Eq. co2_1's periodicity term).
+// sums of Matern-3/2, periodic (order J), quasi-periodic (order J with a
+// Matern-1/2 envelope) and exponentiated-quadratic (even order N, in real
+// modal coordinates) components, state dimension b = 2K <= 16 (Sec. 2.1; the
+// quasi-periodic family is Eq. co2_1's periodicity term, the EQ
+// approximation the one of the paper's experiments).
 //
 // Structure exploited: the transition A_n = blockdiag(Phi_1 .. Phi_K) is block
-// diagonal with 2x2 blocks (a Matern-3/2 block in scaled coordinates, or a
-// rotation by j w dt, damped by the envelope), Pinf is diagonal, and H picks
-// the first coordinate of every block.  The posterior covariance is dense, so
+// diagonal with 2x2 blocks (a Matern-3/2 block in scaled coordinates, a
+// rotation by j w dt damped by the envelope, or an EQ pole pair's damped
+// rotation exp(a x) R(b x), x = dt / l), and H picks the first coordinate of
+// every block.  Pinf is diagonal except on an EQ component's block, where it
+// is the dense modal covariance s P_m; each CTA keeps the whole Pinf in
+// shared memory.  The posterior covariance is dense, so
 // the Kalman and adjoint recursions run on a group of 16 lanes per chunk: lane
 // c owns column c of every b x b matrix.  Left products with the block
 // diagonal Phi are then local to a lane, right products need the partner
@@ -43,11 +48,33 @@ static constexpr double G_LOG_2PI = 1.8378770664093454836;
 static constexpr double G_LN2 = 0.69314718055994530942;
 
 // block kinds
-enum { GB_MATERN32 = 0, GB_PERIODIC = 1, GB_QUASI = 2 };
+enum { GB_MATERN32 = 0, GB_PERIODIC = 1, GB_QUASI = 2, GB_EQ = 3 };
 
 // per-chunk partial sums: ll, noise, per component (rate, envelope rate), then
-// the diagonal of the Pinf adjoint for every state (lane)
-static constexpr int GPART = 2 + 2 * GMAXCOMP + GL;
+// the diagonal of the Pinf adjoint for every state (lane), then the adjoint
+// contracted with an EQ component's P_m (its variance derivative)
+static constexpr int GPART = 2 + 2 * GMAXCOMP + GL + 1;
+static constexpr int GP_EQ = 2 + 2 * GMAXCOMP + GL;
+
+// Pinf (b x b, row-major, zero-padded to GL x GL) and, for an EQ component,
+// dPinf / d(its variance) = P_m on its block: built by each CTA in shared
+// memory from the per-block weights and the model constants.
+__device__ __forceinline__ void g_pinf_smem(const GModel& gm, const double* __restrict__ theta,
+                                            const double* __restrict__ gconst, double* s_pinf, double* s_dpe) {
+    const double veq = (gm.eq_nk > 0) ? theta[gm.cpoff[gm.eq_comp] + 1] : 0.0;
+    const int o = 2 * gm.eq_k0, ne = 2 * gm.eq_nk;
+    for (int idx = threadIdx.x; idx < GL * GL; idx += blockDim.x) {
+        const int r = idx / GL, c = idx % GL;
+        double v = (r == c && r < gm.b) ? gconst[(r >> 1) * GNC] : 0.0;
+        double d = 0.0;
+        if (r >= o && r < o + ne && c >= o && c < o + ne) {
+            d = gm.eqP[(r - o) * 16 + (c - o)];
+            v += veq * d;
+        }
+        s_pinf[idx] = v;
+        s_dpe[idx] = d;
+    }
+}
 
 __device__ __forceinline__ unsigned half_mask() { return (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu; }
 
@@ -96,6 +123,8 @@ __global__ void k_gsetup(GModel gm, const double* __restrict__ theta, double* __
     double w = 0.0, dwv = 0.0, dwl = 0.0;
     if (gm.bkind[k] == GB_MATERN32) {
         w = th[1]; dwv = 1.0; dwl = 0.0;
+    } else if (gm.bkind[k] == GB_EQ) {
+        w = 0.0; dwv = 0.0; dwl = 0.0;   // dense modal Pinf: g_pinf_smem
     } else {
         const int j = gm.bj[k];
         const double var = th[0], lp = th[1];
@@ -135,6 +164,13 @@ __global__ void __launch_bounds__(256) k_gdisc(GModel gm, const double* __restri
                 double P[2][2];
                 phi<2>(lam * dt, exp(-lam * dt), P);
                 p00 = P[0][0]; p01 = P[0][1]; p10 = P[1][0]; p11 = P[1][1];
+            } else if (gm.bkind[k] == GB_EQ) {
+                // expm([[a, b], [-b, a]] x) = e^(a x) [[cos bx, sin bx], [-sin bx, cos bx]], x = dt / l
+                const double x = dt / th[0];
+                double sn, cs;
+                sincos(gm.eqb[k] * x, &sn, &cs);
+                const double e = exp(gm.eqa[k] * x);
+                p00 = e * cs; p01 = e * sn; p10 = -e * sn; p11 = e * cs;
             } else {
                 const double w = 2.0 * M_PI / th[2];
                 double sn, cs;
@@ -512,13 +548,17 @@ struct GArgs {
 };
 
 __global__ void __launch_bounds__(GCTA) k_gfold(GArgs a, double* __restrict__ nodes) {
+    __shared__ double s_pinf[GL * GL], s_dpe[GL * GL];
+    g_pinf_smem(a.gm, a.theta, a.gconst, s_pinf, s_dpe);
+    __syncthreads();
     const int lane = threadIdx.x & (GL - 1);
     const int64_t c = blockIdx.x * (int64_t)GGRP + (threadIdx.x >> 4);
     if (c >= a.nc) return;   // the whole group leaves together
     const bool on = lane < a.gm.b;
-    const bool even = (lane & 1) == 0;
     const double s2 = a.theta[a.gm.P - 1];
-    const double pw = on ? a.gconst[(lane >> 1) * GNC] : 0.0;   // Pinf[lane][lane]
+    double ph = 0.0;         // (Pinf h)[lane]
+#pragma unroll
+    for (int r = 0; r < GL; r += 2) ph += s_pinf[r * GL + lane];
     const int64_t s = c * a.L, e = min(a.n, s + a.L);
     GElem el;
     double Cm[GL];   // C - Pinf, column lane
@@ -526,7 +566,7 @@ __global__ void __launch_bounds__(GCTA) k_gfold(GArgs a, double* __restrict__ no
     for (int r = 0; r < GL; ++r) {
         el.A[r] = (s > 0 && r == lane && on) ? 1.0 : 0.0;
         el.J[r] = 0.0;
-        Cm[r] = (s > 0 && r == lane) ? -pw : 0.0;
+        Cm[r] = (s > 0) ? -s_pinf[r * GL + lane] : 0.0;
     }
     el.bv = 0.0;
     el.eta = 0.0;
@@ -540,11 +580,11 @@ __global__ void __launch_bounds__(GCTA) k_gfold(GArgs a, double* __restrict__ no
             g_right_t(ph, lane, Cm);
         }
         if (a.missing && isnan(yi)) continue;               // missing: no update (Eqs. mean4-mean6)
-        const double c0 = g_hsum(Cm) + (even ? pw : 0.0);   // (C h)[lane]
+        const double c0 = g_hsum(Cm) + ph;                  // (C h)[lane]
         const double a0 = g_hsum(el.A);                      // (h^T A)[lane]
-        const double S = s2 + gsum(even ? c0 : 0.0);
+        const double S = s2 + gsum(((lane & 1) == 0) ? c0 : 0.0);
         const double rS = 1.0 / S;
-        const double res = yi - gsum(even ? el.bv : 0.0);
+        const double res = yi - gsum(((lane & 1) == 0) ? el.bv : 0.0);
         const double rr = res * rS;
         el.eta = fma(a0, rr, el.eta);
         double v[GL];
@@ -562,7 +602,7 @@ __global__ void __launch_bounds__(GCTA) k_gfold(GArgs a, double* __restrict__ no
         }
     }
 #pragma unroll
-    for (int r = 0; r < GL; ++r) el.C[r] = Cm[r] + ((r == lane) ? pw : 0.0);
+    for (int r = 0; r < GL; ++r) el.C[r] = Cm[r] + s_pinf[r * GL + lane];
     gelem_store(nodes, a.nc, c, lane, el);
 }
 
@@ -641,15 +681,20 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
     constexpr bool GRAD = (MODE == MODE_GRAD);
     constexpr bool POST = (MODE == MODE_POSTERIOR);
     __shared__ GSmem sm[GGRP];
+    __shared__ double s_pinf[GL * GL], s_dpe[GL * GL];
+    g_pinf_smem(a.gm, a.theta, a.gconst, s_pinf, s_dpe);
+    __syncthreads();
     const int lane = threadIdx.x & (GL - 1);
     const int g = threadIdx.x >> 4;
     const int64_t c = blockIdx.x * (int64_t)GGRP + g;
     if (c >= a.nc) return;
     const int64_t nc = a.nc;
-    const bool on = lane < a.gm.b;
     const bool even = (lane & 1) == 0;
+    const bool has_eq = a.gm.eq_nk > 0;
     const double s2 = a.theta[a.gm.P - 1];
-    const double pw = on ? a.gconst[(lane >> 1) * GNC] : 0.0;
+    double ph = 0.0;   // (Pinf h)[lane]
+#pragma unroll
+    for (int r = 0; r < GL; r += 2) ph += s_pinf[r * GL + lane];
     const int64_t s = c * a.L, e = min(a.n, s + a.L);
     int bad = 0;
 
@@ -659,7 +704,7 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
         double P[GL];
         gvs_load(pre, nc, c, lane, P, m);
 #pragma unroll
-        for (int r = 0; r < GL; ++r) D[r] = P[r] - ((r == lane) ? pw : 0.0);
+        for (int r = 0; r < GL; ++r) D[r] = P[r] - s_pinf[r * GL + lane];
     }
     double quad = 0.0, prod = 1.0;
     int expo = 0;
@@ -681,7 +726,7 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
             g_left(ph, Db);
             g_right_t(ph, lane, Db);
         }
-        const double p0 = g_hsum(Db) + (even ? pw : 0.0);
+        const double p0 = g_hsum(Db) + ph;
         // a missing observation stores v = 1/S = 0, so the reverse sweep passes through it
         double rS = 0.0, v = 0.0;
         if (obs) {
@@ -723,7 +768,7 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
             double J[GL], eta, P[GL], W[GL], v[GL];
             gvs_load(suf, nc, c, lane, J, eta);
 #pragma unroll
-            for (int r = 0; r < GL; ++r) P[r] = D[r] + ((r == lane) ? pw : 0.0);
+            for (int r = 0; r < GL; ++r) P[r] = D[r] + s_pinf[r * GL + lane];
             g_inv_ixy(sm[g], lane, J, P, W);            // (I + J P)^-1
             ggather(m, v);
             double w = eta;
@@ -737,6 +782,7 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
             g_sym(sm[g], lane, Lh);
         }
         double gp = 0.0;   // diagonal entry 'lane' of the Pinf adjoint
+        double geq = 0.0;  // column 'lane' of the Pinf adjoint contracted with the EQ block's P_m
         for (int64_t i = e - 1; i >= s; --i) {
             const int64_t j = i - s;
             const double* st = store + ((j * nc + c) * GNF) * GL + lane;
@@ -746,7 +792,7 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
             const double mb = st[GL * GL];
             const double v = st[(GL + 1) * GL];
             const double rS = st[(GL + 2) * GL];
-            const double k = (g_hsum(Db) + (even ? pw : 0.0)) * rS;
+            const double k = (g_hsum(Db) + ph) * rS;
             const double kl = gsum(k * lh);
             double kv[GL];
             ggather(k, kv);
@@ -763,7 +809,7 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                 const double yi = a.y[i];
                 if (a.missing && isnan(yi)) {
                     // predicted only: mean = h^T (mb - Pb lh), variance = h^T Pb h - (Pb h)^T Lh (Pb h)
-                    const double p0 = g_hsum(Db) + (even ? pw : 0.0);
+                    const double p0 = g_hsum(Db) + ph;
                     double pv[GL];
                     ggather(p0, pv);
                     double lp = 0.0;
@@ -802,6 +848,10 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
 #pragma unroll
                 for (int r = 0; r < GL; ++r)
                     if (r == lane) gp += G[r];
+                if (has_eq) {
+#pragma unroll
+                    for (int r = 0; r < GL; ++r) geq = fma(s_dpe[r * GL + lane], G[r], geq);
+                }
             }
             if (i > 0) {
                 const double* ph = a.phis + i * (4 * GK);
@@ -823,6 +873,11 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                             // X = [[0, 1], [-1, -2]]
                             rate = 2.0 * (g0 * d1 + g1 * (-d0 - 2.0 * d1));
                             if (mine) rate -= lt * (even ? mb1 : (-mb0 - 2.0 * mb1));
+                        } else if (kind == GB_EQ) {
+                            // X = [[a, b], [-b, a]] per unit of x = dt / l (rate 1 / l)
+                            const double ea = a.gm.eqa[kb], eb = a.gm.eqb[kb];
+                            rate = 2.0 * (g0 * fma(ea, d0, eb * d1) + g1 * fma(-eb, d0, ea * d1));
+                            if (mine) rate -= lt * (even ? fma(ea, mb0, eb * mb1) : fma(-eb, mb0, ea * mb1));
                         } else {
                             // X = j [[0, -1], [1, 0]] (rotation rate w); envelope X = -I
                             const double jj = (double)a.gm.bj[kb];
@@ -853,10 +908,22 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                     for (int r = 0; r < GL; ++r)
                         if (r == lane) ld = Lh[r];
                     gp -= 0.5 * fma(lh, lh, -ld);
+                    if (has_eq) {   // minus column 'lane' of Phi^T G Phi = (lh lh^T - Lh) / 2
+                        double lv2[GL];
+                        ggather(lh, lv2);
+                        double t = 0.0;
+#pragma unroll
+                        for (int r = 0; r < GL; ++r) t = fma(s_dpe[r * GL + lane], fma(lv2[r], lh, -Lh[r]), t);
+                        geq -= 0.5 * t;
+                    }
                 }
             }
         }
-        if constexpr (GRAD) part[(2 + 2 * GMAXCOMP + lane) * nc + c] = gp;
+        if constexpr (GRAD) {
+            part[(2 + 2 * GMAXCOMP + lane) * nc + c] = gp;
+            geq = gsum(geq);
+            if (lane == 0) part[GP_EQ * nc + c] = geq;
+        }
     }
     if (bad) atomicOr(a.status, bad);
     // per-chunk partials: group sums for the scalar slots, per-lane for the Pinf diagonal
@@ -902,6 +969,9 @@ __global__ void __launch_bounds__(GFIN) k_gfinal(GModel gm, const double* __rest
         if (gm.ckind[q] == SPINGP_MATERN32) {
             const double lam = sqrt(3.0) / th[0];
             g[0] = rate * (-lam / th[0]);
+        } else if (gm.ckind[q] == SPINGP_EQ) {
+            g[0] = rate * (-1.0 / (th[0] * th[0]));           // rate 1 / l
+            g[1] = tot[GP_EQ];                                 // dPinf / d variance = P_m
         } else {
             const double per = th[2];
             g[2] = rate * (-2.0 * M_PI / (per * per));            // d w / d period
@@ -910,6 +980,7 @@ __global__ void __launch_bounds__(GFIN) k_gfinal(GModel gm, const double* __rest
     }
     // Pinf entries: block k is w_k I2
     for (int k = 0; k < gm.K; ++k) {
+        if (gm.bkind[k] == GB_EQ) continue;                   // handled with its component
         const int q = gm.bcomp[k];
         const double gk = tot[2 + 2 * GMAXCOMP + 2 * k] + tot[2 + 2 * GMAXCOMP + 2 * k + 1];
         double* g = grad_out + gm.cpoff[q];

@@ -16,7 +16,16 @@ struct GModel {
     int b, K, P, ncomp;
     int bkind[GMAXBLK], bcomp[GMAXBLK], bj[GMAXBLK];   // per block: kind, component, harmonic
     int ckind[GMAXCOMP], cpoff[GMAXCOMP];              // per component: spingp_kind, theta offset
+    // an exponentiated-quadratic component in real modal coordinates (at most
+    // one): its first block and block count, the block generators
+    // [[a, b], [-b, a]] at unit lengthscale, and its unit-variance stationary
+    // covariance P_m (order x order, row stride 16; Pinf = variance P_m)
+    int eq_comp, eq_k0, eq_nk;
+    double eqa[GMAXBLK], eqb[GMAXBLK];
+    double eqP[16 * 16];
 };
+// host: modal constants of the order-N EQ approximation (eqmodal.cu)
+bool eq_modal(int N, double* a, double* b, double* Pm, int ld);
 
 // device status bits (the status word at the start of every workspace)
 enum { ST_EINVAL = 1 << 1, ST_ENOTSORTED = 1 << 2, ST_ENONFINITE = 1 << 3, ST_ENUMERIC = 1 << 4 };

@@ -18,7 +18,7 @@ WS_LOGLIK, WS_GRAD, WS_POSTERIOR = 0, 1, 2
 SYNC = 1
 MISSING_NAN = 2
 
-KINDS = {"matern12": 1, "matern32": 2, "matern52": 3, "periodic": 4, "quasiperiodic": 5}
+KINDS = {"matern12": 1, "matern32": 2, "matern52": 3, "periodic": 4, "quasiperiodic": 5, "eq": 6}
 
 # names exported by the library, in the order of include/spingp.h
 EXPORTS = ("spingp_model_create", "spingp_model_destroy", "spingp_num_params", "spingp_state_dim",
@@ -144,7 +144,7 @@ def _dev_f64(x, name):
 
 def spingp_model_create(spec):
     """spec: a list of components, each "matern12" | "matern32" | "matern52" |
-    ("periodic", J) | ("quasiperiodic", J, envelope)."""
+    ("periodic", J) | ("quasiperiodic", J, envelope) | ("eq", N) (N even)."""
     lib = load()
     if isinstance(spec, (str, tuple)):
         spec = [spec]

@@ -64,6 +64,9 @@ SINGLE = {
                    [1.0, 1.0, 1.0, 1.0, 1.0, 10.0, 0.01], 1 << 20, 0.01, 2),
     # Matern-3/2, b=2, N=2^26, dt ~ Exp(0.001), l=0.05, s_f=1, s_n=0.1
     "matern32_n64m": (["matern32"], [0.05, 1.0, 0.1], 1 << 26, 0.001, 4),
+    # the paper's timing model (Sec. 4.2): Matern-3/2 + EQ of order 10, b=12,
+    # N=2^20, dt ~ Exp(0.01); Matern l=1, s=1; EQ l=0.5, s=1; s_n=0.1
+    "m32_eq10_n1m": (["matern32", ("eq", 10)], [1.0, 1.0, 0.5, 1.0, 0.1], 1 << 20, 0.01, 5),
 }
 
 

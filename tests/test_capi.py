@@ -80,3 +80,16 @@ def test_entry_points_reject_null_arguments_without_launching(lib):
 def test_status_strings(lib):
     for st in range(9):
         assert isinstance(spingp.spingp_status_str(st), str) and spingp.spingp_status_str(st)
+
+
+def test_eq_model_creation_host_only():
+    """EQ models are built on the host (modal constants at model creation):
+    dimensions, parameter counts and the rejected forms, without a GPU."""
+    from paper_1610_08035_gb300 import spingp
+    m = spingp.Model(["matern32", ("eq", 10)])
+    assert (m.state_dim, m.num_params) == (12, 5)
+    for N in (2, 4, 6, 8, 10, 12, 14, 16):
+        assert spingp.Model([("eq", N)]).state_dim == N
+    for bad in ([("eq", 5)], [("eq", 0)], [("eq", 18)], ["matern32", ("eq", 16)], [("eq", 4), ("eq", 6)]):
+        with pytest.raises(spingp.SpinGPError):
+            spingp.Model(bad)
