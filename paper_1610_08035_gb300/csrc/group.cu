@@ -608,63 +608,255 @@ __global__ void __launch_bounds__(GCTA) k_gfold(GArgs a, double* __restrict__ no
 
 // ------------------------------------------------------------------ odd-even reduction, level by level
 
-// level l from level l-1: node j = (2j) then (2j+1), or a copy of 2j at the end
-__global__ void __launch_bounds__(GCTA) k_gscan_up(const double* __restrict__ lo, int64_t nlo,
-                                                   double* __restrict__ hi, int64_t nhi) {
-    __shared__ GSmem sm[GGRP];
-    const int lane = threadIdx.x & (GL - 1);
-    const int g = threadIdx.x >> 4;
-    const int64_t j = blockIdx.x * (int64_t)GGRP + g;
-    if (j >= nhi) return;
-    GElem x, y, r;
-    gelem_load(lo, nlo, 2 * j, lane, x);
-    if (2 * j + 1 < nlo) {
-        gelem_load(lo, nlo, 2 * j + 1, lane, y);
-        g_combine(sm[g], lane, x, y, r);
-        gelem_store(hi, nhi, j, lane, r);
-    } else {
-        gelem_store(hi, nhi, j, lane, x);
+// Each node of a level is one CTA of 256 threads, thread (r, c) holding entry
+// (r, c) of every 16 x 16 matrix in shared memory: a product is 16 FMAs per
+// thread, so a level costs about one node's dependent chain of ~10 products
+// and a 16-step elimination, whatever its width (the reduction's upper
+// levels have few nodes, and a lane group per node would issue 256 FMAs per
+// lane per product).  The arithmetic is g_combine / g_state_through /
+// g_info_through's: the same products, the same pivoting, the same
+// symmetrisation.
+static constexpr int GSC = GL * GL;   // threads per node
+
+struct GScanSmem {
+    double A[GSC], C[GSC], J[GSC];    // the element (or, down-sweep, the sibling)
+    double A2[GSC], C2[GSC], J2[GSC]; // the second element (up-sweep)
+    double S[GSC];                    // a state's P or an information's J (down-sweep)
+    double N[GSC], M[GSC], T[GSC], U[GSC];
+    double bv[GL], eta[GL], bv2[GL], eta2[GL], v[GL], w[GL], z[GL];
+    int piv;
+};
+
+__device__ __forceinline__ void gc_load_elem(const double* __restrict__ base, int64_t ne, int64_t e, double* A,
+                                             double* C, double* J, double* bv, double* eta) {
+    const int t = threadIdx.x, r = t >> 4, c = t & 15;
+    const double* p = base + e * GL + c;
+    const int64_t st = ne * GL;
+    A[t] = p[r * st];
+    C[t] = p[(GL + r) * st];
+    J[t] = p[(2 * GL + r) * st];
+    if (r == 0) { bv[c] = p[3 * GL * st]; eta[c] = p[(3 * GL + 1) * st]; }
+}
+__device__ __forceinline__ void gc_store_elem(double* __restrict__ base, int64_t ne, int64_t e, const double* A,
+                                              const double* C, const double* J, const double* bv,
+                                              const double* eta) {
+    const int t = threadIdx.x, r = t >> 4, c = t & 15;
+    double* p = base + e * GL + c;
+    const int64_t st = ne * GL;
+    p[r * st] = A[t];
+    p[(GL + r) * st] = C[t];
+    p[(2 * GL + r) * st] = J[t];
+    if (r == 0) { p[3 * GL * st] = bv[c]; p[(3 * GL + 1) * st] = eta[c]; }
+}
+__device__ __forceinline__ void gc_load_vs(const double* __restrict__ base, int64_t ne, int64_t e, double* S,
+                                           double* v) {
+    const int t = threadIdx.x, r = t >> 4, c = t & 15;
+    const double* p = base + e * GL + c;
+    const int64_t st = ne * GL;
+    S[t] = p[r * st];
+    if (r == 0) v[c] = p[GL * st];
+}
+__device__ __forceinline__ void gc_store_vs(double* __restrict__ base, int64_t ne, int64_t e, const double* S,
+                                            const double* v) {
+    const int t = threadIdx.x, r = t >> 4, c = t & 15;
+    double* p = base + e * GL + c;
+    const int64_t st = ne * GL;
+    p[r * st] = S[t];
+    if (r == 0) p[GL * st] = v[c];
+}
+
+// out[r][c] = sum_k X[r][k] Y[k][c]  (TX: X^T, TY: Y^T); returns this thread's entry
+template <bool TX, bool TY>
+__device__ __forceinline__ double gc_mm(const double* X, const double* Y) {
+    const int r = threadIdx.x >> 4, c = threadIdx.x & 15;
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < GL; ++k) s = fma(TX ? X[k * GL + r] : X[r * GL + k], TY ? Y[c * GL + k] : Y[k * GL + c], s);
+    return s;
+}
+// out[i] = sum_k X[i][k] x[k] (TX: X^T), threads i < 16
+template <bool TX>
+__device__ __forceinline__ double gc_mv(const double* X, const double* x) {
+    const int i = threadIdx.x;
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < GL; ++k) s = fma(TX ? X[k * GL + i] : X[i * GL + k], x[k], s);
+    return s;
+}
+
+// M = (I + X Y)^-1 by Gauss-Jordan with partial pivoting (the rule of
+// g_inv_ixy: the first largest |N[r][k]|, r >= k); X, Y, M in shared memory
+__device__ void gc_inv_ixy(GScanSmem& s, const double* X, const double* Y) {
+    const int t = threadIdx.x, r = t >> 4, c = t & 15;
+    s.N[t] = gc_mm<false, false>(X, Y) + ((r == c) ? 1.0 : 0.0);
+    s.M[t] = (r == c) ? 1.0 : 0.0;
+    __syncthreads();
+#pragma unroll 1
+    for (int k = 0; k < GL; ++k) {
+        if (t == 0) {
+            int p = k;
+            double best = fabs(s.N[k * GL + k]);
+            for (int i = k + 1; i < GL; ++i) {
+                const double v = fabs(s.N[i * GL + k]);
+                if (v > best) { best = v; p = i; }
+            }
+            s.piv = p;
+        }
+        __syncthreads();
+        const int p = s.piv;
+        if (p != k && t < 2 * GL) {
+            double* X2 = (t < GL) ? s.N : s.M;
+            const int cc = t & 15;
+            const double u = X2[k * GL + cc];
+            X2[k * GL + cc] = X2[p * GL + cc];
+            X2[p * GL + cc] = u;
+        }
+        __syncthreads();
+        const double inv = 1.0 / s.N[k * GL + k];
+        const double f = s.N[r * GL + k];
+        const double nk = s.N[k * GL + c] * inv, mk = s.M[k * GL + c] * inv;
+        __syncthreads();
+        if (r == k) {
+            s.N[t] = nk;
+            s.M[t] = mk;
+        } else {
+            s.N[t] = fma(-f, nk, s.N[t]);
+            s.M[t] = fma(-f, mk, s.M[t]);
+        }
+        __syncthreads();
     }
 }
 
-// back-substitution from level l (parents) to level l-1 (children): prefix
-// state before each child and the information after it
-__global__ void __launch_bounds__(GCTA) k_gscan_down(const double* __restrict__ lo, int64_t nlo,
-                                                     const double* __restrict__ ppre, const double* __restrict__ psuf,
-                                                     int64_t nhi, double* __restrict__ cpre,
-                                                     double* __restrict__ csuf) {
-    __shared__ GSmem sm[GGRP];
-    const int lane = threadIdx.x & (GL - 1);
-    const int g = threadIdx.x >> 4;
-    const int64_t j = blockIdx.x * (int64_t)GGRP + g;
-    if (j >= nlo) return;
-    double P[GL], m, J[GL], eta;
-    const int64_t parent = j >> 1;
-    if (ppre) {
-        gvs_load(ppre, nhi, parent, lane, P, m);
-        gvs_load(psuf, nhi, parent, lane, J, eta);
-    } else {
-#pragma unroll
-        for (int r = 0; r < GL; ++r) { P[r] = 0.0; J[r] = 0.0; }
-        m = 0.0; eta = 0.0;
+// level l from level l-1: node j = (2j) then (2j+1), or a copy of 2j at the end
+__global__ void __launch_bounds__(GSC) k_gscan_up(const double* __restrict__ lo, int64_t nlo,
+                                                  double* __restrict__ hi, int64_t nhi) {
+    __shared__ GScanSmem s;
+    const int t = threadIdx.x, r = t >> 4, c = t & 15;
+    const int64_t j = blockIdx.x;
+    if (j >= nhi) return;
+    gc_load_elem(lo, nlo, 2 * j, s.A, s.C, s.J, s.bv, s.eta);
+    if (2 * j + 1 >= nlo) {
+        __syncthreads();
+        gc_store_elem(hi, nhi, j, s.A, s.C, s.J, s.bv, s.eta);
+        return;
     }
-    GElem sib;
-    if (j & 1) {
-        gelem_load(lo, nlo, j - 1, lane, sib);
-        double Po[GL], mo;
-        g_state_through(sm[g], lane, P, m, sib, Po, mo);
-        gvs_store(cpre, nlo, j, lane, Po, mo);
-        gvs_store(csuf, nlo, j, lane, J, eta);
+    gc_load_elem(lo, nlo, 2 * j + 1, s.A2, s.C2, s.J2, s.bv2, s.eta2);
+    __syncthreads();
+    // (i = first, j = second):  M = (I + C_i J_j)^-1
+    gc_inv_ixy(s, s.C, s.J2);
+    // A = A_j M A_i
+    s.T[t] = gc_mm<false, false>(s.M, s.A);
+    // bv: w = bv_i + C_i eta_j;  eta: w2 = eta_j - J_j bv_i
+    if (t < GL) {
+        s.v[t] = s.bv[t] + gc_mv<false>(s.C, s.eta2);
+        s.w[t] = s.eta2[t] - gc_mv<false>(s.J2, s.bv);
+    }
+    __syncthreads();
+    const double Anew = gc_mm<false, false>(s.A2, s.T);
+    double bvnew = 0.0, etanew = 0.0;
+    if (t < GL) s.z[t] = gc_mv<false>(s.M, s.v);        // M w
+    __syncthreads();
+    if (t < GL) {
+        bvnew = gc_mv<false>(s.A2, s.z) + s.bv2[t];      // A_j M w + bv_j
+        s.v[t] = gc_mv<true>(s.M, s.w);                  // M^T w2
+    }
+    // C = sym(A_j M C_i A_j^T) + C_j
+    s.T[t] = gc_mm<false, false>(s.M, s.C);
+    __syncthreads();
+    if (t < GL) etanew = gc_mv<true>(s.A, s.v) + s.eta[t];   // A_i^T M^T w2 + eta_i
+    s.U[t] = gc_mm<false, false>(s.A2, s.T);
+    __syncthreads();
+    s.N[t] = gc_mm<false, true>(s.U, s.A2);
+    // J = sym(A_i^T M^T J_j A_i) + J_i
+    s.T[t] = gc_mm<true, false>(s.M, s.J2);
+    __syncthreads();
+    const double Cnew = 0.5 * ((s.N[t] + s.C2[t]) + (s.N[c * GL + r] + s.C2[c * GL + r]));
+    s.U[t] = gc_mm<false, false>(s.T, s.A);
+    __syncthreads();
+    s.T[t] = gc_mm<true, false>(s.A, s.U);
+    __syncthreads();
+    const double Jnew = 0.5 * ((s.T[t] + s.J[t]) + (s.T[c * GL + r] + s.J[c * GL + r]));
+    __syncthreads();
+    s.A[t] = Anew;
+    s.C[t] = Cnew;
+    s.J[t] = Jnew;
+    if (t < GL) { s.bv[t] = bvnew; s.eta[t] = etanew; }
+    __syncthreads();
+    gc_store_elem(hi, nhi, j, s.A, s.C, s.J, s.bv, s.eta);
+}
+
+// back-substitution from level l (parents) to level l-1 (children): the
+// prefix state before each child and the information after it.  Odd child
+// j: the parent's state pushed through node j-1; even child j: the parent's
+// information pulled back through node j+1 (or kept, at the end).
+__global__ void __launch_bounds__(GSC) k_gscan_down(const double* __restrict__ lo, int64_t nlo,
+                                                    const double* __restrict__ ppre, const double* __restrict__ psuf,
+                                                    int64_t nhi, double* __restrict__ cpre,
+                                                    double* __restrict__ csuf) {
+    __shared__ GScanSmem s;
+    const int t = threadIdx.x, r = t >> 4, c = t & 15;
+    const int64_t j = blockIdx.x;
+    if (j >= nlo) return;
+    const int64_t parent = j >> 1;
+    // the parent's state (into S, v) and information (into C2, w)
+    if (ppre) {
+        gc_load_vs(ppre, nhi, parent, s.S, s.v);
+        gc_load_vs(psuf, nhi, parent, s.C2, s.w);
     } else {
-        gvs_store(cpre, nlo, j, lane, P, m);
-        if (j + 1 < nlo) {
-            gelem_load(lo, nlo, j + 1, lane, sib);
-            double Jo[GL], eo;
-            g_info_through(sm[g], lane, sib, J, eta, Jo, eo);
-            gvs_store(csuf, nlo, j, lane, Jo, eo);
-        } else {
-            gvs_store(csuf, nlo, j, lane, J, eta);
-        }
+        s.S[t] = 0.0; s.C2[t] = 0.0;
+        if (t < GL) { s.v[t] = 0.0; s.w[t] = 0.0; }
+    }
+    const bool odd = (j & 1) != 0;
+    const bool through = odd || (j + 1 < nlo);
+    if (through) gc_load_elem(lo, nlo, odd ? j - 1 : j + 1, s.A, s.C, s.J, s.bv, s.eta);
+    __syncthreads();
+    if (!through) {   // the last even child keeps the parent's state and information
+        gc_store_vs(cpre, nlo, j, s.S, s.v);
+        gc_store_vs(csuf, nlo, j, s.C2, s.w);
+        return;
+    }
+    if (odd) {
+        // N(m, P) pushed through e: M = (I + P J_e)^-1, m' = A_e M (m + P eta_e) + bv_e,
+        // P' = sym(A_e M P A_e^T) + C_e
+        gc_inv_ixy(s, s.S, s.J);
+        if (t < GL) s.z[t] = s.v[t] + gc_mv<false>(s.S, s.eta);
+        s.T[t] = gc_mm<false, false>(s.M, s.S);
+        __syncthreads();
+        double mnew = 0.0;
+        if (t < GL) s.bv2[t] = gc_mv<false>(s.M, s.z);
+        s.U[t] = gc_mm<false, false>(s.A, s.T);
+        __syncthreads();
+        if (t < GL) mnew = gc_mv<false>(s.A, s.bv2) + s.bv[t];
+        s.N[t] = gc_mm<false, true>(s.U, s.A);
+        __syncthreads();
+        const double Pnew = 0.5 * ((s.N[t] + s.C[t]) + (s.N[c * GL + r] + s.C[c * GL + r]));
+        __syncthreads();
+        s.T[t] = Pnew;
+        if (t < GL) s.z[t] = mnew;
+        __syncthreads();
+        gc_store_vs(cpre, nlo, j, s.T, s.z);
+        gc_store_vs(csuf, nlo, j, s.C2, s.w);
+    } else {
+        // information (eta, J) pulled back through e: M = (I + C_e J)^-1,
+        // eta' = A_e^T M^T (eta - J bv_e) + eta_e, J' = sym(A_e^T M^T J A_e) + J_e
+        gc_inv_ixy(s, s.C, s.C2);
+        if (t < GL) s.z[t] = s.w[t] - gc_mv<false>(s.C2, s.bv);
+        s.T[t] = gc_mm<true, false>(s.M, s.C2);
+        __syncthreads();
+        double enew = 0.0;
+        if (t < GL) s.bv2[t] = gc_mv<true>(s.M, s.z);
+        s.U[t] = gc_mm<false, false>(s.T, s.A);
+        __syncthreads();
+        if (t < GL) enew = gc_mv<true>(s.A, s.bv2) + s.eta[t];
+        s.N[t] = gc_mm<true, false>(s.A, s.U);
+        __syncthreads();
+        const double Jnew = 0.5 * ((s.N[t] + s.J[t]) + (s.N[c * GL + r] + s.J[c * GL + r]));
+        __syncthreads();
+        s.T[t] = Jnew;
+        if (t < GL) s.z[t] = enew;
+        __syncthreads();
+        gc_store_vs(cpre, nlo, j, s.S, s.v);
+        gc_store_vs(csuf, nlo, j, s.T, s.z);
     }
 }
 
@@ -1049,12 +1241,12 @@ int group_run(const GModel& gm, int mode, const double* t, const double* y, int6
     k_gfold<<<cgrid, GCTA, 0, st>>>(a, (double*)(ws + lay.off_nodes[0]));
     if (ev) cudaEventRecord(ev[1], st);
     for (int l = 1; l <= lay.nlev; ++l)
-        k_gscan_up<<<(unsigned)((lay.lev_n[l] + GGRP - 1) / GGRP), GCTA, 0, st>>>(
+        k_gscan_up<<<(unsigned)lay.lev_n[l], GSC, 0, st>>>(
             (const double*)(ws + lay.off_nodes[l - 1]), lay.lev_n[l - 1], (double*)(ws + lay.off_nodes[l]),
             lay.lev_n[l]);
     for (int l = lay.nlev; l >= 1; --l) {
         const bool top = (l == lay.nlev);
-        k_gscan_down<<<(unsigned)((lay.lev_n[l - 1] + GGRP - 1) / GGRP), GCTA, 0, st>>>(
+        k_gscan_down<<<(unsigned)lay.lev_n[l - 1], GSC, 0, st>>>(
             (const double*)(ws + lay.off_nodes[l - 1]), lay.lev_n[l - 1],
             top ? nullptr : (const double*)(ws + lay.off_pre[l]), top ? nullptr : (const double*)(ws + lay.off_suf[l]),
             lay.lev_n[l], (double*)(ws + lay.off_pre[l - 1]), (double*)(ws + lay.off_suf[l - 1]));
