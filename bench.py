@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary workloads (b = 16 sum, 4096-series batch, N = 2^26)")
+    ap.add_argument("--no-next", action="store_true",
+                    help="skip the rows built beyond the hot path (prediction, literal mode, BTD solver, "
+                         "EQ oracle rate, batched SCG)")
     return ap.parse_args()
 
 
@@ -272,6 +275,120 @@ def extra_workloads(args, dev, flush, world, rank=0):
     return res
 
 
+def _oracle_seconds(fn, reps=1):
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fn()
+        times.append(time.perf_counter() - t0)
+    return float(np.median(times))
+
+
+def next_rows(args, dev, flush):
+    """The rows built beyond the hot path, each timed on the GPU (device time,
+    L2 flushed before each call) with the oracle timed beside it on a bounded
+    sample on one host thread:
+      prediction_n4m  posterior of the N = 2^22, b = 3 series with 10 % of its
+                      observations missing (test points, Eqs. mean4-mean6)
+      literal_n1m     the method as written: Theorem-1 assembly, block cyclic
+                      reduction with selected inverse, Eq. dd1 gradient; b = 3,
+                      N = 2^20 well-separated times (oracle: its Kalman form)
+      btd_solve_n1m   the general BTD solver with selected inverse, b = 3,
+                      2^20 nodes (oracle: the sequential block algorithm)
+      eq_b12_n1m      the oracle rate for the b = 12 EQ model (its GPU rate is
+                      in workloads)
+      scg_batch_4096  5 SCG iterations on the 4096-series batch (2 gradient
+                      evaluations per iteration plus 2)"""
+    import torch
+
+    from oracle import btd, scg, seq
+    from paper_1610_08035_gb300 import spingp, synth
+
+    K = 3
+    res = {}
+    # ---- prediction: the headline series with 10 % missing observations
+    s = synth.single(WORKLOAD)
+    n = len(s.t)
+    rng = np.random.default_rng(11)
+    y = s.y.copy()
+    y[rng.random(n) < 0.1] = np.nan
+    T, Y, TH = (torch.tensor(a, device=dev) for a in (s.t, y, s.theta))
+    m = spingp.Model(s.spec)
+    m.posterior(T, Y, TH, missing=True)
+    ms = _time_calls(lambda: m.posterior(T, Y, TH, sync=False, missing=True), K, flush, torch)
+    smp = 1 << 18
+    osec = _oracle_seconds(lambda: seq.smoother(s.spec, s.theta, s.t[:smp], y[:smp]))
+    res["prediction_n4m"] = {"value": n / (ms * 1e-3), "unit": "steps/s", "ms_per_step": ms, "n": n,
+                             "missing_fraction": 0.1, "gpu_launches_per_step":
+                                 spingp.spingp_launch_count(m.h, n, spingp.WS_POSTERIOR),
+                             "oracle": {"value": smp / osec, "unit": "steps/s", "cores": 1,
+                                        "sample": "first %d steps, sequential C smoother" % smp}}
+    del T, Y, TH, m
+    torch.cuda.empty_cache()
+    # ---- the method as written
+    n = 1 << 20
+    rng = np.random.default_rng(12)
+    t = synth.separated_times(n, 0.5, rng)
+    y = synth.two_sinusoids(t, 0.5, 2.0, 0.05, rng)
+    th = np.array([0.5, 2.0, 0.05])
+    T, Y, TH = (torch.tensor(a, device=dev) for a in (t, y, th))
+    m = spingp.Model("matern52")
+    m.literal(T, Y, TH, what=spingp.WS_GRAD)
+    ms = _time_calls(lambda: m.literal(T, Y, TH, what=spingp.WS_GRAD, sync=False), K, flush, torch)
+    smp = 1 << 18
+    osec = _oracle_seconds(lambda: seq.grad("matern52", th, t[:smp], y[:smp]))
+    res["literal_n1m"] = {"value": n / (ms * 1e-3), "unit": "steps/s", "ms_per_step": ms, "n": n, "b": 3,
+                          "gpu_launches_per_step": spingp.spingp_literal_launch_count(n),
+                          "oracle": {"value": smp / osec, "unit": "steps/s", "cores": 1,
+                                     "sample": "first %d steps, sequential C oracle (Kalman form of the same "
+                                               "log-likelihood and gradient)" % smp}}
+    del T, Y, TH, m
+    # ---- the general BTD solver
+    D, O, r = synth.random_spd_btd(n, 3, seed=13)
+    Dt, Ot, rt = (torch.tensor(a, device=dev) for a in (D, O, r))
+    spingp.btd_solve(Dt, Ot, rt)
+    ms = _time_calls(lambda: spingp.btd_solve(Dt, Ot, rt, sync=False), K, flush, torch)
+    smp = 1 << 14
+    osec = _oracle_seconds(lambda: btd.thomas(D[:smp], O[:smp - 1], r[:smp]))
+    res["btd_solve_n1m"] = {"value": n / (ms * 1e-3), "unit": "nodes/s", "ms_per_step": ms, "n": n, "b": 3,
+                            "gpu_launches_per_step": spingp.spingp_btd_launch_count(n),
+                            "oracle": {"value": smp / osec, "unit": "nodes/s", "cores": 1,
+                                       "sample": "first %d nodes, sequential block LDL^T and selected inverse "
+                                                 "(NumPy, one block per step)" % smp}}
+    del Dt, Ot, rt
+    torch.cuda.empty_cache()
+    # ---- the b = 12 EQ model: oracle rate
+    s = synth.single("m32_eq10_n1m")
+    smp = 1 << 11
+    osec = _oracle_seconds(lambda: seq.grad(s.spec, s.theta, s.t[:smp], s.y[:smp]))
+    res["eq_b12_n1m"] = {"oracle": {"value": smp / osec, "unit": "steps/s", "cores": 1,
+                                    "sample": "first %d steps, sequential C oracle" % smp}}
+    # ---- batched SCG
+    s = synth.batched()
+    off = torch.tensor(s.extra["offsets"], dtype=torch.int64, device=dev)
+    T, Y = torch.tensor(s.t, device=dev), torch.tensor(s.y, device=dev)
+    bt = spingp.Batch(spingp.Model("matern52"), off, T, Y)
+    S = bt.n_series
+    th0 = torch.tensor(np.tile([1.0, 1.0, 0.2], (S, 1)), device=dev)
+    iters = 5
+    bt.optimize(th0, iterations=1)
+    ms = _time_calls(lambda: bt.optimize(th0, iterations=iters, sync=False), 1, flush, torch)
+    evals = 2 * iters + 2
+    offs = s.extra["offsets"]
+    nser = 8
+    nst = int(offs[nser])
+    osec = _oracle_seconds(lambda: [scg.scg(scg.gp_objective("matern52", s.t[offs[i]:offs[i + 1]],
+                                                             s.y[offs[i]:offs[i + 1]], seq.grad),
+                                            np.log([1.0, 1.0, 0.2]), iters) for i in range(nser)])
+    res["scg_batch_4096"] = {"value": evals * len(s.t) / (ms * 1e-3), "unit": "steps/s (gradient evaluations)",
+                             "ms_per_call": ms, "iterations": iters, "n_series": S, "n_total": len(s.t),
+                             "series_iterations_per_s": S * iters / (ms * 1e-3),
+                             "oracle": {"value": evals * nst / osec, "unit": "steps/s (gradient evaluations)",
+                                        "cores": 1, "sample": "the first %d series (%d steps), oracle SCG on the "
+                                                              "sequential C oracle" % (nser, nst)}}
+    return res
+
+
 # ---------------------------------------------------------------- the CUDA path
 
 def main():
@@ -446,6 +563,10 @@ def main():
     # ---- secondary workloads: the other configurations of the same path
     if not args.no_extra and not args.n:
         out["workloads"] = extra_workloads(args, dev, flush, world, rank)
+
+    # ---- the rows built beyond the hot path, each with the oracle beside it
+    if not args.no_next and not args.n and world == 1:
+        out["next"] = next_rows(args, dev, flush)
 
     # ---- the oracle on the host cores (rank 0, single GPU only)
     if not args.no_cpu_baseline and world == 1:

@@ -297,7 +297,7 @@ spingp_status spingp_optimize_batched(const spingp_model* model, const int64_t* 
  * subproblems 2 and 4 need.  Odd-even block cyclic reduction: level l
  * eliminates the odd-numbered nodes of level l-1 by Schur complement, the
  * single node left is solved, and back-substitution recovers x and the
- * selected inverse level by level (2 ceil(log2 n) + 2 kernels).  A pivot
+ * selected inverse level by level (2 ceil(log2 n) + 3 kernels).  A pivot
  * block that is not positive definite gives SPINGP_ENUMERIC.  logdet_out is
  * one device double. */
 size_t spingp_btd_workspace_bytes(int b, int64_t n);

@@ -52,14 +52,14 @@ __device__ __forceinline__ bool chol(const double (&S)[B][B], double (&L)[B][B])
     return ok;
 }
 
-// S^-1 from its Cholesky factor, and log det S
-template <int B>
+// S^-1 from its Cholesky factor, and (LOGDET) log det S
+template <int B, bool LOGDET = true>
 __device__ __forceinline__ void chol_inv(const double (&L)[B][B], double (&Si)[B][B], double& logdet) {
     double Li[B][B];   // L^-1 (lower)
     logdet = 0.0;
 #pragma unroll
     for (int j = 0; j < B; ++j) {
-        logdet += 2.0 * log(L[j][j]);
+        if constexpr (LOGDET) logdet += 2.0 * log(L[j][j]);
 #pragma unroll
         for (int i = 0; i < B; ++i) {
             if (i < j) { Li[i][j] = 0.0; continue; }
@@ -91,7 +91,7 @@ __device__ __forceinline__ void blk_store(double* __restrict__ p, const double (
 
 // Scaled-coordinate pieces of transition i (t_i -> t_{i+1}): Phi, Qt^-1 and
 // log det Qt, with Qt = s_f (P1 - Phi P1 Phi^T).
-template <int B>
+template <int B, bool LOGDET = true>
 __device__ __forceinline__ bool trans_scaled(double x, double sf, double (&Ph)[B][B], double (&Qi)[B][B],
                                              double& ldq) {
     phi<B>(x, exp(-x), Ph);
@@ -107,7 +107,7 @@ __device__ __forceinline__ bool trans_scaled(double x, double sf, double (&Ph)[B
 #pragma unroll
         for (int q = 0; q < B; ++q) Q[r][q] = sf * (P1m[r][q] - Q[r][q]);
     const bool ok = chol<B>(Q, L);
-    chol_inv<B>(L, Qi, ldq);
+    chol_inv<B, LOGDET>(L, Qi, ldq);
     return ok;
 }
 
@@ -191,12 +191,15 @@ __global__ void __launch_bounds__(128) k_assemble(const double* __restrict__ t, 
 //   r'_j = r_2j - O_{2j-1} D_{2j-1}^-1 r_{2j-1} - O_2j^T D_{2j+1}^-1 r_{2j+1}
 //   O'_j = -O_{2j+1} D_{2j+1}^-1 O_2j          (new sub-diagonal block (j+1, j))
 // and log det D_{2j+1} is counted by thread j.
+// The inverse of each eliminated node's D_k (computed by the thread that has it
+// as its right neighbour) is kept in Dinv for the back-substitution.
 template <int B>
 __global__ void __launch_bounds__(128) k_btd_reduce(const double* __restrict__ D, const double* __restrict__ O,
                                                     const double* __restrict__ r, int64_t nlo,
                                                     double* __restrict__ D2, double* __restrict__ O2,
                                                     double* __restrict__ r2, int64_t nhi,
-                                                    double* __restrict__ ld, int* status) {
+                                                    double* __restrict__ ld, double* __restrict__ Dinv,
+                                                    int* status) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= nhi) return;
     const int64_t e = 2 * j;
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(128) k_btd_reduce(const double* __restrict__ D
         double Dk[B][B], L[B][B], Dki[B][B], Ok[B][B], T[B][B], U[B][B], w[B], z[B], l0;
         blk_load<B>(D + k * (B * B), Dk);
         if (!chol<B>(Dk, L)) bad |= ST_ENUMERIC;
-        chol_inv<B>(L, Dki, l0);
+        chol_inv<B, false>(L, Dki, l0);
         blk_load<B>(O + k * (B * B), Ok);
         mat_mul<B>(Ok, Dki, T);            // O_k D_k^-1
         mat_mul_t_sym<B>(T, Ok, U);        // O_k D_k^-1 O_k^T
@@ -231,6 +234,7 @@ __global__ void __launch_bounds__(128) k_btd_reduce(const double* __restrict__ D
         if (!chol<B>(Dk, L)) bad |= ST_ENUMERIC;
         chol_inv<B>(L, Dki, l1);
         ldj = l1;
+        blk_store<B>(Dinv + k * (B * B), Dki);
         blk_load<B>(O + e * (B * B), Oe);
         mat_mul<B>(Dki, Oe, T);            // D_k^-1 O_e
         mat_tmul_sym<B>(Oe, T, U);         // O_e^T D_k^-1 O_e
@@ -288,7 +292,7 @@ __global__ void k_btd_top(const double* __restrict__ D, const double* __restrict
 //   S_kk = D_k^-1 - S_ka Za^T - S_kc Zc^T
 // and the sub-diagonal blocks (k, k-1) = S_ka, (k+1, k) = S_kc^T.
 template <int B>
-__global__ void __launch_bounds__(128) k_btd_back(const double* __restrict__ D, const double* __restrict__ O,
+__global__ void __launch_bounds__(128) k_btd_back(const double* __restrict__ Dinv, const double* __restrict__ O,
                                                   const double* __restrict__ r, int64_t nlo,
                                                   const double* __restrict__ x2, const double* __restrict__ Sd2,
                                                   const double* __restrict__ So2, int64_t nhi,
@@ -307,11 +311,9 @@ __global__ void __launch_bounds__(128) k_btd_back(const double* __restrict__ D, 
     }
     const int64_t k = i, a = k - 1, c = k + 1, ja = a >> 1;
     const bool hasc = c < nlo;
-    double Dk[B][B], L[B][B], Dki[B][B], ldk, Oa[B][B], Oc[B][B], w[B], xa[B], xc[B], z[B];
-    blk_load<B>(D + k * (B * B), Dk);
-    chol<B>(Dk, L);
-    chol_inv<B>(L, Dki, ldk);
-    blk_load<B>(O + a * (B * B), Oa);      // T[k][a]
+    double Dki[B][B], Oa[B][B], Oc[B][B], w[B], xa[B], xc[B], z[B];
+    blk_load<B>(Dinv + k * (B * B), Dki);   // D_k^-1 from the reduction
+    blk_load<B>(O + a * (B * B), Oa);       // T[k][a]
 #pragma unroll
     for (int q = 0; q < B; ++q) { w[q] = r[k * B + q]; xa[q] = x2[ja * B + q]; xc[q] = 0.0; }
     mat_vec<B>(Oa, xa, z);
@@ -393,20 +395,44 @@ __global__ void __launch_bounds__(128) k_btd_back(const double* __restrict__ D, 
     }
 }
 
-// Fixed-order column sums: CTA c sums v[c * ld + 0 .. n) into out[c].
-__global__ void __launch_bounds__(256) k_colsum(const double* __restrict__ v, int64_t n, int64_t ld,
-                                                double* __restrict__ out) {
-    __shared__ double red[256];
-    const double* col = v + blockIdx.x * ld;
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += 256) s += col[i];
+// Fixed-order column sums in two stages: CTA (g, c) sums its contiguous
+// range [g len, (g+1) len) of column c (v[c * ld + i]) into part[c * SUM_G + g];
+// then CTA c sums column c's SUM_G partials into out[c].  The summation
+// order depends only on n, so results are bit-reproducible.
+static constexpr int SUM_G = 128;
+
+__device__ __forceinline__ double cta_sum256(double s, double* red) {
     red[threadIdx.x] = s;
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
         if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+    return red[0];
+}
+
+__global__ void __launch_bounds__(256) k_colsum(const double* __restrict__ v, int64_t n, int64_t ld,
+                                                double* __restrict__ part) {
+    __shared__ double red[256];
+    const int64_t len = (n + SUM_G - 1) / SUM_G;
+    const int64_t lo = blockIdx.x * len, hi = min(n, lo + len);
+    const double* col = v + blockIdx.y * ld;
+    double s = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += 256) s += col[i];
+    s = cta_sum256(s, red);
+    if (threadIdx.x == 0) part[blockIdx.y * SUM_G + blockIdx.x] = s;
+}
+__global__ void __launch_bounds__(256) k_colsum_final(const double* __restrict__ part, double* __restrict__ out) {
+    __shared__ double red[256];
+    const double s = (threadIdx.x < SUM_G) ? part[blockIdx.x * SUM_G + threadIdx.x] : 0.0;
+    const double tot = cta_sum256(s, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = tot;
+}
+// sums of ncol columns of length n (stride ld) into out; scratch: ncol x SUM_G doubles
+static void colsum(const double* v, int64_t n, int64_t ld, int ncol, double* out, double* scratch,
+                   cudaStream_t st) {
+    k_colsum<<<dim3(SUM_G, ncol), 256, 0, st>>>(v, n, ld, scratch);
+    k_colsum_final<<<ncol, 256, 0, st>>>(scratch, out);
 }
 
 // ------------------------------------------------------------------ subproblem 4: diag(S X) for a BTD X
@@ -472,7 +498,7 @@ template <int B>
 __device__ __forceinline__ void trans_dx(double x, double sf, double (&Ph)[B][B], double (&Qi)[B][B],
                                          double (&dQ)[B][B], double (&dQi)[B][B]) {
     double ldq, M[B][B], T[B][B], N[B][B];
-    trans_scaled<B>(x, sf, Ph, Qi, ldq);
+    trans_scaled<B, false>(x, sf, Ph, Qi, ldq);
     double P1m[B][B];
 #pragma unroll
     for (int r = 0; r < B; ++r)
@@ -566,7 +592,7 @@ __global__ void __launch_bounds__(128) k_literal_terms(const double* __restrict_
 #pragma unroll
                 for (int q = 0; q < B; ++q) P[r][q] = sf * p1<B>(r, q);
             chol<B>(P, L);
-            chol_inv<B>(L, Dt, l0);
+            chol_inv<B, false>(L, Dt, l0);
 #pragma unroll
             for (int r = 0; r < B; ++r)
 #pragma unroll
@@ -658,13 +684,15 @@ static size_t balign(size_t x) { return (x + 255) & ~(size_t)255; }
 struct BtdLayout {
     int nlev;
     int64_t cnt[64];
-    size_t off_D[64], off_O[64], off_r[64], off_x[64], off_Sd[64], off_So[64], off_top, off_ld, total;
+    size_t off_D[64], off_O[64], off_r[64], off_x[64], off_Sd[64], off_So[64], off_Dinv[64], off_top, off_ld,
+        off_red, total;
     BtdLayout(int b, int64_t n) {
         size_t o = 0;
         nlev = 0;
         cnt[0] = n;
         while (cnt[nlev] > 1) { cnt[nlev + 1] = (cnt[nlev] + 1) / 2; ++nlev; }
         const size_t bb = sizeof(double) * b * b, bv = sizeof(double) * b;
+        for (int l = 0; l < nlev; ++l) { off_Dinv[l] = o; o = balign(o + bb * cnt[l]); }
         for (int l = 1; l <= nlev; ++l) {
             off_D[l] = o; o = balign(o + bb * cnt[l]);
             off_O[l] = o; o = balign(o + bb * cnt[l]);
@@ -677,6 +705,7 @@ struct BtdLayout {
         size_t nld = 1;
         for (int l = 1; l <= nlev; ++l) nld += cnt[l];
         off_ld = o; o = balign(o + sizeof(double) * nld);
+        off_red = o; o = balign(o + sizeof(double) * SUM_G);
         total = o;
     }
 };
@@ -697,7 +726,7 @@ static int btd_core(int64_t n, const double* D, const double* O, const double* r
         const double* rl = (l == 1) ? r : lvl(lay.off_r, l - 1);
         k_btd_reduce<B><<<(unsigned)((lay.cnt[l] + 127) / 128), 128, 0, st>>>(
             Dl, Ol, rl, lay.cnt[l - 1], lvl(lay.off_D, l), lvl(lay.off_O, l), lvl(lay.off_r, l), lay.cnt[l],
-            ld + ldo, status);
+            ld + ldo, lvl(lay.off_Dinv, l - 1), status);
         ldo += lay.cnt[l];
     }
     {
@@ -709,7 +738,7 @@ static int btd_core(int64_t n, const double* D, const double* O, const double* r
         k_btd_top<B><<<1, 32, 0, st>>>(Dt, rt, xt, St, ld + ldo, status);
     }
     for (int l = lay.nlev; l >= 1; --l) {
-        const double* Dl = (l == 1) ? D : lvl(lay.off_D, l - 1);
+        const double* Dl = lvl(lay.off_Dinv, l - 1);
         const double* Ol = (l == 1) ? O : lvl(lay.off_O, l - 1);
         const double* rl = (l == 1) ? r : lvl(lay.off_r, l - 1);
         double* xl = (l == 1) ? x : lvl(lay.off_x, l - 1);
@@ -719,15 +748,16 @@ static int btd_core(int64_t n, const double* D, const double* O, const double* r
             Dl, Ol, rl, lay.cnt[l - 1], lvl(lay.off_x, l), lvl(lay.off_Sd, l), lvl(lay.off_So, l), lay.cnt[l], xl,
             Sdl, Sol, want_s);
     }
-    k_colsum<<<1, 256, 0, st>>>(ld, ldo + 1, 0, logdet);
+    colsum(ld, ldo + 1, 0, 1, logdet, (double*)(sc + lay.off_red), st);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
+// part: n doubles, then SUM_G doubles of sum scratch
 template <int B>
 static int assemble_core(const double* t, const double* y, int64_t n, const double* theta, double* D, double* O,
                          double* r, double* logdet_kinv, double* part, int* status, cudaStream_t st) {
     k_assemble<B><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(t, y, n, theta, D, O, r, part, status);
-    k_colsum<<<1, 256, 0, st>>>(part, n, 0, logdet_kinv);
+    colsum(part, n, 0, 1, logdet_kinv, part + n, st);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
@@ -743,7 +773,7 @@ int btd_solve(int b, int64_t n, const double* D, const double* O, const double* 
     return SPG_DISPATCH_B(b, btd_core)(n, D, O, r, logdet, x, Sd, So, w + 256, (int*)w, st);
 }
 
-size_t assemble_ws_bytes(int64_t n) { return 256 + balign(sizeof(double) * (size_t)n); }
+size_t assemble_ws_bytes(int64_t n) { return 256 + balign(sizeof(double) * ((size_t)n + SUM_G)); }
 
 int assemble(int b, const double* t, const double* y, int64_t n, const double* theta, double* D, double* O,
              double* r, double* logdet_kinv, void* ws, cudaStream_t st) {
@@ -752,7 +782,7 @@ int assemble(int b, const double* t, const double* y, int64_t n, const double* t
     return SPG_DISPATCH_B(b, assemble_core)(t, y, n, theta, D, O, r, logdet_kinv, (double*)(w + 256), (int*)w, st);
 }
 
-size_t diagprod_ws_bytes(int64_t n) { return 256 + balign(sizeof(double) * (size_t)n); }
+size_t diagprod_ws_bytes(int64_t n) { return 256 + balign(sizeof(double) * ((size_t)n + SUM_G)); }
 
 template <int B>
 static int diagprod_t(int64_t n, const double* Sd, const double* So, const double* Xd, const double* Xo,
@@ -760,7 +790,7 @@ static int diagprod_t(int64_t n, const double* Sd, const double* So, const doubl
     if (cudaMemsetAsync(w, 0, sizeof(int), st) != cudaSuccess) return 1;
     double* part = (double*)(w + 256);
     k_btd_diagprod<B><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(Sd, So, Xd, Xo, n, diag, part);
-    k_colsum<<<1, 256, 0, st>>>(part, n, 0, trace);
+    colsum(part, n, 0, 1, trace, part + n, st);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
@@ -773,7 +803,7 @@ int btd_diagprod(int b, int64_t n, const double* Sd, const double* So, const dou
 // selected inverse (gradient and posterior), per-step parts, sums, then the
 // reduction's scratch.
 struct LitLayout {
-    size_t D, O, r, x, Sd, So, part, sums, lds, btd, total;
+    size_t D, O, r, x, Sd, So, part, red, sums, lds, btd, total;
     LitLayout(int b, int64_t n, int mode) {
         const size_t bb = sizeof(double) * b * b, bv = sizeof(double) * b, nn = (size_t)n;
         const bool sel = mode != MODE_LOGLIK;
@@ -785,7 +815,8 @@ struct LitLayout {
         x = o; o = balign(o + bv * nn);
         Sd = o; o = balign(o + (sel ? bb * nn : 0));
         So = o; o = balign(o + (sel ? bb * nn : 0));
-        part = o; o = balign(o + sizeof(double) * nn * ncol);
+        part = o; o = balign(o + sizeof(double) * (nn * ncol + SUM_G));
+        red = o; o = balign(o + sizeof(double) * SUM_G * 5);
         sums = o; o = balign(o + sizeof(double) * 8);
         lds = o; o = balign(o + sizeof(double) * 2);
         btd = o; o = balign(o + BtdLayout(b, n).total);
@@ -815,7 +846,7 @@ static int literal_t(int mode, const double* t, const double* y, int64_t n, cons
     else
         k_literal_terms<B, false><<<g, 128, 0, st>>>(t, y, n, theta, at(lay.x), sel ? at(lay.Sd) : nullptr, nullptr,
                                                      at(lay.part), mean, sel ? var : nullptr);
-    k_colsum<<<mode == MODE_GRAD ? 5 : 2, 256, 0, st>>>(at(lay.part), n, n, at(lay.sums));
+    colsum(at(lay.part), n, n, mode == MODE_GRAD ? 5 : 2, at(lay.sums), at(lay.red), st);
     k_literal_final<<<1, 32, 0, st>>>(theta, n, at(lay.sums), at(lay.lds), ll, mode == MODE_GRAD ? grad : nullptr);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
@@ -829,8 +860,9 @@ int literal_run(int b, int mode, const double* t, const double* y, int64_t n, co
 int64_t btd_launch_count(int64_t n) {
     int nlev = 0;
     for (int64_t c = n; c > 1; c = (c + 1) / 2) ++nlev;
-    return 2 * (int64_t)nlev + 2;
+    return 2 * (int64_t)nlev + 3;   // levels down and up, the top, the two-stage sum
 }
-int64_t literal_launch_count(int64_t n) { return 2 + btd_launch_count(n) + 3; }
+// assembly + its sum, the solve, the per-step terms + their sums + the final combination
+int64_t literal_launch_count(int64_t n) { return 3 + btd_launch_count(n) + 4; }
 
 }  // namespace spg

@@ -219,5 +219,5 @@ def test_btd_error_statuses():
     assert st == spingp.EINVAL                          # workspace too small
     assert spingp.spingp_btd_solve(4, 64, Dt, Ot, rt, ld, x, None, None, ws, 1 << 30, 0) == spingp.EINVAL
     assert lib.spingp_btd_workspace_bytes(4, 64) == 0
-    assert spingp.spingp_btd_launch_count(64) == 2 * 6 + 2
-    assert spingp.spingp_literal_launch_count(64) == 2 + 2 * 6 + 2 + 3
+    assert spingp.spingp_btd_launch_count(64) == 2 * 6 + 3
+    assert spingp.spingp_literal_launch_count(64) == 3 + (2 * 6 + 3) + 4
