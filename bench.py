@@ -275,6 +275,28 @@ def extra_workloads(args, dev, flush, world, rank=0):
     return res
 
 
+# Whole-call FP64 work per unit of the rows built beyond the hot path (ncu,
+# profiles/next_rows_kernels.md): flops = 2 DFMA + DADD + DMUL thread
+# instructions; instructions = everything the FP64 pipe executed.  Units:
+# steps, or nodes for the BTD solver; the batched SCG's gradient evaluations
+# use the chain kernels' counts above.
+NEXT_FLOPS_PER_UNIT = {"prediction_n4m": 529.0, "literal_n1m": 3801.2, "btd_solve_n1m": 1221.0,
+                       "eq_b12_n1m": 15814.8, "scg_batch_4096": 268.2 + 364.2}
+NEXT_FP64_INST_PER_UNIT = {"prediction_n4m": 350.3, "literal_n1m": 2686.9, "btd_solve_n1m": 1044.3,
+                           "eq_b12_n1m": 10769.2, "scg_batch_4096": 167.9 + 223.7}
+
+
+def _next_roofline(key, units_per_s, fp64_tflops):
+    """FP64 roofline of a whole call: achieved TFLOP/s against the measured
+    FMA probe, and the FP64-pipe instruction fraction."""
+    fl, inst = NEXT_FLOPS_PER_UNIT[key], NEXT_FP64_INST_PER_UNIT[key]
+    ach = fl * units_per_s / 1e12
+    return {"bound": "alu", "kernel": "whole call", "achieved": ach, "peak": fp64_tflops, "unit": "TFLOP/s",
+            "frac": ach / fp64_tflops, "pipe_frac": inst * units_per_s / (fp64_tflops * 1e12 / 2.0),
+            "flops_per_unit": fl, "fp64_inst_per_unit": inst, "traffic": None,
+            "peak_kind": "measured FP64 FMA probe (spingp_probe_fp64)"}
+
+
 def _oracle_seconds(fn, reps=1):
     times = []
     for _ in range(reps):
@@ -284,7 +306,7 @@ def _oracle_seconds(fn, reps=1):
     return float(np.median(times))
 
 
-def next_rows(args, dev, flush):
+def next_rows(args, dev, flush, fp64_tflops):
     """The rows built beyond the hot path, each timed on the GPU (device time,
     L2 flushed before each call) with the oracle timed beside it on a bounded
     sample on one host thread:
@@ -319,6 +341,8 @@ def next_rows(args, dev, flush):
     smp = 1 << 18
     osec = _oracle_seconds(lambda: seq.smoother(s.spec, s.theta, s.t[:smp], y[:smp]))
     res["prediction_n4m"] = {"value": n / (ms * 1e-3), "unit": "steps/s", "ms_per_step": ms, "n": n,
+                             "chunk_len": m.chunk_len(n),
+                             "roofline": _next_roofline("prediction_n4m", n / (ms * 1e-3), fp64_tflops),
                              "missing_fraction": 0.1, "gpu_launches_per_step":
                                  spingp.spingp_launch_count(m.h, n, spingp.WS_POSTERIOR),
                              "oracle": {"value": smp / osec, "unit": "steps/s", "cores": 1,
@@ -338,6 +362,7 @@ def next_rows(args, dev, flush):
     smp = 1 << 18
     osec = _oracle_seconds(lambda: seq.grad("matern52", th, t[:smp], y[:smp]))
     res["literal_n1m"] = {"value": n / (ms * 1e-3), "unit": "steps/s", "ms_per_step": ms, "n": n, "b": 3,
+                          "roofline": _next_roofline("literal_n1m", n / (ms * 1e-3), fp64_tflops),
                           "gpu_launches_per_step": spingp.spingp_literal_launch_count(n),
                           "oracle": {"value": smp / osec, "unit": "steps/s", "cores": 1,
                                      "sample": "first %d steps, sequential C oracle (Kalman form of the same "
@@ -351,6 +376,7 @@ def next_rows(args, dev, flush):
     smp = 1 << 14
     osec = _oracle_seconds(lambda: btd.thomas(D[:smp], O[:smp - 1], r[:smp]))
     res["btd_solve_n1m"] = {"value": n / (ms * 1e-3), "unit": "nodes/s", "ms_per_step": ms, "n": n, "b": 3,
+                            "roofline": _next_roofline("btd_solve_n1m", n / (ms * 1e-3), fp64_tflops),
                             "gpu_launches_per_step": spingp.spingp_btd_launch_count(n),
                             "oracle": {"value": smp / osec, "unit": "nodes/s", "cores": 1,
                                        "sample": "first %d nodes, sequential block LDL^T and selected inverse "
@@ -383,6 +409,8 @@ def next_rows(args, dev, flush):
     res["scg_batch_4096"] = {"value": evals * len(s.t) / (ms * 1e-3), "unit": "steps/s (gradient evaluations)",
                              "ms_per_call": ms, "iterations": iters, "n_series": S, "n_total": len(s.t),
                              "series_iterations_per_s": S * iters / (ms * 1e-3),
+                             "roofline": _next_roofline("scg_batch_4096", evals * len(s.t) / (ms * 1e-3),
+                                                        fp64_tflops),
                              "oracle": {"value": evals * nst / osec, "unit": "steps/s (gradient evaluations)",
                                         "cores": 1, "sample": "the first %d series (%d steps), oracle SCG on the "
                                                               "sequential C oracle" % (nser, nst)}}
@@ -566,7 +594,11 @@ def main():
 
     # ---- the rows built beyond the hot path, each with the oracle beside it
     if not args.no_next and not args.n and world == 1:
-        out["next"] = next_rows(args, dev, flush)
+        out["next"] = next_rows(args, dev, flush, fp64_tflops)
+        if "m32_eq10_n1m" in out.get("workloads", {}):
+            w = out["workloads"]["m32_eq10_n1m"]
+            out["next"]["eq_b12_n1m"].update({"value": w["value"], "unit": "steps/s", "ms_per_step": w["ms_per_step"],
+                                               "roofline": _next_roofline("eq_b12_n1m", w["value"], fp64_tflops)})
 
     # ---- the oracle on the host cores (rank 0, single GPU only)
     if not args.no_cpu_baseline and world == 1:

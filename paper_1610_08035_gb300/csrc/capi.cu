@@ -49,11 +49,25 @@ spingp_status prepare_device() {
 
 int matern_dim(int kind) { return kind; }
 
+// SMs of the current device (152 on GB300), read once per device
+int device_sms() {
+    static int sms[SPG_MAXDEV];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= SPG_MAXDEV) return 152;
+    if (sms[dev] <= 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+        sms[dev] = v;
+    }
+    return sms[dev];
+}
+
 int64_t default_chunk(int64_t n) {
-    // about 2e4 chunks (enough threads to cover the GPU), L a power of two in [16, 512]
-    int64_t L = 16;
-    while (L < 512 && L * 20000 < n) L *= 2;
-    return L;
+    // two blocks of 128 chunks per SM (the chain kernels run 128 threads per
+    // block, one chunk per thread), L in [16, 512]
+    const int64_t target = 2 * 128 * (int64_t)device_sms();
+    int64_t L = (n + target - 1) / target;
+    return L < 16 ? 16 : (L > 512 ? 512 : L);
 }
 
 int64_t default_group_chunk(int64_t n);
