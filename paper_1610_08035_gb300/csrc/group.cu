@@ -268,24 +268,7 @@ __device__ __forceinline__ void gelem_store(double* __restrict__ base, int64_t n
     p[3 * GL * s] = x.bv;
     p[(3 * GL + 1) * s] = x.eta;
 }
-__device__ __forceinline__ void gelem_load(const double* __restrict__ base, int64_t ne, int64_t e, int lane,
-                                           GElem& x) {
-    const double* p = base + e * GL + lane;
-    const int64_t s = ne * GL;
-#pragma unroll
-    for (int r = 0; r < GL; ++r) { x.A[r] = p[r * s]; x.C[r] = p[(GL + r) * s]; x.J[r] = p[(2 * GL + r) * s]; }
-    x.bv = p[3 * GL * s];
-    x.eta = p[(3 * GL + 1) * s];
-}
 // a state (m, P) or information (eta, J): column + entry
-__device__ __forceinline__ void gvs_store(double* __restrict__ base, int64_t ne, int64_t e, int lane,
-                                          const double (&S)[GL], double v) {
-    double* p = base + e * GL + lane;
-    const int64_t s = ne * GL;
-#pragma unroll
-    for (int r = 0; r < GL; ++r) p[r * s] = S[r];
-    p[GL * s] = v;
-}
 __device__ __forceinline__ void gvs_load(const double* __restrict__ base, int64_t ne, int64_t e, int lane,
                                          double (&S)[GL], double& v) {
     const double* p = base + e * GL + lane;
@@ -318,16 +301,6 @@ __device__ __forceinline__ void g_mul(const double* __restrict__ sm, const doubl
         const double yk = y[k];
 #pragma unroll
         for (int r = 0; r < GL; ++r) out[r] = fma(sm[k * GL + r], yk, out[r]);
-    }
-}
-// out = M^T y
-__device__ __forceinline__ void g_tmul(const double* __restrict__ sm, const double (&y)[GL], double (&out)[GL]) {
-#pragma unroll
-    for (int r = 0; r < GL; ++r) {
-        double s = 0.0;
-#pragma unroll
-        for (int k = 0; k < GL; ++k) s = fma(sm[r * GL + k], y[k], s);
-        out[r] = s;
     }
 }
 // row 'lane' of M (columns in sm) dotted with a full vector
@@ -392,19 +365,6 @@ __device__ void g_inv_ixy(GSmem& s, int lane, const double (&Xc)[GL], const doub
     __syncwarp(mask);
 }
 
-// column 'lane' of X Z^T where X's and Z's columns are put in s.X and s.N
-__device__ __forceinline__ void g_mul_bt(GSmem& s, int lane, const double (&Xc)[GL], const double (&Zc)[GL],
-                                         double (&out)[GL]) {
-    const unsigned mask = half_mask();
-    g_put(s.X, lane, Xc);
-    g_put(s.N, lane, Zc);
-    __syncwarp(mask);
-    double zrow[GL];
-#pragma unroll
-    for (int k = 0; k < GL; ++k) zrow[k] = s.N[k * GL + lane];   // Z[lane][k]
-    g_mul(s.X, zrow, out);                                       // sum_k X[:, k] Z[lane][k]
-    __syncwarp(mask);
-}
 // symmetrise a column-distributed matrix: X <- (X + X^T)/2
 __device__ __forceinline__ void g_sym(GSmem& s, int lane, double (&Xc)[GL]) {
     const unsigned mask = half_mask();
@@ -413,124 +373,6 @@ __device__ __forceinline__ void g_sym(GSmem& s, int lane, double (&Xc)[GL]) {
 #pragma unroll
     for (int q = 0; q < GL; ++q) Xc[q] = 0.5 * (Xc[q] + s.X[q * GL + lane]);
     __syncwarp(mask);
-}
-
-// (ei then ej): the same combine as the b <= 3 chain path, every product
-// through the group:  M = (I + C_i J_j)^-1,  A = A_j M A_i,
-// bv = A_j M (bv_i + C_i eta_j) + bv_j,  C = A_j M C_i A_j^T + C_j,
-// eta = A_i^T M^T (eta_j - J_j bv_i) + eta_i,  J = A_i^T M^T J_j A_i + J_i.
-__device__ void g_combine(GSmem& s, int lane, const GElem& ei, const GElem& ej, GElem& r) {
-    const unsigned mask = half_mask();
-    double M[GL], T[GL], U[GL], v[GL];
-    g_inv_ixy(s, lane, ei.C, ej.J, M);
-    // A
-    g_put(s.X, lane, M); __syncwarp(mask);
-    g_mul(s.X, ei.A, T); __syncwarp(mask);            // M A_i
-    g_put(s.X, lane, ej.A); __syncwarp(mask);
-    g_mul(s.X, T, r.A); __syncwarp(mask);             // A_j M A_i
-    // bv
-    ggather(ej.eta, v);
-    double wc = ei.bv;
-#pragma unroll
-    for (int k = 0; k < GL; ++k) wc = fma(ei.C[k], v[k], wc);
-    ggather(wc, v);
-    g_put(s.X, lane, M); __syncwarp(mask);
-    const double zc = g_rowdot(s.X, lane, v); __syncwarp(mask);
-    ggather(zc, v);
-    g_put(s.X, lane, ej.A); __syncwarp(mask);
-    r.bv = g_rowdot(s.X, lane, v) + ej.bv; __syncwarp(mask);
-    // C
-    g_put(s.X, lane, M); __syncwarp(mask);
-    g_mul(s.X, ei.C, T); __syncwarp(mask);            // M C_i
-    g_put(s.X, lane, ej.A); __syncwarp(mask);
-    g_mul(s.X, T, U); __syncwarp(mask);               // A_j M C_i
-    g_mul_bt(s, lane, U, ej.A, T);                    // (A_j M C_i) A_j^T
-#pragma unroll
-    for (int q = 0; q < GL; ++q) r.C[q] = T[q] + ej.C[q];
-    g_sym(s, lane, r.C);
-    // eta
-    ggather(ei.bv, v);
-    double w2 = ej.eta;
-#pragma unroll
-    for (int k = 0; k < GL; ++k) w2 = fma(-ej.J[k], v[k], w2);
-    ggather(w2, v);
-    double z2 = 0.0;
-#pragma unroll
-    for (int k = 0; k < GL; ++k) z2 = fma(M[k], v[k], z2);
-    ggather(z2, v);
-    double e2 = ei.eta;
-#pragma unroll
-    for (int k = 0; k < GL; ++k) e2 = fma(ei.A[k], v[k], e2);
-    r.eta = e2;
-    // J
-    g_put(s.X, lane, M); __syncwarp(mask);
-    g_tmul(s.X, ej.J, T); __syncwarp(mask);           // M^T J_j
-    g_put(s.X, lane, T); __syncwarp(mask);
-    g_mul(s.X, ei.A, U); __syncwarp(mask);            // M^T J_j A_i
-    g_put(s.X, lane, ei.A); __syncwarp(mask);
-    g_tmul(s.X, U, T); __syncwarp(mask);              // A_i^T M^T J_j A_i
-#pragma unroll
-    for (int q = 0; q < GL; ++q) r.J[q] = T[q] + ei.J[q];
-    g_sym(s, lane, r.J);
-}
-
-// N(m, P) before element e, pushed through it:  M = (I + P J_e)^-1,
-// m' = A_e M (m + P eta_e) + bv_e,  P' = A_e M P A_e^T + C_e.
-__device__ void g_state_through(GSmem& s, int lane, const double (&P)[GL], double m, const GElem& e,
-                                double (&Po)[GL], double& mo) {
-    const unsigned mask = half_mask();
-    double M[GL], T[GL], U[GL], v[GL];
-    g_inv_ixy(s, lane, P, e.J, M);
-    ggather(e.eta, v);
-    double wc = m;
-#pragma unroll
-    for (int k = 0; k < GL; ++k) wc = fma(P[k], v[k], wc);
-    ggather(wc, v);
-    g_put(s.X, lane, M); __syncwarp(mask);
-    const double zc = g_rowdot(s.X, lane, v); __syncwarp(mask);
-    ggather(zc, v);
-    g_put(s.X, lane, e.A); __syncwarp(mask);
-    mo = g_rowdot(s.X, lane, v) + e.bv; __syncwarp(mask);
-    g_put(s.X, lane, M); __syncwarp(mask);
-    g_mul(s.X, P, T); __syncwarp(mask);               // M P
-    g_put(s.X, lane, e.A); __syncwarp(mask);
-    g_mul(s.X, T, U); __syncwarp(mask);               // A_e M P
-    g_mul_bt(s, lane, U, e.A, T);
-#pragma unroll
-    for (int q = 0; q < GL; ++q) Po[q] = T[q] + e.C[q];
-    g_sym(s, lane, Po);
-}
-
-// information (eta, J) after element e pulled back through it and joined
-// with e's own:  M = (I + C_e J)^-1,  eta' = A_e^T M^T (eta - J bv_e) + eta_e,
-// J' = A_e^T M^T J A_e + J_e.
-__device__ void g_info_through(GSmem& s, int lane, const GElem& e, const double (&J)[GL], double eta,
-                               double (&Jo)[GL], double& eo) {
-    const unsigned mask = half_mask();
-    double M[GL], T[GL], U[GL], v[GL];
-    g_inv_ixy(s, lane, e.C, J, M);
-    ggather(e.bv, v);
-    double w2 = eta;
-#pragma unroll
-    for (int k = 0; k < GL; ++k) w2 = fma(-J[k], v[k], w2);
-    ggather(w2, v);
-    double z2 = 0.0;
-#pragma unroll
-    for (int k = 0; k < GL; ++k) z2 = fma(M[k], v[k], z2);
-    ggather(z2, v);
-    double e2 = e.eta;
-#pragma unroll
-    for (int k = 0; k < GL; ++k) e2 = fma(e.A[k], v[k], e2);
-    eo = e2;
-    g_put(s.X, lane, M); __syncwarp(mask);
-    g_tmul(s.X, J, T); __syncwarp(mask);              // M^T J
-    g_put(s.X, lane, T); __syncwarp(mask);
-    g_mul(s.X, e.A, U); __syncwarp(mask);             // M^T J A_e
-    g_put(s.X, lane, e.A); __syncwarp(mask);
-    g_tmul(s.X, U, T); __syncwarp(mask);              // A_e^T M^T J A_e
-#pragma unroll
-    for (int q = 0; q < GL; ++q) Jo[q] = T[q] + e.J[q];
-    g_sym(s, lane, Jo);
 }
 
 // ------------------------------------------------------------------ k_gfold: in-chunk elimination
