@@ -579,15 +579,15 @@ class Batch:
             raise ValueError("theta must have n_series x %d entries" % self.model.num_params)
         return theta
 
-    def loglik(self, theta, sync=True, out=None):
+    def loglik(self, theta, sync=True, out=None, missing=False):
         ws = self.workspace(WS_LOGLIK)
         ll = out if out is not None else torch.empty(self.n_series, dtype=torch.float64, device=self.t.device)
         _check(spingp_loglik_batched(self.model.h, self.offsets, self.n_series, self.n_total, self.t, self.y,
-                                     self._theta(theta), ll, ws, ws.numel(), SYNC if sync else 0),
+                                     self._theta(theta), ll, ws, ws.numel(), Model._flags(sync, missing)),
                "spingp_loglik_batched")
         return ll
 
-    def grad(self, theta, sync=True, out=None):
+    def grad(self, theta, sync=True, out=None, missing=False):
         ws = self.workspace(WS_GRAD)
         if out is None:
             ll = torch.empty(self.n_series, dtype=torch.float64, device=self.t.device)
@@ -595,19 +595,19 @@ class Batch:
         else:
             ll, g = out
         _check(spingp_grad_batched(self.model.h, self.offsets, self.n_series, self.n_total, self.t, self.y,
-                                   self._theta(theta), ll, g, ws, ws.numel(), SYNC if sync else 0),
+                                   self._theta(theta), ll, g, ws, ws.numel(), Model._flags(sync, missing)),
                "spingp_grad_batched")
         return ll, g.view(self.n_series, self.model.num_params)
 
-    def posterior(self, theta, sync=True):
+    def posterior(self, theta, sync=True, missing=False):
         ws = self.workspace(WS_POSTERIOR)
         dev = self.t.device
         mean = torch.empty(self.n_total, dtype=torch.float64, device=dev)
         var = torch.empty(self.n_total, dtype=torch.float64, device=dev)
         ll = torch.empty(self.n_series, dtype=torch.float64, device=dev)
         _check(spingp_posterior_batched(self.model.h, self.offsets, self.n_series, self.n_total, self.t, self.y,
-                                        self._theta(theta), ll, mean, var, ws, ws.numel(), SYNC if sync else 0),
-               "spingp_posterior_batched")
+                                        self._theta(theta), ll, mean, var, ws, ws.numel(),
+                                        Model._flags(sync, missing)), "spingp_posterior_batched")
         return mean, var, ll
 
     def optimize(self, theta0, iterations=100, tol=1e-8, sync=True):

@@ -69,6 +69,30 @@ def test_batched_small(spec, L):
     assert np.allclose(ll3.cpu().numpy()[nz], ll[nz], rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("L", [0, 16])
+def test_batched_missing_observations(L):
+    """Missing observations (NaN, Eqs. mean4-mean6) inside a batch: runs of
+    them, single ones, a series with none observed and one observed only at
+    its ends -- log-likelihood, gradient and posterior of every series
+    against the oracle, where NaN means missing too."""
+    lengths = [40, 1, 3000, 7, 0, 513, 129, 1000, 64, 2500, 90]
+    offsets, t, y, th = small_batch("matern52", 19, lengths)
+    rng = np.random.default_rng(4)
+    miss = rng.random(len(y)) < 0.2
+    miss[offsets[2] + 100:offsets[2] + 700] = True          # a long run
+    miss[offsets[3]:offsets[4]] = True                       # nothing observed
+    miss[offsets[9] + 1:offsets[10] - 1] = True              # only the ends observed
+    y = y.copy()
+    y[miss] = np.nan
+    m = spingp.Model("matern52", chunk_len=L)
+    bt = spingp.Batch(m, _t(offsets, torch.int64), _t(t), _t(y))
+    ll, g = bt.grad(_t(th.reshape(-1)), missing=True)
+    mean, var, llp = bt.posterior(_t(th.reshape(-1)), missing=True)
+    check_series("matern52", offsets, t, y, th, ll.cpu().numpy(), g.cpu().numpy(), range(len(lengths)),
+                 mean.cpu().numpy(), var.cpu().numpy())
+    assert np.allclose(llp.cpu().numpy(), ll.cpu().numpy(), rtol=1e-12, atol=0)
+
+
 def test_batched_matches_single_series_path():
     """A batch of one equals the single-series entry point (within FP64
     reduction-order rounding)."""
