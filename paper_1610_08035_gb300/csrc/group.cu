@@ -89,9 +89,10 @@ __device__ __forceinline__ double gsum(double v) {
 }
 
 // all 16 entries of a lane-distributed vector
+template <int NR>
 __device__ __forceinline__ void ggather(double mine, double (&v)[GL]) {
 #pragma unroll
-    for (int r = 0; r < GL; ++r) v[r] = gshfl(mine, r);
+    for (int r = 0; r < NR; ++r) v[r] = gshfl(mine, r);
 }
 
 // ------------------------------------------------------------------ setup: per-block constants
@@ -187,9 +188,10 @@ __global__ void __launch_bounds__(256) k_gdisc(GModel gm, const double* __restri
 // ------------------------------------------------------------------ group linear algebra on columns
 
 // X <- blockdiag(Phi) X  (column-local: rows 2k, 2k+1 mix)
+template <int NR>
 __device__ __forceinline__ void g_left(const double* __restrict__ ph, double (&X)[GL]) {
 #pragma unroll
-    for (int k = 0; k < GK; ++k) {
+    for (int k = 0; k < NR / 2; ++k) {
         const double a = ph[4 * k], b = ph[4 * k + 1], c = ph[4 * k + 2], d = ph[4 * k + 3];
         const double x0 = X[2 * k], x1 = X[2 * k + 1];
         X[2 * k] = fma(a, x0, b * x1);
@@ -197,9 +199,10 @@ __device__ __forceinline__ void g_left(const double* __restrict__ ph, double (&X
     }
 }
 // X <- blockdiag(Phi)^T X
+template <int NR>
 __device__ __forceinline__ void g_left_t(const double* __restrict__ ph, double (&X)[GL]) {
 #pragma unroll
-    for (int k = 0; k < GK; ++k) {
+    for (int k = 0; k < NR / 2; ++k) {
         const double a = ph[4 * k], b = ph[4 * k + 1], c = ph[4 * k + 2], d = ph[4 * k + 3];
         const double x0 = X[2 * k], x1 = X[2 * k + 1];
         X[2 * k] = fma(a, x0, c * x1);
@@ -207,23 +210,25 @@ __device__ __forceinline__ void g_left_t(const double* __restrict__ ph, double (
     }
 }
 // column c of X Phi^T (right product: the partner column of c's block)
+template <int NR>
 __device__ __forceinline__ void g_right_t(const double* __restrict__ ph, int lane, double (&X)[GL]) {
     const int k = lane >> 1, odd = lane & 1;
     // row 'odd' of Phi_k: (Phi X^T)... column c of X Phi^T = sum_q X[:, 2k+q] Phi_k[odd][q]
     const double f0 = ph[4 * k + 2 * odd], f1 = ph[4 * k + 2 * odd + 1];
 #pragma unroll
-    for (int r = 0; r < GL; ++r) {
+    for (int r = 0; r < NR; ++r) {
         const double p = gxor(X[r], 1);
         const double x0 = odd ? p : X[r], x1 = odd ? X[r] : p;
         X[r] = fma(f0, x0, f1 * x1);
     }
 }
 // column c of X Phi: sum_q X[:, 2k+q] Phi_k[q][odd]
+template <int NR>
 __device__ __forceinline__ void g_right(const double* __restrict__ ph, int lane, double (&X)[GL]) {
     const int k = lane >> 1, odd = lane & 1;
     const double f0 = ph[4 * k + odd], f1 = ph[4 * k + 2 + odd];
 #pragma unroll
-    for (int r = 0; r < GL; ++r) {
+    for (int r = 0; r < NR; ++r) {
         const double p = gxor(X[r], 1);
         const double x0 = odd ? p : X[r], x1 = odd ? X[r] : p;
         X[r] = fma(f0, x0, f1 * x1);
@@ -244,10 +249,11 @@ __device__ __forceinline__ double g_vleft_t(const double* __restrict__ ph, int l
     return fma(ph[4 * k + odd], v0, ph[4 * k + 2 + odd] * v1);
 }
 // h^T x for a column: sum of the even entries
+template <int NR>
 __device__ __forceinline__ double g_hsum(const double (&X)[GL]) {
     double s = 0.0;
 #pragma unroll
-    for (int k = 0; k < GK; ++k) s += X[2 * k];
+    for (int k = 0; k < NR / 2; ++k) s += X[2 * k];
     return s;
 }
 
@@ -259,22 +265,27 @@ struct GElem {
 };
 
 // element e's value f of lane l at base[(f * ne + e) * GL + l]
+template <int NR>
 __device__ __forceinline__ void gelem_store(double* __restrict__ base, int64_t ne, int64_t e, int lane,
                                             const GElem& x) {
     double* p = base + e * GL + lane;
     const int64_t s = ne * GL;
 #pragma unroll
-    for (int r = 0; r < GL; ++r) { p[r * s] = x.A[r]; p[(GL + r) * s] = x.C[r]; p[(2 * GL + r) * s] = x.J[r]; }
+    for (int r = 0; r < GL; ++r) {
+        const bool in = r < NR;   // rows past the state are zero
+        p[r * s] = in ? x.A[r] : 0.0; p[(GL + r) * s] = in ? x.C[r] : 0.0; p[(2 * GL + r) * s] = in ? x.J[r] : 0.0;
+    }
     p[3 * GL * s] = x.bv;
     p[(3 * GL + 1) * s] = x.eta;
 }
 // a state (m, P) or information (eta, J): column + entry
+template <int NR>
 __device__ __forceinline__ void gvs_load(const double* __restrict__ base, int64_t ne, int64_t e, int lane,
                                          double (&S)[GL], double& v) {
     const double* p = base + e * GL + lane;
     const int64_t s = ne * GL;
 #pragma unroll
-    for (int r = 0; r < GL; ++r) S[r] = p[r * s];
+    for (int r = 0; r < GL; ++r) S[r] = (r < NR) ? p[r * s] : 0.0;
     v = p[GL * s];
 }
 
@@ -288,52 +299,56 @@ struct GSmem {
     double R[GL * GL];
 };
 
+template <int NR>
 __device__ __forceinline__ void g_put(double* __restrict__ sm, int lane, const double (&col)[GL]) {
 #pragma unroll
-    for (int r = 0; r < GL; ++r) sm[lane * GL + r] = col[r];
+    for (int r = 0; r < NR; ++r) sm[lane * GL + r] = col[r];
 }
 // out = M y where M's columns are in sm (column-major) and y is this lane's column
+template <int NR>
 __device__ __forceinline__ void g_mul(const double* __restrict__ sm, const double (&y)[GL], double (&out)[GL]) {
 #pragma unroll
-    for (int r = 0; r < GL; ++r) out[r] = 0.0;
+    for (int r = 0; r < NR; ++r) out[r] = 0.0;
 #pragma unroll
-    for (int k = 0; k < GL; ++k) {
+    for (int k = 0; k < NR; ++k) {
         const double yk = y[k];
 #pragma unroll
-        for (int r = 0; r < GL; ++r) out[r] = fma(sm[k * GL + r], yk, out[r]);
+        for (int r = 0; r < NR; ++r) out[r] = fma(sm[k * GL + r], yk, out[r]);
     }
 }
 // row 'lane' of M (columns in sm) dotted with a full vector
+template <int NR>
 __device__ __forceinline__ double g_rowdot(const double* __restrict__ sm, int lane, const double (&v)[GL]) {
     double s = 0.0;
 #pragma unroll
-    for (int k = 0; k < GL; ++k) s = fma(sm[k * GL + lane], v[k], s);
+    for (int k = 0; k < NR; ++k) s = fma(sm[k * GL + lane], v[k], s);
     return s;
 }
 
 // M = (I + X Y)^-1 with X (symmetric) given by this lane's column Xc, Y by its
 // column Yc; result: this lane's column of M in Mc.  Gauss-Jordan with partial
 // pivoting on the group (columns in shared memory).  I + X Y has eigenvalues >= 1.
+template <int NR>
 __device__ void g_inv_ixy(GSmem& s, int lane, const double (&Xc)[GL], const double (&Yc)[GL], double (&Mc)[GL]) {
     const unsigned mask = half_mask();
-    g_put(s.X, lane, Xc);
+    g_put<NR>(s.X, lane, Xc);
     __syncwarp(mask);
     double col[GL];
-    g_mul(s.X, Yc, col);            // column 'lane' of X Y
+    g_mul<NR>(s.X, Yc, col);            // column 'lane' of X Y
 #pragma unroll
-    for (int r = 0; r < GL; ++r)
+    for (int r = 0; r < NR; ++r)
         if (r == lane) col[r] += 1.0;
     __syncwarp(mask);
-    g_put(s.N, lane, col);
+    g_put<NR>(s.N, lane, col);
 #pragma unroll
-    for (int r = 0; r < GL; ++r) s.R[lane * GL + r] = (r == lane) ? 1.0 : 0.0;
+    for (int r = 0; r < NR; ++r) s.R[lane * GL + r] = (r == lane) ? 1.0 : 0.0;
     __syncwarp(mask);
 #pragma unroll 1
-    for (int k = 0; k < GL; ++k) {
+    for (int k = 0; k < NR; ++k) {
         // pivot row: largest |N[r][k]| for r >= k (every lane computes the same)
         int p = k;
         double best = fabs(s.N[k * GL + k]);
-        for (int r = k + 1; r < GL; ++r) {
+        for (int r = k + 1; r < NR; ++r) {
             const double v = fabs(s.N[k * GL + r]);
             if (v > best) { best = v; p = r; }
         }
@@ -348,10 +363,10 @@ __device__ void g_inv_ixy(GSmem& s, int lane, const double (&Xc)[GL], const doub
         double nk = s.N[lane * GL + k] * inv, rk = s.R[lane * GL + k] * inv;
         double colk[GL];
 #pragma unroll
-        for (int r = 0; r < GL; ++r) colk[r] = s.N[k * GL + r];
+        for (int r = 0; r < NR; ++r) colk[r] = s.N[k * GL + r];
         __syncwarp(mask);
 #pragma unroll
-        for (int r = 0; r < GL; ++r) {
+        for (int r = 0; r < NR; ++r) {
             if (r == k) continue;
             s.N[lane * GL + r] = fma(-colk[r], nk, s.N[lane * GL + r]);
             s.R[lane * GL + r] = fma(-colk[r], rk, s.R[lane * GL + r]);
@@ -361,17 +376,18 @@ __device__ void g_inv_ixy(GSmem& s, int lane, const double (&Xc)[GL], const doub
         __syncwarp(mask);
     }
 #pragma unroll
-    for (int r = 0; r < GL; ++r) Mc[r] = s.R[lane * GL + r];
+    for (int r = 0; r < NR; ++r) Mc[r] = s.R[lane * GL + r];
     __syncwarp(mask);
 }
 
 // symmetrise a column-distributed matrix: X <- (X + X^T)/2
+template <int NR>
 __device__ __forceinline__ void g_sym(GSmem& s, int lane, double (&Xc)[GL]) {
     const unsigned mask = half_mask();
-    g_put(s.X, lane, Xc);
+    g_put<NR>(s.X, lane, Xc);
     __syncwarp(mask);
 #pragma unroll
-    for (int q = 0; q < GL; ++q) Xc[q] = 0.5 * (Xc[q] + s.X[q * GL + lane]);
+    for (int q = 0; q < NR; ++q) Xc[q] = 0.5 * (Xc[q] + s.X[q * GL + lane]);
     __syncwarp(mask);
 }
 
@@ -389,6 +405,7 @@ struct GArgs {
     int missing;          // 1: a NaN observation is missing (a test point)
 };
 
+template <int NR>
 __global__ void __launch_bounds__(GCTA) k_gfold(GArgs a, double* __restrict__ nodes) {
     __shared__ double s_pinf[GL * GL], s_dpe[GL * GL];
     g_pinf_smem(a.gm, a.theta, a.gconst, s_pinf, s_dpe);
@@ -400,12 +417,12 @@ __global__ void __launch_bounds__(GCTA) k_gfold(GArgs a, double* __restrict__ no
     const double s2 = a.theta[a.gm.P - 1];
     double ph = 0.0;         // (Pinf h)[lane]
 #pragma unroll
-    for (int r = 0; r < GL; r += 2) ph += s_pinf[r * GL + lane];
+    for (int r = 0; r < NR; r += 2) ph += s_pinf[r * GL + lane];
     const int64_t s = c * a.L, e = min(a.n, s + a.L);
     GElem el;
     double Cm[GL];   // C - Pinf, column lane
 #pragma unroll
-    for (int r = 0; r < GL; ++r) {
+    for (int r = 0; r < NR; ++r) {
         el.A[r] = (s > 0 && r == lane && on) ? 1.0 : 0.0;
         el.J[r] = 0.0;
         Cm[r] = (s > 0) ? -s_pinf[r * GL + lane] : 0.0;
@@ -416,36 +433,36 @@ __global__ void __launch_bounds__(GCTA) k_gfold(GArgs a, double* __restrict__ no
         const double yi = a.y[i];
         if (i > 0) {
             const double* ph = a.phis + i * (4 * GK);
-            g_left(ph, el.A);
+            g_left<NR>(ph, el.A);
             el.bv = g_vleft(ph, lane, el.bv);
-            g_left(ph, Cm);
-            g_right_t(ph, lane, Cm);
+            g_left<NR>(ph, Cm);
+            g_right_t<NR>(ph, lane, Cm);
         }
         if (a.missing && isnan(yi)) continue;               // missing: no update (Eqs. mean4-mean6)
-        const double c0 = g_hsum(Cm) + ph;                  // (C h)[lane]
-        const double a0 = g_hsum(el.A);                      // (h^T A)[lane]
+        const double c0 = g_hsum<NR>(Cm) + ph;                  // (C h)[lane]
+        const double a0 = g_hsum<NR>(el.A);                      // (h^T A)[lane]
         const double S = s2 + gsum(((lane & 1) == 0) ? c0 : 0.0);
         const double rS = 1.0 / S;
         const double res = yi - gsum(((lane & 1) == 0) ? el.bv : 0.0);
         const double rr = res * rS;
         el.eta = fma(a0, rr, el.eta);
         double v[GL];
-        ggather(a0, v);
+        ggather<NR>(a0, v);
         const double ar = a0 * rS;
 #pragma unroll
-        for (int r = 0; r < GL; ++r) el.J[r] = fma(v[r], ar, el.J[r]);
+        for (int r = 0; r < NR; ++r) el.J[r] = fma(v[r], ar, el.J[r]);
         el.bv = fma(c0, rr, el.bv);
-        ggather(c0, v);
+        ggather<NR>(c0, v);
         const double cr = c0 * rS;
 #pragma unroll
-        for (int r = 0; r < GL; ++r) {
+        for (int r = 0; r < NR; ++r) {
             el.A[r] = fma(-v[r], ar, el.A[r]);
             Cm[r] = fma(-v[r], cr, Cm[r]);
         }
     }
 #pragma unroll
-    for (int r = 0; r < GL; ++r) el.C[r] = Cm[r] + s_pinf[r * GL + lane];
-    gelem_store(nodes, a.nc, c, lane, el);
+    for (int r = 0; r < NR; ++r) el.C[r] = Cm[r] + s_pinf[r * GL + lane];
+    gelem_store<NR>(nodes, a.nc, c, lane, el);
 }
 
 // ------------------------------------------------------------------ odd-even reduction, level by level
@@ -706,7 +723,7 @@ __global__ void __launch_bounds__(GSC) k_gscan_down(const double* __restrict__ l
 
 static constexpr int GNF = GL + 3;   // stored per lane per step: predicted covariance column, mean entry, v, 1/S
 
-template <int MODE>
+template <int MODE, int NR>
 __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restrict__ pre,
                                                  const double* __restrict__ suf, double* __restrict__ store,
                                                  double* __restrict__ part, double* __restrict__ mean_out,
@@ -717,6 +734,12 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
     __shared__ GSmem sm[GGRP];
     __shared__ double s_pinf[GL * GL], s_dpe[GL * GL];
     g_pinf_smem(a.gm, a.theta, a.gconst, s_pinf, s_dpe);
+    // the group scratch starts at zero: the column products below write only
+    // rows < NR, so rows past the state stay exactly zero
+    {
+        double* z = reinterpret_cast<double*>(sm);
+        for (int i = threadIdx.x; i < (int)(sizeof(sm) / sizeof(double)); i += blockDim.x) z[i] = 0.0;
+    }
     __syncthreads();
     const int lane = threadIdx.x & (GL - 1);
     const int g = threadIdx.x >> 4;
@@ -728,7 +751,7 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
     const double s2 = a.theta[a.gm.P - 1];
     double ph = 0.0;   // (Pinf h)[lane]
 #pragma unroll
-    for (int r = 0; r < GL; r += 2) ph += s_pinf[r * GL + lane];
+    for (int r = 0; r < NR; r += 2) ph += s_pinf[r * GL + lane];
     const int64_t s = c * a.L, e = min(a.n, s + a.L);
     int bad = 0;
 
@@ -736,9 +759,9 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
     double m, D[GL];
     {
         double P[GL];
-        gvs_load(pre, nc, c, lane, P, m);
+        gvs_load<NR>(pre, nc, c, lane, P, m);
 #pragma unroll
-        for (int r = 0; r < GL; ++r) D[r] = P[r] - s_pinf[r * GL + lane];
+        for (int r = 0; r < NR; ++r) D[r] = P[r] - s_pinf[r * GL + lane];
     }
     double quad = 0.0, prod = 1.0;
     int expo = 0;
@@ -751,16 +774,16 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
         if (i == 0) {
             mb = 0.0;
 #pragma unroll
-            for (int r = 0; r < GL; ++r) Db[r] = 0.0;
+            for (int r = 0; r < NR; ++r) Db[r] = 0.0;
         } else {
             const double* ph = a.phis + i * (4 * GK);
             mb = g_vleft(ph, lane, m);
 #pragma unroll
-            for (int r = 0; r < GL; ++r) Db[r] = D[r];
-            g_left(ph, Db);
-            g_right_t(ph, lane, Db);
+            for (int r = 0; r < NR; ++r) Db[r] = D[r];
+            g_left<NR>(ph, Db);
+            g_right_t<NR>(ph, lane, Db);
         }
-        const double p0 = g_hsum(Db) + ph;
+        const double p0 = g_hsum<NR>(Db) + ph;
         // a missing observation stores v = 1/S = 0, so the reverse sweep passes through it
         double rS = 0.0, v = 0.0;
         if (obs) {
@@ -778,17 +801,17 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
         if constexpr (BWD) {
             double* st = store + ((j * nc + c) * GNF) * GL + lane;
 #pragma unroll
-            for (int r = 0; r < GL; ++r) st[r * GL] = Db[r];
+            for (int r = 0; r < NR; ++r) st[r * GL] = Db[r];
             st[GL * GL] = mb;
             st[(GL + 1) * GL] = v;
             st[(GL + 2) * GL] = rS;
         }
         double pv[GL];
-        ggather(p0, pv);
+        ggather<NR>(p0, pv);
         m = fma(p0, v * rS, mb);
         const double pr = p0 * rS;
 #pragma unroll
-        for (int r = 0; r < GL; ++r) D[r] = fma(-pv[r], pr, Db[r]);
+        for (int r = 0; r < NR; ++r) D[r] = fma(-pv[r], pr, Db[r]);
     }
     double acc[2 + 2 * GMAXCOMP];
 #pragma unroll
@@ -800,20 +823,20 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
         double lh, Lh[GL];
         {
             double J[GL], eta, P[GL], W[GL], v[GL];
-            gvs_load(suf, nc, c, lane, J, eta);
+            gvs_load<NR>(suf, nc, c, lane, J, eta);
 #pragma unroll
-            for (int r = 0; r < GL; ++r) P[r] = D[r] + s_pinf[r * GL + lane];
-            g_inv_ixy(sm[g], lane, J, P, W);            // (I + J P)^-1
-            ggather(m, v);
+            for (int r = 0; r < NR; ++r) P[r] = D[r] + s_pinf[r * GL + lane];
+            g_inv_ixy<NR>(sm[g], lane, J, P, W);            // (I + J P)^-1
+            ggather<NR>(m, v);
             double w = eta;
 #pragma unroll
-            for (int k = 0; k < GL; ++k) w = fma(-J[k], v[k], w);   // (eta - J m)[lane]
-            ggather(w, v);
+            for (int k = 0; k < NR; ++k) w = fma(-J[k], v[k], w);   // (eta - J m)[lane]
+            ggather<NR>(w, v);
             const unsigned mask = half_mask();
-            g_put(sm[g].X, lane, W); __syncwarp(mask);
-            lh = -g_rowdot(sm[g].X, lane, v); __syncwarp(mask);
-            g_mul(sm[g].X, J, Lh); __syncwarp(mask);     // W J
-            g_sym(sm[g], lane, Lh);
+            g_put<NR>(sm[g].X, lane, W); __syncwarp(mask);
+            lh = -g_rowdot<NR>(sm[g].X, lane, v); __syncwarp(mask);
+            g_mul<NR>(sm[g].X, J, Lh); __syncwarp(mask);     // W J
+            g_sym<NR>(sm[g], lane, Lh);
         }
         double gp = 0.0;   // diagonal entry 'lane' of the Pinf adjoint
         double geq = 0.0;  // column 'lane' of the Pinf adjoint contracted with the EQ block's P_m
@@ -822,17 +845,17 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
             const double* st = store + ((j * nc + c) * GNF) * GL + lane;
             double Db[GL];
 #pragma unroll
-            for (int r = 0; r < GL; ++r) Db[r] = st[r * GL];
+            for (int r = 0; r < NR; ++r) Db[r] = st[r * GL];
             const double mb = st[GL * GL];
             const double v = st[(GL + 1) * GL];
             const double rS = st[(GL + 2) * GL];
-            const double k = (g_hsum(Db) + ph) * rS;
+            const double k = (g_hsum<NR>(Db) + ph) * rS;
             const double kl = gsum(k * lh);
             double kv[GL];
-            ggather(k, kv);
+            ggather<NR>(k, kv);
             double u = 0.0;
 #pragma unroll
-            for (int r = 0; r < GL; ++r) u = fma(Lh[r], kv[r], u);
+            for (int r = 0; r < NR; ++r) u = fma(Lh[r], kv[r], u);
             const double kuk = gsum(k * u);
             const double al = fma(v, rS, kl);
             const double cc = rS + kuk;
@@ -843,12 +866,12 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                 const double yi = a.y[i];
                 if (a.missing && isnan(yi)) {
                     // predicted only: mean = h^T (mb - Pb lh), variance = h^T Pb h - (Pb h)^T Lh (Pb h)
-                    const double p0 = g_hsum(Db) + ph;
+                    const double p0 = g_hsum<NR>(Db) + ph;
                     double pv[GL];
-                    ggather(p0, pv);
+                    ggather<NR>(p0, pv);
                     double lp = 0.0;
 #pragma unroll
-                    for (int r = 0; r < GL; ++r) lp = fma(Lh[r], pv[r], lp);
+                    for (int r = 0; r < NR; ++r) lp = fma(Lh[r], pv[r], lp);
                     const double hm = gsum(even ? mb : 0.0), pl = gsum(p0 * lh);
                     const double hph = gsum(even ? p0 : 0.0), plp = gsum(p0 * lp);
                     if (lane == 0) {
@@ -865,9 +888,9 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
             }
             const double lt = lh - (even ? al : 0.0);
             double uv[GL], Lt[GL];
-            ggather(u, uv);
+            ggather<NR>(u, uv);
 #pragma unroll
-            for (int r = 0; r < GL; ++r) {
+            for (int r = 0; r < NR; ++r) {
                 double x = Lh[r];
                 if ((r & 1) == 0) x -= u;
                 if (even) x -= uv[r];
@@ -875,16 +898,16 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                 Lt[r] = x;
             }
             double lv[GL], G[GL];
-            ggather(lt, lv);
+            ggather<NR>(lt, lv);
 #pragma unroll
-            for (int r = 0; r < GL; ++r) G[r] = 0.5 * fma(lv[r], lt, -Lt[r]);
+            for (int r = 0; r < NR; ++r) G[r] = 0.5 * fma(lv[r], lt, -Lt[r]);
             if constexpr (GRAD) {
 #pragma unroll
-                for (int r = 0; r < GL; ++r)
+                for (int r = 0; r < NR; ++r)
                     if (r == lane) gp += G[r];
                 if (has_eq) {
 #pragma unroll
-                    for (int r = 0; r < GL; ++r) geq = fma(s_dpe[r * GL + lane], G[r], geq);
+                    for (int r = 0; r < NR; ++r) geq = fma(s_dpe[r * GL + lane], G[r], geq);
                 }
             }
             if (i > 0) {
@@ -895,7 +918,7 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                     const double mp = gxor(mb, 1);
                     const double mb0 = even ? mb : mp, mb1 = even ? mp : mb;
 #pragma unroll
-                    for (int kb = 0; kb < GK; ++kb) {
+                    for (int kb = 0; kb < NR / 2; ++kb) {
                         if (kb >= a.gm.K) break;
                         const int kind = a.gm.bkind[kb];
                         const int cp = a.gm.bcomp[kb];
@@ -933,21 +956,21 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                 // propagate to the previous step: lh = Phi^T lt, Lh = Phi^T Lt Phi
                 lh = g_vleft_t(ph, lane, lt);
 #pragma unroll
-                for (int r = 0; r < GL; ++r) Lh[r] = Lt[r];
-                g_right(ph, lane, Lh);
-                g_left_t(ph, Lh);
+                for (int r = 0; r < NR; ++r) Lh[r] = Lt[r];
+                g_right<NR>(ph, lane, Lh);
+                g_left_t<NR>(ph, Lh);
                 if constexpr (GRAD) {
                     double ld = 0.0;
 #pragma unroll
-                    for (int r = 0; r < GL; ++r)
+                    for (int r = 0; r < NR; ++r)
                         if (r == lane) ld = Lh[r];
                     gp -= 0.5 * fma(lh, lh, -ld);
                     if (has_eq) {   // minus column 'lane' of Phi^T G Phi = (lh lh^T - Lh) / 2
                         double lv2[GL];
-                        ggather(lh, lv2);
+                        ggather<NR>(lh, lv2);
                         double t = 0.0;
 #pragma unroll
-                        for (int r = 0; r < GL; ++r) t = fma(s_dpe[r * GL + lane], fma(lv2[r], lh, -Lh[r]), t);
+                        for (int r = 0; r < NR; ++r) t = fma(s_dpe[r * GL + lane], fma(lv2[r], lh, -Lh[r]), t);
                         geq -= 0.5 * t;
                     }
                 }
@@ -1080,7 +1103,17 @@ int group_run(const GModel& gm, int mode, const double* t, const double* y, int6
     k_gsetup<<<1, 32, 0, st>>>(gm, theta, gconst, status);
     k_gdisc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gm, t, y, n, theta, phis, status, missing);
     const unsigned cgrid = (unsigned)((lay.nc + GGRP - 1) / GGRP);
-    k_gfold<<<cgrid, GCTA, 0, st>>>(a, (double*)(ws + lay.off_nodes[0]));
+    // rows of the per-lane column arithmetic: the state dimension rounded up to 4
+    const int NRr = (gm.b <= 4) ? 4 : (gm.b <= 8) ? 8 : (gm.b <= 12) ? 12 : 16;
+    auto fold = [&](double* nodes0) {
+        switch (NRr) {
+        case 4: k_gfold<4><<<cgrid, GCTA, 0, st>>>(a, nodes0); break;
+        case 8: k_gfold<8><<<cgrid, GCTA, 0, st>>>(a, nodes0); break;
+        case 12: k_gfold<12><<<cgrid, GCTA, 0, st>>>(a, nodes0); break;
+        default: k_gfold<16><<<cgrid, GCTA, 0, st>>>(a, nodes0); break;
+        }
+    };
+    fold((double*)(ws + lay.off_nodes[0]));
     if (ev) cudaEventRecord(ev[1], st);
     for (int l = 1; l <= lay.nlev; ++l)
         k_gscan_up<<<(unsigned)lay.lev_n[l], GSC, 0, st>>>(
@@ -1102,14 +1135,22 @@ int group_run(const GModel& gm, int mode, const double* t, const double* y, int6
     const double* pre = (const double*)(ws + lay.off_pre[0]);
     const double* suf = (const double*)(ws + lay.off_suf[0]);
     int na = 1;
+#define SPG_GCHUNK(M, NRv) k_gchunk<M, NRv><<<cgrid, GCTA, 0, st>>>(a, pre, suf, store, part, \
+                                                                    (M) == MODE_POSTERIOR ? mean_out : nullptr, \
+                                                                    (M) == MODE_POSTERIOR ? var_out : nullptr)
+#define SPG_GCHUNK_NR(M) \
+    switch (NRr) { case 4: SPG_GCHUNK(M, 4); break; case 8: SPG_GCHUNK(M, 8); break; \
+                   case 12: SPG_GCHUNK(M, 12); break; default: SPG_GCHUNK(M, 16); break; }
     if (mode == MODE_LOGLIK) {
-        k_gchunk<MODE_LOGLIK><<<cgrid, GCTA, 0, st>>>(a, pre, suf, store, part, nullptr, nullptr);
+        SPG_GCHUNK_NR(MODE_LOGLIK)
     } else if (mode == MODE_GRAD) {
-        k_gchunk<MODE_GRAD><<<cgrid, GCTA, 0, st>>>(a, pre, suf, store, part, nullptr, nullptr);
+        SPG_GCHUNK_NR(MODE_GRAD)
         na = GPART;
     } else {
-        k_gchunk<MODE_POSTERIOR><<<cgrid, GCTA, 0, st>>>(a, pre, suf, store, part, mean_out, var_out);
+        SPG_GCHUNK_NR(MODE_POSTERIOR)
     }
+#undef SPG_GCHUNK_NR
+#undef SPG_GCHUNK
     if (ev) cudaEventRecord(ev[3], st);
     k_gfinal<<<1, GFIN, 0, st>>>(gm, part, lay.nc, na, theta, gconst, ll_out, grad_out);
     if (ev) cudaEventRecord(ev[4], st);
