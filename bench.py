@@ -281,9 +281,9 @@ def extra_workloads(args, dev, flush, world, rank=0):
 # steps, or nodes for the BTD solver; the batched SCG's gradient evaluations
 # use the chain kernels' counts above.
 NEXT_FLOPS_PER_UNIT = {"prediction_n4m": 529.0, "literal_n1m": 3801.2, "btd_solve_n1m": 1221.0,
-                       "eq_b12_n1m": 15814.8, "scg_batch_4096": 268.2 + 364.2}
+                       "eq_b12_n1m": 12896.7, "scg_batch_4096": 268.2 + 364.2}
 NEXT_FP64_INST_PER_UNIT = {"prediction_n4m": 350.3, "literal_n1m": 2686.9, "btd_solve_n1m": 1044.3,
-                           "eq_b12_n1m": 10769.2, "scg_batch_4096": 167.9 + 223.7}
+                           "eq_b12_n1m": 8887.7, "scg_batch_4096": 167.9 + 223.7}
 
 
 def _next_roofline(key, units_per_s, fp64_tflops):
