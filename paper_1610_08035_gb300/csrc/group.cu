@@ -838,6 +838,11 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
             g_mul<NR>(sm[g].X, J, Lh); __syncwarp(mask);     // W J
             g_sym<NR>(sm[g], lane, Lh);
         }
+        // per-block sums of the rate terms (dt times d ll / dx), folded into
+        // the component slots once per chunk
+        double brate[NR / 2], benv[NR / 2];
+#pragma unroll
+        for (int kb = 0; kb < NR / 2; ++kb) { brate[kb] = 0.0; benv[kb] = 0.0; }
         double gp = 0.0;   // diagonal entry 'lane' of the Pinf adjoint
         double geq = 0.0;  // column 'lane' of the Pinf adjoint contracted with the EQ block's P_m
         for (int64_t i = e - 1; i >= s; --i) {
@@ -902,9 +907,10 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
 #pragma unroll
             for (int r = 0; r < NR; ++r) G[r] = 0.5 * fma(lv[r], lt, -Lt[r]);
             if constexpr (GRAD) {
+                double gsel = 0.0;   // G[lane][lane]: a select, then one add
 #pragma unroll
-                for (int r = 0; r < NR; ++r)
-                    if (r == lane) gp += G[r];
+                for (int r = 0; r < NR; ++r) gsel = (r == lane) ? G[r] : gsel;
+                gp += gsel;
                 if (has_eq) {
 #pragma unroll
                     for (int r = 0; r < NR; ++r) geq = fma(s_dpe[r * GL + lane], G[r], geq);
@@ -921,7 +927,6 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                     for (int kb = 0; kb < NR / 2; ++kb) {
                         if (kb >= a.gm.K) break;
                         const int kind = a.gm.bkind[kb];
-                        const int cp = a.gm.bcomp[kb];
                         const double d0 = Db[2 * kb], d1 = Db[2 * kb + 1];
                         const double g0 = G[2 * kb], g1 = G[2 * kb + 1];
                         const bool mine = (lane >> 1) == kb;
@@ -945,12 +950,8 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                                 if (mine) envr += lt * (even ? mb0 : mb1);
                             }
                         }
-#pragma unroll
-                        for (int q = 0; q < GMAXCOMP; ++q)
-                            if (q == cp) {
-                                acc[2 + 2 * q] = fma(rate, dt, acc[2 + 2 * q]);
-                                acc[3 + 2 * q] = fma(envr, dt, acc[3 + 2 * q]);
-                            }
+                        brate[kb] = fma(rate, dt, brate[kb]);
+                        if (kind == GB_QUASI) benv[kb] = fma(envr, dt, benv[kb]);
                     }
                 }
                 // propagate to the previous step: lh = Phi^T lt, Lh = Phi^T Lt Phi
@@ -977,6 +978,14 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
             }
         }
         if constexpr (GRAD) {
+#pragma unroll
+            for (int kb = 0; kb < NR / 2; ++kb) {
+                if (kb >= a.gm.K) break;
+                const int cp = a.gm.bcomp[kb];
+#pragma unroll
+                for (int q = 0; q < GMAXCOMP; ++q)
+                    if (q == cp) { acc[2 + 2 * q] += brate[kb]; acc[3 + 2 * q] += benv[kb]; }
+            }
             part[(2 + 2 * GMAXCOMP + lane) * nc + c] = gp;
             geq = gsum(geq);
             if (lane == 0) part[GP_EQ * nc + c] = geq;
