@@ -208,6 +208,25 @@ spingp_status spingp_profile_read(spingp_model* model, double* ms_out, int* call
 size_t spingp_probe_fp64_bytes(void);
 spingp_status spingp_probe_fp64(void* scratch, size_t scratch_bytes, double* tflops_out, void* stream);
 
+/* Log-likelihood and gradient from HOST buffers (Sec. 2.4; the same result
+ * as spingp_grad, bit for bit): t, y (n doubles each) and theta are host
+ * memory -- pinned memory lets the copies run asynchronously -- and ll_out
+ * (1 double) and grad_out (P doubles) are host memory written on the stream
+ * (valid after the stream synchronises; SPINGP_SYNC does that).  For the
+ * single-Matern chain path t and y are copied in pieces of whole fold blocks
+ * on a copy stream the model keeps, and each piece's elimination starts as
+ * soon as its piece has arrived, so the transfer overlaps the computation;
+ * structured models copy first, then run.  ws is device scratch of
+ * spingp_workspace_bytes_host(model, n) bytes (it also holds the device
+ * copies of t, y and theta).  The model's copy stream and events are
+ * created on the first call, on the current device; a model's host-buffer
+ * calls must not run concurrently from several host threads, and a model
+ * used this way stays on one device. */
+size_t spingp_workspace_bytes_host(const spingp_model* model, int64_t n);
+spingp_status spingp_grad_host(spingp_model* model, const double* t, const double* y, int64_t n,
+                               const double* theta, double* ll_out, double* grad_out, void* ws, size_t ws_bytes,
+                               unsigned flags, void* stream);
+
 /* Size of the fixed device scratch used by spingp_loglik_noalloc (8 MiB). */
 #define SPINGP_NOALLOC_SCRATCH_BYTES (8u << 20)
 

@@ -28,6 +28,10 @@ struct spingp_model {
     spg_prof* prof;  // NULL unless profiling was enabled
     int group;       // 1: structured model on the group path (spg::GModel below)
     spg::GModel gm;
+    // host-buffer calls: a copy stream and its events, created on first use
+    int feed_dev;    // device they belong to, -1 = none
+    cudaStream_t feed_copy, feed_fold[spg::FEED_PIECES];
+    cudaEvent_t feed_ev[1 + spg::FEED_PIECES], feed_done[spg::FEED_PIECES];
 };
 
 namespace {
@@ -277,6 +281,7 @@ spingp_status spingp_model_create(const spingp_model_desc* d, spingp_model** out
         } else return SPINGP_EINVAL;
     }
     m.P += 1;
+    m.feed_dev = -1;
     if (!single_matern(&m)) {
         if (!build_group(&m)) return SPINGP_EUNSUPPORTED;
         m.group = 1;
@@ -290,6 +295,18 @@ spingp_status spingp_model_create(const spingp_model_desc* d, spingp_model** out
 
 void spingp_model_destroy(spingp_model* m) {
     if (!m) return;
+    if (m->feed_dev >= 0) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(m->feed_dev);
+        cudaStreamDestroy(m->feed_copy);
+        for (int i = 0; i <= spg::FEED_PIECES; ++i) cudaEventDestroy(m->feed_ev[i]);
+        for (int i = 0; i < spg::FEED_PIECES; ++i) {
+            cudaStreamDestroy(m->feed_fold[i]);
+            cudaEventDestroy(m->feed_done[i]);
+        }
+        cudaSetDevice(cur);
+    }
     if (m->prof) {
         for (int i = 0; i < m->prof->cap; ++i)
             for (int k = 0; k < 5; ++k) cudaEventDestroy(m->prof->ev[i][k]);
@@ -392,9 +409,81 @@ spingp_status spingp_probe_fp64(void* scratch, size_t bytes, double* tflops_out,
     return spg::probe_fp64(scratch, bytes, tflops_out, (cudaStream_t)stream) ? SPINGP_ECUDA : SPINGP_OK;
 }
 
-// ---------------------------------------------------------------- hyperparameter fitting (Sec. 4.3)
+// ---------------------------------------------------------------- host buffers in, host results out
 
 static size_t align256c(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static size_t hostws_chain(const spingp_model* m, int64_t n) {
+    return align256c(spingp_workspace_bytes(m, n, SPINGP_WS_GRAD));
+}
+
+size_t spingp_workspace_bytes_host(const spingp_model* m, int64_t n) {
+    if (!m || n < 1) return 0;
+    const size_t base = spingp_workspace_bytes(m, n, SPINGP_WS_GRAD);
+    if (base == 0) return 0;
+    return hostws_chain(m, n) + 2 * align256c(sizeof(double) * (size_t)n) + 2 * align256c(sizeof(double) * 64);
+}
+
+static spingp_status feed_ready(spingp_model* m) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SPINGP_ECUDA;
+    if (m->feed_dev == dev) return SPINGP_OK;
+    if (m->feed_dev >= 0) return SPINGP_EINVAL;   // the model's copy stream lives on another device
+    if (cudaStreamCreateWithFlags(&m->feed_copy, cudaStreamNonBlocking) != cudaSuccess) return SPINGP_ECUDA;
+    for (int i = 0; i <= spg::FEED_PIECES; ++i)
+        if (cudaEventCreateWithFlags(&m->feed_ev[i], cudaEventDisableTiming) != cudaSuccess) return SPINGP_ECUDA;
+    for (int i = 0; i < spg::FEED_PIECES; ++i)
+        if (cudaStreamCreateWithFlags(&m->feed_fold[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&m->feed_done[i], cudaEventDisableTiming) != cudaSuccess)
+            return SPINGP_ECUDA;
+    m->feed_dev = dev;
+    return SPINGP_OK;
+}
+
+spingp_status spingp_grad_host(spingp_model* m, const double* t, const double* y, int64_t n, const double* theta,
+                               double* ll_out, double* grad_out, void* ws, size_t ws_bytes, unsigned flags,
+                               void* stream) {
+    if (!m || !t || !y || !theta || !ll_out || !grad_out || !ws || n < 1) return SPINGP_EINVAL;
+    if (((uintptr_t)ws & 255u) != 0) return SPINGP_EINVAL;
+    if (!single_matern(m) && !m->group) return SPINGP_EUNSUPPORTED;
+    const size_t need = spingp_workspace_bytes_host(m, n);
+    if (need == 0 || ws_bytes < need) return SPINGP_EINVAL;
+    spingp_status st = prepare_device();
+    if (st != SPINGP_OK) return st;
+    if ((st = feed_ready(m)) != SPINGP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* w = (char*)ws;
+    const size_t o_t = hostws_chain(m, n), o_y = o_t + align256c(sizeof(double) * (size_t)n);
+    const size_t o_th = o_y + align256c(sizeof(double) * (size_t)n), o_out = o_th + align256c(sizeof(double) * 64);
+    double *td = (double*)(w + o_t), *yd = (double*)(w + o_y), *thd = (double*)(w + o_th), *od = (double*)(w + o_out);
+    if (cudaMemcpyAsync(thd, theta, sizeof(double) * m->P, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return SPINGP_ECUDA;
+    cudaEvent_t* ev = NULL;
+    if ((st = profile_slot(m, &ev)) != SPINGP_OK) return st;
+    const int miss = (flags & SPINGP_MISSING_NAN) ? 1 : 0;
+    const int64_t L = chunk_len(m, n);
+    int rc;
+    if (m->group) {
+        if (cudaMemcpyAsync(td, t, sizeof(double) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(yd, y, sizeof(double) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return SPINGP_ECUDA;
+        rc = spg::group_run(m->gm, spg::MODE_GRAD, td, yd, n, L, thd, od, od + 1, NULL, NULL, ws, s, ev, miss);
+    } else {
+        spg::HostFeed f;
+        f.t = t; f.y = y; f.copy = m->feed_copy; f.npieces = spg::FEED_PIECES;
+        for (int i = 0; i <= spg::FEED_PIECES; ++i) f.ev[i] = m->feed_ev[i];
+        for (int i = 0; i < spg::FEED_PIECES; ++i) { f.fold[i] = m->feed_fold[i]; f.done[i] = m->feed_done[i]; }
+        rc = spg::matern_run(m->b, spg::MODE_GRAD, td, yd, n, L, thd, od, od + 1, NULL, NULL, ws, s, ev, miss, &f);
+    }
+    if (rc) return SPINGP_ECUDA;
+    if (cudaMemcpyAsync(ll_out, od, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(grad_out, od + 1, sizeof(double) * m->P, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return SPINGP_ECUDA;
+    if (flags & SPINGP_SYNC) return spingp_ws_status(ws, stream);
+    return SPINGP_OK;
+}
+
+// ---------------------------------------------------------------- hyperparameter fitting (Sec. 4.3)
 
 static size_t optimize_inner_bytes(const spingp_model* m, bool batched, int64_t S, int64_t n) {
     return batched ? spingp_workspace_bytes_batched(m, S, n, SPINGP_WS_GRAD)

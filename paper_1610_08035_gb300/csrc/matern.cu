@@ -236,11 +236,11 @@ __device__ __forceinline__ void tree_down_coop(double* spre, double* ssuf, const
 // so the prediction is a single sandwich Phi (C - Pinf) Phi^T.
 template <int B, bool BATCH>
 __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict__ nodes, double* __restrict__ btot,
-                                              double* __restrict__ phis) {
+                                              double* __restrict__ phis, int64_t blk0) {
     constexpr int NE = Dims<B>::NE;
     __shared__ double sm[CTA * NE];
     const int tid = threadIdx.x;
-    const int64_t blk = blockIdx.x;
+    const int64_t blk = blk0 + blockIdx.x;   // launches may cover a range of blocks
     const int64_t c = blk * CTA + tid;
     const int64_t nc = a.nchunks;
     const ChunkRange cr = chunk_range<BATCH>(a, c);
@@ -1082,7 +1082,7 @@ int matern_launch_count_t(int64_t n, int64_t L, int mode) {
 template <int B>
 int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
                  double* ll_out, double* grad_out, double* mean_out, double* var_out, void* wsv, cudaStream_t st,
-                 cudaEvent_t* ev, int missing) {
+                 cudaEvent_t* ev, int missing, const HostFeed* feed) {
     Layout<B> lay(n, L, mode);
     char* ws = (char*)wsv;
     int* status = (int*)ws;
@@ -1097,7 +1097,37 @@ int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t 
     const unsigned grid = (unsigned)lay.nb;
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
     if (ev) cudaEventRecord(ev[0], st);
-    k_fold<B, false><<<grid, CTA, 0, st>>>(a, nodes, btot, phis);
+    if (!feed) {
+        k_fold<B, false><<<grid, CTA, 0, st>>>(a, nodes, btot, phis, 0);
+    } else {
+        // t and y arrive from host memory in pieces of whole blocks on the copy
+        // stream; each piece's fold starts once its copy is done, so the
+        // copies of the later pieces overlap the fold of the earlier ones.
+        // (A chunk's first step reads the previous step's time: the pieces
+        // are copied in order, so it has arrived with an earlier piece.)
+        if (cudaEventRecord(feed->ev[0], st) != cudaSuccess) return 1;
+        if (cudaStreamWaitEvent(feed->copy, feed->ev[0], 0) != cudaSuccess) return 1;
+        const int64_t per = (lay.nb + feed->npieces - 1) / feed->npieces;
+        const int64_t span = (int64_t)CTA * L;   // steps per block
+        int p = 0;
+        for (int64_t b0 = 0; b0 < lay.nb; b0 += per, ++p) {
+            const int64_t b1 = min(lay.nb, b0 + per);
+            const int64_t s0 = b0 * span, s1 = min(n, b1 * span);
+            if (s1 > s0) {
+                const size_t bytes = sizeof(double) * (size_t)(s1 - s0);
+                if (cudaMemcpyAsync(const_cast<double*>(t) + s0, feed->t + s0, bytes, cudaMemcpyHostToDevice,
+                                    feed->copy) != cudaSuccess) return 1;
+                if (cudaMemcpyAsync(const_cast<double*>(y) + s0, feed->y + s0, bytes, cudaMemcpyHostToDevice,
+                                    feed->copy) != cudaSuccess) return 1;
+            }
+            if (cudaEventRecord(feed->ev[1 + p], feed->copy) != cudaSuccess) return 1;
+            if (cudaStreamWaitEvent(feed->fold[p], feed->ev[1 + p], 0) != cudaSuccess) return 1;
+            k_fold<B, false><<<(unsigned)(b1 - b0), CTA, 0, feed->fold[p]>>>(a, nodes, btot, phis, b0);
+            if (cudaEventRecord(feed->done[p], feed->fold[p]) != cudaSuccess) return 1;
+        }
+        for (int q = 0; q < p; ++q)
+            if (cudaStreamWaitEvent(st, feed->done[q], 0) != cudaSuccess) return 1;
+    }
     if (ev) cudaEventRecord(ev[1], st);
     scan_level<B>(btot, lay.nb, bpre, bsuf, lay, ws, 0, st);
     if (ev) cudaEventRecord(ev[2], st);
@@ -1156,7 +1186,7 @@ int matern_run_batched_t(int mode, const int64_t* offsets, int64_t nseries, int6
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
     if (ev) cudaEventRecord(ev[0], st);
     k_chunk_starts<<<1, CS_THREADS, 0, st>>>(offsets, nseries, n_total, L, cstart, status);
-    k_fold<B, true><<<grid, CTA, 0, st>>>(a, nodes, btot, phis);
+    k_fold<B, true><<<grid, CTA, 0, st>>>(a, nodes, btot, phis, 0);
     if (ev) cudaEventRecord(ev[1], st);
     scan_level<B>(btot, lay.nb, bpre, bsuf, lay, ws, 0, st);
     if (ev) cudaEventRecord(ev[2], st);
@@ -1208,14 +1238,17 @@ int matern_prepare() {
 
 int matern_run(int b, int mode, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
                double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws, cudaStream_t st,
-               cudaEvent_t* ev, int missing) {
+               cudaEvent_t* ev, int missing, const HostFeed* feed) {
     switch (b) {
-    case 1: return matern_run_t<1>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev, missing);
-    case 2: return matern_run_t<2>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev, missing);
+    case 1:
+        return matern_run_t<1>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev, missing, feed);
+    case 2:
+        return matern_run_t<2>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev, missing, feed);
     default:
-        return matern_run_t<3>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev, missing);
+        return matern_run_t<3>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev, missing, feed);
     }
 }
+int64_t matern_fold_blocks(int64_t n, int64_t L) { return ((n + L - 1) / L + CTA - 1) / CTA; }
 
 size_t matern_ws_bytes_batched(int b, int64_t nseries, int64_t n_total, int64_t L, int mode) {
     switch (b) {

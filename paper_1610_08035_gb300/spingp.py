@@ -26,7 +26,8 @@ EXPORTS = ("spingp_model_create", "spingp_model_destroy", "spingp_num_params", "
            "spingp_grad", "spingp_posterior", "spingp_workspace_bytes_batched", "spingp_loglik_batched",
            "spingp_grad_batched", "spingp_posterior_batched", "spingp_launch_count",
            "spingp_launch_count_batched", "spingp_profile_enable",
-           "spingp_profile_read", "spingp_probe_fp64_bytes", "spingp_probe_fp64", "spingp_loglik_noalloc",
+           "spingp_profile_read", "spingp_probe_fp64_bytes", "spingp_probe_fp64", "spingp_workspace_bytes_host",
+           "spingp_grad_host", "spingp_loglik_noalloc",
            "spingp_btd_workspace_bytes", "spingp_btd_solve", "spingp_btd_launch_count",
            "spingp_btd_diag_product_workspace_bytes", "spingp_btd_diag_product",
            "spingp_assemble_workspace_bytes", "spingp_assemble", "spingp_literal_workspace_bytes",
@@ -84,6 +85,9 @@ def load():
     lib.spingp_probe_fp64_bytes.restype = sz
     lib.spingp_probe_fp64.argtypes = [vp, sz, ctypes.POINTER(ctypes.c_double), vp]
     lib.spingp_loglik_noalloc.argtypes = [vp, dp, dp, i64, dp, dp, u32, vp]
+    lib.spingp_workspace_bytes_host.argtypes = [vp, i64]
+    lib.spingp_workspace_bytes_host.restype = sz
+    lib.spingp_grad_host.argtypes = [vp, dp, dp, i64, dp, dp, dp, vp, sz, u32, vp]
     lib.spingp_btd_workspace_bytes.argtypes = [ctypes.c_int, i64]
     lib.spingp_btd_workspace_bytes.restype = sz
     lib.spingp_btd_solve.argtypes = [ctypes.c_int, i64, dp, dp, dp, dp, dp, dp, dp, vp, sz, u32, vp]
@@ -257,6 +261,16 @@ def spingp_probe_fp64(device=None):
     return out.value
 
 
+def spingp_workspace_bytes_host(h, n):
+    return load().spingp_workspace_bytes_host(h, int(n))
+
+
+def spingp_grad_host(h, t, y, n, theta, ll_out, grad_out, ws, ws_bytes, flags, stream=None):
+    """t, y, theta, ll_out, grad_out: host tensors (pinned for overlap)."""
+    return load().spingp_grad_host(h, _ptr(t), _ptr(y), int(n), _ptr(theta), _ptr(ll_out), _ptr(grad_out),
+                                   _ptr(ws), ws_bytes, flags, stream if stream is not None else _stream())
+
+
 def spingp_loglik_noalloc(h, t, y, n, theta, ll_out, flags, stream=None):
     """spingp_loglik without a workspace: the library's fixed device scratch
     is used instead, so nothing is allocated (see include/spingp.h)."""
@@ -417,6 +431,31 @@ class Model:
             ll, g = out
         _check(spingp_grad(self.h, t, y, n, theta, ll, g, ws, ws.numel(), self._flags(sync, missing)),
                "spingp_grad")
+        return ll, g
+
+    def grad_host(self, t, y, theta, sync=True, out=None, missing=False, device=None):
+        """spingp_grad from host (CPU) tensors: t, y, theta float64 on the
+        host (pin them for overlapped copies); returns host (ll, grad)."""
+        for name, v in (("t", t), ("y", y), ("theta", theta)):
+            if not (isinstance(v, torch.Tensor) and not v.is_cuda and v.dtype == torch.float64 and v.is_contiguous()):
+                raise TypeError("%s must be a contiguous float64 host tensor" % name)
+        n = t.numel()
+        if y.numel() != n or theta.numel() != self.num_params:
+            raise ValueError("shapes do not match the model")
+        device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        key = ("host", device)
+        nbytes = spingp_workspace_bytes_host(self.h, n)
+        ws = self._ws.get(key)
+        if ws is None or ws.numel() < nbytes:
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+            self._ws[key] = ws
+        if out is None:
+            ll = torch.empty(1, dtype=torch.float64).pin_memory()
+            g = torch.empty(self.num_params, dtype=torch.float64).pin_memory()
+        else:
+            ll, g = out
+        _check(spingp_grad_host(self.h, t, y, n, theta, ll, g, ws, ws.numel(), self._flags(sync, missing)),
+               "spingp_grad_host")
         return ll, g
 
     def posterior(self, t, y, theta, sync=True, with_loglik=True, missing=False):
