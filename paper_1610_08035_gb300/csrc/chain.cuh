@@ -70,6 +70,107 @@ __device__ __forceinline__ void phi(double x, double e, double (&P)[B][B]) {
     }
 }
 
+// ------------------------------------------------------------------ Jordan coordinates (the chain kernels)
+//
+// F1 + I is nilpotent with one Jordan chain: (F1 + I) V = V N, where N has
+// ones on the superdiagonal and V is unit lower triangular with columns
+// v_1 = (1, -1, 1, ..) (the null vector of F1 + I) and (F1 + I) v_{k+1} = v_k
+// (b = 2: V = [[1, 0], [-1, 1]]; b = 3: V = [[1, 0, 0], [-1, 1, 0], [1, -2, 1]]).
+// The first row of V is e_1^T, so H V = H, and in the state w = V^-1 z~
+//     A_i = e^-x T(x),  T(x) = sum_k (N x)^k / k!   (unit upper triangular Toeplitz),
+//     Pinf = s_f PJ,  PJ = V^-1 P1 V^-T,  H = e_1^T,  dA/dx = (N - I) A.
+// A product with T costs b(b-1)/2 multiply-adds per column where a dense A
+// costs b^2, and a step's transition is the pair (x, e^-x).
+
+// PJ = V^-1 P1 V^-T (b = 2: [[1, 1], [1, 2]]; b = 3: [[1, 1, 2/3], [1, 4/3, 4/3], [2/3, 4/3, 8/3]]).
+template <int B>
+__device__ __forceinline__ double pj(int i, int j) {
+    if constexpr (B == 1) return 1.0;
+    else if constexpr (B == 2) return (i == 1 && j == 1) ? 2.0 : 1.0;
+    else {
+        const int lo = i < j ? i : j, hi = i < j ? j : i;
+        if (lo == 0) return hi == 2 ? (2.0 / 3.0) : 1.0;
+        if (lo == 1) return 4.0 / 3.0;
+        return 8.0 / 3.0;
+    }
+}
+
+// the Toeplitz coefficients of T(x): c[k] = x^k / k!
+template <int B>
+struct JCoef {
+    double c[B];
+    __device__ __forceinline__ explicit JCoef(double x) {
+        c[0] = 1.0;
+        if constexpr (B > 1) c[1] = x;
+        if constexpr (B > 2) c[2] = 0.5 * x * x;
+    }
+};
+
+// X <- e T X (X has NC columns; row r mixes rows k >= r, so rows go in increasing order)
+template <int B, int NC>
+__device__ __forceinline__ void jprop(const JCoef<B>& t, double e, double (&X)[B][NC]) {
+#pragma unroll
+    for (int r = 0; r < B; ++r)
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            double s = X[r][q];
+#pragma unroll
+            for (int k = r + 1; k < B; ++k) s = fma(t.c[k - r], X[k][q], s);
+            X[r][q] = s * e;
+        }
+}
+template <int B>
+__device__ __forceinline__ void jprop_vec(const JCoef<B>& t, double e, double (&v)[B]) {
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+        double s = v[r];
+#pragma unroll
+        for (int k = r + 1; k < B; ++k) s = fma(t.c[k - r], v[k], s);
+        v[r] = s * e;
+    }
+}
+// v <- e T^T v (entry r mixes entries k <= r: decreasing order)
+template <int B>
+__device__ __forceinline__ void jprop_tvec(const JCoef<B>& t, double e, double (&v)[B]) {
+#pragma unroll
+    for (int r = B - 1; r >= 0; --r) {
+        double s = v[r];
+#pragma unroll
+        for (int k = r - 1; k >= 0; --k) s = fma(t.c[r - k], v[k], s);
+        v[r] = s * e;
+    }
+}
+
+// Symmetric D <- e2 T D T^T (REV = false) or D <- e2 T^T D T (REV = true).
+// T^T = R T R for the index reversal R (T is Toeplitz), so the second is the
+// first on reversed indices.  Only the upper triangle of W = T D is needed:
+// (W T^T)_ij, j >= i, reads W_il for l >= j.
+template <int B, bool REV>
+__device__ __forceinline__ void jsand(const JCoef<B>& t, double e2, double (&D)[B][B]) {
+    double W[B][B];
+#pragma unroll
+    for (int i = 0; i < B; ++i)
+#pragma unroll
+        for (int j = i; j < B; ++j) {
+            const int ii = REV ? B - 1 - i : i, jj = REV ? B - 1 - j : j;
+            double s = D[ii][jj];
+#pragma unroll
+            for (int k = i + 1; k < B; ++k) s = fma(t.c[k - i], D[REV ? B - 1 - k : k][jj], s);
+            W[i][j] = s;
+        }
+#pragma unroll
+    for (int i = 0; i < B; ++i)
+#pragma unroll
+        for (int j = i; j < B; ++j) {
+            double s = W[i][j];
+#pragma unroll
+            for (int l = j + 1; l < B; ++l) s = fma(t.c[l - j], W[i][l], s);
+            const int ii = REV ? B - 1 - i : i, jj = REV ? B - 1 - j : j;
+            D[ii][jj] = s * e2;
+            D[jj][ii] = s * e2;
+        }
+}
+
 // ------------------------------------------------------------------ small dense helpers (fully unrolled)
 
 template <int B>

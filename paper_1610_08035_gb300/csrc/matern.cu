@@ -229,11 +229,12 @@ __device__ __forceinline__ void tree_down_coop(double* spre, double* ssuf, const
 
 // ------------------------------------------------------------------ k_fold
 
-// One thread per chunk: discretise every step (storing Phi for the later
-// pass) and eliminate the chunk's interior nodes into its element; then the
-// block's odd-even up-sweep over its CTA elements, writing every tree node
-// and the block total.  The conditional covariance is carried as C - Pinf,
-// so the prediction is a single sandwich Phi (C - Pinf) Phi^T.
+// One thread per chunk: discretise every step (storing x = lam dt and e^-x
+// for the later pass) and eliminate the chunk's interior nodes into its
+// element; then the block's odd-even up-sweep over its CTA elements, writing
+// every tree node and the block total.  Jordan coordinates (chain.cuh); the
+// conditional covariance is carried as C - Pinf, so the prediction is a
+// single sandwich e^-2x T (C - Pinf) T^T.
 template <int B, bool BATCH>
 __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict__ nodes, double* __restrict__ btot,
                                               double* __restrict__ phis, int64_t blk0) {
@@ -251,6 +252,9 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
         const double ell = cr.th[0], sf = cr.th[1], s2 = cr.th[2];
         if (!theta_ok<B>(ell, sf, s2)) bad |= ST_EINVAL;
         const double lam = sqrt(2.0 * B - 1.0) / ell;
+        double sp0[B];   // first column of Pinf
+#pragma unroll
+        for (int r = 0; r < B; ++r) sp0[r] = sf * pj<B>(r, 0);
         const int64_t s = cr.s, e = cr.e;
         // el.C holds C - Pinf until the end of the chunk
         if (s == cr.s0) {
@@ -263,7 +267,7 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
 #pragma unroll
             for (int i = 0; i < B; ++i)
 #pragma unroll
-                for (int j = 0; j < B; ++j) el.C[i][j] = -sf * p1<B>(i, j);
+                for (int j = 0; j < B; ++j) el.C[i][j] = -sf * pj<B>(i, j);
         }
         double tp = (s > cr.s0) ? a.t[s - 1] : 0.0;
         for (int64_t i = s; i < e; ++i) {
@@ -273,28 +277,17 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
             if (i > cr.s0) {
                 const double dt = ti - tp;
                 if (dt < 0.0) bad |= ST_ENOTSORTED;
-                const double x = lam * dt;
-                double Ph[B][B], T[B][B];
-                phi<B>(x, exp(-x), Ph);
+                const double x = lam * dt, ex = exp(-x);
                 {
-                    double* ph = phis + ((i - s) * (B * B)) * nc + c;
-#pragma unroll
-                    for (int r = 0; r < B; ++r)
-#pragma unroll
-                        for (int q = 0; q < B; ++q) ph[(r * B + q) * nc] = Ph[r][q];
+                    double* ph = phis + ((i - s) * 2) * nc + c;
+                    ph[0] = x;
+                    ph[nc] = ex;
                 }
-                // A <- Phi A,  bv <- Phi bv,  C <- Phi (C - Pinf) Phi^T + Pinf
-                mat_mul<B>(Ph, el.A, T);
-#pragma unroll
-                for (int r = 0; r < B; ++r)
-#pragma unroll
-                    for (int q = 0; q < B; ++q) el.A[r][q] = T[r][q];
-                double w[B];
-                mat_vec<B>(Ph, el.bv, w);
-#pragma unroll
-                for (int r = 0; r < B; ++r) el.bv[r] = w[r];
-                mat_mul<B>(Ph, el.C, T);
-                mat_mul_t_sym<B>(T, Ph, el.C);
+                // A <- e T A,  bv <- e T bv,  C - Pinf <- e^2 T (C - Pinf) T^T
+                const JCoef<B> tc(x);
+                jprop<B, B>(tc, ex, el.A);
+                jprop_vec<B>(tc, ex, el.bv);
+                jsand<B, false>(tc, ex * ex, el.C);
             }
             // condition on y_i: innovation of y_i given the node before the chunk
             // (a missing observation has infinite noise: no update, Eqs. mean4-mean6)
@@ -303,7 +296,7 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
 #pragma unroll
             for (int r = 0; r < B; ++r) {
                 a0[r] = el.A[0][r];
-                c0[r] = (p1<B>(r, 0) != 0.0) ? el.C[r][0] + sf * p1<B>(r, 0) : el.C[r][0];
+                c0[r] = el.C[r][0] + sp0[r];
             }
             const double S = c0[0] + s2;
             const double rS = 1.0 / S;
@@ -331,7 +324,7 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
 #pragma unroll
         for (int r = 0; r < B; ++r)
 #pragma unroll
-            for (int q = 0; q < B; ++q) el.C[r][q] += sf * p1<B>(r, q);
+            for (int q = 0; q < B; ++q) el.C[r][q] += sf * pj<B>(r, q);
     }
     if (bad) atomicOr(a.status, bad);
     // odd-even up-sweep inside the block (chunks past the end are identities):
@@ -500,9 +493,9 @@ __global__ void __launch_bounds__(SCAN_CTA, 1) k_scan_tile(const double* __restr
 
 // ------------------------------------------------------------------ k_chunk (forward, then reverse sweep)
 
-// per-block partial sums: ll, d/dlam, d/d(s_n), the adjoint of Pinf on the
-// entries where P1 is non-zero (packed; the others stay zero)
-template <int B> struct Acc { static constexpr int N = 3 + Dims<B>::NS; };
+// per-block partial sums: ll, sum_i x_i d ll/dx_i, 2 d ll/d(s_n), y^T C^-1 y,
+// observed steps
+template <int B> struct Acc { static constexpr int N = 5; };
 // per-step stored values: predicted mean (B), predicted covariance minus Pinf
 // (packed), innovation, 1/S
 template <int B> struct Stored { static constexpr int N = B + Dims<B>::NS + 2; };
@@ -521,11 +514,15 @@ template <int B> struct Stored { static constexpr int N = B + Dims<B>::NS + 2; }
 //       cc = 1/S + k^T Lh k        (C^-1)_ii
 //       lt = lh - al e1,  Lt = (I - k e1^T)^T Lh (I - k e1^T) + e1 e1^T / S
 //       G  = (lt lt^T - Lt)/2      d ll / d(predicted covariance)
-//       lh <- Phi^T lt, Lh <- Phi^T Lt Phi   (to the previous step)
+//       lh <- A^T lt, Lh <- A^T Lt A   (to the previous step)
 //     posterior mean_i = y_i - s_n al, latent variance = s_n k_0 - s_n^2 k^T Lh k
 //     (the diagonal of the selected inverse); gradient terms
-//       d ll/dx_i = -lt^T F1 mb + 2 <G, F1 (Pb - Pinf)>,  x_i = lam dt_i
-//       d ll/ds_n = sum (al^2 - cc)/2,  d ll/dPinf = sum G - sum Phi^T G Phi.
+//       d ll/dx_i = -lt^T F mb + 2 <G, F (Pb - Pinf)>,  x_i = lam dt_i, F = N - I
+//       (A = e^-x T(x) in Jordan coordinates, dA/dx = F A; Pinf and H do
+//       not depend on lam there), d ll/ds_n = sum (al^2 - cc)/2.
+//     d ll/ds_f follows from the others: ll(c s_f, c s_n) has derivative
+//     (y^T C^-1 y - n_obs)/2 in c at c = 1 (C scales by c), so
+//     s_f d ll/ds_f = (y^T C^-1 y - n_obs)/2 - s_n d ll/ds_n.
 //  4. Fixed-order block reduction of the partial sums.
 template <int B, int MODE, bool BATCH>
 __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __restrict__ nodes,
@@ -612,6 +609,9 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
     int bad = 0;
     if (cr.valid) {
         const int64_t s = cr.s, e = cr.e;
+        double sp0[B];   // first column of Pinf
+#pragma unroll
+        for (int r = 0; r < B; ++r) sp0[r] = sf * pj<B>(r, 0);
         // ---- 2. forward: filtered mean m and D = P - Pinf
         double m[B], D[B][B];
         {
@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
 #pragma unroll
             for (int r = 0; r < B; ++r)
 #pragma unroll
-                for (int q = 0; q < B; ++q) D[r][q] = P[r][q] - sf * p1<B>(r, q);
+                for (int q = 0; q < B; ++q) D[r][q] = P[r][q] - sf * pj<B>(r, q);
         }
         double quad = 0.0, prod = 1.0;
         int expo = 0;
@@ -636,19 +636,21 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
 #pragma unroll
                     for (int q = 0; q < B; ++q) Db[r][q] = 0.0; }
             } else {
-                double Ph[B][B], T[B][B];
-                const double* ph = phis + (j * (B * B)) * nc + c;
+                const double* ph = phis + (j * 2) * nc + c;
+                const double x = ph[0], ex = ph[nc];
+                const JCoef<B> tc(x);
 #pragma unroll
-                for (int r = 0; r < B; ++r)
+                for (int r = 0; r < B; ++r) {
+                    mb[r] = m[r];
 #pragma unroll
-                    for (int q = 0; q < B; ++q) Ph[r][q] = ph[(r * B + q) * nc];
-                mat_vec<B>(Ph, m, mb);
-                mat_mul<B>(Ph, D, T);
-                mat_mul_t_sym<B>(T, Ph, Db);
+                    for (int q = 0; q < B; ++q) Db[r][q] = D[r][q];
+                }
+                jprop_vec<B>(tc, ex, mb);
+                jsand<B, false>(tc, ex * ex, Db);
             }
             double p0[B];   // first column of the predicted covariance
 #pragma unroll
-            for (int r = 0; r < B; ++r) p0[r] = (r == 0 || p1<B>(r, 0) != 0.0) ? Db[r][0] + sf * p1<B>(r, 0) : Db[r][0];
+            for (int r = 0; r < B; ++r) p0[r] = Db[r][0] + sp0[r];
             // a missing observation stores v = 1/S = 0: the reverse sweep then
             // passes its adjoints through unchanged
             double rS = 0.0, v = 0.0;
@@ -684,6 +686,8 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
             }
         }
         acc[0] = -0.5 * (quad + log(prod) + (double)expo * LN2 + (double)nobs * LOG_2PI);
+        acc[3] = quad;
+        acc[4] = (double)nobs;
 
         if constexpr (BWD) {
             // ---- 3. reverse sweep, seeded by the information after the chunk
@@ -694,7 +698,7 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
 #pragma unroll
                 for (int r = 0; r < B; ++r)
 #pragma unroll
-                    for (int q = 0; q < B; ++q) P[r][q] = D[r][q] + sf * p1<B>(r, q);
+                    for (int q = 0; q < B; ++q) P[r][q] = D[r][q] + sf * pj<B>(r, q);
                 mat_mul<B>(J, P, N);
 #pragma unroll
                 for (int i = 0; i < B; ++i) N[i][i] += 1.0;
@@ -708,11 +712,7 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
                 mat_mul<B>(W, J, Lh);
                 symmetrize<B>(Lh);
             }
-            double gl = 0.0, gs = 0.0, GP[B][B];
-#pragma unroll
-            for (int i = 0; i < B; ++i)
-#pragma unroll
-                for (int j = 0; j < B; ++j) GP[i][j] = 0.0;
+            double gx = 0.0, gs = 0.0;
             for (int64_t i = e - 1; i >= s; --i) {
                 const int64_t j = i - s;
                 const double* st = store + (j * NF) * nc + c;
@@ -726,10 +726,9 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
                     for (int q = r; q < B; ++q) { Db[r][q] = st[(f++) * nc]; Db[q][r] = Db[r][q]; }
                 const double v = st[(f++) * nc];
                 const double rS = st[(f++) * nc];
-                double k[B];
+                double p0[B], k[B];
 #pragma unroll
-                for (int r = 0; r < B; ++r)
-                    k[r] = ((r == 0 || p1<B>(r, 0) != 0.0) ? Db[r][0] + sf * p1<B>(r, 0) : Db[r][0]) * rS;
+                for (int r = 0; r < B; ++r) { p0[r] = Db[r][0] + sp0[r]; k[r] = p0[r] * rS; }
                 double kl = 0.0, u[B], kuk = 0.0;
 #pragma unroll
                 for (int r = 0; r < B; ++r) kl = fma(k[r], lh[r], kl);
@@ -743,10 +742,7 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
                     const double yi = a.y[i];
                     if (a.missing && isnan(yi)) {
                         // predicted only: mean = (mb - Pb lh)_0, variance = Pb_00 - Pb_0^T Lh Pb_0
-                        double p0[B], w[B], pl = 0.0, q = 0.0;
-#pragma unroll
-                        for (int r = 0; r < B; ++r)
-                            p0[r] = (r == 0 || p1<B>(r, 0) != 0.0) ? Db[r][0] + sf * p1<B>(r, 0) : Db[r][0];
+                        double w[B], pl = 0.0, q = 0.0;
                         mat_vec<B>(Lh, p0, w);
 #pragma unroll
                         for (int r = 0; r < B; ++r) { pl = fma(p0[r], lh[r], pl); q = fma(p0[r], w[r], q); }
@@ -757,7 +753,7 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
                         var_out[i] = s2 * k[0] - s2 * s2 * kuk;
                     }
                 }
-                double lt[B], Lt[B][B], G[B][B];
+                double lt[B], Lt[B][B];
 #pragma unroll
                 for (int r = 0; r < B; ++r) {
                     lt[r] = lh[r];
@@ -768,65 +764,49 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
 #pragma unroll
                 for (int q = 1; q < B; ++q) { Lt[0][q] -= u[q]; Lt[q][0] = Lt[0][q]; }
                 Lt[0][0] = Lt[0][0] - 2.0 * u[0] + cc;
-                if constexpr (GRAD) {
-#pragma unroll
-                    for (int r = 0; r < B; ++r)
-#pragma unroll
-                        for (int q = r; q < B; ++q) {
-                            G[r][q] = 0.5 * fma(lt[r], lt[q], -Lt[r][q]);
-                            G[q][r] = G[r][q];
-                            if (p1<B>(r, q) != 0.0) GP[r][q] += G[r][q];
-                        }
-                }
                 if (i > cr.s0) {
-                    const double dt = a.t[i] - a.t[i - 1];
+                    const double* ph = phis + (j * 2) * nc + c;
+                    const double x = ph[0], ex = ph[nc];
                     if constexpr (GRAD) {
-                        // d ll / dx = -lt^T F1 mb + 2 <G, F1 Db>
-                        double fm = 0.0, fg = 0.0, cm = 0.0;
-#pragma unroll
-                        for (int r = 0; r + 1 < B; ++r) fm = fma(lt[r], mb[r + 1], fm);
-#pragma unroll
-                        for (int q = 0; q < B; ++q) cm = fma(fcoef<B>(q), mb[q], cm);
-                        fm = fma(-lt[B - 1], cm, fm);
-#pragma unroll
-                        for (int r = 0; r + 1 < B; ++r)
-#pragma unroll
-                            for (int q = 0; q < B; ++q) fg = fma(G[r][q], Db[r + 1][q], fg);
-#pragma unroll
-                        for (int q = 0; q < B; ++q) {
-                            double cd = 0.0;
-#pragma unroll
-                            for (int jj = 0; jj < B; ++jj) cd = fma(fcoef<B>(jj), Db[jj][q], cd);
-                            fg = fma(-G[B - 1][q], cd, fg);
-                        }
-                        gl = fma(2.0 * fg - fm, dt, gl);
-                    }
-                    double Ph[B][B], T[B][B];
-                    const double* ph = phis + (j * (B * B)) * nc + c;
-#pragma unroll
-                    for (int r = 0; r < B; ++r)
-#pragma unroll
-                        for (int q = 0; q < B; ++q) Ph[r][q] = ph[(r * B + q) * nc];
-                    mat_tvec<B>(Ph, lt, lh);
-                    mat_mul<B>(Lt, Ph, T);
-                    mat_tmul_sym<B>(Ph, T, Lh);
-                    if constexpr (GRAD) {
+                        // d ll/dx = <G2, F Db> - lt^T F mb with G2 = lt lt^T - Lt (= 2 G), F = N - I:
+                        // <G2, N Db> - <G2, Db> - lt^T N mb + lt^T mb
+                        double G2[B][B];
 #pragma unroll
                         for (int r = 0; r < B; ++r)
 #pragma unroll
-                            for (int q = r; q < B; ++q)
-                                if (p1<B>(r, q) != 0.0) GP[r][q] -= 0.5 * fma(lh[r], lh[q], -Lh[r][q]);
+                            for (int q = r; q < B; ++q) { G2[r][q] = fma(lt[r], lt[q], -Lt[r][q]); G2[q][r] = G2[r][q]; }
+                        double gn = 0.0, go = 0.0, gd = 0.0, mn = 0.0, md = 0.0;
+#pragma unroll
+                        for (int r = 0; r + 1 < B; ++r)
+#pragma unroll
+                            for (int q = 0; q < B; ++q) gn = fma(G2[r][q], Db[r + 1][q], gn);
+#pragma unroll
+                        for (int r = 0; r < B; ++r)
+#pragma unroll
+                            for (int q = r + 1; q < B; ++q) go = fma(G2[r][q], Db[r][q], go);
+#pragma unroll
+                        for (int r = 0; r < B; ++r) gd = fma(G2[r][r], Db[r][r], gd);
+#pragma unroll
+                        for (int r = 0; r + 1 < B; ++r) mn = fma(lt[r], mb[r + 1], mn);
+#pragma unroll
+                        for (int r = 0; r < B; ++r) md = fma(lt[r], mb[r], md);
+                        const double dx = (gn - fma(2.0, go, gd)) - (mn - md);
+                        gx = fma(dx, x, gx);
                     }
+                    const JCoef<B> tc(x);
+#pragma unroll
+                    for (int r = 0; r < B; ++r) {
+                        lh[r] = lt[r];
+#pragma unroll
+                        for (int q = 0; q < B; ++q) Lh[r][q] = Lt[r][q];
+                    }
+                    jprop_tvec<B>(tc, ex, lh);
+                    jsand<B, true>(tc, ex * ex, Lh);
                 }
             }
             if constexpr (GRAD) {
-                acc[1] = gl;
+                acc[1] = gx;
                 acc[2] = gs;
-                int f = 3;
-#pragma unroll
-                for (int r = 0; r < B; ++r)
-#pragma unroll
-                    for (int q = r; q < B; ++q) acc[f++] = GP[r][q];
             }
         }
     }
@@ -857,6 +837,17 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
 
 // ------------------------------------------------------------------ k_finalize (fixed-order reduction)
 
+// The gradient from the summed partials (gx = sum_i x_i d ll/dx_i,
+// gs = 2 d ll/ds_n, quad = y^T C^-1 y, nobs observed steps).  x = lam dt with
+// lam = sqrt(2b - 1)/l, so d ll/dl = -gx / l; s_f from the scaling identity.
+__device__ __forceinline__ void chain_grad(double gx, double gs, double quad, double nobs, const double* theta,
+                                           double* g) {
+    const double ell = theta[0], sf = theta[1], s2 = theta[2];
+    g[0] = -gx / ell;
+    g[2] = 0.5 * gs;
+    g[1] = (0.5 * (quad - nobs) - s2 * g[2]) / sf;
+}
+
 template <int B>
 __global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ part, int64_t nb, int na,
                                                   const double* __restrict__ theta, double* __restrict__ ll_out,
@@ -876,22 +867,8 @@ __global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ par
     }
     if (tid == 0) {
         if (ll_out) ll_out[0] = red[0];
-        if (grad_out && na == Acc<B>::N) {
-            const double ell = theta[0];
-            const double lam = sqrt(2.0 * B - 1.0) / ell;
-            grad_out[0] = red[1 * 256] * (-lam / ell);   // dl/dl = dl/dlam * dlam/dl
-            double gsf = 0.0;
-            int f = 3;
-#pragma unroll
-            for (int r = 0; r < B; ++r)
-#pragma unroll
-                for (int q = r; q < B; ++q) {
-                    const double w = (r == q) ? 1.0 : 2.0;
-                    gsf += w * p1<B>(r, q) * red[(f++) * 256];
-                }
-            grad_out[1] = gsf;
-            grad_out[2] = 0.5 * red[2 * 256];
-        }
+        if (grad_out && na == Acc<B>::N)
+            chain_grad(red[1 * 256], red[2 * 256], red[3 * 256], red[4 * 256], theta, grad_out);
     }
 }
 
@@ -973,23 +950,7 @@ __global__ void __launch_bounds__(256) k_finalize_batched(const double* __restri
         for (int f = 0; f < NA; ++f) acc[f] += __shfl_xor_sync(0xffffffffu, acc[f], d);
     if (lane == 0) {
         if (ll_out) ll_out[w] = acc[0];
-        if (grad_out && na == NA) {
-            const double ell = theta[w * P];
-            const double lam = sqrt(2.0 * B - 1.0) / ell;
-            double* g = grad_out + w * P;
-            g[0] = acc[1] * (-lam / ell);
-            double gsf = 0.0;
-            int f = 3;
-#pragma unroll
-            for (int r = 0; r < B; ++r)
-#pragma unroll
-                for (int q = r; q < B; ++q) {
-                    const double wt = (r == q) ? 1.0 : 2.0;
-                    gsf += wt * p1<B>(r, q) * acc[f++];
-                }
-            g[1] = gsf;
-            g[2] = 0.5 * acc[2];
-        }
+        if (grad_out && na == NA) chain_grad(acc[1], acc[2], acc[3], acc[4], theta + w * P, grad_out + w * P);
     }
 }
 
@@ -1004,7 +965,7 @@ static bool single_tile(int64_t ne) { return ne <= (int64_t)SCAN_TS; }
 static int64_t mid_tiles(int64_t ne) { return (ne + SCAN_TS - 1) / SCAN_TS; }
 
 // Workspace: [status | tree nodes | block totals | block prefix | block suffix |
-//             grid scan levels | Phi per step | block partials | stored steps]
+//             grid scan levels | (x, e^-x) per step | block partials | stored steps]
 template <int B>
 struct Layout {
     int64_t nc, nb;
@@ -1039,7 +1000,7 @@ struct Layout {
             ++nlev;
             ne = nt;
         }
-        off_phis = o; o = align256(o + sizeof(double) * (size_t)(B * B) * L * nc);
+        off_phis = o; o = align256(o + sizeof(double) * (size_t)2 * L * nc);
         off_part = o; o = align256(o + sizeof(double) * Acc<B>::N * (nseries > 0 ? nc : nb));
         off_store = o;
         if (mode != MODE_LOGLIK) o = align256(o + sizeof(double) * Stored<B>::N * (size_t)L * nc);
