@@ -35,11 +35,11 @@ WORKLOAD = "matern52_n4m"
 # profiles/chain_kernels_grad_matern52_n2m.md): flops = 2 x DFMA + DADD + DMUL
 # thread instructions; FP64 instructions = everything the FP64 pipe executed
 # (the pipe issues one warp instruction per 16 cycles per SM whatever its kind).
-FLOPS_PER_STEP = {"elimination": 187.2, "chunk_pass": 236.2}
-FP64_INST_PER_STEP = {"elimination": 117.9, "chunk_pass": 147.6}
+FLOPS_PER_STEP = {"elimination": 171.5, "chunk_pass": 231.2}
+FP64_INST_PER_STEP = {"elimination": 107.1, "chunk_pass": 141.6}
 # DRAM bytes per step moved by the chunk pass (ncu dram__bytes_read + write,
 # same capture); None once the kernel has changed since the counters were taken
-DRAM_BYTES_PER_STEP = {"chunk_pass": 181.9}
+DRAM_BYTES_PER_STEP = {"chunk_pass": 213.8}
 # algorithmic HBM bytes per step of the whole call: t and y in (16 B); the
 # gradient and log-likelihood outputs are O(1) per series
 ALGO_BYTES_PER_STEP = 16.0
@@ -281,9 +281,9 @@ def extra_workloads(args, dev, flush, world, rank=0):
 # steps, or nodes for the BTD solver; the batched SCG's gradient evaluations
 # use the chain kernels' counts above.
 NEXT_FLOPS_PER_UNIT = {"prediction_n4m": 353.9, "literal_n1m": 3801.2, "btd_solve_n1m": 1221.0,
-                       "eq_b12_n1m": 12896.7, "scg_batch_4096": 187.2 + 236.2}
+                       "eq_b12_n1m": 12896.7, "scg_batch_4096": 171.5 + 231.2}
 NEXT_FP64_INST_PER_UNIT = {"prediction_n4m": 248.3, "literal_n1m": 2686.9, "btd_solve_n1m": 1044.3,
-                           "eq_b12_n1m": 8887.7, "scg_batch_4096": 117.9 + 147.6}
+                           "eq_b12_n1m": 8887.7, "scg_batch_4096": 107.1 + 141.6}
 
 
 def _next_roofline(key, units_per_s, fp64_tflops):

@@ -208,6 +208,14 @@ spingp_status spingp_profile_read(spingp_model* model, double* ms_out, int* call
 size_t spingp_probe_fp64_bytes(void);
 spingp_status spingp_probe_fp64(void* scratch, size_t scratch_bytes, double* tflops_out, void* stream);
 
+/* y[i] = e^-x[i] for i < n, computed on the stream by the table-driven
+ * exponential that the chain kernels use for the discretisation (the
+ * e^-lam dt factor of Eq. ss_matern's expm).  x, y: device arrays of n
+ * doubles (x[i] >= 0; 0 for x[i] > 708; NaN propagates), owned by the
+ * caller.  Its accuracy is tested against a correctly rounded exponential.
+ * SPINGP_EINVAL for n < 0 or a NULL array with n > 0. */
+spingp_status spingp_probe_exp_neg(const double* x, double* y, int64_t n, void* stream);
+
 /* Log-likelihood and gradient from HOST buffers (Sec. 2.4; the same result
  * as spingp_grad, bit for bit): t, y (n doubles each) and theta are host
  * memory -- pinned memory lets the copies run asynchronously -- and ll_out

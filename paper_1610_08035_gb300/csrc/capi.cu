@@ -409,6 +409,11 @@ spingp_status spingp_probe_fp64(void* scratch, size_t bytes, double* tflops_out,
     return spg::probe_fp64(scratch, bytes, tflops_out, (cudaStream_t)stream) ? SPINGP_ECUDA : SPINGP_OK;
 }
 
+spingp_status spingp_probe_exp_neg(const double* x, double* y, int64_t n, void* stream) {
+    if (n < 0 || (n > 0 && (!x || !y))) return SPINGP_EINVAL;
+    return spg::probe_exp_neg(x, y, n, (cudaStream_t)stream) ? SPINGP_ECUDA : SPINGP_OK;
+}
+
 // ---------------------------------------------------------------- host buffers in, host results out
 
 static size_t align256c(size_t x) { return (x + 255) & ~(size_t)255; }

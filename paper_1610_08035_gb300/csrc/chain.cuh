@@ -80,7 +80,8 @@ __device__ __forceinline__ void phi(double x, double e, double (&P)[B][B]) {
 //     A_i = e^-x T(x),  T(x) = sum_k (N x)^k / k!   (unit upper triangular Toeplitz),
 //     Pinf = s_f PJ,  PJ = V^-1 P1 V^-T,  H = e_1^T,  dA/dx = (N - I) A.
 // A product with T costs b(b-1)/2 multiply-adds per column where a dense A
-// costs b^2, and a step's transition is the pair (x, e^-x).
+// costs b^2, and a step's transition is carried by x and e^-x (the chain
+// kernels store x, x^2/2, e^-x and e^-2x per step).
 
 // PJ = V^-1 P1 V^-T (b = 2: [[1, 1], [1, 2]]; b = 3: [[1, 1, 2/3], [1, 4/3, 4/3], [2/3, 4/3, 8/3]]).
 template <int B>
@@ -95,20 +96,58 @@ __device__ __forceinline__ double pj(int i, int j) {
     }
 }
 
-// the Toeplitz coefficients of T(x): c[k] = x^k / k!
+// the Toeplitz coefficients of T(x): c[k] = x^k / k! (given x and x^2 / 2)
 template <int B>
 struct JCoef {
     double c[B];
-    __device__ __forceinline__ explicit JCoef(double x) {
+    __device__ __forceinline__ JCoef(double x, double h) {
         c[0] = 1.0;
         if constexpr (B > 1) c[1] = x;
-        if constexpr (B > 2) c[2] = 0.5 * x * x;
+        if constexpr (B > 2) c[2] = h;
     }
 };
 
-// X <- e T X (X has NC columns; row r mixes rows k >= r, so rows go in increasing order)
+// ------------------------------------------------------------------ e^-x (table-driven)
+//
+// e^-x for x >= 0 by the table-driven method of Tang (ACM TOMS 15, 1989):
+// k = round(128 x / ln 2) = 128 m + j (0 <= j < 128), r = k ln2/128 - x
+// (|r| <= ln2/256; ln2/128 is carried in two parts), and
+//     e^-x = 2^-m 2^(-j/128) e^r,
+// with e^r - 1 from its degree-5 Taylor polynomial (the truncation is below
+// 6e-19 relative), 2^(-j/128) from a 128-entry table that the caller fills
+// (exp_neg_table), and 2^-m applied to the exponent bits.  x > 708 gives 0
+// (e^-x is then below the smallest normal double); NaN propagates.  Against
+// a correctly rounded e^-x the error is about one unit in the last place.
+static constexpr int EXPTAB = 128;
+
+__device__ __forceinline__ void exp_neg_table(double* tbl, int tid, int nthreads) {
+    for (int j = tid; j < EXPTAB; j += nthreads) tbl[j] = exp2(-(double)j / EXPTAB);
+}
+
+__device__ __forceinline__ double exp_neg(double x, const double* tbl) {
+    constexpr double INV = 184.6649652337873;          // 128 / ln 2
+    constexpr double L_HI = 0.0054152123481245725;     // ln 2 / 128, leading part
+    constexpr double L_LO = 1.8117553233174215e-19;    // ln 2 / 128 - L_HI
+    constexpr double MAGIC = 6755399441055744.0;       // 1.5 * 2^52: the sum rounds to an integer
+    const double kb = fma(x, INV, MAGIC);
+    const int k = __double2loint(kb);
+    const double kd = kb - MAGIC;
+    double r = fma(kd, L_HI, -x);
+    r = fma(kd, L_LO, r);
+    double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+    q = fma(r, q, 1.0 / 6.0);
+    q = fma(r, q, 0.5);
+    q = fma(r, q, 1.0);
+    const double t = tbl[k & (EXPTAB - 1)];
+    const double y = fma(t, r * q, t);
+    const unsigned long long m = (unsigned long long)(long long)(k >> 7);
+    const double s = __longlong_as_double((long long)((unsigned long long)__double_as_longlong(y) - (m << 52)));
+    return x <= 708.0 ? s : (x > 708.0 ? 0.0 : x);
+}
+
+// X <- T X (X has NC columns; row r mixes rows k >= r, so rows go in increasing order)
 template <int B, int NC>
-__device__ __forceinline__ void jprop(const JCoef<B>& t, double e, double (&X)[B][NC]) {
+__device__ __forceinline__ void jprop_unscaled(const JCoef<B>& t, double (&X)[B][NC]) {
 #pragma unroll
     for (int r = 0; r < B; ++r)
 #pragma unroll
@@ -116,7 +155,7 @@ __device__ __forceinline__ void jprop(const JCoef<B>& t, double e, double (&X)[B
             double s = X[r][q];
 #pragma unroll
             for (int k = r + 1; k < B; ++k) s = fma(t.c[k - r], X[k][q], s);
-            X[r][q] = s * e;
+            X[r][q] = s;
         }
 }
 template <int B>
@@ -170,6 +209,20 @@ __device__ __forceinline__ void jsand(const JCoef<B>& t, double e2, double (&D)[
             D[jj][ii] = s * e2;
         }
 }
+
+// ------------------------------------------------------------------ classification on the bit pattern
+// (integer instructions: the FP64 pipe is the chain kernels' bottleneck)
+
+__device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+// finite: the exponent field is not all ones
+__device__ __forceinline__ bool is_finite_b(double v) {
+    return (dbits(v) & 0x7ff0000000000000ULL) != 0x7ff0000000000000ULL;
+}
+__device__ __forceinline__ bool is_nan_b(double v) { return (dbits(v) & 0x7fffffffffffffffULL) > 0x7ff0000000000000ULL; }
+// v < 0 (for non-NaN v; -0 is not below 0)
+__device__ __forceinline__ bool is_negative_b(double v) { return dbits(v) > 0x8000000000000000ULL; }
+// 0 < v < inf
+__device__ __forceinline__ bool is_positive_finite_b(double v) { return dbits(v) - 1ULL < 0x7fefffffffffffffULL; }
 
 // ------------------------------------------------------------------ small dense helpers (fully unrolled)
 

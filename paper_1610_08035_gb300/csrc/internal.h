@@ -102,6 +102,7 @@ int scg_launch(int what, const ScgState& st, cudaStream_t s, int k, double tol, 
 
 size_t probe_fp64_bytes();
 int probe_fp64(void* scratch, size_t bytes, double* tflops, cudaStream_t st);
+int probe_exp_neg(const double* x, double* y, int64_t n, cudaStream_t st);
 
 }  // namespace spg
 

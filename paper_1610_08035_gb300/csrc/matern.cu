@@ -101,6 +101,7 @@ __device__ __forceinline__ bool theta_ok(double ell, double sf, double s2) {
 static constexpr int CTA = 128;
 static constexpr int CTA_LV = 7;
 static constexpr int TREE = 2 * CTA;      // node slots per block (255 used)
+static constexpr int NPH = 4;             // stored per step: x, x^2/2, e^-x, e^-2x
 static_assert((1 << CTA_LV) == CTA, "CTA must be 2^CTA_LV");
 
 __device__ __forceinline__ int tree_off(int level) { return TREE - (TREE >> level); }
@@ -229,8 +230,8 @@ __device__ __forceinline__ void tree_down_coop(double* spre, double* ssuf, const
 
 // ------------------------------------------------------------------ k_fold
 
-// One thread per chunk: discretise every step (storing x = lam dt and e^-x
-// for the later pass) and eliminate the chunk's interior nodes into its
+// One thread per chunk: discretise every step (storing x = lam dt, x^2/2,
+// e^-x and e^-2x for the later pass) and eliminate the chunk's interior nodes into its
 // element; then the block's odd-even up-sweep over its CTA elements, writing
 // every tree node and the block total.  Jordan coordinates (chain.cuh); the
 // conditional covariance is carried as C - Pinf, so the prediction is a
@@ -240,8 +241,11 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
                                               double* __restrict__ phis, int64_t blk0) {
     constexpr int NE = Dims<B>::NE;
     __shared__ double sm[CTA * NE];
+    __shared__ double etab[EXPTAB];
     const int tid = threadIdx.x;
     const int64_t blk = blk0 + blockIdx.x;   // launches may cover a range of blocks
+    exp_neg_table(etab, tid, CTA);
+    __syncthreads();
     const int64_t c = blk * CTA + tid;
     const int64_t nc = a.nchunks;
     const ChunkRange cr = chunk_range<BATCH>(a, c);
@@ -270,29 +274,34 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
                 for (int j = 0; j < B; ++j) el.C[i][j] = -sf * pj<B>(i, j);
         }
         double tp = (s > cr.s0) ? a.t[s - 1] : 0.0;
+        // el.A holds A / sa: the factors e^-x of the steps are collected in sa
+        double sa = 1.0;
         for (int64_t i = s; i < e; ++i) {
             const double ti = a.t[i], yi = a.y[i];
-            const bool obs = !(a.missing && isnan(yi));
-            if (!isfinite(ti) || (obs && !isfinite(yi))) bad |= ST_ENONFINITE;
+            const bool obs = !(a.missing && is_nan_b(yi));
+            if (!is_finite_b(ti) || (obs && !is_finite_b(yi))) bad |= ST_ENONFINITE;
             if (i > cr.s0) {
                 const double dt = ti - tp;
-                if (dt < 0.0) bad |= ST_ENOTSORTED;
-                const double x = lam * dt, ex = exp(-x);
+                if (is_negative_b(dt)) bad |= ST_ENOTSORTED;
+                const double x = lam * dt, h = 0.5 * x * x, ex = exp_neg(x, etab), e2 = ex * ex;
                 {
-                    double* ph = phis + ((i - s) * 2) * nc + c;
+                    double* ph = phis + ((i - s) * NPH) * nc + c;
                     ph[0] = x;
-                    ph[nc] = ex;
+                    ph[nc] = h;
+                    ph[2 * nc] = ex;
+                    ph[3 * nc] = e2;
                 }
                 // A <- e T A,  bv <- e T bv,  C - Pinf <- e^2 T (C - Pinf) T^T
-                const JCoef<B> tc(x);
-                jprop<B, B>(tc, ex, el.A);
+                const JCoef<B> tc(x, h);
+                jprop_unscaled<B, B>(tc, el.A);
+                sa *= ex;
                 jprop_vec<B>(tc, ex, el.bv);
-                jsand<B, false>(tc, ex * ex, el.C);
+                jsand<B, false>(tc, e2, el.C);
             }
             // condition on y_i: innovation of y_i given the node before the chunk
             // (a missing observation has infinite noise: no update, Eqs. mean4-mean6)
             if (obs) {
-            double a0[B], c0[B];
+            double a0[B], c0[B];   // a0: the first row of A / sa
 #pragma unroll
             for (int r = 0; r < B; ++r) {
                 a0[r] = el.A[0][r];
@@ -302,10 +311,11 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
             const double rS = 1.0 / S;
             const double res = yi - el.bv[0];
             const double rr = res * rS;
+            const double rra = rr * sa, rSa = rS * sa * sa;
 #pragma unroll
             for (int r = 0; r < B; ++r) {
-                el.eta[r] = fma(a0[r], rr, el.eta[r]);
-                const double ar = a0[r] * rS;
+                el.eta[r] = fma(a0[r], rra, el.eta[r]);
+                const double ar = a0[r] * rSa;
 #pragma unroll
                 for (int q = r; q < B; ++q) { el.J[r][q] = fma(ar, a0[q], el.J[r][q]); el.J[q][r] = el.J[r][q]; }
             }
@@ -324,7 +334,7 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
 #pragma unroll
         for (int r = 0; r < B; ++r)
 #pragma unroll
-            for (int q = 0; q < B; ++q) el.C[r][q] += sf * pj<B>(r, q);
+            for (int q = 0; q < B; ++q) { el.C[r][q] += sf * pj<B>(r, q); el.A[r][q] *= sa; }
     }
     if (bad) atomicOr(a.status, bad);
     // odd-even up-sweep inside the block (chunks past the end are identities):
@@ -499,6 +509,7 @@ template <int B> struct Acc { static constexpr int N = 5; };
 // per-step stored values: predicted mean (B), predicted covariance minus Pinf
 // (packed), innovation, 1/S
 template <int B> struct Stored { static constexpr int N = B + Dims<B>::NS + 2; };
+// per-step transition: x, x^2/2, e^-x, e^-2x
 
 // One thread per chunk, CTA chunks per block.
 //  1. Back-substitution of the block's odd-even tree: from the block's own
@@ -628,7 +639,7 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
         for (int64_t i = s; i < e; ++i) {
             const int64_t j = i - s;
             const double yi = a.y[i];
-            const bool obs = !(a.missing && isnan(yi));
+            const bool obs = !(a.missing && is_nan_b(yi));
             double mb[B], Db[B][B];
             if (i == cr.s0) {
 #pragma unroll
@@ -636,17 +647,16 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
 #pragma unroll
                     for (int q = 0; q < B; ++q) Db[r][q] = 0.0; }
             } else {
-                const double* ph = phis + (j * 2) * nc + c;
-                const double x = ph[0], ex = ph[nc];
-                const JCoef<B> tc(x);
+                const double* ph = phis + (j * NPH) * nc + c;
+                const JCoef<B> tc(ph[0], ph[nc]);
 #pragma unroll
                 for (int r = 0; r < B; ++r) {
                     mb[r] = m[r];
 #pragma unroll
                     for (int q = 0; q < B; ++q) Db[r][q] = D[r][q];
                 }
-                jprop_vec<B>(tc, ex, mb);
-                jsand<B, false>(tc, ex * ex, Db);
+                jprop_vec<B>(tc, ph[2 * nc], mb);
+                jsand<B, false>(tc, ph[3 * nc], Db);
             }
             double p0[B];   // first column of the predicted covariance
 #pragma unroll
@@ -656,7 +666,7 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
             double rS = 0.0, v = 0.0;
             if (obs) {
                 const double S = p0[0] + s2;
-                if (!(S > 0.0) || !isfinite(S)) bad |= ST_ENUMERIC;
+                if (!is_positive_finite_b(S)) bad |= ST_ENUMERIC;
                 rS = 1.0 / S;
                 v = yi - mb[0];
                 quad = fma(v * v, rS, quad);
@@ -740,7 +750,7 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
                 if constexpr (GRAD) gs = fma(al, al, gs) - cc;
                 if constexpr (POST) {
                     const double yi = a.y[i];
-                    if (a.missing && isnan(yi)) {
+                    if (a.missing && is_nan_b(yi)) {
                         // predicted only: mean = (mb - Pb lh)_0, variance = Pb_00 - Pb_0^T Lh Pb_0
                         double w[B], pl = 0.0, q = 0.0;
                         mat_vec<B>(Lh, p0, w);
@@ -765,8 +775,8 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
                 for (int q = 1; q < B; ++q) { Lt[0][q] -= u[q]; Lt[q][0] = Lt[0][q]; }
                 Lt[0][0] = Lt[0][0] - 2.0 * u[0] + cc;
                 if (i > cr.s0) {
-                    const double* ph = phis + (j * 2) * nc + c;
-                    const double x = ph[0], ex = ph[nc];
+                    const double* ph = phis + (j * NPH) * nc + c;
+                    const double x = ph[0];
                     if constexpr (GRAD) {
                         // d ll/dx = <G2, F Db> - lt^T F mb with G2 = lt lt^T - Lt (= 2 G), F = N - I:
                         // <G2, N Db> - <G2, Db> - lt^T N mb + lt^T mb
@@ -793,15 +803,15 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
                         const double dx = (gn - fma(2.0, go, gd)) - (mn - md);
                         gx = fma(dx, x, gx);
                     }
-                    const JCoef<B> tc(x);
+                    const JCoef<B> tc(x, ph[nc]);
 #pragma unroll
                     for (int r = 0; r < B; ++r) {
                         lh[r] = lt[r];
 #pragma unroll
                         for (int q = 0; q < B; ++q) Lh[r][q] = Lt[r][q];
                     }
-                    jprop_tvec<B>(tc, ex, lh);
-                    jsand<B, true>(tc, ex * ex, Lh);
+                    jprop_tvec<B>(tc, ph[2 * nc], lh);
+                    jsand<B, true>(tc, ph[3 * nc], Lh);
                 }
             }
             if constexpr (GRAD) {
@@ -965,7 +975,7 @@ static bool single_tile(int64_t ne) { return ne <= (int64_t)SCAN_TS; }
 static int64_t mid_tiles(int64_t ne) { return (ne + SCAN_TS - 1) / SCAN_TS; }
 
 // Workspace: [status | tree nodes | block totals | block prefix | block suffix |
-//             grid scan levels | (x, e^-x) per step | block partials | stored steps]
+//             grid scan levels | transition per step | block partials | stored steps]
 template <int B>
 struct Layout {
     int64_t nc, nb;
@@ -1000,7 +1010,7 @@ struct Layout {
             ++nlev;
             ne = nt;
         }
-        off_phis = o; o = align256(o + sizeof(double) * (size_t)2 * L * nc);
+        off_phis = o; o = align256(o + sizeof(double) * (size_t)NPH * L * nc);
         off_part = o; o = align256(o + sizeof(double) * Acc<B>::N * (nseries > 0 ? nc : nb));
         off_store = o;
         if (mode != MODE_LOGLIK) o = align256(o + sizeof(double) * Stored<B>::N * (size_t)L * nc);

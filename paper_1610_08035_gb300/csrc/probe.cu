@@ -1,8 +1,10 @@
 // probe.cu -- measured FP64 throughput of the current device (the ALU roofline
-// denominator for the FP64-bound chain kernels).
+// denominator for the FP64-bound chain kernels), and the chain kernels'
+// table-driven e^-x applied to a caller's array (for its accuracy test).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "chain.cuh"
 #include "internal.h"
 
 namespace spg {
@@ -52,6 +54,24 @@ int probe_fp64(void* scratch, size_t bytes, double* tflops, cudaStream_t st) {
     const double flops = 2.0 * 8.0 * PROBE_ITERS * (double)blocks * PROBE_THREADS;
     *tflops = flops / (ms * 1e-3) / 1e12;
     return 0;
+}
+
+// y_i = e^-x_i by the chain kernels' exp_neg (chain.cuh)
+__global__ void __launch_bounds__(256) k_probe_exp_neg(const double* __restrict__ x, double* __restrict__ y,
+                                                       int64_t n) {
+    __shared__ double tbl[EXPTAB];
+    exp_neg_table(tbl, threadIdx.x, blockDim.x);
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = exp_neg(x[i], tbl);
+}
+
+int probe_exp_neg(const double* x, double* y, int64_t n, cudaStream_t st) {
+    if (n < 0 || (n > 0 && (!x || !y))) return 1;
+    if (n == 0) return 0;
+    const int64_t blocks = (n + 255) / 256;
+    k_probe_exp_neg<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(x, y, n);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
 }  // namespace spg

@@ -26,7 +26,8 @@ EXPORTS = ("spingp_model_create", "spingp_model_destroy", "spingp_num_params", "
            "spingp_grad", "spingp_posterior", "spingp_workspace_bytes_batched", "spingp_loglik_batched",
            "spingp_grad_batched", "spingp_posterior_batched", "spingp_launch_count",
            "spingp_launch_count_batched", "spingp_profile_enable",
-           "spingp_profile_read", "spingp_probe_fp64_bytes", "spingp_probe_fp64", "spingp_workspace_bytes_host",
+           "spingp_profile_read", "spingp_probe_fp64_bytes", "spingp_probe_fp64", "spingp_probe_exp_neg",
+           "spingp_workspace_bytes_host",
            "spingp_grad_host", "spingp_loglik_noalloc",
            "spingp_btd_workspace_bytes", "spingp_btd_solve", "spingp_btd_launch_count",
            "spingp_btd_diag_product_workspace_bytes", "spingp_btd_diag_product",
@@ -84,6 +85,7 @@ def load():
     lib.spingp_probe_fp64_bytes.argtypes = []
     lib.spingp_probe_fp64_bytes.restype = sz
     lib.spingp_probe_fp64.argtypes = [vp, sz, ctypes.POINTER(ctypes.c_double), vp]
+    lib.spingp_probe_exp_neg.argtypes = [dp, dp, i64, vp]
     lib.spingp_loglik_noalloc.argtypes = [vp, dp, dp, i64, dp, dp, u32, vp]
     lib.spingp_workspace_bytes_host.argtypes = [vp, i64]
     lib.spingp_workspace_bytes_host.restype = sz
@@ -259,6 +261,15 @@ def spingp_probe_fp64(device=None):
     _check(lib.spingp_probe_fp64(_ptr(scratch), scratch.numel(), ctypes.byref(out), _stream()),
            "spingp_probe_fp64")
     return out.value
+
+
+def spingp_probe_exp_neg(x):
+    """e^-x of a CUDA float64 tensor by the chain kernels' table-driven exponential."""
+    _dev_f64(x, "x")
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    _check(load().spingp_probe_exp_neg(_ptr(x), _ptr(y), x.numel(), _stream()), "spingp_probe_exp_neg")
+    return y
 
 
 def spingp_workspace_bytes_host(h, n):
