@@ -280,9 +280,9 @@ def extra_workloads(args, dev, flush, world, rank=0):
 # instructions; instructions = everything the FP64 pipe executed.  Units:
 # steps, or nodes for the BTD solver; the batched SCG's gradient evaluations
 # use the chain kernels' counts above.
-NEXT_FLOPS_PER_UNIT = {"prediction_n4m": 353.9, "literal_n1m": 3801.2, "btd_solve_n1m": 1221.0,
+NEXT_FLOPS_PER_UNIT = {"prediction_n4m": 333.8, "literal_n1m": 3801.2, "btd_solve_n1m": 1221.0,
                        "eq_b12_n1m": 12896.7, "scg_batch_4096": 171.5 + 231.2}
-NEXT_FP64_INST_PER_UNIT = {"prediction_n4m": 248.3, "literal_n1m": 2686.9, "btd_solve_n1m": 1044.3,
+NEXT_FP64_INST_PER_UNIT = {"prediction_n4m": 231.4, "literal_n1m": 2686.9, "btd_solve_n1m": 1044.3,
                            "eq_b12_n1m": 8887.7, "scg_batch_4096": 107.1 + 141.6}
 
 
@@ -461,6 +461,8 @@ def main():
     for _ in range(max(args.warmup, 0)):
         model.grad(T, Y, TH, sync=True, out=(ll, g))
     fp64_tflops = spingp.spingp_probe_fp64(dev)
+    # context for the design choice: the FP64 tensor-core instruction's rate on this device
+    fp64_mma_tflops = spingp.spingp_probe_fp64_tensor(dev)
 
     # ---- device-timed region
     K = args.steps
@@ -506,7 +508,8 @@ def main():
             # the FP64 pipe's instruction rate: every FP64 instruction (not only
             # FMAs) takes a pipe slot; peak = probe FMA rate = TFLOP/s / 2
             "fp64_inst_per_s": inst * n / (stage_ms[dom] * 1e-3) if inst else None,
-            "pipe_frac": inst * n / (stage_ms[dom] * 1e-3) / (fp64_tflops * 1e12 / 2.0) if inst else None}
+            "pipe_frac": inst * n / (stage_ms[dom] * 1e-3) / (fp64_tflops * 1e12 / 2.0) if inst else None,
+            "fp64_tensor_tflops": fp64_mma_tflops}
     hbm = {"algorithmic_bytes_per_step": ALGO_BYTES_PER_STEP,
            "achieved_gbs": ALGO_BYTES_PER_STEP * n / (ms_per_step * 1e-3) / 1e9}
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")

@@ -208,6 +208,12 @@ spingp_status spingp_profile_read(spingp_model* model, double* ms_out, int* call
 size_t spingp_probe_fp64_bytes(void);
 spingp_status spingp_probe_fp64(void* scratch, size_t scratch_bytes, double* tflops_out, void* stream);
 
+/* The same measurement for the FP64 tensor-core instruction (mma.sync
+ * m8n8k4, eight independent products per warp; 512 flop each): the rate a
+ * kernel that moved the b x b block products onto tensor cores could reach.
+ * Same arguments and behaviour as spingp_probe_fp64. */
+spingp_status spingp_probe_fp64_tensor(void* scratch, size_t scratch_bytes, double* tflops_out, void* stream);
+
 /* y[i] = e^-x[i] for i < n, computed on the stream by the table-driven
  * exponential that the chain kernels use for the discretisation (the
  * e^-lam dt factor of Eq. ss_matern's expm).  x, y: device arrays of n

@@ -406,7 +406,12 @@ size_t spingp_probe_fp64_bytes(void) { return spg::probe_fp64_bytes(); }
 
 spingp_status spingp_probe_fp64(void* scratch, size_t bytes, double* tflops_out, void* stream) {
     if (!scratch || !tflops_out) return SPINGP_EINVAL;
-    return spg::probe_fp64(scratch, bytes, tflops_out, (cudaStream_t)stream) ? SPINGP_ECUDA : SPINGP_OK;
+    return spg::probe_fp64(scratch, bytes, tflops_out, (cudaStream_t)stream, 0) ? SPINGP_ECUDA : SPINGP_OK;
+}
+
+spingp_status spingp_probe_fp64_tensor(void* scratch, size_t bytes, double* tflops_out, void* stream) {
+    if (!scratch || !tflops_out) return SPINGP_EINVAL;
+    return spg::probe_fp64(scratch, bytes, tflops_out, (cudaStream_t)stream, 1) ? SPINGP_ECUDA : SPINGP_OK;
 }
 
 spingp_status spingp_probe_exp_neg(const double* x, double* y, int64_t n, void* stream) {

@@ -101,7 +101,7 @@ int scg_launch(int what, const ScgState& st, cudaStream_t s, int k, double tol, 
                double* theta_out, double* ll_out, double* grad_out, int* status);
 
 size_t probe_fp64_bytes();
-int probe_fp64(void* scratch, size_t bytes, double* tflops, cudaStream_t st);
+int probe_fp64(void* scratch, size_t bytes, double* tflops, cudaStream_t st, int tensor);
 int probe_exp_neg(const double* x, double* y, int64_t n, cudaStream_t st);
 
 }  // namespace spg

@@ -24,6 +24,27 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_probe_fp64(double* out, int i
     out[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
 }
 
+// eight independent FP64 tensor-core products per warp (mma.sync m8n8k4, the
+// only FP64 matrix instruction on this architecture: tcgen05 has no FP64
+// kind); 8 x 8 x 4 multiply-adds each
+__global__ void __launch_bounds__(PROBE_THREADS) k_probe_fp64_mma(double* out, int iters, double a, double b) {
+    double c[8][2];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { c[k][0] = k + threadIdx.x * 1e-3; c[k][1] = -k; }
+    const double av = a + threadIdx.x * 1e-9;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};\n"
+                         : "+d"(c[k][0]), "+d"(c[k][1])
+                         : "d"(av), "d"(b));
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += c[k][0] + c[k][1];
+    out[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = s;
+}
+
 static int sm_count() {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -33,7 +54,7 @@ static int sm_count() {
 
 size_t probe_fp64_bytes() { return sizeof(double) * (size_t)sm_count() * PROBE_BLOCKS_PER_SM * PROBE_THREADS; }
 
-int probe_fp64(void* scratch, size_t bytes, double* tflops, cudaStream_t st) {
+int probe_fp64(void* scratch, size_t bytes, double* tflops, cudaStream_t st, int tensor) {
     const int sms = sm_count();
     if (sms <= 0 || !scratch || bytes < probe_fp64_bytes()) return 1;
     const unsigned blocks = (unsigned)(sms * PROBE_BLOCKS_PER_SM);
@@ -41,9 +62,16 @@ int probe_fp64(void* scratch, size_t bytes, double* tflops, cudaStream_t st) {
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return 1;
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return 1; }
-    k_probe_fp64<<<blocks, PROBE_THREADS, 0, st>>>(out, 64, 1.0000001, 1e-9);
-    cudaEventRecord(e0, st);
-    k_probe_fp64<<<blocks, PROBE_THREADS, 0, st>>>(out, PROBE_ITERS, 1.0000001, 1e-9);
+    const int iters = tensor ? PROBE_ITERS / 8 : PROBE_ITERS;
+    if (tensor) {
+        k_probe_fp64_mma<<<blocks, PROBE_THREADS, 0, st>>>(out, 8, 1.0000001, 1e-9);
+        cudaEventRecord(e0, st);
+        k_probe_fp64_mma<<<blocks, PROBE_THREADS, 0, st>>>(out, iters, 1.0000001, 1e-9);
+    } else {
+        k_probe_fp64<<<blocks, PROBE_THREADS, 0, st>>>(out, 64, 1.0000001, 1e-9);
+        cudaEventRecord(e0, st);
+        k_probe_fp64<<<blocks, PROBE_THREADS, 0, st>>>(out, iters, 1.0000001, 1e-9);
+    }
     cudaEventRecord(e1, st);
     int rc = cudaEventSynchronize(e1) == cudaSuccess ? 0 : 1;
     float ms = 0.0f;
@@ -51,7 +79,9 @@ int probe_fp64(void* scratch, size_t bytes, double* tflops, cudaStream_t st) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc || ms <= 0.0f) return 1;
-    const double flops = 2.0 * 8.0 * PROBE_ITERS * (double)blocks * PROBE_THREADS;
+    // FMA: 8 per thread per iteration; mma: 8 per warp per iteration, 256 multiply-adds each
+    const double flops = tensor ? 2.0 * 256.0 * 8.0 * iters * (double)blocks * (PROBE_THREADS / 32)
+                                : 2.0 * 8.0 * iters * (double)blocks * PROBE_THREADS;
     *tflops = flops / (ms * 1e-3) / 1e12;
     return 0;
 }

@@ -26,7 +26,8 @@ EXPORTS = ("spingp_model_create", "spingp_model_destroy", "spingp_num_params", "
            "spingp_grad", "spingp_posterior", "spingp_workspace_bytes_batched", "spingp_loglik_batched",
            "spingp_grad_batched", "spingp_posterior_batched", "spingp_launch_count",
            "spingp_launch_count_batched", "spingp_profile_enable",
-           "spingp_profile_read", "spingp_probe_fp64_bytes", "spingp_probe_fp64", "spingp_probe_exp_neg",
+           "spingp_profile_read", "spingp_probe_fp64_bytes", "spingp_probe_fp64", "spingp_probe_fp64_tensor",
+           "spingp_probe_exp_neg",
            "spingp_workspace_bytes_host",
            "spingp_grad_host", "spingp_loglik_noalloc",
            "spingp_btd_workspace_bytes", "spingp_btd_solve", "spingp_btd_launch_count",
@@ -85,6 +86,7 @@ def load():
     lib.spingp_probe_fp64_bytes.argtypes = []
     lib.spingp_probe_fp64_bytes.restype = sz
     lib.spingp_probe_fp64.argtypes = [vp, sz, ctypes.POINTER(ctypes.c_double), vp]
+    lib.spingp_probe_fp64_tensor.argtypes = [vp, sz, ctypes.POINTER(ctypes.c_double), vp]
     lib.spingp_probe_exp_neg.argtypes = [dp, dp, i64, vp]
     lib.spingp_loglik_noalloc.argtypes = [vp, dp, dp, i64, dp, dp, u32, vp]
     lib.spingp_workspace_bytes_host.argtypes = [vp, i64]
@@ -260,6 +262,17 @@ def spingp_probe_fp64(device=None):
     out = ctypes.c_double()
     _check(lib.spingp_probe_fp64(_ptr(scratch), scratch.numel(), ctypes.byref(out), _stream()),
            "spingp_probe_fp64")
+    return out.value
+
+
+def spingp_probe_fp64_tensor(device=None):
+    """Measured FP64 tensor-core TFLOP/s (mma.sync m8n8k4) of the current device."""
+    lib = load()
+    scratch = torch.empty(lib.spingp_probe_fp64_bytes(), dtype=torch.uint8,
+                          device=device if device is not None else "cuda")
+    out = ctypes.c_double()
+    _check(lib.spingp_probe_fp64_tensor(_ptr(scratch), scratch.numel(), ctypes.byref(out), _stream()),
+           "spingp_probe_fp64_tensor")
     return out.value
 
 
