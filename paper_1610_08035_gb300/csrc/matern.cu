@@ -511,6 +511,14 @@ template <int B> struct Acc { static constexpr int N = 5; };
 template <int B> struct Stored { static constexpr int N = B + Dims<B>::NS + 2; };
 // per-step transition: x, x^2/2, e^-x, e^-2x
 
+// the transition of step j of chunk c (slot j of the [step][field][chunk] layout)
+__device__ __forceinline__ void load_trans(const double* __restrict__ phis, int64_t j, int64_t nc, int64_t c,
+                                           double (&p)[NPH]) {
+    const double* ph = phis + (j * NPH) * nc + c;
+#pragma unroll
+    for (int f = 0; f < NPH; ++f) p[f] = ph[f * nc];
+}
+
 // One thread per chunk, CTA chunks per block.
 //  1. Back-substitution of the block's odd-even tree: from the block's own
 //     prefix state and suffix information (grid level) down to every chunk.
@@ -636,9 +644,21 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
         double quad = 0.0, prod = 1.0;
         int expo = 0;
         int64_t nobs = 0;
+        // each step's y and transition are loaded one step ahead, so their
+        // latency overlaps the previous step's arithmetic (slot 0 of a series'
+        // first chunk holds no transition; it is loaded and not used)
+        double ynx = a.y[s], tnx[NPH];
+        load_trans(phis, 0, nc, c, tnx);
         for (int64_t i = s; i < e; ++i) {
             const int64_t j = i - s;
-            const double yi = a.y[i];
+            const double yi = ynx;
+            double tr[NPH];
+#pragma unroll
+            for (int f = 0; f < NPH; ++f) tr[f] = tnx[f];
+            if (i + 1 < e) {
+                ynx = a.y[i + 1];
+                load_trans(phis, j + 1, nc, c, tnx);
+            }
             const bool obs = !(a.missing && is_nan_b(yi));
             double mb[B], Db[B][B];
             if (i == cr.s0) {
@@ -647,16 +667,15 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
 #pragma unroll
                     for (int q = 0; q < B; ++q) Db[r][q] = 0.0; }
             } else {
-                const double* ph = phis + (j * NPH) * nc + c;
-                const JCoef<B> tc(ph[0], ph[nc]);
+                const JCoef<B> tc(tr[0], tr[1]);
 #pragma unroll
                 for (int r = 0; r < B; ++r) {
                     mb[r] = m[r];
 #pragma unroll
                     for (int q = 0; q < B; ++q) Db[r][q] = D[r][q];
                 }
-                jprop_vec<B>(tc, ph[2 * nc], mb);
-                jsand<B, false>(tc, ph[3 * nc], Db);
+                jprop_vec<B>(tc, tr[2], mb);
+                jsand<B, false>(tc, tr[3], Db);
             }
             double p0[B];   // first column of the predicted covariance
 #pragma unroll
@@ -723,19 +742,37 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
                 symmetrize<B>(Lh);
             }
             double gx = 0.0, gs = 0.0;
+            // the stored step and its transition are loaded one step ahead
+            double snx[NF], tnx[NPH];
+            {
+                const double* st = store + ((e - 1 - s) * NF) * nc + c;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) snx[f] = st[f * nc];
+                load_trans(phis, e - 1 - s, nc, c, tnx);
+            }
             for (int64_t i = e - 1; i >= s; --i) {
                 const int64_t j = i - s;
-                const double* st = store + (j * NF) * nc + c;
+                double sv[NF], tr[NPH];
+#pragma unroll
+                for (int f = 0; f < NF; ++f) sv[f] = snx[f];
+#pragma unroll
+                for (int f = 0; f < NPH; ++f) tr[f] = tnx[f];
+                if (i > s) {
+                    const double* st = store + ((j - 1) * NF) * nc + c;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) snx[f] = st[f * nc];
+                    load_trans(phis, j - 1, nc, c, tnx);
+                }
                 double mb[B], Db[B][B];
                 int f = 0;
 #pragma unroll
-                for (int r = 0; r < B; ++r) mb[r] = st[(f++) * nc];
+                for (int r = 0; r < B; ++r) mb[r] = sv[f++];
 #pragma unroll
                 for (int r = 0; r < B; ++r)
 #pragma unroll
-                    for (int q = r; q < B; ++q) { Db[r][q] = st[(f++) * nc]; Db[q][r] = Db[r][q]; }
-                const double v = st[(f++) * nc];
-                const double rS = st[(f++) * nc];
+                    for (int q = r; q < B; ++q) { Db[r][q] = sv[f++]; Db[q][r] = Db[r][q]; }
+                const double v = sv[f++];
+                const double rS = sv[f++];
                 double p0[B], k[B];
 #pragma unroll
                 for (int r = 0; r < B; ++r) { p0[r] = Db[r][0] + sp0[r]; k[r] = p0[r] * rS; }
@@ -775,8 +812,7 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
                 for (int q = 1; q < B; ++q) { Lt[0][q] -= u[q]; Lt[q][0] = Lt[0][q]; }
                 Lt[0][0] = Lt[0][0] - 2.0 * u[0] + cc;
                 if (i > cr.s0) {
-                    const double* ph = phis + (j * NPH) * nc + c;
-                    const double x = ph[0];
+                    const double x = tr[0];
                     if constexpr (GRAD) {
                         // d ll/dx = <G2, F Db> - lt^T F mb with G2 = lt lt^T - Lt (= 2 G), F = N - I:
                         // <G2, N Db> - <G2, Db> - lt^T N mb + lt^T mb
@@ -803,15 +839,15 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
                         const double dx = (gn - fma(2.0, go, gd)) - (mn - md);
                         gx = fma(dx, x, gx);
                     }
-                    const JCoef<B> tc(x, ph[nc]);
+                    const JCoef<B> tc(x, tr[1]);
 #pragma unroll
                     for (int r = 0; r < B; ++r) {
                         lh[r] = lt[r];
 #pragma unroll
                         for (int q = 0; q < B; ++q) Lh[r][q] = Lt[r][q];
                     }
-                    jprop_tvec<B>(tc, ph[2 * nc], lh);
-                    jsand<B, true>(tc, ph[3 * nc], Lh);
+                    jprop_tvec<B>(tc, tr[2], lh);
+                    jsand<B, true>(tc, tr[3], Lh);
                 }
             }
             if constexpr (GRAD) {
