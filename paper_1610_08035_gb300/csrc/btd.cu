@@ -25,51 +25,45 @@ namespace spg {
 
 // ------------------------------------------------------------------ small SPD helpers (b <= 3)
 
-// Cholesky factor L (lower) of a symmetric positive-definite S; false when a
-// pivot is not positive and finite.
-template <int B>
-__device__ __forceinline__ bool chol(const double (&S)[B][B], double (&L)[B][B]) {
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < B; ++j) {
-        double d = S[j][j];
-#pragma unroll
-        for (int k = 0; k < j; ++k) d = fma(-L[j][k], L[j][k], d);
-        ok = ok && (d > 0.0) && isfinite(d);
-        const double l = sqrt(d > 0.0 ? d : 1.0);
-        L[j][j] = l;
-        const double il = 1.0 / l;
-#pragma unroll
-        for (int i = j + 1; i < B; ++i) {
-            double x = S[i][j];
-#pragma unroll
-            for (int k = 0; k < j; ++k) x = fma(-L[i][k], L[j][k], x);
-            L[i][j] = x * il;
-        }
-#pragma unroll
-        for (int i = 0; i < j; ++i) L[i][j] = 0.0;
-    }
-    return ok;
-}
-
-// S^-1 from its Cholesky factor, and (LOGDET) log det S
+// Inverse of a symmetric positive-definite block (b <= 3) from its cofactors,
+// S^-1 = adj(S) / det S, and (LOGDET) log det S: a short dependency chain
+// (one reciprocal, one log) where a Cholesky route needs b square roots, b
+// reciprocals and b logs in sequence.  Positive definiteness is checked on the
+// leading principal minors (Sylvester's criterion); false when one of them is
+// not positive and finite.
 template <int B, bool LOGDET = true>
-__device__ __forceinline__ void chol_inv(const double (&L)[B][B], double (&Si)[B][B], double& logdet) {
-    double Li[B][B];   // L^-1 (lower)
-    logdet = 0.0;
-#pragma unroll
-    for (int j = 0; j < B; ++j) {
-        if constexpr (LOGDET) logdet += 2.0 * log(L[j][j]);
-#pragma unroll
-        for (int i = 0; i < B; ++i) {
-            if (i < j) { Li[i][j] = 0.0; continue; }
-            double x = (i == j) ? 1.0 : 0.0;
-#pragma unroll
-            for (int k = j; k < i; ++k) x = fma(-L[i][k], Li[k][j], x);
-            Li[i][j] = x / L[i][i];
-        }
+__device__ __forceinline__ bool spd_inv(const double (&S)[B][B], double (&Si)[B][B], double& logdet) {
+    double det;
+    bool ok;
+    if constexpr (B == 1) {
+        det = S[0][0];
+        Si[0][0] = 1.0 / det;
+        ok = is_positive_finite_b(det);
+    } else if constexpr (B == 2) {
+        det = fma(S[0][0], S[1][1], -S[0][1] * S[0][1]);
+        const double r = 1.0 / det;
+        Si[0][0] = S[1][1] * r;
+        Si[1][1] = S[0][0] * r;
+        Si[0][1] = -S[0][1] * r;
+        Si[1][0] = Si[0][1];
+        ok = is_positive_finite_b(S[0][0]) && is_positive_finite_b(det);
+    } else {
+        const double c00 = fma(S[1][1], S[2][2], -S[1][2] * S[1][2]);
+        const double c01 = fma(S[0][2], S[1][2], -S[0][1] * S[2][2]);
+        const double c02 = fma(S[0][1], S[1][2], -S[0][2] * S[1][1]);
+        const double c11 = fma(S[0][0], S[2][2], -S[0][2] * S[0][2]);
+        const double c12 = fma(S[0][1], S[0][2], -S[0][0] * S[1][2]);
+        const double c22 = fma(S[0][0], S[1][1], -S[0][1] * S[0][1]);
+        det = fma(S[0][0], c00, fma(S[0][1], c01, S[0][2] * c02));
+        const double r = 1.0 / det;
+        Si[0][0] = c00 * r; Si[0][1] = c01 * r; Si[0][2] = c02 * r;
+        Si[1][1] = c11 * r; Si[1][2] = c12 * r; Si[2][2] = c22 * r;
+        Si[1][0] = Si[0][1]; Si[2][0] = Si[0][2]; Si[2][1] = Si[1][2];
+        ok = is_positive_finite_b(S[0][0]) && is_positive_finite_b(c22) && is_positive_finite_b(det);
     }
-    mat_tmul_sym<B>(Li, Li, Si);   // L^-T L^-1
+    if constexpr (LOGDET) logdet = log(det);
+    else logdet = 0.0;
+    return ok;
 }
 
 template <int B>
@@ -95,7 +89,7 @@ template <int B, bool LOGDET = true>
 __device__ __forceinline__ bool trans_scaled(double x, double sf, double (&Ph)[B][B], double (&Qi)[B][B],
                                              double& ldq) {
     phi<B>(x, exp(-x), Ph);
-    double P1m[B][B], T[B][B], Q[B][B], L[B][B];
+    double P1m[B][B], T[B][B], Q[B][B];
 #pragma unroll
     for (int r = 0; r < B; ++r)
 #pragma unroll
@@ -106,9 +100,7 @@ __device__ __forceinline__ bool trans_scaled(double x, double sf, double (&Ph)[B
     for (int r = 0; r < B; ++r)
 #pragma unroll
         for (int q = 0; q < B; ++q) Q[r][q] = sf * (P1m[r][q] - Q[r][q]);
-    const bool ok = chol<B>(Q, L);
-    chol_inv<B, LOGDET>(L, Qi, ldq);
-    return ok;
+    return spd_inv<B, LOGDET>(Q, Qi, ldq);
 }
 
 // One thread per step i: D_i = Q_{i-1}^-1 + A_i^T Q_i^-1 A_i + H^T H / s_n
@@ -131,13 +123,12 @@ __global__ void __launch_bounds__(128) k_assemble(const double* __restrict__ t, 
     double Dt[B][B], ldq_prev;
     // Q_{i-1}^-1 (or Pinf^-1) in scaled coordinates
     if (i == 0) {
-        double P[B][B], L[B][B];
+        double P[B][B];
 #pragma unroll
         for (int r = 0; r < B; ++r)
 #pragma unroll
             for (int q = 0; q < B; ++q) P[r][q] = sf * p1<B>(r, q);
-        if (!chol<B>(P, L)) bad |= ST_ENUMERIC;
-        chol_inv<B>(L, Dt, ldq_prev);
+        if (!spd_inv<B>(P, Dt, ldq_prev)) bad |= ST_ENUMERIC;
     } else {
         const double dt = t[i] - t[i - 1];
         if (!(dt > 0.0)) bad |= (dt < 0.0) ? ST_ENOTSORTED : ST_ENUMERIC;   // Q = 0 at a tie: no precision
@@ -210,10 +201,9 @@ __global__ void __launch_bounds__(128) k_btd_reduce(const double* __restrict__ D
     int bad = 0;
     if (e > 0) {   // left odd neighbour k = e-1, T[e][k] = O_k
         const int64_t k = e - 1;
-        double Dk[B][B], L[B][B], Dki[B][B], Ok[B][B], T[B][B], U[B][B], w[B], z[B], l0;
+        double Dk[B][B], Dki[B][B], Ok[B][B], T[B][B], U[B][B], w[B], z[B], l0;
         blk_load<B>(D + k * (B * B), Dk);
-        if (!chol<B>(Dk, L)) bad |= ST_ENUMERIC;
-        chol_inv<B, false>(L, Dki, l0);
+        if (!spd_inv<B, false>(Dk, Dki, l0)) bad |= ST_ENUMERIC;
         blk_load<B>(O + k * (B * B), Ok);
         mat_mul<B>(Ok, Dki, T);            // O_k D_k^-1
         mat_mul_t_sym<B>(T, Ok, U);        // O_k D_k^-1 O_k^T
@@ -229,10 +219,9 @@ __global__ void __launch_bounds__(128) k_btd_reduce(const double* __restrict__ D
     }
     if (e + 1 < nlo) {   // right odd neighbour k = e+1, T[e][k] = O_e^T
         const int64_t k = e + 1;
-        double Dk[B][B], L[B][B], Dki[B][B], Oe[B][B], T[B][B], U[B][B], w[B], z[B], l1;
+        double Dk[B][B], Dki[B][B], Oe[B][B], T[B][B], U[B][B], w[B], z[B], l1;
         blk_load<B>(D + k * (B * B), Dk);
-        if (!chol<B>(Dk, L)) bad |= ST_ENUMERIC;
-        chol_inv<B>(L, Dki, l1);
+        if (!spd_inv<B>(Dk, Dki, l1)) bad |= ST_ENUMERIC;
         ldj = l1;
         blk_store<B>(Dinv + k * (B * B), Dki);
         blk_load<B>(O + e * (B * B), Oe);
@@ -272,10 +261,9 @@ template <int B>
 __global__ void k_btd_top(const double* __restrict__ D, const double* __restrict__ r, double* __restrict__ x,
                           double* __restrict__ Sd, double* __restrict__ ld, int* status) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double Dk[B][B], L[B][B], Si[B][B], w[B], z[B], l;
+    double Dk[B][B], Si[B][B], w[B], z[B], l;
     blk_load<B>(D, Dk);
-    if (!chol<B>(Dk, L)) atomicOr(status, ST_ENUMERIC);
-    chol_inv<B>(L, Si, l);
+    if (!spd_inv<B>(Dk, Si, l)) atomicOr(status, ST_ENUMERIC);
 #pragma unroll
     for (int q = 0; q < B; ++q) w[q] = r[q];
     mat_vec<B>(Si, w, z);
@@ -285,8 +273,9 @@ __global__ void k_btd_top(const double* __restrict__ D, const double* __restrict
     ld[0] = l;
 }
 
-// Back-substitution from level l (x', S'd, S'o known) to level l-1: even node
-// 2j copies node j; odd node k (neighbours a = k-1, c = k+1) gets
+// Back-substitution from level l (x', S'd, S'o known) to level l-1, one thread
+// per node j of level l: even node 2j copies node j; odd node k = 2j+1
+// (neighbours a = k-1, c = k+1) gets
 //   x_k = D_k^-1 (r_k - O_{k-1} x_a - O_k^T x_c),  Za = D_k^-1 O_{k-1}, Zc = D_k^-1 O_k^T
 //   S_ka = -(Za S_aa + Zc S_ca),  S_kc = -(Za S_ca^T + Zc S_cc)
 //   S_kk = D_k^-1 - S_ka Za^T - S_kc Zc^T
@@ -298,18 +287,18 @@ __global__ void __launch_bounds__(128) k_btd_back(const double* __restrict__ Din
                                                   const double* __restrict__ So2, int64_t nhi,
                                                   double* __restrict__ x, double* __restrict__ Sd,
                                                   double* __restrict__ So, int want_s) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= nlo) return;
-    if ((i & 1) == 0) {
-        const int64_t j = i >> 1;
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= nhi) return;
+    {
+        const int64_t i = 2 * j;
 #pragma unroll
         for (int q = 0; q < B; ++q) x[i * B + q] = x2[j * B + q];
         if (want_s)
 #pragma unroll
             for (int q = 0; q < B * B; ++q) Sd[i * (B * B) + q] = Sd2[j * (B * B) + q];
-        return;
     }
-    const int64_t k = i, a = k - 1, c = k + 1, ja = a >> 1;
+    const int64_t k = 2 * j + 1, a = k - 1, c = k + 1, ja = j;
+    if (k >= nlo) return;
     const bool hasc = c < nlo;
     double Dki[B][B], Oa[B][B], Oc[B][B], w[B], xa[B], xc[B], z[B];
     blk_load<B>(Dinv + k * (B * B), Dki);   // D_k^-1 from the reduction
@@ -586,13 +575,12 @@ __global__ void __launch_bounds__(128) k_literal_terms(const double* __restrict_
         }
         double Dt[B][B], YD[B][B], Ot[B][B], YO[B][B], dld_l;
         if (i == 0) {
-            double P[B][B], L[B][B], l0;
+            double P[B][B], l0;
 #pragma unroll
             for (int r = 0; r < B; ++r)
 #pragma unroll
                 for (int q = 0; q < B; ++q) P[r][q] = sf * p1<B>(r, q);
-            chol<B>(P, L);
-            chol_inv<B, false>(L, Dt, l0);
+            spd_inv<B, false>(P, Dt, l0);
 #pragma unroll
             for (int r = 0; r < B; ++r)
 #pragma unroll
@@ -744,7 +732,7 @@ static int btd_core(int64_t n, const double* D, const double* O, const double* r
         double* xl = (l == 1) ? x : lvl(lay.off_x, l - 1);
         double* Sdl = (l == 1) ? Sd : lvl(lay.off_Sd, l - 1);
         double* Sol = (l == 1) ? So : lvl(lay.off_So, l - 1);
-        k_btd_back<B><<<(unsigned)((lay.cnt[l - 1] + 127) / 128), 128, 0, st>>>(
+        k_btd_back<B><<<(unsigned)((lay.cnt[l] + 127) / 128), 128, 0, st>>>(
             Dl, Ol, rl, lay.cnt[l - 1], lvl(lay.off_x, l), lvl(lay.off_Sd, l), lvl(lay.off_So, l), lay.cnt[l], xl,
             Sdl, Sol, want_s);
     }
