@@ -19,6 +19,7 @@
 #include <stdint.h>
 
 #include "chain.cuh"
+#include "coop.cuh"
 #include "internal.h"
 
 namespace spg {
@@ -271,6 +272,171 @@ __global__ void k_btd_top(const double* __restrict__ D, const double* __restrict
     for (int q = 0; q < B; ++q) x[q] = z[q];
     blk_store<B>(Sd, Si);
     ld[0] = l;
+}
+
+// ------------------------------------------------------------------ the narrow upper levels on lane groups
+//
+// A level with few nodes is a chain of dependent FP64 work, and on GB300 a
+// warp instruction costs its sub-partition the same issue time however few
+// lanes are active.  These forms spread one node over a lane group (coop.cuh:
+// lane B r + c holds entry (r, c) of every block, vectors are row-replicated),
+// so a b x b product is b FMAs per lane.  They follow the one-thread kernels
+// term by term (same cofactors, products summed in the same order, same
+// symmetrisation).  A missing neighbour is computed on a stand-in block and
+// masked out, so every lane runs the same shuffles.
+
+// entry (i, k) of a lane-group block read from its upper triangle
+template <int B>
+__device__ __forceinline__ double csh_upper(double S, int i, int k) {
+    return csh<B>(S, (i < k ? i : k) * B + (i < k ? k : i));
+}
+
+// spd_inv on a lane group: entry (r, c) of S^-1 and, on every lane, log det S
+template <int B, bool LOGDET>
+__device__ __forceinline__ bool cspd_inv(double S, double& Si, double& logdet, const CPos<B>& p) {
+    double det, cof;
+    bool ok;
+    if constexpr (B == 1) {
+        det = S;
+        cof = 1.0;
+        ok = is_positive_finite_b(det);
+    } else if constexpr (B == 2) {
+        const double s00 = csh<B>(S, 0), s01 = csh<B>(S, 1), s11 = csh<B>(S, 3);
+        det = fma(s00, s11, -s01 * s01);
+        cof = (p.row == p.col) ? (p.row == 0 ? s11 : s00) : -s01;
+        ok = is_positive_finite_b(s00) && is_positive_finite_b(det);
+    } else {
+        // cofactor (r, c) = S[r1][c1] S[r2][c2] - S[r1][c2] S[r2][c1], r1 = r+1, r2 = r+2 (mod 3),
+        // read from the upper triangle as spd_inv does
+        const int r1 = (p.row + 1) % 3, r2 = (p.row + 2) % 3, c1 = (p.col + 1) % 3, c2 = (p.col + 2) % 3;
+        cof = fma(csh_upper<B>(S, r1, c1), csh_upper<B>(S, r2, c2),
+                  -(csh_upper<B>(S, r1, c2) * csh_upper<B>(S, r2, c1)));
+        const double s00 = csh<B>(S, 0), s01 = csh<B>(S, 1), s02 = csh<B>(S, 2);
+        const double c00 = csh<B>(cof, 0), c01 = csh<B>(cof, 1), c02 = csh<B>(cof, 2), c22 = csh<B>(cof, 8);
+        det = fma(s00, c00, fma(s01, c01, s02 * c02));
+        ok = is_positive_finite_b(s00) && is_positive_finite_b(c22) && is_positive_finite_b(det);
+    }
+    Si = cof * (1.0 / det);
+    if constexpr (LOGDET) logdet = log(det);
+    else logdet = 0.0;
+    return ok;
+}
+
+// k_btd_reduce on lane groups: group g is node g of the level above
+template <int B>
+__global__ void __launch_bounds__(128) k_btd_reduce_coop(const double* __restrict__ D, const double* __restrict__ O,
+                                                         const double* __restrict__ r, int64_t nlo,
+                                                         double* __restrict__ D2, double* __restrict__ O2,
+                                                         double* __restrict__ r2, int64_t nhi,
+                                                         double* __restrict__ ld, double* __restrict__ Dinv,
+                                                         int* status) {
+    constexpr int W = Coop<B>::W, BB = B * B;
+    const CPos<B> p;
+    const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / W;
+    const bool act = g < nhi;
+    const int64_t j = act ? g : nhi - 1;   // groups past the end mirror the last node and store nothing
+    const int64_t e = 2 * j;
+    const int ent = p.row * B + p.col;
+    double Dn = D[e * BB + ent], rn = r[e * B + p.row];
+    int bad = 0;
+    {   // left odd neighbour k = e-1 (stand-in: node e itself)
+        const bool has = e > 0;
+        const int64_t k = has ? e - 1 : e;
+        double Dki, l0;
+        const bool ok = cspd_inv<B, false>(D[k * BB + ent], Dki, l0, p);
+        if (has && !ok) bad |= ST_ENUMERIC;
+        const double Ok = O[k * BB + ent];
+        const double T = cmm<B>(Ok, Dki, p);
+        const double U = csym_upper<B>(cmmt<B>(T, Ok, p), p);
+        const double z = cmv<B>(T, r[k * B + p.row], p);
+        if (has) { Dn -= U; rn -= z; }
+    }
+    double ldj = 0.0;
+    {   // right odd neighbour k = e+1 (stand-in: node e; O_e stands in by O_{e-1}, nlo >= 2)
+        const bool has = e + 1 < nlo;
+        const int64_t k = has ? e + 1 : e, oe = has ? e : e - 1;
+        double Dki, l1;
+        const bool ok = cspd_inv<B, true>(D[k * BB + ent], Dki, l1, p);
+        if (has && !ok) bad |= ST_ENUMERIC;
+        const double Oe = O[oe * BB + ent];
+        const double T = cmm<B>(Dki, Oe, p);
+        const double U = csym_upper<B>(cmtm<B>(Oe, T, p), p);
+        const double z = cmv<B>(Dki, r[k * B + p.row], p);
+        const double w = cmtv<B>(Oe, z, p);
+        if (has) { Dn -= U; rn -= w; ldj = l1; }
+        if (act && has && p.valid) Dinv[k * BB + ent] = Dki;
+        const bool haso = has && (k + 1 < nlo);   // O'_j = -O_k D_k^-1 O_e
+        const double V = -cmm<B>(O[(haso ? k : oe) * BB + ent], T, p);
+        if (act && haso && p.valid) O2[j * BB + ent] = V;
+    }
+    Dn = 0.5 * (Dn + csh<B>(Dn, p.col * B + p.row));
+    if (act && p.valid) {
+        D2[j * BB + ent] = Dn;
+        if (p.col == 0) r2[j * B + p.row] = rn;
+        if (ent == 0) ld[j] = ldj;
+    }
+    if (act && bad) atomicOr(status, bad);
+}
+
+// k_btd_back on lane groups: group g is node g of the level above
+template <int B>
+__global__ void __launch_bounds__(128) k_btd_back_coop(const double* __restrict__ Dinv, const double* __restrict__ O,
+                                                       const double* __restrict__ r, int64_t nlo,
+                                                       const double* __restrict__ x2, const double* __restrict__ Sd2,
+                                                       const double* __restrict__ So2, int64_t nhi,
+                                                       double* __restrict__ x, double* __restrict__ Sd,
+                                                       double* __restrict__ So, int want_s) {
+    constexpr int W = Coop<B>::W, BB = B * B;
+    const CPos<B> p;
+    const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / W;
+    const bool act = g < nhi;
+    const int64_t j = act ? g : nhi - 1;
+    const int ent = p.row * B + p.col;
+    if (act && p.valid) {   // even node 2j is node j of the level above
+        if (p.col == 0) x[(2 * j) * B + p.row] = x2[j * B + p.row];
+        if (want_s) Sd[(2 * j) * BB + ent] = Sd2[j * BB + ent];
+    }
+    // odd node k = 2j+1; a group whose k is past the end computes on node k-2's data and stores nothing
+    const int64_t k = 2 * j + 1;
+    const bool hask = k < nlo;
+    const int64_t kk = hask ? k : k - 2;          // nlo >= 2, so node 1 exists
+    const int64_t a = kk - 1, ja = a >> 1;
+    const bool hasc = kk + 1 < nlo;
+    const int64_t oc = hasc ? kk : a, jc = hasc ? ja + 1 : ja;
+    const double Dki = Dinv[kk * BB + ent];
+    const double Oa = O[a * BB + ent];            // T[k][a]
+    const double Oc = O[oc * BB + ent];           // T[c][k]; T[k][c] = Oc^T
+    double w = r[kk * B + p.row] - cmv<B>(Oa, x2[ja * B + p.row], p);
+    const double wc = w - cmtv<B>(Oc, x2[jc * B + p.row], p);
+    w = hasc ? wc : w;
+    const double xk = cmv<B>(Dki, w, p);
+    if (act && hask && p.valid && p.col == 0) x[k * B + p.row] = xk;
+    if (!want_s) return;                          // uniform over the launch
+    const double Za = cmm<B>(Dki, Oa, p);
+    const double Saa = Sd2[ja * BB + ent];
+    double Ska = cmm<B>(Za, Saa, p);
+    const double Zc = cmmt<B>(Dki, Oc, p);
+    const double Scc = Sd2[jc * BB + ent];
+    const double Sca = So2[ja * BB + ent];        // S[c][a] of the level above (a stand-in when !hasc)
+    const double T1 = cmm<B>(Zc, Sca, p);
+    const double T2 = cmmt<B>(Za, Sca, p);
+    double Skc = cmm<B>(Zc, Scc, p);
+    Ska = hasc ? -(Ska + T1) : -Ska;
+    Skc = -(T2 + Skc);
+    double s = Dki;
+#pragma unroll
+    for (int m = 0; m < B; ++m) {
+        s = fma(-csh<B>(Ska, p.row * B + m), csh<B>(Za, p.col * B + m), s);
+        const double t = fma(-csh<B>(Skc, p.row * B + m), csh<B>(Zc, p.col * B + m), s);
+        s = hasc ? t : s;
+    }
+    const double Skk = 0.5 * (s + csh<B>(s, p.col * B + p.row));
+    const double SkcT = csh<B>(Skc, p.col * B + p.row);
+    if (act && hask && p.valid) {
+        Sd[k * BB + ent] = Skk;
+        So[a * BB + ent] = Ska;                   // block (k, k-1)
+        if (hasc) So[k * BB + ent] = SkcT;        // block (k+1, k) = Skc^T
+    }
 }
 
 // Back-substitution from level l (x', S'd, S'o known) to level l-1, one thread
@@ -698,6 +864,14 @@ struct BtdLayout {
     }
 };
 
+// Levels with at most this many nodes run on lane groups (k_btd_*_coop):
+// below it a level is one node's dependent chain; above it the lane groups'
+// extra shuffles and duplicated lanes cost more than they save (measured per
+// level on GB300: the reduction breaks even near 4096 nodes, the
+// back-substitution near 8192).
+static constexpr int64_t BTD_COOP_REDUCE = 2048;
+static constexpr int64_t BTD_COOP_BACK = 4096;
+
 // Odd-even reduction, top solve, back-substitution, log det sum.  sc is
 // BtdLayout(B, n).total bytes of scratch; status is OR-ed with error bits.
 template <int B>
@@ -712,9 +886,14 @@ static int btd_core(int64_t n, const double* D, const double* O, const double* r
         const double* Dl = (l == 1) ? D : lvl(lay.off_D, l - 1);
         const double* Ol = (l == 1) ? O : lvl(lay.off_O, l - 1);
         const double* rl = (l == 1) ? r : lvl(lay.off_r, l - 1);
-        k_btd_reduce<B><<<(unsigned)((lay.cnt[l] + 127) / 128), 128, 0, st>>>(
-            Dl, Ol, rl, lay.cnt[l - 1], lvl(lay.off_D, l), lvl(lay.off_O, l), lvl(lay.off_r, l), lay.cnt[l],
-            ld + ldo, lvl(lay.off_Dinv, l - 1), status);
+        if (lay.cnt[l] <= BTD_COOP_REDUCE)
+            k_btd_reduce_coop<B><<<(unsigned)((lay.cnt[l] * Coop<B>::W + 127) / 128), 128, 0, st>>>(
+                Dl, Ol, rl, lay.cnt[l - 1], lvl(lay.off_D, l), lvl(lay.off_O, l), lvl(lay.off_r, l), lay.cnt[l],
+                ld + ldo, lvl(lay.off_Dinv, l - 1), status);
+        else
+            k_btd_reduce<B><<<(unsigned)((lay.cnt[l] + 127) / 128), 128, 0, st>>>(
+                Dl, Ol, rl, lay.cnt[l - 1], lvl(lay.off_D, l), lvl(lay.off_O, l), lvl(lay.off_r, l), lay.cnt[l],
+                ld + ldo, lvl(lay.off_Dinv, l - 1), status);
         ldo += lay.cnt[l];
     }
     {
@@ -732,9 +911,14 @@ static int btd_core(int64_t n, const double* D, const double* O, const double* r
         double* xl = (l == 1) ? x : lvl(lay.off_x, l - 1);
         double* Sdl = (l == 1) ? Sd : lvl(lay.off_Sd, l - 1);
         double* Sol = (l == 1) ? So : lvl(lay.off_So, l - 1);
-        k_btd_back<B><<<(unsigned)((lay.cnt[l] + 127) / 128), 128, 0, st>>>(
-            Dl, Ol, rl, lay.cnt[l - 1], lvl(lay.off_x, l), lvl(lay.off_Sd, l), lvl(lay.off_So, l), lay.cnt[l], xl,
-            Sdl, Sol, want_s);
+        if (lay.cnt[l] <= BTD_COOP_BACK)
+            k_btd_back_coop<B><<<(unsigned)((lay.cnt[l] * Coop<B>::W + 127) / 128), 128, 0, st>>>(
+                Dl, Ol, rl, lay.cnt[l - 1], lvl(lay.off_x, l), lvl(lay.off_Sd, l), lvl(lay.off_So, l), lay.cnt[l],
+                xl, Sdl, Sol, want_s);
+        else
+            k_btd_back<B><<<(unsigned)((lay.cnt[l] + 127) / 128), 128, 0, st>>>(
+                Dl, Ol, rl, lay.cnt[l - 1], lvl(lay.off_x, l), lvl(lay.off_Sd, l), lvl(lay.off_So, l), lay.cnt[l],
+                xl, Sdl, Sol, want_s);
     }
     colsum(ld, ldo + 1, 0, 1, logdet, (double*)(sc + lay.off_red), st);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
