@@ -30,8 +30,8 @@ struct spingp_model {
     spg::GModel gm;
     // host-buffer calls: a copy stream and its events, created on first use
     int feed_dev;    // device they belong to, -1 = none
-    cudaStream_t feed_copy, feed_fold[spg::FEED_PIECES];
-    cudaEvent_t feed_ev[1 + spg::FEED_PIECES], feed_done[spg::FEED_PIECES];
+    cudaStream_t feed_copy;
+    cudaEvent_t feed_ev[1 + spg::FEED_PIECES];
 };
 
 namespace {
@@ -301,10 +301,6 @@ void spingp_model_destroy(spingp_model* m) {
         cudaSetDevice(m->feed_dev);
         cudaStreamDestroy(m->feed_copy);
         for (int i = 0; i <= spg::FEED_PIECES; ++i) cudaEventDestroy(m->feed_ev[i]);
-        for (int i = 0; i < spg::FEED_PIECES; ++i) {
-            cudaStreamDestroy(m->feed_fold[i]);
-            cudaEventDestroy(m->feed_done[i]);
-        }
         cudaSetDevice(cur);
     }
     if (m->prof) {
@@ -442,10 +438,6 @@ static spingp_status feed_ready(spingp_model* m) {
     if (cudaStreamCreateWithFlags(&m->feed_copy, cudaStreamNonBlocking) != cudaSuccess) return SPINGP_ECUDA;
     for (int i = 0; i <= spg::FEED_PIECES; ++i)
         if (cudaEventCreateWithFlags(&m->feed_ev[i], cudaEventDisableTiming) != cudaSuccess) return SPINGP_ECUDA;
-    for (int i = 0; i < spg::FEED_PIECES; ++i)
-        if (cudaStreamCreateWithFlags(&m->feed_fold[i], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&m->feed_done[i], cudaEventDisableTiming) != cudaSuccess)
-            return SPINGP_ECUDA;
     m->feed_dev = dev;
     return SPINGP_OK;
 }
@@ -482,7 +474,6 @@ spingp_status spingp_grad_host(spingp_model* m, const double* t, const double* y
         spg::HostFeed f;
         f.t = t; f.y = y; f.copy = m->feed_copy; f.npieces = spg::FEED_PIECES;
         for (int i = 0; i <= spg::FEED_PIECES; ++i) f.ev[i] = m->feed_ev[i];
-        for (int i = 0; i < spg::FEED_PIECES; ++i) { f.fold[i] = m->feed_fold[i]; f.done[i] = m->feed_done[i]; }
         rc = spg::matern_run(m->b, spg::MODE_GRAD, td, yd, n, L, thd, od, od + 1, NULL, NULL, ws, s, ev, miss, &f);
     }
     if (rc) return SPINGP_ECUDA;

@@ -37,25 +37,23 @@ size_t matern_ws_bytes(int b, int64_t n, int64_t L, int mode);
 int matern_prepare();
 // ev: NULL, or 5 events recorded around the four stages
 // missing: 1 = a NaN observation is a missing one (predicted, not conditioned on)
-// host feed: t and y copied from host memory piece by piece on a copy
-// stream; piece p's elimination runs on its own stream fold[p] once the piece
-// has arrived, so the pieces' folds run concurrently and overlap the later
-// copies.  ev[0] orders the copies after earlier work on the main stream,
-// ev[1 + p] marks piece p's copy, done[p] its fold.
-static constexpr int FEED_PIECES = 8;
+// Inputs from host memory (matern_run with a feed): t and y are copied on the
+// copy stream in FEED_PIECES pieces of steps -- piece p is steps
+// [p W, (p+1) W) of every chunk, W = ceil(L / FEED_PIECES) -- and the
+// elimination runs as one launch per piece on the main stream, each after its
+// piece's copy.  ev[0] orders the copies after earlier work on the main
+// stream, ev[1 + p] marks piece p's copy.
+static constexpr int FEED_PIECES = 4;
 struct HostFeed {
     const double* t;
     const double* y;
     cudaStream_t copy;
-    cudaStream_t fold[FEED_PIECES];
     cudaEvent_t ev[1 + FEED_PIECES];
-    cudaEvent_t done[FEED_PIECES];
     int npieces;
 };
 int matern_run(int b, int mode, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
                double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws, cudaStream_t st,
                cudaEvent_t* ev, int missing, const HostFeed* feed = nullptr);
-int64_t matern_fold_blocks(int64_t n, int64_t L);
 int matern_launch_count(int b, int64_t n, int64_t L, int mode);
 
 // batches of independent series: offsets (device, nseries + 1 entries), theta

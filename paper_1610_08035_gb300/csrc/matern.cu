@@ -236,9 +236,16 @@ __device__ __forceinline__ void tree_down_coop(double* spre, double* ssuf, const
 // every tree node and the block total.  Jordan coordinates (chain.cuh); the
 // conditional covariance is carried as C - Pinf, so the prediction is a
 // single sandwich e^-2x T (C - Pinf) T^T.
+// A launch may cover steps [j0, j1) of every chunk only (a piece of the
+// elimination, for inputs that arrive in pieces): the first piece starts the
+// element, the others resume it from `state` (the element as carried, then
+// the scale sa: Dims::NE + 1 fields of nc entries), and only the last piece
+// finishes the element and runs the block's up-sweep.  One launch with
+// j0 = 0, j1 >= L does the whole chunk; the pieces give the same bits.
 template <int B, bool BATCH>
 __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict__ nodes, double* __restrict__ btot,
-                                              double* __restrict__ phis, int64_t blk0) {
+                                              double* __restrict__ phis, int64_t blk0, int64_t j0, int64_t j1,
+                                              double* __restrict__ state, int first, int last) {
     constexpr int NE = Dims<B>::NE;
     __shared__ double sm[CTA * NE];
     __shared__ double etab[EXPTAB];
@@ -254,14 +261,20 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
     int bad = 0;
     if (cr.valid) {
         const double ell = cr.th[0], sf = cr.th[1], s2 = cr.th[2];
-        if (!theta_ok<B>(ell, sf, s2)) bad |= ST_EINVAL;
+        if (first && !theta_ok<B>(ell, sf, s2)) bad |= ST_EINVAL;
         const double lam = sqrt(2.0 * B - 1.0) / ell;
         double sp0[B];   // first column of Pinf
 #pragma unroll
         for (int r = 0; r < B; ++r) sp0[r] = sf * pj<B>(r, 0);
         const int64_t s = cr.s, e = cr.e;
-        // el.C holds C - Pinf until the end of the chunk
-        if (s == cr.s0) {
+        const int64_t i0 = min(e, s + j0), i1 = min(e, s + j1);
+        // el.C holds C - Pinf until the end of the chunk; el.A holds A / sa:
+        // the factors e^-x of the steps are collected in sa
+        double sa = 1.0;
+        if (!first) {
+            elem_load<B>(state, nc, c, el);
+            sa = state[NE * nc + c];
+        } else if (s == cr.s0) {
             // the first state has the stationary prior: no dependence on an earlier node
 #pragma unroll
             for (int i = 0; i < B; ++i)
@@ -273,10 +286,8 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
 #pragma unroll
                 for (int j = 0; j < B; ++j) el.C[i][j] = -sf * pj<B>(i, j);
         }
-        double tp = (s > cr.s0) ? a.t[s - 1] : 0.0;
-        // el.A holds A / sa: the factors e^-x of the steps are collected in sa
-        double sa = 1.0;
-        for (int64_t i = s; i < e; ++i) {
+        double tp = (i0 > cr.s0 && i0 < i1) ? a.t[i0 - 1] : 0.0;
+        for (int64_t i = i0; i < i1; ++i) {
             const double ti = a.t[i], yi = a.y[i];
             const bool obs = !(a.missing && is_nan_b(yi));
             if (!is_finite_b(ti) || (obs && !is_finite_b(yi))) bad |= ST_ENONFINITE;
@@ -331,12 +342,18 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
             }
             tp = ti;
         }
+        if (!last) {
+            elem_store<B>(state, nc, c, el);
+            state[NE * nc + c] = sa;
+        } else {
 #pragma unroll
-        for (int r = 0; r < B; ++r)
+            for (int r = 0; r < B; ++r)
 #pragma unroll
-            for (int q = 0; q < B; ++q) { el.C[r][q] += sf * pj<B>(r, q); el.A[r][q] *= sa; }
+                for (int q = 0; q < B; ++q) { el.C[r][q] += sf * pj<B>(r, q); el.A[r][q] *= sa; }
+        }
     }
     if (bad) atomicOr(a.status, bad);
+    if (!last) return;   // uniform over the launch: the up-sweep runs after the last piece
     // odd-even up-sweep inside the block (chunks past the end are identities):
     // the wide lower levels one combine per thread, the upper levels (at most
     // TREE_COOP_CNT combines) one combine per lane group
@@ -1011,11 +1028,12 @@ static bool single_tile(int64_t ne) { return ne <= (int64_t)SCAN_TS; }
 static int64_t mid_tiles(int64_t ne) { return (ne + SCAN_TS - 1) / SCAN_TS; }
 
 // Workspace: [status | tree nodes | block totals | block prefix | block suffix |
-//             grid scan levels | transition per step | block partials | stored steps]
+//             grid scan levels | transition per step | block partials | stored steps |
+//             elimination state between pieces]
 template <int B>
 struct Layout {
     int64_t nc, nb;
-    size_t off_nodes, off_btot, off_bpre, off_bsuf, off_phis, off_part, off_store, total;
+    size_t off_nodes, off_btot, off_bpre, off_bsuf, off_phis, off_part, off_store, off_state, total;
     int nlev;
     int64_t lev_n[8];
     size_t lev_tot[8], lev_pre[8], lev_suf[8];
@@ -1050,6 +1068,7 @@ struct Layout {
         off_part = o; o = align256(o + sizeof(double) * Acc<B>::N * (nseries > 0 ? nc : nb));
         off_store = o;
         if (mode != MODE_LOGLIK) o = align256(o + sizeof(double) * Stored<B>::N * (size_t)L * nc);
+        off_state = o; o = align256(o + sizeof(double) * (NE + 1) * (size_t)nc);   // a piecewise elimination
         total = o;
     }
 };
@@ -1100,40 +1119,58 @@ int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t 
     double* phis = (double*)(ws + lay.off_phis);
     double* part = (double*)(ws + lay.off_part);
     double* store = (double*)(ws + lay.off_store);
+    double* state = (double*)(ws + lay.off_state);
     ChainArgs a{t, y, n, L, lay.nc, lay.nb, theta, status, nullptr, nullptr, 0, 3, missing};
     const unsigned grid = (unsigned)lay.nb;
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
     if (ev) cudaEventRecord(ev[0], st);
     if (!feed) {
-        k_fold<B, false><<<grid, CTA, 0, st>>>(a, nodes, btot, phis, 0);
+        k_fold<B, false><<<grid, CTA, 0, st>>>(a, nodes, btot, phis, 0, 0, L, state, 1, 1);
     } else {
-        // t and y arrive from host memory in pieces of whole blocks on the copy
-        // stream; each piece's fold starts once its copy is done, so the
-        // copies of the later pieces overlap the fold of the earlier ones.
-        // (A chunk's first step reads the previous step's time: the pieces
-        // are copied in order, so it has arrived with an earlier piece.)
+        // t and y arrive from host memory in pieces of steps: piece p holds
+        // steps [p W, (p+1) W) of every chunk (strided copies, chunk = row of
+        // L steps), and fold launch p eliminates exactly those steps once its
+        // copy is done.  The copy of piece p+1 overlaps the fold of piece p,
+        // and every launch keeps all SMs busy.  Piece 0 also carries the
+        // step before each chunk (its first transition needs that time).
+        const int64_t W = (L + feed->npieces - 1) / feed->npieces;
+        const int64_t np = (L + W - 1) / W;
+        const int64_t nfull = n / L, tail = n - nfull * L;
         if (cudaEventRecord(feed->ev[0], st) != cudaSuccess) return 1;
         if (cudaStreamWaitEvent(feed->copy, feed->ev[0], 0) != cudaSuccess) return 1;
-        const int64_t per = (lay.nb + feed->npieces - 1) / feed->npieces;
-        const int64_t span = (int64_t)CTA * L;   // steps per block
-        int p = 0;
-        for (int64_t b0 = 0; b0 < lay.nb; b0 += per, ++p) {
-            const int64_t b1 = min(lay.nb, b0 + per);
-            const int64_t s0 = b0 * span, s1 = min(n, b1 * span);
-            if (s1 > s0) {
-                const size_t bytes = sizeof(double) * (size_t)(s1 - s0);
-                if (cudaMemcpyAsync(const_cast<double*>(t) + s0, feed->t + s0, bytes, cudaMemcpyHostToDevice,
-                                    feed->copy) != cudaSuccess) return 1;
-                if (cudaMemcpyAsync(const_cast<double*>(y) + s0, feed->y + s0, bytes, cudaMemcpyHostToDevice,
-                                    feed->copy) != cudaSuccess) return 1;
+        for (int64_t p = 0; p < np; ++p) {
+            const int64_t c0 = p * W, c1 = min(L, c0 + W);
+            const bool prev = (p == 0 && c1 < L);   // piece 0 also copies column L-1 of the row before
+            for (int arr = 0; arr < 2; ++arr) {
+                double* dst = const_cast<double*>(arr ? y : t);
+                const double* src = arr ? feed->y : feed->t;
+                const size_t w = sizeof(double) * (size_t)(c1 - c0), pitch = sizeof(double) * (size_t)L;
+                if (!prev) {
+                    if (nfull > 0 && cudaMemcpy2DAsync(dst + c0, pitch, src + c0, pitch, w, (size_t)nfull,
+                                                       cudaMemcpyHostToDevice, feed->copy) != cudaSuccess)
+                        return 1;
+                } else {
+                    // row 0, then rows 1.. from one step before their start (c1 + 1 <= L)
+                    if (nfull > 0 && cudaMemcpyAsync(dst, src, w, cudaMemcpyHostToDevice, feed->copy) != cudaSuccess)
+                        return 1;
+                    if (nfull > 1 &&
+                        cudaMemcpy2DAsync(dst + L - 1, pitch, src + L - 1, pitch, w + sizeof(double),
+                                          (size_t)(nfull - 1), cudaMemcpyHostToDevice, feed->copy) != cudaSuccess)
+                        return 1;
+                }
+                if (tail > c0) {   // the last, shorter chunk
+                    const int64_t b0 = nfull * L + c0 - ((prev && nfull > 0) ? 1 : 0);
+                    const int64_t b1 = nfull * L + min(c1, tail);
+                    if (cudaMemcpyAsync(dst + b0, src + b0, sizeof(double) * (size_t)(b1 - b0),
+                                        cudaMemcpyHostToDevice, feed->copy) != cudaSuccess)
+                        return 1;
+                }
             }
             if (cudaEventRecord(feed->ev[1 + p], feed->copy) != cudaSuccess) return 1;
-            if (cudaStreamWaitEvent(feed->fold[p], feed->ev[1 + p], 0) != cudaSuccess) return 1;
-            k_fold<B, false><<<(unsigned)(b1 - b0), CTA, 0, feed->fold[p]>>>(a, nodes, btot, phis, b0);
-            if (cudaEventRecord(feed->done[p], feed->fold[p]) != cudaSuccess) return 1;
+            if (cudaStreamWaitEvent(st, feed->ev[1 + p], 0) != cudaSuccess) return 1;
+            k_fold<B, false><<<grid, CTA, 0, st>>>(a, nodes, btot, phis, 0, c0, c1, state, p == 0 ? 1 : 0,
+                                                   p == np - 1 ? 1 : 0);
         }
-        for (int q = 0; q < p; ++q)
-            if (cudaStreamWaitEvent(st, feed->done[q], 0) != cudaSuccess) return 1;
     }
     if (ev) cudaEventRecord(ev[1], st);
     scan_level<B>(btot, lay.nb, bpre, bsuf, lay, ws, 0, st);
@@ -1188,12 +1225,13 @@ int matern_run_batched_t(int mode, const int64_t* offsets, int64_t nseries, int6
     double* phis = (double*)(ws + lay.off_phis);
     double* part = (double*)(ws + lay.off_part);
     double* store = (double*)(ws + lay.off_store);
+    double* state = (double*)(ws + lay.off_state);
     ChainArgs a{t, y, n_total, L, lay.nc, lay.nb, theta, status, offsets, cstart, nseries, 3, missing};
     const unsigned grid = (unsigned)lay.nb;
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
     if (ev) cudaEventRecord(ev[0], st);
     k_chunk_starts<<<1, CS_THREADS, 0, st>>>(offsets, nseries, n_total, L, cstart, status);
-    k_fold<B, true><<<grid, CTA, 0, st>>>(a, nodes, btot, phis, 0);
+    k_fold<B, true><<<grid, CTA, 0, st>>>(a, nodes, btot, phis, 0, 0, L, state, 1, 1);
     if (ev) cudaEventRecord(ev[1], st);
     scan_level<B>(btot, lay.nb, bpre, bsuf, lay, ws, 0, st);
     if (ev) cudaEventRecord(ev[2], st);
@@ -1255,7 +1293,6 @@ int matern_run(int b, int mode, const double* t, const double* y, int64_t n, int
         return matern_run_t<3>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev, missing, feed);
     }
 }
-int64_t matern_fold_blocks(int64_t n, int64_t L) { return ((n + L - 1) / L + CTA - 1) / CTA; }
 
 size_t matern_ws_bytes_batched(int b, int64_t nseries, int64_t n_total, int64_t L, int mode) {
     switch (b) {

@@ -45,3 +45,41 @@ def test_grad_host_errors():
     with pytest.raises(spingp.SpinGPError) as e:
         m.grad_host(tu, t, torch.ones(3, dtype=torch.float64))
     assert e.value.status == spingp.ENOTSORTED
+
+
+@pytest.mark.parametrize("L", [8, 9, 17, 64, 0])
+@pytest.mark.parametrize("n", [5003, 4 * 128 * 17])
+def test_grad_host_step_pieces(L, n):
+    """The host path eliminates each chunk in four launches over strided
+    pieces of its steps (the copy of the next piece overlapping).  Chunk
+    lengths that do not divide into four, fewer than four pieces (L = 9), a
+    last chunk shorter than a piece, and n a multiple of L all give the
+    device call's bits."""
+    rng = np.random.default_rng(L + n)
+    t = synth.exp_times(n, 0.02, rng)
+    y = synth.two_sinusoids(t, 0.5, 1.0, 0.1, rng)
+    theta = [0.4, 1.5, 0.08]
+    m = spingp.Model("matern52", chunk_len=L)
+    ll_d, g_d = m.grad(torch.tensor(t, device="cuda"), torch.tensor(y, device="cuda"),
+                       torch.tensor(theta, dtype=torch.float64, device="cuda"))
+    ll_h, g_h = m.grad_host(torch.from_numpy(t).pin_memory(), torch.from_numpy(y).pin_memory(),
+                            torch.tensor(theta, dtype=torch.float64))
+    assert ll_h.item() == ll_d.item()
+    assert torch.equal(g_h, g_d.cpu())
+
+
+def test_grad_host_missing_observations():
+    n = 20011
+    rng = np.random.default_rng(5)
+    t = synth.exp_times(n, 0.02, rng)
+    y = synth.two_sinusoids(t, 0.5, 1.0, 0.1, rng)
+    y[rng.random(n) < 0.2] = np.nan
+    theta = [0.4, 1.5, 0.08]
+    m = spingp.Model("matern32", chunk_len=13)
+    ll_d, g_d = m.grad(torch.tensor(t, device="cuda"), torch.tensor(y, device="cuda"),
+                       torch.tensor(theta, dtype=torch.float64, device="cuda"), missing=True)
+    ll_h, g_h = m.grad_host(torch.from_numpy(t).pin_memory(), torch.from_numpy(y).pin_memory(),
+                            torch.tensor(theta, dtype=torch.float64), missing=True)
+    assert np.isfinite(ll_d.item())
+    assert ll_h.item() == ll_d.item()
+    assert torch.equal(g_h, g_d.cpu())
