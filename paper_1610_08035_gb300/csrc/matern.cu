@@ -287,8 +287,11 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
                 for (int j = 0; j < B; ++j) el.C[i][j] = -sf * pj<B>(i, j);
         }
         double tp = (i0 > cr.s0 && i0 < i1) ? a.t[i0 - 1] : 0.0;
+        // t and y are loaded one step ahead
+        double tnx = (i0 < i1) ? a.t[i0] : 0.0, ynx = (i0 < i1) ? a.y[i0] : 0.0;
         for (int64_t i = i0; i < i1; ++i) {
-            const double ti = a.t[i], yi = a.y[i];
+            const double ti = tnx, yi = ynx;
+            if (i + 1 < i1) { tnx = a.t[i + 1]; ynx = a.y[i + 1]; }
             const bool obs = !(a.missing && is_nan_b(yi));
             if (!is_finite_b(ti) || (obs && !is_finite_b(yi))) bad |= ST_ENONFINITE;
             if (i > cr.s0) {
