@@ -119,7 +119,10 @@ int spingp_state_dim(const spingp_model* model);
 spingp_status spingp_set_chunk_len(spingp_model* model, int chunk_len);
 int spingp_get_chunk_len(const spingp_model* model, int64_t n);
 
-/* Workspace bytes needed for one series of n steps. */
+/* Workspace bytes needed for one series of n steps (0 for n < 1).
+ * The single-series calls below need n >= 1 and return SPINGP_EINVAL for
+ * n < 1 before any device work; an empty series is a batch entry (the
+ * batched calls give it log-likelihood 0 and a zero gradient). */
 size_t spingp_workspace_bytes(const spingp_model* model, int64_t n, spingp_ws_kind what);
 
 /* Log marginal likelihood (Eq. ml2), written to ll_out[0].  Computed through

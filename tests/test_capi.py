@@ -74,6 +74,11 @@ def test_entry_points_reject_null_arguments_without_launching(lib):
     assert lib.spingp_loglik(h, null, null, 10, null, null, null, 0, 0, null) == spingp.EINVAL
     assert lib.spingp_grad(h, null, null, 10, null, null, null, null, 0, 0, null) == spingp.EINVAL
     assert lib.spingp_posterior(h, null, null, 10, null, null, null, null, null, 0, 0, null) == spingp.EINVAL
+    # an empty series (n = 0) is rejected before any device work, whatever the pointers
+    fake = ctypes.c_void_p(256)
+    assert lib.spingp_loglik(h, fake, fake, 0, fake, fake, fake, 1 << 20, 0, null) == spingp.EINVAL
+    assert lib.spingp_grad(h, fake, fake, 0, fake, fake, fake, fake, 1 << 20, 0, null) == spingp.EINVAL
+    assert spingp.spingp_workspace_bytes(h, 0, spingp.WS_GRAD) == 0
     spingp.spingp_model_destroy(h)
 
 
