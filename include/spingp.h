@@ -231,10 +231,11 @@ spingp_status spingp_probe_exp_neg(const double* x, double* y, int64_t n, void* 
  * (1 double) and grad_out (P doubles) are host memory written on the stream
  * (valid after the stream synchronises; SPINGP_SYNC does that).  For the
  * single-Matern chain path t and y are copied on a copy stream the model
- * keeps, in four pieces of steps (piece p: the p-th quarter of every chunk,
- * as strided copies), and the in-chunk elimination runs as one launch per
- * piece as soon as that piece has arrived, so the transfer overlaps the
- * computation; structured models copy first, then run.  ws is device scratch of
+ * keeps, in four pieces of steps (piece p: a range of steps of every chunk,
+ * as strided copies; the widths double from 1/16 of a chunk), and the
+ * in-chunk elimination runs as one launch per piece as soon as that piece
+ * has arrived, so the transfer overlaps the computation; structured models
+ * copy first, then run.  ws is device scratch of
  * spingp_workspace_bytes_host(model, n) bytes (it also holds the device
  * copies of t, y and theta).  The model's copy stream and events are
  * created on the first call, on the current device; a model's host-buffer

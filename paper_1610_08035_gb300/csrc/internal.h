@@ -38,8 +38,8 @@ int matern_prepare();
 // ev: NULL, or 5 events recorded around the four stages
 // missing: 1 = a NaN observation is a missing one (predicted, not conditioned on)
 // Inputs from host memory (matern_run with a feed): t and y are copied on the
-// copy stream in FEED_PIECES pieces of steps -- piece p is steps
-// [p W, (p+1) W) of every chunk, W = ceil(L / FEED_PIECES) -- and the
+// copy stream in FEED_PIECES pieces of steps -- piece p is a range of step
+// columns of every chunk, the widths doubling from L/16 -- and the
 // elimination runs as one launch per piece on the main stream, each after its
 // piece's copy.  ev[0] orders the copies after earlier work on the main
 // stream, ev[1 + p] marks piece p's copy.

@@ -1131,18 +1131,23 @@ int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t 
         k_fold<B, false><<<grid, CTA, 0, st>>>(a, nodes, btot, phis, 0, 0, L, state, 1, 1);
     } else {
         // t and y arrive from host memory in pieces of steps: piece p holds
-        // steps [p W, (p+1) W) of every chunk (strided copies, chunk = row of
-        // L steps), and fold launch p eliminates exactly those steps once its
-        // copy is done.  The copy of piece p+1 overlaps the fold of piece p,
-        // and every launch keeps all SMs busy.  Piece 0 also carries the
-        // step before each chunk (its first transition needs that time).
-        const int64_t W = (L + feed->npieces - 1) / feed->npieces;
-        const int64_t np = (L + W - 1) / W;
+        // steps [bnd[p], bnd[p+1]) of every chunk (strided copies, chunk = row
+        // of L steps), and fold launch p eliminates exactly those steps once
+        // its copy is done.  The copy of piece p+1 overlaps the fold of piece
+        // p, and every launch keeps all SMs busy.  The widths double from
+        // L/16 (a step column copies about twice as fast as it folds), so the
+        // first copy, which nothing overlaps, is short.  Piece 0 also carries
+        // the step before each chunk (its first transition needs that time).
+        int64_t bnd[FEED_PIECES + 1];
+        int64_t np = 0;
+        bnd[0] = 0;
+        for (int64_t w = max((int64_t)1, (L + 15) / 16); bnd[np] < L && np < feed->npieces; w *= 2, ++np)
+            bnd[np + 1] = (np + 1 == feed->npieces) ? L : min(L, bnd[np] + w);
         const int64_t nfull = n / L, tail = n - nfull * L;
         if (cudaEventRecord(feed->ev[0], st) != cudaSuccess) return 1;
         if (cudaStreamWaitEvent(feed->copy, feed->ev[0], 0) != cudaSuccess) return 1;
         for (int64_t p = 0; p < np; ++p) {
-            const int64_t c0 = p * W, c1 = min(L, c0 + W);
+            const int64_t c0 = bnd[p], c1 = bnd[p + 1];
             const bool prev = (p == 0 && c1 < L);   // piece 0 also copies column L-1 of the row before
             for (int arr = 0; arr < 2; ++arr) {
                 double* dst = const_cast<double*>(arr ? y : t);

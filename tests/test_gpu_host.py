@@ -51,10 +51,10 @@ def test_grad_host_errors():
 @pytest.mark.parametrize("n", [5003, 4 * 128 * 17])
 def test_grad_host_step_pieces(L, n):
     """The host path eliminates each chunk in four launches over strided
-    pieces of its steps (the copy of the next piece overlapping).  Chunk
-    lengths that do not divide into four, fewer than four pieces (L = 9), a
-    last chunk shorter than a piece, and n a multiple of L all give the
-    device call's bits."""
+    pieces of its steps, of doubling widths (the copy of the next piece
+    overlapping).  Pieces of one step (L = 8, 9), widths that leave an odd
+    remainder, a last chunk shorter than the first pieces, and n a multiple
+    of L all give the device call's bits."""
     rng = np.random.default_rng(L + n)
     t = synth.exp_times(n, 0.02, rng)
     y = synth.two_sinusoids(t, 0.5, 1.0, 0.1, rng)
