@@ -7,9 +7,10 @@ N = 2^22 steps with dt ~ Exp(0.01), l = 0.5, s_f = 2, s_n = 0.05.
 
 Prints one JSON line (rank 0).  The device-timed value brackets each step's
 spingp_grad call with CUDA events on its stream, after an untimed 256 MiB
-write that flushes L2; with N GPUs (torchrun) every rank runs its own
-independent series (replicas, weak scaling), the time is the max over ranks
-and the value counts the steps of all ranks.  Extra keys: the roofline of the
+write that flushes L2; with N GPUs (torchrun) the one series is split across
+the ranks (one all-gather of the ranges' elements and one all-reduce per
+step, strong scaling), the time is the max over ranks and the value counts
+the series' steps once.  Extra keys: the roofline of the
 dominant kernel (live stage timing), the HBM roofline of the whole step, the
 end-to-end figure through the public API with host buffers, the "plain GPU
 form" comparator (the forward kernel run 2P+1 times for central differences),
@@ -60,6 +61,8 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary workloads (b = 16 sum, 4096-series batch, N = 2^26)")
+    ap.add_argument("--split", action="store_true",
+                    help="the split-series path even on one GPU (under torchrun; N > 1 always uses it)")
     ap.add_argument("--no-next", action="store_true",
                     help="skip the rows built beyond the hot path (prediction, literal mode, BTD solver, "
                          "EQ oracle rate, batched SCG)")
@@ -434,16 +437,18 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
+    if world > 1 or args.split:
         dist.init_process_group("nccl", device_id=dev)
+        main_split(args, world, rank, local, dev)
+        dist.destroy_process_group()
+        return
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    # each rank: its own independent series of the same shape (replicas)
-    s = synth.single(WORKLOAD, n=args.n or None, seed=1 + 1000 * rank)
+    s = synth.single(WORKLOAD, n=args.n or None, seed=1)
     n = len(s.t)
     T = torch.tensor(s.t, device=dev)
     Y = torch.tensor(s.y, device=dev)
@@ -528,7 +533,7 @@ def main():
            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "n": n, "b": 3, "model": "matern52", "chunk_len": L,
-                      "theta": [float(v) for v in s.theta], "parallelism": "replicas" if world > 1 else "single",
+                      "theta": [float(v) for v in s.theta], "parallelism": "single",
                       "l2": "flushed between timed iterations (256 MiB write, untimed)"},
            "roofline": roof, "hbm_roofline": hbm, "stages_ms_per_call": stage_ms,
            "gpu_launches": spingp.spingp_launch_count(model.h, n, spingp.WS_GRAD) * K,
@@ -616,6 +621,111 @@ def main():
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def main_split(args, world, rank, local, dev):
+    """N > 1 GPUs: the one series of the headline workload split across the
+    ranks (strong scaling).  Rank r holds the r-th contiguous range; a step is
+    the range's reduction to one element, one all-gather of the G elements,
+    the range's finish from them and one all-reduce of (ll, gradient)
+    (shard.grad_split_series).  The value counts the series' steps once."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1610_08035_gb300 import autotune, shard, spingp, synth
+
+    def barrier():
+        dist.barrier()
+        torch.cuda.synchronize()
+
+    s = synth.single(WORKLOAD, n=args.n or None, seed=1)     # the same series on every rank
+    n = len(s.t)
+    a, b = shard.range_split(n, world)[rank]
+    t_prev = None if rank == 0 else float(s.t[a - 1])
+    T = torch.tensor(s.t[a:b], device=dev)
+    Y = torch.tensor(s.y[a:b], device=dev)
+    TH = torch.tensor(s.theta, device=dev)
+    model = spingp.Model(s.spec)
+    if args.chunk >= 0:
+        model.set_chunk_len(args.chunk)
+    else:
+        autotune.tune(model, T, Y, TH, spingp.WS_GRAD)
+    L = model.chunk_len(b - a)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(max(args.warmup, 0)):
+        ll, g = shard.grad_split_series(model, T, Y, TH, t_prev)
+    fp64_tflops = spingp.spingp_probe_fp64(dev)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    barrier()
+    clocks = ClockSampler(local, enabled=not args.no_clocks)
+    time.sleep(0.3 if not args.no_clocks else 0.0)
+    for k in range(K):
+        flush.fill_(k & 0xFF)                        # 256 MiB write: L2 flushed, untimed
+        evs[k][0].record()
+        ll, g = shard.grad_split_series(model, T, Y, TH, t_prev, sync=False)
+        evs[k][1].record()
+    barrier()
+    clk = clocks.stop()
+    st = spingp.spingp_ws_status(model.workspace(b - a, spingp.WS_GRAD, dev))
+    if st != spingp.OK:
+        raise spingp.SpinGPError(st, "benchmark step")
+    tt = torch.tensor([float(np.sum([e0.elapsed_time(e1) for e0, e1 in evs]))], dtype=torch.float64, device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ms_per_step = float(tt.item()) / K
+    value = n / (ms_per_step * 1e-3)
+
+    # per GPU: the whole step's FP64 work over its range
+    flops = sum(FLOPS_PER_STEP.values()) * (b - a)
+    inst = sum(FP64_INST_PER_STEP.values()) * (b - a)
+    achieved = flops / (ms_per_step * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": "whole step per GPU (split series)", "achieved": achieved, "peak": fp64_tflops,
+            "unit": "TFLOP/s", "frac": achieved / fp64_tflops, "traffic": None,
+            "peak_kind": "measured FP64 FMA probe (spingp_probe_fp64)",
+            "pipe_frac": inst / (ms_per_step * 1e-3) / (fp64_tflops * 1e12 / 2.0)}
+    out = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+           "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": n, "b": 3, "model": "matern52", "chunk_len": L,
+                      "theta": [float(v) for v in s.theta], "parallelism": "series split over %d ranks" % world,
+                      "l2": "flushed between timed iterations (256 MiB write, untimed)"},
+           "roofline": roof,
+           "hbm_roofline": {"algorithmic_bytes_per_step": ALGO_BYTES_PER_STEP,
+                            "achieved_gbs": ALGO_BYTES_PER_STEP * n / (ms_per_step * 1e-3) / 1e9},
+           "gpu_launches": spingp.spingp_segment_launch_count(model.h, b - a) * K,
+           "clocks": clk}
+
+    # end to end: the range's inputs from pinned host memory every step, the
+    # result read back to the host
+    if not args.no_e2e:
+        th_h = torch.from_numpy(s.t[a:b].copy()).pin_memory()
+        yh_h = torch.from_numpy(s.y[a:b].copy()).pin_memory()
+        ll_h = torch.empty(1, dtype=torch.float64).pin_memory()
+        g_h = torch.empty(3, dtype=torch.float64).pin_memory()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record()
+        for _ in range(K):
+            T.copy_(th_h, non_blocking=True)
+            Y.copy_(yh_h, non_blocking=True)
+            ll, g = shard.grad_split_series(model, T, Y, TH, t_prev, sync=False)
+            ll_h.copy_(ll, non_blocking=True)
+            g_h.copy_(g, non_blocking=True)
+        e1.record()
+        barrier()
+        tt = torch.tensor([e0.elapsed_time(e1) / K], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+        out["e2e"] = {"value": n / (e2e_ms * 1e-3), "unit": "steps/s", "h2d_bytes_per_step": 16 * (b - a),
+                      "d2h_bytes_per_step": 32, "ms_per_step": e2e_ms,
+                      "api": "spingp_segment_reduce + spingp_segment_grad per rank, NCCL all-gather and all-reduce"}
+    # the other configurations: the batch sharded by series, the single series as replicas
+    if not args.no_extra and not args.n:
+        out["workloads"] = extra_workloads(args, dev, flush, world, rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 if __name__ == "__main__":

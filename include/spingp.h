@@ -225,6 +225,42 @@ spingp_status spingp_probe_fp64_tensor(void* scratch, size_t scratch_bytes, doub
  * SPINGP_EINVAL for n < 0 or a NULL array with n > 0. */
 spingp_status spingp_probe_exp_neg(const double* x, double* y, int64_t n, void* stream);
 
+/* ---- one series split across ranks (one process per GPU) -------------------
+ * The series is cut into G <= 32 contiguous ranges, range r on rank r; the
+ * odd-even reduction of Sec. 3.1 then spans the ranks with one exchange:
+ *   1. spingp_segment_reduce: each rank reduces its range to one element, the
+ *      Schur complement of K~ on the state before the range and the range's
+ *      last state, in conditional-covariance form (A, b, C, eta, J: b^2, b,
+ *      b(b+1)/2, b, b(b+1)/2 doubles in that order, upper triangles row by
+ *      row; spingp_segment_elem_size doubles), written to elem_out (device).
+ *      The range of rank 0 starts the series (first = 1); every other range
+ *      continues it (first = 0), and t_prev is the time of the last step of
+ *      the range before it (host value, finite, <= t[0]).
+ *   2. the caller all-gathers the G elements, in rank order, into one device
+ *      array elems of G x elem_size doubles (rank-major);
+ *   3. spingp_segment_grad: from elems, this range's share of the
+ *      log-likelihood and gradient (ll_out[0], grad_out[0 .. P-1], device);
+ *      the series' values are the sums of the shares over the ranks (one
+ *      all-reduce).
+ * Calls 1 and 3 of a rank take the same t, y, n, theta, t_prev, first, flags
+ * and the same workspace (spingp_workspace_bytes(model, n, SPINGP_WS_GRAD)),
+ * with no other call on that workspace in between: call 3 reuses what call 1
+ * left in it.  With G = 1 the result is spingp_grad's.  Single Matern models
+ * only (SPINGP_EUNSUPPORTED otherwise).  SPINGP_EINVAL for n < 1, G outside
+ * [1, 32], rank outside [0, G), first != (rank == 0), or a non-finite t_prev
+ * when first = 0. */
+int spingp_segment_elem_size(const spingp_model* model);
+/* GPU launches of one rank's spingp_segment_reduce plus spingp_segment_grad
+ * for a range of n steps; -1 when unsupported or n < 1. */
+int spingp_segment_launch_count(const spingp_model* model, int64_t n);
+spingp_status spingp_segment_reduce(const spingp_model* model, const double* t, const double* y, int64_t n,
+                                    const double* theta, double t_prev, int first, double* elem_out, void* ws,
+                                    size_t ws_bytes, unsigned flags, void* stream);
+spingp_status spingp_segment_grad(const spingp_model* model, const double* t, const double* y, int64_t n,
+                                  const double* theta, double t_prev, int first, const double* elems, int n_ranks,
+                                  int rank, double* ll_out, double* grad_out, void* ws, size_t ws_bytes,
+                                  unsigned flags, void* stream);
+
 /* Log-likelihood and gradient from HOST buffers (Sec. 2.4; the same result
  * as spingp_grad, bit for bit): t, y (n doubles each) and theta are host
  * memory -- pinned memory lets the copies run asynchronously -- and ll_out

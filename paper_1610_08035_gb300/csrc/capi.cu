@@ -1,5 +1,6 @@
 // capi.cu -- the extern "C" boundary declared in include/spingp.h.
 #include <cuda_runtime.h>
+#include <cmath>
 #include <math.h>
 #include <mutex>
 #include <stdint.h>
@@ -413,6 +414,54 @@ spingp_status spingp_probe_fp64_tensor(void* scratch, size_t bytes, double* tflo
 spingp_status spingp_probe_exp_neg(const double* x, double* y, int64_t n, void* stream) {
     if (n < 0 || (n > 0 && (!x || !y))) return SPINGP_EINVAL;
     return spg::probe_exp_neg(x, y, n, (cudaStream_t)stream) ? SPINGP_ECUDA : SPINGP_OK;
+}
+
+// ---------------------------------------------------------------- a series split across ranks
+
+int spingp_segment_elem_size(const spingp_model* m) { return (m && single_matern(m)) ? spg::matern_elem_size(m->b) : -1; }
+
+int spingp_segment_launch_count(const spingp_model* m, int64_t n) {
+    if (!m || !single_matern(m) || n < 1) return -1;
+    return spg::matern_segment_launch_count(m->b, n, chunk_len(m, n));
+}
+
+static spingp_status segment_call(const spingp_model* m, int phase, const double* t, const double* y, int64_t n,
+                                  const double* theta, double t_prev, int first, const double* elems, int n_ranks,
+                                  int rank, double* elem_out, double* ll_out, double* grad_out, void* ws,
+                                  size_t ws_bytes, unsigned flags, void* stream) {
+    if (!m || !t || !y || !theta || !ws || n < 1) return SPINGP_EINVAL;
+    if (!single_matern(m)) return SPINGP_EUNSUPPORTED;
+    if (((uintptr_t)ws & 255u) != 0) return SPINGP_EINVAL;
+    if (!first && !std::isfinite(t_prev)) return SPINGP_EINVAL;
+    const int64_t L = chunk_len(m, n);
+    if (ws_bytes < spg::matern_ws_bytes(m->b, n, L, spg::MODE_GRAD)) return SPINGP_EINVAL;
+    spingp_status st = prepare_device();
+    if (st != SPINGP_OK) return st;
+    const int miss = (flags & SPINGP_MISSING_NAN) ? 1 : 0;
+    if (spg::matern_segment(m->b, phase, t, y, n, L, theta, first ? 0.0 : t_prev, first ? 1 : 0, elems, n_ranks, rank,
+                            elem_out, ll_out, grad_out, ws, (cudaStream_t)stream, miss))
+        return SPINGP_ECUDA;
+    if (flags & SPINGP_SYNC) return spingp_ws_status(ws, stream);
+    return SPINGP_OK;
+}
+
+spingp_status spingp_segment_reduce(const spingp_model* m, const double* t, const double* y, int64_t n,
+                                    const double* theta, double t_prev, int first, double* elem_out, void* ws,
+                                    size_t ws_bytes, unsigned flags, void* stream) {
+    if (!elem_out) return SPINGP_EINVAL;
+    return segment_call(m, 0, t, y, n, theta, t_prev, first, NULL, 1, 0, elem_out, NULL, NULL, ws, ws_bytes, flags,
+                        stream);
+}
+
+spingp_status spingp_segment_grad(const spingp_model* m, const double* t, const double* y, int64_t n,
+                                  const double* theta, double t_prev, int first, const double* elems, int n_ranks,
+                                  int rank, double* ll_out, double* grad_out, void* ws, size_t ws_bytes,
+                                  unsigned flags, void* stream) {
+    if (!elems || !ll_out || !grad_out) return SPINGP_EINVAL;
+    if (n_ranks < 1 || n_ranks > spg::SEG_MAX_RANKS || rank < 0 || rank >= n_ranks) return SPINGP_EINVAL;
+    if ((first != 0) != (rank == 0)) return SPINGP_EINVAL;
+    return segment_call(m, 1, t, y, n, theta, t_prev, first, elems, n_ranks, rank, NULL, ll_out, grad_out, ws,
+                        ws_bytes, flags, stream);
 }
 
 // ---------------------------------------------------------------- host buffers in, host results out

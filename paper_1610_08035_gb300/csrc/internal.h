@@ -55,6 +55,14 @@ int matern_run(int b, int mode, const double* t, const double* y, int64_t n, int
                double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws, cudaStream_t st,
                cudaEvent_t* ev, int missing, const HostFeed* feed = nullptr);
 int matern_launch_count(int b, int64_t n, int64_t L, int mode);
+// a series split across ranks (phase 0: reduce this range to its element;
+// phase 1: from all G elements, this range's share of ll and gradient)
+static constexpr int SEG_MAX_RANKS = 32;
+int matern_segment(int b, int phase, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
+                   double t_prev, int first, const double* elems, int G, int rank, double* elem_out, double* ll_out,
+                   double* grad_out, void* ws, cudaStream_t st, int missing);
+int matern_elem_size(int b);
+int matern_segment_launch_count(int b, int64_t n, int64_t L);
 
 // batches of independent series: offsets (device, nseries + 1 entries), theta
 // per series (nseries x 3), per-series ll_out / grad_out

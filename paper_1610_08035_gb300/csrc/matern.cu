@@ -45,6 +45,11 @@ struct ChainArgs {
     int64_t nseries;
     int P;                    // theta entries per series
     int missing;              // 1: a NaN observation is missing (a test point)
+    // one series: the index of its first step (0), or -1 when the steps
+    // continue a series split across ranks; t_prev is then the time of the
+    // step before step 0
+    int64_t s0;
+    double t_prev;
 };
 
 // The steps of chunk c: [s, e), inside the series that starts at step s0 and
@@ -66,7 +71,7 @@ __device__ __forceinline__ ChunkRange chunk_range(const ChainArgs& a, int64_t c)
         r.valid = c < a.nchunks;
         r.s = c * a.L;
         r.e = min(a.n, r.s + a.L);
-        r.s0 = 0;
+        r.s0 = a.s0;
         r.series = 0;
         r.th = a.theta;
     } else {
@@ -286,7 +291,7 @@ __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict
 #pragma unroll
                 for (int j = 0; j < B; ++j) el.C[i][j] = -sf * pj<B>(i, j);
         }
-        double tp = (i0 > cr.s0 && i0 < i1) ? a.t[i0 - 1] : 0.0;
+        double tp = (i0 > cr.s0 && i0 < i1) ? (i0 > 0 ? a.t[i0 - 1] : a.t_prev) : 0.0;
         // t and y are loaded one step ahead
         double tnx = (i0 < i1) ? a.t[i0] : 0.0, ynx = (i0 < i1) ? a.y[i0] : 0.0;
         for (int64_t i = i0; i < i1; ++i) {
@@ -1032,11 +1037,12 @@ static int64_t mid_tiles(int64_t ne) { return (ne + SCAN_TS - 1) / SCAN_TS; }
 
 // Workspace: [status | tree nodes | block totals | block prefix | block suffix |
 //             grid scan levels | transition per step | block partials | stored steps |
-//             elimination state between pieces]
+//             elimination state between pieces | the ranks' elements of a split series]
+static constexpr int SEG_MAX = SEG_MAX_RANKS;   // ranks of a split series (one scan tile)
 template <int B>
 struct Layout {
     int64_t nc, nb;
-    size_t off_nodes, off_btot, off_bpre, off_bsuf, off_phis, off_part, off_store, off_state, total;
+    size_t off_nodes, off_btot, off_bpre, off_bsuf, off_phis, off_part, off_store, off_state, off_seg, total;
     int nlev;
     int64_t lev_n[8];
     size_t lev_tot[8], lev_pre[8], lev_suf[8];
@@ -1072,25 +1078,47 @@ struct Layout {
         off_store = o;
         if (mode != MODE_LOGLIK) o = align256(o + sizeof(double) * Stored<B>::N * (size_t)L * nc);
         off_state = o; o = align256(o + sizeof(double) * (NE + 1) * (size_t)nc);   // a piecewise elimination
+        off_seg = o; o = align256(o + sizeof(double) * (SEG_MAX * (NE + 2 * NM) + 2 * NM));   // split series
         total = o;
     }
 };
 
+// top_pre / top_suf: the state before the first element and the information
+// after the last (NM contiguous doubles each), or NULL for a whole series
+// (up = false: the level totals are already in the workspace, from scan_total)
 template <int B>
 static void scan_level(const double* E, int64_t ne, double* pre_out, double* suf_out, const Layout<B>& lay,
-                       char* ws, int lev, cudaStream_t st) {
+                       char* ws, int lev, cudaStream_t st, const double* top_pre = nullptr,
+                       const double* top_suf = nullptr, bool up = true) {
     const size_t smem = ScanSmem<B>::bytes;
     if (single_tile(ne)) {
-        k_scan_tile<B, true><<<1, SCAN_CTA, smem, st>>>(E, ne, nullptr, 1, nullptr, nullptr, pre_out, suf_out);
+        k_scan_tile<B, true><<<1, SCAN_CTA, smem, st>>>(E, ne, nullptr, 1, top_pre, top_suf, pre_out, suf_out);
         return;
     }
     const int64_t nt = lay.lev_n[lev];
     double* tot = (double*)(ws + lay.lev_tot[lev]);
     double* tpre = (double*)(ws + lay.lev_pre[lev]);
     double* tsuf = (double*)(ws + lay.lev_suf[lev]);
-    k_scan_tile<B, false><<<(unsigned)nt, SCAN_CTA, smem, st>>>(E, ne, tot, nt, nullptr, nullptr, nullptr, nullptr);
-    scan_level<B>(tot, nt, tpre, tsuf, lay, ws, lev + 1, st);
+    if (up)
+        k_scan_tile<B, false><<<(unsigned)nt, SCAN_CTA, smem, st>>>(E, ne, tot, nt, nullptr, nullptr, nullptr,
+                                                                    nullptr);
+    scan_level<B>(tot, nt, tpre, tsuf, lay, ws, lev + 1, st, top_pre, top_suf, up);
     k_scan_tile<B, true><<<(unsigned)nt, SCAN_CTA, smem, st>>>(E, ne, nullptr, nt, tpre, tsuf, pre_out, suf_out);
+}
+
+// the up-sweep only: the single element of all ne (NE contiguous doubles)
+template <int B>
+static void scan_total(const double* E, int64_t ne, double* total, const Layout<B>& lay, char* ws, int lev,
+                       cudaStream_t st) {
+    const size_t smem = ScanSmem<B>::bytes;
+    if (single_tile(ne)) {
+        k_scan_tile<B, false><<<1, SCAN_CTA, smem, st>>>(E, ne, total, 1, nullptr, nullptr, nullptr, nullptr);
+        return;
+    }
+    const int64_t nt = lay.lev_n[lev];
+    double* tot = (double*)(ws + lay.lev_tot[lev]);
+    k_scan_tile<B, false><<<(unsigned)nt, SCAN_CTA, smem, st>>>(E, ne, tot, nt, nullptr, nullptr, nullptr, nullptr);
+    scan_total<B>(tot, nt, total, lay, ws, lev + 1, st);
 }
 
 template <int B>
@@ -1266,6 +1294,74 @@ int matern_run_batched_t(int mode, const int64_t* offsets, int64_t nseries, int6
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
+// ------------------------------------------------------------------ a series split across ranks
+//
+// Rank r of G holds a contiguous range of the series.  Phase 0 reduces the
+// range to one element: the in-chunk elimination and the up-sweep, whose
+// total is the Schur complement of K~ on the state before the range and the
+// range's last state (for the first range, A = 0: it starts from the prior).
+// The ranks' elements are all-gathered.  Phase 1 runs the same odd-even
+// reduction over the G elements (one scan tile) for the state before this
+// range and the information after it, then this range's down-sweep, chunk
+// pass and final reduction: its share of the log-likelihood and gradient
+// (the final reduction is linear in the partial sums, so the shares add up).
+// Phase 1 reuses the workspace that phase 0 filled.
+
+// elements arrive rank-major ([G][NE]); the scan reads them field-major
+__global__ void __launch_bounds__(256) k_elems_to_soa(const double* __restrict__ in, double* __restrict__ out, int G,
+                                                      int ne) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < G * ne) {
+        const int k = i / ne, f = i % ne;
+        out[f * G + k] = in[i];
+    }
+}
+
+template <int B>
+int matern_segment_t(int phase, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
+                     double t_prev, int first, const double* elems, int G, int rank, double* elem_out,
+                     double* ll_out, double* grad_out, void* wsv, cudaStream_t st, int missing) {
+    constexpr int NE = Dims<B>::NE, NM = Dims<B>::NM;
+    if (G < 1 || G > SEG_MAX || rank < 0 || rank >= G) return 1;
+    Layout<B> lay(n, L, MODE_GRAD);
+    char* ws = (char*)wsv;
+    int* status = (int*)ws;
+    double* nodes = (double*)(ws + lay.off_nodes);
+    double* btot = (double*)(ws + lay.off_btot);
+    double* bpre = (double*)(ws + lay.off_bpre);
+    double* bsuf = (double*)(ws + lay.off_bsuf);
+    double* phis = (double*)(ws + lay.off_phis);
+    double* part = (double*)(ws + lay.off_part);
+    double* store = (double*)(ws + lay.off_store);
+    double* state = (double*)(ws + lay.off_state);
+    ChainArgs a{t, y, n, L, lay.nc, lay.nb, theta, status, nullptr, nullptr, 0, 3, missing, first ? 0 : -1, t_prev};
+    const unsigned grid = (unsigned)lay.nb;
+    if (phase == 0) {
+        if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
+        k_fold<B, false><<<grid, CTA, 0, st>>>(a, nodes, btot, phis, 0, 0, L, state, 1, 1);
+        scan_total<B>(btot, lay.nb, elem_out, lay, ws, 0, st);
+    } else {
+        double* esoa = (double*)(ws + lay.off_seg);
+        double* gpre = esoa + SEG_MAX * NE;
+        double* gsuf = gpre + SEG_MAX * NM;
+        double* tpre = gsuf + SEG_MAX * NM;
+        double* tsuf = tpre + NM;
+        k_elems_to_soa<<<(unsigned)((G * NE + 255) / 256), 256, 0, st>>>(elems, esoa, G, NE);
+        k_scan_tile<B, true><<<1, SCAN_CTA, ScanSmem<B>::bytes, st>>>(esoa, G, nullptr, 1, nullptr, nullptr, gpre,
+                                                                      gsuf);
+        // this rank's entry (field f at f * G + rank) as NM contiguous doubles
+        if (cudaMemcpy2DAsync(tpre, sizeof(double), gpre + rank, sizeof(double) * G, sizeof(double), NM,
+                              cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+            cudaMemcpy2DAsync(tsuf, sizeof(double), gsuf + rank, sizeof(double) * G, sizeof(double), NM,
+                              cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return 1;
+        scan_level<B>(btot, lay.nb, bpre, bsuf, lay, ws, 0, st, tpre, tsuf, false);
+        k_chunk<B, MODE_GRAD, false><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part, nullptr, nullptr);
+        k_finalize<B><<<1, 256, 0, st>>>(part, lay.nb, Acc<B>::N, theta, ll_out, grad_out);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
 template <int B>
 static void set_smem_attr() {
     cudaFuncSetAttribute(k_scan_tile<B, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1329,6 +1425,31 @@ int matern_run_batched(int b, int mode, const int64_t* offsets, int64_t nseries,
     default: return matern_run_batched_t<3>(mode, offsets, nseries, n_total, t, y, L, theta, ll_out, grad_out,
                                             mean_out, var_out, ws, st, ev, missing);
     }
+}
+
+int matern_segment(int b, int phase, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
+                   double t_prev, int first, const double* elems, int G, int rank, double* elem_out, double* ll_out,
+                   double* grad_out, void* ws, cudaStream_t st, int missing) {
+    switch (b) {
+    case 1: return matern_segment_t<1>(phase, t, y, n, L, theta, t_prev, first, elems, G, rank, elem_out, ll_out,
+                                       grad_out, ws, st, missing);
+    case 2: return matern_segment_t<2>(phase, t, y, n, L, theta, t_prev, first, elems, G, rank, elem_out, ll_out,
+                                       grad_out, ws, st, missing);
+    default: return matern_segment_t<3>(phase, t, y, n, L, theta, t_prev, first, elems, G, rank, elem_out, ll_out,
+                                        grad_out, ws, st, missing);
+    }
+}
+int matern_elem_size(int b) { return b == 1 ? Dims<1>::NE : b == 2 ? Dims<2>::NE : Dims<3>::NE; }
+
+// launches of both phases: fold + up-sweep; transpose, the ranks' scan tile,
+// the range's down-sweep, chunk pass, final reduction
+template <int B>
+static int segment_launches_t(int64_t n, int64_t L) {
+    Layout<B> lay(n, L, MODE_GRAD);
+    return 1 + (lay.nlev + 1) + 2 + (lay.nlev + 1) + 2;
+}
+int matern_segment_launch_count(int b, int64_t n, int64_t L) {
+    return b == 1 ? segment_launches_t<1>(n, L) : b == 2 ? segment_launches_t<2>(n, L) : segment_launches_t<3>(n, L);
 }
 
 int matern_launch_count(int b, int64_t n, int64_t L, int mode) {

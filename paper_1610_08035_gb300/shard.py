@@ -1,4 +1,4 @@
-"""Sharding batches of independent series across ranks (one process per GPU).
+"""Sharding across ranks (one process per GPU).
 
 A batch of series has no exchange step: each rank takes a subset of whole
 series, runs the batched entry points on its own GPU, and only the per-series
@@ -6,8 +6,16 @@ results are gathered at the end.  Series are assigned by the longest-
 processing-time rule (longest first, to the rank with the least work so far),
 which keeps every rank within one longest series of the mean load.
 
-Host-side logic only (no GPU work): the tests run it on CPU ranks with the
-gloo backend.
+One long series is cut into contiguous ranges, one per rank (Sec. 3.1's
+reduction spans the ranks): every rank reduces its range to one element,
+the elements are all-gathered, every rank finishes its range from them, and
+the shares of the log-likelihood and gradient are all-reduced -- one
+all-gather of G elements and one all-reduce of P + 1 numbers.  The element
+algebra runs in the library (spingp_segment_reduce / spingp_segment_grad);
+this module holds the range split and the exchange.
+
+The exchange is host-side logic: the tests run it on CPU ranks with the gloo
+backend, with a stand-in model.
 """
 import heapq
 
@@ -64,3 +72,33 @@ def gather_per_series(values, series, n_series, group=None):
         keep = i >= 0
         out[i[keep]] = v[keep]
     return out
+
+
+def range_split(n, world):
+    """Contiguous ranges [a_r, b_r) of n steps for `world` ranks, as equal as
+    whole steps allow (every rank gets at least one step: n >= world)."""
+    if n < world:
+        raise ValueError("fewer steps than ranks")
+    edges = (np.arange(world + 1, dtype=np.int64) * n) // world
+    return [(int(edges[r]), int(edges[r + 1])) for r in range(world)]
+
+
+def grad_split_series(model, t, y, theta, t_prev, group=None, missing=False, sync=True):
+    """Log-likelihood and gradient of one series split across the ranks of
+    `group`: this rank holds the contiguous range t, y (device tensors) of
+    the series, ranks in time order; t_prev is the time of the previous
+    rank's last step (None on rank 0).  Every rank returns the whole series'
+    (ll, grad).  `model` provides segment_reduce / segment_grad
+    (spingp.Model does).  sync=False leaves the device status word to be
+    read later (spingp_ws_status), with no host synchronisation."""
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    if (t_prev is None) != (rank == 0):
+        raise ValueError("t_prev must be None exactly on rank 0")
+    elem = model.segment_reduce(t, y, theta, t_prev=t_prev, missing=missing, sync=sync)
+    elems = [torch.empty_like(elem) for _ in range(world)]
+    dist.all_gather(elems, elem, group=group)
+    ll, g = model.segment_grad(t, y, theta, torch.stack(elems), rank, t_prev=t_prev, missing=missing, sync=sync)
+    out = torch.cat([ll.reshape(1), g.reshape(-1)])
+    dist.all_reduce(out, op=dist.ReduceOp.SUM, group=group)
+    return out[:1], out[1:]

@@ -28,7 +28,8 @@ EXPORTS = ("spingp_model_create", "spingp_model_destroy", "spingp_num_params", "
            "spingp_launch_count_batched", "spingp_profile_enable",
            "spingp_profile_read", "spingp_probe_fp64_bytes", "spingp_probe_fp64", "spingp_probe_fp64_tensor",
            "spingp_probe_exp_neg",
-           "spingp_workspace_bytes_host",
+           "spingp_workspace_bytes_host", "spingp_segment_elem_size", "spingp_segment_launch_count",
+           "spingp_segment_reduce", "spingp_segment_grad",
            "spingp_grad_host", "spingp_loglik_noalloc",
            "spingp_btd_workspace_bytes", "spingp_btd_solve", "spingp_btd_launch_count",
            "spingp_btd_diag_product_workspace_bytes", "spingp_btd_diag_product",
@@ -87,6 +88,11 @@ def load():
     lib.spingp_probe_fp64_bytes.restype = sz
     lib.spingp_probe_fp64.argtypes = [vp, sz, ctypes.POINTER(ctypes.c_double), vp]
     lib.spingp_probe_fp64_tensor.argtypes = [vp, sz, ctypes.POINTER(ctypes.c_double), vp]
+    lib.spingp_segment_elem_size.argtypes = [vp]
+    lib.spingp_segment_launch_count.argtypes = [vp, i64]
+    lib.spingp_segment_reduce.argtypes = [vp, dp, dp, i64, dp, ctypes.c_double, ctypes.c_int, dp, vp, sz, u32, vp]
+    lib.spingp_segment_grad.argtypes = [vp, dp, dp, i64, dp, ctypes.c_double, ctypes.c_int, dp, ctypes.c_int,
+                                        ctypes.c_int, dp, dp, vp, sz, u32, vp]
     lib.spingp_probe_exp_neg.argtypes = [dp, dp, i64, vp]
     lib.spingp_loglik_noalloc.argtypes = [vp, dp, dp, i64, dp, dp, u32, vp]
     lib.spingp_workspace_bytes_host.argtypes = [vp, i64]
@@ -285,6 +291,27 @@ def spingp_probe_exp_neg(x):
     return y
 
 
+def spingp_segment_elem_size(h):
+    return load().spingp_segment_elem_size(h)
+
+
+def spingp_segment_launch_count(h, n):
+    return load().spingp_segment_launch_count(h, int(n))
+
+
+def spingp_segment_reduce(h, t, y, n, theta, t_prev, first, elem_out, ws, ws_bytes, flags, stream=None):
+    return load().spingp_segment_reduce(h, _ptr(t), _ptr(y), int(n), _ptr(theta), float(t_prev), int(first),
+                                        _ptr(elem_out), _ptr(ws), int(ws_bytes), flags,
+                                        stream if stream is not None else _stream())
+
+
+def spingp_segment_grad(h, t, y, n, theta, t_prev, first, elems, n_ranks, rank, ll_out, grad_out, ws, ws_bytes,
+                        flags, stream=None):
+    return load().spingp_segment_grad(h, _ptr(t), _ptr(y), int(n), _ptr(theta), float(t_prev), int(first),
+                                      _ptr(elems), int(n_ranks), int(rank), _ptr(ll_out), _ptr(grad_out), _ptr(ws),
+                                      int(ws_bytes), flags, stream if stream is not None else _stream())
+
+
 def spingp_workspace_bytes_host(h, n):
     return load().spingp_workspace_bytes_host(h, int(n))
 
@@ -480,6 +507,34 @@ class Model:
             ll, g = out
         _check(spingp_grad_host(self.h, t, y, n, theta, ll, g, ws, ws.numel(), self._flags(sync, missing)),
                "spingp_grad_host")
+        return ll, g
+
+    def segment_reduce(self, t, y, theta, t_prev=None, ws=None, sync=True, missing=False):
+        """Phase 1 of a series split across ranks: this range's element
+        (device, spingp_segment_elem_size doubles).  t_prev: the time of the
+        previous range's last step, None for the range that starts the
+        series.  ws: this rank's workspace (kept for segment_grad)."""
+        n = self._args(t, y, theta)
+        ws = ws if ws is not None else self.workspace(n, WS_GRAD, t.device)
+        elem = torch.empty(spingp_segment_elem_size(self.h), dtype=torch.float64, device=t.device)
+        first = t_prev is None
+        _check(spingp_segment_reduce(self.h, t, y, n, theta, 0.0 if first else t_prev, first, elem, ws, ws.numel(),
+                                     self._flags(sync, missing)), "spingp_segment_reduce")
+        return elem
+
+    def segment_grad(self, t, y, theta, elems, rank, t_prev=None, ws=None, sync=True, missing=False):
+        """Phase 2: this range's share of (ll, grad) from all ranks' elements
+        (device, n_ranks x elem_size, rank order); the same arguments and
+        workspace as segment_reduce."""
+        n = self._args(t, y, theta)
+        ws = ws if ws is not None else self.workspace(n, WS_GRAD, t.device)
+        _dev_f64(elems, "elems")
+        elems = elems.contiguous()
+        ll = torch.empty(1, dtype=torch.float64, device=t.device)
+        g = torch.empty(self.num_params, dtype=torch.float64, device=t.device)
+        first = t_prev is None
+        _check(spingp_segment_grad(self.h, t, y, n, theta, 0.0 if first else t_prev, first, elems, elems.shape[0],
+                                   rank, ll, g, ws, ws.numel(), self._flags(sync, missing)), "spingp_segment_grad")
         return ll, g
 
     def posterior(self, t, y, theta, sync=True, with_loglik=True, missing=False):

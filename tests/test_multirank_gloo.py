@@ -83,3 +83,91 @@ def test_two_ranks_reproduce_the_unsharded_batch(tmp_path):
     for i in range(len(thetas)):
         ll, g = seq.grad("matern52", thetas[i], s.t[offsets[i]:offsets[i + 1]], s.y[offsets[i]:offsets[i + 1]])
         assert np.array_equal(full[i], np.concatenate([[ll], g]))
+
+
+# ---- one series split across ranks (the exchange of shard.grad_split_series)
+
+class _OracleRange:
+    """A stand-in for spingp.Model's two phases on CPU ranks.  Its 'element'
+    carries the range's raw data (count, t, y, padded to a fixed size), so after
+    the all-gather each rank sees the series up to its range; its share is then
+    the prediction-error terms of its own steps, ll(y_<=b) - ll(y_<a), and the
+    same difference of gradients (oracle).  The shares telescope to the whole
+    series' values only if the exchange delivers every rank's element in rank
+    order and the all-reduce sums every share once."""
+    cap = 600
+
+    def __init__(self, spec):
+        self.spec = spec
+
+    def segment_reduce(self, t, y, theta, t_prev=None, missing=False, sync=True):
+        e = torch.zeros(1 + 2 * self.cap, dtype=torch.float64)
+        n = t.numel()
+        e[0] = n
+        e[1:1 + n] = t
+        e[1 + self.cap:1 + self.cap + n] = y
+        if t_prev is not None:
+            assert t_prev <= float(t[0])
+        return e
+
+    def segment_grad(self, t, y, theta, elems, rank, t_prev=None, missing=False, sync=True):
+        from oracle import seq
+        ts, ys = [], []
+        for e in elems[:rank + 1]:
+            n = int(e[0])
+            ts.append(e[1:1 + n].numpy())
+            ys.append(e[1 + self.cap:1 + self.cap + n].numpy())
+        assert np.array_equal(ts[-1], t.numpy()) and np.array_equal(ys[-1], y.numpy())
+        tall, yall = np.concatenate(ts), np.concatenate(ys)
+        a = len(tall) - t.numel()
+        th = theta.numpy()
+        ll1, g1 = seq.grad(self.spec, th, tall, yall)
+        ll0, g0 = seq.grad(self.spec, th, tall[:a], yall[:a]) if a > 0 else (0.0, np.zeros_like(g1))
+        return (torch.tensor([ll1 - ll0], dtype=torch.float64),
+                torch.tensor(g1 - g0, dtype=torch.float64))
+
+
+def _split_worker(rank, world, port, out_path):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        rng = np.random.default_rng(23)
+        n = 1000
+        t = synth.exp_times(n, 0.05, rng)
+        y = synth.two_sinusoids(t, 0.7, 1.0, 0.1, rng)
+        theta = torch.tensor([0.7, 1.2, 0.1], dtype=torch.float64)
+        a, b = shard.range_split(n, world)[rank]
+        t_prev = None if rank == 0 else float(t[a - 1])
+        ll, g = shard.grad_split_series(_OracleRange("matern32"), torch.from_numpy(t[a:b].copy()),
+                                        torch.from_numpy(y[a:b].copy()), theta, t_prev)
+        np.save(out_path + ".%d.npy" % rank, np.concatenate([ll.numpy(), g.numpy()]))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_split_series_exchange_on_gloo(tmp_path, world):
+    from oracle import seq
+    out = str(tmp_path / "split")
+    mp.spawn(_split_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+    rng = np.random.default_rng(23)
+    t = synth.exp_times(1000, 0.05, rng)
+    y = synth.two_sinusoids(t, 0.7, 1.0, 0.1, rng)
+    llo, go = seq.grad("matern32", [0.7, 1.2, 0.1], t, y)
+    for r in range(world):
+        got = np.load(out + ".%d.npy" % r)
+        assert abs(got[0] - llo) <= 1e-10 * abs(llo)
+        assert np.max(np.abs(got[1:] - go) / np.abs(go)) <= 1e-9
+
+
+def test_range_split():
+    for n, world in ((10, 3), (1000, 7), (5, 5), (2 ** 22, 8)):
+        rs = shard.range_split(n, world)
+        assert rs[0][0] == 0 and rs[-1][1] == n
+        assert all(rs[i][1] == rs[i + 1][0] for i in range(world - 1))
+        sizes = [b - a for a, b in rs]
+        assert min(sizes) >= 1 and max(sizes) - min(sizes) <= 1
+    with pytest.raises(ValueError):
+        shard.range_split(3, 4)
