@@ -249,13 +249,13 @@ __device__ __forceinline__ void tree_down_coop(double* spre, double* ssuf, const
 // j0 = 0, j1 >= L does the whole chunk; the pieces give the same bits.
 template <int B, bool BATCH>
 __global__ void __launch_bounds__(CTA, 3) k_fold(ChainArgs a, double* __restrict__ nodes, double* __restrict__ btot,
-                                              double* __restrict__ phis, int64_t blk0, int64_t j0, int64_t j1,
+                                              double* __restrict__ phis, int64_t j0, int64_t j1,
                                               double* __restrict__ state, int first, int last) {
     constexpr int NE = Dims<B>::NE;
     __shared__ double sm[CTA * NE];
     __shared__ double etab[EXPTAB];
     const int tid = threadIdx.x;
-    const int64_t blk = blk0 + blockIdx.x;   // launches may cover a range of blocks
+    const int64_t blk = blockIdx.x;
     exp_neg_table(etab, tid, CTA);
     __syncthreads();
     const int64_t c = blk * CTA + tid;
@@ -407,7 +407,6 @@ struct ScanSmem {
     static constexpr size_t bytes = sizeof(double) * (size_t)(2 * SCAN_TS) * (NE + 2 * NM);
 };
 
-__device__ __forceinline__ int node_off(int level) { return 2 * SCAN_TS - ((2 * SCAN_TS) >> level); }
 
 template <int B>
 __device__ __forceinline__ double elem_identity_field(int f) {
@@ -441,29 +440,34 @@ __global__ void __launch_bounds__(SCAN_CTA, 1) k_scan_tile(const double* __restr
     const CPos<B> p;
     const int64_t tile = blockIdx.x;
     const int64_t k0 = tile * (int64_t)TS;
+    // a launch of one tile (the top of the reduction) needs only
+    // ceil(log2 ne) levels: the tile shrinks to ts = 2^lv elements
+    const int lv = (gridDim.x == 1) ? ((ne <= 1) ? 0 : 32 - __clz((int)ne - 1)) : SCAN_LV;
+    const int ts = 1 << lv;
+    auto noff = [ts](int level) { return 2 * ts - ((2 * ts) >> level); };
 
-    for (int idx = tid; idx < TS * NE; idx += SCAN_CTA) {
-        const int f = idx / TS, j = idx % TS;
+    for (int idx = tid; idx < ts * NE; idx += SCAN_CTA) {
+        const int f = idx / ts, j = idx % ts;
         nodes[j * NE + f] = (k0 + j < ne) ? E[(int64_t)f * ne + k0 + j] : elem_identity_field<B>(f);
     }
     __syncthreads();
 #pragma unroll 1
-    for (int l = 1; l <= SCAN_LV; ++l) {
-        const int cnt = TS >> l;
+    for (int l = 1; l <= lv; ++l) {
+        const int cnt = ts >> l;
         if (wg0 < cnt) {   // warp-uniform
             const int j = min(g, cnt - 1);
             CElem x, y, r;
-            celem_load<B>(nodes + (node_off(l - 1) + 2 * j) * NE, 1, 0, x, p);
-            celem_load<B>(nodes + (node_off(l - 1) + 2 * j + 1) * NE, 1, 0, y, p);
+            celem_load<B>(nodes + (noff(l - 1) + 2 * j) * NE, 1, 0, x, p);
+            celem_load<B>(nodes + (noff(l - 1) + 2 * j + 1) * NE, 1, 0, y, p);
             ccombine<B>(x, y, r, p);
-            if (g < cnt) celem_store<B>(nodes + (node_off(l) + g) * NE, 1, 0, r, p);
+            if (g < cnt) celem_store<B>(nodes + (noff(l) + g) * NE, 1, 0, r, p);
         }
         __syncthreads();
     }
     if constexpr (!DOWN) {
         if (g == 0) {
             CElem r;
-            celem_load<B>(nodes + node_off(SCAN_LV) * NE, 1, 0, r, p);
+            celem_load<B>(nodes + noff(lv) * NE, 1, 0, r, p);
             celem_store<B>(totals, ntiles, tile, r, p);
         }
         return;
@@ -472,10 +476,10 @@ __global__ void __launch_bounds__(SCAN_CTA, 1) k_scan_tile(const double* __restr
             CVS x;
             x.v = 0.0; x.S = 0.0;
             if (pre_in) cvs_load<B>(pre_in, ntiles, tile, x, p);
-            cvs_store<B>(preN + node_off(SCAN_LV) * NM, 1, 0, x, p);
+            cvs_store<B>(preN + noff(lv) * NM, 1, 0, x, p);
             x.v = 0.0; x.S = 0.0;
             if (suf_in) cvs_load<B>(suf_in, ntiles, tile, x, p);
-            cvs_store<B>(sufN + node_off(SCAN_LV) * NM, 1, 0, x, p);
+            cvs_store<B>(sufN + noff(lv) * NM, 1, 0, x, p);
         }
         __syncthreads();
         // level l -> its children at level l-1: odd child 2j+1 gets the
@@ -486,8 +490,8 @@ __global__ void __launch_bounds__(SCAN_CTA, 1) k_scan_tile(const double* __restr
         const int gi = odd ? g : g - NG / 2;
         const int wgi0 = odd ? wg0 : wg0 - NG / 2;
 #pragma unroll 1
-        for (int l = SCAN_LV; l >= 1; --l) {
-            const int half = (TS >> (l - 1)) / 2;
+        for (int l = lv; l >= 1; --l) {
+            const int half = (ts >> (l - 1)) / 2;
 #pragma unroll 1
             for (int base = 0; base < half; base += NG / 2) {
                 if (base + wgi0 < half) {   // warp-uniform
@@ -495,29 +499,29 @@ __global__ void __launch_bounds__(SCAN_CTA, 1) k_scan_tile(const double* __restr
                     const bool mine = base + gi < half;
                     CVS pre, suf, o;
                     CElem e;
-                    cvs_load<B>(preN + (node_off(l) + j) * NM, 1, 0, pre, p);
-                    cvs_load<B>(sufN + (node_off(l) + j) * NM, 1, 0, suf, p);
+                    cvs_load<B>(preN + (noff(l) + j) * NM, 1, 0, pre, p);
+                    cvs_load<B>(sufN + (noff(l) + j) * NM, 1, 0, suf, p);
                     if (odd) {
-                        celem_load<B>(nodes + (node_off(l - 1) + 2 * j) * NE, 1, 0, e, p);
+                        celem_load<B>(nodes + (noff(l - 1) + 2 * j) * NE, 1, 0, e, p);
                         cstate_through<B>(pre, e, o, p);
                         if (mine) {
-                            cvs_store<B>(preN + (node_off(l - 1) + 2 * j + 1) * NM, 1, 0, o, p);
-                            cvs_store<B>(sufN + (node_off(l - 1) + 2 * j + 1) * NM, 1, 0, suf, p);
+                            cvs_store<B>(preN + (noff(l - 1) + 2 * j + 1) * NM, 1, 0, o, p);
+                            cvs_store<B>(sufN + (noff(l - 1) + 2 * j + 1) * NM, 1, 0, suf, p);
                         }
                     } else {
-                        celem_load<B>(nodes + (node_off(l - 1) + 2 * j + 1) * NE, 1, 0, e, p);
+                        celem_load<B>(nodes + (noff(l - 1) + 2 * j + 1) * NE, 1, 0, e, p);
                         cinfo_through<B>(e, suf, o, p);
                         if (mine) {
-                            cvs_store<B>(preN + (node_off(l - 1) + 2 * j) * NM, 1, 0, pre, p);
-                            cvs_store<B>(sufN + (node_off(l - 1) + 2 * j) * NM, 1, 0, o, p);
+                            cvs_store<B>(preN + (noff(l - 1) + 2 * j) * NM, 1, 0, pre, p);
+                            cvs_store<B>(sufN + (noff(l - 1) + 2 * j) * NM, 1, 0, o, p);
                         }
                     }
                 }
             }
             __syncthreads();
         }
-        for (int idx = tid; idx < TS * NM; idx += SCAN_CTA) {
-            const int f = idx / TS, j = idx % TS;
+        for (int idx = tid; idx < ts * NM; idx += SCAN_CTA) {
+            const int f = idx / ts, j = idx % ts;
             if (k0 + j < ne) {
                 pre_out[(int64_t)f * ne + k0 + j] = preN[j * NM + f];
                 suf_out[(int64_t)f * ne + k0 + j] = sufN[j * NM + f];
@@ -1156,7 +1160,7 @@ int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t 
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
     if (ev) cudaEventRecord(ev[0], st);
     if (!feed) {
-        k_fold<B, false><<<grid, CTA, 0, st>>>(a, nodes, btot, phis, 0, 0, L, state, 1, 1);
+        k_fold<B, false><<<grid, CTA, 0, st>>>(a, nodes, btot, phis, 0, L, state, 1, 1);
     } else {
         // t and y arrive from host memory in pieces of steps: piece p holds
         // steps [bnd[p], bnd[p+1]) of every chunk (strided copies, chunk = row
@@ -1204,7 +1208,7 @@ int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t 
             }
             if (cudaEventRecord(feed->ev[1 + p], feed->copy) != cudaSuccess) return 1;
             if (cudaStreamWaitEvent(st, feed->ev[1 + p], 0) != cudaSuccess) return 1;
-            k_fold<B, false><<<grid, CTA, 0, st>>>(a, nodes, btot, phis, 0, c0, c1, state, p == 0 ? 1 : 0,
+            k_fold<B, false><<<grid, CTA, 0, st>>>(a, nodes, btot, phis, c0, c1, state, p == 0 ? 1 : 0,
                                                    p == np - 1 ? 1 : 0);
         }
     }
@@ -1267,7 +1271,7 @@ int matern_run_batched_t(int mode, const int64_t* offsets, int64_t nseries, int6
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
     if (ev) cudaEventRecord(ev[0], st);
     k_chunk_starts<<<1, CS_THREADS, 0, st>>>(offsets, nseries, n_total, L, cstart, status);
-    k_fold<B, true><<<grid, CTA, 0, st>>>(a, nodes, btot, phis, 0, 0, L, state, 1, 1);
+    k_fold<B, true><<<grid, CTA, 0, st>>>(a, nodes, btot, phis, 0, L, state, 1, 1);
     if (ev) cudaEventRecord(ev[1], st);
     scan_level<B>(btot, lay.nb, bpre, bsuf, lay, ws, 0, st);
     if (ev) cudaEventRecord(ev[2], st);
@@ -1338,7 +1342,7 @@ int matern_segment_t(int phase, const double* t, const double* y, int64_t n, int
     const unsigned grid = (unsigned)lay.nb;
     if (phase == 0) {
         if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
-        k_fold<B, false><<<grid, CTA, 0, st>>>(a, nodes, btot, phis, 0, 0, L, state, 1, 1);
+        k_fold<B, false><<<grid, CTA, 0, st>>>(a, nodes, btot, phis, 0, L, state, 1, 1);
         scan_total<B>(btot, lay.nb, elem_out, lay, ws, 0, st);
     } else {
         double* esoa = (double*)(ws + lay.off_seg);
