@@ -1,9 +1,14 @@
-"""Randomised parity of the chain path: seeded random series lengths, chunk
-lengths, hyperparameters, time spacings (with ties and long gaps) and missing
-observations, through every entry point that shares the chain kernels --
-gradient, log-likelihood, posterior, the host-buffer call and one series split
-in ranges -- against the oracle at the parity bars of test_gpu_parity, and
-the host-buffer and split results against the device call."""
+"""Randomised parity, seeded:
+- the chain path: random series lengths, chunk lengths, hyperparameters,
+  time spacings (with ties and long gaps) and missing observations, through
+  every entry point that shares the chain kernels -- gradient,
+  log-likelihood, posterior, the host-buffer call and one series split in
+  ranges -- against the oracle at the parity bars of test_gpu_parity, and the
+  host-buffer result against the device call bit for bit;
+- the group path: random sums of Matern-3/2, periodic, quasi-periodic and
+  order-4 EQ components (b <= 16) against the oracle;
+- the general BTD solver: random SPD systems of every size against the
+  oracle's block LDL^T."""
 import numpy as np
 import pytest
 
@@ -81,3 +86,82 @@ def test_fuzz_chain_against_oracle(k):
         gs = gs + gr.cpu().numpy()
     assert abs(ls - llo) <= 1e-9 * abs(llo)
     assert np.all(np.abs(gs - go) <= 1e-8 * gscale)
+
+
+# ---- the group path (structured b <= 16) and the general BTD solver
+
+def _group_case(k):
+    rng = np.random.default_rng(2000 + k)
+    comps, theta = [], []
+    b = 0
+    for _ in range(int(rng.integers(1, 4))):
+        kind = int(rng.integers(0, 4))
+        if kind == 0 and b + 2 <= 16:
+            comps.append("matern32"); theta += [float(np.exp(rng.uniform(-1.5, 1.0))), float(np.exp(rng.uniform(-1, 1)))]
+            b += 2
+        elif kind == 1 and b + 4 <= 16:
+            J = int(rng.integers(1, 4))
+            if b + 2 * (J + 1) > 16:
+                continue
+            comps.append(("periodic", J))
+            theta += [float(np.exp(rng.uniform(-1, 1))), float(np.exp(rng.uniform(-0.5, 0.7))),
+                      float(np.exp(rng.uniform(-0.5, 1.0)))]
+            b += 2 * (J + 1)
+        elif kind == 2:
+            J = int(rng.integers(1, 4))
+            if b + 2 * (J + 1) > 16:
+                continue
+            comps.append(("quasiperiodic", J, "matern12"))
+            theta += [float(np.exp(rng.uniform(-1, 1))), float(np.exp(rng.uniform(-0.5, 0.7))),
+                      float(np.exp(rng.uniform(-0.5, 1.0))), float(np.exp(rng.uniform(0.0, 2.0)))]
+            b += 2 * (J + 1)
+        elif kind == 3 and b + 4 <= 16 and not any(isinstance(c, tuple) and c[0] == "eq" for c in comps):
+            comps.append(("eq", 4)); theta += [float(np.exp(rng.uniform(-1, 1))), float(np.exp(rng.uniform(-1, 1)))]
+            b += 4
+    if not comps:
+        comps, theta = ["matern32"], [1.0, 1.0]
+    theta.append(float(np.exp(rng.uniform(np.log(0.01), np.log(0.3)))))
+    n = int(np.exp(rng.uniform(0.0, np.log(6000))))
+    d = rng.exponential(float(np.exp(rng.uniform(np.log(0.005), np.log(0.1)))), n)
+    d[0] = 0.0
+    d[rng.random(n) < 0.02] = 0.0
+    t = np.cumsum(d)
+    y = synth.two_sinusoids(t, 0.8, 1.0, 0.1, rng)
+    L = int(rng.choice([0, 8, 33, 200]))
+    return comps, theta, t, y, L
+
+
+@pytest.mark.parametrize("k", range(24))
+def test_fuzz_group_against_oracle(k):
+    spec, theta, t, y, L = _group_case(k)
+    m = spingp.Model(spec, chunk_len=L)
+    assert m.num_params == len(theta)
+    T, Y, TH = _t(t), _t(y), _t(theta)
+    ll, g = m.grad(T, Y, TH)
+    mean, var, ll_p = m.posterior(T, Y, TH)
+    llo, go, mo, vo, g1 = seq.grad(spec, theta, t, y, posterior=True, l1=True)
+    assert abs(ll.item() - llo) <= 1e-9 * abs(llo), (spec, ll.item(), llo)
+    assert abs(ll_p.item() - llo) <= 1e-9 * abs(llo)
+    gscale = np.maximum(np.maximum(np.abs(go), g1), 1e-12)
+    assert np.all(np.abs(g.cpu().numpy() - go) <= 1e-8 * gscale), (spec, g.cpu().numpy(), go)
+    assert np.all(np.abs(mean.cpu().numpy() - mo) <= 1e-8 * np.maximum(np.abs(mo), np.sqrt(vo)))
+    assert np.all(np.abs(var.cpu().numpy() - vo) <= 1e-8 * vo)
+
+
+@pytest.mark.parametrize("k", range(24))
+def test_fuzz_btd_solver(k):
+    """Random SPD block-tridiagonal systems: every level size from 1 up, on
+    both the one-thread and the lane-group levels."""
+    from oracle import btd
+    rng = np.random.default_rng(3000 + k)
+    b = int(rng.integers(1, 4))
+    n = int(np.exp(rng.uniform(0.0, np.log(20000))))
+    D, O, r = synth.random_spd_btd(n, b, seed=4000 + k)
+    ld, x, Sd, So = spingp.btd_solve(_t(D), _t(O), _t(r))
+    lo, xo, Sdo, Soo = btd.thomas(D, O, r)
+    assert abs(ld.item() - lo) <= 1e-11 * abs(lo)
+    xs = np.max(np.abs(xo))
+    assert np.max(np.abs(x.cpu().numpy() - xo)) <= 1e-10 * xs
+    assert np.max(np.abs(Sd.cpu().numpy() - Sdo)) <= 1e-10 * np.max(np.abs(Sdo))
+    if n > 1:
+        assert np.max(np.abs(So.cpu().numpy() - Soo)) <= 1e-10 * np.max(np.abs(Sdo))
