@@ -283,9 +283,9 @@ def extra_workloads(args, dev, flush, world, rank=0):
 # instructions; instructions = everything the FP64 pipe executed.  Units:
 # steps, or nodes for the BTD solver; the batched SCG's gradient evaluations
 # use the chain kernels' counts above.
-NEXT_FLOPS_PER_UNIT = {"prediction_n4m": 334.7, "literal_n1m": 2916.0, "btd_solve_n1m": 901.8,
+NEXT_FLOPS_PER_UNIT = {"prediction_n4m": 334.7, "literal_n1m": 2481.9, "btd_solve_n1m": 901.8,
                        "eq_b12_n1m": 12896.7, "scg_batch_4096": 171.5 + 231.2}
-NEXT_FP64_INST_PER_UNIT = {"prediction_n4m": 232.4, "literal_n1m": 1880.7, "btd_solve_n1m": 563.2,
+NEXT_FP64_INST_PER_UNIT = {"prediction_n4m": 232.4, "literal_n1m": 1673.5, "btd_solve_n1m": 563.2,
                            "eq_b12_n1m": 8887.7, "scg_batch_4096": 107.1 + 141.6}
 
 

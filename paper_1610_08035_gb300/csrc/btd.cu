@@ -109,20 +109,45 @@ __device__ __forceinline__ bool trans_scaled(double x, double sf, double (&Ph)[B
 // r_i = H^T y_i / s_n; and -log det of Q_{i-1} (Pinf at i = 0) toward log det Kinv.
 // Paper coordinates: z = Dl z~ with Dl = diag(1, lam, ..), so a precision
 // block transforms as Dl^-1 (.) Dl^-1, entry (r, q) scaled by lam^-(r+q).
+// Each transition is computed once: thread j derives the one out of its step
+// and hands Q^-1 and log det Q to thread j+1 through shared memory (the first
+// thread of a block derives its incoming one itself).
+static constexpr int ASM_CTA = 128;
+
 template <int B>
-__global__ void __launch_bounds__(128) k_assemble(const double* __restrict__ t, const double* __restrict__ y,
-                                                  int64_t n, const double* __restrict__ theta,
-                                                  double* __restrict__ Dout, double* __restrict__ Oout,
-                                                  double* __restrict__ rout, double* __restrict__ ldpart,
-                                                  int* status) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+__global__ void __launch_bounds__(ASM_CTA) k_assemble(const double* __restrict__ t, const double* __restrict__ y,
+                                                      int64_t n, const double* __restrict__ theta,
+                                                      double* __restrict__ Dout, double* __restrict__ Oout,
+                                                      double* __restrict__ rout, double* __restrict__ ldpart,
+                                                      int* status) {
+    constexpr int BB = B * B;
+    __shared__ double s_qi[ASM_CTA * BB];
+    __shared__ double s_ld[ASM_CTA];
+    const int j = threadIdx.x;
+    const int64_t i = blockIdx.x * (int64_t)ASM_CTA + j;
+    const bool valid = i < n;
     const double ell = theta[0], sf = theta[1], s2 = theta[2];
     const double lam = sqrt(2.0 * B - 1.0) / ell;
-    int bad = (ell > 0.0 && sf > 0.0 && s2 > 0.0 && isfinite(ell) && isfinite(sf) && isfinite(s2)) ? 0 : ST_EINVAL;
+    int bad = 0;
+    // the transition out of step i (i -> i+1)
+    const bool hasn = valid && i + 1 < n;
+    double Ph[B][B], Qi[B][B], ldq = 0.0;
+    if (hasn) {
+        const double dt = t[i + 1] - t[i];
+        if (!(dt > 0.0)) bad |= (dt < 0.0) ? ST_ENOTSORTED : ST_ENUMERIC;   // Q = 0 at a tie: no precision
+        if (!trans_scaled<B>(lam * dt, sf, Ph, Qi, ldq)) bad |= ST_ENUMERIC;
+#pragma unroll
+        for (int r = 0; r < B; ++r)
+#pragma unroll
+            for (int q = 0; q < B; ++q) s_qi[j * BB + r * B + q] = Qi[r][q];
+        s_ld[j] = ldq;
+    }
+    __syncthreads();
+    if (!valid) return;
+    if (!(ell > 0.0 && sf > 0.0 && s2 > 0.0 && isfinite(ell) && isfinite(sf) && isfinite(s2))) bad |= ST_EINVAL;
     if (!isfinite(t[i]) || !isfinite(y[i])) bad |= ST_ENONFINITE;
-    double Dt[B][B], ldq_prev;
     // Q_{i-1}^-1 (or Pinf^-1) in scaled coordinates
+    double Dt[B][B], ldq_prev;
     if (i == 0) {
         double P[B][B];
 #pragma unroll
@@ -130,17 +155,20 @@ __global__ void __launch_bounds__(128) k_assemble(const double* __restrict__ t, 
 #pragma unroll
             for (int q = 0; q < B; ++q) P[r][q] = sf * p1<B>(r, q);
         if (!spd_inv<B>(P, Dt, ldq_prev)) bad |= ST_ENUMERIC;
+    } else if (j > 0) {
+#pragma unroll
+        for (int r = 0; r < B; ++r)
+#pragma unroll
+            for (int q = 0; q < B; ++q) Dt[r][q] = s_qi[(j - 1) * BB + r * B + q];
+        ldq_prev = s_ld[j - 1];
     } else {
         const double dt = t[i] - t[i - 1];
-        if (!(dt > 0.0)) bad |= (dt < 0.0) ? ST_ENOTSORTED : ST_ENUMERIC;   // Q = 0 at a tie: no precision
-        double Ph[B][B];
-        if (!trans_scaled<B>(lam * dt, sf, Ph, Dt, ldq_prev)) bad |= ST_ENUMERIC;
+        double Pp[B][B];
+        trans_scaled<B>(lam * dt, sf, Pp, Dt, ldq_prev);   // its status was set by the thread that owns step i-1
     }
     double Ot[B][B];
-    if (i + 1 < n) {
-        const double dt = t[i + 1] - t[i];
-        double Ph[B][B], Qi[B][B], ldq, T[B][B], U[B][B];
-        if (!(dt > 0.0) || !trans_scaled<B>(lam * dt, sf, Ph, Qi, ldq)) bad |= ST_ENUMERIC;
+    if (hasn) {
+        double T[B][B], U[B][B];
         mat_mul<B>(Qi, Ph, T);          // Qt^-1 Phi
         mat_tmul_sym<B>(Ph, T, U);      // Phi^T Qt^-1 Phi
 #pragma unroll
@@ -159,7 +187,7 @@ __global__ void __launch_bounds__(128) k_assemble(const double* __restrict__ t, 
     for (int r = 0; r < B; ++r)
 #pragma unroll
         for (int q = 0; q < B; ++q) Dp[r * B + q] = Dt[r][q] * lp[r] * lp[q];
-    if (i + 1 < n) {
+    if (hasn) {
         double* Op = Oout + i * (B * B);
 #pragma unroll
         for (int r = 0; r < B; ++r)
@@ -711,16 +739,39 @@ __device__ __forceinline__ double quad(const double (&u)[B], const double (&X)[B
 // <S, X> = <Dl^-1 S Dl^-1, Xt> and x^T X x = (Dl^-1 x)^T Xt (Dl^-1 x), and
 // dX/dlam = Dl^-1 (dt dXt/dx - (E Xt + Xt E) / lam) Dl^-1 with E = diag(0, 1, ..).
 template <int B, bool GRAD>
-__global__ void __launch_bounds__(128) k_literal_terms(const double* __restrict__ t, const double* __restrict__ y,
-                                                       int64_t n, const double* __restrict__ theta,
-                                                       const double* __restrict__ x,
-                                                       const double* __restrict__ Sd,
-                                                       const double* __restrict__ So, double* __restrict__ part,
-                                                       double* __restrict__ mean, double* __restrict__ var) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+__global__ void __launch_bounds__(ASM_CTA) k_literal_terms(const double* __restrict__ t, const double* __restrict__ y,
+                                                           int64_t n, const double* __restrict__ theta,
+                                                           const double* __restrict__ x,
+                                                           const double* __restrict__ Sd,
+                                                           const double* __restrict__ So, double* __restrict__ part,
+                                                           double* __restrict__ mean, double* __restrict__ var) {
+    constexpr int BB = B * B;
+    // the transition out of step i, computed by its thread and handed to the
+    // next thread (Qt^-1, dQt/dx, d(Qt^-1)/dx); the first thread of a block
+    // derives its incoming one itself
+    __shared__ double s_tr[GRAD ? ASM_CTA * 3 * BB : 1];
+    const int j = threadIdx.x;
+    const int64_t i = blockIdx.x * (int64_t)ASM_CTA + j;
+    const bool valid = i < n;
     const double ell = theta[0], sf = theta[1], s2 = theta[2];
     const double lam = sqrt(2.0 * B - 1.0) / ell;
+    double Ph[B][B], Qn[B][B], dQn[B][B], dQin[B][B];
+    const bool hasn = valid && i + 1 < n;
+    if constexpr (GRAD) {
+        if (hasn) {
+            trans_dx<B>(lam * (t[i + 1] - t[i]), sf, Ph, Qn, dQn, dQin);
+#pragma unroll
+            for (int r = 0; r < B; ++r)
+#pragma unroll
+                for (int q = 0; q < B; ++q) {
+                    s_tr[(3 * j) * BB + r * B + q] = Qn[r][q];
+                    s_tr[(3 * j + 1) * BB + r * B + q] = dQn[r][q];
+                    s_tr[(3 * j + 2) * BB + r * B + q] = dQin[r][q];
+                }
+        }
+        __syncthreads();
+    }
+    if (!valid) return;
     const double yi = y[i], x0 = x[i * B];
     part[i] = yi * yi / s2;
     part[n + i] = yi * x0 / s2;
@@ -754,8 +805,20 @@ __global__ void __launch_bounds__(128) k_literal_terms(const double* __restrict_
             dld_l = -(double)(B * (B - 1)) / lam;
         } else {
             const double dp = t[i] - t[i - 1];
-            double Ph[B][B], dQ[B][B], dQi[B][B];
-            trans_dx<B>(lam * dp, sf, Ph, Dt, dQ, dQi);
+            double dQ[B][B], dQi[B][B];
+            if (j > 0) {
+#pragma unroll
+                for (int r = 0; r < B; ++r)
+#pragma unroll
+                    for (int q = 0; q < B; ++q) {
+                        Dt[r][q] = s_tr[(3 * (j - 1)) * BB + r * B + q];
+                        dQ[r][q] = s_tr[(3 * (j - 1) + 1) * BB + r * B + q];
+                        dQi[r][q] = s_tr[(3 * (j - 1) + 2) * BB + r * B + q];
+                    }
+            } else {
+                double Pp[B][B];
+                trans_dx<B>(lam * dp, sf, Pp, Dt, dQ, dQi);
+            }
 #pragma unroll
             for (int r = 0; r < B; ++r)
 #pragma unroll
@@ -766,19 +829,18 @@ __global__ void __launch_bounds__(128) k_literal_terms(const double* __restrict_
         for (int r = 0; r < B; ++r)
 #pragma unroll
             for (int q = 0; q < B; ++q) { Ot[r][q] = 0.0; YO[r][q] = 0.0; }
-        if (i + 1 < n) {
+        if (hasn) {
             const double dn = t[i + 1] - t[i];
-            double Ph[B][B], Qi[B][B], dQ[B][B], dQi[B][B], T[B][B], U[B][B], FP[B][B], W[B][B], V[B][B];
-            trans_dx<B>(lam * dn, sf, Ph, Qi, dQ, dQi);
-            mat_mul<B>(Qi, Ph, T);      // Qt^-1 Phi
+            double T[B][B], U[B][B], FP[B][B], W[B][B], V[B][B];
+            mat_mul<B>(Qn, Ph, T);      // Qt^-1 Phi
             mat_tmul_sym<B>(Ph, T, U);  // Phi^T Qt^-1 Phi
             f1_mul<B>(Ph, FP);          // dPhi/dx
             mat_tmul<B>(T, FP, W);      // Phi^T Qt^-1 F1 Phi
-            mat_mul<B>(dQi, Ph, V);     // d(Qt^-1)/dx Phi
+            mat_mul<B>(dQin, Ph, V);    // d(Qt^-1)/dx Phi
             double PV[B][B];
             mat_tmul<B>(Ph, V, PV);     // Phi^T d(Qt^-1)/dx Phi
             double QF[B][B];
-            mat_mul<B>(Qi, FP, QF);     // Qt^-1 F1 Phi
+            mat_mul<B>(Qn, FP, QF);     // Qt^-1 F1 Phi
 #pragma unroll
             for (int r = 0; r < B; ++r)
 #pragma unroll
@@ -928,7 +990,7 @@ static int btd_core(int64_t n, const double* D, const double* O, const double* r
 template <int B>
 static int assemble_core(const double* t, const double* y, int64_t n, const double* theta, double* D, double* O,
                          double* r, double* logdet_kinv, double* part, int* status, cudaStream_t st) {
-    k_assemble<B><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(t, y, n, theta, D, O, r, part, status);
+    k_assemble<B><<<(unsigned)((n + ASM_CTA - 1) / ASM_CTA), ASM_CTA, 0, st>>>(t, y, n, theta, D, O, r, part, status);
     colsum(part, n, 0, 1, logdet_kinv, part + n, st);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
@@ -1011,12 +1073,12 @@ static int literal_t(int mode, const double* t, const double* y, int64_t n, cons
     if (btd_core<B>(n, at(lay.D), at(lay.O), at(lay.r), at(lay.lds), at(lay.x), sel ? at(lay.Sd) : nullptr,
                     sel ? at(lay.So) : nullptr, w + lay.btd, status, st))
         return 1;
-    const unsigned g = (unsigned)((n + 127) / 128);
+    const unsigned g = (unsigned)((n + ASM_CTA - 1) / ASM_CTA);
     if (mode == MODE_GRAD)
-        k_literal_terms<B, true><<<g, 128, 0, st>>>(t, y, n, theta, at(lay.x), at(lay.Sd), at(lay.So), at(lay.part),
+        k_literal_terms<B, true><<<g, ASM_CTA, 0, st>>>(t, y, n, theta, at(lay.x), at(lay.Sd), at(lay.So), at(lay.part),
                                                     nullptr, nullptr);
     else
-        k_literal_terms<B, false><<<g, 128, 0, st>>>(t, y, n, theta, at(lay.x), sel ? at(lay.Sd) : nullptr, nullptr,
+        k_literal_terms<B, false><<<g, ASM_CTA, 0, st>>>(t, y, n, theta, at(lay.x), sel ? at(lay.Sd) : nullptr, nullptr,
                                                      at(lay.part), mean, sel ? var : nullptr);
     colsum(at(lay.part), n, n, mode == MODE_GRAD ? 5 : 2, at(lay.sums), at(lay.red), st);
     k_literal_final<<<1, 32, 0, st>>>(theta, n, at(lay.sums), at(lay.lds), ll, mode == MODE_GRAD ? grad : nullptr);
