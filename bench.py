@@ -669,7 +669,7 @@ def main_split(args, world, rank, local, dev):
         evs[k][1].record()
     barrier()
     clk = clocks.stop()
-    st = spingp.spingp_ws_status(model.workspace(b - a, spingp.WS_GRAD, dev))
+    st = spingp.spingp_ws_status(model.workspace(b - a, spingp.WS_GRAD, dev, purpose="segment"))
     if st != spingp.OK:
         raise spingp.SpinGPError(st, "benchmark step")
     tt = torch.tensor([float(np.sum([e0.elapsed_time(e1) for e0, e1 in evs]))], dtype=torch.float64, device=dev)

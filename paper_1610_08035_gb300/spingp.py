@@ -440,12 +440,12 @@ class Model:
     def chunk_len(self, n):
         return spingp_get_chunk_len(self.h, n)
 
-    def workspace(self, n, what, device=None):
+    def workspace(self, n, what, device=None, purpose=None):
         nbytes = spingp_workspace_bytes(self.h, n, what)
         if nbytes == 0:
             raise SpinGPError(EUNSUPPORTED, "spingp_workspace_bytes")
         device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-        key = (what, device)
+        key = (what, device, purpose)
         ws = self._ws.get(key)
         if ws is None or ws.numel() < nbytes:
             ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
@@ -515,7 +515,8 @@ class Model:
         previous range's last step, None for the range that starts the
         series.  ws: this rank's workspace (kept for segment_grad)."""
         n = self._args(t, y, theta)
-        ws = ws if ws is not None else self.workspace(n, WS_GRAD, t.device)
+        # a workspace of its own: segment_grad needs what this call leaves in it
+        ws = ws if ws is not None else self.workspace(n, WS_GRAD, t.device, purpose="segment")
         elem = torch.empty(spingp_segment_elem_size(self.h), dtype=torch.float64, device=t.device)
         first = t_prev is None
         _check(spingp_segment_reduce(self.h, t, y, n, theta, 0.0 if first else t_prev, first, elem, ws, ws.numel(),
@@ -527,7 +528,7 @@ class Model:
         (device, n_ranks x elem_size, rank order); the same arguments and
         workspace as segment_reduce."""
         n = self._args(t, y, theta)
-        ws = ws if ws is not None else self.workspace(n, WS_GRAD, t.device)
+        ws = ws if ws is not None else self.workspace(n, WS_GRAD, t.device, purpose="segment")
         _dev_f64(elems, "elems")
         elems = elems.contiguous()
         ll = torch.empty(1, dtype=torch.float64, device=t.device)
