@@ -1155,7 +1155,7 @@ int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t 
     double* part = (double*)(ws + lay.off_part);
     double* store = (double*)(ws + lay.off_store);
     double* state = (double*)(ws + lay.off_state);
-    ChainArgs a{t, y, n, L, lay.nc, lay.nb, theta, status, nullptr, nullptr, 0, 3, missing};
+    ChainArgs a{t, y, n, L, lay.nc, lay.nb, theta, status, nullptr, nullptr, 0, 3, missing, 0, 0.0};
     const unsigned grid = (unsigned)lay.nb;
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
     if (ev) cudaEventRecord(ev[0], st);
@@ -1266,7 +1266,7 @@ int matern_run_batched_t(int mode, const int64_t* offsets, int64_t nseries, int6
     double* part = (double*)(ws + lay.off_part);
     double* store = (double*)(ws + lay.off_store);
     double* state = (double*)(ws + lay.off_state);
-    ChainArgs a{t, y, n_total, L, lay.nc, lay.nb, theta, status, offsets, cstart, nseries, 3, missing};
+    ChainArgs a{t, y, n_total, L, lay.nc, lay.nb, theta, status, offsets, cstart, nseries, 3, missing, 0, 0.0};
     const unsigned grid = (unsigned)lay.nb;
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
     if (ev) cudaEventRecord(ev[0], st);
