@@ -9,7 +9,6 @@ mathematics, not by the implementation.
   quasi-Newton method (scipy L-BFGS-B) finds on the same objective, with a
   vanishing gradient there."""
 import numpy as np
-import pytest
 from scipy.optimize import minimize
 
 from oracle import dense, scg, seq
