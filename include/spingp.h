@@ -428,8 +428,10 @@ spingp_status spingp_literal(const spingp_model* model, spingp_ws_kind what, con
 int spingp_literal_launch_count(int64_t n);
 
 /* Synchronise the stream and return the device status recorded in ws by the
- * last call that used it (SPINGP_OK if none). */
+ * last call that used it (SPINGP_OK if none).  spingp_sync_status is the same
+ * call under the name of a status read at a synchronisation point. */
 spingp_status spingp_ws_status(void* ws, void* stream);
+spingp_status spingp_sync_status(void* ws, void* stream);
 
 const char* spingp_status_str(spingp_status status);
 

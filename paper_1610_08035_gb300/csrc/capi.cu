@@ -712,6 +712,8 @@ spingp_status spingp_ws_status(void* ws, void* stream) {
     return SPINGP_OK;
 }
 
+spingp_status spingp_sync_status(void* ws, void* stream) { return spingp_ws_status(ws, stream); }
+
 const char* spingp_status_str(spingp_status s) {
     switch (s) {
     case SPINGP_OK: return "ok";

@@ -36,7 +36,7 @@ EXPORTS = ("spingp_model_create", "spingp_model_destroy", "spingp_num_params", "
            "spingp_assemble_workspace_bytes", "spingp_assemble", "spingp_literal_workspace_bytes",
            "spingp_literal", "spingp_literal_launch_count", "spingp_optimize_workspace_bytes", "spingp_optimize",
            "spingp_optimize_workspace_bytes_batched", "spingp_optimize_batched", "spingp_ws_status",
-           "spingp_status_str")
+           "spingp_sync_status", "spingp_status_str")
 STAGES = ("elimination", "reduction", "chunk_pass", "final_reduction")
 
 _lib = None
@@ -120,6 +120,7 @@ def load():
     lib.spingp_optimize_workspace_bytes_batched.restype = sz
     lib.spingp_optimize_batched.argtypes = [vp, dp, i64, i64, dp, dp, dp, ctypes.c_int, dbl, dp, dp, vp, sz, u32, vp]
     lib.spingp_ws_status.argtypes = [vp, vp]
+    lib.spingp_sync_status.argtypes = [vp, vp]
     lib.spingp_status_str.argtypes = [ctypes.c_int]
     lib.spingp_status_str.restype = ctypes.c_char_p
     _lib = lib
@@ -401,6 +402,9 @@ def spingp_optimize_batched(h, offsets, n_series, n_total, t, y, theta_inout, it
 
 def spingp_ws_status(ws, stream=None):
     return load().spingp_ws_status(_ptr(ws), stream if stream is not None else _stream())
+
+
+spingp_sync_status = spingp_ws_status
 
 
 def spingp_status_str(st):
