@@ -759,11 +759,12 @@ class Batch:
 class LogLik(torch.autograd.Function):
     """log p(y | t, theta) with the hand-written adjoint as its backward.
 
-    forward runs spingp_grad once and keeps the gradient; backward returns
-    grad_output * gradient for theta (t and y get no gradient)."""
+    LogLik.apply(t, y, theta, model): forward runs spingp_grad once and keeps
+    the gradient; backward returns grad_output * gradient for theta (t and y
+    get no gradient)."""
 
     @staticmethod
-    def forward(ctx, theta, t, y, model):
+    def forward(ctx, t, y, theta, model):
         ll, g = model.grad(t, y, theta.detach().contiguous())
         ctx.save_for_backward(g)
         return ll[0]
@@ -771,4 +772,4 @@ class LogLik(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         (g,) = ctx.saved_tensors
-        return grad_out * g, None, None, None
+        return None, None, grad_out * g, None

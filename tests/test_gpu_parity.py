@@ -145,7 +145,7 @@ def test_autograd_function():
     s = synth.single("matern32_n1000")
     m = spingp.Model(s.spec)
     th = _t(s.theta).requires_grad_(True)
-    ll = spingp.LogLik.apply(th, _t(s.t), _t(s.y), m)
+    ll = spingp.LogLik.apply(_t(s.t), _t(s.y), th, m)
     (2.0 * ll).backward()
     _, go = seq.grad(s.spec, s.theta, s.t, s.y)
     assert np.all(np.abs(th.grad.cpu().numpy() - 2.0 * go) <= 1e-8 * np.maximum(1.0, np.abs(2.0 * go)))
