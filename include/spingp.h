@@ -234,9 +234,10 @@ spingp_status spingp_probe_exp_neg(const double* x, double* y, int64_t n, void* 
  * odd-even reduction of Sec. 3.1 then spans the ranks with one exchange:
  *   1. spingp_segment_reduce: each rank reduces its range to one element, the
  *      Schur complement of K~ on the state before the range and the range's
- *      last state, in conditional-covariance form (A, b, C, eta, J: b^2, b,
- *      b(b+1)/2, b, b(b+1)/2 doubles in that order, upper triangles row by
- *      row; spingp_segment_elem_size doubles), written to elem_out (device).
+ *      last state, in conditional-covariance form (for a single Matern
+ *      model A, b, C, eta, J: b^2, b, b(b+1)/2, b, b(b+1)/2 doubles in that
+ *      order, upper triangles row by row; spingp_segment_elem_size doubles
+ *      in every case), written to elem_out (device).
  *      The range of rank 0 starts the series (first = 1); every other range
  *      continues it (first = 0), and t_prev is the time of the last step of
  *      the range before it (host value, finite, <= t[0]).
@@ -249,8 +250,10 @@ spingp_status spingp_probe_exp_neg(const double* x, double* y, int64_t n, void* 
  * Calls 1 and 3 of a rank take the same t, y, n, theta, t_prev, first, flags
  * and the same workspace (spingp_workspace_bytes(model, n, SPINGP_WS_GRAD)),
  * with no other call on that workspace in between: call 3 reuses what call 1
- * left in it.  With G = 1 the result is spingp_grad's.  Single Matern models
- * only (SPINGP_EUNSUPPORTED otherwise).  SPINGP_EINVAL for n < 1, G outside
+ * left in it.  With G = 1 the result is spingp_grad's.  Every model runs
+ * this way; for the structured models (b > 3 or sums) the element is the
+ * group path's (b x b blocks padded to 16 x 16: spingp_segment_elem_size
+ * doubles).  SPINGP_EINVAL for n < 1, G outside
  * [1, 32], rank outside [0, G), first != (rank == 0), or a non-finite t_prev
  * when first = 0. */
 int spingp_segment_elem_size(const spingp_model* model);

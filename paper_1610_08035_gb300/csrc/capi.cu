@@ -418,11 +418,16 @@ spingp_status spingp_probe_exp_neg(const double* x, double* y, int64_t n, void* 
 
 // ---------------------------------------------------------------- a series split across ranks
 
-int spingp_segment_elem_size(const spingp_model* m) { return (m && single_matern(m)) ? spg::matern_elem_size(m->b) : -1; }
+int spingp_segment_elem_size(const spingp_model* m) {
+    if (!m) return -1;
+    if (single_matern(m)) return spg::matern_elem_size(m->b);
+    return m->group ? spg::group_elem_size() : -1;
+}
 
 int spingp_segment_launch_count(const spingp_model* m, int64_t n) {
-    if (!m || !single_matern(m) || n < 1) return -1;
-    return spg::matern_segment_launch_count(m->b, n, chunk_len(m, n));
+    if (!m || n < 1) return -1;
+    if (single_matern(m)) return spg::matern_segment_launch_count(m->b, n, chunk_len(m, n));
+    return m->group ? spg::group_segment_launch_count(n, chunk_len(m, n)) : -1;
 }
 
 static spingp_status segment_call(const spingp_model* m, int phase, const double* t, const double* y, int64_t n,
@@ -430,17 +435,21 @@ static spingp_status segment_call(const spingp_model* m, int phase, const double
                                   int rank, double* elem_out, double* ll_out, double* grad_out, void* ws,
                                   size_t ws_bytes, unsigned flags, void* stream) {
     if (!m || !t || !y || !theta || !ws || n < 1) return SPINGP_EINVAL;
-    if (!single_matern(m)) return SPINGP_EUNSUPPORTED;
+    if (!single_matern(m) && !m->group) return SPINGP_EUNSUPPORTED;
     if (((uintptr_t)ws & 255u) != 0) return SPINGP_EINVAL;
     if (!first && !std::isfinite(t_prev)) return SPINGP_EINVAL;
     const int64_t L = chunk_len(m, n);
-    if (ws_bytes < spg::matern_ws_bytes(m->b, n, L, spg::MODE_GRAD)) return SPINGP_EINVAL;
+    const size_t need = m->group ? spg::group_ws_bytes(n, L, spg::MODE_GRAD) : spg::matern_ws_bytes(m->b, n, L, spg::MODE_GRAD);
+    if (ws_bytes < need) return SPINGP_EINVAL;
     spingp_status st = prepare_device();
     if (st != SPINGP_OK) return st;
     const int miss = (flags & SPINGP_MISSING_NAN) ? 1 : 0;
-    if (spg::matern_segment(m->b, phase, t, y, n, L, theta, first ? 0.0 : t_prev, first ? 1 : 0, elems, n_ranks, rank,
-                            elem_out, ll_out, grad_out, ws, (cudaStream_t)stream, miss))
-        return SPINGP_ECUDA;
+    const double tp = first ? 0.0 : t_prev;
+    const int rc = m->group ? spg::group_segment(m->gm, phase, t, y, n, L, theta, tp, first ? 1 : 0, elems, n_ranks,
+                                                 rank, elem_out, ll_out, grad_out, ws, (cudaStream_t)stream, miss)
+                            : spg::matern_segment(m->b, phase, t, y, n, L, theta, tp, first ? 1 : 0, elems, n_ranks,
+                                                  rank, elem_out, ll_out, grad_out, ws, (cudaStream_t)stream, miss);
+    if (rc) return SPINGP_ECUDA;
     if (flags & SPINGP_SYNC) return spingp_ws_status(ws, stream);
     return SPINGP_OK;
 }

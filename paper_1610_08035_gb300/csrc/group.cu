@@ -145,14 +145,16 @@ __global__ void k_gsetup(GModel gm, const double* __restrict__ theta, double* __
 // ------------------------------------------------------------------ discretisation: Phi_n per block
 
 // Phi for step i (transition from t_{i-1}): 4 entries per block, row-major.
+// (t_prev: the time before step 0 when the steps continue a split series, s0 = -1)
 __global__ void __launch_bounds__(256) k_gdisc(GModel gm, const double* __restrict__ t, const double* __restrict__ y,
                                                 int64_t n, const double* __restrict__ theta,
-                                                double* __restrict__ phis, int* status, int missing) {
+                                                double* __restrict__ phis, int* status, int missing, int64_t s0,
+                                                double t_prev) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     int bad = 0;
     if (!isfinite(t[i]) || (!isfinite(y[i]) && !(missing && isnan(y[i])))) bad |= ST_ENONFINITE;
-    const double dt = (i > 0) ? t[i] - t[i - 1] : 0.0;
+    const double dt = (i > 0) ? t[i] - t[i - 1] : (s0 < 0 ? t[0] - t_prev : 0.0);
     if (dt < 0.0) bad |= ST_ENOTSORTED;
     double* ph = phis + i * (4 * GK);
 #pragma unroll 1
@@ -403,6 +405,8 @@ struct GArgs {
     const double* phis;
     int* status;
     int missing;          // 1: a NaN observation is missing (a test point)
+    int64_t s0;           // the series' first step: 0, or -1 when the steps continue a split series
+    double t_prev;        // with s0 = -1: the time of the step before step 0
 };
 
 template <int NR>
@@ -423,15 +427,15 @@ __global__ void __launch_bounds__(GCTA) k_gfold(GArgs a, double* __restrict__ no
     double Cm[GL];   // C - Pinf, column lane
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-        el.A[r] = (s > 0 && r == lane && on) ? 1.0 : 0.0;
+        el.A[r] = (s > a.s0 && r == lane && on) ? 1.0 : 0.0;
         el.J[r] = 0.0;
-        Cm[r] = (s > 0) ? -s_pinf[r * GL + lane] : 0.0;
+        Cm[r] = (s > a.s0) ? -s_pinf[r * GL + lane] : 0.0;
     }
     el.bv = 0.0;
     el.eta = 0.0;
     for (int64_t i = s; i < e; ++i) {
         const double yi = a.y[i];
-        if (i > 0) {
+        if (i > a.s0) {
             const double* ph = a.phis + i * (4 * GK);
             g_left<NR>(ph, el.A);
             el.bv = g_vleft(ph, lane, el.bv);
@@ -771,7 +775,7 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
         const double yi = a.y[i];
         const bool obs = !(a.missing && isnan(yi));   // the same in every lane of the group
         double mb, Db[GL];
-        if (i == 0) {
+        if (i == a.s0) {
             mb = 0.0;
 #pragma unroll
             for (int r = 0; r < NR; ++r) Db[r] = 0.0;
@@ -916,10 +920,10 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                     for (int r = 0; r < NR; ++r) geq = fma(s_dpe[r * GL + lane], G[r], geq);
                 }
             }
-            if (i > 0) {
+            if (i > a.s0) {
                 const double* ph = a.phis + i * (4 * GK);
                 if constexpr (GRAD) {
-                    const double dt = a.t[i] - a.t[i - 1];
+                    const double dt = (i > 0) ? a.t[i] - a.t[i - 1] : a.t[0] - a.t_prev;
                     // per block: 2 <G_k,:, X_k Db_k,:> (column 'lane' part) - lt_k^T X_k mb_k (row 'lane' part)
                     const double mp = gxor(mb, 1);
                     const double mb0 = even ? mb : mp, mb1 = even ? mp : mb;
@@ -1085,9 +1089,56 @@ struct GLayout {
         off_part = o; o = galign(o + sizeof(double) * GPART * (size_t)nc);
         off_store = o;
         if (mode != MODE_LOGLIK) o = galign(o + sizeof(double) * GNF * GL * (size_t)L * nc);
+        // a split series: the ranks' elements and their reduction tree, and
+        // this rank's prefix / suffix as one node
+        seg_nlev = 0;
+        seg_n[0] = SEG_MAX_RANKS;
+        while (seg_n[seg_nlev] > 1) { seg_n[seg_nlev + 1] = (seg_n[seg_nlev] + 1) / 2; ++seg_nlev; }
+        for (int l = 0; l <= seg_nlev; ++l) {
+            off_seg_nodes[l] = o; o = galign(o + sizeof(double) * GNE * GL * (size_t)seg_n[l]);
+            off_seg_pre[l] = o; o = galign(o + sizeof(double) * GNM * GL * (size_t)seg_n[l]);
+            off_seg_suf[l] = o; o = galign(o + sizeof(double) * GNM * GL * (size_t)seg_n[l]);
+        }
+        off_seg_top = o; o = galign(o + sizeof(double) * 2 * GNM * GL);
         total = o;
     }
+    int seg_nlev;
+    int64_t seg_n[8];
+    size_t off_seg_nodes[8], off_seg_pre[8], off_seg_suf[8], off_seg_top;
 };
+
+// The up-sweep of the level-by-level reduction over cnt[0] elements at
+// nodes[0] (cnt[l] nodes at level l, nlev levels above level 0).
+static void gscan_up(char* ws, const size_t* nodes, const int64_t* cnt, int nlev, cudaStream_t st) {
+    for (int l = 1; l <= nlev; ++l)
+        k_gscan_up<<<(unsigned)cnt[l], GSC, 0, st>>>((const double*)(ws + nodes[l - 1]), cnt[l - 1],
+                                                     (double*)(ws + nodes[l]), cnt[l]);
+}
+// The down-sweep: the state before and the information after every level-0
+// element, from top_pre / top_suf at the single top node (NULL: zero, a
+// whole series).
+static int gscan_down(char* ws, const size_t* nodes, const size_t* pre, const size_t* suf, const int64_t* cnt,
+                      int nlev, const double* top_pre, const double* top_suf, cudaStream_t st) {
+    for (int l = nlev; l >= 1; --l) {
+        const bool top = (l == nlev);
+        k_gscan_down<<<(unsigned)cnt[l - 1], GSC, 0, st>>>(
+            (const double*)(ws + nodes[l - 1]), cnt[l - 1], top ? top_pre : (const double*)(ws + pre[l]),
+            top ? top_suf : (const double*)(ws + suf[l]), cnt[l], (double*)(ws + pre[l - 1]),
+            (double*)(ws + suf[l - 1]));
+    }
+    if (nlev == 0) {   // one element: its prefix and suffix are the top's
+        const size_t b = sizeof(double) * GNM * GL;
+        if (top_pre) {
+            if (cudaMemcpyAsync(ws + pre[0], top_pre, b, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                cudaMemcpyAsync(ws + suf[0], top_suf, b, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                return 1;
+        } else if (cudaMemsetAsync(ws + pre[0], 0, b, st) != cudaSuccess ||
+                   cudaMemsetAsync(ws + suf[0], 0, b, st) != cudaSuccess) {
+            return 1;
+        }
+    }
+    return 0;
+}
 
 size_t group_ws_bytes(int64_t n, int64_t L, int mode) { return GLayout(n, L, mode).total; }
 
@@ -1106,11 +1157,11 @@ int group_run(const GModel& gm, int mode, const double* t, const double* y, int6
     double* phis = (double*)(ws + lay.off_phis);
     double* part = (double*)(ws + lay.off_part);
     double* store = (double*)(ws + lay.off_store);
-    GArgs a{gm, t, y, n, L, lay.nc, theta, gconst, phis, status, missing};
+    GArgs a{gm, t, y, n, L, lay.nc, theta, gconst, phis, status, missing, 0, 0.0};
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
     if (ev) cudaEventRecord(ev[0], st);
     k_gsetup<<<1, 32, 0, st>>>(gm, theta, gconst, status);
-    k_gdisc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gm, t, y, n, theta, phis, status, missing);
+    k_gdisc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gm, t, y, n, theta, phis, status, missing, 0, 0.0);
     const unsigned cgrid = (unsigned)((lay.nc + GGRP - 1) / GGRP);
     // rows of the per-lane column arithmetic: the state dimension rounded up to 4
     const int NRr = (gm.b <= 4) ? 4 : (gm.b <= 8) ? 8 : (gm.b <= 12) ? 12 : 16;
@@ -1124,22 +1175,8 @@ int group_run(const GModel& gm, int mode, const double* t, const double* y, int6
     };
     fold((double*)(ws + lay.off_nodes[0]));
     if (ev) cudaEventRecord(ev[1], st);
-    for (int l = 1; l <= lay.nlev; ++l)
-        k_gscan_up<<<(unsigned)lay.lev_n[l], GSC, 0, st>>>(
-            (const double*)(ws + lay.off_nodes[l - 1]), lay.lev_n[l - 1], (double*)(ws + lay.off_nodes[l]),
-            lay.lev_n[l]);
-    for (int l = lay.nlev; l >= 1; --l) {
-        const bool top = (l == lay.nlev);
-        k_gscan_down<<<(unsigned)lay.lev_n[l - 1], GSC, 0, st>>>(
-            (const double*)(ws + lay.off_nodes[l - 1]), lay.lev_n[l - 1],
-            top ? nullptr : (const double*)(ws + lay.off_pre[l]), top ? nullptr : (const double*)(ws + lay.off_suf[l]),
-            lay.lev_n[l], (double*)(ws + lay.off_pre[l - 1]), (double*)(ws + lay.off_suf[l - 1]));
-    }
-    if (lay.nlev == 0) {
-        // one chunk: zero prefix and suffix
-        if (cudaMemsetAsync(ws + lay.off_pre[0], 0, sizeof(double) * GNM * GL, st) != cudaSuccess) return 1;
-        if (cudaMemsetAsync(ws + lay.off_suf[0], 0, sizeof(double) * GNM * GL, st) != cudaSuccess) return 1;
-    }
+    gscan_up(ws, lay.off_nodes, lay.lev_n, lay.nlev, st);
+    if (gscan_down(ws, lay.off_nodes, lay.off_pre, lay.off_suf, lay.lev_n, lay.nlev, nullptr, nullptr, st)) return 1;
     if (ev) cudaEventRecord(ev[2], st);
     const double* pre = (const double*)(ws + lay.off_pre[0]);
     const double* suf = (const double*)(ws + lay.off_suf[0]);
@@ -1164,6 +1201,100 @@ int group_run(const GModel& gm, int mode, const double* t, const double* y, int6
     k_gfinal<<<1, GFIN, 0, st>>>(gm, part, lay.nc, na, theta, gconst, ll_out, grad_out);
     if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+// ------------------------------------------------------------------ a series split across ranks
+//
+// The same two phases as the chain path (matern.cu): phase 0 reduces this
+// rank's range to its top element (GNE x GL doubles: element e's value f of
+// lane l at [f * GL + l]); phase 1 takes all G elements (rank-major), runs
+// the level-by-level reduction over them for the state before this range and
+// the information after it, then this range's down-sweep, chunk pass and
+// final reduction (its share of ll and gradient).  Phase 1 reuses the
+// workspace that phase 0 filled.
+
+// rank-major elements [G][GNE * GL] to the level layout [(f * G + e) * GL + l]
+__global__ void __launch_bounds__(256) k_gelems_to_soa(const double* __restrict__ in, double* __restrict__ out, int G) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int per = GNE * GL;
+    if (i < G * per) {
+        const int e = i / per, fl = i % per, f = fl / GL, l = fl % GL;
+        out[((int64_t)f * G + e) * GL + l] = in[i];
+    }
+}
+
+int group_segment(const GModel& gm, int phase, const double* t, const double* y, int64_t n, int64_t L,
+                  const double* theta, double t_prev, int first, const double* elems, int G, int rank,
+                  double* elem_out, double* ll_out, double* grad_out, void* wsv, cudaStream_t st, int missing) {
+    if (G < 1 || G > SEG_MAX_RANKS || rank < 0 || rank >= G) return 1;
+    GLayout lay(n, L, MODE_GRAD);
+    char* ws = (char*)wsv;
+    int* status = (int*)ws;
+    double* gconst = (double*)(ws + lay.off_gconst);
+    double* phis = (double*)(ws + lay.off_phis);
+    double* part = (double*)(ws + lay.off_part);
+    double* store = (double*)(ws + lay.off_store);
+    const int64_t s0 = first ? 0 : -1;
+    GArgs a{gm, t, y, n, L, lay.nc, theta, gconst, phis, status, missing, s0, t_prev};
+    const unsigned cgrid = (unsigned)((lay.nc + GGRP - 1) / GGRP);
+    const int NRr = (gm.b <= 4) ? 4 : (gm.b <= 8) ? 8 : (gm.b <= 12) ? 12 : 16;
+    if (phase == 0) {
+        if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
+        k_gsetup<<<1, 32, 0, st>>>(gm, theta, gconst, status);
+        k_gdisc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gm, t, y, n, theta, phis, status, missing, s0, t_prev);
+        double* nodes0 = (double*)(ws + lay.off_nodes[0]);
+        switch (NRr) {
+        case 4: k_gfold<4><<<cgrid, GCTA, 0, st>>>(a, nodes0); break;
+        case 8: k_gfold<8><<<cgrid, GCTA, 0, st>>>(a, nodes0); break;
+        case 12: k_gfold<12><<<cgrid, GCTA, 0, st>>>(a, nodes0); break;
+        default: k_gfold<16><<<cgrid, GCTA, 0, st>>>(a, nodes0); break;
+        }
+        gscan_up(ws, lay.off_nodes, lay.lev_n, lay.nlev, st);
+        if (cudaMemcpyAsync(elem_out, ws + lay.off_nodes[lay.nlev], sizeof(double) * GNE * GL,
+                            cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return 1;
+    } else {
+        // the ranks' tree over the G elements: levels of G, ceil(G/2), .. nodes
+        int64_t cnt[8];
+        int gl = 0;
+        cnt[0] = G;
+        while (cnt[gl] > 1) { cnt[gl + 1] = (cnt[gl] + 1) / 2; ++gl; }
+        k_gelems_to_soa<<<(unsigned)((G * GNE * GL + 255) / 256), 256, 0, st>>>(
+            elems, (double*)(ws + lay.off_seg_nodes[0]), G);
+        gscan_up(ws, lay.off_seg_nodes, cnt, gl, st);
+        if (gscan_down(ws, lay.off_seg_nodes, lay.off_seg_pre, lay.off_seg_suf, cnt, gl, nullptr, nullptr, st))
+            return 1;
+        // this rank's entry (value f of lane l at (f * G + rank) * GL + l) as one node
+        double* tpre = (double*)(ws + lay.off_seg_top);
+        double* tsuf = tpre + GNM * GL;
+        const double* gpre = (const double*)(ws + lay.off_seg_pre[0]);
+        const double* gsuf = (const double*)(ws + lay.off_seg_suf[0]);
+        if (cudaMemcpy2DAsync(tpre, sizeof(double) * GL, gpre + (int64_t)rank * GL, sizeof(double) * GL * G,
+                              sizeof(double) * GL, GNM, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+            cudaMemcpy2DAsync(tsuf, sizeof(double) * GL, gsuf + (int64_t)rank * GL, sizeof(double) * GL * G,
+                              sizeof(double) * GL, GNM, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return 1;
+        if (gscan_down(ws, lay.off_nodes, lay.off_pre, lay.off_suf, lay.lev_n, lay.nlev, tpre, tsuf, st)) return 1;
+        const double* pre = (const double*)(ws + lay.off_pre[0]);
+        const double* suf = (const double*)(ws + lay.off_suf[0]);
+        switch (NRr) {
+        case 4: k_gchunk<MODE_GRAD, 4><<<cgrid, GCTA, 0, st>>>(a, pre, suf, store, part, nullptr, nullptr); break;
+        case 8: k_gchunk<MODE_GRAD, 8><<<cgrid, GCTA, 0, st>>>(a, pre, suf, store, part, nullptr, nullptr); break;
+        case 12: k_gchunk<MODE_GRAD, 12><<<cgrid, GCTA, 0, st>>>(a, pre, suf, store, part, nullptr, nullptr); break;
+        default: k_gchunk<MODE_GRAD, 16><<<cgrid, GCTA, 0, st>>>(a, pre, suf, store, part, nullptr, nullptr); break;
+        }
+        k_gfinal<<<1, GFIN, 0, st>>>(gm, part, lay.nc, GPART, theta, gconst, ll_out, grad_out);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+int group_elem_size() { return GNE * GL; }
+int group_segment_launch_count(int64_t n, int64_t L) {
+    GLayout lay(n, L, MODE_GRAD);
+    int gl = 0;
+    for (int64_t c = SEG_MAX_RANKS; c > 1; c = (c + 1) / 2) ++gl;
+    // phase 0: setup, disc, fold, up levels; phase 1: transpose, the ranks' tree (at most), the range's
+    // down levels, chunk, final
+    return 3 + lay.nlev + 1 + 2 * gl + lay.nlev + 2;
 }
 
 }  // namespace spg

@@ -118,6 +118,11 @@ int group_launch_count(int64_t n, int64_t L, int mode);
 int group_run(const GModel& gm, int mode, const double* t, const double* y, int64_t n, int64_t L,
               const double* theta, double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws,
               cudaStream_t st, cudaEvent_t* ev, int missing);
+int group_segment(const GModel& gm, int phase, const double* t, const double* y, int64_t n, int64_t L,
+                  const double* theta, double t_prev, int first, const double* elems, int G, int rank,
+                  double* elem_out, double* ll_out, double* grad_out, void* ws, cudaStream_t st, int missing);
+int group_elem_size();
+int group_segment_launch_count(int64_t n, int64_t L);
 }  // namespace spg
 
 struct spingp_model;

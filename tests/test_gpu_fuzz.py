@@ -6,7 +6,8 @@
   ranges -- against the oracle at the parity bars of test_gpu_parity, and the
   host-buffer result against the device call bit for bit;
 - the group path: random sums of Matern-3/2, periodic, quasi-periodic and
-  order-4 EQ components (b <= 16) against the oracle;
+  order-4 EQ components (b <= 16) against the oracle, whole and split in
+  ranges;
 - the general BTD solver: random SPD systems of every size against the
   oracle's block LDL^T."""
 import numpy as np
@@ -146,6 +147,24 @@ def test_fuzz_group_against_oracle(k):
     assert np.all(np.abs(g.cpu().numpy() - go) <= 1e-8 * gscale), (spec, g.cpu().numpy(), go)
     assert np.all(np.abs(mean.cpu().numpy() - mo) <= 1e-8 * np.maximum(np.abs(mo), np.sqrt(vo)))
     assert np.all(np.abs(var.cpu().numpy() - vo) <= 1e-8 * vo)
+    # the series split in ranges
+    G = min(len(t), 1 + k % 4)
+    ranges = shard.range_split(len(t), G)
+    wss, elems = [], []
+    for r, (a, b) in enumerate(ranges):
+        ws = torch.empty(spingp.spingp_workspace_bytes(m.h, b - a, spingp.WS_GRAD), dtype=torch.uint8, device=DEV)
+        tp = None if r == 0 else float(t[a - 1])
+        elems.append(m.segment_reduce(T[a:b], Y[a:b], TH, t_prev=tp, ws=ws))
+        wss.append(ws)
+    E = torch.stack(elems)
+    ls, gs = 0.0, 0.0
+    for r, (a, b) in enumerate(ranges):
+        tp = None if r == 0 else float(t[a - 1])
+        lr, gr = m.segment_grad(T[a:b], Y[a:b], TH, E, r, t_prev=tp, ws=wss[r])
+        ls += lr.item()
+        gs = gs + gr.cpu().numpy()
+    assert abs(ls - llo) <= 1e-9 * abs(llo)
+    assert np.all(np.abs(gs - go) <= 1e-8 * gscale), (spec, G, gs, go)
 
 
 @pytest.mark.parametrize("k", range(24))
