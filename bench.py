@@ -50,7 +50,7 @@ FP64_NOMINAL_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # SMs x max SM clock x FP64 flop
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="spingp", choices=["spingp", "reference"])
     ap.add_argument("--n", type=int, default=0, help="override the series length (profiling runs only)")
@@ -72,9 +72,13 @@ def parse():
 # ---------------------------------------------------------------- clocks during the timed region
 
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples every 25 ms, each with its timestamp; stop(t0, t1)
+    keeps the samples taken inside the timed region [t0, t1] (wall clock),
+    so the idle lead-in and tail do not enter the median."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 25
 
     def __init__(self, gpu_index, enabled=True):
         self.p = None
@@ -82,12 +86,20 @@ class ClockSampler:
             return
         try:
             self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                                       "-lms", "200", "-i", str(gpu_index)],
+                                       "-lms", str(self.PERIOD_MS), "-i", str(gpu_index)],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
 
-    def stop(self):
+    @staticmethod
+    def _when(stamp):
+        import datetime
+        try:
+            return datetime.datetime.strptime(stamp, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def stop(self, t0=None, t1=None):
         if self.p is None:
             return None
         self.p.terminate()
@@ -96,23 +108,31 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.p.kill()
             out, _ = self.p.communicate()
-        sm, smax, reasons = [], 0.0, set()
+        rows = []
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         for line in out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax = max(smax, float(f[2]))
+                sm, smax, pw = float(f[2]), float(f[3]), float(f[4])
             except ValueError:
                 continue
-            for name, val in zip(names, f[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(name)
-        if not sm:
+            rs = {name for name, val in zip(names, f[6:10]) if val.lower().startswith("active")}
+            rows.append((self._when(f[0]), sm, smax, pw, rs))
+        if not rows:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+        inside = rows
+        if t0 is not None and t1 is not None:
+            inside = [r for r in rows if r[0] is not None and t0 <= r[0] <= t1]
+        window = bool(inside) and t0 is not None
+        if not inside:   # a region shorter than the period: the samples nearest to it
+            mid = 0.5 * (t0 + t1) if t0 is not None else 0.0
+            inside = sorted(rows, key=lambda r: abs((r[0] or 0.0) - mid))[:2]
+        reasons = set().union(*(r[4] for r in inside))
+        return {"sm_mhz": float(np.median([r[1] for r in inside])), "sm_max_mhz": max(r[2] for r in rows),
+                "power_w_max": max(r[3] for r in inside), "reasons": sorted(reasons), "samples": len(inside),
+                "in_timed_region": window, "period_ms": self.PERIOD_MS}
 
 
 # ---------------------------------------------------------------- the oracle (CPU baseline / reference arm)
@@ -477,13 +497,15 @@ def main():
     barrier()
     clocks = ClockSampler(local, enabled=not args.no_clocks)
     time.sleep(0.3 if not args.no_clocks else 0.0)
+    w0 = time.time()
     for k in range(K):
         flush.fill_(k & 0xFF)                        # 256 MiB write: L2 (~126 MiB) flushed, untimed
         evs[k][0].record()
         model.grad(T, Y, TH, sync=False, out=(ll, g))
         evs[k][1].record()
     barrier()
-    clk = clocks.stop()
+    w1 = time.time()
+    clk = clocks.stop(w0, w1)
     stages, calls = spingp.spingp_profile_read(model.h)
     spingp.spingp_profile_enable(model.h, False)
     st = spingp.spingp_ws_status(model.workspace(n, spingp.WS_GRAD, dev))
@@ -662,13 +684,15 @@ def main_split(args, world, rank, local, dev):
     barrier()
     clocks = ClockSampler(local, enabled=not args.no_clocks)
     time.sleep(0.3 if not args.no_clocks else 0.0)
+    w0 = time.time()
     for k in range(K):
         flush.fill_(k & 0xFF)                        # 256 MiB write: L2 flushed, untimed
         evs[k][0].record()
         ll, g = shard.grad_split_series(model, T, Y, TH, t_prev, sync=False)
         evs[k][1].record()
     barrier()
-    clk = clocks.stop()
+    w1 = time.time()
+    clk = clocks.stop(w0, w1)
     st = spingp.spingp_ws_status(model.workspace(b - a, spingp.WS_GRAD, dev, purpose="segment"))
     if st != spingp.OK:
         raise spingp.SpinGPError(st, "benchmark step")
