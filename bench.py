@@ -294,8 +294,35 @@ def extra_workloads(args, dev, flush, world, rank=0):
         entry["comparator"] = {"kind": "forward kernel x 7 per series, one launch sequence per series",
                                "value": n_all / (cms * 1e-3), "unit": "steps/s", "ms_per_step": cms,
                                "speedup_of_batched_adjoint": cms / ms}
+    if not args.no_cpu_baseline and world == 1:
+        entry["cpu_baseline"] = batched_oracle_rate(s)
     res["batched_4096"] = entry
     return res
+
+
+def batched_oracle_rate(s, n_series=1024):
+    """The oracle over the batch's first n_series series, one series per task,
+    on every host core (the C oracle runs with the interpreter lock released,
+    so threads run in parallel): steps/s over the wall time."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from oracle import seq
+    offs, th = s.extra["offsets"], s.extra["thetas"]
+    k = min(n_series, len(offs) - 1)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    seq.grad("matern52", th[0], s.t[offs[0]:offs[0] + 100], s.y[offs[0]:offs[0] + 100])
+
+    def one(i):
+        seq.grad("matern52", th[i], s.t[offs[i]:offs[i + 1]], s.y[offs[i]:offs[i + 1]])
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(one, range(k)))
+    sec = time.perf_counter() - t0
+    steps = int(offs[k] - offs[0])
+    return {"value": steps / sec, "unit": "steps/s", "cores": cores, "kind": "oracle",
+            "sample": "first %d of %d series (%d steps), sequential C oracle per series, %d threads" % (
+                k, len(offs) - 1, steps, cores)}
 
 
 # Whole-call FP64 work per unit of the rows built beyond the hot path (ncu,
@@ -638,6 +665,13 @@ def main():
         out["cpu_baseline"] = {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle",
                                "sample": "first %d of %d steps, sequential C oracle (Kalman filter + two-filter "
                                          "adjoint), 1 host thread" % (sample, n)}
+        # context: the dense oracle (Cholesky of the N x N covariance) on the
+        # N = 1000 Matern-3/2 workload
+        from oracle import dense
+        s1 = synth.single("matern32_n1000")
+        dsec = _oracle_seconds(lambda: dense.grad(s1.spec, s1.theta, s1.t, s1.y), reps=3)
+        out["cpu_baseline"]["dense_oracle_n1000"] = {"value": len(s1.t) / dsec, "unit": "steps/s",
+                                                     "seconds": dsec, "workload": "matern32_n1000"}
 
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -302,7 +302,7 @@ static void expm_taylor(int n, const double* M, double* E) {
     int sq = 0;
     while (nrm > 0.25) { nrm *= 0.5; ++sq; }
     double scale = ldexp(1.0, -sq);
-    static double T[4 * OB2], U[4 * OB2], Ms[4 * OB2];
+    static _Thread_local double T[4 * OB2], U[4 * OB2], Ms[4 * OB2];   /* per thread: callers may run in parallel */
     for (int i = 0; i < n * n; ++i) Ms[i] = M[i] * scale;
     meye(n, E);
     meye(n, T);
@@ -550,7 +550,7 @@ static void om_transition(const om_t* om, const double* th, double dt, double* A
                expm([[F, Fl], [0, F]] dt) (Van Loan 1978) */
             int N = om->order[c], m = 2 * N;
             double a1[16], F[OB2], Fl[OB2];
-            static double M[4 * OB2], E[4 * OB2];
+            static _Thread_local double M[4 * OB2], E[4 * OB2];
             eq_factor(N, a1);
             eq_F(N, a1, th[po], F, Fl);
             memset(M, 0, sizeof(double) * m * m);
