@@ -211,28 +211,56 @@ __global__ void __launch_bounds__(ASM_CTA) k_assemble(const double* __restrict__
 //   r'_j = r_2j - O_{2j-1} D_{2j-1}^-1 r_{2j-1} - O_2j^T D_{2j+1}^-1 r_{2j+1}
 //   O'_j = -O_{2j+1} D_{2j+1}^-1 O_2j          (new sub-diagonal block (j+1, j))
 // and log det D_{2j+1} is counted by thread j.
-// The inverse of each eliminated node's D_k (computed by the thread that has it
-// as its right neighbour) is kept in Dinv for the back-substitution.
+// The inverse of each eliminated node's D_k is computed once, by the thread
+// that has it as its right neighbour; it is kept in Dinv for the
+// back-substitution and handed through shared memory to the next thread,
+// which has the same node as its left neighbour (a block's first thread
+// derives its left one itself).
+static constexpr int BTD_CTA = 128;
+
 template <int B>
-__global__ void __launch_bounds__(128) k_btd_reduce(const double* __restrict__ D, const double* __restrict__ O,
-                                                    const double* __restrict__ r, int64_t nlo,
-                                                    double* __restrict__ D2, double* __restrict__ O2,
-                                                    double* __restrict__ r2, int64_t nhi,
-                                                    double* __restrict__ ld, double* __restrict__ Dinv,
-                                                    int* status) {
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= nhi) return;
+__global__ void __launch_bounds__(BTD_CTA) k_btd_reduce(const double* __restrict__ D, const double* __restrict__ O,
+                                                        const double* __restrict__ r, int64_t nlo,
+                                                        double* __restrict__ D2, double* __restrict__ O2,
+                                                        double* __restrict__ r2, int64_t nhi,
+                                                        double* __restrict__ ld, double* __restrict__ Dinv,
+                                                        int* status) {
+    __shared__ double s_inv[BTD_CTA * B * B];
+    const int64_t j = blockIdx.x * (int64_t)BTD_CTA + threadIdx.x;
     const int64_t e = 2 * j;
-    double Dn[B][B], rn[B], ldj = 0.0;
+    const bool act = j < nhi;
+    const bool right = act && e + 1 < nlo;   // right odd neighbour k = e+1, T[e][k] = O_e^T
+    int bad = 0;
+    double ldj = 0.0, Dri[B][B];
+    if (right) {
+        double Dk[B][B];
+        blk_load<B>(D + (e + 1) * (B * B), Dk);
+        if (!spd_inv<B>(Dk, Dri, ldj)) bad |= ST_ENUMERIC;
+        blk_store<B>(Dinv + (e + 1) * (B * B), Dri);
+#pragma unroll
+        for (int a = 0; a < B; ++a)
+#pragma unroll
+            for (int c = 0; c < B; ++c) s_inv[(a * B + c) * BTD_CTA + threadIdx.x] = Dri[a][c];
+    }
+    __syncthreads();
+    if (!act) return;
+    double Dn[B][B], rn[B];
     blk_load<B>(D + e * (B * B), Dn);
 #pragma unroll
     for (int q = 0; q < B; ++q) rn[q] = r[e * B + q];
-    int bad = 0;
     if (e > 0) {   // left odd neighbour k = e-1, T[e][k] = O_k
         const int64_t k = e - 1;
-        double Dk[B][B], Dki[B][B], Ok[B][B], T[B][B], U[B][B], w[B], z[B], l0;
-        blk_load<B>(D + k * (B * B), Dk);
-        if (!spd_inv<B, false>(Dk, Dki, l0)) bad |= ST_ENUMERIC;
+        double Dki[B][B], Ok[B][B], T[B][B], U[B][B], w[B], z[B];
+        if (threadIdx.x > 0) {
+#pragma unroll
+            for (int a = 0; a < B; ++a)
+#pragma unroll
+                for (int c = 0; c < B; ++c) Dki[a][c] = s_inv[(a * B + c) * BTD_CTA + threadIdx.x - 1];
+        } else {
+            double Dk[B][B], l0;
+            blk_load<B>(D + k * (B * B), Dk);
+            if (!spd_inv<B, false>(Dk, Dki, l0)) bad |= ST_ENUMERIC;
+        }
         blk_load<B>(O + k * (B * B), Ok);
         mat_mul<B>(Ok, Dki, T);            // O_k D_k^-1
         mat_mul_t_sym<B>(T, Ok, U);        // O_k D_k^-1 O_k^T
@@ -246,19 +274,15 @@ __global__ void __launch_bounds__(128) k_btd_reduce(const double* __restrict__ D
             for (int c = 0; c < B; ++c) Dn[a][c] -= U[a][c];
         }
     }
-    if (e + 1 < nlo) {   // right odd neighbour k = e+1, T[e][k] = O_e^T
+    if (right) {
         const int64_t k = e + 1;
-        double Dk[B][B], Dki[B][B], Oe[B][B], T[B][B], U[B][B], w[B], z[B], l1;
-        blk_load<B>(D + k * (B * B), Dk);
-        if (!spd_inv<B>(Dk, Dki, l1)) bad |= ST_ENUMERIC;
-        ldj = l1;
-        blk_store<B>(Dinv + k * (B * B), Dki);
+        double Oe[B][B], T[B][B], U[B][B], w[B], z[B];
         blk_load<B>(O + e * (B * B), Oe);
-        mat_mul<B>(Dki, Oe, T);            // D_k^-1 O_e
+        mat_mul<B>(Dri, Oe, T);            // D_k^-1 O_e
         mat_tmul_sym<B>(Oe, T, U);         // O_e^T D_k^-1 O_e
 #pragma unroll
         for (int q = 0; q < B; ++q) w[q] = r[k * B + q];
-        mat_vec<B>(Dki, w, z);
+        mat_vec<B>(Dri, w, z);
         mat_tvec<B>(Oe, z, w);
 #pragma unroll
         for (int a = 0; a < B; ++a) {
@@ -553,12 +577,13 @@ __global__ void __launch_bounds__(128) k_btd_back(const double* __restrict__ Din
 #pragma unroll
             for (int q = 0; q < B; ++q) Ska[p][q] = -Ska[p][q];
     }
-    // S_kk = Dk^-1 - Ska Za^T - Skc Zc^T
+    // S_kk = Dk^-1 - Ska Za^T - Skc Zc^T: symmetric, so its upper triangle
+    // is computed and mirrored
     double Skk[B][B];
 #pragma unroll
     for (int p = 0; p < B; ++p)
 #pragma unroll
-        for (int q = 0; q < B; ++q) {
+        for (int q = p; q < B; ++q) {
             double s = Dki[p][q];
 #pragma unroll
             for (int m = 0; m < B; ++m) {
@@ -566,8 +591,8 @@ __global__ void __launch_bounds__(128) k_btd_back(const double* __restrict__ Din
                 if (hasc) s = fma(-Skc[p][m], Zc[q][m], s);
             }
             Skk[p][q] = s;
+            Skk[q][p] = s;
         }
-    symmetrize<B>(Skk);
     blk_store<B>(Sd + k * (B * B), Skk);
     blk_store<B>(So + a * (B * B), Ska);            // block (k, k-1)
     if (hasc) {
@@ -953,7 +978,7 @@ static int btd_core(int64_t n, const double* D, const double* O, const double* r
                 Dl, Ol, rl, lay.cnt[l - 1], lvl(lay.off_D, l), lvl(lay.off_O, l), lvl(lay.off_r, l), lay.cnt[l],
                 ld + ldo, lvl(lay.off_Dinv, l - 1), status);
         else
-            k_btd_reduce<B><<<(unsigned)((lay.cnt[l] + 127) / 128), 128, 0, st>>>(
+            k_btd_reduce<B><<<(unsigned)((lay.cnt[l] + BTD_CTA - 1) / BTD_CTA), BTD_CTA, 0, st>>>(
                 Dl, Ol, rl, lay.cnt[l - 1], lvl(lay.off_D, l), lvl(lay.off_O, l), lvl(lay.off_r, l), lay.cnt[l],
                 ld + ldo, lvl(lay.off_Dinv, l - 1), status);
         ldo += lay.cnt[l];

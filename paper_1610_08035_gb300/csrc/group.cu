@@ -847,6 +847,8 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
         double brate[NR / 2], benv[NR / 2];
 #pragma unroll
         for (int kb = 0; kb < NR / 2; ++kb) { brate[kb] = 0.0; benv[kb] = 0.0; }
+        // gp, geq and G below carry twice their values (the factor 1/2 of the
+        // adjoint is applied once per chunk, an exact power-of-two scaling)
         double gp = 0.0;   // diagonal entry 'lane' of the Pinf adjoint
         double geq = 0.0;  // column 'lane' of the Pinf adjoint contracted with the EQ block's P_m
         for (int64_t i = e - 1; i >= s; --i) {
@@ -896,20 +898,21 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                 }
             }
             const double lt = lh - (even ? al : 0.0);
+            // Lt = Lh - h u^T - u h^T + cc h h^T = Lh - h ub^T - ub h^T with ub = u - (cc / 2) h
+            const double ub = even ? fma(-0.5, cc, u) : u;
             double uv[GL], Lt[GL];
-            ggather<NR>(u, uv);
+            ggather<NR>(ub, uv);
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
                 double x = Lh[r];
-                if ((r & 1) == 0) x -= u;
+                if ((r & 1) == 0) x -= ub;
                 if (even) x -= uv[r];
-                if ((r & 1) == 0 && even) x += cc;
                 Lt[r] = x;
             }
             double lv[GL], G[GL];
             ggather<NR>(lt, lv);
 #pragma unroll
-            for (int r = 0; r < NR; ++r) G[r] = 0.5 * fma(lv[r], lt, -Lt[r]);
+            for (int r = 0; r < NR; ++r) G[r] = fma(lv[r], lt, -Lt[r]);   // 2 x the adjoint of Q
             if constexpr (GRAD) {
                 double gsel = 0.0;   // G[lane][lane]: a select, then one add
 #pragma unroll
@@ -924,7 +927,8 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                 const double* ph = a.phis + i * (4 * GK);
                 if constexpr (GRAD) {
                     const double dt = (i > 0) ? a.t[i] - a.t[i - 1] : a.t[0] - a.t_prev;
-                    // per block: 2 <G_k,:, X_k Db_k,:> (column 'lane' part) - lt_k^T X_k mb_k (row 'lane' part)
+                    // per block: 2 <G_k,:, X_k Db_k,:> (column 'lane' part) - lt_k^T X_k mb_k (row 'lane' part);
+                    // G holds 2 G, so the first term is <G_k,:, X_k Db_k,:>
                     const double mp = gxor(mb, 1);
                     const double mb0 = even ? mb : mp, mb1 = even ? mp : mb;
 #pragma unroll
@@ -937,20 +941,20 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                         double rate = 0.0, envr = 0.0;
                         if (kind == GB_MATERN32) {
                             // X = [[0, 1], [-1, -2]]
-                            rate = 2.0 * (g0 * d1 + g1 * (-d0 - 2.0 * d1));
+                            rate = g0 * d1 + g1 * (-d0 - 2.0 * d1);
                             if (mine) rate -= lt * (even ? mb1 : (-mb0 - 2.0 * mb1));
                         } else if (kind == GB_EQ) {
                             // X = [[a, b], [-b, a]] per unit of x = dt / l (rate 1 / l)
                             const double ea = a.gm.eqa[kb], eb = a.gm.eqb[kb];
-                            rate = 2.0 * (g0 * fma(ea, d0, eb * d1) + g1 * fma(-eb, d0, ea * d1));
+                            rate = g0 * fma(ea, d0, eb * d1) + g1 * fma(-eb, d0, ea * d1);
                             if (mine) rate -= lt * (even ? fma(ea, mb0, eb * mb1) : fma(-eb, mb0, ea * mb1));
                         } else {
                             // X = j [[0, -1], [1, 0]] (rotation rate w); envelope X = -I
                             const double jj = (double)a.gm.bj[kb];
-                            rate = jj * 2.0 * (g0 * (-d1) + g1 * d0);
+                            rate = jj * (g0 * (-d1) + g1 * d0);
                             if (mine) rate -= jj * lt * (even ? -mb1 : mb0);
                             if (kind == GB_QUASI) {
-                                envr = -2.0 * (g0 * d0 + g1 * d1);
+                                envr = -(g0 * d0 + g1 * d1);
                                 if (mine) envr += lt * (even ? mb0 : mb1);
                             }
                         }
@@ -969,14 +973,14 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
 #pragma unroll
                     for (int r = 0; r < NR; ++r)
                         if (r == lane) ld = Lh[r];
-                    gp -= 0.5 * fma(lh, lh, -ld);
-                    if (has_eq) {   // minus column 'lane' of Phi^T G Phi = (lh lh^T - Lh) / 2
+                    gp -= fma(lh, lh, -ld);
+                    if (has_eq) {   // minus column 'lane' of 2 Phi^T G Phi = lh lh^T - Lh
                         double lv2[GL];
                         ggather<NR>(lh, lv2);
                         double t = 0.0;
 #pragma unroll
                         for (int r = 0; r < NR; ++r) t = fma(s_dpe[r * GL + lane], fma(lv2[r], lh, -Lh[r]), t);
-                        geq -= 0.5 * t;
+                        geq -= t;
                     }
                 }
             }
@@ -990,8 +994,8 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                 for (int q = 0; q < GMAXCOMP; ++q)
                     if (q == cp) { acc[2 + 2 * q] += brate[kb]; acc[3 + 2 * q] += benv[kb]; }
             }
-            part[(2 + 2 * GMAXCOMP + lane) * nc + c] = gp;
-            geq = gsum(geq);
+            part[(2 + 2 * GMAXCOMP + lane) * nc + c] = 0.5 * gp;
+            geq = 0.5 * gsum(geq);
             if (lane == 0) part[GP_EQ * nc + c] = geq;
         }
     }
