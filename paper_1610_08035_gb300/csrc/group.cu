@@ -844,9 +844,32 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
         }
         // per-block sums of the rate terms (dt times d ll / dx), folded into
         // the component slots once per chunk
-        double brate[NR / 2], benv[NR / 2];
+        // - brate[kb]: the column part <G_k,:, X_k Db_k,:> over this lane's
+        //   column, without the harmonic number of a rotation block (applied
+        //   once per chunk); benv[kb]: <G_k,:, Db_k,:> (the envelope's X = -I,
+        //   sign applied once per chunk);
+        // - rmine, emine: the row part lt_k^T X_k mb_k (resp. lt_k^T mb_k) of
+        //   the lane's own block only, from the row of X_k that the lane holds
+        //   (xm0, xm1): one term per lane instead of one per block
+        double brate[NR / 2], benv[NR / 2], rmine = 0.0, emine = 0.0;
 #pragma unroll
         for (int kb = 0; kb < NR / 2; ++kb) { brate[kb] = 0.0; benv[kb] = 0.0; }
+        const int kbm = lane >> 1;
+        double xm0 = 0.0, xm1 = 0.0;
+#pragma unroll
+        for (int kb = 0; kb < NR / 2; ++kb) {
+            if (kb >= a.gm.K) break;
+            if (kb != kbm) continue;
+            const int kind = a.gm.bkind[kb];
+            if (kind == GB_MATERN32) {            // X = [[0, 1], [-1, -2]]
+                xm0 = even ? 0.0 : -1.0; xm1 = even ? 1.0 : -2.0;
+            } else if (kind == GB_EQ) {           // X = [[a, b], [-b, a]]
+                const double ea = a.gm.eqa[kb], eb = a.gm.eqb[kb];
+                xm0 = even ? ea : -eb; xm1 = even ? eb : ea;
+            } else {                              // X = j [[0, -1], [1, 0]], j applied per chunk
+                xm0 = even ? 0.0 : 1.0; xm1 = even ? -1.0 : 0.0;
+            }
+        }
         // gp, geq and G below carry twice their values (the factor 1/2 of the
         // adjoint is applied once per chunk, an exact power-of-two scaling)
         double gp = 0.0;   // diagonal entry 'lane' of the Pinf adjoint
@@ -931,35 +954,26 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                     // G holds 2 G, so the first term is <G_k,:, X_k Db_k,:>
                     const double mp = gxor(mb, 1);
                     const double mb0 = even ? mb : mp, mb1 = even ? mp : mb;
+                    const double tl = dt * lt;
+                    rmine = fma(tl, fma(xm0, mb0, xm1 * mb1), rmine);
+                    emine = fma(tl, mb, emine);
 #pragma unroll
                     for (int kb = 0; kb < NR / 2; ++kb) {
                         if (kb >= a.gm.K) break;
                         const int kind = a.gm.bkind[kb];
                         const double d0 = Db[2 * kb], d1 = Db[2 * kb + 1];
                         const double g0 = G[2 * kb], g1 = G[2 * kb + 1];
-                        const bool mine = (lane >> 1) == kb;
-                        double rate = 0.0, envr = 0.0;
                         if (kind == GB_MATERN32) {
-                            // X = [[0, 1], [-1, -2]]
-                            rate = g0 * d1 + g1 * (-d0 - 2.0 * d1);
-                            if (mine) rate -= lt * (even ? mb1 : (-mb0 - 2.0 * mb1));
+                            brate[kb] = fma(dt, fma(g1, fma(-2.0, d1, -d0), g0 * d1), brate[kb]);
                         } else if (kind == GB_EQ) {
                             // X = [[a, b], [-b, a]] per unit of x = dt / l (rate 1 / l)
                             const double ea = a.gm.eqa[kb], eb = a.gm.eqb[kb];
-                            rate = g0 * fma(ea, d0, eb * d1) + g1 * fma(-eb, d0, ea * d1);
-                            if (mine) rate -= lt * (even ? fma(ea, mb0, eb * mb1) : fma(-eb, mb0, ea * mb1));
+                            brate[kb] = fma(dt, g0 * fma(ea, d0, eb * d1) + g1 * fma(-eb, d0, ea * d1), brate[kb]);
                         } else {
                             // X = j [[0, -1], [1, 0]] (rotation rate w); envelope X = -I
-                            const double jj = (double)a.gm.bj[kb];
-                            rate = jj * (g0 * (-d1) + g1 * d0);
-                            if (mine) rate -= jj * lt * (even ? -mb1 : mb0);
-                            if (kind == GB_QUASI) {
-                                envr = -(g0 * d0 + g1 * d1);
-                                if (mine) envr += lt * (even ? mb0 : mb1);
-                            }
+                            brate[kb] = fma(dt, fma(g1, d0, -g0 * d1), brate[kb]);
+                            if (kind == GB_QUASI) benv[kb] = fma(dt, fma(g0, d0, g1 * d1), benv[kb]);
                         }
-                        brate[kb] = fma(rate, dt, brate[kb]);
-                        if (kind == GB_QUASI) benv[kb] = fma(envr, dt, benv[kb]);
                     }
                 }
                 // propagate to the previous step: lh = Phi^T lt, Lh = Phi^T Lt Phi
@@ -989,10 +1003,15 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
 #pragma unroll
             for (int kb = 0; kb < NR / 2; ++kb) {
                 if (kb >= a.gm.K) break;
+                const int kind = a.gm.bkind[kb];
+                double r = brate[kb], ev = -benv[kb];
+                if (kb == kbm) { r -= rmine; ev += emine; }
+                if (kind != GB_MATERN32 && kind != GB_EQ) r *= (double)a.gm.bj[kb];
+                if (kind != GB_QUASI) ev = 0.0;
                 const int cp = a.gm.bcomp[kb];
 #pragma unroll
                 for (int q = 0; q < GMAXCOMP; ++q)
-                    if (q == cp) { acc[2 + 2 * q] += brate[kb]; acc[3 + 2 * q] += benv[kb]; }
+                    if (q == cp) { acc[2 + 2 * q] += r; acc[3 + 2 * q] += ev; }
             }
             part[(2 + 2 * GMAXCOMP + lane) * nc + c] = 0.5 * gp;
             geq = 0.5 * gsum(geq);
