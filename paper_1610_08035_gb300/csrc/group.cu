@@ -725,7 +725,7 @@ __global__ void __launch_bounds__(GSC) k_gscan_down(const double* __restrict__ l
 
 // ------------------------------------------------------------------ k_gchunk: forward, reverse sweep
 
-static constexpr int GNF = GL + 3;   // stored per lane per step: predicted covariance column, mean entry, v, 1/S
+static constexpr int GNF = GL + 4;   // stored per lane per step: predicted covariance column, mean entry, v, 1/S, gain entry
 
 template <int MODE, int NR>
 __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restrict__ pre,
@@ -802,6 +802,7 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
             prod = __longlong_as_double((long long)((bits & 0x800FFFFFFFFFFFFFULL) | 0x3FF0000000000000ULL));
             ++nobs;
         }
+        const double pr = p0 * rS;   // the gain entry k = (Pb h)[lane] / S
         if constexpr (BWD) {
             double* st = store + ((j * nc + c) * GNF) * GL + lane;
 #pragma unroll
@@ -809,11 +810,11 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
             st[GL * GL] = mb;
             st[(GL + 1) * GL] = v;
             st[(GL + 2) * GL] = rS;
+            st[(GL + 3) * GL] = pr;
         }
         double pv[GL];
         ggather<NR>(p0, pv);
         m = fma(p0, v * rS, mb);
-        const double pr = p0 * rS;
 #pragma unroll
         for (int r = 0; r < NR; ++r) D[r] = fma(-pv[r], pr, Db[r]);
     }
@@ -883,7 +884,7 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
             const double mb = st[GL * GL];
             const double v = st[(GL + 1) * GL];
             const double rS = st[(GL + 2) * GL];
-            const double k = (g_hsum<NR>(Db) + ph) * rS;
+            const double k = st[(GL + 3) * GL];
             const double kl = gsum(k * lh);
             double kv[GL];
             ggather<NR>(k, kv);
