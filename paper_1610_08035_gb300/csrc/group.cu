@@ -488,6 +488,7 @@ struct GScanSmem {
     double N[GSC], M[GSC], T[GSC], U[GSC];
     double bv[GL], eta[GL], bv2[GL], eta2[GL], v[GL], w[GL], z[GL];
     int piv;
+    double inv;                       // 1 / pivot
 };
 
 __device__ __forceinline__ void gc_load_elem(const double* __restrict__ base, int64_t ne, int64_t e, double* A,
@@ -556,14 +557,21 @@ __device__ void gc_inv_ixy(GScanSmem& s, const double* X, const double* Y) {
     __syncthreads();
 #pragma unroll 1
     for (int k = 0; k < GL; ++k) {
-        if (t == 0) {
-            int p = k;
-            double best = fabs(s.N[k * GL + k]);
-            for (int i = k + 1; i < GL; ++i) {
-                const double v = fabs(s.N[i * GL + k]);
-                if (v > best) { best = v; p = i; }
+        // the pivot row over 16 lanes (largest |N[i][k]|, i >= k, the first on
+        // ties), and its reciprocal, once for the block
+        if (t < GL) {
+            double best = (t >= k) ? fabs(s.N[t * GL + k]) : -1.0;
+            int p = t;
+#pragma unroll
+            for (int off = 8; off > 0; off >>= 1) {
+                const double ob = __shfl_down_sync(0x0000ffffu, best, off, GL);
+                const int op = __shfl_down_sync(0x0000ffffu, p, off, GL);
+                if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
             }
-            s.piv = p;
+            if (t == 0) {
+                s.piv = p;
+                s.inv = 1.0 / s.N[p * GL + k];
+            }
         }
         __syncthreads();
         const int p = s.piv;
@@ -575,7 +583,7 @@ __device__ void gc_inv_ixy(GScanSmem& s, const double* X, const double* Y) {
             X2[p * GL + cc] = u;
         }
         __syncthreads();
-        const double inv = 1.0 / s.N[k * GL + k];
+        const double inv = s.inv;
         const double f = s.N[r * GL + k];
         const double nk = s.N[k * GL + c] * inv, mk = s.M[k * GL + c] * inv;
         __syncthreads();
