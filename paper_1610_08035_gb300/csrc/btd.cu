@@ -123,11 +123,14 @@ __global__ void __launch_bounds__(ASM_CTA) k_assemble(const double* __restrict__
     constexpr int BB = B * B;
     __shared__ double s_qi[ASM_CTA * BB];
     __shared__ double s_ld[ASM_CTA];
+    __shared__ double s_loglam;
     const int j = threadIdx.x;
     const int64_t i = blockIdx.x * (int64_t)ASM_CTA + j;
     const bool valid = i < n;
     const double ell = theta[0], sf = theta[1], s2 = theta[2];
     const double lam = sqrt(2.0 * B - 1.0) / ell;
+    const double il = ell * (1.0 / sqrt(2.0 * B - 1.0));   // 1 / lam
+    if (j == 0) s_loglam = log(lam);                      // once per block
     int bad = 0;
     // the transition out of step i (i -> i+1)
     const bool hasn = valid && i + 1 < n;
@@ -176,30 +179,31 @@ __global__ void __launch_bounds__(ASM_CTA) k_assemble(const double* __restrict__
 #pragma unroll
             for (int q = 0; q < B; ++q) { Dt[r][q] += U[r][q]; Ot[r][q] = -T[r][q]; }
     }
-    Dt[0][0] += 1.0 / s2;
-    // back to the paper's coordinates
-    double lp[B];
-    lp[0] = 1.0;
+    const double is2 = 1.0 / s2;
+    Dt[0][0] += is2;
+    // back to the paper's coordinates: entry (r, q) scaled by lam^-(r+q)
+    double pw[2 * B - 1];
+    pw[0] = 1.0;
 #pragma unroll
-    for (int r = 1; r < B; ++r) lp[r] = lp[r - 1] / lam;
+    for (int k = 1; k < 2 * B - 1; ++k) pw[k] = pw[k - 1] * il;
     double* Dp = Dout + i * (B * B);
 #pragma unroll
     for (int r = 0; r < B; ++r)
 #pragma unroll
-        for (int q = 0; q < B; ++q) Dp[r * B + q] = Dt[r][q] * lp[r] * lp[q];
+        for (int q = 0; q < B; ++q) Dp[r * B + q] = Dt[r][q] * pw[r + q];
     if (hasn) {
         double* Op = Oout + i * (B * B);
 #pragma unroll
         for (int r = 0; r < B; ++r)
 #pragma unroll
-            for (int q = 0; q < B; ++q) Op[r * B + q] = Ot[r][q] * lp[r] * lp[q];
+            for (int q = 0; q < B; ++q) Op[r * B + q] = Ot[r][q] * pw[r + q];
     }
     double* rp = rout + i * B;
-    rp[0] = y[i] / s2;
+    rp[0] = y[i] * is2;
 #pragma unroll
     for (int r = 1; r < B; ++r) rp[r] = 0.0;
     // log det Q (paper coordinates) = log det Qt + 2 sum_r r log lam
-    ldpart[i] = -(ldq_prev + (double)(B * (B - 1)) * log(lam));
+    ldpart[i] = -(ldq_prev + (double)(B * (B - 1)) * s_loglam);
     if (bad) atomicOr(status, bad);
 }
 
@@ -741,9 +745,12 @@ template <int B>
 __device__ __forceinline__ double quad(const double (&u)[B], const double (&X)[B][B], const double (&v)[B]) {
     double s = 0.0;
 #pragma unroll
-    for (int r = 0; r < B; ++r)
+    for (int r = 0; r < B; ++r) {
+        double w = 0.0;
 #pragma unroll
-        for (int q = 0; q < B; ++q) s = fma(u[r] * X[r][q], v[q], s);
+        for (int q = 0; q < B; ++q) w = fma(X[r][q], v[q], w);
+        s = fma(u[r], w, s);
+    }
     return s;
 }
 
@@ -780,6 +787,8 @@ __global__ void __launch_bounds__(ASM_CTA) k_literal_terms(const double* __restr
     const bool valid = i < n;
     const double ell = theta[0], sf = theta[1], s2 = theta[2];
     const double lam = sqrt(2.0 * B - 1.0) / ell;
+    const double il = ell * (1.0 / sqrt(2.0 * B - 1.0));   // 1 / lam
+    const double is2 = 1.0 / s2;
     double Ph[B][B], Qn[B][B], dQn[B][B], dQin[B][B];
     const bool hasn = valid && i + 1 < n;
     if constexpr (GRAD) {
@@ -798,15 +807,15 @@ __global__ void __launch_bounds__(ASM_CTA) k_literal_terms(const double* __restr
     }
     if (!valid) return;
     const double yi = y[i], x0 = x[i * B];
-    part[i] = yi * yi / s2;
-    part[n + i] = yi * x0 / s2;
+    part[i] = yi * yi * is2;
+    part[n + i] = yi * x0 * is2;
     if (mean) mean[i] = x0;
     if (var) var[i] = Sd[i * (B * B)];
     if constexpr (GRAD) {
         double lp[B];
         lp[0] = 1.0;
 #pragma unroll
-        for (int r = 1; r < B; ++r) lp[r] = lp[r - 1] / lam;
+        for (int r = 1; r < B; ++r) lp[r] = lp[r - 1] * il;
         double xi[B], xn[B], Si[B][B], Sn[B][B];
 #pragma unroll
         for (int r = 0; r < B; ++r) {
@@ -827,7 +836,7 @@ __global__ void __launch_bounds__(ASM_CTA) k_literal_terms(const double* __restr
             for (int r = 0; r < B; ++r)
 #pragma unroll
                 for (int q = 0; q < B; ++q) YD[r][q] = 0.0;
-            dld_l = -(double)(B * (B - 1)) / lam;
+            dld_l = -(double)(B * (B - 1)) * il;
         } else {
             const double dp = t[i] - t[i - 1];
             double dQ[B][B], dQi[B][B];
@@ -848,7 +857,7 @@ __global__ void __launch_bounds__(ASM_CTA) k_literal_terms(const double* __restr
             for (int r = 0; r < B; ++r)
 #pragma unroll
                 for (int q = 0; q < B; ++q) YD[r][q] = dp * dQi[r][q];
-            dld_l = -(dp * frob<B>(Dt, dQ) + (double)(B * (B - 1)) / lam);   // tr(Qt^-1 dQt), both symmetric
+            dld_l = -(dp * frob<B>(Dt, dQ) + (double)(B * (B - 1)) * il);   // tr(Qt^-1 dQt), both symmetric
         }
 #pragma unroll
         for (int r = 0; r < B; ++r)
@@ -887,18 +896,18 @@ __global__ void __launch_bounds__(ASM_CTA) k_literal_terms(const double* __restr
         for (int r = 0; r < B; ++r)
 #pragma unroll
             for (int q = 0; q < B; ++q) {
-                YD[r][q] -= (double)(r + q) / lam * Dt[r][q];
-                YO[r][q] -= (double)(r + q) / lam * Ot[r][q];
+                YD[r][q] = fma(-(double)(r + q) * il, Dt[r][q], YD[r][q]);
+                YO[r][q] = fma(-(double)(r + q) * il, Ot[r][q], YO[r][q]);
             }
         const double g_lam = -0.5 * quad<B>(xi, YD, xi) - quad<B>(xn, YO, xi) - 0.5 * frob<B>(Si, YD) -
                              frob<B>(Sn, YO) + 0.5 * dld_l;
         // s_f: Kinv is proportional to 1 / s_f
         const double g_sf = (0.5 * quad<B>(xi, Dt, xi) + quad<B>(xn, Ot, xi) + 0.5 * frob<B>(Si, Dt) +
-                             frob<B>(Sn, Ot) - 0.5 * (double)B) / sf;
+                             frob<B>(Sn, Ot) - 0.5 * (double)B) * (1.0 / sf);
         const double e0 = yi - x0;
-        part[2 * n + i] = g_lam * (-lam / ell);
+        part[2 * n + i] = g_lam * (-lam * (1.0 / ell));
         part[3 * n + i] = g_sf;
-        part[4 * n + i] = 0.5 * (e0 * e0 + Sd[i * (B * B)]) / (s2 * s2) - 0.5 / s2;
+        part[4 * n + i] = fma(0.5 * (e0 * e0 + Sd[i * (B * B)]), is2 * is2, -0.5 * is2);
     }
 }
 
