@@ -330,10 +330,10 @@ def batched_oracle_rate(s, n_series=1024):
 # instructions; instructions = everything the FP64 pipe executed.  Units:
 # steps, or nodes for the BTD solver; the batched SCG's gradient evaluations
 # use the chain kernels' counts above.
-NEXT_FLOPS_PER_UNIT = {"prediction_n4m": 334.7, "literal_n1m": 2481.9, "btd_solve_n1m": 901.8,
-                       "eq_b12_n1m": 12896.7, "scg_batch_4096": 171.5 + 231.2}
-NEXT_FP64_INST_PER_UNIT = {"prediction_n4m": 232.4, "literal_n1m": 1673.5, "btd_solve_n1m": 563.2,
-                           "eq_b12_n1m": 8887.7, "scg_batch_4096": 107.1 + 141.6}
+NEXT_FLOPS_PER_UNIT = {"prediction_n4m": 334.7, "literal_n1m": 2157.0, "btd_solve_n1m": 821.6,
+                       "eq_b12_n1m": 11687.0, "scg_batch_4096": 171.5 + 231.2}
+NEXT_FP64_INST_PER_UNIT = {"prediction_n4m": 232.4, "literal_n1m": 1485.5, "btd_solve_n1m": 520.0,
+                           "eq_b12_n1m": 7555.9, "scg_batch_4096": 107.1 + 141.6}
 
 
 def _next_roofline(key, units_per_s, fp64_tflops):
