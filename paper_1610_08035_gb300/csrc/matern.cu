@@ -802,29 +802,41 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
                     for (int q = r; q < B; ++q) { Db[r][q] = sv[f++]; Db[q][r] = Db[r][q]; }
                 const double v = sv[f++];
                 const double rS = sv[f++];
+                // a missing step (posterior): k is taken as Pb e1, so kl and kuk
+                // below are the prediction's Pb_0^T lh and Pb_0^T Lh Pb_0; its
+                // adjoint then passes through unchanged (kl, kuk, u zeroed)
+                double yi = 0.0;
+                bool pmiss = false;
+                if constexpr (POST) {
+                    yi = a.y[i];
+                    pmiss = a.missing && is_nan_b(yi);
+                }
+                const double rk = pmiss ? 1.0 : rS;
                 double p0[B], k[B];
 #pragma unroll
-                for (int r = 0; r < B; ++r) { p0[r] = Db[r][0] + sp0[r]; k[r] = p0[r] * rS; }
+                for (int r = 0; r < B; ++r) { p0[r] = Db[r][0] + sp0[r]; k[r] = p0[r] * rk; }
                 double kl = 0.0, u[B], kuk = 0.0;
 #pragma unroll
                 for (int r = 0; r < B; ++r) kl = fma(k[r], lh[r], kl);
                 mat_vec<B>(Lh, k, u);
 #pragma unroll
                 for (int r = 0; r < B; ++r) kuk = fma(k[r], u[r], kuk);
+                if constexpr (POST) {
+                    if (pmiss) {
+                        // predicted only: mean = (mb - Pb lh)_0, variance = Pb_00 - Pb_0^T Lh Pb_0
+                        mean_out[i] = mb[0] - kl;
+                        var_out[i] = p0[0] - kuk;
+                        kl = 0.0;
+                        kuk = 0.0;
+#pragma unroll
+                        for (int r = 0; r < B; ++r) u[r] = 0.0;
+                    }
+                }
                 const double al = fma(v, rS, kl);     // (C^-1 y)_i
                 const double cc = rS + kuk;           // (C^-1)_ii
                 if constexpr (GRAD) gs = fma(al, al, gs) - cc;
                 if constexpr (POST) {
-                    const double yi = a.y[i];
-                    if (a.missing && is_nan_b(yi)) {
-                        // predicted only: mean = (mb - Pb lh)_0, variance = Pb_00 - Pb_0^T Lh Pb_0
-                        double w[B], pl = 0.0, q = 0.0;
-                        mat_vec<B>(Lh, p0, w);
-#pragma unroll
-                        for (int r = 0; r < B; ++r) { pl = fma(p0[r], lh[r], pl); q = fma(p0[r], w[r], q); }
-                        mean_out[i] = mb[0] - pl;
-                        var_out[i] = p0[0] - q;
-                    } else {
+                    if (!pmiss) {
                         mean_out[i] = fma(-s2, al, yi);
                         var_out[i] = s2 * k[0] - s2 * s2 * kuk;
                     }

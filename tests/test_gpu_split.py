@@ -122,3 +122,28 @@ def test_split_series_group_path(spec, theta, G):
     assert np.max(np.abs(g - g_w) / gscale) <= 1e-9
     assert abs(ll - llo) <= 1e-9 * abs(llo)
     assert np.max(np.abs(g - go) / gscale) <= 1e-8
+
+
+def test_split_series_group_path_uneven_ranges_and_missing():
+    """The group path with ranges of 1 step, shorter than a chunk, and long
+    ones, missing observations (one at a range boundary)."""
+    n = 9001
+    rng = np.random.default_rng(44)
+    t = synth.exp_times(n, 0.02, rng)
+    y = synth.two_sinusoids(t, 0.8, 1.0, 0.1, rng)
+    y[rng.random(n) < 0.1] = np.nan
+    y[4000] = np.nan
+    cuts = [0, 1, 2, 50, 4001, 4002, n]
+    ranges = list(zip(cuts[:-1], cuts[1:]))
+    spec, theta = GROUP[0]
+    m = spingp.Model(spec)
+    T, Y, TH = _t(t), _t(y), _t(theta)
+    ll_w, g_w = m.grad(T, Y, TH, missing=True)
+    ll_w, g_w = ll_w.item(), g_w.cpu().numpy()
+    ll, g = _split_grad(m, T, Y, TH, ranges, t, missing=True)
+    assert abs(ll - ll_w) <= 1e-11 * abs(ll_w)
+    llo, go, gabs = seq.grad(spec, theta, t, y, l1=True)
+    gscale = np.maximum(np.abs(go), gabs)
+    assert np.max(np.abs(g - g_w) / gscale) <= 1e-9
+    assert abs(ll - llo) <= 1e-9 * abs(llo)
+    assert np.max(np.abs(g - go) / gscale) <= 1e-8
