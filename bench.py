@@ -12,6 +12,7 @@ the ranks (one all-gather of the ranges' elements and one all-reduce per
 step, strong scaling), the time is the max over ranks and the value counts
 the series' steps once.  Extra keys: the roofline of the
 dominant kernel (live stage timing), the HBM roofline of the whole step, the
+median of CUDA-graph replays of the same call, the
 end-to-end figure through the public API with host buffers, the "plain GPU
 form" comparator (the forward kernel run 2P+1 times for central differences),
 the oracle timed on host cores, and SM clocks sampled during the timed region.
@@ -587,6 +588,36 @@ def main():
            "roofline": roof, "hbm_roofline": hbm, "stages_ms_per_call": stage_ms,
            "gpu_launches": spingp.spingp_launch_count(model.h, n, spingp.WS_GRAD) * K,
            "clocks": clk}
+
+    # ---- the same call captured once in a CUDA graph: the median of at least
+    # 20 replays, each timed alone with L2 flushed (untimed) before it
+    gstream = torch.cuda.Stream(device=dev)
+    gstream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(gstream):
+        model.grad(T, Y, TH, sync=False, out=(ll, g))
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=gstream):
+            model.grad(T, Y, TH, sync=False, out=(ll, g))
+    torch.cuda.current_stream().wait_stream(gstream)
+    torch.cuda.synchronize()
+    reps = max(K, 20)
+    gms = []
+    for k in range(reps):
+        flush.fill_(k & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        gms.append(e0.elapsed_time(e1))
+    st = spingp.spingp_ws_status(model.workspace(n, spingp.WS_GRAD, dev))
+    if st != spingp.OK:
+        raise spingp.SpinGPError(st, "graph replay")
+    gmed = float(np.median(gms))
+    out["graph_replay"] = {"value": world * n / (gmed * 1e-3), "unit": "steps/s", "ms_median": gmed,
+                           "replays": reps, "gpu_launches_per_replay": spingp.spingp_launch_count(
+                               model.h, n, spingp.WS_GRAD)}
+    del graph
 
     # ---- end to end through the public API: pinned host buffers in (the
     # library overlaps their copy with the elimination), results to the host,
