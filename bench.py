@@ -332,9 +332,9 @@ def batched_oracle_rate(s, n_series=1024):
 # steps, or nodes for the BTD solver; the batched SCG's gradient evaluations
 # use the chain kernels' counts above.
 NEXT_FLOPS_PER_UNIT = {"prediction_n4m": 344.2, "literal_n1m": 2157.0, "btd_solve_n1m": 821.6,
-                       "eq_b12_n1m": 11687.0, "scg_batch_4096": 171.5 + 231.2}
+                       "eq_b12_n1m": 11627.0, "scg_batch_4096": 171.5 + 231.2}
 NEXT_FP64_INST_PER_UNIT = {"prediction_n4m": 226.0, "literal_n1m": 1485.5, "btd_solve_n1m": 520.0,
-                           "eq_b12_n1m": 7555.9, "scg_batch_4096": 107.1 + 141.6}
+                           "eq_b12_n1m": 7523.9, "scg_batch_4096": 107.1 + 141.6}
 
 
 def _next_roofline(key, units_per_s, fp64_tflops):

@@ -157,11 +157,18 @@ __global__ void __launch_bounds__(256) k_gdisc(GModel gm, const double* __restri
     const double dt = (i > 0) ? t[i] - t[i - 1] : (s0 < 0 ? t[0] - t_prev : 0.0);
     if (dt < 0.0) bad |= ST_ENOTSORTED;
     double* ph = phis + i * (4 * GK);
+    // per component, once: x = dt / l of the EQ blocks; the rotation by w dt
+    // and the envelope of a (quasi-)periodic component, whose harmonic j + 1
+    // follows from harmonic j by angle addition (its blocks come in order
+    // j = 0, 1, .., J)
+    int pc = -1, pj = -1;
+    double xe = 0.0, wdt = 0.0, c1 = 1.0, s1 = 0.0, cj = 1.0, sj = 0.0, env = 1.0;
 #pragma unroll 1
     for (int k = 0; k < GK; ++k) {
         double p00 = 0.0, p01 = 0.0, p10 = 0.0, p11 = 0.0;
         if (k < gm.K) {
-            const double* th = theta + gm.cpoff[gm.bcomp[k]];
+            const int comp = gm.bcomp[k];
+            const double* th = theta + gm.cpoff[comp];
             if (gm.bkind[k] == GB_MATERN32) {
                 const double lam = sqrt(3.0) / th[0];
                 double P[2][2];
@@ -169,18 +176,34 @@ __global__ void __launch_bounds__(256) k_gdisc(GModel gm, const double* __restri
                 p00 = P[0][0]; p01 = P[0][1]; p10 = P[1][0]; p11 = P[1][1];
             } else if (gm.bkind[k] == GB_EQ) {
                 // expm([[a, b], [-b, a]] x) = e^(a x) [[cos bx, sin bx], [-sin bx, cos bx]], x = dt / l
-                const double x = dt / th[0];
+                if (comp != pc) xe = dt / th[0];
                 double sn, cs;
-                sincos(gm.eqb[k] * x, &sn, &cs);
-                const double e = exp(gm.eqa[k] * x);
+                sincos(gm.eqb[k] * xe, &sn, &cs);
+                const double e = exp(gm.eqa[k] * xe);
                 p00 = e * cs; p01 = e * sn; p10 = -e * sn; p11 = e * cs;
             } else {
-                const double w = 2.0 * M_PI / th[2];
-                double sn, cs;
-                sincos(gm.bj[k] * w * dt, &sn, &cs);
-                const double env = (gm.bkind[k] == GB_QUASI) ? exp(-dt / th[3]) : 1.0;
-                p00 = env * cs; p01 = -env * sn; p10 = env * sn; p11 = env * cs;
+                const int j = gm.bj[k];
+                if (comp != pc) {
+                    wdt = (2.0 * M_PI / th[2]) * dt;
+                    sincos(wdt, &s1, &c1);
+                    env = (gm.bkind[k] == GB_QUASI) ? exp(-dt / th[3]) : 1.0;
+                    pj = -1;
+                }
+                if (j == 0) {
+                    cj = 1.0; sj = 0.0;
+                } else if (j == 1) {
+                    cj = c1; sj = s1;
+                } else if (j == pj + 1) {   // cos, sin of (j - 1 + 1) w dt
+                    const double cn = fma(cj, c1, -sj * s1);
+                    sj = fma(sj, c1, cj * s1);
+                    cj = cn;
+                } else {
+                    sincos(j * wdt, &sj, &cj);
+                }
+                pj = j;
+                p00 = env * cj; p01 = -env * sj; p10 = env * sj; p11 = env * cj;
             }
+            pc = comp;
         }
         ph[4 * k + 0] = p00; ph[4 * k + 1] = p01; ph[4 * k + 2] = p10; ph[4 * k + 3] = p11;
     }
