@@ -516,21 +516,21 @@ spingp_status spingp_grad_host(spingp_model* m, const double* t, const double* y
     const size_t o_t = hostws_chain(m, n), o_y = o_t + align256c(sizeof(double) * (size_t)n);
     const size_t o_th = o_y + align256c(sizeof(double) * (size_t)n), o_out = o_th + align256c(sizeof(double) * 64);
     double *td = (double*)(w + o_t), *yd = (double*)(w + o_y), *thd = (double*)(w + o_th), *od = (double*)(w + o_out);
-    if (cudaMemcpyAsync(thd, theta, sizeof(double) * m->P, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return SPINGP_ECUDA;
     cudaEvent_t* ev = NULL;
     if ((st = profile_slot(m, &ev)) != SPINGP_OK) return st;
     const int miss = (flags & SPINGP_MISSING_NAN) ? 1 : 0;
     const int64_t L = chunk_len(m, n);
     int rc;
     if (m->group) {
-        if (cudaMemcpyAsync(td, t, sizeof(double) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        if (cudaMemcpyAsync(thd, theta, sizeof(double) * m->P, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(td, t, sizeof(double) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(yd, y, sizeof(double) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
             return SPINGP_ECUDA;
         rc = spg::group_run(m->gm, spg::MODE_GRAD, td, yd, n, L, thd, od, od + 1, NULL, NULL, ws, s, ev, miss);
     } else {
         spg::HostFeed f;
         f.t = t; f.y = y; f.copy = m->feed_copy; f.npieces = spg::FEED_PIECES;
+        f.theta_h = theta; f.theta_bytes = sizeof(double) * m->P;   // on the copy stream, ahead of t
         for (int i = 0; i <= spg::FEED_PIECES; ++i) f.ev[i] = m->feed_ev[i];
         rc = spg::matern_run(m->b, spg::MODE_GRAD, td, yd, n, L, thd, od, od + 1, NULL, NULL, ws, s, ev, miss, &f);
     }

@@ -42,11 +42,14 @@ int matern_prepare();
 // columns of every chunk, the widths doubling from L/16 -- and the
 // elimination runs as one launch per piece on the main stream, each after its
 // piece's copy.  ev[0] orders the copies after earlier work on the main
-// stream, ev[1 + p] marks piece p's copy.
+// stream, ev[1 + p] marks piece p's copy.  theta_h (host, theta_bytes) is
+// copied to the run's theta on the copy stream ahead of piece 0.
 static constexpr int FEED_PIECES = 4;
 struct HostFeed {
     const double* t;
     const double* y;
+    const double* theta_h;
+    size_t theta_bytes;
     cudaStream_t copy;
     cudaEvent_t ev[1 + FEED_PIECES];
     int npieces;

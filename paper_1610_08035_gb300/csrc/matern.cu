@@ -1190,6 +1190,9 @@ int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t 
         const int64_t nfull = n / L, tail = n - nfull * L;
         if (cudaEventRecord(feed->ev[0], st) != cudaSuccess) return 1;
         if (cudaStreamWaitEvent(feed->copy, feed->ev[0], 0) != cudaSuccess) return 1;
+        if (feed->theta_h && cudaMemcpyAsync(const_cast<double*>(theta), feed->theta_h, feed->theta_bytes,
+                                             cudaMemcpyHostToDevice, feed->copy) != cudaSuccess)
+            return 1;
         for (int64_t p = 0; p < np; ++p) {
             const int64_t c0 = bnd[p], c1 = bnd[p + 1];
             const bool prev = (p == 0 && c1 < L);   // piece 0 also copies column L-1 of the row before
