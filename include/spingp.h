@@ -105,6 +105,18 @@ typedef enum { SPINGP_WS_LOGLIK = 0, SPINGP_WS_GRAD = 1, SPINGP_WS_POSTERIOR = 2
  * log-likelihoods and gradients then cover the observed points only.  Without
  * this flag a NaN observation is an error (SPINGP_ENONFINITE). */
 #define SPINGP_MISSING_NAN 2u
+/* Return the gradient with respect to log theta instead of theta:
+ * d ll / d log theta_p = theta_p d ll / d theta_p (a diagonal rescaling; the
+ * paper's hyperparameters are positive).  Honoured by spingp_grad,
+ * spingp_grad_batched, spingp_grad_host and spingp_segment_grad (each rank's
+ * share is rescaled; the shares still sum to the series' value); one more
+ * kernel launch per call. */
+#define SPINGP_LOG_GRAD 4u
+/* Return predictive variances of an observation instead of latent ones: the
+ * latent variance H P^s H^T plus the noise variance s_n (the series' last
+ * theta entry).  Honoured by spingp_posterior and spingp_posterior_batched;
+ * one more kernel launch per call. */
+#define SPINGP_PREDICTIVE 8u
 
 /* Create a model handle from a host-side description (Sec. 2.1).  The handle
  * holds host constants only; it owns no device memory.  Returns EINVAL for a

@@ -173,8 +173,10 @@ spingp_status run(const spingp_model* m, int mode, const double* t, const double
     st = profile_slot(m, &ev);
     if (st != SPINGP_OK) return st;
     const int miss = (flags & SPINGP_MISSING_NAN) ? 1 : 0;
-    const int rc = m->group ? spg::group_run(m->gm, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s, ev, miss)
-                            : spg::matern_run(m->b, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s, ev, miss);
+    int rc = m->group ? spg::group_run(m->gm, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s, ev, miss)
+                      : spg::matern_run(m->b, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s, ev, miss);
+    if (!rc && grad && (flags & SPINGP_LOG_GRAD)) rc = spg::grad_to_log(grad, theta, m->P, s);
+    if (!rc && var && (flags & SPINGP_PREDICTIVE)) rc = spg::add_noise(var, n, theta + m->P - 1, s);
     if (rc) return SPINGP_ECUDA;
     if (flags & SPINGP_SYNC) return spingp_ws_status(ws, stream);
     return SPINGP_OK;
@@ -212,6 +214,9 @@ spingp_status run_batched(const spingp_model* m, int mode, const int64_t* offset
     if (st != SPINGP_OK) return st;
     if (spg::matern_run_batched(m->b, mode, offsets, n_series, n_total, t, y, L, theta, ll, grad, mean, var, ws, s,
                                 ev, (flags & SPINGP_MISSING_NAN) ? 1 : 0))
+        return SPINGP_ECUDA;
+    if (grad && (flags & SPINGP_LOG_GRAD) && spg::grad_to_log(grad, theta, n_series * m->P, s)) return SPINGP_ECUDA;
+    if (var && (flags & SPINGP_PREDICTIVE) && spg::add_noise_batched(var, offsets, n_series, theta, m->P, s))
         return SPINGP_ECUDA;
     if (flags & SPINGP_SYNC) return spingp_ws_status(ws, stream);
     return SPINGP_OK;
@@ -445,10 +450,12 @@ static spingp_status segment_call(const spingp_model* m, int phase, const double
     if (st != SPINGP_OK) return st;
     const int miss = (flags & SPINGP_MISSING_NAN) ? 1 : 0;
     const double tp = first ? 0.0 : t_prev;
-    const int rc = m->group ? spg::group_segment(m->gm, phase, t, y, n, L, theta, tp, first ? 1 : 0, elems, n_ranks,
-                                                 rank, elem_out, ll_out, grad_out, ws, (cudaStream_t)stream, miss)
-                            : spg::matern_segment(m->b, phase, t, y, n, L, theta, tp, first ? 1 : 0, elems, n_ranks,
-                                                  rank, elem_out, ll_out, grad_out, ws, (cudaStream_t)stream, miss);
+    int rc = m->group ? spg::group_segment(m->gm, phase, t, y, n, L, theta, tp, first ? 1 : 0, elems, n_ranks,
+                                           rank, elem_out, ll_out, grad_out, ws, (cudaStream_t)stream, miss)
+                      : spg::matern_segment(m->b, phase, t, y, n, L, theta, tp, first ? 1 : 0, elems, n_ranks,
+                                            rank, elem_out, ll_out, grad_out, ws, (cudaStream_t)stream, miss);
+    // the shares are linear in the gradient, so each scales on its own
+    if (!rc && grad_out && (flags & SPINGP_LOG_GRAD)) rc = spg::grad_to_log(grad_out, theta, m->P, (cudaStream_t)stream);
     if (rc) return SPINGP_ECUDA;
     if (flags & SPINGP_SYNC) return spingp_ws_status(ws, stream);
     return SPINGP_OK;
@@ -534,6 +541,7 @@ spingp_status spingp_grad_host(spingp_model* m, const double* t, const double* y
         for (int i = 0; i <= spg::FEED_PIECES; ++i) f.ev[i] = m->feed_ev[i];
         rc = spg::matern_run(m->b, spg::MODE_GRAD, td, yd, n, L, thd, od, od + 1, NULL, NULL, ws, s, ev, miss, &f);
     }
+    if (!rc && (flags & SPINGP_LOG_GRAD)) rc = spg::grad_to_log(od + 1, thd, m->P, s);
     if (rc) return SPINGP_ECUDA;
     if (cudaMemcpyAsync(ll_out, od, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(grad_out, od + 1, sizeof(double) * m->P, cudaMemcpyDeviceToHost, s) != cudaSuccess)

@@ -58,6 +58,12 @@ int matern_run(int b, int mode, const double* t, const double* y, int64_t n, int
                double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws, cudaStream_t st,
                cudaEvent_t* ev, int missing, const HostFeed* feed = nullptr);
 int matern_launch_count(int b, int64_t n, int64_t L, int mode);
+// output conventions by flag (post.cu): the gradient in log theta (count
+// entries, theta in the same layout), predictive variances (latent + s_n)
+int grad_to_log(double* grad, const double* theta, int64_t count, cudaStream_t st);
+int add_noise(double* var, int64_t n, const double* s_n, cudaStream_t st);
+int add_noise_batched(double* var, const int64_t* offsets, int64_t n_series, const double* theta, int P,
+                      cudaStream_t st);
 // a series split across ranks (phase 0: reduce this range to its element;
 // phase 1: from all G elements, this range's share of ll and gradient)
 static constexpr int SEG_MAX_RANKS = 32;

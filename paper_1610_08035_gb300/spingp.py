@@ -17,6 +17,8 @@ OK, EINVAL, ENOTSORTED, ENONFINITE, ENUMERIC, ECUDA, ETIMEOUT, ENOMEM, EUNSUPPOR
 WS_LOGLIK, WS_GRAD, WS_POSTERIOR = 0, 1, 2
 SYNC = 1
 MISSING_NAN = 2
+LOG_GRAD = 4      # gradient with respect to log theta
+PREDICTIVE = 8    # posterior variances of an observation (latent + noise variance)
 
 KINDS = {"matern12": 1, "matern32": 2, "matern52": 3, "periodic": 4, "quasiperiodic": 5, "eq": 6}
 
@@ -465,8 +467,9 @@ class Model:
         return t.numel()
 
     @staticmethod
-    def _flags(sync, missing):
-        return (SYNC if sync else 0) | (MISSING_NAN if missing else 0)
+    def _flags(sync, missing, log_params=False, predictive=False):
+        return ((SYNC if sync else 0) | (MISSING_NAN if missing else 0) | (LOG_GRAD if log_params else 0)
+                | (PREDICTIVE if predictive else 0))
 
     def loglik(self, t, y, theta, sync=True, out=None, missing=False):
         n = self._args(t, y, theta)
@@ -476,7 +479,8 @@ class Model:
                "spingp_loglik")
         return ll
 
-    def grad(self, t, y, theta, sync=True, out=None, missing=False):
+    def grad(self, t, y, theta, sync=True, out=None, missing=False, log_params=False):
+        """(ll, d ll / d theta); with log_params, d ll / d log theta."""
         n = self._args(t, y, theta)
         ws = self.workspace(n, WS_GRAD, t.device)
         if out is None:
@@ -484,11 +488,11 @@ class Model:
             g = torch.empty(self.num_params, dtype=torch.float64, device=t.device)
         else:
             ll, g = out
-        _check(spingp_grad(self.h, t, y, n, theta, ll, g, ws, ws.numel(), self._flags(sync, missing)),
+        _check(spingp_grad(self.h, t, y, n, theta, ll, g, ws, ws.numel(), self._flags(sync, missing, log_params)),
                "spingp_grad")
         return ll, g
 
-    def grad_host(self, t, y, theta, sync=True, out=None, missing=False, device=None):
+    def grad_host(self, t, y, theta, sync=True, out=None, missing=False, device=None, log_params=False):
         """spingp_grad from host (CPU) tensors: t, y, theta float64 on the
         host (pin them for overlapped copies); returns host (ll, grad)."""
         for name, v in (("t", t), ("y", y), ("theta", theta)):
@@ -509,8 +513,8 @@ class Model:
             g = torch.empty(self.num_params, dtype=torch.float64).pin_memory()
         else:
             ll, g = out
-        _check(spingp_grad_host(self.h, t, y, n, theta, ll, g, ws, ws.numel(), self._flags(sync, missing)),
-               "spingp_grad_host")
+        _check(spingp_grad_host(self.h, t, y, n, theta, ll, g, ws, ws.numel(),
+                                self._flags(sync, missing, log_params)), "spingp_grad_host")
         return ll, g
 
     def segment_reduce(self, t, y, theta, t_prev=None, ws=None, sync=True, missing=False):
@@ -527,7 +531,8 @@ class Model:
                                      self._flags(sync, missing)), "spingp_segment_reduce")
         return elem
 
-    def segment_grad(self, t, y, theta, elems, rank, t_prev=None, ws=None, sync=True, missing=False):
+    def segment_grad(self, t, y, theta, elems, rank, t_prev=None, ws=None, sync=True, missing=False,
+                     log_params=False):
         """Phase 2: this range's share of (ll, grad) from all ranks' elements
         (device, n_ranks x elem_size, rank order); the same arguments and
         workspace as segment_reduce."""
@@ -539,29 +544,34 @@ class Model:
         g = torch.empty(self.num_params, dtype=torch.float64, device=t.device)
         first = t_prev is None
         _check(spingp_segment_grad(self.h, t, y, n, theta, 0.0 if first else t_prev, first, elems, elems.shape[0],
-                                   rank, ll, g, ws, ws.numel(), self._flags(sync, missing)), "spingp_segment_grad")
+                                   rank, ll, g, ws, ws.numel(), self._flags(sync, missing, log_params)),
+               "spingp_segment_grad")
         return ll, g
 
-    def posterior(self, t, y, theta, sync=True, with_loglik=True, missing=False):
+    def posterior(self, t, y, theta, sync=True, with_loglik=True, missing=False, predictive=False):
+        """(mean, var, ll): latent posterior mean and variance at t; with
+        predictive, var is the variance of an observation there (+ s_n)."""
         n = self._args(t, y, theta)
         ws = self.workspace(n, WS_POSTERIOR, t.device)
         mean = torch.empty(n, dtype=torch.float64, device=t.device)
         var = torch.empty(n, dtype=torch.float64, device=t.device)
         ll = torch.empty(1, dtype=torch.float64, device=t.device) if with_loglik else None
         _check(spingp_posterior(self.h, t, y, n, theta, ll, mean, var, ws, ws.numel(),
-                                self._flags(sync, missing)), "spingp_posterior")
+                                self._flags(sync, missing, predictive=predictive)), "spingp_posterior")
         return mean, var, ll
 
-    def predict(self, t, y, theta, t_star):
+    def predict(self, t, y, theta, t_star, predictive=False):
         """Latent predictive mean and variance at new times t_star (Eqs.
         mean4-mean6): the test times join the chain with missing (NaN)
         observations, one posterior pass covers both.  t must be sorted;
-        t_star may be in any order.  Returns (mean, var) at t_star."""
+        t_star may be in any order.  Returns (mean, var) at t_star; with
+        predictive, var is that of a new observation (+ s_n)."""
         _dev_f64(t_star, "t_star")
         t_all = torch.cat([t, t_star])
         y_all = torch.cat([y, torch.full_like(t_star, float("nan"))])
         t_sorted, order = torch.sort(t_all, stable=True)
-        mean, var, _ = self.posterior(t_sorted, y_all[order].contiguous(), theta, with_loglik=False, missing=True)
+        mean, var, _ = self.posterior(t_sorted, y_all[order].contiguous(), theta, with_loglik=False, missing=True,
+                                      predictive=predictive)
         where = torch.empty_like(order)
         where[order] = torch.arange(order.numel(), device=order.device)
         idx = where[t.numel():]
@@ -710,7 +720,7 @@ class Batch:
                "spingp_loglik_batched")
         return ll
 
-    def grad(self, theta, sync=True, out=None, missing=False):
+    def grad(self, theta, sync=True, out=None, missing=False, log_params=False):
         ws = self.workspace(WS_GRAD)
         if out is None:
             ll = torch.empty(self.n_series, dtype=torch.float64, device=self.t.device)
@@ -718,11 +728,11 @@ class Batch:
         else:
             ll, g = out
         _check(spingp_grad_batched(self.model.h, self.offsets, self.n_series, self.n_total, self.t, self.y,
-                                   self._theta(theta), ll, g, ws, ws.numel(), Model._flags(sync, missing)),
-               "spingp_grad_batched")
+                                   self._theta(theta), ll, g, ws, ws.numel(),
+                                   Model._flags(sync, missing, log_params)), "spingp_grad_batched")
         return ll, g.view(self.n_series, self.model.num_params)
 
-    def posterior(self, theta, sync=True, missing=False):
+    def posterior(self, theta, sync=True, missing=False, predictive=False):
         ws = self.workspace(WS_POSTERIOR)
         dev = self.t.device
         mean = torch.empty(self.n_total, dtype=torch.float64, device=dev)
@@ -730,7 +740,8 @@ class Batch:
         ll = torch.empty(self.n_series, dtype=torch.float64, device=dev)
         _check(spingp_posterior_batched(self.model.h, self.offsets, self.n_series, self.n_total, self.t, self.y,
                                         self._theta(theta), ll, mean, var, ws, ws.numel(),
-                                        Model._flags(sync, missing)), "spingp_posterior_batched")
+                                        Model._flags(sync, missing, predictive=predictive)),
+               "spingp_posterior_batched")
         return mean, var, ll
 
     def optimize(self, theta0, iterations=100, tol=1e-8, sync=True):

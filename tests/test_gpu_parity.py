@@ -234,3 +234,49 @@ def test_large_series_full_size():
     q = 4.0 * (ll2 - ll + 0.5 * n * np.log(2.0))
     lhs = s.theta[1] * g[1] + s.theta[2] * g[2]
     assert abs(lhs - (0.5 * q - 0.5 * n)) <= 1e-8 * (abs(s.theta[1] * g[1]) + abs(s.theta[2] * g[2]) + n)
+
+
+@pytest.mark.parametrize("spec", [["matern52"], ["matern32", ("quasiperiodic", 3, "matern12")]])
+def test_log_gradient_and_predictive_variance_flags(spec):
+    """SPINGP_LOG_GRAD returns theta * d ll / d theta (readings R11) and
+    SPINGP_PREDICTIVE adds the noise variance to the latent variances (R8),
+    for the single-series, batched, host-buffer and split calls."""
+    theta = [0.5, 2.0, 0.05] if spec == ["matern52"] else [1.0, 1.0, 1.0, 1.0, 1.0, 5.0, 0.05]
+    n = 3001
+    rng = np.random.default_rng(17)
+    t = np.cumsum(rng.exponential(0.01, n))
+    y = np.sin(3 * t) + 0.2 * rng.standard_normal(n)
+    m = spingp.Model(spec)
+    T, Y, TH = _t(t), _t(y), _t(theta)
+    ll, g = m.grad(T, Y, TH)
+    ll2, g2 = m.grad(T, Y, TH, log_params=True)
+    assert ll2.item() == ll.item()
+    assert torch.equal(g2, g * TH)
+    llh, gh = m.grad_host(torch.from_numpy(t).pin_memory(), torch.from_numpy(y).pin_memory(),
+                          torch.tensor(theta, dtype=torch.float64), log_params=True)
+    assert torch.equal(gh, (g * TH).cpu())
+    mean, var, _ = m.posterior(T, Y, TH)
+    mean2, var2, _ = m.posterior(T, Y, TH, predictive=True)
+    assert torch.equal(mean2, mean)
+    assert torch.equal(var2, var + TH[-1])
+    # split in two ranges: the shares of the log-gradient sum to the whole
+    h = n // 2
+    e0 = m.segment_reduce(T[:h], Y[:h], TH)
+    ws1 = torch.empty(spingp.spingp_workspace_bytes(m.h, n - h, spingp.WS_GRAD), dtype=torch.uint8, device=DEV)
+    e1 = m.segment_reduce(T[h:], Y[h:], TH, t_prev=float(t[h - 1]), ws=ws1)
+    E = torch.stack([e0, e1])
+    _, s0 = m.segment_grad(T[:h], Y[:h], TH, E, 0, log_params=True)
+    _, s1 = m.segment_grad(T[h:], Y[h:], TH, E, 1, t_prev=float(t[h - 1]), ws=ws1, log_params=True)
+    assert torch.allclose(s0 + s1, g * TH, rtol=1e-10, atol=0.0)
+    if spec == ["matern52"]:
+        off = torch.tensor([0, 1000, 1000, n], dtype=torch.int64, device=DEV)
+        b = spingp.Batch(m, off, T, Y)
+        ths = torch.tensor([theta, [0.7, 1.0, 0.1], theta], dtype=torch.float64, device=DEV)
+        _, gb = b.grad(ths)
+        _, gb2 = b.grad(ths, log_params=True)
+        assert torch.equal(gb2, gb * ths)
+        _, vb, _ = b.posterior(ths)
+        _, vb2, _ = b.posterior(ths, predictive=True)
+        noise = torch.cat([torch.full((1000,), theta[2], dtype=torch.float64, device=DEV),
+                           torch.full((n - 1000,), theta[2], dtype=torch.float64, device=DEV)])
+        assert torch.equal(vb2, vb + noise)
