@@ -116,3 +116,23 @@ def test_eq_model_errors():
         spingp.Model(["matern32", ("eq", 16)])               # b = 18 > 16
     with pytest.raises(spingp.SpinGPError):
         spingp.Model([("eq", 4), ("eq", 6)])                 # one EQ component
+
+
+def test_eq_model_full_size_identity():
+    """The paper's b = 12 model (Matern-3/2 + EQ order 10) at N = 2^20, in the
+    benchmark's launch configuration: scaling every variance (s_m32, s_eq,
+    s_n) by c scales C by c, so sum_v s_v dl/ds_v = (y^T C^-1 y - N)/2 with
+    y^T C^-1 y read off l(2 s) - l(s); a property that holds at any size."""
+    s = synth.single("m32_eq10_n1m")
+    m = spingp.Model(s.spec)
+    T, Y = _t(s.t), _t(s.y)
+    th = np.asarray(s.theta, dtype=np.float64).copy()
+    ll, g = m.grad(T, Y, _t(th))
+    ll, g = float(ll.cpu()[0]), g.cpu().numpy()
+    var_idx = [1, 3, 4]
+    th2 = th.copy(); th2[var_idx] *= 2.0
+    ll2 = float(m.loglik(T, Y, _t(th2)).cpu()[0])
+    n = len(s.t)
+    q = 4.0 * (ll2 - ll + 0.5 * n * np.log(2.0))
+    lhs = sum(th[i] * g[i] for i in var_idx)
+    assert abs(lhs - (0.5 * q - 0.5 * n)) <= 1e-8 * (sum(abs(th[i] * g[i]) for i in var_idx) + n)
