@@ -807,8 +807,9 @@ def main_split(args, world, rank, local, dev):
         tt = torch.tensor([e0.elapsed_time(e1) / K], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_ms = float(tt.item())
-        out["e2e"] = {"value": n / (e2e_ms * 1e-3), "unit": "steps/s", "h2d_bytes_per_step": 16 * (b - a),
-                      "d2h_bytes_per_step": 32, "ms_per_step": e2e_ms,
+        # bytes of the whole job (every rank copies its own range in, its share out)
+        out["e2e"] = {"value": n / (e2e_ms * 1e-3), "unit": "steps/s", "h2d_bytes_per_step": 16 * n,
+                      "d2h_bytes_per_step": 32 * world, "ms_per_step": e2e_ms,
                       "api": "spingp_segment_reduce + spingp_segment_grad per rank, NCCL all-gather and all-reduce"}
     # the other configurations: the batch sharded by series, the single series as replicas
     if not args.no_extra and not args.n:
