@@ -147,7 +147,7 @@ def _split_worker(rank, world, port, out_path):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("world", [2, 3, 4])
 def test_split_series_exchange_on_gloo(tmp_path, world):
     from oracle import seq
     out = str(tmp_path / "split")
