@@ -841,7 +841,8 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
             st[GL * GL] = mb;
             st[(GL + 1) * GL] = v;
             st[(GL + 2) * GL] = rS;
-            st[(GL + 3) * GL] = pr;
+            // the posterior's missing step keeps (Pb h)[lane] there, for its prediction
+            st[(GL + 3) * GL] = (POST && !obs) ? p0 : pr;
         }
         double pv[GL];
         ggather<NR>(p0, pv);
@@ -915,42 +916,39 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
             const double mb = st[GL * GL];
             const double v = st[(GL + 1) * GL];
             const double rS = st[(GL + 2) * GL];
+            // the gain entry; (Pb h)[lane] at a missing step of the posterior,
+            // whose kl, kuk below are then (Pb h)^T lh and (Pb h)^T Lh (Pb h)
             const double k = st[(GL + 3) * GL];
-            const double kl = gsum(k * lh);
+            double kl = gsum(k * lh);
             double kv[GL];
             ggather<NR>(k, kv);
             double u = 0.0;
 #pragma unroll
             for (int r = 0; r < NR; ++r) u = fma(Lh[r], kv[r], u);
-            const double kuk = gsum(k * u);
+            double kuk = gsum(k * u);
+            if constexpr (POST) {
+                const double yi = a.y[i];
+                const double hk = gsum(even ? k : 0.0);
+                if (a.missing && isnan(yi)) {
+                    // predicted only: mean = h^T (mb - Pb lh), variance = h^T Pb h - (Pb h)^T Lh (Pb h);
+                    // the adjoint then passes through unchanged
+                    const double hm = gsum(even ? mb : 0.0);
+                    if (lane == 0) {
+                        mean_out[i] = hm - kl;
+                        var_out[i] = hk - kuk;
+                    }
+                    kl = 0.0;
+                    kuk = 0.0;
+                    u = 0.0;
+                } else if (lane == 0) {
+                    mean_out[i] = fma(-s2, fma(v, rS, kl), yi);
+                    var_out[i] = s2 * hk - s2 * s2 * kuk;
+                }
+            }
             const double al = fma(v, rS, kl);
             const double cc = rS + kuk;
             if constexpr (GRAD) {
                 if (lane == 0) acc[1] = fma(al, al, acc[1]) - cc;
-            }
-            if constexpr (POST) {
-                const double yi = a.y[i];
-                if (a.missing && isnan(yi)) {
-                    // predicted only: mean = h^T (mb - Pb lh), variance = h^T Pb h - (Pb h)^T Lh (Pb h)
-                    const double p0 = g_hsum<NR>(Db) + ph;
-                    double pv[GL];
-                    ggather<NR>(p0, pv);
-                    double lp = 0.0;
-#pragma unroll
-                    for (int r = 0; r < NR; ++r) lp = fma(Lh[r], pv[r], lp);
-                    const double hm = gsum(even ? mb : 0.0), pl = gsum(p0 * lh);
-                    const double hph = gsum(even ? p0 : 0.0), plp = gsum(p0 * lp);
-                    if (lane == 0) {
-                        mean_out[i] = hm - pl;
-                        var_out[i] = hph - plp;
-                    }
-                } else {
-                    const double hk = gsum(even ? k : 0.0);
-                    if (lane == 0) {
-                        mean_out[i] = fma(-s2, al, yi);
-                        var_out[i] = s2 * hk - s2 * s2 * kuk;
-                    }
-                }
             }
             const double lt = lh - (even ? al : 0.0);
             // Lt = Lh - h u^T - u h^T + cc h h^T = Lh - h ub^T - ub h^T with ub = u - (cc / 2) h
