@@ -77,55 +77,70 @@ int64_t default_chunk(int64_t n) {
 
 int64_t default_group_chunk(int64_t n);
 
-// An EQ component of order >= 8 is ill-conditioned in the modal coordinates
-// of the group path (its modal variances cancel to f's by ~7 digits), and
-// short chunks carry rank-deficient information about their entry state:
-// the default keeps its chunks at least this long.
-static constexpr int64_t EQ_MIN_CHUNK = 64;
-
 int64_t chunk_len(const spingp_model* m, int64_t n) {
     if (m->chunk_len > 0) return (int64_t)m->chunk_len;
-    if (!m->group) return default_chunk(n);
-    int64_t L = default_group_chunk(n);
-    if (m->gm.eq_nk >= 4 && L < EQ_MIN_CHUNK) L = EQ_MIN_CHUNK;
-    return L;
+    return m->group ? default_group_chunk(n) : default_chunk(n);
 }
 
 bool single_matern(const spingp_model* m) { return m->ncomp == 1 && m->kinds[0] >= 1 && m->kinds[0] <= 3; }
 
 // Build the 2x2-block description for the group path; false if the model has
 // a component that is not made of 2x2 blocks or is too large.
+//
+// The state lists the EQ component's sections first (when there is one), then
+// the other components' blocks in component order: f sums the first
+// coordinate of every block, so the order is internal, and with the EQ blocks
+// at fixed positions the kernels index their coupling blocks at compile time.
 bool build_group(spingp_model* m) {
     spg::GModel g;
     memset(&g, 0, sizeof(g));
     g.eq_comp = -1;
     if (m->ncomp > spg::GMAXCOMP) return false;
-    int K = 0, P = 0;
+    int K = 0, P = 0, neq = 0;
+    for (int c = 0; c < m->ncomp; ++c) neq += (m->kinds[c] == SPINGP_EQ);
+    if (neq > 1) return false;                                  // one EQ component
     for (int c = 0; c < m->ncomp; ++c) {
-        const int k = m->kinds[c];
-        g.ckind[c] = k;
+        g.ckind[c] = m->kinds[c];
         g.cpoff[c] = P;
-        int nb, kind;
-        if (k == SPINGP_MATERN32) { nb = 1; kind = 0; P += 2; }
-        else if (k == SPINGP_PERIODIC) { nb = m->orders[c] + 1; kind = 1; P += 3; }
-        else if (k == SPINGP_QUASIPERIODIC && m->envs[c] == SPINGP_MATERN12) { nb = m->orders[c] + 1; kind = 2; P += 4; }
-        else if (k == SPINGP_EQ) {
-            if (g.eq_nk > 0) return false;                     // one EQ component
-            const int N = m->orders[c];
-            nb = N / 2; kind = 3; P += 2;
-            if (K + nb > spg::GMAXBLK) return false;
-            double a[8], b[8];
-            if (!spg::eq_modal(N, a, b, g.eqP, 16)) return false;
-            g.eq_comp = c; g.eq_k0 = K; g.eq_nk = nb;
-            for (int j = 0; j < nb; ++j) { g.eqa[K + j] = a[j]; g.eqb[K + j] = b[j]; }
-        }
-        else return false;
-        for (int j = 0; j < nb; ++j) {
-            if (K >= spg::GMAXBLK) return false;
-            g.bkind[K] = kind; g.bcomp[K] = c; g.bj[K] = (kind == 0) ? 0 : j;
-            ++K;
-        }
+        const int k = m->kinds[c];
+        P += (k == SPINGP_MATERN32 || k == SPINGP_EQ) ? 2 : (k == SPINGP_PERIODIC) ? 3 : 4;
     }
+    for (int pass = 0; pass < 2; ++pass)
+        for (int c = 0; c < m->ncomp; ++c) {
+            const int k = m->kinds[c];
+            if ((k == SPINGP_EQ) != (pass == 0)) continue;
+            int nb, kind;
+            if (k == SPINGP_MATERN32) { nb = 1; kind = 0; }
+            else if (k == SPINGP_PERIODIC) { nb = m->orders[c] + 1; kind = 1; }
+            else if (k == SPINGP_QUASIPERIODIC && m->envs[c] == SPINGP_MATERN12) { nb = m->orders[c] + 1; kind = 2; }
+            else if (k == SPINGP_EQ) {
+                const int N = m->orders[c];
+                nb = N / 2; kind = 3;
+                if (K + nb > spg::GMAXBLK) return false;
+                double a[8], b[8], u[16], w[16], Pb[32];
+                if (!spg::eq_cascade(N, a, b, u, w, Pb)) return false;
+                g.eq_comp = c; g.eq_k0 = K; g.eq_nk = nb;
+                for (int j = 0; j < nb; ++j) {
+                    g.eqa[K + j] = a[j]; g.eqb[K + j] = b[j];
+                    for (int q = 0; q < 2; ++q) { g.equ[2 * (K + j) + q] = u[2 * j + q]; g.eqw[2 * (K + j) + q] = w[2 * j + q]; }
+                    for (int r = 0; r < 2; ++r)
+                        for (int q = 0; q < 2; ++q) g.eqP[(2 * j + r) * 16 + 2 * j + q] = Pb[4 * j + 2 * r + q];
+                }
+            }
+            else return false;
+            for (int j = 0; j < nb; ++j) {
+                if (K >= spg::GMAXBLK) return false;
+                g.bkind[K] = kind; g.bcomp[K] = c; g.bj[K] = (kind == 0) ? 0 : j;
+                ++K;
+            }
+        }
+    for (int k = 1; k < g.eq_nk; ++k)
+        for (int i = 0; i < k; ++i) {
+            const double al = g.eqa[k] - g.eqa[i], bc = g.eqb[k] - g.eqb[i], ba = g.eqb[k] + g.eqb[i];
+            g.eqrc[k * (k - 1) / 2 + i] = 1.0 / (al * al + bc * bc);
+            g.eqra[k * (k - 1) / 2 + i] = 1.0 / (al * al + ba * ba);
+        }
+    g.phs = 4 * spg::GMAXBLK + 2 * g.eq_nk * (g.eq_nk - 1);
     g.K = K; g.b = 2 * K; g.P = P + 1; g.ncomp = m->ncomp;
     if (g.b != m->b || g.P != m->P) return false;
     m->gm = g;
@@ -164,7 +179,7 @@ spingp_status run(const spingp_model* m, int mode, const double* t, const double
     if (((uintptr_t)ws & 255u) != 0) return SPINGP_EINVAL;
     if (!single_matern(m) && !m->group) return SPINGP_EUNSUPPORTED;
     const int64_t L = chunk_len(m, n);
-    const size_t need = m->group ? spg::group_ws_bytes(n, L, mode) : spg::matern_ws_bytes(m->b, n, L, mode);
+    const size_t need = m->group ? spg::group_ws_bytes(m->gm, n, L, mode) : spg::matern_ws_bytes(m->b, n, L, mode);
     if (ws_bytes < need) return SPINGP_EINVAL;
     spingp_status st = prepare_device();
     if (st != SPINGP_OK) return st;
@@ -333,7 +348,7 @@ size_t spingp_workspace_bytes(const spingp_model* m, int64_t n, spingp_ws_kind w
     if (!m || n < 1) return 0;
     const int mode = what == SPINGP_WS_GRAD ? spg::MODE_GRAD
                    : what == SPINGP_WS_POSTERIOR ? spg::MODE_POSTERIOR : spg::MODE_LOGLIK;
-    if (m->group) return spg::group_ws_bytes(n, chunk_len(m, n), mode);
+    if (m->group) return spg::group_ws_bytes(m->gm, n, chunk_len(m, n), mode);
     if (!single_matern(m)) return 0;
     return spg::matern_ws_bytes(m->b, n, chunk_len(m, n), mode);
 }
@@ -444,7 +459,7 @@ static spingp_status segment_call(const spingp_model* m, int phase, const double
     if (((uintptr_t)ws & 255u) != 0) return SPINGP_EINVAL;
     if (!first && !std::isfinite(t_prev)) return SPINGP_EINVAL;
     const int64_t L = chunk_len(m, n);
-    const size_t need = m->group ? spg::group_ws_bytes(n, L, spg::MODE_GRAD) : spg::matern_ws_bytes(m->b, n, L, spg::MODE_GRAD);
+    const size_t need = m->group ? spg::group_ws_bytes(m->gm, n, L, spg::MODE_GRAD) : spg::matern_ws_bytes(m->b, n, L, spg::MODE_GRAD);
     if (ws_bytes < need) return SPINGP_EINVAL;
     spingp_status st = prepare_device();
     if (st != SPINGP_OK) return st;

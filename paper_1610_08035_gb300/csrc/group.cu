@@ -1,26 +1,29 @@
 // group.cu -- the hot path for structured state spaces built from 2x2 blocks:
 // sums of Matern-3/2, periodic (order J), quasi-periodic (order J with a
-// Matern-1/2 envelope) and exponentiated-quadratic (even order N, in real
-// modal coordinates) components, state dimension b = 2K <= 16 (Sec. 2.1; the
-// quasi-periodic family is Eq. co2_1's periodicity term, the EQ
-// approximation the one of the paper's experiments).
+// Matern-1/2 envelope) and exponentiated-quadratic (even order N, a cascade
+// of second-order sections) components, state dimension b = 2K <= 16
+// (Sec. 2.1; the quasi-periodic family is Eq. co2_1's periodicity term, the
+// EQ approximation the one of the paper's experiments).
 //
-// Structure exploited: the transition A_n = blockdiag(Phi_1 .. Phi_K) is block
-// diagonal with 2x2 blocks (a Matern-3/2 block in scaled coordinates, a
-// rotation by j w dt damped by the envelope, or an EQ pole pair's damped
-// rotation exp(a x) R(b x), x = dt / l), and H picks the first coordinate of
-// every block.  Pinf is diagonal except on an EQ component's block, where it
-// is the dense modal covariance s P_m; each CTA keeps the whole Pinf in
-// shared memory.  The posterior covariance is dense, so
-// the Kalman and adjoint recursions run on a group of 16 lanes per chunk: lane
-// c owns column c of every b x b matrix.  Left products with the block
-// diagonal Phi are then local to a lane, right products need the partner
-// column of the same block (one shuffle per entry), and H^T-column sums of a
-// symmetric matrix are local as well.
+// Structure exploited: the transition A_n is made of 2x2 blocks.  Its
+// diagonal blocks are a Matern-3/2 block in scaled coordinates, a rotation by
+// j w dt damped by the envelope, or an EQ section's damped rotation
+// exp(a x) R(b x), x = dt / l; an EQ component (its sections first in the
+// state) adds the coupling blocks of its sections below the diagonal, so that
+// part of A_n is block lower triangular.  H picks the first coordinate of
+// every block.  Pinf is diagonal except on the EQ sections, where it has
+// dense 2x2 blocks s P_k; each CTA keeps the whole Pinf in shared memory.
+// The posterior covariance is dense, so the Kalman and adjoint recursions run
+// on a group of 16 lanes per chunk: lane c owns column c of every b x b
+// matrix.  Left products with A_n are then local to a lane; without an EQ
+// coupling a right product needs only the partner column of the same block
+// (one shuffle per entry), and with one a sandwich A X A^T of a symmetric X
+// is two left products around a transpose through shared memory.  H^T-column
+// sums of a symmetric matrix are local as well.
 //
 // Kernels, in order:
 //   k_gsetup     per-block constants from theta (Pinf weights, rates)
-//   k_gdisc      one thread per step: Phi_n for every block (stored)
+//   k_gdisc      one thread per step: the transition's blocks (stored)
 //   k_gfold      one group per chunk: sequential elimination into an element
 //   k_gscan_up / k_gscan_down   odd-even reduction of chunk elements, level by
 //                level, with group-cooperative combines (global memory)
@@ -146,6 +149,69 @@ __global__ void k_gsetup(GModel gm, const double* __restrict__ theta, double* __
 
 // Phi for step i (transition from t_{i-1}): 4 entries per block, row-major.
 // (t_prev: the time before step 0 when the steps continue a split series, s0 = -1)
+// The coupling blocks of the EQ component's transition F = expm(T x), block
+// (k, i) for sections k > i, written to out[4 (k (k - 1) / 2 + i) ..]
+// row-major.  T has the diagonal blocks T_k = a_k I + b_k J, J = [[0, 1],
+// [-1, 0]], and below them T_ki = -u_k w_i^T.  F commutes with T, and with
+// E = F - I block (k, i) of T F = F T reads
+//   T_k E_ki - E_ki T_i = E_kk T_ki - T_ki E_ii + sum_{i<j<k} (E_kj T_ji - T_kj E_ji)
+//                       = -p w_i^T + u_k q^T,
+//   p = sum_{j=i+1..k} E_kj u_j,   q = sum_{j=i..k-1} E_ji^T w_j,
+// Parlett's recurrence for a function of a block triangular matrix, taken in
+// E so that the identity terms cancel exactly and a small x loses no digits.
+// X -> T_k X - X T_i acts on the part of X that commutes with J,
+// (X - J X J) / 2, as left multiplication by (a_k - a_i) + (b_k - b_i) J, and
+// on the part that anticommutes, (X + J X J) / 2, as (a_k - a_i) + (b_k + b_i) J:
+// each part is solved by one complex division (reciprocal moduli from the
+// model).  Row k runs i = k-1 down to 0, so p accumulates along the row and q
+// per column.
+__device__ void g_eq_coupling(const GModel& gm, double x, double* __restrict__ out) {
+    const int nk = gm.eq_nk;
+    double c0[GK], c1[GK], q0[GK], q1[GK];
+#pragma unroll
+    for (int k = 0; k < GK; ++k) {
+        c0[k] = 0.0; c1[k] = 0.0; q0[k] = 0.0; q1[k] = 0.0;
+        if (k < nk) {
+            const double bx = gm.eqb[k] * x;
+            double sn, cs;
+            sincos(bx, &sn, &cs);
+            const double sh = sin(0.5 * bx), em = expm1(gm.eqa[k] * x);
+            c0[k] = fma(em, cs, -2.0 * sh * sh);     // e^(a x) cos(b x) - 1
+            c1[k] = (1.0 + em) * sn;                 // e^(a x) sin(b x)
+            // q_k starts at E_kk^T w_k, E_kk = [[c0, c1], [-c1, c0]]
+            const double w0 = gm.eqw[2 * k], w1 = gm.eqw[2 * k + 1];
+            q0[k] = fma(c0[k], w0, -c1[k] * w1);
+            q1[k] = fma(c1[k], w0, c0[k] * w1);
+        }
+    }
+#pragma unroll
+    for (int k = 1; k < GK; ++k) {
+        if (k >= nk) break;
+        const double uk0 = gm.equ[2 * k], uk1 = gm.equ[2 * k + 1], wk0 = gm.eqw[2 * k], wk1 = gm.eqw[2 * k + 1];
+        double p0 = fma(c0[k], uk0, c1[k] * uk1), p1 = fma(-c1[k], uk0, c0[k] * uk1);   // E_kk u_k
+#pragma unroll
+        for (int i = k - 1; i >= 0; --i) {
+            const int ci = k * (k - 1) / 2 + i;
+            const double wi0 = gm.eqw[2 * i], wi1 = gm.eqw[2 * i + 1];
+            const double r00 = fma(-p0, wi0, uk0 * q0[i]), r01 = fma(-p0, wi1, uk0 * q1[i]);
+            const double r10 = fma(-p1, wi0, uk1 * q0[i]), r11 = fma(-p1, wi1, uk1 * q1[i]);
+            const double pc = 0.5 * (r00 + r11), qc = 0.5 * (r01 - r10);   // commuting part [[pc, qc], [-qc, pc]]
+            const double ra = 0.5 * (r00 - r11), sa = 0.5 * (r01 + r10);   // anticommuting part [[ra, sa], [sa, -ra]]
+            const double al = gm.eqa[k] - gm.eqa[i], bc = gm.eqb[k] - gm.eqb[i], ba = gm.eqb[k] + gm.eqb[i];
+            const double Pc = fma(al, pc, bc * qc) * gm.eqrc[ci], Qc = fma(al, qc, -bc * pc) * gm.eqrc[ci];
+            const double Ra = fma(al, ra, -ba * sa) * gm.eqra[ci], Sa = fma(al, sa, ba * ra) * gm.eqra[ci];
+            const double x00 = Pc + Ra, x01 = Qc + Sa, x10 = Sa - Qc, x11 = Pc - Ra;
+            double* o = out + 4 * ci;
+            o[0] = x00; o[1] = x01; o[2] = x10; o[3] = x11;
+            const double ui0 = gm.equ[2 * i], ui1 = gm.equ[2 * i + 1];
+            p0 = fma(x00, ui0, fma(x01, ui1, p0));
+            p1 = fma(x10, ui0, fma(x11, ui1, p1));
+            q0[i] = fma(x00, wk0, fma(x10, wk1, q0[i]));   // += X^T w_k
+            q1[i] = fma(x01, wk0, fma(x11, wk1, q1[i]));
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_gdisc(GModel gm, const double* __restrict__ t, const double* __restrict__ y,
                                                 int64_t n, const double* __restrict__ theta,
                                                 double* __restrict__ phis, int* status, int missing, int64_t s0,
@@ -156,7 +222,7 @@ __global__ void __launch_bounds__(256) k_gdisc(GModel gm, const double* __restri
     if (!isfinite(t[i]) || (!isfinite(y[i]) && !(missing && isnan(y[i])))) bad |= ST_ENONFINITE;
     const double dt = (i > 0) ? t[i] - t[i - 1] : (s0 < 0 ? t[0] - t_prev : 0.0);
     if (dt < 0.0) bad |= ST_ENOTSORTED;
-    double* ph = phis + i * (4 * GK);
+    double* ph = phis + i * gm.phs;
     // per component, once: x = dt / l of the EQ blocks; the rotation by w dt
     // and the envelope of a (quasi-)periodic component, whose harmonic j + 1
     // follows from harmonic j by angle addition (its blocks come in order
@@ -207,6 +273,7 @@ __global__ void __launch_bounds__(256) k_gdisc(GModel gm, const double* __restri
         }
         ph[4 * k + 0] = p00; ph[4 * k + 1] = p01; ph[4 * k + 2] = p10; ph[4 * k + 3] = p11;
     }
+    if (gm.eq_nk > 1) g_eq_coupling(gm, dt / theta[gm.cpoff[gm.eq_comp]], ph + 4 * GK);
     if (bad) atomicOr(status, bad);
 }
 
@@ -282,6 +349,97 @@ __device__ __forceinline__ double g_hsum(const double (&X)[GL]) {
     return s;
 }
 
+// ------------------------------------------------------------------ the transition with EQ coupling blocks
+
+// coupling block (k, i), k > i, of a step's transition (after the GK diagonal blocks)
+__device__ __forceinline__ const double* g_cpl(const double* __restrict__ ph, int k, int i) {
+    return ph + 4 * GK + 4 * (k * (k - 1) / 2 + i);
+}
+// X <- A X for a column: the diagonal blocks, plus sum_{i<k} A_ki X_i on the
+// rows of EQ section k (nk sections, the first blocks of the state)
+template <int NR>
+__device__ __forceinline__ void g_left_c(const double* __restrict__ ph, int nk, double (&X)[GL]) {
+    double add[NR];
+#pragma unroll
+    for (int k = 0; k < NR / 2; ++k) {
+        double s0 = 0.0, s1 = 0.0;
+        if (k > 0 && k < nk) {
+#pragma unroll
+            for (int i = 0; i < k; ++i) {
+                const double* o = g_cpl(ph, k, i);
+                s0 = fma(o[0], X[2 * i], fma(o[1], X[2 * i + 1], s0));
+                s1 = fma(o[2], X[2 * i], fma(o[3], X[2 * i + 1], s1));
+            }
+        }
+        add[2 * k] = s0; add[2 * k + 1] = s1;
+    }
+    g_left<NR>(ph, X);
+#pragma unroll
+    for (int r = 2; r < NR; ++r) X[r] += add[r];
+}
+// X <- A^T X for a column: sum_{k>i} A_ki^T X_k on the rows of section i
+template <int NR>
+__device__ __forceinline__ void g_left_t_c(const double* __restrict__ ph, int nk, double (&X)[GL]) {
+    double add[NR];
+#pragma unroll
+    for (int i = 0; i < NR / 2; ++i) {
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int k = i + 1; k < NR / 2; ++k) {
+            if (k < nk) {
+                const double* o = g_cpl(ph, k, i);
+                s0 = fma(o[0], X[2 * k], fma(o[2], X[2 * k + 1], s0));
+                s1 = fma(o[1], X[2 * k], fma(o[3], X[2 * k + 1], s1));
+            }
+        }
+        add[2 * i] = s0; add[2 * i + 1] = s1;
+    }
+    g_left_t<NR>(ph, X);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) X[r] += add[r];
+}
+// X <- its row 'lane', given its column 'lane' in every lane of the group:
+// a transpose through the group's shared scratch tb (rows of stride GL + 1,
+// so neither the column writes nor the row reads meet a bank conflict)
+template <int NR>
+__device__ __forceinline__ void g_transpose(double* __restrict__ tb, int lane, double (&X)[GL]) {
+    const unsigned mask = half_mask();
+#pragma unroll
+    for (int r = 0; r < NR; ++r) tb[r * (GL + 1) + lane] = X[r];
+    __syncwarp(mask);
+#pragma unroll
+    for (int j = 0; j < NR; ++j) X[j] = (lane < NR) ? tb[lane * (GL + 1) + j] : 0.0;
+    __syncwarp(mask);
+}
+// X <- A X A^T for a symmetric X by columns: with Y = A X, column 'lane' of
+// A Y^T is A times row 'lane' of Y
+template <int NR>
+__device__ __forceinline__ void g_sandwich_c(const double* __restrict__ ph, int nk, double* tb, int lane,
+                                             double (&X)[GL]) {
+    g_left_c<NR>(ph, nk, X);
+    g_transpose<NR>(tb, lane, X);
+    g_left_c<NR>(ph, nk, X);
+}
+// X <- A^T X A for a symmetric X by columns
+template <int NR>
+__device__ __forceinline__ void g_sandwich_t_c(const double* __restrict__ ph, int nk, double* tb, int lane,
+                                               double (&X)[GL]) {
+    g_left_t_c<NR>(ph, nk, X);
+    g_transpose<NR>(tb, lane, X);
+    g_left_t_c<NR>(ph, nk, X);
+}
+// entry 'lane' of A v (resp. A^T v) for a lane-distributed vector v
+template <int NR, bool TR>
+__device__ __forceinline__ double g_vleft_c(const double* __restrict__ ph, int nk, int lane, double v) {
+    double vv[GL];
+    ggather<NR>(v, vv);
+    if constexpr (TR) g_left_t_c<NR>(ph, nk, vv); else g_left_c<NR>(ph, nk, vv);
+    double r = 0.0;
+#pragma unroll
+    for (int q = 0; q < NR; ++q) r = (q == lane) ? vv[q] : r;
+    return r;
+}
+
 // ------------------------------------------------------------------ elements in global memory
 
 struct GElem {
@@ -319,7 +477,7 @@ __device__ __forceinline__ void gvs_load(const double* __restrict__ base, int64_
 // Per-group shared scratch: one b x b matrix stored by columns (col c at sm[c*GL])
 // and inverse workspace.
 struct GSmem {
-    double X[GL * GL];
+    double X[GL * (GL + 1)];   // also the transpose scratch of g_transpose
     double N[GL * GL];
     double R[GL * GL];
 };
@@ -432,14 +590,19 @@ struct GArgs {
     double t_prev;        // with s0 = -1: the time of the step before step 0
 };
 
-template <int NR>
+// EQT: the model has an EQ component of two or more sections (coupling
+// blocks in the transition)
+template <int NR, bool EQT>
 __global__ void __launch_bounds__(GCTA) k_gfold(GArgs a, double* __restrict__ nodes) {
     __shared__ double s_pinf[GL * GL], s_dpe[GL * GL];
+    __shared__ double s_tb[EQT ? GGRP * GL * (GL + 1) : 1];
     g_pinf_smem(a.gm, a.theta, a.gconst, s_pinf, s_dpe);
     __syncthreads();
     const int lane = threadIdx.x & (GL - 1);
     const int64_t c = blockIdx.x * (int64_t)GGRP + (threadIdx.x >> 4);
     if (c >= a.nc) return;   // the whole group leaves together
+    const int phs = EQT ? a.gm.phs : 4 * GK, nk = a.gm.eq_nk;
+    double* tb = s_tb + (EQT ? (threadIdx.x >> 4) * GL * (GL + 1) : 0);
     const bool on = lane < a.gm.b;
     const double s2 = a.theta[a.gm.P - 1];
     double ph = 0.0;         // (Pinf h)[lane]
@@ -459,11 +622,17 @@ __global__ void __launch_bounds__(GCTA) k_gfold(GArgs a, double* __restrict__ no
     for (int64_t i = s; i < e; ++i) {
         const double yi = a.y[i];
         if (i > a.s0) {
-            const double* ph = a.phis + i * (4 * GK);
-            g_left<NR>(ph, el.A);
-            el.bv = g_vleft(ph, lane, el.bv);
-            g_left<NR>(ph, Cm);
-            g_right_t<NR>(ph, lane, Cm);
+            const double* ph = a.phis + i * phs;
+            if constexpr (EQT) {
+                g_left_c<NR>(ph, nk, el.A);
+                el.bv = g_vleft_c<NR, false>(ph, nk, lane, el.bv);
+                g_sandwich_c<NR>(ph, nk, tb, lane, Cm);
+            } else {
+                g_left<NR>(ph, el.A);
+                el.bv = g_vleft(ph, lane, el.bv);
+                g_left<NR>(ph, Cm);
+                g_right_t<NR>(ph, lane, Cm);
+            }
         }
         if (a.missing && isnan(yi)) continue;               // missing: no update (Eqs. mean4-mean6)
         const double c0 = g_hsum<NR>(Cm) + ph;                  // (C h)[lane]
@@ -758,7 +927,7 @@ __global__ void __launch_bounds__(GSC) k_gscan_down(const double* __restrict__ l
 
 static constexpr int GNF = GL + 4;   // stored per lane per step: predicted covariance column, mean entry, v, 1/S, gain entry
 
-template <int MODE, int NR>
+template <int MODE, int NR, bool EQT>
 __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restrict__ pre,
                                                  const double* __restrict__ suf, double* __restrict__ store,
                                                  double* __restrict__ part, double* __restrict__ mean_out,
@@ -783,6 +952,8 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
     const int64_t nc = a.nc;
     const bool even = (lane & 1) == 0;
     const bool has_eq = a.gm.eq_nk > 0;
+    const int phs = EQT ? a.gm.phs : 4 * GK, nk = a.gm.eq_nk;
+    double* tb = sm[g].X;   // transpose scratch (EQT)
     const double s2 = a.theta[a.gm.P - 1];
     double ph = 0.0;   // (Pinf h)[lane]
 #pragma unroll
@@ -811,12 +982,17 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
 #pragma unroll
             for (int r = 0; r < NR; ++r) Db[r] = 0.0;
         } else {
-            const double* ph = a.phis + i * (4 * GK);
-            mb = g_vleft(ph, lane, m);
+            const double* ph = a.phis + i * phs;
 #pragma unroll
             for (int r = 0; r < NR; ++r) Db[r] = D[r];
-            g_left<NR>(ph, Db);
-            g_right_t<NR>(ph, lane, Db);
+            if constexpr (EQT) {
+                mb = g_vleft_c<NR, false>(ph, nk, lane, m);
+                g_sandwich_c<NR>(ph, nk, tb, lane, Db);
+            } else {
+                mb = g_vleft(ph, lane, m);
+                g_left<NR>(ph, Db);
+                g_right_t<NR>(ph, lane, Db);
+            }
         }
         const double p0 = g_hsum<NR>(Db) + ph;
         // a missing observation stores v = 1/S = 0, so the reverse sweep passes through it
@@ -871,7 +1047,8 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
             ggather<NR>(w, v);
             const unsigned mask = half_mask();
             g_put<NR>(sm[g].X, lane, W); __syncwarp(mask);
-            lh = -g_rowdot<NR>(sm[g].X, lane, v); __syncwarp(mask);
+            // (lanes past the rows hold no column; the scratch there may hold transposes)
+            lh = (lane < NR) ? -g_rowdot<NR>(sm[g].X, lane, v) : 0.0; __syncwarp(mask);
             g_mul<NR>(sm[g].X, J, Lh); __syncwarp(mask);     // W J
             g_sym<NR>(sm[g], lane, Lh);
         }
@@ -977,7 +1154,7 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                 }
             }
             if (i > a.s0) {
-                const double* ph = a.phis + i * (4 * GK);
+                const double* ph = a.phis + i * phs;
                 if constexpr (GRAD) {
                     const double dt = (i > 0) ? a.t[i] - a.t[i - 1] : a.t[0] - a.t_prev;
                     // per block: 2 <G_k,:, X_k Db_k,:> (column 'lane' part) - lt_k^T X_k mb_k (row 'lane' part);
@@ -1005,13 +1182,44 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                             if (kind == GB_QUASI) benv[kb] = fma(dt, fma(g0, d0, g1 * d1), benv[kb]);
                         }
                     }
+                    if constexpr (EQT) {
+                        // the EQ generator's coupling blocks -u_k w_i^T (k > i): the
+                        // column part <G, T_c Db> over this lane's column, T_c Db's
+                        // rows of section k being -u_k sig_k, sig_k = sum_{i<k} w_i^T Db_i
+                        // (a running sum down the sections), into the EQ component's
+                        // slot (block 0); the row part lt^T T_c mb of the lane's own
+                        // entry, (T_c mb)[lane] = -u_k[odd] sum_{i<k} w_i^T mb_i
+                        double sig = 0.0, cpt = 0.0;
+#pragma unroll
+                        for (int k = 0; k < NR / 2; ++k) {
+                            if (k < nk) {
+                                if (k > 0)
+                                    cpt = fma(-sig, fma(a.gm.equ[2 * k], G[2 * k], a.gm.equ[2 * k + 1] * G[2 * k + 1]),
+                                              cpt);
+                                sig = fma(a.gm.eqw[2 * k], Db[2 * k], fma(a.gm.eqw[2 * k + 1], Db[2 * k + 1], sig));
+                            }
+                        }
+                        brate[0] = fma(dt, cpt, brate[0]);
+                        double mv[GL];
+                        ggather<NR>(mb, mv);
+                        double sm_ = 0.0;
+#pragma unroll
+                        for (int q = 0; q < NR / 2; ++q)
+                            if (q < kbm && q < nk) sm_ = fma(a.gm.eqw[2 * q], mv[2 * q], fma(a.gm.eqw[2 * q + 1], mv[2 * q + 1], sm_));
+                        if (kbm < nk) rmine = fma(tl, -a.gm.equ[lane] * sm_, rmine);
+                    }
                 }
                 // propagate to the previous step: lh = Phi^T lt, Lh = Phi^T Lt Phi
-                lh = g_vleft_t(ph, lane, lt);
 #pragma unroll
                 for (int r = 0; r < NR; ++r) Lh[r] = Lt[r];
-                g_right<NR>(ph, lane, Lh);
-                g_left_t<NR>(ph, Lh);
+                if constexpr (EQT) {
+                    lh = g_vleft_c<NR, true>(ph, nk, lane, lt);
+                    g_sandwich_t_c<NR>(ph, nk, tb, lane, Lh);
+                } else {
+                    lh = g_vleft_t(ph, lane, lt);
+                    g_right<NR>(ph, lane, Lh);
+                    g_left_t<NR>(ph, Lh);
+                }
                 if constexpr (GRAD) {
                     double ld = 0.0;
 #pragma unroll
@@ -1126,11 +1334,11 @@ struct GLayout {
     int64_t lev_n[40];      // node counts, level 0 = chunks
     size_t off_gconst, off_phis, off_nodes[40], off_pre[40], off_suf[40], off_part, off_store, total;
 
-    GLayout(int64_t n, int64_t L, int mode) {
+    GLayout(int64_t n, int64_t L, int mode, int phs) {
         nc = (n + L - 1) / L;
         size_t o = 256;
         off_gconst = o; o = galign(o + sizeof(double) * GK * GNC);
-        off_phis = o; o = galign(o + sizeof(double) * 4 * GK * (size_t)n);
+        off_phis = o; o = galign(o + sizeof(double) * phs * (size_t)n);
         nlev = 0;
         lev_n[0] = nc;
         while (lev_n[nlev] > 1) { lev_n[nlev + 1] = (lev_n[nlev] + 1) / 2; ++nlev; }
@@ -1193,17 +1401,44 @@ static int gscan_down(char* ws, const size_t* nodes, const size_t* pre, const si
     return 0;
 }
 
-size_t group_ws_bytes(int64_t n, int64_t L, int mode) { return GLayout(n, L, mode).total; }
+// k_gfold / k_gchunk for the state's row count (the dimension rounded up to
+// 4) and whether the transition has EQ coupling blocks
+static void gfold_launch(int NRr, bool eqt, unsigned grid, cudaStream_t st, const GArgs& a, double* nodes0) {
+#define SPG_GFOLD(NRv) (eqt ? k_gfold<NRv, true><<<grid, GCTA, 0, st>>>(a, nodes0) \
+                            : k_gfold<NRv, false><<<grid, GCTA, 0, st>>>(a, nodes0))
+    switch (NRr) {
+    case 4: SPG_GFOLD(4); break;
+    case 8: SPG_GFOLD(8); break;
+    case 12: SPG_GFOLD(12); break;
+    default: SPG_GFOLD(16); break;
+    }
+#undef SPG_GFOLD
+}
+template <int M>
+static void gchunk_launch(int NRr, bool eqt, unsigned grid, cudaStream_t st, const GArgs& a, const double* pre,
+                          const double* suf, double* store, double* part, double* mean_out, double* var_out) {
+#define SPG_GCHUNK(NRv) (eqt ? k_gchunk<M, NRv, true><<<grid, GCTA, 0, st>>>(a, pre, suf, store, part, mean_out, var_out) \
+                             : k_gchunk<M, NRv, false><<<grid, GCTA, 0, st>>>(a, pre, suf, store, part, mean_out, var_out))
+    switch (NRr) {
+    case 4: SPG_GCHUNK(4); break;
+    case 8: SPG_GCHUNK(8); break;
+    case 12: SPG_GCHUNK(12); break;
+    default: SPG_GCHUNK(16); break;
+    }
+#undef SPG_GCHUNK
+}
+
+size_t group_ws_bytes(const GModel& gm, int64_t n, int64_t L, int mode) { return GLayout(n, L, mode, gm.phs).total; }
 
 int group_launch_count(int64_t n, int64_t L, int mode) {
-    GLayout lay(n, L, mode);
+    GLayout lay(n, L, mode, 4 * GK);
     return 2 + 1 + 2 * lay.nlev + 1 + 1;
 }
 
 int group_run(const GModel& gm, int mode, const double* t, const double* y, int64_t n, int64_t L,
               const double* theta, double* ll_out, double* grad_out, double* mean_out, double* var_out, void* wsv,
               cudaStream_t st, cudaEvent_t* ev, int missing) {
-    GLayout lay(n, L, mode);
+    GLayout lay(n, L, mode, gm.phs);
     char* ws = (char*)wsv;
     int* status = (int*)ws;
     double* gconst = (double*)(ws + lay.off_gconst);
@@ -1218,15 +1453,8 @@ int group_run(const GModel& gm, int mode, const double* t, const double* y, int6
     const unsigned cgrid = (unsigned)((lay.nc + GGRP - 1) / GGRP);
     // rows of the per-lane column arithmetic: the state dimension rounded up to 4
     const int NRr = (gm.b <= 4) ? 4 : (gm.b <= 8) ? 8 : (gm.b <= 12) ? 12 : 16;
-    auto fold = [&](double* nodes0) {
-        switch (NRr) {
-        case 4: k_gfold<4><<<cgrid, GCTA, 0, st>>>(a, nodes0); break;
-        case 8: k_gfold<8><<<cgrid, GCTA, 0, st>>>(a, nodes0); break;
-        case 12: k_gfold<12><<<cgrid, GCTA, 0, st>>>(a, nodes0); break;
-        default: k_gfold<16><<<cgrid, GCTA, 0, st>>>(a, nodes0); break;
-        }
-    };
-    fold((double*)(ws + lay.off_nodes[0]));
+    const bool eqt = gm.eq_nk > 1;
+    gfold_launch(NRr, eqt, cgrid, st, a, (double*)(ws + lay.off_nodes[0]));
     if (ev) cudaEventRecord(ev[1], st);
     gscan_up(ws, lay.off_nodes, lay.lev_n, lay.nlev, st);
     if (gscan_down(ws, lay.off_nodes, lay.off_pre, lay.off_suf, lay.lev_n, lay.nlev, nullptr, nullptr, st)) return 1;
@@ -1234,22 +1462,14 @@ int group_run(const GModel& gm, int mode, const double* t, const double* y, int6
     const double* pre = (const double*)(ws + lay.off_pre[0]);
     const double* suf = (const double*)(ws + lay.off_suf[0]);
     int na = 1;
-#define SPG_GCHUNK(M, NRv) k_gchunk<M, NRv><<<cgrid, GCTA, 0, st>>>(a, pre, suf, store, part, \
-                                                                    (M) == MODE_POSTERIOR ? mean_out : nullptr, \
-                                                                    (M) == MODE_POSTERIOR ? var_out : nullptr)
-#define SPG_GCHUNK_NR(M) \
-    switch (NRr) { case 4: SPG_GCHUNK(M, 4); break; case 8: SPG_GCHUNK(M, 8); break; \
-                   case 12: SPG_GCHUNK(M, 12); break; default: SPG_GCHUNK(M, 16); break; }
     if (mode == MODE_LOGLIK) {
-        SPG_GCHUNK_NR(MODE_LOGLIK)
+        gchunk_launch<MODE_LOGLIK>(NRr, eqt, cgrid, st, a, pre, suf, store, part, nullptr, nullptr);
     } else if (mode == MODE_GRAD) {
-        SPG_GCHUNK_NR(MODE_GRAD)
+        gchunk_launch<MODE_GRAD>(NRr, eqt, cgrid, st, a, pre, suf, store, part, nullptr, nullptr);
         na = GPART;
     } else {
-        SPG_GCHUNK_NR(MODE_POSTERIOR)
+        gchunk_launch<MODE_POSTERIOR>(NRr, eqt, cgrid, st, a, pre, suf, store, part, mean_out, var_out);
     }
-#undef SPG_GCHUNK_NR
-#undef SPG_GCHUNK
     if (ev) cudaEventRecord(ev[3], st);
     k_gfinal<<<1, GFIN, 0, st>>>(gm, part, lay.nc, na, theta, gconst, ll_out, grad_out);
     if (ev) cudaEventRecord(ev[4], st);
@@ -1280,7 +1500,7 @@ int group_segment(const GModel& gm, int phase, const double* t, const double* y,
                   const double* theta, double t_prev, int first, const double* elems, int G, int rank,
                   double* elem_out, double* ll_out, double* grad_out, void* wsv, cudaStream_t st, int missing) {
     if (G < 1 || G > SEG_MAX_RANKS || rank < 0 || rank >= G) return 1;
-    GLayout lay(n, L, MODE_GRAD);
+    GLayout lay(n, L, MODE_GRAD, gm.phs);
     char* ws = (char*)wsv;
     int* status = (int*)ws;
     double* gconst = (double*)(ws + lay.off_gconst);
@@ -1295,13 +1515,7 @@ int group_segment(const GModel& gm, int phase, const double* t, const double* y,
         if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
         k_gsetup<<<1, 32, 0, st>>>(gm, theta, gconst, status);
         k_gdisc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gm, t, y, n, theta, phis, status, missing, s0, t_prev);
-        double* nodes0 = (double*)(ws + lay.off_nodes[0]);
-        switch (NRr) {
-        case 4: k_gfold<4><<<cgrid, GCTA, 0, st>>>(a, nodes0); break;
-        case 8: k_gfold<8><<<cgrid, GCTA, 0, st>>>(a, nodes0); break;
-        case 12: k_gfold<12><<<cgrid, GCTA, 0, st>>>(a, nodes0); break;
-        default: k_gfold<16><<<cgrid, GCTA, 0, st>>>(a, nodes0); break;
-        }
+        gfold_launch(NRr, gm.eq_nk > 1, cgrid, st, a, (double*)(ws + lay.off_nodes[0]));
         gscan_up(ws, lay.off_nodes, lay.lev_n, lay.nlev, st);
         if (cudaMemcpyAsync(elem_out, ws + lay.off_nodes[lay.nlev], sizeof(double) * GNE * GL,
                             cudaMemcpyDeviceToDevice, st) != cudaSuccess)
@@ -1330,19 +1544,14 @@ int group_segment(const GModel& gm, int phase, const double* t, const double* y,
         if (gscan_down(ws, lay.off_nodes, lay.off_pre, lay.off_suf, lay.lev_n, lay.nlev, tpre, tsuf, st)) return 1;
         const double* pre = (const double*)(ws + lay.off_pre[0]);
         const double* suf = (const double*)(ws + lay.off_suf[0]);
-        switch (NRr) {
-        case 4: k_gchunk<MODE_GRAD, 4><<<cgrid, GCTA, 0, st>>>(a, pre, suf, store, part, nullptr, nullptr); break;
-        case 8: k_gchunk<MODE_GRAD, 8><<<cgrid, GCTA, 0, st>>>(a, pre, suf, store, part, nullptr, nullptr); break;
-        case 12: k_gchunk<MODE_GRAD, 12><<<cgrid, GCTA, 0, st>>>(a, pre, suf, store, part, nullptr, nullptr); break;
-        default: k_gchunk<MODE_GRAD, 16><<<cgrid, GCTA, 0, st>>>(a, pre, suf, store, part, nullptr, nullptr); break;
-        }
+        gchunk_launch<MODE_GRAD>(NRr, gm.eq_nk > 1, cgrid, st, a, pre, suf, store, part, nullptr, nullptr);
         k_gfinal<<<1, GFIN, 0, st>>>(gm, part, lay.nc, GPART, theta, gconst, ll_out, grad_out);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 int group_elem_size() { return GNE * GL; }
 int group_segment_launch_count(int64_t n, int64_t L) {
-    GLayout lay(n, L, MODE_GRAD);
+    GLayout lay(n, L, MODE_GRAD, 4 * GK);
     int gl = 0;
     for (int64_t c = SEG_MAX_RANKS; c > 1; c = (c + 1) / 2) ++gl;
     // phase 0: setup, disc, fold, up levels; phase 1: transpose, the ranks' tree (at most), the range's

@@ -16,16 +16,26 @@ struct GModel {
     int b, K, P, ncomp;
     int bkind[GMAXBLK], bcomp[GMAXBLK], bj[GMAXBLK];   // per block: kind, component, harmonic
     int ckind[GMAXCOMP], cpoff[GMAXCOMP];              // per component: spingp_kind, theta offset
-    // an exponentiated-quadratic component in real modal coordinates (at most
-    // one): its first block and block count, the block generators
-    // [[a, b], [-b, a]] at unit lengthscale, and its unit-variance stationary
-    // covariance P_m (order x order, row stride 16; Pinf = variance P_m)
+    // an exponentiated-quadratic component as a cascade of second-order
+    // sections (at most one, its blocks first: eq_k0 = 0): block count, the
+    // diagonal generator blocks [[a, b], [-b, a]] at unit lengthscale, the
+    // coupling blocks -u_k w_i^T below the diagonal (k > i), and its
+    // unit-variance stationary covariance P (block diagonal, order x order,
+    // row stride 16; Pinf = variance P)
     int eq_comp, eq_k0, eq_nk;
     double eqa[GMAXBLK], eqb[GMAXBLK];
+    double equ[2 * GMAXBLK], eqw[2 * GMAXBLK];
+    // per coupling block (k, i), k > i, at index k (k - 1) / 2 + i:
+    // 1 / ((a_k - a_i)^2 + (b_k - b_i)^2) and 1 / ((a_k - a_i)^2 + (b_k + b_i)^2)
+    double eqrc[GMAXBLK * (GMAXBLK - 1) / 2], eqra[GMAXBLK * (GMAXBLK - 1) / 2];
     double eqP[16 * 16];
+    // doubles per step of the stored transition: 4 per diagonal block (GMAXBLK
+    // of them), then 4 per EQ block below the diagonal
+    int phs;
 };
-// host: modal constants of the order-N EQ approximation (eqmodal.cu)
-bool eq_modal(int N, double* a, double* b, double* Pm, int ld);
+// host: constants of the order-N EQ cascade (eqcascade.cu); per section k:
+// pole a[k] + i b[k], u[2k..], w[2k..], P[4k..4k+3]
+bool eq_cascade(int N, double* a, double* b, double* u, double* w, double* P);
 
 // device status bits (the status word at the start of every workspace)
 enum { ST_EINVAL = 1 << 1, ST_ENOTSORTED = 1 << 2, ST_ENONFINITE = 1 << 3, ST_ENUMERIC = 1 << 4 };
@@ -122,7 +132,7 @@ int probe_exp_neg(const double* x, double* y, int64_t n, cudaStream_t st);
 }  // namespace spg
 
 namespace spg {
-size_t group_ws_bytes(int64_t n, int64_t L, int mode);
+size_t group_ws_bytes(const GModel& gm, int64_t n, int64_t L, int mode);
 int group_launch_count(int64_t n, int64_t L, int mode);
 int group_run(const GModel& gm, int mode, const double* t, const double* y, int64_t n, int64_t L,
               const double* theta, double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws,
