@@ -321,10 +321,12 @@ spingp_status spingp_grad_host(spingp_model* model, const double* t, const doubl
  * n <= 65536 for state dimension b <= 3).  The call allocates nothing and
  * frees nothing.  The first call on a device performs a one-time set-up for
  * that device (looking up the array's device address); make that first call
- * before capturing any stream.  All calls on a device share the one array
+ * before capturing any stream.  After a device reset the next call repeats
+ * the set-up for the new context.  All calls on a device share the one array
  * and it keeps the last call's contents: the call clears what must start at
  * zero itself, and two calls that can overlap on the GPU (different streams,
- * or different host threads) race on the scratch and corrupt each other.
+ * or different host threads) race on the scratch and corrupt each other; the
+ * library serialises only the set-up, so the caller serialises the calls.
  * With SPINGP_SYNC the call synchronises the stream and returns the device
  * status, as spingp_loglik does. */
 spingp_status spingp_loglik_noalloc(const spingp_model* model, const double* t, const double* y, int64_t n,

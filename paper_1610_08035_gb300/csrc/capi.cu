@@ -35,19 +35,43 @@ struct spingp_model {
     cudaEvent_t feed_ev[1 + spg::FEED_PIECES];
 };
 
+namespace spg {
+// The driver's unique ID of the current context (cuCtxGetId, reached through
+// the runtime's driver entry point, so the library does not link the driver
+// library itself); 0 if the driver does not provide it or no context is
+// current.  Per-device state that a device reset invalidates is tagged with it.
+unsigned long long context_id() {
+    typedef int (*ctx_id_fn)(void*, unsigned long long*);   // CUresult cuCtxGetId(CUcontext, unsigned long long*)
+    static const ctx_id_fn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (ctx_id_fn) nullptr;
+        return (ctx_id_fn)p;
+    }();
+    unsigned long long id = 0;
+    if (!fn || fn(nullptr, &id) != 0) return 0;
+    return id;
+}
+}  // namespace spg
+
 namespace {
 
 std::mutex g_prep_mu;
 bool g_prepared[SPG_MAXDEV];
+unsigned long long g_prep_ctx[SPG_MAXDEV];
 
-// one-time per-device set-up (shared-memory opt-in of the scan kernels)
+// per-device set-up (shared-memory opt-in of the scan kernels), once per
+// context: a device reset destroys the context and the attributes with it
 spingp_status prepare_device() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= SPG_MAXDEV) return SPINGP_ECUDA;
     std::lock_guard<std::mutex> lock(g_prep_mu);
-    if (!g_prepared[dev]) {
+    if (!g_prepared[dev] || spg::context_id() != g_prep_ctx[dev]) {
         if (spg::matern_prepare()) return SPINGP_ECUDA;
         g_prepared[dev] = true;
+        g_prep_ctx[dev] = spg::context_id();
     }
     return SPINGP_OK;
 }

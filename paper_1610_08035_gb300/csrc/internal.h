@@ -37,6 +37,9 @@ struct GModel {
 // pole a[k] + i b[k], u[2k..], w[2k..], P[4k..4k+3]
 bool eq_cascade(int N, double* a, double* b, double* u, double* w, double* P);
 
+// the driver's unique ID of the current context, 0 if unavailable (capi.cu)
+unsigned long long context_id();
+
 // device status bits (the status word at the start of every workspace)
 enum { ST_EINVAL = 1 << 1, ST_ENOTSORTED = 1 << 2, ST_ENONFINITE = 1 << 3, ST_ENUMERIC = 1 << 4 };
 

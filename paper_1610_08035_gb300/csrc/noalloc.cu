@@ -2,8 +2,12 @@
 //
 // Its scratch is a fixed array in the library's own device image.  Host code
 // may not pass the array's name to a kernel (on the host that name is only a
-// stand-in, not a device address), so the device address is looked up once
-// per device with cudaGetSymbolAddress and cached.
+// stand-in, not a device address), so the device address is looked up with
+// cudaGetSymbolAddress once per device and context, and cached with the
+// context's unique ID: after a device reset the new context gets a new ID,
+// and the next call looks the address up again.  The mutex guards only that
+// cache; the calls themselves share the one array, so a caller must not let
+// two calls on one device overlap.
 #include <cuda_runtime.h>
 #include <mutex>
 #include <stdint.h>
@@ -19,19 +23,21 @@ namespace {
 
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[NOALLOC_MAXDEV];
+unsigned long long g_noalloc_ctx[NOALLOC_MAXDEV];
 
-// Set-up, once per device, with that device current: resolve the scratch
-// array's device address and opt the reduction kernels into their shared
-// memory size.  Neither step allocates memory.
+// Set-up, once per device and context, with that device current: resolve the
+// scratch array's device address and opt the reduction kernels into their
+// shared memory size.  Neither step allocates memory.
 spingp_status noalloc_scratch(void** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAXDEV) return SPINGP_ECUDA;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    if (!g_noalloc_ptr[dev] || spg::context_id() != g_noalloc_ctx[dev]) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SPINGP_ECUDA;
         if (spg::matern_prepare()) return SPINGP_ECUDA;
         g_noalloc_ptr[dev] = p;
+        g_noalloc_ctx[dev] = spg::context_id();   // read after the set-up, which makes the context current
     }
     *out = g_noalloc_ptr[dev];
     return SPINGP_OK;
