@@ -45,7 +45,31 @@ DRAM_BYTES_PER_STEP = {"chunk_pass": 213.8}
 # algorithmic HBM bytes per step of the whole call: t and y in (16 B); the
 # gradient and log-likelihood outputs are O(1) per series
 ALGO_BYTES_PER_STEP = 16.0
+# Algorithmic FP64 work per step of one log-likelihood + gradient evaluation:
+# the sequential method written as dense b x b algebra in the paper's
+# coordinates (covariance Kalman filter, inversion-free adjoint, gradient
+# contractions; the discretisation not counted), from the counted
+# restatement in oracle/flops.py, 12 b^3 + (21 + 2 P_A) b^2 + 11 b + 11 with
+# P_A the parameters the transition depends on.  Per workload: b = 3 (P_A = 1),
+# b = 2 (P_A = 1), b = 16 (P_A = 3), b = 12 (P_A = 2).
+ALGO_FLOPS_PER_STEP = {"matern52_n4m": 575.0, "batched_4096": 575.0, "matern32_n64m": 221.0,
+                       "sum_qp_n1m": 56251.0, "m32_eq10_n1m": 24479.0}
+# y of every synthetic series but the N = 1000 plain-method one (whose y is
+# drawn from the state-space model)
+Y_KIND = "two sinusoids + Gaussian noise (the paper's simulated data, Sec. 4.2)"
 FP64_NOMINAL_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # SMs x max SM clock x FP64 flop/clk/SM
+
+
+def _algorithmic(key, steps_per_s, fp64_tflops):
+    """The whole call against the FP64 peak, in units of the dense
+    sequential method's arithmetic (ALGO_FLOPS_PER_STEP): above 1 where the
+    GPU's formulation (Jordan coordinates, block structure, the variance
+    scaling identity) needs fewer operations than the dense form."""
+    fl = ALGO_FLOPS_PER_STEP[key]
+    ach = fl * steps_per_s / 1e12
+    return {"algorithmic_flops_per_step": fl, "algorithmic_achieved": ach,
+            "algorithmic_frac": ach / fp64_tflops if fp64_tflops else None,
+            "algorithmic_scope": "whole call; flops of the dense sequential method (oracle/flops.py)"}
 
 
 def parse():
@@ -157,8 +181,8 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_1610_08035_gb300 import synth
-    s = synth.single(WORKLOAD, n=args.n or None)
-    sample = min(len(s.t), 1 << 18)
+    s = synth.single(WORKLOAD, n=args.n or None, seed=1)
+    sample = len(s.t)                     # the whole series every step (~9 s on one core)
     for _ in range(args.warmup):
         oracle_rate(s, min(sample, 1 << 14))
     rates = []
@@ -166,13 +190,13 @@ def run_reference(args):
         r, _ = oracle_rate(s, sample)
         rates.append(r)
     value = float(np.median(rates))
-    desc = "first %d steps of the %d-step workload per step, sequential C oracle (Kalman filter + two-filter adjoint)" % (
-        sample, len(s.t))
+    desc = "the whole %d-step series per step, sequential C oracle (Kalman filter + two-filter adjoint)" % sample
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sample / value, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": len(s.t), "b": 3, "sample_steps": sample},
+        "config": {"workload": WORKLOAD, "n": len(s.t), "b": 3, "model": "matern52",
+                   "theta": [float(v) for v in s.theta], "parallelism": "single", "y": Y_KIND},
         "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -194,7 +218,14 @@ def _time_calls(fn, K, flush, torch):
     return ms / K
 
 
-def extra_workloads(args, dev, flush, world, rank=0):
+# Whole-call FP64 work per step executed by the kernels of each secondary
+# workload (ncu: flops = 2 DFMA + DADD + DMUL thread instructions, and every
+# instruction of the FP64 pipe), from the captures listed in
+# profiles/workload_kernels_grad.md; None until taken for the current kernels.
+WORKLOAD_EXEC_PER_STEP = {"sum_qp_n1m": None, "m32_eq10_n1m": None, "matern32_n64m": None, "batched_4096": None}
+
+
+def extra_workloads(args, dev, flush, world, rank=0, fp64_tflops=None):
     """loglik + gradient throughput of the other configurations: the b = 16
     sum (Matern-3/2 + quasi-periodic), the paper's own b = 12 timing model
     (Matern-3/2 + the order-10 EQ approximation), the batch of 4096 independent series of
@@ -218,8 +249,11 @@ def extra_workloads(args, dev, flush, world, rank=0):
 
     K = max(3, min(args.steps, 5))
     res = {}
+    # oracle samples for the cpu baselines (about 5-10 s of host work each)
+    oracle_sample = {"sum_qp_n1m": 1 << 15, "m32_eq10_n1m": 1 << 12, "matern32_n64m": 1 << 20}
     for name in ("sum_qp_n1m", "m32_eq10_n1m", "matern32_n64m"):
         s = synth.single(name)
+        n = len(s.t)
         T, Y, TH = (torch.tensor(a, device=dev) for a in (s.t, s.y, s.theta))
         m = spingp.Model(s.spec)
         if name == "matern32_n64m":
@@ -230,10 +264,49 @@ def extra_workloads(args, dev, flush, world, rank=0):
         for _ in range(3):
             m.grad(T, Y, TH, out=(ll, g))
         ms = max_ms(_time_calls(lambda: m.grad(T, Y, TH, sync=False, out=(ll, g)), K, flush, torch))
-        st = spingp.spingp_ws_status(m.workspace(len(s.t), spingp.WS_GRAD, dev))
-        res[name] = {"value": world * len(s.t) / (ms * 1e-3), "unit": "steps/s", "ms_per_step": ms, "n": len(s.t),
-                     "b": m.state_dim, "params": P, "chunk_len": m.chunk_len(len(s.t)), "status": st,
-                     "gpu_launches_per_step": spingp.spingp_launch_count(m.h, len(s.t), spingp.WS_GRAD)}
+        st = spingp.spingp_ws_status(m.workspace(n, spingp.WS_GRAD, dev))
+        entry = {"value": world * n / (ms * 1e-3), "unit": "steps/s", "ms_per_step": ms, "n": n,
+                 "b": m.state_dim, "params": P, "chunk_len": m.chunk_len(n), "status": st, "y": Y_KIND,
+                 "gpu_launches_per_step": spingp.spingp_launch_count(m.h, n, spingp.WS_GRAD)}
+        roof = {"bound": "alu", "kernel": "whole call", "peak": fp64_tflops, "unit": "TFLOP/s",
+                "peak_kind": "measured FP64 FMA probe (spingp_probe_fp64)"}
+        roof.update(_algorithmic(name, n / (ms * 1e-3), fp64_tflops))
+        ex = WORKLOAD_EXEC_PER_STEP.get(name)
+        if ex is not None:
+            fl, inst = ex
+            roof.update({"achieved": fl * n / (ms * 1e-3) / 1e12, "frac": fl * n / (ms * 1e-3) / 1e12 / fp64_tflops,
+                         "pipe_frac": inst * n / (ms * 1e-3) / (fp64_tflops * 1e12 / 2.0),
+                         "flops_per_step": fl, "fp64_inst_per_step": inst})
+        entry["roofline"] = roof
+        if name == "matern32_n64m":
+            # the long-series workload's step: log-likelihood + gradient +
+            # posterior mean, captured once in a CUDA graph and replayed
+            mean = torch.empty(n, dtype=torch.float64, device=dev)
+            var = torch.empty(n, dtype=torch.float64, device=dev)
+            m.posterior(T, Y, TH, with_loglik=False, out=(mean, var, None))
+            gst = torch.cuda.Stream(device=dev)
+            gst.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(gst):
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph, stream=gst):
+                    m.grad(T, Y, TH, sync=False, out=(ll, g))
+                    m.posterior(T, Y, TH, sync=False, with_loglik=False, out=(mean, var, None))
+            torch.cuda.current_stream().wait_stream(gst)
+            torch.cuda.synchronize()
+            gms = max_ms(_time_calls(graph.replay, K, flush, torch))
+            st2 = spingp.spingp_ws_status(m.workspace(n, spingp.WS_POSTERIOR, dev))
+            entry["graph_grad_posterior"] = {
+                "value": world * n / (gms * 1e-3), "unit": "steps/s", "ms_per_step": gms, "captured_graph": True,
+                "status": st2, "what": "spingp_grad then spingp_posterior (mean and variance), one graph",
+                "gpu_launches_per_step": spingp.spingp_launch_count(m.h, n, spingp.WS_GRAD)
+                + spingp.spingp_launch_count(m.h, n, spingp.WS_POSTERIOR)}
+            del graph, mean, var
+        if not args.no_cpu_baseline and world == 1:
+            smp = oracle_sample[name]
+            rate, _ = oracle_rate(s, smp)
+            entry["cpu_baseline"] = {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                                     "sample": "first %d of %d steps, sequential C oracle, 1 host thread" % (smp, n)}
+        res[name] = entry
         del T, Y, TH, m
         torch.cuda.empty_cache()
     # the batch (this rank's shard of whole series)
@@ -254,7 +327,10 @@ def extra_workloads(args, dev, flush, world, rank=0):
     g = torch.empty(3 * B, dtype=torch.float64, device=dev)
     for _ in range(3):
         bt.grad(TH, out=(ll, g))
-    # captured once into a CUDA graph and replayed (no host work per call)
+    # the same call issued eagerly (the binding's host work and the launches
+    # on the stream every call) ...
+    ems = max_ms(_time_calls(lambda: bt.grad(TH, sync=False, out=(ll, g)), K, flush, torch))
+    # ... and captured once into a CUDA graph and replayed (no host work per call)
     stream = torch.cuda.Stream(device=dev)
     stream.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(stream):
@@ -264,9 +340,22 @@ def extra_workloads(args, dev, flush, world, rank=0):
     torch.cuda.current_stream().wait_stream(stream)
     ms = max_ms(_time_calls(graph.replay, K, flush, torch))
     n_total = len(s.t)
+    nl = spingp.spingp_launch_count_batched(m.h, B, n_total, spingp.WS_GRAD)
     entry = {"value": n_all / (ms * 1e-3), "unit": "steps/s", "ms_per_step": ms, "n_series": 4096,
-             "n_total": n_all, "b": 3, "captured_graph": True, "scaling": "strong",
-             "gpu_launches_per_step": spingp.spingp_launch_count_batched(m.h, B, n_total, spingp.WS_GRAD)}
+             "n_total": n_all, "b": 3, "captured_graph": True, "scaling": "strong", "y": Y_KIND,
+             "gpu_launches_per_step": nl,
+             "eager": {"ms_per_step": ems, "value": n_all / (ems * 1e-3), "unit": "steps/s",
+                       "graph_saving_ms": ems - ms, "graph_saving_frac": (ems - ms) / ems, "launches": nl}}
+    roof = {"bound": "alu", "kernel": "whole call", "peak": fp64_tflops, "unit": "TFLOP/s",
+            "peak_kind": "measured FP64 FMA probe (spingp_probe_fp64)"}
+    roof.update(_algorithmic("batched_4096", n_all / (ms * 1e-3), fp64_tflops))
+    ex = WORKLOAD_EXEC_PER_STEP.get("batched_4096")
+    if ex is not None:
+        fl, inst = ex
+        roof.update({"achieved": fl * n_all / (ms * 1e-3) / 1e12, "frac": fl * n_all / (ms * 1e-3) / 1e12 / fp64_tflops,
+                     "pipe_frac": inst * n_all / (ms * 1e-3) / (fp64_tflops * 1e12 / 2.0),
+                     "flops_per_step": fl, "fp64_inst_per_step": inst})
+    entry["roofline"] = roof
     if not args.no_comparator:
         # plain GPU form: per series, the forward kernel at theta and theta +- h e_p
         h = 1e-5
@@ -332,15 +421,18 @@ def batched_oracle_rate(s, n_series=1024):
 # steps, or nodes for the BTD solver; the batched SCG's gradient evaluations
 # use the chain kernels' counts above.
 NEXT_FLOPS_PER_UNIT = {"prediction_n4m": 344.2, "literal_n1m": 2157.0, "btd_solve_n1m": 821.6,
-                       "eq_b12_n1m": 11627.0, "scg_batch_4096": 171.5 + 231.2}
+                       "eq_b12_n1m": None, "scg_batch_4096": 171.5 + 231.2}
 NEXT_FP64_INST_PER_UNIT = {"prediction_n4m": 226.0, "literal_n1m": 1485.5, "btd_solve_n1m": 520.0,
-                           "eq_b12_n1m": 7523.9, "scg_batch_4096": 107.1 + 141.6}
+                           "eq_b12_n1m": None, "scg_batch_4096": 107.1 + 141.6}
 
 
 def _next_roofline(key, units_per_s, fp64_tflops):
     """FP64 roofline of a whole call: achieved TFLOP/s against the measured
-    FMA probe, and the FP64-pipe instruction fraction."""
+    FMA probe, and the FP64-pipe instruction fraction (None where the counts
+    were not taken for the current kernels)."""
     fl, inst = NEXT_FLOPS_PER_UNIT[key], NEXT_FP64_INST_PER_UNIT[key]
+    if fl is None or inst is None:
+        return None
     ach = fl * units_per_s / 1e12
     return {"bound": "alu", "kernel": "whole call", "achieved": ach, "peak": fp64_tflops, "unit": "TFLOP/s",
             "frac": ach / fp64_tflops, "pipe_frac": inst * units_per_s / (fp64_tflops * 1e12 / 2.0),
@@ -565,6 +657,7 @@ def main():
             "fp64_inst_per_s": inst * n / (stage_ms[dom] * 1e-3) if inst else None,
             "pipe_frac": inst * n / (stage_ms[dom] * 1e-3) / (fp64_tflops * 1e12 / 2.0) if inst else None,
             "fp64_tensor_tflops": fp64_mma_tflops}
+    roof.update(_algorithmic(WORKLOAD, n / (ms_per_step * 1e-3), fp64_tflops))
     hbm = {"algorithmic_bytes_per_step": ALGO_BYTES_PER_STEP,
            "achieved_gbs": ALGO_BYTES_PER_STEP * n / (ms_per_step * 1e-3) / 1e9}
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -582,9 +675,10 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "n": n, "b": 3, "model": "matern52", "chunk_len": L,
-                      "theta": [float(v) for v in s.theta], "parallelism": "single",
+           "config": {"workload": WORKLOAD, "n": n, "b": 3, "model": "matern52",
+                      "theta": [float(v) for v in s.theta], "parallelism": "single", "y": Y_KIND,
                       "l2": "flushed between timed iterations (256 MiB write, untimed)"},
+           "launch": {"chunk_len": L},
            "roofline": roof, "hbm_roofline": hbm, "stages_ms_per_call": stage_ms,
            "gpu_launches": spingp.spingp_launch_count(model.h, n, spingp.WS_GRAD) * K,
            "clocks": clk}
@@ -679,7 +773,7 @@ def main():
 
     # ---- secondary workloads: the other configurations of the same path
     if not args.no_extra and not args.n:
-        out["workloads"] = extra_workloads(args, dev, flush, world, rank)
+        out["workloads"] = extra_workloads(args, dev, flush, world, rank, fp64_tflops)
 
     # ---- the rows built beyond the hot path, each with the oracle beside it
     if not args.no_next and not args.n and world == 1:
@@ -777,9 +871,10 @@ def main_split(args, world, rank, local, dev):
     out = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "n": n, "b": 3, "model": "matern52", "chunk_len": L,
+           "config": {"workload": WORKLOAD, "n": n, "b": 3, "model": "matern52",
                       "theta": [float(v) for v in s.theta], "parallelism": "series split over %d ranks" % world,
-                      "l2": "flushed between timed iterations (256 MiB write, untimed)"},
+                      "y": Y_KIND, "l2": "flushed between timed iterations (256 MiB write, untimed)"},
+           "launch": {"chunk_len": L},
            "roofline": roof,
            "hbm_roofline": {"algorithmic_bytes_per_step": ALGO_BYTES_PER_STEP,
                             "achieved_gbs": ALGO_BYTES_PER_STEP * n / (ms_per_step * 1e-3) / 1e9},
@@ -813,7 +908,7 @@ def main_split(args, world, rank, local, dev):
                       "api": "spingp_segment_reduce + spingp_segment_grad per rank, NCCL all-gather and all-reduce"}
     # the other configurations: the batch sharded by series, the single series as replicas
     if not args.no_extra and not args.n:
-        out["workloads"] = extra_workloads(args, dev, flush, world, rank)
+        out["workloads"] = extra_workloads(args, dev, flush, world, rank, fp64_tflops)
     if rank == 0:
         print(json.dumps(out), flush=True)
 

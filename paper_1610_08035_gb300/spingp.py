@@ -548,14 +548,18 @@ class Model:
                "spingp_segment_grad")
         return ll, g
 
-    def posterior(self, t, y, theta, sync=True, with_loglik=True, missing=False, predictive=False):
+    def posterior(self, t, y, theta, sync=True, with_loglik=True, missing=False, predictive=False, out=None):
         """(mean, var, ll): latent posterior mean and variance at t; with
-        predictive, var is the variance of an observation there (+ s_n)."""
+        predictive, var is the variance of an observation there (+ s_n).
+        out: (mean, var, ll) buffers to write instead (ll may be None)."""
         n = self._args(t, y, theta)
         ws = self.workspace(n, WS_POSTERIOR, t.device)
-        mean = torch.empty(n, dtype=torch.float64, device=t.device)
-        var = torch.empty(n, dtype=torch.float64, device=t.device)
-        ll = torch.empty(1, dtype=torch.float64, device=t.device) if with_loglik else None
+        if out is not None:
+            mean, var, ll = out
+        else:
+            mean = torch.empty(n, dtype=torch.float64, device=t.device)
+            var = torch.empty(n, dtype=torch.float64, device=t.device)
+            ll = torch.empty(1, dtype=torch.float64, device=t.device) if with_loglik else None
         _check(spingp_posterior(self.h, t, y, n, theta, ll, mean, var, ws, ws.numel(),
                                 self._flags(sync, missing, predictive=predictive)), "spingp_posterior")
         return mean, var, ll

@@ -68,3 +68,6 @@ def test_reference_arm_prints_one_valid_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == "matern52_n4m"
+    # the reference arm times the whole series, the configuration the GPU arm runs
+    assert d["config"]["n"] == 300000 and "sample_steps" not in d["config"]
+    assert abs(d["ms_per_step"] - 1e3 * 300000 / d["value"]) <= 1e-9 * d["ms_per_step"]

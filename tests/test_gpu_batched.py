@@ -141,15 +141,21 @@ def test_batched_graph_capture():
 def test_batched_full_config_sampled():
     """The batched workload at full size: 4096 Matern-5/2 series, lengths
     log-uniform in [256, 65536] (about 4.8e7 steps), per-series hyperparameters;
-    48 sampled series against the oracle, the rest by the variance-scaling
-    identity (a property that holds for every series)."""
+    48 series against the oracle -- the longest, the shortest, the ones with
+    the smallest and largest lengthscale and 44 drawn at random -- and every
+    series by the variance-scaling identity (a property that holds for each)."""
     s = synth.batched()
     offsets, th = s.extra["offsets"], s.extra["thetas"]
     m = spingp.Model("matern52")
     bt = spingp.Batch(m, _t(offsets, torch.int64), _t(s.t), _t(s.y))
     ll, g = bt.grad(_t(th.reshape(-1)))
     ll, g = ll.cpu().numpy(), g.cpu().numpy()
-    idx = np.random.default_rng(0).choice(len(th), 48, replace=False)
+    lens = np.diff(offsets)
+    ends = [int(np.argmax(lens)), int(np.argmin(lens)), int(np.argmin(th[:, 0])), int(np.argmax(th[:, 0]))]
+    rest = np.setdiff1d(np.arange(len(th)), ends)
+    idx = np.concatenate([ends, np.random.default_rng(0).choice(rest, 48 - len(set(ends)), replace=False)])
+    idx = np.unique(idx)
+    assert len(idx) == 48 and lens[idx].max() == lens.max() and lens[idx].min() == lens.min()
     check_series("matern52", offsets, s.t, s.y, th, ll, g, idx)
     th2 = th.copy(); th2[:, 1:] *= 2.0
     ll2 = bt.loglik(_t(th2.reshape(-1))).cpu().numpy()

@@ -29,6 +29,10 @@ def test_bench_line_has_the_contract_keys():
     ro = d["roofline"]
     assert ro["bound"] == "alu" and ro["unit"] == "TFLOP/s" and 0.0 < ro["frac"] < 1.5
     assert abs(ro["frac"] - ro["achieved"] / ro["peak"]) <= 1e-12
+    # the dense sequential method's flops (oracle/flops.py) over the whole call
+    assert ro["algorithmic_flops_per_step"] == 575.0
+    assert abs(ro["algorithmic_achieved"] - 575.0 * d["value"] / 1e12) <= 1e-9 * ro["algorithmic_achieved"]
+    assert abs(ro["algorithmic_frac"] - ro["algorithmic_achieved"] / ro["peak"]) <= 1e-12
     assert d["gpu_launches"] == 5 * d["graph_replay"]["gpu_launches_per_replay"]
     e = d["e2e"]
     assert e["h2d_bytes_per_step"] == 16 * n + 24 and e["d2h_bytes_per_step"] == 32 and e["value"] > 0

@@ -79,6 +79,27 @@ def test_config3_against_oracle():
     check(s.spec, s.theta, s.t, s.y, 0, posterior=True)
 
 
+def test_config3_full_size_against_oracle():
+    """The b = 16 workload (Matern-3/2 + quasi-periodic of order 6 with a
+    Matern-1/2 envelope, 7 parameters) in the benchmark's launch
+    configuration: the log-likelihood over the whole N = 2^20 series, and the
+    log-likelihood and all 7 gradient entries over its first 2^18 steps,
+    against the oracle (its gradient at b = 16 runs at ~5e3 steps/s on one
+    host core, so the whole series' gradient would take minutes)."""
+    s = synth.single("sum_qp_n1m")
+    m = spingp.Model(s.spec)
+    ll = float(m.loglik(_t(s.t), _t(s.y), _t(s.theta)).cpu()[0])
+    llo = seq.loglik(s.spec, s.theta, s.t, s.y)
+    assert abs(ll - llo) <= 1e-9 * abs(llo), (ll, llo)
+    n = 1 << 18
+    t, y = s.t[:n], s.y[:n]
+    ll, g = m.grad(_t(t), _t(y), _t(s.theta))
+    ll, g = float(ll.cpu()[0]), g.cpu().numpy()
+    llo, go, g1 = seq.grad(s.spec, s.theta, t, y, l1=True)
+    assert abs(ll - llo) <= 1e-9 * abs(llo), (ll, llo)
+    assert np.all(np.abs(g - go) <= 1e-8 * np.maximum(np.abs(go), g1)), (g, go, g1)
+
+
 def test_config3_full_size_identity():
     """b = 16 at N = 2^20: scaling every variance (s_m32, s_per, s_n) by c scales
     C by c, so sum_v s_v dl/ds_v = (y^T C^-1 y - N)/2 with y^T C^-1 y read off

@@ -207,18 +207,20 @@ def test_workspace_too_small_is_rejected():
 def test_large_series_full_size():
     """Matern-3/2, N = 2^26, dt ~ Exp(0.001), l = 0.05 (the long-series
     workload) in the default launch configuration.  Checks: the log-likelihood
-    against the oracle over the whole series; the posterior mean and variance
-    at 16 sampled steps against the oracle on a window of +-20000 steps around
-    each (400 lengthscales: the data outside the window changes the posterior
-    at its centre by far less than FP64 resolution); and the variance-scaling
+    and all three gradient entries against the oracle over the whole series
+    (the L1-scaled gradient bar); the posterior mean and variance at 16
+    sampled steps against the oracle on a window of +-20000 steps around each
+    (400 lengthscales: the data outside the window changes the posterior at
+    its centre by far less than FP64 resolution); and the variance-scaling
     identity for the gradient."""
     s = synth.single("matern32_n64m")
     m = spingp.Model(s.spec)
     T, Y, TH = _t(s.t), _t(s.y), _t(s.theta)
     ll, g = m.grad(T, Y, TH)
     ll, g = float(ll.cpu()[0]), g.cpu().numpy()
-    llo = seq.loglik(s.spec, s.theta, s.t, s.y)
+    llo, go, g1 = seq.grad(s.spec, s.theta, s.t, s.y, l1=True)
     assert abs(ll - llo) <= 1e-9 * abs(llo), (ll, llo)
+    assert np.all(np.abs(g - go) <= 1e-8 * np.maximum(np.abs(go), g1)), (g, go, g1)
     mean, var, _ = m.posterior(T, Y, TH, with_loglik=False)
     mean, var = mean.cpu().numpy(), var.cpu().numpy()
     idx = np.random.default_rng(1).integers(20000, len(s.t) - 20000, 16)
@@ -234,6 +236,38 @@ def test_large_series_full_size():
     q = 4.0 * (ll2 - ll + 0.5 * n * np.log(2.0))
     lhs = s.theta[1] * g[1] + s.theta[2] * g[2]
     assert abs(lhs - (0.5 * q - 0.5 * n)) <= 1e-8 * (abs(s.theta[1] * g[1]) + abs(s.theta[2] * g[2]) + n)
+
+
+def test_large_series_step_in_a_captured_graph():
+    """The long-series workload's step (N = 2^26: log-likelihood, gradient
+    and posterior mean) captured once into a CUDA graph and replayed: the
+    replay writes the same bits as the eager calls."""
+    s = synth.single("matern32_n64m")
+    n = len(s.t)
+    m = spingp.Model(s.spec)
+    T, Y, TH = _t(s.t), _t(s.y), _t(s.theta)
+    ll_e, g_e = m.grad(T, Y, TH)
+    mean_e, var_e, _ = m.posterior(T, Y, TH, with_loglik=False)
+    ll = torch.empty(1, dtype=torch.float64, device=DEV)
+    g = torch.empty(3, dtype=torch.float64, device=DEV)
+    mean = torch.empty(n, dtype=torch.float64, device=DEV)
+    var = torch.empty(n, dtype=torch.float64, device=DEV)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            m.grad(T, Y, TH, sync=False, out=(ll, g))
+            m.posterior(T, Y, TH, sync=False, with_loglik=False, out=(mean, var, None))
+    torch.cuda.current_stream().wait_stream(stream)
+    for _ in range(2):
+        ll.fill_(float("nan")); g.fill_(float("nan")); mean.fill_(float("nan"))
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(ll, ll_e) and torch.equal(g, g_e)
+        assert torch.equal(mean, mean_e) and torch.equal(var, var_e)
+    assert spingp.spingp_ws_status(m.workspace(n, spingp.WS_GRAD, DEV)) == spingp.OK
+    assert spingp.spingp_ws_status(m.workspace(n, spingp.WS_POSTERIOR, DEV)) == spingp.OK
 
 
 @pytest.mark.parametrize("spec", [["matern52"], ["matern32", ("quasiperiodic", 3, "matern12")]])
