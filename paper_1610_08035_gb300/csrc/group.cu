@@ -149,9 +149,9 @@ __global__ void k_gsetup(GModel gm, const double* __restrict__ theta, double* __
 
 // Phi for step i (transition from t_{i-1}): 4 entries per block, row-major.
 // (t_prev: the time before step 0 when the steps continue a split series, s0 = -1)
-// The coupling blocks of the EQ component's transition F = expm(T x), block
-// (k, i) for sections k > i, written to out[4 (k (k - 1) / 2 + i) ..]
-// row-major.  T has the diagonal blocks T_k = a_k I + b_k J, J = [[0, 1],
+// The EQ component's blocks of the transition F = expm(T x): its diagonal
+// blocks at ph[4 k ..], and the coupling blocks (k, i) for sections k > i at
+// ph[4 GK + 4 (k (k - 1) / 2 + i) ..], row-major.  T has the diagonal blocks T_k = a_k I + b_k J, J = [[0, 1],
 // [-1, 0]], and below them T_ki = -u_k w_i^T.  F commutes with T, and with
 // E = F - I block (k, i) of T F = F T reads
 //   T_k E_ki - E_ki T_i = E_kk T_ki - T_ki E_ii + sum_{i<j<k} (E_kj T_ji - T_kj E_ji)
@@ -165,19 +165,24 @@ __global__ void k_gsetup(GModel gm, const double* __restrict__ theta, double* __
 // each part is solved by one complex division (reciprocal moduli from the
 // model).  Row k runs i = k-1 down to 0, so p accumulates along the row and q
 // per column.
-__device__ void g_eq_coupling(const GModel& gm, double x, double* __restrict__ out) {
+__device__ void g_eq_blocks(const GModel& gm, double x, double* __restrict__ ph) {
     const int nk = gm.eq_nk;
+    double* __restrict__ out = ph + 4 * GK;
     double c0[GK], c1[GK], q0[GK], q1[GK];
 #pragma unroll
     for (int k = 0; k < GK; ++k) {
         c0[k] = 0.0; c1[k] = 0.0; q0[k] = 0.0; q1[k] = 0.0;
         if (k < nk) {
-            const double bx = gm.eqb[k] * x;
-            double sn, cs;
-            sincos(bx, &sn, &cs);
-            const double sh = sin(0.5 * bx), em = expm1(gm.eqa[k] * x);
-            c0[k] = fma(em, cs, -2.0 * sh * sh);     // e^(a x) cos(b x) - 1
-            c1[k] = (1.0 + em) * sn;                 // e^(a x) sin(b x)
+            // with s, c = sin, cos(b x / 2): e^(a x) cos(b x) - 1 = expm1(a x)(1 - 2 s^2) - 2 s^2
+            // and e^(a x) sin(b x) = e^(a x) 2 s c, free of cancellation for small x
+            double sh, ch;
+            sincos(0.5 * gm.eqb[k] * x, &sh, &ch);
+            const double em = expm1(gm.eqa[k] * x), s2 = 2.0 * sh * sh;
+            c0[k] = fma(em, 1.0 - s2, -s2);
+            c1[k] = (1.0 + em) * (2.0 * sh * ch);
+            // the diagonal block e^(a x) [[cos bx, sin bx], [-sin bx, cos bx]] = I + E_kk
+            ph[4 * k + 0] = 1.0 + c0[k]; ph[4 * k + 1] = c1[k];
+            ph[4 * k + 2] = -c1[k];      ph[4 * k + 3] = 1.0 + c0[k];
             // q_k starts at E_kk^T w_k, E_kk = [[c0, c1], [-c1, c0]]
             const double w0 = gm.eqw[2 * k], w1 = gm.eqw[2 * k + 1];
             q0[k] = fma(c0[k], w0, -c1[k] * w1);
@@ -223,12 +228,12 @@ __global__ void __launch_bounds__(256) k_gdisc(GModel gm, const double* __restri
     const double dt = (i > 0) ? t[i] - t[i - 1] : (s0 < 0 ? t[0] - t_prev : 0.0);
     if (dt < 0.0) bad |= ST_ENOTSORTED;
     double* ph = phis + i * gm.phs;
-    // per component, once: x = dt / l of the EQ blocks; the rotation by w dt
-    // and the envelope of a (quasi-)periodic component, whose harmonic j + 1
-    // follows from harmonic j by angle addition (its blocks come in order
-    // j = 0, 1, .., J)
+    // per component, once: the rotation by w dt and the envelope of a
+    // (quasi-)periodic component, whose harmonic j + 1 follows from harmonic
+    // j by angle addition (its blocks come in order j = 0, 1, .., J); the EQ
+    // sections are written by g_eq_blocks
     int pc = -1, pj = -1;
-    double xe = 0.0, wdt = 0.0, c1 = 1.0, s1 = 0.0, cj = 1.0, sj = 0.0, env = 1.0;
+    double wdt = 0.0, c1 = 1.0, s1 = 0.0, cj = 1.0, sj = 0.0, env = 1.0;
 #pragma unroll 1
     for (int k = 0; k < GK; ++k) {
         double p00 = 0.0, p01 = 0.0, p10 = 0.0, p11 = 0.0;
@@ -241,12 +246,8 @@ __global__ void __launch_bounds__(256) k_gdisc(GModel gm, const double* __restri
                 phi<2>(lam * dt, exp(-lam * dt), P);
                 p00 = P[0][0]; p01 = P[0][1]; p10 = P[1][0]; p11 = P[1][1];
             } else if (gm.bkind[k] == GB_EQ) {
-                // expm([[a, b], [-b, a]] x) = e^(a x) [[cos bx, sin bx], [-sin bx, cos bx]], x = dt / l
-                if (comp != pc) xe = dt / th[0];
-                double sn, cs;
-                sincos(gm.eqb[k] * xe, &sn, &cs);
-                const double e = exp(gm.eqa[k] * xe);
-                p00 = e * cs; p01 = e * sn; p10 = -e * sn; p11 = e * cs;
+                pc = comp;
+                continue;                 // g_eq_blocks below
             } else {
                 const int j = gm.bj[k];
                 if (comp != pc) {
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(256) k_gdisc(GModel gm, const double* __restri
         }
         ph[4 * k + 0] = p00; ph[4 * k + 1] = p01; ph[4 * k + 2] = p10; ph[4 * k + 3] = p11;
     }
-    if (gm.eq_nk > 1) g_eq_coupling(gm, dt / theta[gm.cpoff[gm.eq_comp]], ph + 4 * GK);
+    if (gm.eq_nk > 0) g_eq_blocks(gm, dt / theta[gm.cpoff[gm.eq_comp]], ph);
     if (bad) atomicOr(status, bad);
 }
 
@@ -356,13 +357,16 @@ __device__ __forceinline__ const double* g_cpl(const double* __restrict__ ph, in
     return ph + 4 * GK + 4 * (k * (k - 1) / 2 + i);
 }
 // X <- A X for a column: the diagonal blocks, plus sum_{i<k} A_ki X_i on the
-// rows of EQ section k (nk sections, the first blocks of the state)
+// rows of EQ section k (nk sections, the first blocks of the state); the
+// blocks run from the last down, so the rows a block reads are still the
+// input's, and the coupling terms accumulate into the diagonal block's sums
 template <int NR>
 __device__ __forceinline__ void g_left_c(const double* __restrict__ ph, int nk, double (&X)[GL]) {
-    double add[NR];
 #pragma unroll
-    for (int k = 0; k < NR / 2; ++k) {
-        double s0 = 0.0, s1 = 0.0;
+    for (int k = NR / 2 - 1; k >= 0; --k) {
+        const double a = ph[4 * k], b = ph[4 * k + 1], c = ph[4 * k + 2], d = ph[4 * k + 3];
+        const double x0 = X[2 * k], x1 = X[2 * k + 1];
+        double s0 = b * x1, s1 = d * x1;
         if (k > 0 && k < nk) {
 #pragma unroll
             for (int i = 0; i < k; ++i) {
@@ -371,19 +375,19 @@ __device__ __forceinline__ void g_left_c(const double* __restrict__ ph, int nk, 
                 s1 = fma(o[2], X[2 * i], fma(o[3], X[2 * i + 1], s1));
             }
         }
-        add[2 * k] = s0; add[2 * k + 1] = s1;
+        X[2 * k] = fma(a, x0, s0);
+        X[2 * k + 1] = fma(c, x0, s1);
     }
-    g_left<NR>(ph, X);
-#pragma unroll
-    for (int r = 2; r < NR; ++r) X[r] += add[r];
 }
 // X <- A^T X for a column: sum_{k>i} A_ki^T X_k on the rows of section i
+// (the blocks run from the first up, for the same reason)
 template <int NR>
 __device__ __forceinline__ void g_left_t_c(const double* __restrict__ ph, int nk, double (&X)[GL]) {
-    double add[NR];
 #pragma unroll
     for (int i = 0; i < NR / 2; ++i) {
-        double s0 = 0.0, s1 = 0.0;
+        const double a = ph[4 * i], b = ph[4 * i + 1], c = ph[4 * i + 2], d = ph[4 * i + 3];
+        const double x0 = X[2 * i], x1 = X[2 * i + 1];
+        double s0 = c * x1, s1 = d * x1;
 #pragma unroll
         for (int k = i + 1; k < NR / 2; ++k) {
             if (k < nk) {
@@ -392,11 +396,9 @@ __device__ __forceinline__ void g_left_t_c(const double* __restrict__ ph, int nk
                 s1 = fma(o[1], X[2 * k], fma(o[3], X[2 * k + 1], s1));
             }
         }
-        add[2 * i] = s0; add[2 * i + 1] = s1;
+        X[2 * i] = fma(a, x0, s0);
+        X[2 * i + 1] = fma(b, x0, s1);
     }
-    g_left_t<NR>(ph, X);
-#pragma unroll
-    for (int r = 0; r < NR; ++r) X[r] += add[r];
 }
 // X <- its row 'lane', given its column 'lane' in every lane of the group:
 // a transpose through the group's shared scratch tb (rows of stride GL + 1,
@@ -428,15 +430,42 @@ __device__ __forceinline__ void g_sandwich_t_c(const double* __restrict__ ph, in
     g_transpose<NR>(tb, lane, X);
     g_left_t_c<NR>(ph, nk, X);
 }
-// entry 'lane' of A v (resp. A^T v) for a lane-distributed vector v
-template <int NR, bool TR>
+// entry 'lane' of A v for a lane-distributed vector v: the diagonal block
+// through the partner lane, and for a lane of EQ section k the couplings
+// A_ki, i < k, from the gathered entries of the sections before it
+template <int NR>
 __device__ __forceinline__ double g_vleft_c(const double* __restrict__ ph, int nk, int lane, double v) {
+    double r = g_vleft(ph, lane, v);
     double vv[GL];
-    ggather<NR>(v, vv);
-    if constexpr (TR) g_left_t_c<NR>(ph, nk, vv); else g_left_c<NR>(ph, nk, vv);
-    double r = 0.0;
 #pragma unroll
-    for (int q = 0; q < NR; ++q) r = (q == lane) ? vv[q] : r;
+    for (int q = 0; q < NR; ++q)
+        if (q < 2 * (nk - 1)) vv[q] = gshfl(v, q);    // uniform over the group
+    const int k = lane >> 1, odd = lane & 1;
+#pragma unroll
+    for (int i = 0; i < NR / 2 - 1; ++i) {
+        if (i < k && k < nk) {
+            const double* o = g_cpl(ph, k, i) + 2 * odd;
+            r = fma(o[0], vv[2 * i], fma(o[1], vv[2 * i + 1], r));
+        }
+    }
+    return r;
+}
+// entry 'lane' of A^T v: for a lane of section i, the couplings A_ki^T, k > i
+template <int NR>
+__device__ __forceinline__ double g_vleft_t_c(const double* __restrict__ ph, int nk, int lane, double v) {
+    double r = g_vleft_t(ph, lane, v);
+    double vv[GL];
+#pragma unroll
+    for (int q = 2; q < NR; ++q)
+        if (q < 2 * nk) vv[q] = gshfl(v, q);
+    const int i = lane >> 1, odd = lane & 1;
+#pragma unroll
+    for (int k = 1; k < NR / 2; ++k) {
+        if (k > i && k < nk) {
+            const double* o = g_cpl(ph, k, i) + odd;
+            r = fma(o[0], vv[2 * k], fma(o[2], vv[2 * k + 1], r));
+        }
+    }
     return r;
 }
 
@@ -625,7 +654,7 @@ __global__ void __launch_bounds__(GCTA) k_gfold(GArgs a, double* __restrict__ no
             const double* ph = a.phis + i * phs;
             if constexpr (EQT) {
                 g_left_c<NR>(ph, nk, el.A);
-                el.bv = g_vleft_c<NR, false>(ph, nk, lane, el.bv);
+                el.bv = g_vleft_c<NR>(ph, nk, lane, el.bv);
                 g_sandwich_c<NR>(ph, nk, tb, lane, Cm);
             } else {
                 g_left<NR>(ph, el.A);
@@ -986,7 +1015,7 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
 #pragma unroll
             for (int r = 0; r < NR; ++r) Db[r] = D[r];
             if constexpr (EQT) {
-                mb = g_vleft_c<NR, false>(ph, nk, lane, m);
+                mb = g_vleft_c<NR>(ph, nk, lane, m);
                 g_sandwich_c<NR>(ph, nk, tb, lane, Db);
             } else {
                 mb = g_vleft(ph, lane, m);
@@ -1083,7 +1112,14 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
         // gp, geq and G below carry twice their values (the factor 1/2 of the
         // adjoint is applied once per chunk, an exact power-of-two scaling)
         double gp = 0.0;   // diagonal entry 'lane' of the Pinf adjoint
-        double geq = 0.0;  // column 'lane' of the Pinf adjoint contracted with the EQ block's P_m
+        double geq = 0.0;  // column 'lane' of the Pinf adjoint contracted with the EQ sections' P
+        // dPinf / d(EQ variance) is block diagonal (a 2 x 2 block per section):
+        // column 'lane' has nonzeros only in the rows of the lane's own
+        // section, which are this lane's and its partner's
+        const int eb = lane >> 1;
+        const bool eq_lane = has_eq && eb < a.gm.eq_nk;
+        const double pe0 = eq_lane ? s_dpe[(2 * eb) * GL + lane] : 0.0;
+        const double pe1 = eq_lane ? s_dpe[(2 * eb + 1) * GL + lane] : 0.0;
         for (int64_t i = e - 1; i >= s; --i) {
             const int64_t j = i - s;
             const double* st = store + ((j * nc + c) * GNF) * GL + lane;
@@ -1149,8 +1185,11 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                 for (int r = 0; r < NR; ++r) gsel = (r == lane) ? G[r] : gsel;
                 gp += gsel;
                 if (has_eq) {
+                    double g0 = 0.0, g1 = 0.0;   // rows 2 eb, 2 eb + 1 of G's column: selects
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) geq = fma(s_dpe[r * GL + lane], G[r], geq);
+                    for (int q = 0; q < NR / 2; ++q)
+                        if (q == eb) { g0 = G[2 * q]; g1 = G[2 * q + 1]; }
+                    geq = fma(pe0, g0, fma(pe1, g1, geq));
                 }
             }
             if (i > a.s0) {
@@ -1213,7 +1252,7 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
 #pragma unroll
                 for (int r = 0; r < NR; ++r) Lh[r] = Lt[r];
                 if constexpr (EQT) {
-                    lh = g_vleft_c<NR, true>(ph, nk, lane, lt);
+                    lh = g_vleft_t_c<NR>(ph, nk, lane, lt);
                     g_sandwich_t_c<NR>(ph, nk, tb, lane, Lh);
                 } else {
                     lh = g_vleft_t(ph, lane, lt);
@@ -1226,13 +1265,14 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                     for (int r = 0; r < NR; ++r)
                         if (r == lane) ld = Lh[r];
                     gp -= fma(lh, lh, -ld);
-                    if (has_eq) {   // minus column 'lane' of 2 Phi^T G Phi = lh lh^T - Lh
-                        double lv2[GL];
-                        ggather<NR>(lh, lv2);
-                        double t = 0.0;
+                    if (has_eq) {   // minus column 'lane' of 2 Phi^T G Phi = lh lh^T - Lh, rows 2 eb, 2 eb + 1
+                        const double lp = gxor(lh, 1);
+                        const double l0 = (lane & 1) ? lp : lh, l1 = (lane & 1) ? lh : lp;
+                        double h0 = 0.0, h1 = 0.0;
 #pragma unroll
-                        for (int r = 0; r < NR; ++r) t = fma(s_dpe[r * GL + lane], fma(lv2[r], lh, -Lh[r]), t);
-                        geq -= t;
+                        for (int q = 0; q < NR / 2; ++q)
+                            if (q == eb) { h0 = Lh[2 * q]; h1 = Lh[2 * q + 1]; }
+                        geq -= fma(pe0, fma(l0, lh, -h0), pe1 * fma(l1, lh, -h1));
                     }
                 }
             }
