@@ -168,6 +168,21 @@ spingp_status spingp_posterior(const spingp_model* model, const double* t, const
                                const double* theta, double* ll_out, double* mean_out, double* var_out,
                                void* ws, size_t ws_bytes, unsigned flags, void* stream);
 
+/* spingp_posterior plus the first off-diagonal of the selected inverse
+ * (Sec. 3.1: the blocks of inv(K~) next to its diagonal, subproblem 4's
+ * operand) for the latent function: cov_lag1_out[i] = H P^s_{i+1,i} H^T =
+ * Cov(f(t_{i+1}), f(t_i) | y) for i = 0 .. n-2 (device, n - 1 doubles; may be
+ * NULL only when n = 1).  P^s_{i+1,i} is formed in the reverse sweep as
+ * (I - Pb_{i+1} Lt_{i+1}) A_{i+1} P_i, with P_i the filtered covariance and
+ * Lt_{i+1} the adjoint information of y_{i+1} and after on the predicted
+ * state; a missing observation (SPINGP_MISSING_NAN) leaves Lt unchanged
+ * there.  The same workspace and flags as spingp_posterior (SPINGP_PREDICTIVE
+ * affects var_out only). */
+spingp_status spingp_posterior_lag1(const spingp_model* model, const double* t, const double* y, int64_t n,
+                                    const double* theta, double* ll_out, double* mean_out, double* var_out,
+                                    double* cov_lag1_out, void* ws, size_t ws_bytes, unsigned flags,
+                                    void* stream);
+
 /* ---- batches of independent series ----------------------------------------
  * n_series series, each with its own hyperparameters, concatenated: series i
  * owns steps [offsets[i], offsets[i+1]) of t and y, with offsets[0] = 0,

@@ -198,7 +198,7 @@ spingp_status profile_slot(const spingp_model* m, cudaEvent_t** ev) {
 
 spingp_status run(const spingp_model* m, int mode, const double* t, const double* y, int64_t n,
                   const double* theta, double* ll, double* grad, double* mean, double* var, void* ws,
-                  size_t ws_bytes, unsigned flags, void* stream) {
+                  size_t ws_bytes, unsigned flags, void* stream, double* lag1 = nullptr) {
     if (!m || !t || !y || !theta || !ws || n < 1) return SPINGP_EINVAL;
     if (((uintptr_t)ws & 255u) != 0) return SPINGP_EINVAL;
     if (!single_matern(m) && !m->group) return SPINGP_EUNSUPPORTED;
@@ -212,8 +212,8 @@ spingp_status run(const spingp_model* m, int mode, const double* t, const double
     st = profile_slot(m, &ev);
     if (st != SPINGP_OK) return st;
     const int miss = (flags & SPINGP_MISSING_NAN) ? 1 : 0;
-    int rc = m->group ? spg::group_run(m->gm, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s, ev, miss)
-                      : spg::matern_run(m->b, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s, ev, miss);
+    int rc = m->group ? spg::group_run(m->gm, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s, ev, miss, lag1)
+                      : spg::matern_run(m->b, mode, t, y, n, L, theta, ll, grad, mean, var, ws, s, ev, miss, nullptr, lag1);
     if (!rc && grad && (flags & SPINGP_LOG_GRAD)) rc = spg::grad_to_log(grad, theta, m->P, s);
     if (!rc && var && (flags & SPINGP_PREDICTIVE)) rc = spg::add_noise(var, n, theta + m->P - 1, s);
     if (rc) return SPINGP_ECUDA;
@@ -397,6 +397,14 @@ spingp_status spingp_posterior(const spingp_model* m, const double* t, const dou
     if (!mean_out || !var_out) return SPINGP_EINVAL;
     return run(m, spg::MODE_POSTERIOR, t, y, n, theta, ll_out, NULL, mean_out, var_out, ws, ws_bytes, flags,
                stream);
+}
+
+spingp_status spingp_posterior_lag1(const spingp_model* m, const double* t, const double* y, int64_t n,
+                                    const double* theta, double* ll_out, double* mean_out, double* var_out,
+                                    double* cov_lag1_out, void* ws, size_t ws_bytes, unsigned flags, void* stream) {
+    if (!mean_out || !var_out || (n > 1 && !cov_lag1_out)) return SPINGP_EINVAL;
+    return run(m, spg::MODE_POSTERIOR, t, y, n, theta, ll_out, NULL, mean_out, var_out, ws, ws_bytes, flags,
+               stream, n > 1 ? cov_lag1_out : nullptr);
 }
 
 int spingp_launch_count(const spingp_model* m, int64_t n, spingp_ws_kind what) {

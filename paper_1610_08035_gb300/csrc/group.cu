@@ -617,6 +617,7 @@ struct GArgs {
     int missing;          // 1: a NaN observation is missing (a test point)
     int64_t s0;           // the series' first step: 0, or -1 when the steps continue a split series
     double t_prev;        // with s0 = -1: the time of the step before step 0
+    double* lag1 = nullptr;   // posterior: n - 1 entries Cov(f_{i+1}, f_i | y), or NULL
 };
 
 // EQT: the model has an EQ component of two or more sections (coupling
@@ -992,12 +993,15 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
 
     // ---- forward from the prefix state (m, D = P - Pinf)
     double m, D[GL];
+    double pe_pre;   // (P h)[lane] of the filtered state before the chunk (the lag-one output)
     {
         double P[GL];
         gvs_load<NR>(pre, nc, c, lane, P, m);
+        pe_pre = g_hsum<NR>(P);
 #pragma unroll
         for (int r = 0; r < NR; ++r) D[r] = P[r] - s_pinf[r * GL + lane];
     }
+    (void)pe_pre;
     double quad = 0.0, prod = 1.0;
     int expo = 0;
     int64_t nobs = 0;
@@ -1046,8 +1050,9 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
             st[GL * GL] = mb;
             st[(GL + 1) * GL] = v;
             st[(GL + 2) * GL] = rS;
-            // the posterior's missing step keeps (Pb h)[lane] there, for its prediction
-            st[(GL + 3) * GL] = (POST && !obs) ? p0 : pr;
+            // the gradient keeps the gain entry there; the posterior keeps
+            // (Pb h)[lane] (the prediction at a missing step, the lag-one term)
+            st[(GL + 3) * GL] = POST ? p0 : pr;
         }
         double pv[GL];
         ggather<NR>(p0, pv);
@@ -1129,9 +1134,14 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
             const double mb = st[GL * GL];
             const double v = st[(GL + 1) * GL];
             const double rS = st[(GL + 2) * GL];
-            // the gain entry; (Pb h)[lane] at a missing step of the posterior,
-            // whose kl, kuk below are then (Pb h)^T lh and (Pb h)^T Lh (Pb h)
-            const double k = st[(GL + 3) * GL];
+            // the gain entry (Pb h)[lane] / S; (Pb h)[lane] itself at a missing
+            // step of the posterior, whose kl, kuk below are then (Pb h)^T lh
+            // and (Pb h)^T Lh (Pb h)
+            const double ks = st[(GL + 3) * GL];
+            double k = ks;
+            if constexpr (POST) {
+                if (!(a.missing && isnan(a.y[i]))) k = ks * rS;
+            }
             double kl = gsum(k * lh);
             double kv[GL];
             ggather<NR>(k, kv);
@@ -1194,6 +1204,29 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
             }
             if (i > a.s0) {
                 const double* ph = a.phis + i * phs;
+                if constexpr (POST) {
+                    if (a.lag1) {
+                        // Cov(f_i, f_{i-1} | y) = h^T w - (Pb h)^T Lt w, w = A P_{i-1} h
+                        // (Lt: the adjoint with y_i and after, on the predicted state i;
+                        // P_{i-1} h = (Pb_{i-1} h) s_n / S_{i-1}, or Pb_{i-1} h at a
+                        // missing step; the chunk's prefix state before its first step)
+                        double w = pe_pre;
+                        if (i > s) {
+                            const double* sp = store + (((j - 1) * nc + c) * GNF) * GL + lane;
+                            const double rsp = sp[(GL + 2) * GL];
+                            w = sp[(GL + 3) * GL] * ((rsp == 0.0) ? 1.0 : s2 * rsp);
+                        }
+                        if constexpr (EQT) w = g_vleft_c<NR>(ph, nk, lane, w);
+                        else w = g_vleft(ph, lane, w);
+                        double pv[GL];
+                        ggather<NR>(ks, pv);
+                        double tl2 = 0.0;                       // (Pb h)^T Lt[:, lane]
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) tl2 = fma(pv[r], Lt[r], tl2);
+                        const double hw = gsum(even ? w : 0.0), q = gsum(w * tl2);
+                        if (lane == 0) a.lag1[i - 1] = hw - q;
+                    }
+                }
                 if constexpr (GRAD) {
                     const double dt = (i > 0) ? a.t[i] - a.t[i - 1] : a.t[0] - a.t_prev;
                     // per block: 2 <G_k,:, X_k Db_k,:> (column 'lane' part) - lt_k^T X_k mb_k (row 'lane' part);
@@ -1477,7 +1510,7 @@ int group_launch_count(int64_t n, int64_t L, int mode) {
 
 int group_run(const GModel& gm, int mode, const double* t, const double* y, int64_t n, int64_t L,
               const double* theta, double* ll_out, double* grad_out, double* mean_out, double* var_out, void* wsv,
-              cudaStream_t st, cudaEvent_t* ev, int missing) {
+              cudaStream_t st, cudaEvent_t* ev, int missing, double* lag1_out) {
     GLayout lay(n, L, mode, gm.phs);
     char* ws = (char*)wsv;
     int* status = (int*)ws;
@@ -1486,6 +1519,7 @@ int group_run(const GModel& gm, int mode, const double* t, const double* y, int6
     double* part = (double*)(ws + lay.off_part);
     double* store = (double*)(ws + lay.off_store);
     GArgs a{gm, t, y, n, L, lay.nc, theta, gconst, phis, status, missing, 0, 0.0};
+    a.lag1 = (mode == MODE_POSTERIOR) ? lag1_out : nullptr;
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
     if (ev) cudaEventRecord(ev[0], st);
     k_gsetup<<<1, 32, 0, st>>>(gm, theta, gconst, status);

@@ -67,9 +67,10 @@ struct HostFeed {
     cudaEvent_t ev[1 + FEED_PIECES];
     int npieces;
 };
+// lag1_out (posterior only, else ignored): n - 1 entries Cov(f_{i+1}, f_i | y), or NULL
 int matern_run(int b, int mode, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
                double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws, cudaStream_t st,
-               cudaEvent_t* ev, int missing, const HostFeed* feed = nullptr);
+               cudaEvent_t* ev, int missing, const HostFeed* feed = nullptr, double* lag1_out = nullptr);
 int matern_launch_count(int b, int64_t n, int64_t L, int mode);
 // output conventions by flag (post.cu): the gradient in log theta (count
 // entries, theta in the same layout), predictive variances (latent + s_n)
@@ -139,7 +140,7 @@ size_t group_ws_bytes(const GModel& gm, int64_t n, int64_t L, int mode);
 int group_launch_count(int64_t n, int64_t L, int mode);
 int group_run(const GModel& gm, int mode, const double* t, const double* y, int64_t n, int64_t L,
               const double* theta, double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws,
-              cudaStream_t st, cudaEvent_t* ev, int missing);
+              cudaStream_t st, cudaEvent_t* ev, int missing, double* lag1_out = nullptr);
 int group_segment(const GModel& gm, int phase, const double* t, const double* y, int64_t n, int64_t L,
                   const double* theta, double t_prev, int first, const double* elems, int G, int rank,
                   double* elem_out, double* ll_out, double* grad_out, void* ws, cudaStream_t st, int missing);

@@ -50,6 +50,8 @@ struct ChainArgs {
     // step before step 0
     int64_t s0;
     double t_prev;
+    // posterior of one series: n - 1 entries Cov(f_{i+1}, f_i | y), or NULL
+    double* lag1 = nullptr;
 };
 
 // The steps of chunk c: [s, e), inside the series that starts at step s0 and
@@ -662,14 +664,18 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
         for (int r = 0; r < B; ++r) sp0[r] = sf * pj<B>(r, 0);
         // ---- 2. forward: filtered mean m and D = P - Pinf
         double m[B], D[B][B];
+        double pe_pre[B];   // P e1 of the filtered state before the chunk (the lag-one output)
         {
             double P[B][B];
             vs_load<B>(spre, 1, (int64_t)tid * NM, m, P);
 #pragma unroll
-            for (int r = 0; r < B; ++r)
+            for (int r = 0; r < B; ++r) {
+                pe_pre[r] = P[r][0];
 #pragma unroll
                 for (int q = 0; q < B; ++q) D[r][q] = P[r][q] - sf * pj<B>(r, q);
+            }
         }
+        (void)pe_pre;
         double quad = 0.0, prod = 1.0;
         int expo = 0;
         int64_t nobs = 0;
@@ -854,6 +860,37 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
                 Lt[0][0] = Lt[0][0] - 2.0 * u[0] + cc;
                 if (i > cr.s0) {
                     const double x = tr[0];
+                    if constexpr (POST) {
+                        if (a.lag1) {
+                            // Cov(f_i, f_{i-1} | y) = e1^T w - Pb_0^T Lt w with
+                            // w = A P_{i-1} e1 (Lt: the adjoint with y_i and after, the
+                            // information on the predicted state i; P_{i-1}: the filtered
+                            // covariance, Pb_{i-1} e1 times s_n / S_{i-1}, or Pb_{i-1} e1 at
+                            // a missing step; the chunk's prefix state before its first step)
+                            double w[B];
+                            if (i > s) {
+                                const double rsp = snx[NF - 1];
+                                const double fac = (rsp == 0.0) ? 1.0 : s2 * rsp;
+#pragma unroll
+                                for (int r = 0; r < B; ++r)   // Db_prev[0][r]: row 0 of the stored upper triangle
+                                    w[r] = (snx[B + r] + sp0[r]) * fac;
+                            } else {
+#pragma unroll
+                                for (int r = 0; r < B; ++r) w[r] = pe_pre[r];
+                            }
+                            const JCoef<B> tw(x, tr[1]);
+                            jprop_vec<B>(tw, tr[2], w);
+                            double ltw = 0.0;
+#pragma unroll
+                            for (int r = 0; r < B; ++r) {
+                                double t = 0.0;
+#pragma unroll
+                                for (int q = 0; q < B; ++q) t = fma(Lt[r][q], w[q], t);
+                                ltw = fma(p0[r], t, ltw);
+                            }
+                            a.lag1[i - 1] = w[0] - ltw;
+                        }
+                    }
                     if constexpr (GRAD) {
                         // d ll/dx = <G2, F Db> - lt^T F mb with G2 = lt lt^T - Lt (= 2 G), F = N - I:
                         // <G2, N Db> - <G2, Db> - lt^T N mb + lt^T mb
@@ -1155,7 +1192,7 @@ int matern_launch_count_t(int64_t n, int64_t L, int mode) {
 template <int B>
 int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
                  double* ll_out, double* grad_out, double* mean_out, double* var_out, void* wsv, cudaStream_t st,
-                 cudaEvent_t* ev, int missing, const HostFeed* feed) {
+                 cudaEvent_t* ev, int missing, const HostFeed* feed, double* lag1_out) {
     Layout<B> lay(n, L, mode);
     char* ws = (char*)wsv;
     int* status = (int*)ws;
@@ -1167,7 +1204,8 @@ int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t 
     double* part = (double*)(ws + lay.off_part);
     double* store = (double*)(ws + lay.off_store);
     double* state = (double*)(ws + lay.off_state);
-    ChainArgs a{t, y, n, L, lay.nc, lay.nb, theta, status, nullptr, nullptr, 0, 3, missing, 0, 0.0};
+    ChainArgs a{t, y, n, L, lay.nc, lay.nb, theta, status, nullptr, nullptr, 0, 3, missing, 0, 0.0,
+                mode == MODE_POSTERIOR ? lag1_out : nullptr};
     const unsigned grid = (unsigned)lay.nb;
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
     if (ev) cudaEventRecord(ev[0], st);
@@ -1406,14 +1444,14 @@ int matern_prepare() {
 
 int matern_run(int b, int mode, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
                double* ll_out, double* grad_out, double* mean_out, double* var_out, void* ws, cudaStream_t st,
-               cudaEvent_t* ev, int missing, const HostFeed* feed) {
+               cudaEvent_t* ev, int missing, const HostFeed* feed, double* lag1_out) {
     switch (b) {
     case 1:
-        return matern_run_t<1>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev, missing, feed);
+        return matern_run_t<1>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev, missing, feed, lag1_out);
     case 2:
-        return matern_run_t<2>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev, missing, feed);
+        return matern_run_t<2>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev, missing, feed, lag1_out);
     default:
-        return matern_run_t<3>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev, missing, feed);
+        return matern_run_t<3>(mode, t, y, n, L, theta, ll_out, grad_out, mean_out, var_out, ws, st, ev, missing, feed, lag1_out);
     }
 }
 
