@@ -79,7 +79,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="spingp", choices=["spingp", "reference"])
     ap.add_argument("--n", type=int, default=0, help="override the series length (profiling runs only)")
-    ap.add_argument("--chunk", type=int, default=-1, help="chunk length; -1 = autotune, 0 = library default")
+    ap.add_argument("--chunk", type=int, default=-1,
+                    help="chunk length; -1 = autotune (with --only: the library default), 0 = library default")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -88,6 +89,10 @@ def parse():
                     help="skip the secondary workloads (b = 16 sum, 4096-series batch, N = 2^26)")
     ap.add_argument("--split", action="store_true",
                     help="the split-series path even on one GPU (under torchrun; N > 1 always uses it)")
+    ap.add_argument("--only", default="",
+                    help="profiling: time only this workload's gradient call (matern52_n4m, sum_qp_n1m, "
+                         "m32_eq10_n1m, matern32_n64m or batched_4096), --n steps (--n series for the batch), "
+                         "and print one short line")
     ap.add_argument("--no-next", action="store_true",
                     help="skip the rows built beyond the hot path (prediction, literal mode, BTD solver, "
                          "EQ oracle rate, batched SCG)")
@@ -218,11 +223,13 @@ def _time_calls(fn, K, flush, torch):
     return ms / K
 
 
-# Whole-call FP64 work per step executed by the kernels of each secondary
-# workload (ncu: flops = 2 DFMA + DADD + DMUL thread instructions, and every
-# instruction of the FP64 pipe), from the captures listed in
-# profiles/workload_kernels_grad.md; None until taken for the current kernels.
-WORKLOAD_EXEC_PER_STEP = {"sum_qp_n1m": None, "m32_eq10_n1m": None, "matern32_n64m": None, "batched_4096": None}
+# FP64 work per step executed by the per-step kernels of each secondary
+# workload (discretisation, elimination, chunk pass; ncu: flops = 2 DFMA +
+# DADD + DMUL thread instructions, and every FP64-pipe instruction), from the
+# captures in profiles/workload_kernels_grad.md.  The reduction levels (work
+# per chunk, not per step) are left out of the flops and kept in the time.
+WORKLOAD_EXEC_PER_STEP = {"sum_qp_n1m": (12310.5, 8059.1), "m32_eq10_n1m": (21120.6, 13421.2),
+                          "matern32_n64m": (215.1, 144.1), "batched_4096": (397.6, 246.9)}
 
 
 def extra_workloads(args, dev, flush, world, rank=0, fp64_tflops=None):
@@ -416,14 +423,15 @@ def batched_oracle_rate(s, n_series=1024):
 
 
 # Whole-call FP64 work per unit of the rows built beyond the hot path (ncu,
-# profiles/next_rows_kernels.md): flops = 2 DFMA + DADD + DMUL thread
+# profiles/next_rows_kernels.md; the b = 12 EQ row from its per-step kernels,
+# profiles/workload_kernels_grad.md): flops = 2 DFMA + DADD + DMUL thread
 # instructions; instructions = everything the FP64 pipe executed.  Units:
 # steps, or nodes for the BTD solver; the batched SCG's gradient evaluations
 # use the chain kernels' counts above.
 NEXT_FLOPS_PER_UNIT = {"prediction_n4m": 344.2, "literal_n1m": 2157.0, "btd_solve_n1m": 821.6,
-                       "eq_b12_n1m": None, "scg_batch_4096": 171.5 + 231.2}
+                       "eq_b12_n1m": 21120.6, "scg_batch_4096": 171.5 + 231.2}
 NEXT_FP64_INST_PER_UNIT = {"prediction_n4m": 226.0, "literal_n1m": 1485.5, "btd_solve_n1m": 520.0,
-                           "eq_b12_n1m": None, "scg_batch_4096": 107.1 + 141.6}
+                           "eq_b12_n1m": 13421.2, "scg_batch_4096": 107.1 + 141.6}
 
 
 def _next_roofline(key, units_per_s, fp64_tflops):
@@ -560,12 +568,56 @@ def next_rows(args, dev, flush, fp64_tflops):
     return res
 
 
+# ---------------------------------------------------------------- one workload alone (profiling)
+
+def run_only(args):
+    """The gradient call of one workload, --warmup untimed and --steps timed
+    calls (L2 flushed before each), at the workload's size or --n steps
+    (--n series for the batch): the command the ncu summaries in profiles/
+    capture."""
+    import torch
+
+    from paper_1610_08035_gb300 import spingp, synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    if args.only == "batched_4096":
+        s = synth.batched(n_series=args.n or 4096)
+        off = torch.tensor(s.extra["offsets"], dtype=torch.int64, device=dev)
+        m = spingp.Model("matern52")
+        bt = spingp.Batch(m, off, torch.tensor(s.t, device=dev), torch.tensor(s.y, device=dev))
+        TH = torch.tensor(s.theta, device=dev)
+        ll = torch.empty(bt.n_series, dtype=torch.float64, device=dev)
+        g = torch.empty(3 * bt.n_series, dtype=torch.float64, device=dev)
+        call = lambda: bt.grad(TH, sync=False, out=(ll, g))   # noqa: E731
+        units, what = len(s.t), "steps (%d series)" % bt.n_series
+    else:
+        s = synth.single(args.only, n=args.n or None, seed=1 if args.only == WORKLOAD else None)
+        T, Y, TH = (torch.tensor(a, device=dev) for a in (s.t, s.y, s.theta))
+        m = spingp.Model(s.spec)
+        ll = torch.empty(1, dtype=torch.float64, device=dev)
+        g = torch.empty(m.num_params, dtype=torch.float64, device=dev)
+        call = lambda: m.grad(T, Y, TH, sync=False, out=(ll, g))   # noqa: E731
+        units, what = len(s.t), "steps"
+    if args.chunk > 0:
+        m.set_chunk_len(args.chunk)
+    for _ in range(max(args.warmup, 0)):
+        call()
+    torch.cuda.synchronize()
+    ms = _time_calls(call, max(args.steps, 1), flush, torch)
+    print(json.dumps({"only": args.only, "units": units, "what": what, "ms_per_call": ms,
+                      "value": units / (ms * 1e-3), "unit": "steps/s"}), flush=True)
+
+
 # ---------------------------------------------------------------- the CUDA path
 
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.only:
+        run_only(args)
         return
     import torch
     import torch.distributed as dist

@@ -66,16 +66,15 @@ typedef enum {
  *       approximation (Sec. 2.1; the paper's experiments use N = 10): the
  *       spectral density with exp(l^2 w^2/2) replaced by its Taylor
  *       polynomial of order N, whose stable spectral factor is an SDE of
- *       order N (Hartikainen & Sarkka 2010).  The library works in real modal
- *       coordinates (N/2 damped rotations).  The approximation error against
- *       the exact covariance falls with N (below 2e-4 s at N = 10); the
- *       state space is ill-conditioned at higher orders (at N = 10 its modal
- *       variances reach ~1e6 s against f's s), which limits the precision:
- *       at N = 10, against a companion-form Kalman filter, measured errors
- *       are ~1e-10 (log-likelihood), ~3e-8 (gradient) and ~7e-7 (posterior
- *       mean and variance) relative; orders <= 6 keep the 1e-8 level.  The
- *       default chunk length for orders >= 8 is at least 64 (shorter chunks
- *       lose more).  At most one EQ component per model. */
+ *       order N (Hartikainen & Sarkka 2010).  The library realizes it as a
+ *       cascade of N/2 second-order sections whose states are uncorrelated
+ *       at stationarity (a block-diagonal stationary covariance, a
+ *       transition with damped-rotation diagonal blocks and coupling blocks
+ *       below them), which keeps f's quantities free of cancellation; the
+ *       modal (diagonalised) form of the same SDE has a stationary
+ *       covariance of condition ~1e11 at N = 10.  The approximation error
+ *       against the exact covariance falls with N (below 2e-4 s at N = 10).
+ *       At most one EQ component per model. */
 typedef enum {
     SPINGP_MATERN12 = 1,
     SPINGP_MATERN32 = 2,

@@ -128,7 +128,7 @@ __global__ void k_gsetup(GModel gm, const double* __restrict__ theta, double* __
     if (gm.bkind[k] == GB_MATERN32) {
         w = th[1]; dwv = 1.0; dwl = 0.0;
     } else if (gm.bkind[k] == GB_EQ) {
-        w = 0.0; dwv = 0.0; dwl = 0.0;   // dense modal Pinf: g_pinf_smem
+        w = 0.0; dwv = 0.0; dwl = 0.0;   // 2 x 2 blocks of the EQ sections' Pinf: g_pinf_smem
     } else {
         const int j = gm.bj[k];
         const double var = th[0], lp = th[1];
