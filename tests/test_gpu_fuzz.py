@@ -117,8 +117,11 @@ def _group_case(k):
                       float(np.exp(rng.uniform(-0.5, 1.0))), float(np.exp(rng.uniform(0.0, 2.0)))]
             b += 2 * (J + 1)
         elif kind == 3 and b + 4 <= 16 and not any(isinstance(c, tuple) and c[0] == "eq" for c in comps):
-            comps.append(("eq", 4)); theta += [float(np.exp(rng.uniform(-1, 1))), float(np.exp(rng.uniform(-1, 1)))]
-            b += 4
+            N = int(rng.choice([4, 6, 8]))
+            if b + N > 16:
+                N = 4
+            comps.append(("eq", N)); theta += [float(np.exp(rng.uniform(-1, 1))), float(np.exp(rng.uniform(-1, 1)))]
+            b += N
     if not comps:
         comps, theta = ["matern32"], [1.0, 1.0]
     theta.append(float(np.exp(rng.uniform(np.log(0.01), np.log(0.3)))))
@@ -128,19 +131,30 @@ def _group_case(k):
     d[rng.random(n) < 0.02] = 0.0
     t = np.cumsum(d)
     y = synth.two_sinusoids(t, 0.8, 1.0, 0.1, rng)
+    if k % 3 == 1:                       # every third case with missing observations
+        y[rng.random(n) < 0.1] = np.nan
     L = int(rng.choice([0, 8, 33, 200]))
     return comps, theta, t, y, L
 
 
 @pytest.mark.parametrize("k", range(24))
 def test_fuzz_group_against_oracle(k):
+    """Random structured models (with missing observations in every third
+    case) through the gradient, the posterior with its lag-one covariances,
+    and the series split in ranges."""
     spec, theta, t, y, L = _group_case(k)
+    miss = bool(np.isnan(y).any())
     m = spingp.Model(spec, chunk_len=L)
     assert m.num_params == len(theta)
     T, Y, TH = _t(t), _t(y), _t(theta)
-    ll, g = m.grad(T, Y, TH)
-    mean, var, ll_p = m.posterior(T, Y, TH)
+    ll, g = m.grad(T, Y, TH, missing=miss)
+    mean, var, lag, ll_p = m.posterior_lag1(T, Y, TH, missing=miss)
     llo, go, mo, vo, g1 = seq.grad(spec, theta, t, y, posterior=True, l1=True)
+    if len(t) > 1:
+        sm = seq.smoother(spec, theta, t, y, blocks=True)
+        h = seq.continuous(spec, theta)[2]
+        co = np.einsum("i,nij,j->n", h, sm["Pc"], h)
+        assert np.all(np.abs(lag.cpu().numpy() - co) <= 1e-8 * np.sqrt(vo[1:] * vo[:-1]))
     assert abs(ll.item() - llo) <= 1e-9 * abs(llo), (spec, ll.item(), llo)
     assert abs(ll_p.item() - llo) <= 1e-9 * abs(llo)
     gscale = np.maximum(np.maximum(np.abs(go), g1), 1e-12)
@@ -154,13 +168,13 @@ def test_fuzz_group_against_oracle(k):
     for r, (a, b) in enumerate(ranges):
         ws = torch.empty(spingp.spingp_workspace_bytes(m.h, b - a, spingp.WS_GRAD), dtype=torch.uint8, device=DEV)
         tp = None if r == 0 else float(t[a - 1])
-        elems.append(m.segment_reduce(T[a:b], Y[a:b], TH, t_prev=tp, ws=ws))
+        elems.append(m.segment_reduce(T[a:b], Y[a:b], TH, t_prev=tp, ws=ws, missing=miss))
         wss.append(ws)
     E = torch.stack(elems)
     ls, gs = 0.0, 0.0
     for r, (a, b) in enumerate(ranges):
         tp = None if r == 0 else float(t[a - 1])
-        lr, gr = m.segment_grad(T[a:b], Y[a:b], TH, E, r, t_prev=tp, ws=wss[r])
+        lr, gr = m.segment_grad(T[a:b], Y[a:b], TH, E, r, t_prev=tp, ws=wss[r], missing=miss)
         ls += lr.item()
         gs = gs + gr.cpu().numpy()
     assert abs(ls - llo) <= 1e-9 * abs(llo)
