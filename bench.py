@@ -263,8 +263,7 @@ def extra_workloads(args, dev, flush, world, rank=0, fp64_tflops=None):
         n = len(s.t)
         T, Y, TH = (torch.tensor(a, device=dev) for a in (s.t, s.y, s.theta))
         m = spingp.Model(s.spec)
-        if name == "matern32_n64m":
-            autotune.tune(m, T, Y, TH, spingp.WS_GRAD)
+        autotune.tune(m, T, Y, TH, spingp.WS_GRAD)
         P = m.num_params
         ll = torch.empty(1, dtype=torch.float64, device=dev)
         g = torch.empty(P, dtype=torch.float64, device=dev)
@@ -332,6 +331,7 @@ def extra_workloads(args, dev, flush, world, rank=0, fp64_tflops=None):
     B = bt.n_series
     ll = torch.empty(B, dtype=torch.float64, device=dev)
     g = torch.empty(3 * B, dtype=torch.float64, device=dev)
+    autotune.tune_batch(bt, TH, spingp.WS_GRAD)
     for _ in range(3):
         bt.grad(TH, out=(ll, g))
     # the same call issued eagerly (the binding's host work and the launches
@@ -350,6 +350,7 @@ def extra_workloads(args, dev, flush, world, rank=0, fp64_tflops=None):
     nl = spingp.spingp_launch_count_batched(m.h, B, n_total, spingp.WS_GRAD)
     entry = {"value": n_all / (ms * 1e-3), "unit": "steps/s", "ms_per_step": ms, "n_series": 4096,
              "n_total": n_all, "b": 3, "captured_graph": True, "scaling": "strong", "y": Y_KIND,
+             "chunk_len": m.chunk_len(n_total), "chunk_len_autotuned": True,
              "gpu_launches_per_step": nl,
              "eager": {"ms_per_step": ems, "value": n_all / (ems * 1e-3), "unit": "steps/s",
                        "graph_saving_ms": ems - ms, "graph_saving_frac": (ems - ms) / ems, "launches": nl}}
