@@ -702,52 +702,58 @@ __global__ void __launch_bounds__(GCTA) k_gfold(GArgs a, double* __restrict__ no
 // g_info_through's: the same products, the same pivoting, the same
 // symmetrisation.
 static constexpr int GSC = GL * GL;   // threads per node
+// the matrices in shared memory keep rows of GL + 1 doubles: a column read
+// (X[k][c] over the threads of a row) and a row read of a transposed operand
+// (Y[c][k] over c) then fall on distinct banks
+static constexpr int GSX = GL + 1;
+static constexpr int GSP = GL * GSX;
 
 struct GScanSmem {
-    double A[GSC], C[GSC], J[GSC];    // the element (or, down-sweep, the sibling)
-    double A2[GSC], C2[GSC], J2[GSC]; // the second element (up-sweep)
-    double S[GSC];                    // a state's P or an information's J (down-sweep)
-    double N[GSC], M[GSC], T[GSC], U[GSC];
+    double A[GSP], C[GSP], J[GSP];    // the element (or, down-sweep, the sibling)
+    double A2[GSP], C2[GSP], J2[GSP]; // the second element (up-sweep)
+    double S[GSP];                    // a state's P or an information's J (down-sweep)
+    double N[GSP], M[GSP], T[GSP], U[GSP];
     double bv[GL], eta[GL], bv2[GL], eta2[GL], v[GL], w[GL], z[GL];
     int piv;
+    int perm[GL];                     // the pivot row of each column (the inverse's row order)
     double inv;                       // 1 / pivot
 };
 
 __device__ __forceinline__ void gc_load_elem(const double* __restrict__ base, int64_t ne, int64_t e, double* A,
                                              double* C, double* J, double* bv, double* eta) {
-    const int t = threadIdx.x, r = t >> 4, c = t & 15;
+    const int t = threadIdx.x, r = t >> 4, c = t & 15, q = r * GSX + c;
     const double* p = base + e * GL + c;
     const int64_t st = ne * GL;
-    A[t] = p[r * st];
-    C[t] = p[(GL + r) * st];
-    J[t] = p[(2 * GL + r) * st];
+    A[q] = p[r * st];
+    C[q] = p[(GL + r) * st];
+    J[q] = p[(2 * GL + r) * st];
     if (r == 0) { bv[c] = p[3 * GL * st]; eta[c] = p[(3 * GL + 1) * st]; }
 }
 __device__ __forceinline__ void gc_store_elem(double* __restrict__ base, int64_t ne, int64_t e, const double* A,
                                               const double* C, const double* J, const double* bv,
                                               const double* eta) {
-    const int t = threadIdx.x, r = t >> 4, c = t & 15;
+    const int t = threadIdx.x, r = t >> 4, c = t & 15, q = r * GSX + c;
     double* p = base + e * GL + c;
     const int64_t st = ne * GL;
-    p[r * st] = A[t];
-    p[(GL + r) * st] = C[t];
-    p[(2 * GL + r) * st] = J[t];
+    p[r * st] = A[q];
+    p[(GL + r) * st] = C[q];
+    p[(2 * GL + r) * st] = J[q];
     if (r == 0) { p[3 * GL * st] = bv[c]; p[(3 * GL + 1) * st] = eta[c]; }
 }
 __device__ __forceinline__ void gc_load_vs(const double* __restrict__ base, int64_t ne, int64_t e, double* S,
                                            double* v) {
-    const int t = threadIdx.x, r = t >> 4, c = t & 15;
+    const int t = threadIdx.x, r = t >> 4, c = t & 15, q = r * GSX + c;
     const double* p = base + e * GL + c;
     const int64_t st = ne * GL;
-    S[t] = p[r * st];
+    S[q] = p[r * st];
     if (r == 0) v[c] = p[GL * st];
 }
 __device__ __forceinline__ void gc_store_vs(double* __restrict__ base, int64_t ne, int64_t e, const double* S,
                                             const double* v) {
-    const int t = threadIdx.x, r = t >> 4, c = t & 15;
+    const int t = threadIdx.x, r = t >> 4, c = t & 15, q = r * GSX + c;
     double* p = base + e * GL + c;
     const int64_t st = ne * GL;
-    p[r * st] = S[t];
+    p[r * st] = S[q];
     if (r == 0) p[GL * st] = v[c];
 }
 
@@ -757,7 +763,7 @@ __device__ __forceinline__ double gc_mm(const double* X, const double* Y) {
     const int r = threadIdx.x >> 4, c = threadIdx.x & 15;
     double s = 0.0;
 #pragma unroll
-    for (int k = 0; k < GL; ++k) s = fma(TX ? X[k * GL + r] : X[r * GL + k], TY ? Y[c * GL + k] : Y[k * GL + c], s);
+    for (int k = 0; k < GL; ++k) s = fma(TX ? X[k * GSX + r] : X[r * GSX + k], TY ? Y[c * GSX + k] : Y[k * GSX + c], s);
     return s;
 }
 // out[i] = sum_k X[i][k] x[k] (TX: X^T), threads i < 16
@@ -766,23 +772,29 @@ __device__ __forceinline__ double gc_mv(const double* X, const double* x) {
     const int i = threadIdx.x;
     double s = 0.0;
 #pragma unroll
-    for (int k = 0; k < GL; ++k) s = fma(TX ? X[k * GL + i] : X[i * GL + k], x[k], s);
+    for (int k = 0; k < GL; ++k) s = fma(TX ? X[k * GSX + i] : X[i * GSX + k], x[k], s);
     return s;
 }
 
-// M = (I + X Y)^-1 by Gauss-Jordan with partial pivoting (the rule of
-// g_inv_ixy: the first largest |N[r][k]|, r >= k); X, Y, M in shared memory
+// M = (I + X Y)^-1 by Gauss-Jordan with partial pivoting (at step k the
+// largest |N[r][k]| among the rows not yet used as pivots, the first row on
+// ties); X, Y, M in shared memory.  The pivot rows stay in place: step k
+// rescales the pivot row p and subtracts it from every other row, reading
+// one buffer and writing the other (T and U, idle here, are the second pair),
+// so a step needs two block barriers; at the end row k of the inverse is
+// row perm[k] of the accumulated right-hand side.
 __device__ void gc_inv_ixy(GScanSmem& s, const double* X, const double* Y) {
-    const int t = threadIdx.x, r = t >> 4, c = t & 15;
-    s.N[t] = gc_mm<false, false>(X, Y) + ((r == c) ? 1.0 : 0.0);
-    s.M[t] = (r == c) ? 1.0 : 0.0;
+    const int t = threadIdx.x, r = t >> 4, c = t & 15, q = r * GSX + c;
+    double *Na = s.N, *Ma = s.M, *Nb = s.T, *Mb = s.U;
+    Na[q] = gc_mm<false, false>(X, Y) + ((r == c) ? 1.0 : 0.0);
+    Ma[q] = (r == c) ? 1.0 : 0.0;
+    bool used = false;   // threads t < 16: row t has been a pivot
     __syncthreads();
 #pragma unroll 1
     for (int k = 0; k < GL; ++k) {
-        // the pivot row over 16 lanes (largest |N[i][k]|, i >= k, the first on
-        // ties), and its reciprocal, once for the block
+        // the pivot row over 16 lanes, and its reciprocal, once for the block
         if (t < GL) {
-            double best = (t >= k) ? fabs(s.N[t * GL + k]) : -1.0;
+            double best = used ? -1.0 : fabs(Na[t * GSX + k]);
             int p = t;
 #pragma unroll
             for (int off = 8; off > 0; off >>= 1) {
@@ -792,39 +804,39 @@ __device__ void gc_inv_ixy(GScanSmem& s, const double* X, const double* Y) {
             }
             if (t == 0) {
                 s.piv = p;
-                s.inv = 1.0 / s.N[p * GL + k];
+                s.perm[k] = p;
+                s.inv = 1.0 / Na[p * GSX + k];
             }
         }
         __syncthreads();
         const int p = s.piv;
-        if (p != k && t < 2 * GL) {
-            double* X2 = (t < GL) ? s.N : s.M;
-            const int cc = t & 15;
-            const double u = X2[k * GL + cc];
-            X2[k * GL + cc] = X2[p * GL + cc];
-            X2[p * GL + cc] = u;
-        }
-        __syncthreads();
         const double inv = s.inv;
-        const double f = s.N[r * GL + k];
-        const double nk = s.N[k * GL + c] * inv, mk = s.M[k * GL + c] * inv;
-        __syncthreads();
-        if (r == k) {
-            s.N[t] = nk;
-            s.M[t] = mk;
+        if (t == p) used = true;
+        const double pn = Na[p * GSX + c] * inv, pm = Ma[p * GSX + c] * inv;
+        if (r == p) {
+            Nb[q] = pn;
+            Mb[q] = pm;
         } else {
-            s.N[t] = fma(-f, nk, s.N[t]);
-            s.M[t] = fma(-f, mk, s.M[t]);
+            const double f = Na[r * GSX + k];
+            Nb[q] = fma(-f, pn, Na[q]);
+            Mb[q] = fma(-f, pm, Ma[q]);
         }
         __syncthreads();
+        double* u = Na; Na = Nb; Nb = u;
+        u = Ma; Ma = Mb; Mb = u;
     }
+    // GL steps (even): Ma is s.M again
+    const double out = Ma[s.perm[r] * GSX + c];
+    __syncthreads();
+    s.M[q] = out;
+    __syncthreads();
 }
 
 // level l from level l-1: node j = (2j) then (2j+1), or a copy of 2j at the end
 __global__ void __launch_bounds__(GSC) k_gscan_up(const double* __restrict__ lo, int64_t nlo,
                                                   double* __restrict__ hi, int64_t nhi) {
     __shared__ GScanSmem s;
-    const int t = threadIdx.x, r = t >> 4, c = t & 15;
+    const int t = threadIdx.x, r = t >> 4, c = t & 15, q = r * GSX + c;
     const int64_t j = blockIdx.x;
     if (j >= nhi) return;
     gc_load_elem(lo, nlo, 2 * j, s.A, s.C, s.J, s.bv, s.eta);
@@ -838,7 +850,7 @@ __global__ void __launch_bounds__(GSC) k_gscan_up(const double* __restrict__ lo,
     // (i = first, j = second):  M = (I + C_i J_j)^-1
     gc_inv_ixy(s, s.C, s.J2);
     // A = A_j M A_i
-    s.T[t] = gc_mm<false, false>(s.M, s.A);
+    s.T[q] = gc_mm<false, false>(s.M, s.A);
     // bv: w = bv_i + C_i eta_j;  eta: w2 = eta_j - J_j bv_i
     if (t < GL) {
         s.v[t] = s.bv[t] + gc_mv<false>(s.C, s.eta2);
@@ -854,25 +866,25 @@ __global__ void __launch_bounds__(GSC) k_gscan_up(const double* __restrict__ lo,
         s.v[t] = gc_mv<true>(s.M, s.w);                  // M^T w2
     }
     // C = sym(A_j M C_i A_j^T) + C_j
-    s.T[t] = gc_mm<false, false>(s.M, s.C);
+    s.T[q] = gc_mm<false, false>(s.M, s.C);
     __syncthreads();
     if (t < GL) etanew = gc_mv<true>(s.A, s.v) + s.eta[t];   // A_i^T M^T w2 + eta_i
-    s.U[t] = gc_mm<false, false>(s.A2, s.T);
+    s.U[q] = gc_mm<false, false>(s.A2, s.T);
     __syncthreads();
-    s.N[t] = gc_mm<false, true>(s.U, s.A2);
+    s.N[q] = gc_mm<false, true>(s.U, s.A2);
     // J = sym(A_i^T M^T J_j A_i) + J_i
-    s.T[t] = gc_mm<true, false>(s.M, s.J2);
+    s.T[q] = gc_mm<true, false>(s.M, s.J2);
     __syncthreads();
-    const double Cnew = 0.5 * ((s.N[t] + s.C2[t]) + (s.N[c * GL + r] + s.C2[c * GL + r]));
-    s.U[t] = gc_mm<false, false>(s.T, s.A);
+    const double Cnew = 0.5 * ((s.N[q] + s.C2[q]) + (s.N[c * GSX + r] + s.C2[c * GSX + r]));
+    s.U[q] = gc_mm<false, false>(s.T, s.A);
     __syncthreads();
-    s.T[t] = gc_mm<true, false>(s.A, s.U);
+    s.T[q] = gc_mm<true, false>(s.A, s.U);
     __syncthreads();
-    const double Jnew = 0.5 * ((s.T[t] + s.J[t]) + (s.T[c * GL + r] + s.J[c * GL + r]));
+    const double Jnew = 0.5 * ((s.T[q] + s.J[q]) + (s.T[c * GSX + r] + s.J[c * GSX + r]));
     __syncthreads();
-    s.A[t] = Anew;
-    s.C[t] = Cnew;
-    s.J[t] = Jnew;
+    s.A[q] = Anew;
+    s.C[q] = Cnew;
+    s.J[q] = Jnew;
     if (t < GL) { s.bv[t] = bvnew; s.eta[t] = etanew; }
     __syncthreads();
     gc_store_elem(hi, nhi, j, s.A, s.C, s.J, s.bv, s.eta);
@@ -887,7 +899,7 @@ __global__ void __launch_bounds__(GSC) k_gscan_down(const double* __restrict__ l
                                                     int64_t nhi, double* __restrict__ cpre,
                                                     double* __restrict__ csuf) {
     __shared__ GScanSmem s;
-    const int t = threadIdx.x, r = t >> 4, c = t & 15;
+    const int t = threadIdx.x, r = t >> 4, c = t & 15, q = r * GSX + c;
     const int64_t j = blockIdx.x;
     if (j >= nlo) return;
     const int64_t parent = j >> 1;
@@ -896,7 +908,7 @@ __global__ void __launch_bounds__(GSC) k_gscan_down(const double* __restrict__ l
         gc_load_vs(ppre, nhi, parent, s.S, s.v);
         gc_load_vs(psuf, nhi, parent, s.C2, s.w);
     } else {
-        s.S[t] = 0.0; s.C2[t] = 0.0;
+        s.S[q] = 0.0; s.C2[q] = 0.0;
         if (t < GL) { s.v[t] = 0.0; s.w[t] = 0.0; }
     }
     const bool odd = (j & 1) != 0;
@@ -913,18 +925,18 @@ __global__ void __launch_bounds__(GSC) k_gscan_down(const double* __restrict__ l
         // P' = sym(A_e M P A_e^T) + C_e
         gc_inv_ixy(s, s.S, s.J);
         if (t < GL) s.z[t] = s.v[t] + gc_mv<false>(s.S, s.eta);
-        s.T[t] = gc_mm<false, false>(s.M, s.S);
+        s.T[q] = gc_mm<false, false>(s.M, s.S);
         __syncthreads();
         double mnew = 0.0;
         if (t < GL) s.bv2[t] = gc_mv<false>(s.M, s.z);
-        s.U[t] = gc_mm<false, false>(s.A, s.T);
+        s.U[q] = gc_mm<false, false>(s.A, s.T);
         __syncthreads();
         if (t < GL) mnew = gc_mv<false>(s.A, s.bv2) + s.bv[t];
-        s.N[t] = gc_mm<false, true>(s.U, s.A);
+        s.N[q] = gc_mm<false, true>(s.U, s.A);
         __syncthreads();
-        const double Pnew = 0.5 * ((s.N[t] + s.C[t]) + (s.N[c * GL + r] + s.C[c * GL + r]));
+        const double Pnew = 0.5 * ((s.N[q] + s.C[q]) + (s.N[c * GSX + r] + s.C[c * GSX + r]));
         __syncthreads();
-        s.T[t] = Pnew;
+        s.T[q] = Pnew;
         if (t < GL) s.z[t] = mnew;
         __syncthreads();
         gc_store_vs(cpre, nlo, j, s.T, s.z);
@@ -934,18 +946,18 @@ __global__ void __launch_bounds__(GSC) k_gscan_down(const double* __restrict__ l
         // eta' = A_e^T M^T (eta - J bv_e) + eta_e, J' = sym(A_e^T M^T J A_e) + J_e
         gc_inv_ixy(s, s.C, s.C2);
         if (t < GL) s.z[t] = s.w[t] - gc_mv<false>(s.C2, s.bv);
-        s.T[t] = gc_mm<true, false>(s.M, s.C2);
+        s.T[q] = gc_mm<true, false>(s.M, s.C2);
         __syncthreads();
         double enew = 0.0;
         if (t < GL) s.bv2[t] = gc_mv<true>(s.M, s.z);
-        s.U[t] = gc_mm<false, false>(s.T, s.A);
+        s.U[q] = gc_mm<false, false>(s.T, s.A);
         __syncthreads();
         if (t < GL) enew = gc_mv<true>(s.A, s.bv2) + s.eta[t];
-        s.N[t] = gc_mm<true, false>(s.A, s.U);
+        s.N[q] = gc_mm<true, false>(s.A, s.U);
         __syncthreads();
-        const double Jnew = 0.5 * ((s.N[t] + s.J[t]) + (s.N[c * GL + r] + s.J[c * GL + r]));
+        const double Jnew = 0.5 * ((s.N[q] + s.J[q]) + (s.N[c * GSX + r] + s.J[c * GSX + r]));
         __syncthreads();
-        s.T[t] = Jnew;
+        s.T[q] = Jnew;
         if (t < GL) s.z[t] = enew;
         __syncthreads();
         gc_store_vs(cpre, nlo, j, s.S, s.v);
