@@ -430,9 +430,11 @@ def batched_oracle_rate(s, n_series=1024):
 # steps, or nodes for the BTD solver; the batched SCG's gradient evaluations
 # use the chain kernels' counts above.
 NEXT_FLOPS_PER_UNIT = {"prediction_n4m": 344.2, "literal_n1m": 2157.0, "btd_solve_n1m": 821.6,
-                       "eq_b12_n1m": 21120.6, "scg_batch_4096": 171.5 + 231.2}
+                       "eq_b12_n1m": 21120.6, "scg_batch_4096": 171.5 + 231.2,
+                       "posterior_lag1_n4m": 171.5 + 224.1}
 NEXT_FP64_INST_PER_UNIT = {"prediction_n4m": 226.0, "literal_n1m": 1485.5, "btd_solve_n1m": 520.0,
-                           "eq_b12_n1m": 13421.2, "scg_batch_4096": 107.1 + 141.6}
+                           "eq_b12_n1m": 13421.2, "scg_batch_4096": 107.1 + 141.6,
+                           "posterior_lag1_n4m": 107.1 + 143.5}
 
 
 def _next_roofline(key, units_per_s, fp64_tflops):
@@ -464,6 +466,8 @@ def next_rows(args, dev, flush, fp64_tflops):
     sample on one host thread:
       prediction_n4m  posterior of the N = 2^22, b = 3 series with 10 % of its
                       observations missing (test points, Eqs. mean4-mean6)
+      posterior_lag1_n4m  the posterior of the same series with the first
+                      off-diagonal of the selected inverse (Sec. 3.1)
       literal_n1m     the method as written: Theorem-1 assembly, block cyclic
                       reduction with selected inverse, Eq. dd1 gradient; b = 3,
                       N = 2^20 well-separated times (oracle: its Kalman form)
@@ -499,6 +503,24 @@ def next_rows(args, dev, flush, fp64_tflops):
                                  spingp.spingp_launch_count(m.h, n, spingp.WS_POSTERIOR),
                              "oracle": {"value": smp / osec, "unit": "steps/s", "cores": 1,
                                         "sample": "first %d steps, sequential C smoother" % smp}}
+    del T, Y, TH, m
+    torch.cuda.empty_cache()
+    # ---- the posterior with the first off-diagonal of the selected inverse
+    s = synth.single(WORKLOAD)
+    n = len(s.t)
+    T, Y, TH = (torch.tensor(a, device=dev) for a in (s.t, s.y, s.theta))
+    m = spingp.Model(s.spec)
+    m.posterior_lag1(T, Y, TH)
+    ms = _time_calls(lambda: m.posterior_lag1(T, Y, TH, sync=False), K, flush, torch)
+    smp = 1 << 18
+    osec = _oracle_seconds(lambda: seq.smoother(s.spec, s.theta, s.t[:smp], s.y[:smp], blocks=True))
+    res["posterior_lag1_n4m"] = {"value": n / (ms * 1e-3), "unit": "steps/s", "ms_per_step": ms, "n": n,
+                                 "chunk_len": m.chunk_len(n),
+                                 "roofline": _next_roofline("posterior_lag1_n4m", n / (ms * 1e-3), fp64_tflops),
+                                 "gpu_launches_per_step": spingp.spingp_launch_count(m.h, n, spingp.WS_POSTERIOR),
+                                 "oracle": {"value": smp / osec, "unit": "steps/s", "cores": 1,
+                                            "sample": "first %d steps, sequential C RTS smoother with its "
+                                                      "lag-one blocks" % smp}}
     del T, Y, TH, m
     torch.cuda.empty_cache()
     # ---- the method as written
