@@ -15,7 +15,7 @@ torch = pytest.importorskip("torch")
 
 from golden.make_golden import load_config1  # noqa: E402
 from oracle import seq  # noqa: E402
-from paper_1610_08035_gb300 import spingp, synth  # noqa: E402
+from paper_1610_08035_gb300 import autotune, spingp, synth  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
@@ -107,9 +107,12 @@ def test_parity_three_reduction_levels():
 
 def test_parity_headline_full_size():
     """Matern-5/2, N = 2^22, dt ~ Exp(0.01), l=0.5, s_f=2, s_n=0.05, in the
-    benchmark's launch configuration (default chunk length): loglik + gradient."""
+    benchmark's launch configuration (the autotuned chunk length): loglik +
+    gradient."""
     s = synth.single("matern52_n4m")
-    check_against_oracle(s.spec, s.theta, s.t, s.y, 0, posterior=False)
+    m = spingp.Model(s.spec)
+    L = autotune.tune(m, _t(s.t), _t(s.y), _t(s.theta), spingp.WS_GRAD) or m.chunk_len(len(s.t))
+    check_against_oracle(s.spec, s.theta, s.t, s.y, L, posterior=False)
 
 
 @pytest.mark.parametrize("spec,theta", MATERN)
@@ -216,6 +219,7 @@ def test_large_series_full_size():
     s = synth.single("matern32_n64m")
     m = spingp.Model(s.spec)
     T, Y, TH = _t(s.t), _t(s.y), _t(s.theta)
+    autotune.tune(m, T, Y, TH, spingp.WS_GRAD)           # the benchmark's launch configuration
     ll, g = m.grad(T, Y, TH)
     ll, g = float(ll.cpu()[0]), g.cpu().numpy()
     llo, go, g1 = seq.grad(s.spec, s.theta, s.t, s.y, l1=True)
@@ -246,6 +250,7 @@ def test_large_series_step_in_a_captured_graph():
     n = len(s.t)
     m = spingp.Model(s.spec)
     T, Y, TH = _t(s.t), _t(s.y), _t(s.theta)
+    autotune.tune(m, T, Y, TH, spingp.WS_GRAD)
     ll_e, g_e = m.grad(T, Y, TH)
     mean_e, var_e, _ = m.posterior(T, Y, TH, with_loglik=False)
     ll = torch.empty(1, dtype=torch.float64, device=DEV)
