@@ -33,8 +33,8 @@ METRIC = "loglik+grad time steps/s (FP64, N=2^22,b=3) vs plain GPU form; % HBM r
 WORKLOAD = "matern52_n4m"
 
 # FP64 work per time step of each stage of the gradient call for b = 3, counted
-# with ncu at the benchmark's chunk length 108 (N = 2^21;
-# profiles/chain_kernels_grad_matern52_n2m.md): flops = 2 x DFMA + DADD + DMUL
+# with ncu at the benchmark's chunk length 108 (N = 2^21, one kernel and one
+# launch per capture, `--only matern52_n4m --n 2097152 --chunk 108`): flops = 2 x DFMA + DADD + DMUL
 # thread instructions; FP64 instructions = everything the FP64 pipe executed
 # (the pipe issues one warp instruction per 16 cycles per SM whatever its kind).
 FLOPS_PER_STEP = {"elimination": 171.5, "chunk_pass": 231.2}
@@ -225,9 +225,11 @@ def _time_calls(fn, K, flush, torch):
 
 # FP64 work per step executed by the per-step kernels of each secondary
 # workload (discretisation, elimination, chunk pass; ncu: flops = 2 DFMA +
-# DADD + DMUL thread instructions, and every FP64-pipe instruction), from the
-# captures in profiles/workload_kernels_grad.md.  The reduction levels (work
-# per chunk, not per step) are left out of the flops and kept in the time.
+# DADD + DMUL thread instructions, and every FP64-pipe instruction), captured
+# one kernel and one launch at a time with `--only <workload>` at 2^18 steps
+# (b = 16, b = 12; chunk length 432), 2^22 (b = 2; 108) and 512 series of the
+# batch.  The reduction levels (work per chunk, not per step) are left out of
+# the flops and kept in the time.
 WORKLOAD_EXEC_PER_STEP = {"sum_qp_n1m": (12310.5, 8059.1), "m32_eq10_n1m": (21120.6, 13421.2),
                           "matern32_n64m": (215.1, 144.1), "batched_4096": (397.6, 246.9)}
 
@@ -423,9 +425,9 @@ def batched_oracle_rate(s, n_series=1024):
                 k, len(offs) - 1, steps, cores)}
 
 
-# Whole-call FP64 work per unit of the rows built beyond the hot path (ncu,
-# profiles/next_rows_kernels.md; the b = 12 EQ row from its per-step kernels,
-# profiles/workload_kernels_grad.md): flops = 2 DFMA + DADD + DMUL thread
+# Whole-call FP64 work per unit of the rows built beyond the hot path (ncu
+# captures of each row's kernels; the b = 12 EQ and lag-one rows from their
+# per-step kernels only): flops = 2 DFMA + DADD + DMUL thread
 # instructions; instructions = everything the FP64 pipe executed.  Units:
 # steps, or nodes for the BTD solver; the batched SCG's gradient evaluations
 # use the chain kernels' counts above.
@@ -596,8 +598,7 @@ def next_rows(args, dev, flush, fp64_tflops):
 def run_only(args):
     """The gradient call of one workload, --warmup untimed and --steps timed
     calls (L2 flushed before each), at the workload's size or --n steps
-    (--n series for the batch): the command the ncu summaries in profiles/
-    capture."""
+    (--n series for the batch): a command for ncu to capture."""
     import torch
 
     from paper_1610_08035_gb300 import spingp, synth

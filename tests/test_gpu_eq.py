@@ -81,6 +81,21 @@ def test_eq_against_dense_gp_and_exact_kernel():
     assert np.max(np.abs(g.cpu().numpy() - gd)) <= 1e-8 * np.max(np.abs(gd))
 
 
+def test_eq16_lag1_against_dense_posterior_covariance():
+    """The posterior's lag-one covariances at order 16 against the dense GP's
+    posterior covariance K - K C^-1 K (its first off-diagonal)."""
+    from scipy.linalg import cho_factor, cho_solve
+    spec, theta = [("eq", 16)], [0.8, 1.1, 0.2]
+    t, y = _data(700, 31)
+    m = spingp.Model(spec, chunk_len=8)
+    mean, var, lag, _ = m.posterior_lag1(_t(t), _t(y), _t(theta))
+    K, _ = dense.gram(spec, theta, t)
+    C = K + theta[-1] * np.eye(len(t))
+    Sig = K - K @ cho_solve(cho_factor(C, lower=True), K)
+    co, vo = np.diag(Sig, -1), np.diag(Sig)
+    assert np.all(np.abs(lag.cpu().numpy() - co) <= 1e-8 * np.sqrt(vo[1:] * vo[:-1]))
+
+
 @pytest.mark.parametrize("L", [0, 8])
 def test_eq16_against_dense_gp(L):
     """Order 16 (b = 16, the largest state) against the dense GP.  The

@@ -85,6 +85,19 @@ def test_lag1_group_missing(spec, theta):
     _check(spec, theta, t, y, 32, missing=True)
 
 
+@pytest.mark.parametrize("spec,theta", [("matern52", [0.5, 2.0, 0.05]), GROUP[1]])
+def test_lag1_missing_edges(spec, theta):
+    """A missing first and last observation, a run of missing ones across
+    chunk boundaries, and an all-missing series (the prior's lag-one
+    covariance k(t_{i+1} - t_i))."""
+    t, y = _series(700, 0.02, 41)
+    y[0] = y[-1] = np.nan
+    y[100:260] = np.nan
+    _check(spec, theta, t, y, 16, missing=True)
+    y[:] = np.nan
+    _check(spec, theta, t, y, 16, missing=True)
+
+
 def test_lag1_single_step_needs_no_buffer():
     m = spingp.Model("matern52")
     T, Y, TH = _t([0.0]), _t([0.3]), _t([0.5, 2.0, 0.05])
