@@ -286,9 +286,11 @@ def extra_workloads(args, dev, flush, world, rank=0, fp64_tflops=None):
                          "pipe_frac": inst * n / (ms * 1e-3) / (fp64_tflops * 1e12 / 2.0),
                          "flops_per_step": fl, "fp64_inst_per_step": inst})
         entry["roofline"] = roof
-        if name == "matern32_n64m":
-            # the long-series workload's step: log-likelihood + gradient +
-            # posterior mean, captured once in a CUDA graph and replayed
+        if name in ("matern32_n64m", "sum_qp_n1m"):
+            # the step these workloads are stated with: log-likelihood +
+            # gradient + posterior (the long series' mean; config 3's
+            # variances through the selected inverse), captured once in a
+            # CUDA graph and replayed
             mean = torch.empty(n, dtype=torch.float64, device=dev)
             var = torch.empty(n, dtype=torch.float64, device=dev)
             m.posterior(T, Y, TH, with_loglik=False, out=(mean, var, None))
