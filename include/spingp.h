@@ -182,6 +182,24 @@ spingp_status spingp_posterior_lag1(const spingp_model* model, const double* t, 
                                     double* cov_lag1_out, void* ws, size_t ws_bytes, unsigned flags,
                                     void* stream);
 
+/* spingp_grad and spingp_posterior_lag1 in one call: a learning step that also
+ * wants the posterior at the current hyperparameters (Sec. 2.4 and Sec. 3.1
+ * share subproblems 1 to 4: the same elimination, reduction and reverse
+ * sweep give the gradient's trace terms and the selected inverse's blocks).
+ * One forward pass and one reverse sweep, so it costs about what spingp_grad
+ * costs, not the sum of both calls.  Writes ll_out[0], grad_out[0 ..
+ * num_params-1], mean_out[0 .. n-1], var_out[0 .. n-1] (all required) and,
+ * when cov_lag1_out is not NULL, cov_lag1_out[0 .. n-2] as
+ * spingp_posterior_lag1 does.  Each output equals the separate call's up to
+ * rounding order.  Workspace: spingp_workspace_bytes(model, n, SPINGP_WS_GRAD)
+ * (the SPINGP_WS_POSTERIOR size is the same).  SPINGP_LOG_GRAD affects
+ * grad_out only, SPINGP_PREDICTIVE var_out only; SPINGP_MISSING_NAN and
+ * SPINGP_SYNC as for the other calls.  EINVAL for a NULL required output. */
+spingp_status spingp_grad_posterior(const spingp_model* model, const double* t, const double* y, int64_t n,
+                                    const double* theta, double* ll_out, double* grad_out, double* mean_out,
+                                    double* var_out, double* cov_lag1_out, void* ws, size_t ws_bytes,
+                                    unsigned flags, void* stream);
+
 /* ---- batches of independent series ----------------------------------------
  * n_series series, each with its own hyperparameters, concatenated: series i
  * owns steps [offsets[i], offsets[i+1]) of t and y, with offsets[0] = 0,

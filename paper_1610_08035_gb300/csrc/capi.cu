@@ -407,6 +407,15 @@ spingp_status spingp_posterior_lag1(const spingp_model* m, const double* t, cons
                stream, n > 1 ? cov_lag1_out : nullptr);
 }
 
+spingp_status spingp_grad_posterior(const spingp_model* m, const double* t, const double* y, int64_t n,
+                                    const double* theta, double* ll_out, double* grad_out, double* mean_out,
+                                    double* var_out, double* cov_lag1_out, void* ws, size_t ws_bytes,
+                                    unsigned flags, void* stream) {
+    if (!ll_out || !grad_out || !mean_out || !var_out) return SPINGP_EINVAL;
+    return run(m, spg::MODE_GRAD_POSTERIOR, t, y, n, theta, ll_out, grad_out, mean_out, var_out, ws, ws_bytes,
+               flags, stream, n > 1 ? cov_lag1_out : nullptr);
+}
+
 int spingp_launch_count(const spingp_model* m, int64_t n, spingp_ws_kind what) {
     if (!m || n < 1) return -1;
     const int mode = what == SPINGP_WS_GRAD ? spg::MODE_GRAD

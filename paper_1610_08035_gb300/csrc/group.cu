@@ -975,8 +975,8 @@ __global__ void __launch_bounds__(GCTA) k_gchunk(GArgs a, const double* __restri
                                                  double* __restrict__ part, double* __restrict__ mean_out,
                                                  double* __restrict__ var_out) {
     constexpr bool BWD = (MODE != MODE_LOGLIK);
-    constexpr bool GRAD = (MODE == MODE_GRAD);
-    constexpr bool POST = (MODE == MODE_POSTERIOR);
+    constexpr bool GRAD = (MODE == MODE_GRAD || MODE == MODE_GRAD_POSTERIOR);
+    constexpr bool POST = (MODE == MODE_POSTERIOR || MODE == MODE_GRAD_POSTERIOR);
     __shared__ GSmem sm[GGRP];
     __shared__ double s_pinf[GL * GL], s_dpe[GL * GL];
     g_pinf_smem(a.gm, a.theta, a.gconst, s_pinf, s_dpe);
@@ -1531,7 +1531,7 @@ int group_run(const GModel& gm, int mode, const double* t, const double* y, int6
     double* part = (double*)(ws + lay.off_part);
     double* store = (double*)(ws + lay.off_store);
     GArgs a{gm, t, y, n, L, lay.nc, theta, gconst, phis, status, missing, 0, 0.0};
-    a.lag1 = (mode == MODE_POSTERIOR) ? lag1_out : nullptr;
+    a.lag1 = (mode == MODE_POSTERIOR || mode == MODE_GRAD_POSTERIOR) ? lag1_out : nullptr;
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
     if (ev) cudaEventRecord(ev[0], st);
     k_gsetup<<<1, 32, 0, st>>>(gm, theta, gconst, status);
@@ -1552,6 +1552,9 @@ int group_run(const GModel& gm, int mode, const double* t, const double* y, int6
         gchunk_launch<MODE_LOGLIK>(NRr, eqt, cgrid, st, a, pre, suf, store, part, nullptr, nullptr);
     } else if (mode == MODE_GRAD) {
         gchunk_launch<MODE_GRAD>(NRr, eqt, cgrid, st, a, pre, suf, store, part, nullptr, nullptr);
+        na = GPART;
+    } else if (mode == MODE_GRAD_POSTERIOR) {
+        gchunk_launch<MODE_GRAD_POSTERIOR>(NRr, eqt, cgrid, st, a, pre, suf, store, part, mean_out, var_out);
         na = GPART;
     } else {
         gchunk_launch<MODE_POSTERIOR>(NRr, eqt, cgrid, st, a, pre, suf, store, part, mean_out, var_out);

@@ -43,8 +43,9 @@ unsigned long long context_id();
 // device status bits (the status word at the start of every workspace)
 enum { ST_EINVAL = 1 << 1, ST_ENOTSORTED = 1 << 2, ST_ENONFINITE = 1 << 3, ST_ENUMERIC = 1 << 4 };
 
-// what a chain run computes
-enum { MODE_LOGLIK = 0, MODE_GRAD = 1, MODE_POSTERIOR = 2 };
+// what a run computes (MODE_GRAD_POSTERIOR: the gradient and the posterior
+// from one forward pass and one reverse sweep)
+enum { MODE_LOGLIK = 0, MODE_GRAD = 1, MODE_POSTERIOR = 2, MODE_GRAD_POSTERIOR = 3 };
 
 size_t matern_ws_bytes(int b, int64_t n, int64_t L, int mode);
 int matern_prepare();

@@ -585,8 +585,8 @@ __global__ void __launch_bounds__(CTA) k_chunk(ChainArgs a, const double* __rest
     constexpr int NF = Stored<B>::N;
     constexpr int NA = Acc<B>::N;
     constexpr bool BWD = (MODE != MODE_LOGLIK);
-    constexpr bool GRAD = (MODE == MODE_GRAD);
-    constexpr bool POST = (MODE == MODE_POSTERIOR);
+    constexpr bool GRAD = (MODE == MODE_GRAD || MODE == MODE_GRAD_POSTERIOR);
+    constexpr bool POST = (MODE == MODE_POSTERIOR || MODE == MODE_GRAD_POSTERIOR);
     (void)NE;
     __shared__ double spre[CTA * NM];
     __shared__ double ssuf[BWD ? CTA * NM : 1];
@@ -1205,7 +1205,7 @@ int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t 
     double* store = (double*)(ws + lay.off_store);
     double* state = (double*)(ws + lay.off_state);
     ChainArgs a{t, y, n, L, lay.nc, lay.nb, theta, status, nullptr, nullptr, 0, 3, missing, 0, 0.0,
-                mode == MODE_POSTERIOR ? lag1_out : nullptr};
+                (mode == MODE_POSTERIOR || mode == MODE_GRAD_POSTERIOR) ? lag1_out : nullptr};
     const unsigned grid = (unsigned)lay.nb;
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return 1;
     if (ev) cudaEventRecord(ev[0], st);
@@ -1277,6 +1277,11 @@ int matern_run_t(int mode, const double* t, const double* y, int64_t n, int64_t 
     case MODE_GRAD:
         k_chunk<B, MODE_GRAD, false><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part, nullptr,
                                                           nullptr);
+        na = Acc<B>::N;
+        break;
+    case MODE_GRAD_POSTERIOR:
+        k_chunk<B, MODE_GRAD_POSTERIOR, false><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part,
+                                                                    mean_out, var_out);
         na = Acc<B>::N;
         break;
     default:

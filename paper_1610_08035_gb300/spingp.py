@@ -25,7 +25,8 @@ KINDS = {"matern12": 1, "matern32": 2, "matern52": 3, "periodic": 4, "quasiperio
 # names exported by the library, in the order of include/spingp.h
 EXPORTS = ("spingp_model_create", "spingp_model_destroy", "spingp_num_params", "spingp_state_dim",
            "spingp_set_chunk_len", "spingp_get_chunk_len", "spingp_workspace_bytes", "spingp_loglik",
-           "spingp_grad", "spingp_posterior", "spingp_posterior_lag1", "spingp_workspace_bytes_batched", "spingp_loglik_batched",
+           "spingp_grad", "spingp_posterior", "spingp_posterior_lag1", "spingp_grad_posterior",
+           "spingp_workspace_bytes_batched", "spingp_loglik_batched",
            "spingp_grad_batched", "spingp_posterior_batched", "spingp_launch_count",
            "spingp_launch_count_batched", "spingp_profile_enable",
            "spingp_profile_read", "spingp_probe_fp64_bytes", "spingp_probe_fp64", "spingp_probe_fp64_tensor",
@@ -78,6 +79,7 @@ def load():
     lib.spingp_grad.argtypes = [vp, dp, dp, i64, dp, dp, dp, vp, sz, u32, vp]
     lib.spingp_posterior.argtypes = [vp, dp, dp, i64, dp, dp, dp, dp, vp, sz, u32, vp]
     lib.spingp_posterior_lag1.argtypes = [vp, dp, dp, i64, dp, dp, dp, dp, dp, vp, sz, u32, vp]
+    lib.spingp_grad_posterior.argtypes = [vp, dp, dp, i64, dp, dp, dp, dp, dp, dp, vp, sz, u32, vp]
     lib.spingp_workspace_bytes_batched.argtypes = [vp, i64, i64, ctypes.c_int]
     lib.spingp_workspace_bytes_batched.restype = sz
     lib.spingp_loglik_batched.argtypes = [vp, dp, i64, i64, dp, dp, dp, dp, vp, sz, u32, vp]
@@ -225,6 +227,14 @@ def spingp_posterior_lag1(h, t, y, n, theta, ll_out, mean_out, var_out, lag1_out
     return load().spingp_posterior_lag1(h, _ptr(t), _ptr(y), int(n), _ptr(theta), _ptr(ll_out), _ptr(mean_out),
                                         _ptr(var_out), _ptr(lag1_out), _ptr(ws), int(ws_bytes), int(flags),
                                         stream if stream is not None else _stream())
+
+
+
+def spingp_grad_posterior(h, t, y, n, theta, ll_out, grad_out, mean_out, var_out, lag1_out, ws, ws_bytes, flags,
+                          stream=None):
+    return load().spingp_grad_posterior(h, _ptr(t), _ptr(y), int(n), _ptr(theta), _ptr(ll_out), _ptr(grad_out),
+                                        _ptr(mean_out), _ptr(var_out), _ptr(lag1_out), _ptr(ws), int(ws_bytes),
+                                        int(flags), stream if stream is not None else _stream())
 
 
 def spingp_workspace_bytes_batched(h, n_series, n_total, what):
@@ -584,6 +594,26 @@ class Model:
         _check(spingp_posterior_lag1(self.h, t, y, n, theta, ll, mean, var, lag, ws, ws.numel(),
                                      self._flags(sync, missing)), "spingp_posterior_lag1")
         return mean, var, lag[:n - 1], ll
+
+    def grad_posterior(self, t, y, theta, sync=True, missing=False, log_params=False, predictive=False,
+                       lag1=False, out=None):
+        """(ll, grad, mean, var, cov_lag1 or None) from one pass: the gradient
+        of grad() and the posterior of posterior() / posterior_lag1().
+        out: (ll, grad, mean, var, cov_lag1 or None) buffers to write instead."""
+        n = self._args(t, y, theta)
+        ws = self.workspace(n, WS_GRAD, t.device)
+        dev = t.device
+        if out is not None:
+            ll, g, mean, var, lag = out
+        else:
+            ll = torch.empty(1, dtype=torch.float64, device=dev)
+            g = torch.empty(self.num_params, dtype=torch.float64, device=dev)
+            mean = torch.empty(n, dtype=torch.float64, device=dev)
+            var = torch.empty(n, dtype=torch.float64, device=dev)
+            lag = torch.empty(max(n - 1, 1), dtype=torch.float64, device=dev) if lag1 else None
+        _check(spingp_grad_posterior(self.h, t, y, n, theta, ll, g, mean, var, lag, ws, ws.numel(),
+                                     self._flags(sync, missing, log_params, predictive)), "spingp_grad_posterior")
+        return ll, g, mean, var, (lag[:n - 1] if lag is not None else None)
 
     def predict(self, t, y, theta, t_star, predictive=False):
         """Latent predictive mean and variance at new times t_star (Eqs.
