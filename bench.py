@@ -93,6 +93,9 @@ def parse():
                     help="profiling: time only this workload's gradient call (matern52_n4m, sum_qp_n1m, "
                          "m32_eq10_n1m, matern32_n64m or batched_4096), --n steps (--n series for the batch), "
                          "and print one short line")
+    ap.add_argument("--call", default="grad", choices=["grad", "grad_posterior"],
+                    help="with --only on a single series: the call to time (grad_posterior: the fused "
+                         "gradient + posterior mean and variance)")
     ap.add_argument("--no-next", action="store_true",
                     help="skip the rows built beyond the hot path (prediction, literal mode, BTD solver, "
                          "EQ oracle rate, batched SCG)")
@@ -232,6 +235,10 @@ def _time_calls(fn, K, flush, torch):
 # the flops and kept in the time.
 WORKLOAD_EXEC_PER_STEP = {"sum_qp_n1m": (12310.5, 8059.1), "m32_eq10_n1m": (21120.6, 13421.2),
                           "matern32_n64m": (215.1, 144.1), "batched_4096": (397.6, 246.9)}
+# The same for the fused gradient + posterior call (spingp_grad_posterior):
+# the elimination as above, the chunk pass captured with `--only <workload>
+# --call grad_posterior` (b = 16 at 2^18 steps, b = 2 at 2^22).
+GRAD_POSTERIOR_EXEC_PER_STEP = {"sum_qp_n1m": (12398.8, 8251.7), "matern32_n64m": (222.1, 149.1)}
 
 
 def extra_workloads(args, dev, flush, world, rank=0, fp64_tflops=None):
@@ -319,8 +326,15 @@ def extra_workloads(args, dev, flush, world, rank=0, fp64_tflops=None):
             st2 = spingp.spingp_ws_status(m.workspace(n, spingp.WS_GRAD, dev))
             graph2 = capture(two_calls)
             sms_ = max_ms(_time_calls(graph2.replay, K, flush, torch))
+            fl, inst = GRAD_POSTERIOR_EXEC_PER_STEP[name]
+            rate = n / (gms * 1e-3)
             entry["graph_grad_posterior"] = {
-                "value": world * n / (gms * 1e-3), "unit": "steps/s", "ms_per_step": gms, "captured_graph": True,
+                "value": world * rate, "unit": "steps/s", "ms_per_step": gms, "captured_graph": True,
+                "roofline": {"bound": "alu", "kernel": "whole call", "unit": "TFLOP/s", "peak": fp64_tflops,
+                             "achieved": fl * rate / 1e12, "frac": fl * rate / 1e12 / fp64_tflops,
+                             "pipe_frac": inst * rate / (fp64_tflops * 1e12 / 2.0), "flops_per_step": fl,
+                             "fp64_inst_per_step": inst,
+                             "peak_kind": "measured FP64 FMA probe (spingp_probe_fp64)"},
                 "status": st2, "what": "spingp_grad_posterior (ll, gradient, mean and variance), one graph",
                 "gpu_launches_per_step": spingp.spingp_launch_count(m.h, n, spingp.WS_GRAD),
                 "separate_calls": {"ms_per_step": sms_, "what": "spingp_grad then spingp_posterior, one graph",
@@ -614,7 +628,8 @@ def next_rows(args, dev, flush, fp64_tflops):
 # ---------------------------------------------------------------- one workload alone (profiling)
 
 def run_only(args):
-    """The gradient call of one workload, --warmup untimed and --steps timed
+    """The gradient call of one workload (with --call grad_posterior, the
+    fused gradient + posterior call), --warmup untimed and --steps timed
     calls (L2 flushed before each), at the workload's size or --n steps
     (--n series for the batch): a command for ncu to capture."""
     import torch
@@ -639,7 +654,12 @@ def run_only(args):
         m = spingp.Model(s.spec)
         ll = torch.empty(1, dtype=torch.float64, device=dev)
         g = torch.empty(m.num_params, dtype=torch.float64, device=dev)
-        call = lambda: m.grad(T, Y, TH, sync=False, out=(ll, g))   # noqa: E731
+        if args.call == "grad_posterior":
+            mean = torch.empty(len(s.t), dtype=torch.float64, device=dev)
+            var = torch.empty(len(s.t), dtype=torch.float64, device=dev)
+            call = lambda: m.grad_posterior(T, Y, TH, sync=False, out=(ll, g, mean, var, None))   # noqa: E731
+        else:
+            call = lambda: m.grad(T, Y, TH, sync=False, out=(ll, g))   # noqa: E731
         units, what = len(s.t), "steps"
     if args.chunk > 0:
         m.set_chunk_len(args.chunk)
@@ -647,7 +667,7 @@ def run_only(args):
         call()
     torch.cuda.synchronize()
     ms = _time_calls(call, max(args.steps, 1), flush, torch)
-    print(json.dumps({"only": args.only, "units": units, "what": what, "ms_per_call": ms,
+    print(json.dumps({"only": args.only, "call": args.call, "units": units, "what": what, "ms_per_call": ms,
                       "value": units / (ms * 1e-3), "unit": "steps/s"}), flush=True)
 
 
