@@ -311,6 +311,21 @@ spingp_status spingp_segment_grad(const spingp_model* model, const double* t, co
                                   const double* theta, double t_prev, int first, const double* elems, int n_ranks,
                                   int rank, double* ll_out, double* grad_out, void* ws, size_t ws_bytes,
                                   unsigned flags, void* stream);
+/* Step 3 with the posterior as well (spingp_grad_posterior for a split
+ * series): this range's share of ll and gradient, as spingp_segment_grad
+ * writes them, and the posterior mean and latent variance at this range's
+ * own steps, mean_out[0 .. n-1] and var_out[0 .. n-1] (device; all four
+ * outputs required).  The mean and variance at a step use every rank's
+ * observations, before and after the range: the elements of all G ranks
+ * carry the information that the range's reverse sweep starts from, so no
+ * further exchange is needed.  The same arguments, workspace and flags as
+ * spingp_segment_grad; SPINGP_PREDICTIVE adds the noise variance to var_out.
+ * With G = 1 the outputs are spingp_grad_posterior's. */
+spingp_status spingp_segment_grad_posterior(const spingp_model* model, const double* t, const double* y, int64_t n,
+                                            const double* theta, double t_prev, int first, const double* elems,
+                                            int n_ranks, int rank, double* ll_out, double* grad_out,
+                                            double* mean_out, double* var_out, void* ws, size_t ws_bytes,
+                                            unsigned flags, void* stream);
 
 /* Log-likelihood and gradient from HOST buffers (Sec. 2.4; the same result
  * as spingp_grad, bit for bit): t, y (n doubles each) and theta are host

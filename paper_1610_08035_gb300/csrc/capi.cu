@@ -494,7 +494,8 @@ int spingp_segment_launch_count(const spingp_model* m, int64_t n) {
 static spingp_status segment_call(const spingp_model* m, int phase, const double* t, const double* y, int64_t n,
                                   const double* theta, double t_prev, int first, const double* elems, int n_ranks,
                                   int rank, double* elem_out, double* ll_out, double* grad_out, void* ws,
-                                  size_t ws_bytes, unsigned flags, void* stream) {
+                                  size_t ws_bytes, unsigned flags, void* stream, double* mean_out = nullptr,
+                                  double* var_out = nullptr) {
     if (!m || !t || !y || !theta || !ws || n < 1) return SPINGP_EINVAL;
     if (!single_matern(m) && !m->group) return SPINGP_EUNSUPPORTED;
     if (((uintptr_t)ws & 255u) != 0) return SPINGP_EINVAL;
@@ -507,11 +508,15 @@ static spingp_status segment_call(const spingp_model* m, int phase, const double
     const int miss = (flags & SPINGP_MISSING_NAN) ? 1 : 0;
     const double tp = first ? 0.0 : t_prev;
     int rc = m->group ? spg::group_segment(m->gm, phase, t, y, n, L, theta, tp, first ? 1 : 0, elems, n_ranks,
-                                           rank, elem_out, ll_out, grad_out, ws, (cudaStream_t)stream, miss)
+                                           rank, elem_out, ll_out, grad_out, ws, (cudaStream_t)stream, miss,
+                                           mean_out, var_out)
                       : spg::matern_segment(m->b, phase, t, y, n, L, theta, tp, first ? 1 : 0, elems, n_ranks,
-                                            rank, elem_out, ll_out, grad_out, ws, (cudaStream_t)stream, miss);
+                                            rank, elem_out, ll_out, grad_out, ws, (cudaStream_t)stream, miss,
+                                            mean_out, var_out);
     // the shares are linear in the gradient, so each scales on its own
     if (!rc && grad_out && (flags & SPINGP_LOG_GRAD)) rc = spg::grad_to_log(grad_out, theta, m->P, (cudaStream_t)stream);
+    if (!rc && var_out && (flags & SPINGP_PREDICTIVE))
+        rc = spg::add_noise(var_out, n, theta + m->P - 1, (cudaStream_t)stream);
     if (rc) return SPINGP_ECUDA;
     if (flags & SPINGP_SYNC) return spingp_ws_status(ws, stream);
     return SPINGP_OK;
@@ -534,6 +539,18 @@ spingp_status spingp_segment_grad(const spingp_model* m, const double* t, const 
     if ((first != 0) != (rank == 0)) return SPINGP_EINVAL;
     return segment_call(m, 1, t, y, n, theta, t_prev, first, elems, n_ranks, rank, NULL, ll_out, grad_out, ws,
                         ws_bytes, flags, stream);
+}
+
+spingp_status spingp_segment_grad_posterior(const spingp_model* m, const double* t, const double* y, int64_t n,
+                                            const double* theta, double t_prev, int first, const double* elems,
+                                            int n_ranks, int rank, double* ll_out, double* grad_out,
+                                            double* mean_out, double* var_out, void* ws, size_t ws_bytes,
+                                            unsigned flags, void* stream) {
+    if (!elems || !ll_out || !grad_out || !mean_out || !var_out) return SPINGP_EINVAL;
+    if (n_ranks < 1 || n_ranks > spg::SEG_MAX_RANKS || rank < 0 || rank >= n_ranks) return SPINGP_EINVAL;
+    if ((first != 0) != (rank == 0)) return SPINGP_EINVAL;
+    return segment_call(m, 1, t, y, n, theta, t_prev, first, elems, n_ranks, rank, NULL, ll_out, grad_out, ws,
+                        ws_bytes, flags, stream, mean_out, var_out);
 }
 
 // ---------------------------------------------------------------- host buffers in, host results out

@@ -1587,7 +1587,8 @@ __global__ void __launch_bounds__(256) k_gelems_to_soa(const double* __restrict_
 
 int group_segment(const GModel& gm, int phase, const double* t, const double* y, int64_t n, int64_t L,
                   const double* theta, double t_prev, int first, const double* elems, int G, int rank,
-                  double* elem_out, double* ll_out, double* grad_out, void* wsv, cudaStream_t st, int missing) {
+                  double* elem_out, double* ll_out, double* grad_out, void* wsv, cudaStream_t st, int missing,
+                  double* mean_out, double* var_out) {
     if (G < 1 || G > SEG_MAX_RANKS || rank < 0 || rank >= G) return 1;
     GLayout lay(n, L, MODE_GRAD, gm.phs);
     char* ws = (char*)wsv;
@@ -1633,7 +1634,11 @@ int group_segment(const GModel& gm, int phase, const double* t, const double* y,
         if (gscan_down(ws, lay.off_nodes, lay.off_pre, lay.off_suf, lay.lev_n, lay.nlev, tpre, tsuf, st)) return 1;
         const double* pre = (const double*)(ws + lay.off_pre[0]);
         const double* suf = (const double*)(ws + lay.off_suf[0]);
-        gchunk_launch<MODE_GRAD>(NRr, gm.eq_nk > 1, cgrid, st, a, pre, suf, store, part, nullptr, nullptr);
+        if (mean_out)
+            gchunk_launch<MODE_GRAD_POSTERIOR>(NRr, gm.eq_nk > 1, cgrid, st, a, pre, suf, store, part, mean_out,
+                                               var_out);
+        else
+            gchunk_launch<MODE_GRAD>(NRr, gm.eq_nk > 1, cgrid, st, a, pre, suf, store, part, nullptr, nullptr);
         k_gfinal<<<1, GFIN, 0, st>>>(gm, part, lay.nc, GPART, theta, gconst, ll_out, grad_out);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : 1;

@@ -80,11 +80,13 @@ int add_noise(double* var, int64_t n, const double* s_n, cudaStream_t st);
 int add_noise_batched(double* var, const int64_t* offsets, int64_t n_series, const double* theta, int P,
                       cudaStream_t st);
 // a series split across ranks (phase 0: reduce this range to its element;
-// phase 1: from all G elements, this range's share of ll and gradient)
+// phase 1: from all G elements, this range's share of ll and gradient and,
+// when mean_out and var_out are given, the posterior at this range's steps)
 static constexpr int SEG_MAX_RANKS = 32;
 int matern_segment(int b, int phase, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
                    double t_prev, int first, const double* elems, int G, int rank, double* elem_out, double* ll_out,
-                   double* grad_out, void* ws, cudaStream_t st, int missing);
+                   double* grad_out, void* ws, cudaStream_t st, int missing, double* mean_out = nullptr,
+                   double* var_out = nullptr);
 int matern_elem_size(int b);
 int matern_segment_launch_count(int b, int64_t n, int64_t L);
 
@@ -144,7 +146,8 @@ int group_run(const GModel& gm, int mode, const double* t, const double* y, int6
               cudaStream_t st, cudaEvent_t* ev, int missing, double* lag1_out = nullptr);
 int group_segment(const GModel& gm, int phase, const double* t, const double* y, int64_t n, int64_t L,
                   const double* theta, double t_prev, int first, const double* elems, int G, int rank,
-                  double* elem_out, double* ll_out, double* grad_out, void* ws, cudaStream_t st, int missing);
+                  double* elem_out, double* ll_out, double* grad_out, void* ws, cudaStream_t st, int missing,
+                  double* mean_out = nullptr, double* var_out = nullptr);
 int group_elem_size();
 int group_segment_launch_count(int64_t n, int64_t L);
 }  // namespace spg

@@ -1382,7 +1382,8 @@ __global__ void __launch_bounds__(256) k_elems_to_soa(const double* __restrict__
 template <int B>
 int matern_segment_t(int phase, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
                      double t_prev, int first, const double* elems, int G, int rank, double* elem_out,
-                     double* ll_out, double* grad_out, void* wsv, cudaStream_t st, int missing) {
+                     double* ll_out, double* grad_out, void* wsv, cudaStream_t st, int missing, double* mean_out,
+                     double* var_out) {
     constexpr int NE = Dims<B>::NE, NM = Dims<B>::NM;
     if (G < 1 || G > SEG_MAX || rank < 0 || rank >= G) return 1;
     Layout<B> lay(n, L, MODE_GRAD);
@@ -1418,7 +1419,12 @@ int matern_segment_t(int phase, const double* t, const double* y, int64_t n, int
                               cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             return 1;
         scan_level<B>(btot, lay.nb, bpre, bsuf, lay, ws, 0, st, tpre, tsuf, false);
-        k_chunk<B, MODE_GRAD, false><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part, nullptr, nullptr);
+        if (mean_out)
+            k_chunk<B, MODE_GRAD_POSTERIOR, false><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part,
+                                                                        mean_out, var_out);
+        else
+            k_chunk<B, MODE_GRAD, false><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part, nullptr,
+                                                              nullptr);
         k_finalize<B><<<1, 256, 0, st>>>(part, lay.nb, Acc<B>::N, theta, ll_out, grad_out);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
@@ -1491,14 +1497,14 @@ int matern_run_batched(int b, int mode, const int64_t* offsets, int64_t nseries,
 
 int matern_segment(int b, int phase, const double* t, const double* y, int64_t n, int64_t L, const double* theta,
                    double t_prev, int first, const double* elems, int G, int rank, double* elem_out, double* ll_out,
-                   double* grad_out, void* ws, cudaStream_t st, int missing) {
+                   double* grad_out, void* ws, cudaStream_t st, int missing, double* mean_out, double* var_out) {
     switch (b) {
     case 1: return matern_segment_t<1>(phase, t, y, n, L, theta, t_prev, first, elems, G, rank, elem_out, ll_out,
-                                       grad_out, ws, st, missing);
+                                       grad_out, ws, st, missing, mean_out, var_out);
     case 2: return matern_segment_t<2>(phase, t, y, n, L, theta, t_prev, first, elems, G, rank, elem_out, ll_out,
-                                       grad_out, ws, st, missing);
+                                       grad_out, ws, st, missing, mean_out, var_out);
     default: return matern_segment_t<3>(phase, t, y, n, L, theta, t_prev, first, elems, G, rank, elem_out, ll_out,
-                                        grad_out, ws, st, missing);
+                                        grad_out, ws, st, missing, mean_out, var_out);
     }
 }
 int matern_elem_size(int b) { return b == 1 ? Dims<1>::NE : b == 2 ? Dims<2>::NE : Dims<3>::NE; }

@@ -102,3 +102,25 @@ def grad_split_series(model, t, y, theta, t_prev, group=None, missing=False, syn
     out = torch.cat([ll.reshape(1), g.reshape(-1)])
     dist.all_reduce(out, op=dist.ReduceOp.SUM, group=group)
     return out[:1], out[1:]
+
+
+def grad_posterior_split_series(model, t, y, theta, t_prev, group=None, missing=False, sync=True):
+    """grad_split_series plus the posterior at this rank's steps: returns
+    (ll, grad) of the whole series (the same on every rank) and (mean, var)
+    at this rank's range, conditioned on all ranks' observations.  The
+    exchange is grad_split_series': one all-gather of the ranges' elements,
+    one all-reduce of (ll, grad); the posterior needs nothing more, since
+    every rank's element reaches every rank.  `model` provides
+    segment_reduce / segment_grad_posterior (spingp.Model does)."""
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    if (t_prev is None) != (rank == 0):
+        raise ValueError("t_prev must be None exactly on rank 0")
+    elem = model.segment_reduce(t, y, theta, t_prev=t_prev, missing=missing, sync=sync)
+    elems = [torch.empty_like(elem) for _ in range(world)]
+    dist.all_gather(elems, elem, group=group)
+    ll, g, mean, var = model.segment_grad_posterior(t, y, theta, torch.stack(elems), rank, t_prev=t_prev,
+                                                    missing=missing, sync=sync)
+    out = torch.cat([ll.reshape(1), g.reshape(-1)])
+    dist.all_reduce(out, op=dist.ReduceOp.SUM, group=group)
+    return out[:1], out[1:], mean, var

@@ -32,7 +32,7 @@ EXPORTS = ("spingp_model_create", "spingp_model_destroy", "spingp_num_params", "
            "spingp_profile_read", "spingp_probe_fp64_bytes", "spingp_probe_fp64", "spingp_probe_fp64_tensor",
            "spingp_probe_exp_neg",
            "spingp_workspace_bytes_host", "spingp_segment_elem_size", "spingp_segment_launch_count",
-           "spingp_segment_reduce", "spingp_segment_grad",
+           "spingp_segment_reduce", "spingp_segment_grad", "spingp_segment_grad_posterior",
            "spingp_grad_host", "spingp_loglik_noalloc",
            "spingp_btd_workspace_bytes", "spingp_btd_solve", "spingp_btd_launch_count",
            "spingp_btd_diag_product_workspace_bytes", "spingp_btd_diag_product",
@@ -98,6 +98,8 @@ def load():
     lib.spingp_segment_reduce.argtypes = [vp, dp, dp, i64, dp, ctypes.c_double, ctypes.c_int, dp, vp, sz, u32, vp]
     lib.spingp_segment_grad.argtypes = [vp, dp, dp, i64, dp, ctypes.c_double, ctypes.c_int, dp, ctypes.c_int,
                                         ctypes.c_int, dp, dp, vp, sz, u32, vp]
+    lib.spingp_segment_grad_posterior.argtypes = [vp, dp, dp, i64, dp, ctypes.c_double, ctypes.c_int, dp,
+                                                  ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, vp, sz, u32, vp]
     lib.spingp_probe_exp_neg.argtypes = [dp, dp, i64, vp]
     lib.spingp_loglik_noalloc.argtypes = [vp, dp, dp, i64, dp, dp, u32, vp]
     lib.spingp_workspace_bytes_host.argtypes = [vp, i64]
@@ -333,6 +335,14 @@ def spingp_segment_grad(h, t, y, n, theta, t_prev, first, elems, n_ranks, rank, 
                                       int(ws_bytes), flags, stream if stream is not None else _stream())
 
 
+def spingp_segment_grad_posterior(h, t, y, n, theta, t_prev, first, elems, n_ranks, rank, ll_out, grad_out,
+                                  mean_out, var_out, ws, ws_bytes, flags, stream=None):
+    return load().spingp_segment_grad_posterior(h, _ptr(t), _ptr(y), int(n), _ptr(theta), float(t_prev),
+                                                int(first), _ptr(elems), int(n_ranks), int(rank), _ptr(ll_out),
+                                                _ptr(grad_out), _ptr(mean_out), _ptr(var_out), _ptr(ws),
+                                                int(ws_bytes), flags, stream if stream is not None else _stream())
+
+
 def spingp_workspace_bytes_host(h, n):
     return load().spingp_workspace_bytes_host(h, int(n))
 
@@ -565,6 +575,28 @@ class Model:
                                    rank, ll, g, ws, ws.numel(), self._flags(sync, missing, log_params)),
                "spingp_segment_grad")
         return ll, g
+
+    def segment_grad_posterior(self, t, y, theta, elems, rank, t_prev=None, ws=None, sync=True, missing=False,
+                               log_params=False, predictive=False):
+        """Phase 2 with the posterior: this range's share of (ll, grad) and
+        the posterior mean and variance at this range's steps, conditioned on
+        every rank's observations; the same arguments and workspace as
+        segment_reduce.  Returns (ll, grad, mean, var)."""
+        n = self._args(t, y, theta)
+        ws = ws if ws is not None else self.workspace(n, WS_GRAD, t.device, purpose="segment")
+        _dev_f64(elems, "elems")
+        elems = elems.contiguous()
+        dev = t.device
+        ll = torch.empty(1, dtype=torch.float64, device=dev)
+        g = torch.empty(self.num_params, dtype=torch.float64, device=dev)
+        mean = torch.empty(n, dtype=torch.float64, device=dev)
+        var = torch.empty(n, dtype=torch.float64, device=dev)
+        first = t_prev is None
+        _check(spingp_segment_grad_posterior(self.h, t, y, n, theta, 0.0 if first else t_prev, first, elems,
+                                             elems.shape[0], rank, ll, g, mean, var, ws, ws.numel(),
+                                             self._flags(sync, missing, log_params, predictive)),
+               "spingp_segment_grad_posterior")
+        return ll, g, mean, var
 
     def posterior(self, t, y, theta, sync=True, with_loglik=True, missing=False, predictive=False, out=None):
         """(mean, var, ll): latent posterior mean and variance at t; with

@@ -126,6 +126,22 @@ class _OracleRange:
         return (torch.tensor([ll1 - ll0], dtype=torch.float64),
                 torch.tensor(g1 - g0, dtype=torch.float64))
 
+    def segment_grad_posterior(self, t, y, theta, elems, rank, t_prev=None, missing=False, sync=True):
+        """The share above plus the posterior at this range's steps, from the
+        smoother over every rank's data: right only if the exchange brings
+        the later ranks' elements too."""
+        from oracle import seq
+        ll, g = self.segment_grad(t, y, theta, elems, rank, t_prev=t_prev, missing=missing, sync=sync)
+        ts, ys = [], []
+        for e in elems:
+            n = int(e[0])
+            ts.append(e[1:1 + n].numpy())
+            ys.append(e[1 + self.cap:1 + self.cap + n].numpy())
+        a = sum(len(x) for x in ts[:rank])
+        sm = seq.smoother(self.spec, theta.numpy(), np.concatenate(ts), np.concatenate(ys))
+        b = a + t.numel()
+        return ll, g, torch.from_numpy(sm["mean"][a:b].copy()), torch.from_numpy(sm["var"][a:b].copy())
+
 
 def _split_worker(rank, world, port, out_path):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
@@ -145,6 +161,47 @@ def _split_worker(rank, world, port, out_path):
         dist.barrier()
     finally:
         dist.destroy_process_group()
+
+
+def _split_posterior_worker(rank, world, port, out_path):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        rng = np.random.default_rng(29)
+        n = 900
+        t = synth.exp_times(n, 0.05, rng)
+        y = synth.two_sinusoids(t, 0.7, 1.0, 0.1, rng)
+        theta = torch.tensor([0.7, 1.2, 0.1], dtype=torch.float64)
+        a, b = shard.range_split(n, world)[rank]
+        t_prev = None if rank == 0 else float(t[a - 1])
+        ll, g, mean, var = shard.grad_posterior_split_series(_OracleRange("matern32"), torch.from_numpy(t[a:b].copy()),
+                                                             torch.from_numpy(y[a:b].copy()), theta, t_prev)
+        np.save(out_path + ".%d.npy" % rank, np.concatenate([ll.numpy(), g.numpy(), mean.numpy(), var.numpy()]))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_split_series_posterior_exchange_on_gloo(tmp_path, world):
+    """grad_posterior_split_series: every rank gets the whole series' (ll,
+    grad) and the smoother's mean and variance on its own range."""
+    from oracle import seq
+    out = str(tmp_path / "splitpost")
+    mp.spawn(_split_posterior_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+    rng = np.random.default_rng(29)
+    n = 900
+    t = synth.exp_times(n, 0.05, rng)
+    y = synth.two_sinusoids(t, 0.7, 1.0, 0.1, rng)
+    llo, go = seq.grad("matern32", [0.7, 1.2, 0.1], t, y)
+    sm = seq.smoother("matern32", [0.7, 1.2, 0.1], t, y)
+    for r, (a, b) in enumerate(shard.range_split(n, world)):
+        got = np.load(out + ".%d.npy" % r)
+        assert abs(got[0] - llo) <= 1e-10 * abs(llo)
+        assert np.max(np.abs(got[1:4] - go) / np.abs(go)) <= 1e-9
+        k = b - a
+        assert np.array_equal(got[4:4 + k], sm["mean"][a:b]) and np.array_equal(got[4 + k:], sm["var"][a:b])
 
 
 @pytest.mark.parametrize("world", [2, 3, 4])
