@@ -2,12 +2,15 @@
 - the chain path: random series lengths, chunk lengths, hyperparameters,
   time spacings (with ties and long gaps) and missing observations, through
   every entry point that shares the chain kernels -- gradient,
-  log-likelihood, posterior, the host-buffer call and one series split in
-  ranges -- against the oracle at the parity bars of test_gpu_parity, and the
-  host-buffer result against the device call bit for bit;
+  log-likelihood, posterior, the fused gradient + posterior call, the
+  host-buffer call and one series split in ranges (with the split
+  posterior in every other case) -- against the oracle at the parity bars
+  of test_gpu_parity, and the host-buffer result against the device call
+  bit for bit;
 - the group path: random sums of Matern-3/2, periodic, quasi-periodic and
-  order-4 EQ components (b <= 16) against the oracle, whole and split in
-  ranges;
+  order-4 to 8 EQ components (b <= 16) against the oracle, whole (also
+  through the fused call) and split in ranges (with the split posterior in
+  every other case);
 - the general BTD solver: random SPD systems of every size against the
   oracle's block LDL^T."""
 import numpy as np
@@ -49,6 +52,40 @@ def _case(k):
     return spec, theta, t, y, L, miss
 
 
+def _check_posterior(mean, var, mo, vo):
+    assert np.all(np.abs(mean - mo) <= 1e-8 * np.maximum(np.abs(mo), np.sqrt(vo)))
+    assert np.all(np.abs(var - vo) <= 1e-8 * vo)
+
+
+def _check_fused(m, T, Y, TH, miss, ll, llo, go, gscale, mo, vo):
+    """spingp_grad_posterior: the gradient call's log-likelihood bit for bit,
+    the gradient, mean and variance at the parity bars."""
+    llf, gf, mf, vf, _ = m.grad_posterior(T, Y, TH, missing=miss)
+    assert llf.item() == ll.item()
+    assert np.all(np.abs(gf.cpu().numpy() - go) <= 1e-8 * gscale)
+    _check_posterior(mf.cpu().numpy(), vf.cpu().numpy(), mo, vo)
+
+
+def _split_phase2(m, T, Y, TH, E, ranges, t, wss, miss, posterior, mo, vo):
+    """Phase 2 of the split series, rank by rank: the summed shares of
+    (ll, grad); with posterior, spingp_segment_grad_posterior, whose mean and
+    variance at every range's steps are checked against the oracle too."""
+    ls, gs, means, vars_ = 0.0, 0.0, [], []
+    for r, (a, b) in enumerate(ranges):
+        tp = None if r == 0 else float(t[a - 1])
+        if posterior:
+            lr, gr, mr, vr = m.segment_grad_posterior(T[a:b], Y[a:b], TH, E, r, t_prev=tp, ws=wss[r], missing=miss)
+            means.append(mr.cpu().numpy())
+            vars_.append(vr.cpu().numpy())
+        else:
+            lr, gr = m.segment_grad(T[a:b], Y[a:b], TH, E, r, t_prev=tp, ws=wss[r], missing=miss)
+        ls += lr.item()
+        gs = gs + gr.cpu().numpy()
+    if posterior:
+        _check_posterior(np.concatenate(means), np.concatenate(vars_), mo, vo)
+    return ls, gs
+
+
 @pytest.mark.parametrize("k", range(64))
 def test_fuzz_chain_against_oracle(k):
     spec, theta, t, y, L, miss = _case(k)
@@ -65,6 +102,9 @@ def test_fuzz_chain_against_oracle(k):
     mg, vg = mean.cpu().numpy(), var.cpu().numpy()
     assert np.all(np.abs(mg - mo) <= 1e-8 * np.maximum(np.abs(mo), np.sqrt(vo)))
     assert np.all(np.abs(vg - vo) <= 1e-8 * vo)
+    # the fused gradient + posterior call: the gradient call's log-likelihood
+    # bit for bit, every output at the parity bars
+    _check_fused(m, T, Y, TH, miss, ll, llo, go, gscale, mo, vo)
     # the host-buffer call: the device call's bits
     ll_h, g_h = m.grad_host(torch.from_numpy(t).pin_memory(), torch.from_numpy(y).pin_memory(),
                             torch.tensor(theta, dtype=torch.float64), missing=miss)
@@ -79,12 +119,7 @@ def test_fuzz_chain_against_oracle(k):
         elems.append(m.segment_reduce(T[a:b], Y[a:b], TH, t_prev=tp, ws=ws, missing=miss))
         wss.append(ws)
     E = torch.stack(elems)
-    ls, gs = 0.0, 0.0
-    for r, (a, b) in enumerate(ranges):
-        tp = None if r == 0 else float(t[a - 1])
-        lr, gr = m.segment_grad(T[a:b], Y[a:b], TH, E, r, t_prev=tp, ws=wss[r], missing=miss)
-        ls += lr.item()
-        gs = gs + gr.cpu().numpy()
+    ls, gs = _split_phase2(m, T, Y, TH, E, ranges, t, wss, miss, k % 2 == 1, mo, vo)
     assert abs(ls - llo) <= 1e-9 * abs(llo)
     assert np.all(np.abs(gs - go) <= 1e-8 * gscale)
 
@@ -161,6 +196,7 @@ def test_fuzz_group_against_oracle(k):
     assert np.all(np.abs(g.cpu().numpy() - go) <= 1e-8 * gscale), (spec, g.cpu().numpy(), go)
     assert np.all(np.abs(mean.cpu().numpy() - mo) <= 1e-8 * np.maximum(np.abs(mo), np.sqrt(vo)))
     assert np.all(np.abs(var.cpu().numpy() - vo) <= 1e-8 * vo)
+    _check_fused(m, T, Y, TH, miss, ll, llo, go, gscale, mo, vo)
     # the series split in ranges
     G = min(len(t), 1 + k % 4)
     ranges = shard.range_split(len(t), G)
@@ -171,12 +207,7 @@ def test_fuzz_group_against_oracle(k):
         elems.append(m.segment_reduce(T[a:b], Y[a:b], TH, t_prev=tp, ws=ws, missing=miss))
         wss.append(ws)
     E = torch.stack(elems)
-    ls, gs = 0.0, 0.0
-    for r, (a, b) in enumerate(ranges):
-        tp = None if r == 0 else float(t[a - 1])
-        lr, gr = m.segment_grad(T[a:b], Y[a:b], TH, E, r, t_prev=tp, ws=wss[r], missing=miss)
-        ls += lr.item()
-        gs = gs + gr.cpu().numpy()
+    ls, gs = _split_phase2(m, T, Y, TH, E, ranges, t, wss, miss, k % 2 == 0, mo, vo)
     assert abs(ls - llo) <= 1e-9 * abs(llo)
     assert np.all(np.abs(gs - go) <= 1e-8 * gscale), (spec, G, gs, go)
 
