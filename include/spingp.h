@@ -107,14 +107,16 @@ typedef enum { SPINGP_WS_LOGLIK = 0, SPINGP_WS_GRAD = 1, SPINGP_WS_POSTERIOR = 2
 /* Return the gradient with respect to log theta instead of theta:
  * d ll / d log theta_p = theta_p d ll / d theta_p (a diagonal rescaling; the
  * paper's hyperparameters are positive).  Honoured by spingp_grad,
- * spingp_grad_batched, spingp_grad_host and spingp_segment_grad (each rank's
- * share is rescaled; the shares still sum to the series' value); one more
- * kernel launch per call. */
+ * spingp_grad_posterior, their batched forms, spingp_grad_host and the
+ * split-series calls (each rank's share is
+ * rescaled; the shares still sum to the series' value); one more kernel
+ * launch per call. */
 #define SPINGP_LOG_GRAD 4u
 /* Return predictive variances of an observation instead of latent ones: the
  * latent variance H P^s H^T plus the noise variance s_n (the series' last
- * theta entry).  Honoured by spingp_posterior and spingp_posterior_batched;
- * one more kernel launch per call. */
+ * theta entry).  Honoured by every call that returns posterior variances
+ * (spingp_posterior, spingp_posterior_lag1, spingp_grad_posterior, their
+ * batched and split-series forms); one more kernel launch per call. */
 #define SPINGP_PREDICTIVE 8u
 
 /* Create a model handle from a host-side description (Sec. 2.1).  The handle
@@ -235,6 +237,19 @@ spingp_status spingp_posterior_batched(const spingp_model* model, const int64_t*
                                        int64_t n_total, const double* t, const double* y, const double* theta,
                                        double* ll_out, double* mean_out, double* var_out, void* ws,
                                        size_t ws_bytes, unsigned flags, void* stream);
+
+/* spingp_grad_batched and spingp_posterior_batched from one forward pass and
+ * one reverse sweep (Sec. 2.4 and Sec. 3.1 share subproblems 1 to 4; see
+ * spingp_grad_posterior): per-series ll_out[n_series] and
+ * grad_out[n_series x num_params], per-step mean_out and var_out indexed like
+ * t and y (all required when n_total > 0).  Each output equals the separate
+ * call's up to rounding order.  Workspace:
+ * spingp_workspace_bytes_batched(..., SPINGP_WS_GRAD).  SPINGP_LOG_GRAD
+ * affects grad_out only, SPINGP_PREDICTIVE var_out only. */
+spingp_status spingp_grad_posterior_batched(const spingp_model* model, const int64_t* offsets, int64_t n_series,
+                                            int64_t n_total, const double* t, const double* y, const double* theta,
+                                            double* ll_out, double* grad_out, double* mean_out, double* var_out,
+                                            void* ws, size_t ws_bytes, unsigned flags, void* stream);
 
 /* Number of kernels one call of the given kind launches for n steps (the
  * discretisation/elimination pass, the reduction tiles, the per-chunk pass

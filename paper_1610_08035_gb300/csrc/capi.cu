@@ -302,6 +302,15 @@ spingp_status spingp_posterior_batched(const spingp_model* m, const int64_t* off
                        var_out, ws, ws_bytes, flags, stream);
 }
 
+spingp_status spingp_grad_posterior_batched(const spingp_model* m, const int64_t* offsets, int64_t n_series,
+                                            int64_t n_total, const double* t, const double* y, const double* theta,
+                                            double* ll_out, double* grad_out, double* mean_out, double* var_out,
+                                            void* ws, size_t ws_bytes, unsigned flags, void* stream) {
+    if (!ll_out || !grad_out || (n_total > 0 && (!mean_out || !var_out))) return SPINGP_EINVAL;
+    return run_batched(m, spg::MODE_GRAD_POSTERIOR, offsets, n_series, n_total, t, y, theta, ll_out, grad_out,
+                       mean_out, var_out, ws, ws_bytes, flags, stream);
+}
+
 
 spingp_status spingp_model_create(const spingp_model_desc* d, spingp_model** out) {
     if (!out) return SPINGP_EINVAL;

@@ -1344,6 +1344,11 @@ int matern_run_batched_t(int mode, const int64_t* offsets, int64_t nseries, int6
                                                          nullptr);
         na = Acc<B>::N;
         break;
+    case MODE_GRAD_POSTERIOR:
+        k_chunk<B, MODE_GRAD_POSTERIOR, true><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part,
+                                                                   mean_out, var_out);
+        na = Acc<B>::N;
+        break;
     default:
         k_chunk<B, MODE_POSTERIOR, true><<<grid, CTA, 0, st>>>(a, nodes, bpre, bsuf, phis, store, part, mean_out,
                                                               var_out);

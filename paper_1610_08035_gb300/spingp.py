@@ -27,7 +27,7 @@ EXPORTS = ("spingp_model_create", "spingp_model_destroy", "spingp_num_params", "
            "spingp_set_chunk_len", "spingp_get_chunk_len", "spingp_workspace_bytes", "spingp_loglik",
            "spingp_grad", "spingp_posterior", "spingp_posterior_lag1", "spingp_grad_posterior",
            "spingp_workspace_bytes_batched", "spingp_loglik_batched",
-           "spingp_grad_batched", "spingp_posterior_batched", "spingp_launch_count",
+           "spingp_grad_batched", "spingp_posterior_batched", "spingp_grad_posterior_batched", "spingp_launch_count",
            "spingp_launch_count_batched", "spingp_profile_enable",
            "spingp_profile_read", "spingp_probe_fp64_bytes", "spingp_probe_fp64", "spingp_probe_fp64_tensor",
            "spingp_probe_exp_neg",
@@ -84,6 +84,8 @@ def load():
     lib.spingp_workspace_bytes_batched.restype = sz
     lib.spingp_loglik_batched.argtypes = [vp, dp, i64, i64, dp, dp, dp, dp, vp, sz, u32, vp]
     lib.spingp_grad_batched.argtypes = [vp, dp, i64, i64, dp, dp, dp, dp, dp, vp, sz, u32, vp]
+    lib.spingp_grad_posterior_batched.argtypes = [vp, dp, i64, i64, dp, dp, dp, dp, dp, dp, dp, vp, sz, u32,
+                                                  vp]
     lib.spingp_posterior_batched.argtypes = [vp, dp, i64, i64, dp, dp, dp, dp, dp, dp, vp, sz, u32, vp]
     lib.spingp_launch_count.argtypes = [vp, i64, ctypes.c_int]
     lib.spingp_launch_count_batched.argtypes = [vp, i64, i64, ctypes.c_int]
@@ -261,6 +263,14 @@ def spingp_posterior_batched(h, offsets, n_series, n_total, t, y, theta, ll_out,
     return load().spingp_posterior_batched(h, _ptr(offsets), int(n_series), int(n_total), _ptr(t), _ptr(y),
                                            _ptr(theta), _ptr(ll_out), _ptr(mean_out), _ptr(var_out), _ptr(ws),
                                            ws_bytes, flags, stream if stream is not None else _stream())
+
+
+def spingp_grad_posterior_batched(h, offsets, n_series, n_total, t, y, theta, ll_out, grad_out, mean_out, var_out,
+                                  ws, ws_bytes, flags, stream=None):
+    return load().spingp_grad_posterior_batched(h, _ptr(offsets), int(n_series), int(n_total), _ptr(t), _ptr(y),
+                                                _ptr(theta), _ptr(ll_out), _ptr(grad_out), _ptr(mean_out),
+                                                _ptr(var_out), _ptr(ws), ws_bytes, flags,
+                                                stream if stream is not None else _stream())
 
 
 def spingp_launch_count_batched(h, n_series, n_total, what):
@@ -830,6 +840,22 @@ class Batch:
                                         Model._flags(sync, missing, predictive=predictive)),
                "spingp_posterior_batched")
         return mean, var, ll
+
+    def grad_posterior(self, theta, sync=True, missing=False, log_params=False, predictive=False):
+        """(ll, grad, mean, var) from one pass: grad()'s per-series values
+        and posterior()'s per-step mean and variance."""
+        ws = self.workspace(WS_GRAD)
+        dev = self.t.device
+        P = self.model.num_params
+        ll = torch.empty(self.n_series, dtype=torch.float64, device=dev)
+        g = torch.empty(self.n_series * P, dtype=torch.float64, device=dev)
+        mean = torch.empty(self.n_total, dtype=torch.float64, device=dev)
+        var = torch.empty(self.n_total, dtype=torch.float64, device=dev)
+        _check(spingp_grad_posterior_batched(self.model.h, self.offsets, self.n_series, self.n_total, self.t, self.y,
+                                             self._theta(theta), ll, g, mean, var, ws, ws.numel(),
+                                             Model._flags(sync, missing, log_params, predictive)),
+               "spingp_grad_posterior_batched")
+        return ll, g.view(self.n_series, P), mean, var
 
     def optimize(self, theta0, iterations=100, tol=1e-8, sync=True):
         """Fit every series' hyperparameters by scaled conjugate gradients

@@ -173,3 +173,45 @@ def test_graph_capture_replays():
     torch.cuda.synchronize()
     for a, b in zip(ref, out):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("missing", [False, True])
+def test_batched(missing):
+    """spingp_grad_posterior_batched against spingp_grad_batched and
+    spingp_posterior_batched (series of uneven length, an empty one and a
+    one-step one, per-series theta), and sampled series against the oracle."""
+    rng = np.random.default_rng(5 + missing)
+    lens = [300, 0, 1, 2000, 57, 4096, 9]
+    ts, ys, ths = [], [], []
+    for k, n in enumerate(lens):
+        t, y = _series(n, 0.01, 100 + k, missing=0.1 if missing else 0.0) if n else (np.zeros(0), np.zeros(0))
+        ts.append(t)
+        ys.append(y)
+        ths.append([float(np.exp(rng.uniform(-1.5, 1.0))), float(np.exp(rng.uniform(-0.5, 0.5))),
+                    float(np.exp(rng.uniform(-4.0, -1.0)))])
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    t_all, y_all = np.concatenate(ts), np.concatenate(ys)
+    th = np.array(ths)
+    m = spingp.Model("matern52")
+    bt = spingp.Batch(m, torch.tensor(off, device=DEV), _t(t_all), _t(y_all))
+    TH = _t(th.reshape(-1))
+    ll, g, mean, var = bt.grad_posterior(TH, missing=missing)
+    ll1, g1 = bt.grad(TH, missing=missing)
+    mean2, var2, ll2 = bt.posterior(TH, missing=missing)
+    assert torch.equal(ll, ll1)
+    assert torch.allclose(ll, ll2, rtol=1e-13, atol=0.0)
+    _close(g, g1, np.maximum(1.0, np.abs(g1.cpu().numpy())), 1e-11)
+    vmax = float(var2.abs().max())
+    _close(mean, mean2, max(float(mean2.abs().max()), np.sqrt(vmax)))
+    _close(var, var2, vmax)
+    ll, g, mean, var = ll.cpu().numpy(), g.cpu().numpy(), mean.cpu().numpy(), var.cpu().numpy()
+    for i in (0, 2, 3, 4):
+        a, b = off[i], off[i + 1]
+        llo, go, gl1 = seq.grad("matern52", th[i], t_all[a:b], y_all[a:b], l1=True)
+        sm = seq.smoother("matern52", th[i], t_all[a:b], y_all[a:b])
+        assert abs(ll[i] - llo) <= 1e-9 * abs(llo)
+        assert np.all(np.abs(g[i] - go) <= 1e-8 * np.maximum(np.abs(go), gl1))
+        mo, vo = sm["mean"], sm["var"]
+        assert np.all(np.abs(mean[a:b] - mo) <= 1e-8 * np.maximum(np.abs(mo), np.sqrt(vo)))
+        assert np.all(np.abs(var[a:b] - vo) <= 1e-8 * vo)
+    assert ll[1] == 0.0 and np.all(g[1] == 0.0)
