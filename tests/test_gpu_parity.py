@@ -244,8 +244,9 @@ def test_large_series_full_size():
 
 def test_large_series_step_in_a_captured_graph():
     """The long-series workload's step (N = 2^26: log-likelihood, gradient
-    and posterior mean) captured once into a CUDA graph and replayed: the
-    replay writes the same bits as the eager calls."""
+    and posterior mean) captured once into a CUDA graph and replayed, as two
+    calls and as the fused call: each replay writes the same bits as its
+    eager calls."""
     s = synth.single("matern32_n64m")
     n = len(s.t)
     m = spingp.Model(s.spec)
@@ -273,6 +274,28 @@ def test_large_series_step_in_a_captured_graph():
         assert torch.equal(mean, mean_e) and torch.equal(var, var_e)
     assert spingp.spingp_ws_status(m.workspace(n, spingp.WS_GRAD, DEV)) == spingp.OK
     assert spingp.spingp_ws_status(m.workspace(n, spingp.WS_POSTERIOR, DEV)) == spingp.OK
+    # the same step through the fused call (the benchmark's graph): its replay
+    # writes the eager fused call's bits; the log-likelihood is the gradient
+    # call's, the other outputs the separate calls' up to rounding order
+    fused = m.grad_posterior(T, Y, TH)
+    assert torch.equal(fused[0], ll_e)
+    gs = np.maximum(1.0, np.abs(g_e.cpu().numpy()))
+    assert np.all(np.abs(fused[1].cpu().numpy() - g_e.cpu().numpy()) <= 1e-11 * gs)
+    vmax = float(var_e.max())
+    scale = max(float(mean_e.abs().max()), np.sqrt(vmax))
+    assert float((fused[2] - mean_e).abs().max()) <= 1e-13 * scale
+    assert float((fused[3] - var_e).abs().max()) <= 1e-13 * vmax
+    out = (ll, g, mean, var, None)
+    with torch.cuda.stream(stream):
+        graph2 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph2, stream=stream):
+            m.grad_posterior(T, Y, TH, sync=False, out=out)
+    torch.cuda.current_stream().wait_stream(stream)
+    ll.fill_(float("nan")); g.fill_(float("nan")); mean.fill_(float("nan")); var.fill_(float("nan"))
+    graph2.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(fused[:4], out[:4]):
+        assert torch.equal(a, b)
 
 
 @pytest.mark.parametrize("spec", [["matern52"], ["matern32", ("quasiperiodic", 3, "matern12")]])
