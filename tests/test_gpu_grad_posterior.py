@@ -215,3 +215,32 @@ def test_batched(missing):
         assert np.all(np.abs(mean[a:b] - mo) <= 1e-8 * np.maximum(np.abs(mo), np.sqrt(vo)))
         assert np.all(np.abs(var[a:b] - vo) <= 1e-8 * vo)
     assert ll[1] == 0.0 and np.all(g[1] == 0.0)
+
+
+def test_batched_and_split_argument_errors():
+    """The batched and split-series fused calls reject a missing output with
+    EINVAL; a batch of empty series needs no posterior buffers."""
+    m = spingp.Model("matern32")
+    f64 = dict(dtype=torch.float64, device=DEV)
+    off = torch.tensor([0, 3, 5], dtype=torch.int64, device=DEV)
+    T, Y, TH = _t(np.arange(5) * 0.1), _t(np.sin(np.arange(5))), _t([1.0, 1.0, 0.1, 0.5, 2.0, 0.2])
+    ws = torch.empty(spingp.spingp_workspace_bytes_batched(m.h, 2, 5, spingp.WS_GRAD), dtype=torch.uint8, device=DEV)
+    ll, g, mean, var = torch.empty(2, **f64), torch.empty(6, **f64), torch.empty(5, **f64), torch.empty(5, **f64)
+    for args in ((None, g, mean, var), (ll, None, mean, var), (ll, g, None, var), (ll, g, mean, None)):
+        st = spingp.spingp_grad_posterior_batched(m.h, off, 2, 5, T, Y, TH, *args, ws, ws.numel(), spingp.SYNC)
+        assert st == spingp.EINVAL
+    assert spingp.spingp_grad_posterior_batched(m.h, off, 2, 5, T, Y, TH, ll, g, mean, var, ws, ws.numel(),
+                                                spingp.SYNC) == spingp.OK
+    empty = torch.zeros(3, dtype=torch.int64, device=DEV)
+    ws0 = torch.empty(max(spingp.spingp_workspace_bytes_batched(m.h, 2, 0, spingp.WS_GRAD), 256), dtype=torch.uint8,
+                      device=DEV)
+    assert spingp.spingp_grad_posterior_batched(m.h, empty, 2, 0, None, None, TH, ll, g, None, None, ws0, ws0.numel(),
+                                                spingp.SYNC) == spingp.OK
+    assert torch.all(ll == 0.0) and torch.all(g == 0.0)
+    # the split-series form: every output required
+    E = torch.zeros(1, spingp.spingp_segment_elem_size(m.h), **f64)
+    wss = m.workspace(5, spingp.WS_GRAD, DEV)
+    l1, g1 = torch.empty(1, **f64), torch.empty(3, **f64)
+    st = spingp.spingp_segment_grad_posterior(m.h, T, Y, 5, TH[:3], 0.0, 1, E, 1, 0, l1, g1, None, var, wss,
+                                              wss.numel(), spingp.SYNC)
+    assert st == spingp.EINVAL
