@@ -774,12 +774,19 @@ def main():
     roof.update(_algorithmic(WORKLOAD, n / (ms_per_step * 1e-3), fp64_tflops))
     hbm = {"algorithmic_bytes_per_step": ALGO_BYTES_PER_STEP,
            "achieved_gbs": ALGO_BYTES_PER_STEP * n / (ms_per_step * 1e-3) / 1e9}
+    if traffic:
+        # the dominant kernel's measured DRAM bytes (ncu, per step x N) over its
+        # live launch time: the bandwidth it actually draws, beside the
+        # algorithmic figure
+        hbm["dominant_kernel_dram_gbs"] = traffic * n / (stage_ms[dom] * 1e-3) / 1e9
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(peaks_path):
         with open(peaks_path) as f:
             hbm_peak = json.load(f).get("hbm_gbs")
         hbm["peak_gbs"] = hbm_peak
         hbm["frac"] = hbm["achieved_gbs"] / hbm_peak if hbm_peak else None
+        if traffic and hbm_peak:
+            hbm["dominant_kernel_dram_frac"] = hbm["dominant_kernel_dram_gbs"] / hbm_peak
         hbm["peak_kind"] = "measured (MEASURED_PEAKS.json)"
     else:
         hbm["peak_gbs"] = 6800.0
