@@ -19,7 +19,12 @@ Sec. 4.2, "two sinusoids immersed into Gaussian noise"):
   dt_i ~ Uniform(lo, hi) times the lengthscale;
 * general block-tridiagonal inputs: T = B B^T + ridge I for a random lower
   block-bidiagonal B (diagonal blocks N(0, 1) + 2 I, sub-diagonal blocks
-  N(0, 1)), returned as its blocks without forming T.
+  N(0, 1)), returned as its blocks without forming T;
+* a series shaped like the paper's CO2 experiment (Sec. 4.3), with no data
+  from it: a regular weekly grid of 2195 points in years (t_i = i / 52.1775),
+  a slowly rising smooth trend, an annual cycle with its first overtone whose
+  amplitude drifts slowly, and Gaussian noise, centred and scaled to unit
+  variance.
 """
 from dataclasses import dataclass, field
 
@@ -123,3 +128,22 @@ def random_spd_btd(n, b, seed, ridge=0.1):
     O = Bs @ np.transpose(Bd[:-1], (0, 2, 1))            # B[i+1,i] B[i,i]^T
     r = rng.standard_normal((n, b))
     return D, O, r
+
+
+def co2_shaped(seed=6, n=2195):
+    """A weekly series of the CO2 experiment's shape (Sec. 4.3) with the
+    structured model of the b = 16 workload (Matern-3/2 for the trend,
+    quasi-periodic of order 6 with a Matern-1/2 envelope for the cycle) and
+    a starting theta for fitting: (l_m32, s_m32, s_per, l_per, period,
+    l_env, s_n)."""
+    rng = np.random.default_rng(seed)
+    t = np.arange(n, dtype=np.float64) / 52.1775
+    u = t / t[-1]
+    trend = 3.0 * u + 1.5 * u * u + 0.3 * np.sin(2.0 * np.pi * t / 9.5 + rng.uniform(0.0, 2.0 * np.pi))
+    amp = 1.0 + 0.15 * np.sin(2.0 * np.pi * t / 13.0 + rng.uniform(0.0, 2.0 * np.pi))
+    ph = rng.uniform(0.0, 2.0 * np.pi, 2)
+    cycle = amp * (0.8 * np.sin(2.0 * np.pi * t + ph[0]) + 0.25 * np.sin(4.0 * np.pi * t + ph[1]))
+    y = trend + cycle + 0.1 * rng.standard_normal(n)
+    y = (y - y.mean()) / y.std()
+    theta = np.array([5.0, 1.0, 0.5, 1.0, 1.0, 20.0, 0.05])
+    return Series("co2_shaped", ["matern32", ("quasiperiodic", 6, "matern12")], theta, t, y)
