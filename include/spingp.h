@@ -202,6 +202,24 @@ spingp_status spingp_grad_posterior(const spingp_model* model, const double* t, 
                                     double* var_out, double* cov_lag1_out, void* ws, size_t ws_bytes,
                                     unsigned flags, void* stream);
 
+/* Prediction at new times (Eqs. mean4-mean6): the posterior mean and latent
+ * variance of f at n_star test times t_star, given n observations (t, y)
+ * (t ascending; NaN observations are missing).  The test times join the
+ * chain as steps with no observation (infinite noise), so one posterior pass
+ * over the n + n_star merged steps gives them; a test time equal to an
+ * observed one is placed after it.  t_star may be in any order (it is sorted
+ * on the device, stably); mean_out[j], var_out[j] belong to t_star[j].
+ * n = 0 gives the prior at t_star.  All arrays are device memory; ws is
+ * device scratch of spingp_predict_workspace_bytes(model, n, n_star) bytes
+ * (256-byte aligned); its status word reports ENOTSORTED for observed times
+ * out of order and ENONFINITE for a non-finite time.  SPINGP_PREDICTIVE
+ * adds the noise variance to var_out; SPINGP_SYNC as for the other calls.
+ * EINVAL for n < 0, n_star < 1 or a NULL argument. */
+size_t spingp_predict_workspace_bytes(const spingp_model* model, int64_t n, int64_t n_star);
+spingp_status spingp_predict(const spingp_model* model, const double* t, const double* y, int64_t n,
+                             const double* theta, const double* t_star, int64_t n_star, double* mean_out,
+                             double* var_out, void* ws, size_t ws_bytes, unsigned flags, void* stream);
+
 /* ---- batches of independent series ----------------------------------------
  * n_series series, each with its own hyperparameters, concatenated: series i
  * owns steps [offsets[i], offsets[i+1]) of t and y, with offsets[0] = 0,

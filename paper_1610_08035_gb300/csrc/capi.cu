@@ -425,6 +425,39 @@ spingp_status spingp_grad_posterior(const spingp_model* m, const double* t, cons
                flags, stream, n > 1 ? cov_lag1_out : nullptr);
 }
 
+size_t spingp_predict_workspace_bytes(const spingp_model* m, int64_t n, int64_t n_star) {
+    if (!m || n < 0 || n_star < 1) return 0;
+    const size_t inner = spingp_workspace_bytes(m, n + n_star, SPINGP_WS_POSTERIOR);
+    if (inner == 0) return 0;
+    return spg::PredictLayout(n, n_star).off_inner + inner;
+}
+
+spingp_status spingp_predict(const spingp_model* m, const double* t, const double* y, int64_t n,
+                             const double* theta, const double* t_star, int64_t n_star, double* mean_out,
+                             double* var_out, void* ws, size_t ws_bytes, unsigned flags, void* stream) {
+    if (!m || !theta || !t_star || !mean_out || !var_out || !ws || n < 0 || n_star < 1) return SPINGP_EINVAL;
+    if (n > 0 && (!t || !y)) return SPINGP_EINVAL;
+    if (((uintptr_t)ws & 255u) != 0) return SPINGP_EINVAL;
+    const size_t need = spingp_predict_workspace_bytes(m, n, n_star);
+    if (need == 0) return SPINGP_EUNSUPPORTED;
+    if (ws_bytes < need) return SPINGP_EINVAL;
+    spingp_status st = prepare_device();
+    if (st != SPINGP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const spg::PredictLayout lay(n, n_star);
+    char* w = (char*)ws;
+    if (spg::predict_prepare(t, y, n, t_star, n_star, ws, lay, s)) return SPINGP_ECUDA;
+    // the posterior over the merged series; a test point's NaN observation is missing
+    const unsigned inner_flags = SPINGP_MISSING_NAN | (flags & SPINGP_PREDICTIVE);
+    st = run(m, spg::MODE_POSTERIOR, (const double*)(w + lay.off_T), (const double*)(w + lay.off_Y), n + n_star,
+             theta, NULL, NULL, (double*)(w + lay.off_mean), (double*)(w + lay.off_var), w + lay.off_inner,
+             ws_bytes - lay.off_inner, inner_flags, stream);
+    if (st != SPINGP_OK) return st;
+    if (spg::predict_finish(t, n, n_star, ws, lay, mean_out, var_out, s)) return SPINGP_ECUDA;
+    if (flags & SPINGP_SYNC) return spingp_ws_status(ws, stream);
+    return SPINGP_OK;
+}
+
 int spingp_launch_count(const spingp_model* m, int64_t n, spingp_ws_kind what) {
     if (!m || n < 1) return -1;
     const int mode = what == SPINGP_WS_GRAD ? spg::MODE_GRAD

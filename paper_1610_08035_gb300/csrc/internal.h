@@ -77,6 +77,23 @@ int matern_launch_count(int b, int64_t n, int64_t L, int mode);
 // entries, theta in the same layout), predictive variances (latent + s_n)
 int grad_to_log(double* grad, const double* theta, int64_t count, cudaStream_t st);
 int add_noise(double* var, int64_t n, const double* s_n, cudaStream_t st);
+
+// prediction at new times: the call's workspace is [status word][merged
+// times and observations, the posterior over them, sort buffers][the
+// posterior call's own workspace at off_inner]
+struct PredictLayout {
+    size_t off_T, off_Y, off_mean, off_var, off_k0, off_k1, off_i0, off_i1, off_inner;
+    PredictLayout(int64_t n, int64_t m);
+};
+int predict_merge_passes(int64_t m);
+// sort the test times (keeping their positions) and merge them with the
+// observed ones into the layout's T, Y (NaN observations at test points)
+int predict_prepare(const double* t, const double* y, int64_t n, const double* ts, int64_t m, void* ws,
+                    const PredictLayout& lay, cudaStream_t st);
+// the test points' moments into the caller's order; the posterior's status
+// joined into the call's status word
+int predict_finish(const double* t, int64_t n, int64_t m, void* ws, const PredictLayout& lay, double* mean_out,
+                   double* var_out, cudaStream_t st);
 int add_noise_batched(double* var, const int64_t* offsets, int64_t n_series, const double* theta, int P,
                       cudaStream_t st);
 // a series split across ranks (phase 0: reduce this range to its element;

@@ -26,6 +26,7 @@ KINDS = {"matern12": 1, "matern32": 2, "matern52": 3, "periodic": 4, "quasiperio
 EXPORTS = ("spingp_model_create", "spingp_model_destroy", "spingp_num_params", "spingp_state_dim",
            "spingp_set_chunk_len", "spingp_get_chunk_len", "spingp_workspace_bytes", "spingp_loglik",
            "spingp_grad", "spingp_posterior", "spingp_posterior_lag1", "spingp_grad_posterior",
+           "spingp_predict_workspace_bytes", "spingp_predict",
            "spingp_workspace_bytes_batched", "spingp_loglik_batched",
            "spingp_grad_batched", "spingp_posterior_batched", "spingp_grad_posterior_batched", "spingp_launch_count",
            "spingp_launch_count_batched", "spingp_profile_enable",
@@ -80,6 +81,9 @@ def load():
     lib.spingp_posterior.argtypes = [vp, dp, dp, i64, dp, dp, dp, dp, vp, sz, u32, vp]
     lib.spingp_posterior_lag1.argtypes = [vp, dp, dp, i64, dp, dp, dp, dp, dp, vp, sz, u32, vp]
     lib.spingp_grad_posterior.argtypes = [vp, dp, dp, i64, dp, dp, dp, dp, dp, dp, vp, sz, u32, vp]
+    lib.spingp_predict_workspace_bytes.argtypes = [vp, i64, i64]
+    lib.spingp_predict_workspace_bytes.restype = sz
+    lib.spingp_predict.argtypes = [vp, dp, dp, i64, dp, dp, i64, dp, dp, vp, sz, u32, vp]
     lib.spingp_workspace_bytes_batched.argtypes = [vp, i64, i64, ctypes.c_int]
     lib.spingp_workspace_bytes_batched.restype = sz
     lib.spingp_loglik_batched.argtypes = [vp, dp, i64, i64, dp, dp, dp, dp, vp, sz, u32, vp]
@@ -239,6 +243,16 @@ def spingp_grad_posterior(h, t, y, n, theta, ll_out, grad_out, mean_out, var_out
     return load().spingp_grad_posterior(h, _ptr(t), _ptr(y), int(n), _ptr(theta), _ptr(ll_out), _ptr(grad_out),
                                         _ptr(mean_out), _ptr(var_out), _ptr(lag1_out), _ptr(ws), int(ws_bytes),
                                         int(flags), stream if stream is not None else _stream())
+
+
+def spingp_predict_workspace_bytes(h, n, n_star):
+    return load().spingp_predict_workspace_bytes(h, int(n), int(n_star))
+
+
+def spingp_predict(h, t, y, n, theta, t_star, n_star, mean_out, var_out, ws, ws_bytes, flags, stream=None):
+    return load().spingp_predict(h, _ptr(t), _ptr(y), int(n), _ptr(theta), _ptr(t_star), int(n_star),
+                                 _ptr(mean_out), _ptr(var_out), _ptr(ws), int(ws_bytes), int(flags),
+                                 stream if stream is not None else _stream())
 
 
 def spingp_workspace_bytes_batched(h, n_series, n_total, what):
@@ -657,23 +671,24 @@ class Model:
                                      self._flags(sync, missing, log_params, predictive)), "spingp_grad_posterior")
         return ll, g, mean, var, (lag[:n - 1] if lag is not None else None)
 
-    def predict(self, t, y, theta, t_star, predictive=False):
+    def predict(self, t, y, theta, t_star, predictive=False, sync=True):
         """Latent predictive mean and variance at new times t_star (Eqs.
-        mean4-mean6): the test times join the chain with missing (NaN)
-        observations, one posterior pass covers both.  t must be sorted;
-        t_star may be in any order.  Returns (mean, var) at t_star; with
-        predictive, var is that of a new observation (+ s_n)."""
+        mean4-mean6), through spingp_predict: the test times join the chain
+        with missing observations and one posterior pass covers both.  t
+        must be sorted; t_star may be in any order (it is sorted on the
+        device).  NaN observations in y are missing.  Returns (mean, var) at
+        t_star; with predictive, var is that of a new observation (+ s_n)."""
         _dev_f64(t_star, "t_star")
-        t_all = torch.cat([t, t_star])
-        y_all = torch.cat([y, torch.full_like(t_star, float("nan"))])
-        t_sorted, order = torch.sort(t_all, stable=True)
-        mean, var, _ = self.posterior(t_sorted, y_all[order].contiguous(), theta, with_loglik=False, missing=True,
-                                      predictive=predictive)
-        where = torch.empty_like(order)
-        where[order] = torch.arange(order.numel(), device=order.device)
-        idx = where[t.numel():]
-        return mean[idx], var[idx]
-
+        n = self._args(t, y, theta)
+        t_star = t_star.contiguous()
+        m = t_star.numel()
+        dev = t_star.device
+        ws = self._scratch(spingp_predict_workspace_bytes(self.h, n, m), dev, "spingp_predict")
+        mean = torch.empty(m, dtype=torch.float64, device=dev)
+        var = torch.empty(m, dtype=torch.float64, device=dev)
+        _check(spingp_predict(self.h, t, y, n, theta, t_star, m, mean, var, ws,
+                              ws.numel(), self._flags(sync, False, predictive=predictive)), "spingp_predict")
+        return mean, var
 
     def optimize(self, t, y, theta0, iterations=100, tol=1e-8, sync=True, missing=False):
         """Maximise the marginal likelihood from theta0 by scaled conjugate

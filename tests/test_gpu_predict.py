@@ -103,3 +103,69 @@ def test_missing_in_batches():
         llo, go, g1 = seq.grad("matern52", th[i], t[a:b], yi, l1=True)
         assert abs(ll[i] - llo) <= 1e-9 * abs(llo)
         assert np.all(np.abs(g[i] - go) <= 1e-8 * np.maximum(np.abs(go), g1))
+
+
+# ---- spingp_predict itself: the device sort of t*, the merge, the gather
+
+def _host_merged(t, y, ts):
+    """The merged series built on the host (observations first at equal
+    times, the test points in stable sorted order) and where each test point
+    lands: the same posterior pass, assembled without the predict kernels."""
+    order = np.argsort(ts, kind="stable")
+    T = np.concatenate([t, ts[order]])
+    Y = np.concatenate([y, np.full(len(ts), np.nan)])
+    o = np.argsort(T, kind="stable")
+    where = np.empty(len(T), dtype=np.int64)
+    where[o] = np.arange(len(T))
+    pos = np.empty(len(ts), dtype=np.int64)
+    pos[order] = where[len(t):]
+    return T[o], Y[o], pos
+
+
+@pytest.mark.parametrize("spec,theta", [MODELS[2], MODELS[3]])
+@pytest.mark.parametrize("n,m_new", [(1000, 1), (1000, 7), (5000, 4099), (3000, 100000)])
+def test_predict_equals_the_posterior_of_the_merged_series(spec, theta, n, m_new):
+    """Test times in any order, ties among themselves and with observed times,
+    outside the observed range: spingp_predict returns, bit for bit, the
+    posterior call's moments on the host-merged series at each test point."""
+    rng = np.random.default_rng(n + m_new)
+    t = synth.exp_times(n, 0.05, rng)
+    y = synth.two_sinusoids(t, 0.8, 1.0, 0.1, rng)
+    ts = rng.uniform(t[0] - 2.0, t[-1] + 2.0, m_new)
+    k = min(m_new, 5)
+    ts[:k] = t[rng.integers(0, n, k)]                 # tied with observed times
+    if m_new > 10:
+        ts[-4:] = ts[-8:-4]                           # tied among themselves
+    m = spingp.Model(spec)
+    mean, var = m.predict(_t(t), _t(y), _t(theta), _t(ts))
+    T, Y, pos = _host_merged(t, y, ts)
+    mp, vp, _ = m.posterior(_t(T), _t(Y), _t(theta), missing=True, with_loglik=False)
+    assert torch.equal(mean, mp[torch.tensor(pos, device=DEV)])
+    assert torch.equal(var, vp[torch.tensor(pos, device=DEV)])
+
+
+def test_predict_prior_flags_and_errors():
+    """No observations gives the prior (zero mean, variance s_f); the
+    predictive flag adds s_n; unsorted observed times and a NaN test time are
+    reported through the status word; bad arguments are EINVAL."""
+    m = spingp.Model("matern32")
+    th = _t([1.0, 1.7, 0.1])
+    ts = _t([3.0, -1.0, 2.5])
+    empty = torch.empty(0, dtype=torch.float64, device=DEV)
+    mean, var = m.predict(empty, empty, th, ts)
+    assert torch.all(mean == 0.0) and torch.allclose(var, torch.full_like(var, 1.7), rtol=1e-15, atol=0.0)
+    t, y = _t(np.arange(50) * 0.1), _t(np.sin(np.arange(50) * 0.1))
+    mean, var = m.predict(t, y, th, ts)
+    mean2, var2 = m.predict(t, y, th, ts, predictive=True)
+    assert torch.equal(mean, mean2) and torch.allclose(var2, var + 0.1, rtol=1e-15, atol=0.0)
+    with pytest.raises(spingp.SpinGPError) as e:
+        m.predict(torch.flip(t, [0]), y, th, ts)
+    assert e.value.status == spingp.ENOTSORTED
+    with pytest.raises(spingp.SpinGPError) as e:
+        m.predict(t, y, th, _t([0.5, float("nan"), 1.0]))
+    assert e.value.status == spingp.ENONFINITE
+    ws = torch.empty(spingp.spingp_predict_workspace_bytes(m.h, 50, 3), dtype=torch.uint8, device=DEV)
+    out = torch.empty(3, dtype=torch.float64, device=DEV)
+    assert spingp.spingp_predict(m.h, t, y, 50, th, ts, 0, out, out, ws, ws.numel(), spingp.SYNC) == spingp.EINVAL
+    assert spingp.spingp_predict(m.h, t, y, 50, th, ts, 3, None, out, ws, ws.numel(), spingp.SYNC) == spingp.EINVAL
+    assert spingp.spingp_predict(m.h, t, y, 50, th, ts, 3, out, out, ws, 256, spingp.SYNC) == spingp.EINVAL
