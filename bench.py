@@ -537,7 +537,19 @@ def next_rows(args, dev, flush, fp64_tflops):
                                  spingp.spingp_launch_count(m.h, n, spingp.WS_POSTERIOR),
                              "oracle": {"value": smp / osec, "unit": "steps/s", "cores": 1,
                                         "sample": "first %d steps, sequential C smoother" % smp}}
-    del T, Y, TH, m
+    # the same prediction through spingp_predict: the observed 90 % of the
+    # steps and the other 10 % as test times handed over in random order
+    # (sorted, merged and gathered on the device around the posterior pass)
+    obs = ~np.isnan(y)
+    ts = s.t[~obs][rng.permutation(int((~obs).sum()))]
+    TO, YO, TS = (torch.tensor(a, device=dev) for a in (s.t[obs], s.y[obs], ts))
+    m.predict(TO, YO, TH, TS)
+    pms = _time_calls(lambda: m.predict(TO, YO, TH, TS, sync=False), K, flush, torch)
+    res["prediction_n4m"]["predict_call"] = {
+        "value": n / (pms * 1e-3), "unit": "steps/s (observed + test)", "ms_per_call": pms,
+        "n_observed": int(obs.sum()), "n_test": len(ts), "test_order": "random",
+        "what": "spingp_predict: device merge sort of the test times, merge, posterior, gather"}
+    del T, Y, TH, m, TO, YO, TS
     torch.cuda.empty_cache()
     # ---- the posterior with the first off-diagonal of the selected inverse
     s = synth.single(WORKLOAD)

@@ -683,7 +683,13 @@ class Model:
         t_star = t_star.contiguous()
         m = t_star.numel()
         dev = t_star.device
-        ws = self._scratch(spingp_predict_workspace_bytes(self.h, n, m), dev, "spingp_predict")
+        nbytes = spingp_predict_workspace_bytes(self.h, n, m)
+        if nbytes == 0:
+            raise SpinGPError(EUNSUPPORTED, "spingp_predict_workspace_bytes")
+        ws = self._ws.get(("predict", dev))                  # kept between calls, grown when too small
+        if ws is None or ws.numel() < nbytes:
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+            self._ws[("predict", dev)] = ws
         mean = torch.empty(m, dtype=torch.float64, device=dev)
         var = torch.empty(m, dtype=torch.float64, device=dev)
         _check(spingp_predict(self.h, t, y, n, theta, t_star, m, mean, var, ws,
