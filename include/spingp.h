@@ -122,7 +122,13 @@ typedef enum { SPINGP_WS_LOGLIK = 0, SPINGP_WS_GRAD = 1, SPINGP_WS_POSTERIOR = 2
 /* Create a model handle from a host-side description (Sec. 2.1).  The handle
  * holds host constants only; it owns no device memory.  Returns EINVAL for a
  * malformed description and EUNSUPPORTED for a structure this build does not
- * run on the GPU.  *out is set to NULL on error. */
+ * run on the GPU.  *out is set to NULL on error.  The GPU runs:
+ *   - one Matern-1/2, 3/2 or 5/2 component (state dimension 1 to 3);
+ *   - sums of total state dimension <= 16 whose components are Matern-3/2,
+ *     periodic, quasi-periodic with a Matern-1/2 envelope, and at most one
+ *     EQ (every block of their transition is 2 x 2, or an EQ section).
+ * Other structures (a Matern-1/2 or 5/2 inside a sum, a Matern-3/2 or 5/2
+ * envelope, more than 16 states) return EUNSUPPORTED. */
 spingp_status spingp_model_create(const spingp_model_desc* desc, spingp_model** out);
 void spingp_model_destroy(spingp_model* model);
 

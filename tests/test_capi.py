@@ -58,9 +58,12 @@ def test_model_create_and_queries(lib):
 
 
 def test_model_create_rejects_bad_descriptions(lib):
-    with pytest.raises(spingp.SpinGPError) as e:
-        spingp.spingp_model_create(["matern52", "matern32"])
-    assert e.value.status == spingp.EUNSUPPORTED
+    # the structures the header lists as not run on the GPU
+    for spec in (["matern52", "matern32"], ["matern12", "matern32"], [("quasiperiodic", 2, "matern32")],
+                 ["matern32", ("periodic", 7)]):                                   # the last: 18 states
+        with pytest.raises(spingp.SpinGPError) as e:
+            spingp.spingp_model_create(spec)
+        assert e.value.status == spingp.EUNSUPPORTED, spec
     desc = spingp._Desc(1, (ctypes.c_int * 1)(9), None, None)
     h = ctypes.c_void_p()
     assert lib.spingp_model_create(ctypes.byref(desc), ctypes.byref(h)) == spingp.EINVAL
